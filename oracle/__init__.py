@@ -1,0 +1,182 @@
+"""Python access to the plain C FP64 oracle (``ssd_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+CPU-baseline leg of the benchmark, never by the library.  ``build()`` compiles
+the C file with gcc into ``oracle/_build/libssd_oracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ssd_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libssd_oracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, no vectorisation flags, no FMA contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", _SRC,
+                               "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        L.or_create.restype = ctypes.c_void_p
+        L.or_create.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _ip, ctypes.c_int, _ip, ctypes.c_int,
+                                _ip, ctypes.c_int, _ip, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_int, _dp, ctypes.c_char_p, ctypes.c_int]
+        L.or_destroy.argtypes = [ctypes.c_void_p]
+        L.or_residual.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
+        L.or_step.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_int]
+        L.or_sp_coords.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp]
+        L.or_sp_jacobian.argtypes = [ctypes.c_void_p, _dp]
+        L.or_points.argtypes = [ctypes.c_int, _dp, _dp]
+        L.or_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
+        L.or_lagrange.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+        L.or_projection.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
+        L.or_face_info.restype = ctypes.c_char_p
+        L.or_face_info.argtypes = [ctypes.c_void_p, _ip, _ip, _ip]
+        L.or_mortar_list.restype = ctypes.c_int
+        L.or_mortar_list.argtypes = [ctypes.c_void_p, ctypes.c_double, _ip, _ip, _dp, _dp, _dp, _dp]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def points(N: int):
+    Xs, Xf = np.zeros(N), np.zeros(N + 1)
+    lib().or_points(N, _d(Xs), _d(Xf))
+    return Xs, Xf
+
+
+def gauss_legendre(n: int):
+    x, w = np.zeros(n), np.zeros(n)
+    lib().or_gauss_legendre(n, _d(x), _d(w))
+    return x, w
+
+
+def lagrange(nodes, x):
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    x = np.ascontiguousarray(np.atleast_1d(x), dtype=np.float64)
+    val = np.zeros((len(x), len(nodes)))
+    der = np.zeros((len(x), len(nodes)))
+    lib().or_lagrange(_d(nodes), len(nodes), _d(x), len(x), _d(val), _d(der))
+    return val, der
+
+
+def projection(N: int, o: float, s: float):
+    Pf, Pb = np.zeros((N, N)), np.zeros((N, N))
+    lib().or_projection(N, o, s, _d(Pf), _d(Pb))
+    return Pf, Pb
+
+
+def params_array(params) -> np.ndarray:
+    return np.array([params.gamma, params.Rgas, params.mu, params.prandtl, params.omega,
+                     float(params.viscous), params.T_wall], dtype=np.float64)
+
+
+class Oracle:
+    """One mesh + order + flow parameters; residual and SSP-RK3 steps."""
+
+    def __init__(self, mesh: dict, N: int, params):
+        L = lib()
+        self.N = N
+        self.mesh = mesh
+        self.E = int(len(mesh["elem_nodes"]))
+        self._keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(x, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        xy = arr(mesh["xy"], np.float64)
+        en = arr(mesh["elem_nodes"], np.int32)
+        zone = arr(mesh["elem_zone"], np.int32)
+        arc = arr(mesh["edge_arc"], np.int32)
+        bf = arr(mesh["bfaces"], np.int32)
+        pf = arr(mesh["pfaces"], np.int32)
+        Lf = arr(mesh["ifaces_L"], np.int32)
+        Rf = arr(mesh["ifaces_R"], np.int32)
+        prm = arr(params_array(params), np.float64)
+        err = ctypes.create_string_buffer(256)
+        self._h = L.or_create(len(xy), _d(xy), self.E, _i(en), _i(zone), _i(arc), len(bf), _i(bf), len(pf),
+                              _i(pf), len(Lf), _i(Lf), len(Rf), _i(Rf), float(mesh["center"][0]),
+                              float(mesh["center"][1]), float(mesh["r_interface"]), N, _d(prm), err, 256)
+        if not self._h:
+            raise ValueError("oracle mesh set-up failed: " + err.value.decode())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or_destroy(h)
+            self._h = None
+
+    @property
+    def shape(self):
+        return (self.E, 4, self.N, self.N)
+
+    def sp_coords(self, t: float = 0.0):
+        out = np.zeros((self.E, self.N, self.N, 2))
+        lib().or_sp_coords(self._h, t, _d(out))
+        return out[..., 0], out[..., 1]
+
+    def sp_jacobian(self):
+        out = np.zeros((self.E, self.N, self.N))
+        lib().or_sp_jacobian(self._h, _d(out))
+        return out
+
+    def residual(self, Q, t: float = 0.0):
+        Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(self.shape)
+        R = np.zeros(self.shape)
+        lib().or_residual(self._h, _d(Q), t, _d(R))
+        return R
+
+    def step(self, Q, t: float, dt: float, nsteps: int = 1):
+        Q = np.array(Q, dtype=np.float64, order="C").reshape(self.shape)
+        tt = np.array([t], dtype=np.float64)
+        lib().or_step(self._h, _d(Q), _d(tt), dt, nsteps)
+        return Q, float(tt[0])
+
+    def face_info(self):
+        n = 4 * self.E
+        kind, nbr, rev = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32)
+        lib().or_face_info(self._h, _i(kind), _i(nbr), _i(rev))
+        return kind, nbr, rev
+
+    def mortars(self, t: float):
+        n = len(self.mesh["ifaces_L"]) + len(self.mesh["ifaces_R"])
+        lf, rf = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        oL, sL, oR, sR = (np.zeros(n) for _ in range(4))
+        k = lib().or_mortar_list(self._h, t, _i(lf), _i(rf), _d(oL), _d(sL), _d(oR), _d(sR))
+        return {"lf": lf[:k], "rf": rf[:k], "oL": oL[:k], "sL": sL[:k], "oR": oR[:k], "sR": sR[:k]}
+
+    def state_from(self, field_fn, t: float = 0.0):
+        """Sample an analytic field at the SPs -> Q array [E][4][N][N]."""
+        x, y = self.sp_coords(t)
+        q = field_fn(x, y)  # (..., 4)
+        return np.ascontiguousarray(np.moveaxis(q, -1, 1))

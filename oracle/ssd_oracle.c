@@ -1,0 +1,1171 @@
+/*
+ * ssd_oracle.c -- plain, slow FP64 CPU oracle of the sliding-mesh spectral
+ * difference (SSD) method of Zhang & Liang (arXiv:1503.02198).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  It shares no code, header,
+ * table or constant with the CUDA library: every basis, geometry, flux and
+ * projection below is written out here from the paper.
+ *
+ * It follows the paper's steps in order, element by element, in plain loops:
+ *   Sec. 3.1: SPs (Chebyshev-Gauss) and FPs (Legendre-Gauss + end points),
+ *             Lagrange bases (Eqs. hbasis, lbasis), solution polynomial
+ *             (Eq. Qt) evaluated at the FPs,
+ *   Sec. 2.1/2.2: inviscid fluxes with the grid-velocity terms of the
+ *             rotating zone, viscous fluxes,
+ *   Sec. 2.3: transformed fluxes (Eq. transform_relation),
+ *   Sec. 3.1: Rusanov common flux on conforming faces,
+ *   Sec. 3.2: mortars on the sliding interface: Eq. xz, projection of face
+ *             data to mortars (Eqs. prjQ1-2, mortarM, mortarS), Rusanov on the
+ *             mortar, projection of the common flux back (Eqs. prjF1-2), and the
+ *             viscous mortar procedure,
+ *   Sec. 3.1: divergence of the flux polynomials (Eqs. Ft, Gt) at the SPs,
+ *   Sec. 3: explicit SSP Runge-Kutta (three-stage Shu-Osher form).
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *   - projections are defined by the integral statements prjQ1 / prjF1;
+ *     the integrals use exact (N+2)-point Gauss-Legendre quadrature;
+ *   - the quantity projected back is the physical normal flux per unit
+ *     length, oriented from the rotating (L) side to the stationary (R) side;
+ *     the element end-FP flux is then  sigma_f |S| F.n_out;
+ *   - interface faces are exact circular arcs, parameterised linearly in
+ *     angle, so o(t), s(t) are angle ratios;
+ *   - a face whose parameter runs clockwise is handled by reversing its point
+ *     order (the SP set is symmetric);
+ *   - Rusanov wave speed max(|u_n - v_gn| + c) over both sides;
+ *   - conforming viscous coupling: common Q = average, common viscous flux =
+ *     average of both sides' viscous flux evaluated with the common Q;
+ *   - isothermal moving walls through a ghost state (velocity 2 V_w - V,
+ *     wall temperature, interior pressure).
+ */
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXN 12
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* parameters and mesh                                                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double gamma, Rgas, mu, prandtl, omega, T_wall;
+  int viscous;
+} or_params;
+
+enum { FK_NONE = -1, FK_CONF = 0, FK_PERIODIC = 1, FK_BOUNDARY = 2, FK_IFACE_L = 3, FK_IFACE_R = 4 };
+
+typedef struct {
+  int N;
+  double Xs[OR_MAXN];     /* solution points X_s, s = 1..N (stored 0-based) */
+  double Xf[OR_MAXN + 1]; /* flux points X_{s+1/2}, s = 0..N */
+  /* mesh */
+  int nn, ne;
+  double *xy;
+  int *en, *zone, *arc;
+  double cx, cy, rI;
+  /* per element face e*4+f */
+  int *fkind, *fnbr, *frev, *ftag;
+  /* interface faces, sorted counter-clockwise */
+  int nL, nR;
+  int *Lef, *Ref;           /* element-face index */
+  double *La, *Lw, *Ra, *Rw; /* CCW start angle at t = 0 (in [0, 2pi)) and angular width */
+  int *Lrev, *Rrev;         /* 1 if the face parameter runs clockwise */
+  or_params prm;
+  char err[256];
+} or_mesh;
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1: solution and flux points, Lagrange bases                         */
+/* ------------------------------------------------------------------------ */
+
+/* Legendre polynomial P_n and derivative on [-1, 1] (three-term recurrence) */
+static void legendre(int n, double x, double *P, double *dP) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { *P = 1.0; *dP = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  *dP = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+/* roots of P_n on [-1,1] in ascending order, by Newton iteration; weights of
+ * the Gauss-Legendre rule 2 / ((1 - x^2) P_n'(x)^2) */
+static void gauss_legendre(int n, double *x, double *w) {
+  for (int k = 1; k <= n; ++k) {
+    double r = cos(OR_PI * (k - 0.25) / (n + 0.5));
+    for (int it = 0; it < 200; ++it) {
+      double P, dP;
+      legendre(n, r, &P, &dP);
+      double dr = P / dP;
+      r -= dr;
+      if (fabs(dr) < 1e-17) break;
+    }
+    double P, dP;
+    legendre(n, r, &P, &dP);
+    x[n - k] = r; /* cos(...) decreases with k */
+    w[n - k] = 2.0 / ((1.0 - r * r) * dP * dP);
+  }
+}
+
+static void make_points(int N, double *Xs, double *Xf) {
+  for (int s = 1; s <= N; ++s) Xs[s - 1] = 0.5 * (1.0 - cos((2.0 * s - 1.0) * OR_PI / (2.0 * N)));
+  double z[OR_MAXN], w[OR_MAXN];
+  Xf[0] = 0.0;
+  Xf[N] = 1.0;
+  if (N >= 2) {
+    gauss_legendre(N - 1, z, w);
+    for (int k = 0; k < N - 1; ++k) Xf[k + 1] = 0.5 * (1.0 + z[k]);
+  }
+}
+
+/* Lagrange basis on nodes[0..n-1], product formula (Eqs. hbasis / lbasis) */
+static double lag(const double *nodes, int n, int i, double x) {
+  double v = 1.0;
+  for (int s = 0; s < n; ++s)
+    if (s != i) v *= (x - nodes[s]) / (nodes[i] - nodes[s]);
+  return v;
+}
+
+static double lag_d(const double *nodes, int n, int i, double x) {
+  double sum = 0.0;
+  for (int m = 0; m < n; ++m) {
+    if (m == i) continue;
+    double v = 1.0 / (nodes[i] - nodes[m]);
+    for (int s = 0; s < n; ++s)
+      if (s != i && s != m) v *= (x - nodes[s]) / (nodes[i] - nodes[s]);
+    sum += v;
+  }
+  return sum;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry: iso-parametric map of each cell to [0,1]^2 (Sec. 3.1), rigid   */
+/* rotation of the rotating zone (Sec. 2.2), metrics (Sec. 2.3)              */
+/* ------------------------------------------------------------------------ */
+
+static const int FACE_A[4] = {0, 1, 3, 0}; /* start corner of face f's parameter */
+static const int FACE_B[4] = {1, 2, 2, 3}; /* end corner */
+
+/* point and derivative of an edge curve from P to Q at parameter u */
+static void edge_curve(const or_mesh *m, double px, double py, double qx, double qy, int arc, double u,
+                       double *x, double *y, double *dx, double *dy) {
+  if (!arc) {
+    *x = px + u * (qx - px);
+    *y = py + u * (qy - py);
+    *dx = qx - px;
+    *dy = qy - py;
+    return;
+  }
+  double ax = px - m->cx, ay = py - m->cy, bx = qx - m->cx, by = qy - m->cy;
+  double r = sqrt(ax * ax + ay * ay);
+  double phi0 = atan2(ay, ax);
+  double dphi = atan2(ax * by - ay * bx, ax * bx + ay * by);
+  double phi = phi0 + u * dphi;
+  *x = m->cx + r * cos(phi);
+  *y = m->cy + r * sin(phi);
+  *dx = -r * dphi * sin(phi);
+  *dy = r * dphi * cos(phi);
+}
+
+/* Transfinite (Coons) map of element e at (xi, eta) at t = 0: position and the
+ * four derivatives.  With straight edges it is the 4-node bilinear map; an arc
+ * edge is reproduced exactly. */
+static void map_t0(const or_mesh *m, int e, double xi, double eta, double *g) {
+  const int *n = m->en + 4 * e;
+  double X[4], Y[4];
+  for (int k = 0; k < 4; ++k) {
+    X[k] = m->xy[2 * n[k]];
+    Y[k] = m->xy[2 * n[k] + 1];
+  }
+  const int *a = m->arc + 4 * e;
+  double Bx, By, dBx, dBy, Tx, Ty, dTx, dTy, Lx, Ly, dLx, dLy, Rx, Ry, dRx, dRy;
+  edge_curve(m, X[0], Y[0], X[1], Y[1], a[0], xi, &Bx, &By, &dBx, &dBy);   /* f0, eta = 0 */
+  edge_curve(m, X[1], Y[1], X[2], Y[2], a[1], eta, &Rx, &Ry, &dRx, &dRy);  /* f1, xi = 1 */
+  edge_curve(m, X[3], Y[3], X[2], Y[2], a[2], xi, &Tx, &Ty, &dTx, &dTy);   /* f2, eta = 1 */
+  edge_curve(m, X[0], Y[0], X[3], Y[3], a[3], eta, &Lx, &Ly, &dLx, &dLy);  /* f3, xi = 0 */
+  double x = (1 - eta) * Bx + eta * Tx + (1 - xi) * Lx + xi * Rx -
+             ((1 - xi) * (1 - eta) * X[0] + xi * (1 - eta) * X[1] + xi * eta * X[2] + (1 - xi) * eta * X[3]);
+  double y = (1 - eta) * By + eta * Ty + (1 - xi) * Ly + xi * Ry -
+             ((1 - xi) * (1 - eta) * Y[0] + xi * (1 - eta) * Y[1] + xi * eta * Y[2] + (1 - xi) * eta * Y[3]);
+  double x_xi = (1 - eta) * dBx + eta * dTx - Lx + Rx -
+                (-(1 - eta) * X[0] + (1 - eta) * X[1] + eta * X[2] - eta * X[3]);
+  double y_xi = (1 - eta) * dBy + eta * dTy - Ly + Ry -
+                (-(1 - eta) * Y[0] + (1 - eta) * Y[1] + eta * Y[2] - eta * Y[3]);
+  double x_eta = -Bx + Tx + (1 - xi) * dLx + xi * dRx -
+                 (-(1 - xi) * X[0] - xi * X[1] + xi * X[2] + (1 - xi) * X[3]);
+  double y_eta = -By + Ty + (1 - xi) * dLy + xi * dRy -
+                 (-(1 - xi) * Y[0] - xi * Y[1] + xi * Y[2] + (1 - xi) * Y[3]);
+  g[0] = x; g[1] = y; g[2] = x_xi; g[3] = y_xi; g[4] = x_eta; g[5] = y_eta;
+}
+
+/* Map at time t: cells of the rotating zone are rotated rigidly about the
+ * centre by theta = omega t (Sec. 2.2: coordinates updated analytically). */
+static void map_at(const or_mesh *m, int e, double xi, double eta, double t, double *g) {
+  map_t0(m, e, xi, eta, g);
+  if (m->zone[e] == 1) {
+    double th = m->prm.omega * t, c = cos(th), s = sin(th);
+    double dx = g[0] - m->cx, dy = g[1] - m->cy;
+    g[0] = m->cx + c * dx - s * dy;
+    g[1] = m->cy + s * dx + c * dy;
+    for (int k = 2; k < 6; k += 2) {
+      double vx = g[k], vy = g[k + 1];
+      g[k] = c * vx - s * vy;
+      g[k + 1] = s * vx + c * vy;
+    }
+  }
+}
+
+/* grid velocity (u_g, v_g) = omega x r on the rotating zone, 0 elsewhere */
+static void grid_velocity(const or_mesh *m, int e, double x, double y, double *ug, double *vg) {
+  if (m->zone[e] == 1) {
+    *ug = -m->prm.omega * (y - m->cy);
+    *vg = m->prm.omega * (x - m->cx);
+  } else {
+    *ug = 0.0;
+    *vg = 0.0;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2: physical fluxes                                                    */
+/* ------------------------------------------------------------------------ */
+
+static double pressure(const or_params *p, const double *q) {
+  return (p->gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+}
+
+/* inviscid fluxes with grid-velocity terms (Sec. 2.2) */
+static void inviscid_flux(const or_params *p, const double *q, double ug, double vg, double *F, double *G) {
+  double u = q[1] / q[0], v = q[2] / q[0], pr = pressure(p, q);
+  F[0] = q[1];
+  F[1] = q[1] * u + pr;
+  F[2] = q[1] * v;
+  F[3] = (q[3] + pr) * u;
+  G[0] = q[2];
+  G[1] = q[2] * u;
+  G[2] = q[2] * v + pr;
+  G[3] = (q[3] + pr) * v;
+  for (int k = 0; k < 4; ++k) {
+    F[k] -= ug * q[k];
+    G[k] -= vg * q[k];
+  }
+}
+
+/* viscous fluxes (Sec. 2.1) from Q and the physical gradients dQ/dx, dQ/dy of
+ * the conservative variables; includes the leading minus sign of the paper */
+static void viscous_flux(const or_params *p, const double *q, const double *qx, const double *qy, double *F,
+                         double *G) {
+  double rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  double ux = (qx[1] - u * qx[0]) / rho, uy = (qy[1] - u * qy[0]) / rho;
+  double vx = (qx[2] - v * qx[0]) / rho, vy = (qy[2] - v * qy[0]) / rho;
+  double pr = pressure(p, q);
+  double T = pr / (rho * p->Rgas);
+  double px = (p->gamma - 1.0) * (qx[3] - (u * qx[1] + v * qx[2] - 0.5 * (u * u + v * v) * qx[0]));
+  double py = (p->gamma - 1.0) * (qy[3] - (u * qy[1] + v * qy[2] - 0.5 * (u * u + v * v) * qy[0]));
+  double Tx = (px - p->Rgas * T * qx[0]) / (rho * p->Rgas);
+  double Ty = (py - p->Rgas * T * qy[0]) / (rho * p->Rgas);
+  double mu = p->mu, lam = -2.0 / 3.0 * mu;
+  double kc = mu * p->gamma * p->Rgas / ((p->gamma - 1.0) * p->prandtl);
+  double txx = 2.0 * mu * ux + lam * (ux + vy);
+  double tyy = 2.0 * mu * vy + lam * (ux + vy);
+  double txy = mu * (uy + vx);
+  F[0] = 0.0;
+  F[1] = -txx;
+  F[2] = -txy;
+  F[3] = -(u * txx + v * txy + kc * Tx);
+  G[0] = 0.0;
+  G[1] = -txy;
+  G[2] = -tyy;
+  G[3] = -(u * txy + v * tyy + kc * Ty);
+}
+
+/* Rusanov common normal flux (Sec. 3.1) across a face with unit normal n
+ * pointing from L to R; vgn is the grid velocity normal to the face. */
+static void rusanov(const or_params *p, const double *qL, const double *qR, double nx, double ny, double vgn,
+                    double *Fn) {
+  double FL[4], GL[4], FR[4], GR[4];
+  inviscid_flux(p, qL, 0.0, 0.0, FL, GL);
+  inviscid_flux(p, qR, 0.0, 0.0, FR, GR);
+  double unL = (qL[1] * nx + qL[2] * ny) / qL[0], unR = (qR[1] * nx + qR[2] * ny) / qR[0];
+  double cL = sqrt(p->gamma * pressure(p, qL) / qL[0]), cR = sqrt(p->gamma * pressure(p, qR) / qR[0]);
+  double lamL = fabs(unL - vgn) + cL, lamR = fabs(unR - vgn) + cR;
+  double lam = lamL > lamR ? lamL : lamR;
+  for (int k = 0; k < 4; ++k) {
+    double fL = FL[k] * nx + GL[k] * ny - vgn * qL[k];
+    double fR = FR[k] * nx + GR[k] * ny - vgn * qR[k];
+    Fn[k] = 0.5 * (fL + fR) - 0.5 * lam * (qR[k] - qL[k]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.2: mortar matrices                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* M_ij = int_0^1 h_i h_j dz and S_ij = int_0^1 h_i(o + s z) h_j(z) dz (Eqs.
+ * mortarM, mortarS), by (N+2)-point Gauss-Legendre on [0,1] (exact: the
+ * integrands have degree 2N-2). */
+static void mortar_MS(int N, const double *Xs, double o, double s, double *M, double *S) {
+  int nq = N + 2;
+  double z[OR_MAXN + 2], w[OR_MAXN + 2];
+  gauss_legendre(nq, z, w);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double mij = 0.0, sij = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        double zq = 0.5 * (1.0 + z[q]), wq = 0.5 * w[q];
+        mij += wq * lag(Xs, N, i, zq) * lag(Xs, N, j, zq);
+        sij += wq * lag(Xs, N, i, o + s * zq) * lag(Xs, N, j, zq);
+      }
+      M[i * N + j] = mij;
+      S[i * N + j] = sij;
+    }
+}
+
+/* inverse of a small dense matrix by Gauss-Jordan with partial pivoting */
+static int invert(int n, const double *A, double *Ainv) {
+  double W[OR_MAXN * 2 * OR_MAXN];
+  int w2 = 2 * n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < w2; ++j) W[i * w2 + j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(W[r * w2 + c]) > fabs(W[piv * w2 + c])) piv = r;
+    if (W[piv * w2 + c] == 0.0) return -1;
+    if (piv != c)
+      for (int j = 0; j < w2; ++j) {
+        double tmp = W[c * w2 + j];
+        W[c * w2 + j] = W[piv * w2 + j];
+        W[piv * w2 + j] = tmp;
+      }
+    double d = W[c * w2 + c];
+    for (int j = 0; j < w2; ++j) W[c * w2 + j] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = W[r * w2 + c];
+      for (int j = 0; j < w2; ++j) W[r * w2 + j] -= f * W[c * w2 + j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ainv[i * n + j] = W[i * w2 + n + j];
+  return 0;
+}
+
+/* Projection matrices for a mortar with offset o and scale s relative to a face:
+ *   forward  (Eq. prjQ1):  M Q^Xi = S^T Q^Omega  ->  Pf = M^-1 S^T
+ *   backward (Eq. prjF1):  M F^Omega = sum_k s_k S_k F^Xi_k  ->  Pb = s M^-1 S  */
+void or_projection(int N, double o, double s, double *Pf, double *Pb) {
+  double Xs[OR_MAXN], Xf[OR_MAXN + 1], M[OR_MAXN * OR_MAXN], S[OR_MAXN * OR_MAXN], Mi[OR_MAXN * OR_MAXN];
+  make_points(N, Xs, Xf);
+  mortar_MS(N, Xs, o, s, M, S);
+  invert(N, M, Mi);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double f = 0.0, b = 0.0;
+      for (int k = 0; k < N; ++k) {
+        f += Mi[i * N + k] * S[j * N + k];
+        b += Mi[i * N + k] * S[k * N + j];
+      }
+      Pf[i * N + j] = f;
+      Pb[i * N + j] = s * b;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* mesh set-up: face table, interface lists                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { int a, b, ef; } edge_key;
+
+static int cmp_edge(const void *x, const void *y) {
+  const edge_key *p = x, *q = y;
+  if (p->a != q->a) return p->a < q->a ? -1 : 1;
+  if (p->b != q->b) return p->b < q->b ? -1 : 1;
+  return p->ef < q->ef ? -1 : (p->ef > q->ef);
+}
+
+static void face_nodes(const or_mesh *m, int ef, int *na, int *nb) {
+  int e = ef / 4, f = ef % 4;
+  *na = m->en[4 * e + FACE_A[f]];
+  *nb = m->en[4 * e + FACE_B[f]];
+}
+
+static double wrap2pi(double a) {
+  double r = fmod(a, 2.0 * OR_PI);
+  if (r < 0) r += 2.0 * OR_PI;
+  return r;
+}
+
+/* signed angle in (-pi, pi] */
+static double wrap_pi(double a) {
+  double r = wrap2pi(a + OR_PI) - OR_PI;
+  return r;
+}
+
+static int setup_interface_side(or_mesh *m, int n, const int *faces, int kind, int **ef_out, double **a_out,
+                                double **w_out, int **rev_out) {
+  int *ef = malloc(sizeof(int) * (n > 0 ? n : 1));
+  double *a = malloc(sizeof(double) * (n > 0 ? n : 1)), *w = malloc(sizeof(double) * (n > 0 ? n : 1));
+  int *rv = malloc(sizeof(int) * (n > 0 ? n : 1));
+  for (int k = 0; k < n; ++k) {
+    int e = faces[2 * k], f = faces[2 * k + 1], na, nb;
+    ef[k] = 4 * e + f;
+    face_nodes(m, ef[k], &na, &nb);
+    double pa = atan2(m->xy[2 * na + 1] - m->cy, m->xy[2 * na] - m->cx);
+    double pb = atan2(m->xy[2 * nb + 1] - m->cy, m->xy[2 * nb] - m->cx);
+    double d = wrap_pi(pb - pa);
+    if (d > 0) {
+      a[k] = wrap2pi(pa);
+      w[k] = d;
+      rv[k] = 0;
+    } else {
+      a[k] = wrap2pi(pb);
+      w[k] = -d;
+      rv[k] = 1;
+    }
+    if (m->fkind[ef[k]] != FK_NONE) {
+      snprintf(m->err, sizeof m->err, "interface face %d/%d already classified", e, f);
+      return -1;
+    }
+    m->fkind[ef[k]] = kind;
+  }
+  /* sort counter-clockwise by start angle (insertion sort; plain) */
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && a[j] < a[j - 1]; --j) {
+      double ta = a[j]; a[j] = a[j - 1]; a[j - 1] = ta;
+      double tw = w[j]; w[j] = w[j - 1]; w[j - 1] = tw;
+      int te = ef[j]; ef[j] = ef[j - 1]; ef[j - 1] = te;
+      int tr = rv[j]; rv[j] = rv[j - 1]; rv[j - 1] = tr;
+    }
+  double total = 0.0;
+  for (int k = 0; k < n; ++k) total += w[k];
+  if (n > 0 && fabs(total - 2.0 * OR_PI) > 1e-9) {
+    snprintf(m->err, sizeof m->err, "interface side does not close (%.12f)", total);
+    return -1;
+  }
+  *ef_out = ef; *a_out = a; *w_out = w; *rev_out = rv;
+  return 0;
+}
+
+or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *zone, const int *arc, int nb,
+                   const int *bfaces, int np, const int *pfaces, int nL, const int *Lf, int nR, const int *Rf,
+                   double cx, double cy, double rI, int N, const double *prm_in, char *err, int errlen) {
+  or_mesh *m = calloc(1, sizeof(or_mesh));
+  m->N = N;
+  make_points(N, m->Xs, m->Xf);
+  m->nn = nn;
+  m->ne = ne;
+  m->xy = malloc(sizeof(double) * 2 * nn);
+  memcpy(m->xy, xy, sizeof(double) * 2 * nn);
+  m->en = malloc(sizeof(int) * 4 * ne);
+  memcpy(m->en, en, sizeof(int) * 4 * ne);
+  m->zone = malloc(sizeof(int) * ne);
+  memcpy(m->zone, zone, sizeof(int) * ne);
+  m->arc = malloc(sizeof(int) * 4 * ne);
+  memcpy(m->arc, arc, sizeof(int) * 4 * ne);
+  m->cx = cx;
+  m->cy = cy;
+  m->rI = rI;
+  m->prm.gamma = prm_in[0];
+  m->prm.Rgas = prm_in[1];
+  m->prm.mu = prm_in[2];
+  m->prm.prandtl = prm_in[3];
+  m->prm.omega = prm_in[4];
+  m->prm.viscous = (int)prm_in[5];
+  m->prm.T_wall = prm_in[6];
+  int nf = 4 * ne;
+  m->fkind = malloc(sizeof(int) * nf);
+  m->fnbr = malloc(sizeof(int) * nf);
+  m->frev = malloc(sizeof(int) * nf);
+  m->ftag = malloc(sizeof(int) * nf);
+  for (int k = 0; k < nf; ++k) { m->fkind[k] = FK_NONE; m->fnbr[k] = -1; m->frev[k] = 0; m->ftag[k] = 0; }
+  int rc = 0;
+  /* boundary faces */
+  for (int k = 0; k < nb && !rc; ++k) {
+    int ef = 4 * bfaces[3 * k] + bfaces[3 * k + 1];
+    if (m->fkind[ef] != FK_NONE) { snprintf(m->err, sizeof m->err, "boundary face repeated"); rc = -1; }
+    m->fkind[ef] = FK_BOUNDARY;
+    m->ftag[ef] = bfaces[3 * k + 2];
+  }
+  /* periodic pairs: orientation from the translation between the faces */
+  for (int k = 0; k < np && !rc; ++k) {
+    int efA = 4 * pfaces[4 * k] + pfaces[4 * k + 1], efB = 4 * pfaces[4 * k + 2] + pfaces[4 * k + 3];
+    int a0, a1, b0, b1;
+    face_nodes(m, efA, &a0, &a1);
+    face_nodes(m, efB, &b0, &b1);
+    double dx = 0.5 * (m->xy[2 * b0] + m->xy[2 * b1] - m->xy[2 * a0] - m->xy[2 * a1]);
+    double dy = 0.5 * (m->xy[2 * b0 + 1] + m->xy[2 * b1 + 1] - m->xy[2 * a0 + 1] - m->xy[2 * a1 + 1]);
+    double ds = hypot(m->xy[2 * a0] + dx - m->xy[2 * b0], m->xy[2 * a0 + 1] + dy - m->xy[2 * b0 + 1]);
+    double dr = hypot(m->xy[2 * a0] + dx - m->xy[2 * b1], m->xy[2 * a0 + 1] + dy - m->xy[2 * b1 + 1]);
+    int rev = dr < ds;
+    if (m->fkind[efA] != FK_NONE || m->fkind[efB] != FK_NONE) {
+      snprintf(m->err, sizeof m->err, "periodic face repeated");
+      rc = -1;
+    }
+    m->fkind[efA] = m->fkind[efB] = FK_PERIODIC;
+    m->fnbr[efA] = efB;
+    m->fnbr[efB] = efA;
+    m->frev[efA] = m->frev[efB] = rev;
+  }
+  if (!rc) rc = setup_interface_side(m, nL, Lf, FK_IFACE_L, &m->Lef, &m->La, &m->Lw, &m->Lrev);
+  if (!rc) rc = setup_interface_side(m, nR, Rf, FK_IFACE_R, &m->Ref, &m->Ra, &m->Rw, &m->Rrev);
+  m->nL = nL;
+  m->nR = nR;
+  /* conforming faces by shared node pairs */
+  if (!rc) {
+    edge_key *keys = malloc(sizeof(edge_key) * nf);
+    int nk = 0;
+    for (int ef = 0; ef < nf; ++ef) {
+      if (m->fkind[ef] != FK_NONE) continue;
+      int a, b;
+      face_nodes(m, ef, &a, &b);
+      keys[nk].a = a < b ? a : b;
+      keys[nk].b = a < b ? b : a;
+      keys[nk].ef = ef;
+      ++nk;
+    }
+    qsort(keys, nk, sizeof(edge_key), cmp_edge);
+    for (int k = 0; k < nk && !rc; ++k) {
+      if (k + 1 < nk && keys[k + 1].a == keys[k].a && keys[k + 1].b == keys[k].b) {
+        if (k + 2 < nk && keys[k + 2].a == keys[k].a && keys[k + 2].b == keys[k].b) {
+          snprintf(m->err, sizeof m->err, "edge shared by more than two cells");
+          rc = -1;
+          break;
+        }
+        int efA = keys[k].ef, efB = keys[k + 1].ef, a0, a1, b0, b1;
+        face_nodes(m, efA, &a0, &a1);
+        face_nodes(m, efB, &b0, &b1);
+        m->fkind[efA] = m->fkind[efB] = FK_CONF;
+        m->fnbr[efA] = efB;
+        m->fnbr[efB] = efA;
+        m->frev[efA] = m->frev[efB] = (a0 != b0);
+        if (m->zone[efA / 4] != m->zone[efB / 4]) {
+          snprintf(m->err, sizeof m->err, "conforming face joins two zones");
+          rc = -1;
+        }
+        ++k;
+      } else {
+        snprintf(m->err, sizeof m->err, "face %d of element %d has no neighbour and no boundary condition",
+                 keys[k].ef % 4, keys[k].ef / 4);
+        rc = -1;
+      }
+    }
+    free(keys);
+  }
+  if (rc) {
+    if (err) snprintf(err, errlen, "%s", m->err);
+    return NULL;
+  }
+  return m;
+}
+
+void or_destroy(or_mesh *m) {
+  if (!m) return;
+  free(m->xy); free(m->en); free(m->zone); free(m->arc);
+  free(m->fkind); free(m->fnbr); free(m->frev); free(m->ftag);
+  free(m->Lef); free(m->La); free(m->Lw); free(m->Lrev);
+  free(m->Ref); free(m->Ra); free(m->Rw); free(m->Rrev);
+  free(m);
+}
+
+/* physical coordinates of the SPs at time t, [E][N][N][2] (row j = eta index) */
+void or_sp_coords(const or_mesh *m, double t, double *out) {
+  int N = m->N;
+  double g[6];
+  for (int e = 0; e < m->ne; ++e)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        map_at(m, e, m->Xs[i], m->Xs[j], t, g);
+        out[((e * N + j) * N + i) * 2] = g[0];
+        out[((e * N + j) * N + i) * 2 + 1] = g[1];
+      }
+}
+
+/* |J| at the SPs, [E][N][N] */
+void or_sp_jacobian(const or_mesh *m, double *out) {
+  int N = m->N;
+  double g[6];
+  for (int e = 0; e < m->ne; ++e)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        map_t0(m, e, m->Xs[i], m->Xs[j], g);
+        out[(e * N + j) * N + i] = g[2] * g[5] - g[4] * g[3];
+      }
+}
+
+void or_points(int N, double *Xs, double *Xf) { make_points(N, Xs, Xf); }
+
+void or_gauss_legendre(int n, double *x, double *w) { gauss_legendre(n, x, w); }
+
+void or_lagrange(const double *nodes, int n, const double *x, int nx, double *val, double *der) {
+  for (int p = 0; p < nx; ++p)
+    for (int i = 0; i < n; ++i) {
+      val[p * n + i] = lag(nodes, n, i, x[p]);
+      der[p * n + i] = lag_d(nodes, n, i, x[p]);
+    }
+}
+
+const char *or_face_info(const or_mesh *m, int *kind, int *nbr, int *rev) {
+  for (int k = 0; k < 4 * m->ne; ++k) {
+    kind[k] = m->fkind[k];
+    nbr[k] = m->fnbr[k];
+    rev[k] = m->frev[k];
+  }
+  return m->err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* residual                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* index helpers.  Q layout [E][4][N][N] with row j (eta) and column i (xi).
+ * xi-FP arrays [E][4][N][N+1]: row j, FP i.  eta-FP arrays [E][4][N+1][N]:
+ * FP row j, column i. */
+#define IQ(e, v, j, i) ((((size_t)(e) * 4 + (v)) * N + (j)) * N + (i))
+#define IXF(e, v, j, i) ((((size_t)(e) * 4 + (v)) * N + (j)) * (N + 1) + (i))
+#define IEF(e, v, j, i) ((((size_t)(e) * 4 + (v)) * (N + 1) + (j)) * N + (i))
+
+/* value at face point (f, j) of an xi-FP or eta-FP array */
+static size_t face_index(int N, int e, int f, int v, int j) {
+  switch (f) {
+    case 0: return IEF(e, v, 0, j);
+    case 1: return IXF(e, v, j, N);
+    case 2: return IEF(e, v, N, j);
+    default: return IXF(e, v, j, 0);
+  }
+}
+
+static const double FACE_SIGMA[4] = {-1.0, 1.0, 1.0, -1.0};
+
+/* geometry at face point j of face f of element e, time t: outward unit normal,
+ * |S| (length of the contravariant vector), position */
+static void face_geom(const or_mesh *m, int e, int f, int j, double t, double *nx, double *ny, double *S, double *x,
+                      double *y) {
+  double g[6], ax, ay;
+  double xi = 0, eta = 0;
+  switch (f) {
+    case 0: xi = m->Xs[j]; eta = 0.0; break;
+    case 1: xi = 1.0; eta = m->Xs[j]; break;
+    case 2: xi = m->Xs[j]; eta = 1.0; break;
+    default: xi = 0.0; eta = m->Xs[j]; break;
+  }
+  map_at(m, e, xi, eta, t, g);
+  if (f == 1 || f == 3) { ax = g[5]; ay = -g[4]; }  /* (y_eta, -x_eta) */
+  else { ax = -g[3]; ay = g[2]; }                    /* (-y_xi, x_xi) */
+  double len = sqrt(ax * ax + ay * ay);
+  *S = len;
+  *nx = FACE_SIGMA[f] * ax / len;
+  *ny = FACE_SIGMA[f] * ay / len;
+  *x = g[0];
+  *y = g[1];
+}
+
+typedef struct {
+  int nm;            /* number of non-degenerate mortars */
+  int *lf, *rf;      /* index into the sorted L / R lists */
+  double *oL, *sL, *oR, *sR, *m0, *dm;
+} or_mortars;
+
+/* Sec. 3.2: mortars at stage time t.  The rotating (L) side is turned by
+ * theta = omega t; the mortars are the intervals between consecutive node
+ * angles of both sides, in counter-clockwise order. */
+static void build_mortars(const or_mesh *m, double t, or_mortars *mo) {
+  int nL = m->nL, nR = m->nR, nb = nL + nR;
+  double th = m->prm.omega * t;
+  double *ang = malloc(sizeof(double) * nb);
+  for (int k = 0; k < nL; ++k) ang[k] = wrap2pi(m->La[k] + th);
+  for (int k = 0; k < nR; ++k) ang[nL + k] = m->Ra[k];
+  for (int i = 1; i < nb; ++i)
+    for (int j = i; j > 0 && ang[j] < ang[j - 1]; --j) { double tt = ang[j]; ang[j] = ang[j - 1]; ang[j - 1] = tt; }
+  mo->nm = 0;
+  mo->lf = malloc(sizeof(int) * nb); mo->rf = malloc(sizeof(int) * nb);
+  mo->oL = malloc(sizeof(double) * nb); mo->sL = malloc(sizeof(double) * nb);
+  mo->oR = malloc(sizeof(double) * nb); mo->sR = malloc(sizeof(double) * nb);
+  mo->m0 = malloc(sizeof(double) * nb); mo->dm = malloc(sizeof(double) * nb);
+  for (int k = 0; k < nb; ++k) {
+    double a = ang[k], b = (k + 1 < nb) ? ang[k + 1] : ang[0] + 2.0 * OR_PI;
+    double d = b - a;
+    if (d <= 1e-13) continue;
+    double mid = a + 0.5 * d;
+    int fl = -1, fr = -1;
+    double oL = 0, oR = 0;
+    for (int q = 0; q < nL; ++q) {
+      double st = wrap2pi(m->La[q] + th);
+      double off = wrap2pi(mid - st);
+      if (off < m->Lw[q]) { fl = q; oL = wrap_pi(a - st); break; }
+    }
+    for (int q = 0; q < nR; ++q) {
+      double off = wrap2pi(mid - m->Ra[q]);
+      if (off < m->Rw[q]) { fr = q; oR = wrap_pi(a - m->Ra[q]); break; }
+    }
+    if (fl < 0 || fr < 0) continue;
+    int n = mo->nm++;
+    mo->lf[n] = fl;
+    mo->rf[n] = fr;
+    mo->oL[n] = oL / m->Lw[fl];
+    mo->sL[n] = d / m->Lw[fl];
+    mo->oR[n] = oR / m->Rw[fr];
+    mo->sR[n] = d / m->Rw[fr];
+    mo->m0[n] = a;
+    mo->dm[n] = d;
+  }
+  free(ang);
+}
+
+static void free_mortars(or_mortars *mo) {
+  free(mo->lf); free(mo->rf); free(mo->oL); free(mo->sL); free(mo->oR); free(mo->sR); free(mo->m0); free(mo->dm);
+}
+
+/* Read the N values (per variable) at the face points of element face ef from
+ * an FP array in counter-clockwise order (reversed if the face runs clockwise). */
+static void gather_ccw(const or_mesh *m, const double *arr_xi, const double *arr_eta, int ef, int rev, int nv,
+                       double *out) {
+  int N = m->N, e = ef / 4, f = ef % 4;
+  for (int v = 0; v < nv; ++v)
+    for (int j = 0; j < N; ++j) {
+      int jj = rev ? N - 1 - j : j;
+      size_t idx = face_index(N, e, f, v, jj);
+      out[v * N + j] = (f == 1 || f == 3) ? arr_xi[idx] : arr_eta[idx];
+    }
+}
+
+/* Mortar coupling of one family of face fields (nv variables per point):
+ *   mode 0: inviscid common flux: project Q^Omega of both sides to each mortar
+ *           (Eq. prjQ2), Rusanov at the mortar SPs with the radial normal
+ *           (Sec. 3.2), project the common flux back to both sides (Eq. prjF2);
+ *   mode 1: common solution: project, average both sides, project back;
+ *   mode 2: viscous flux: project the face values of F_vis . n (supplied per
+ *           face point in Lval / Rval), average both sides, project back.
+ * Lin/Rin: per sorted L/R face, nv*N values in CCW order.  Lout/Rout receive the
+ * projected-back values in CCW order. */
+static void mortar_couple(const or_mesh *m, const or_mortars *mo, int mode, const double *Lin, const double *Rin,
+                          double *Lout, double *Rout) {
+  int N = m->N;
+  int nv = 4;
+  memset(Lout, 0, sizeof(double) * m->nL * nv * N);
+  memset(Rout, 0, sizeof(double) * m->nR * nv * N);
+  double PfL[OR_MAXN * OR_MAXN], PbL[OR_MAXN * OR_MAXN], PfR[OR_MAXN * OR_MAXN], PbR[OR_MAXN * OR_MAXN];
+  for (int k = 0; k < mo->nm; ++k) {
+    int fl = mo->lf[k], fr = mo->rf[k];
+    or_projection(N, mo->oL[k], mo->sL[k], PfL, PbL);
+    or_projection(N, mo->oR[k], mo->sR[k], PfR, PbR);
+    double qL[4 * OR_MAXN], qR[4 * OR_MAXN], fm[4 * OR_MAXN];
+    for (int v = 0; v < nv; ++v)
+      for (int i = 0; i < N; ++i) {
+        double sl = 0.0, sr = 0.0;
+        for (int j = 0; j < N; ++j) {
+          sl += PfL[i * N + j] * Lin[(fl * nv + v) * N + j];
+          sr += PfR[i * N + j] * Rin[(fr * nv + v) * N + j];
+        }
+        qL[v * N + i] = sl;
+        qR[v * N + i] = sr;
+      }
+    if (mode == 0) {
+      for (int i = 0; i < N; ++i) {
+        double phi = mo->m0[k] + m->Xs[i] * mo->dm[k];
+        double a[4], b[4], Fn[4];
+        for (int v = 0; v < 4; ++v) { a[v] = qL[v * N + i]; b[v] = qR[v * N + i]; }
+        /* on a circle about the rotation centre the grid velocity is tangential */
+        rusanov(&m->prm, a, b, cos(phi), sin(phi), 0.0, Fn);
+        for (int v = 0; v < 4; ++v) fm[v * N + i] = Fn[v];
+      }
+    } else {
+      for (int x = 0; x < nv * N; ++x) fm[x] = 0.5 * (qL[x] + qR[x]);
+    }
+    for (int v = 0; v < nv; ++v)
+      for (int i = 0; i < N; ++i) {
+        double sl = 0.0, sr = 0.0;
+        for (int j = 0; j < N; ++j) {
+          sl += PbL[i * N + j] * fm[v * N + j];
+          sr += PbR[i * N + j] * fm[v * N + j];
+        }
+        Lout[(fl * nv + v) * N + i] += sl;
+        Rout[(fr * nv + v) * N + i] += sr;
+      }
+  }
+}
+
+/* wall state of an isothermal no-slip wall moving with velocity (uw, vw):
+ * interior pressure, wall temperature (boundary condition reading) */
+static void wall_state(const or_params *p, const double *qi, double uw, double vw, double *qw) {
+  double pr = pressure(p, qi);
+  double rho = pr / (p->Rgas * p->T_wall);
+  qw[0] = rho;
+  qw[1] = rho * uw;
+  qw[2] = rho * vw;
+  qw[3] = pr / (p->gamma - 1.0) + 0.5 * rho * (uw * uw + vw * vw);
+}
+
+typedef struct {
+  double *Qxi, *Qeta;   /* Q at xi / eta FPs */
+  double *Fxi, *Geta;   /* transformed fluxes at xi / eta FPs */
+  double *cQxi, *cQeta; /* common solution at face points (viscous) */
+  double *gxi, *geta;   /* physical gradient at FPs: [E][8][..] as two 4-var blocks */
+} or_work;
+
+int or_residual(or_mesh *m, const double *Q, double t, double *dQdt) {
+  int N = m->N, ne = m->ne;
+  const or_params *P = &m->prm;
+  size_t nxf = (size_t)ne * 4 * N * (N + 1);
+  double *Qxi = calloc(nxf, sizeof(double)), *Qeta = calloc(nxf, sizeof(double));
+  double *Fxi = calloc(nxf, sizeof(double)), *Geta = calloc(nxf, sizeof(double));
+  double *cQxi = NULL, *cQeta = NULL, *Gxx = NULL, *Gxy = NULL, *Gex = NULL, *Gey = NULL;
+  double hf[(OR_MAXN + 1) * OR_MAXN], dl[OR_MAXN * (OR_MAXN + 1)];
+  /* h_k(X_{i+1/2}) and l'_{i+1/2}(X_k) */
+  for (int i = 0; i <= N; ++i)
+    for (int k = 0; k < N; ++k) hf[i * N + k] = lag(m->Xs, N, k, m->Xf[i]);
+  for (int k = 0; k < N; ++k)
+    for (int i = 0; i <= N; ++i) dl[k * (N + 1) + i] = lag_d(m->Xf, N + 1, i, m->Xs[k]);
+
+  /* step 1: solution polynomial (Eq. Qt) at all FPs */
+  for (int e = 0; e < ne; ++e)
+    for (int v = 0; v < 4; ++v)
+      for (int j = 0; j < N; ++j)
+        for (int i = 0; i <= N; ++i) {
+          double sx = 0.0, se = 0.0;
+          for (int k = 0; k < N; ++k) {
+            sx += Q[IQ(e, v, j, k)] * hf[i * N + k];
+            se += Q[IQ(e, v, k, j)] * hf[i * N + k];
+          }
+          Qxi[IXF(e, v, j, i)] = sx;
+          Qeta[IEF(e, v, i, j)] = se;
+        }
+
+  /* step 2: inviscid fluxes (with grid velocity) at the FPs, transformed by
+   * Eq. transform_relation: F~ = y_eta F - x_eta G, G~ = -y_xi F + x_xi G */
+  for (int e = 0; e < ne; ++e)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i <= N; ++i) {
+        double g[6], q[4], F[4], G[4], ug, vg;
+        map_at(m, e, m->Xf[i], m->Xs[j], t, g);
+        grid_velocity(m, e, g[0], g[1], &ug, &vg);
+        for (int v = 0; v < 4; ++v) q[v] = Qxi[IXF(e, v, j, i)];
+        inviscid_flux(P, q, ug, vg, F, G);
+        for (int v = 0; v < 4; ++v) Fxi[IXF(e, v, j, i)] = g[5] * F[v] - g[4] * G[v];
+        map_at(m, e, m->Xs[j], m->Xf[i], t, g);
+        grid_velocity(m, e, g[0], g[1], &ug, &vg);
+        for (int v = 0; v < 4; ++v) q[v] = Qeta[IEF(e, v, i, j)];
+        inviscid_flux(P, q, ug, vg, F, G);
+        for (int v = 0; v < 4; ++v) Geta[IEF(e, v, i, j)] = -g[3] * F[v] + g[2] * G[v];
+      }
+
+  /* mortars at this stage time */
+  or_mortars mo;
+  memset(&mo, 0, sizeof mo);
+  int nL = m->nL, nR = m->nR;
+  double *Lin = NULL, *Rin = NULL, *Lout = NULL, *Rout = NULL;
+  if (nL > 0) {
+    build_mortars(m, t, &mo);
+    Lin = malloc(sizeof(double) * nL * 4 * N);
+    Rin = malloc(sizeof(double) * nR * 4 * N);
+    Lout = malloc(sizeof(double) * nL * 4 * N);
+    Rout = malloc(sizeof(double) * nR * 4 * N);
+  }
+
+  /* viscous: common solution, gradients, viscous fluxes at the FPs */
+  double *Fv_face = NULL; /* common viscous normal flux per element face point [E*4][4][N] (outward) */
+  if (P->viscous) {
+    cQxi = calloc(nxf, sizeof(double));
+    cQeta = calloc(nxf, sizeof(double));
+    Gxx = calloc(nxf, sizeof(double)); Gxy = calloc(nxf, sizeof(double));
+    Gex = calloc(nxf, sizeof(double)); Gey = calloc(nxf, sizeof(double));
+    /* (a) common solution at every face point */
+    for (int e = 0; e < ne; ++e)
+      for (int f = 0; f < 4; ++f) {
+        int ef = 4 * e + f, kind = m->fkind[ef];
+        for (int j = 0; j < N; ++j) {
+          double qi[4], qc[4];
+          for (int v = 0; v < 4; ++v) {
+            size_t id = face_index(N, e, f, v, j);
+            qi[v] = (f == 1 || f == 3) ? Qxi[id] : Qeta[id];
+          }
+          if (kind == FK_CONF || kind == FK_PERIODIC) {
+            int eb = m->fnbr[ef] / 4, fb = m->fnbr[ef] % 4, jb = m->frev[ef] ? N - 1 - j : j;
+            for (int v = 0; v < 4; ++v) {
+              size_t id = face_index(N, eb, fb, v, jb);
+              double qo = (fb == 1 || fb == 3) ? Qxi[id] : Qeta[id];
+              qc[v] = 0.5 * (qi[v] + qo);
+            }
+          } else if (kind == FK_BOUNDARY) {
+            double nx, ny, S, x, y, ug, vg;
+            face_geom(m, e, f, j, t, &nx, &ny, &S, &x, &y);
+            grid_velocity(m, e, x, y, &ug, &vg);
+            wall_state(P, qi, ug, vg, qc);
+          } else {
+            continue; /* interface: below */
+          }
+          for (int v = 0; v < 4; ++v) {
+            size_t id = face_index(N, e, f, v, j);
+            if (f == 1 || f == 3) cQxi[id] = qc[v]; else cQeta[id] = qc[v];
+          }
+        }
+      }
+    if (nL > 0) {
+      for (int k = 0; k < nL; ++k) gather_ccw(m, Qxi, Qeta, m->Lef[k], m->Lrev[k], 4, Lin + (size_t)k * 4 * N);
+      for (int k = 0; k < nR; ++k) gather_ccw(m, Qxi, Qeta, m->Ref[k], m->Rrev[k], 4, Rin + (size_t)k * 4 * N);
+      mortar_couple(m, &mo, 1, Lin, Rin, Lout, Rout);
+      for (int side = 0; side < 2; ++side) {
+        int n = side ? nR : nL;
+        for (int k = 0; k < n; ++k) {
+          int ef = side ? m->Ref[k] : m->Lef[k], rev = side ? m->Rrev[k] : m->Lrev[k];
+          const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
+          int e = ef / 4, f = ef % 4;
+          for (int v = 0; v < 4; ++v)
+            for (int j = 0; j < N; ++j) {
+              int jj = rev ? N - 1 - j : j;
+              size_t id = face_index(N, e, f, v, jj);
+              if (f == 1 || f == 3) cQxi[id] = src[v * N + j]; else cQeta[id] = src[v * N + j];
+            }
+        }
+      }
+    }
+    /* (b) gradients at the SPs: derivative of the degree-N polynomial through
+     * the FP values, with the common solution at the end FPs; mapped to x, y
+     * with the metrics at the SP (chain rule). */
+    double *Qx = calloc((size_t)ne * 4 * N * N, sizeof(double)), *Qy = calloc((size_t)ne * 4 * N * N, sizeof(double));
+    for (int e = 0; e < ne; ++e)
+      for (int j = 0; j < N; ++j)
+        for (int k = 0; k < N; ++k) {
+          double g[6];
+          map_at(m, e, m->Xs[k], m->Xs[j], t, g);
+          double J = g[2] * g[5] - g[4] * g[3];
+          for (int v = 0; v < 4; ++v) {
+            double dxi = 0.0, deta = 0.0;
+            for (int i = 0; i <= N; ++i) {
+              double ax = (i == 0 || i == N) ? cQxi[IXF(e, v, j, i)] : Qxi[IXF(e, v, j, i)];
+              double ae = (i == 0 || i == N) ? cQeta[IEF(e, v, i, k)] : Qeta[IEF(e, v, i, k)];
+              dxi += ax * dl[k * (N + 1) + i];
+              deta += ae * dl[j * (N + 1) + i];
+            }
+            /* SP (k, j): xi derivative along row j, eta derivative along column k */
+            Qx[IQ(e, v, j, k)] = (g[5] * dxi - g[3] * deta) / J;
+            Qy[IQ(e, v, j, k)] = (-g[4] * dxi + g[2] * deta) / J;
+          }
+        }
+    /* (c) gradients interpolated to the FPs */
+    for (int e = 0; e < ne; ++e)
+      for (int v = 0; v < 4; ++v)
+        for (int j = 0; j < N; ++j)
+          for (int i = 0; i <= N; ++i) {
+            double a = 0, b = 0, c = 0, d = 0;
+            for (int k = 0; k < N; ++k) {
+              a += Qx[IQ(e, v, j, k)] * hf[i * N + k];
+              b += Qy[IQ(e, v, j, k)] * hf[i * N + k];
+              c += Qx[IQ(e, v, k, j)] * hf[i * N + k];
+              d += Qy[IQ(e, v, k, j)] * hf[i * N + k];
+            }
+            Gxx[IXF(e, v, j, i)] = a;
+            Gxy[IXF(e, v, j, i)] = b;
+            Gex[IEF(e, v, i, j)] = c;
+            Gey[IEF(e, v, i, j)] = d;
+          }
+    free(Qx);
+    free(Qy);
+    /* (d) viscous fluxes at the interior FPs, transformed and added */
+    for (int e = 0; e < ne; ++e)
+      for (int j = 0; j < N; ++j)
+        for (int i = 1; i < N; ++i) {
+          double g[6], q[4], qx[4], qy[4], F[4], G[4];
+          map_at(m, e, m->Xf[i], m->Xs[j], t, g);
+          for (int v = 0; v < 4; ++v) { q[v] = Qxi[IXF(e, v, j, i)]; qx[v] = Gxx[IXF(e, v, j, i)]; qy[v] = Gxy[IXF(e, v, j, i)]; }
+          viscous_flux(P, q, qx, qy, F, G);
+          for (int v = 0; v < 4; ++v) Fxi[IXF(e, v, j, i)] += g[5] * F[v] - g[4] * G[v];
+          map_at(m, e, m->Xs[j], m->Xf[i], t, g);
+          for (int v = 0; v < 4; ++v) { q[v] = Qeta[IEF(e, v, i, j)]; qx[v] = Gex[IEF(e, v, i, j)]; qy[v] = Gey[IEF(e, v, i, j)]; }
+          viscous_flux(P, q, qx, qy, F, G);
+          for (int v = 0; v < 4; ++v) Geta[IEF(e, v, i, j)] += -g[3] * F[v] + g[2] * G[v];
+        }
+    /* (e) common viscous normal flux at the face points */
+    Fv_face = calloc((size_t)ne * 4 * 4 * N, sizeof(double));
+    double *vL = NULL, *vR = NULL;
+    if (nL > 0) { vL = calloc((size_t)nL * 4 * N, sizeof(double)); vR = calloc((size_t)nR * 4 * N, sizeof(double)); }
+    for (int e = 0; e < ne; ++e)
+      for (int f = 0; f < 4; ++f) {
+        int ef = 4 * e + f, kind = m->fkind[ef];
+        for (int j = 0; j < N; ++j) {
+          double nx, ny, S, x, y, qc[4], gx[4], gy[4], F[4], G[4], fo[4];
+          face_geom(m, e, f, j, t, &nx, &ny, &S, &x, &y);
+          for (int v = 0; v < 4; ++v) {
+            size_t id = face_index(N, e, f, v, j);
+            int isx = (f == 1 || f == 3);
+            qc[v] = isx ? cQxi[id] : cQeta[id];
+            gx[v] = isx ? Gxx[id] : Gex[id];
+            gy[v] = isx ? Gxy[id] : Gey[id];
+          }
+          viscous_flux(P, qc, gx, gy, F, G);
+          for (int v = 0; v < 4; ++v) fo[v] = F[v] * nx + G[v] * ny; /* own side, outward */
+          if (kind == FK_CONF || kind == FK_PERIODIC) {
+            int eb = m->fnbr[ef] / 4, fb = m->fnbr[ef] % 4, jb = m->frev[ef] ? N - 1 - j : j;
+            double gbx[4], gby[4], Fb[4], Gb[4];
+            for (int v = 0; v < 4; ++v) {
+              size_t id = face_index(N, eb, fb, v, jb);
+              int isx = (fb == 1 || fb == 3);
+              gbx[v] = isx ? Gxx[id] : Gex[id];
+              gby[v] = isx ? Gxy[id] : Gey[id];
+            }
+            viscous_flux(P, qc, gbx, gby, Fb, Gb);
+            for (int v = 0; v < 4; ++v) Fv_face[((size_t)ef * 4 + v) * N + j] = 0.5 * (fo[v] + Fb[v] * nx + Gb[v] * ny);
+          } else if (kind == FK_BOUNDARY) {
+            for (int v = 0; v < 4; ++v) Fv_face[((size_t)ef * 4 + v) * N + j] = fo[v];
+          } else {
+            /* interface: store F_vis . n with n oriented from L to R, in the
+             * face's own point order; projected below */
+            double sgn = (kind == FK_IFACE_L) ? 1.0 : -1.0;
+            for (int v = 0; v < 4; ++v) Fv_face[((size_t)ef * 4 + v) * N + j] = sgn * fo[v];
+          }
+        }
+      }
+    if (nL > 0) {
+      for (int side = 0; side < 2; ++side) {
+        int n = side ? nR : nL;
+        for (int k = 0; k < n; ++k) {
+          int ef = side ? m->Ref[k] : m->Lef[k], rev = side ? m->Rrev[k] : m->Lrev[k];
+          double *dst = (side ? vR : vL) + (size_t)k * 4 * N;
+          for (int v = 0; v < 4; ++v)
+            for (int j = 0; j < N; ++j) dst[v * N + j] = Fv_face[((size_t)ef * 4 + v) * N + (rev ? N - 1 - j : j)];
+        }
+      }
+      mortar_couple(m, &mo, 2, vL, vR, Lout, Rout);
+      for (int side = 0; side < 2; ++side) {
+        int n = side ? nR : nL;
+        for (int k = 0; k < n; ++k) {
+          int ef = side ? m->Ref[k] : m->Lef[k], rev = side ? m->Rrev[k] : m->Lrev[k];
+          const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
+          double sgn = side ? -1.0 : 1.0; /* back to outward orientation */
+          for (int v = 0; v < 4; ++v)
+            for (int j = 0; j < N; ++j) Fv_face[((size_t)ef * 4 + v) * N + (rev ? N - 1 - j : j)] = sgn * src[v * N + j];
+        }
+      }
+      free(vL);
+      free(vR);
+    }
+  }
+
+  /* step 3: common inviscid flux at every face point (Rusanov on conforming and
+   * periodic faces and through boundary ghost states); end FP value
+   * F~ = sigma_f |S| (F_inv + F_vis).n_out */
+  for (int e = 0; e < ne; ++e)
+    for (int f = 0; f < 4; ++f) {
+      int ef = 4 * e + f, kind = m->fkind[ef];
+      if (kind == FK_IFACE_L || kind == FK_IFACE_R) continue;
+      for (int j = 0; j < N; ++j) {
+        double nx, ny, S, x, y, ug, vg, qi[4], qo[4], Fn[4];
+        face_geom(m, e, f, j, t, &nx, &ny, &S, &x, &y);
+        grid_velocity(m, e, x, y, &ug, &vg);
+        double vgn = ug * nx + vg * ny;
+        for (int v = 0; v < 4; ++v) {
+          size_t id = face_index(N, e, f, v, j);
+          qi[v] = (f == 1 || f == 3) ? Qxi[id] : Qeta[id];
+        }
+        if (kind == FK_CONF || kind == FK_PERIODIC) {
+          int eb = m->fnbr[ef] / 4, fb = m->fnbr[ef] % 4, jb = m->frev[ef] ? N - 1 - j : j;
+          for (int v = 0; v < 4; ++v) {
+            size_t id = face_index(N, eb, fb, v, jb);
+            qo[v] = (fb == 1 || fb == 3) ? Qxi[id] : Qeta[id];
+          }
+        } else {
+          /* isothermal no-slip wall moving with the grid: ghost state */
+          double pr = pressure(P, qi), rho = pr / (P->Rgas * P->T_wall);
+          double u = qi[1] / qi[0], v = qi[2] / qi[0];
+          double gu = 2.0 * ug - u, gv = 2.0 * vg - v;
+          qo[0] = rho;
+          qo[1] = rho * gu;
+          qo[2] = rho * gv;
+          qo[3] = pr / (P->gamma - 1.0) + 0.5 * rho * (gu * gu + gv * gv);
+        }
+        rusanov(P, qi, qo, nx, ny, vgn, Fn);
+        for (int v = 0; v < 4; ++v) {
+          double fv = Fv_face ? Fv_face[((size_t)ef * 4 + v) * N + j] : 0.0;
+          size_t id = face_index(N, e, f, v, j);
+          double val = FACE_SIGMA[f] * S * (Fn[v] + fv);
+          if (f == 1 || f == 3) Fxi[id] = val; else Geta[id] = val;
+        }
+      }
+    }
+  /* sliding interface: Eqs. prjQ2 -> Rusanov -> prjF2 */
+  if (nL > 0) {
+    for (int k = 0; k < nL; ++k) gather_ccw(m, Qxi, Qeta, m->Lef[k], m->Lrev[k], 4, Lin + (size_t)k * 4 * N);
+    for (int k = 0; k < nR; ++k) gather_ccw(m, Qxi, Qeta, m->Ref[k], m->Rrev[k], 4, Rin + (size_t)k * 4 * N);
+    mortar_couple(m, &mo, 0, Lin, Rin, Lout, Rout);
+    for (int side = 0; side < 2; ++side) {
+      int n = side ? nR : nL;
+      for (int k = 0; k < n; ++k) {
+        int ef = side ? m->Ref[k] : m->Lef[k], rev = side ? m->Rrev[k] : m->Lrev[k];
+        int e = ef / 4, f = ef % 4;
+        const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
+        double sgn = side ? -1.0 : 1.0; /* L -> R normal is outward for L, inward for R */
+        for (int j = 0; j < N; ++j) {
+          int jj = rev ? N - 1 - j : j;
+          double nx, ny, S, x, y;
+          face_geom(m, e, f, jj, t, &nx, &ny, &S, &x, &y);
+          for (int v = 0; v < 4; ++v) {
+            double fv = Fv_face ? Fv_face[((size_t)ef * 4 + v) * N + jj] : 0.0;
+            size_t id = face_index(N, e, f, v, jj);
+            double val = FACE_SIGMA[f] * S * (sgn * src[v * N + j] + fv);
+            if (f == 1 || f == 3) Fxi[id] = val; else Geta[id] = val;
+          }
+        }
+      }
+    }
+  }
+
+  /* step 4: divergence of the flux polynomials (Eqs. Ft, Gt) at the SPs;
+   * dQ/dt = -(dF~/dxi + dG~/deta) / |J| */
+  for (int e = 0; e < ne; ++e)
+    for (int j = 0; j < N; ++j)
+      for (int k = 0; k < N; ++k) {
+        double g[6];
+        map_t0(m, e, m->Xs[k], m->Xs[j], g);
+        double J = g[2] * g[5] - g[4] * g[3];
+        for (int v = 0; v < 4; ++v) {
+          double dF = 0.0, dG = 0.0;
+          for (int i = 0; i <= N; ++i) {
+            dF += Fxi[IXF(e, v, j, i)] * dl[k * (N + 1) + i];
+            dG += Geta[IEF(e, v, i, k)] * dl[j * (N + 1) + i];
+          }
+          dQdt[IQ(e, v, j, k)] = -(dF + dG) / J;
+        }
+      }
+
+  free(Qxi); free(Qeta); free(Fxi); free(Geta);
+  free(cQxi); free(cQeta); free(Gxx); free(Gxy); free(Gex); free(Gey); free(Fv_face);
+  if (nL > 0) { free(Lin); free(Rin); free(Lout); free(Rout); free_mortars(&mo); }
+  return 0;
+}
+
+/* Three-stage SSP Runge-Kutta (Shu-Osher form), stage times t, t+dt, t+dt/2 */
+int or_step(or_mesh *m, double *Q, double *t, double dt, int nsteps) {
+  size_t n = (size_t)m->ne * 4 * m->N * m->N;
+  double *q1 = malloc(n * sizeof(double)), *q2 = malloc(n * sizeof(double)), *r = malloc(n * sizeof(double));
+  for (int s = 0; s < nsteps; ++s) {
+    double tn = *t;
+    or_residual(m, Q, tn, r);
+    for (size_t i = 0; i < n; ++i) q1[i] = Q[i] + dt * r[i];
+    or_residual(m, q1, tn + dt, r);
+    for (size_t i = 0; i < n; ++i) q2[i] = 0.75 * Q[i] + 0.25 * (q1[i] + dt * r[i]);
+    or_residual(m, q2, tn + 0.5 * dt, r);
+    for (size_t i = 0; i < n; ++i) Q[i] = Q[i] / 3.0 + 2.0 / 3.0 * (q2[i] + dt * r[i]);
+    *t = tn + dt;
+  }
+  free(q1); free(q2); free(r);
+  return 0;
+}
+
+/* mortar list at time t, for tests: returns the number of mortars; arrays must
+ * hold nL + nR entries */
+int or_mortar_list(const or_mesh *m, double t, int *lf, int *rf, double *oL, double *sL, double *oR, double *sR) {
+  or_mortars mo;
+  build_mortars(m, t, &mo);
+  for (int k = 0; k < mo.nm; ++k) {
+    lf[k] = mo.lf[k]; rf[k] = mo.rf[k]; oL[k] = mo.oL[k]; sL[k] = mo.sL[k]; oR[k] = mo.oR[k]; sR[k] = mo.sR[k];
+  }
+  int n = mo.nm;
+  free_mortars(&mo);
+  return n;
+}

@@ -1,0 +1,385 @@
+"""Synthetic quadrilateral meshes for the sliding-mesh SD workloads.
+
+The paper's meshes exist only as figures, so these generators build meshes of
+the same kind: a rotating inner zone and a stationary outer zone that meet on
+a circular sliding interface (Sec. 3.2), conforming quads inside each zone,
+periodic or wall boundaries outside.  They hold no part of the SD method: they
+only place nodes and list cells, boundary faces, periodic face pairs and the
+two sides of the interface.
+
+Mesh format (a dict of numpy arrays; the same dict feeds the oracle and the
+CUDA library):
+
+``xy``          float64 (n_nodes, 2)  node coordinates
+``elem_nodes``  int32 (E, 4)          corners n0..n3, counter-clockwise
+``elem_zone``   int32 (E,)            0 stationary, 1 rotating
+``edge_arc``    int32 (E, 4)          1 if local face f is a circular arc about
+                                      ``center`` (else a straight segment)
+``bfaces``      int32 (nb, 3)         (elem, local face, bc tag)
+``pfaces``      int32 (np, 4)         periodic pairs (eA, fA, eB, fB)
+``ifaces_L``    int32 (nL, 2)         interface faces of the rotating zone
+``ifaces_R``    int32 (nR, 2)         interface faces of the stationary zone
+``center``      float64 (2,)          rotation centre (also every arc's centre)
+``r_interface`` float                 radius of the sliding interface
+
+Local faces follow the reference square [0,1]^2 with n0=(0,0), n1=(1,0),
+n2=(1,1), n3=(0,1): f0 is eta=0 (n0->n1), f1 is xi=1 (n1->n2), f2 is eta=1
+(n3->n2), f3 is xi=0 (n0->n3).
+
+Boundary tags: 1 isothermal no-slip wall (moving with its zone).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+BC_WALL = 1
+
+# corner pairs of the four local faces, in the order of their face parameter
+FACE_CORNERS = ((0, 1), (1, 2), (3, 2), (0, 3))
+
+
+class _NodeTable:
+    """Node list with de-duplication by rounded coordinate (one table per zone,
+    so that the two sides of a sliding interface never share a node)."""
+
+    def __init__(self, offset: int = 0):
+        self.offset = offset
+        self.xy: list[tuple[float, float]] = []
+        self.key: dict[tuple[int, int], int] = {}
+
+    def add(self, x: float, y: float) -> int:
+        k = (int(round(x * 1e9)), int(round(y * 1e9)))
+        idx = self.key.get(k)
+        if idx is None:
+            idx = self.offset + len(self.xy)
+            self.key[k] = idx
+            self.xy.append((float(x), float(y)))
+        return idx
+
+
+class _MeshBuilder:
+    def __init__(self, center=(0.0, 0.0)):
+        self.center = np.asarray(center, dtype=np.float64)
+        self.zones: list[_NodeTable] = []
+        self.cells: list[list[int]] = []
+        self.zone_of: list[int] = []
+        self.arcs: list[list[int]] = []
+
+    def node_table(self) -> _NodeTable:
+        off = sum(len(z.xy) for z in self.zones)
+        t = _NodeTable(off)
+        self.zones.append(t)
+        return t
+
+    def all_xy(self) -> np.ndarray:
+        pts = [p for z in self.zones for p in z.xy]
+        return np.asarray(pts, dtype=np.float64).reshape(-1, 2)
+
+    def add_cell(self, xy_lookup, corners, zone, arc_edges=()):
+        """Add a quad given 4 node ids in either orientation.  ``arc_edges``
+        lists unordered node-id pairs whose edge is a circular arc."""
+        c = list(corners)
+        p = np.array([xy_lookup(n) for n in c])
+        area2 = 0.0
+        for k in range(4):
+            x0, y0 = p[k]
+            x1, y1 = p[(k + 1) % 4]
+            area2 += x0 * y1 - x1 * y0
+        if area2 < 0:
+            c = [c[0], c[3], c[2], c[1]]
+        arcset = {frozenset(e) for e in arc_edges}
+        arc = [1 if frozenset((c[a], c[b])) in arcset else 0 for a, b in FACE_CORNERS]
+        self.cells.append(c)
+        self.zone_of.append(zone)
+        self.arcs.append(arc)
+        return len(self.cells) - 1
+
+
+def _face_of(cell: list[int], a: int, b: int) -> int:
+    for f, (i, j) in enumerate(FACE_CORNERS):
+        if {cell[i], cell[j]} == {a, b}:
+            return f
+    raise ValueError("edge not in cell")
+
+
+def _finish(mb: _MeshBuilder, bfaces, pfaces, ifL, ifR, r_interface) -> dict:
+    return {
+        "xy": mb.all_xy(),
+        "elem_nodes": np.asarray(mb.cells, dtype=np.int32).reshape(-1, 4),
+        "elem_zone": np.asarray(mb.zone_of, dtype=np.int32),
+        "edge_arc": np.asarray(mb.arcs, dtype=np.int32).reshape(-1, 4),
+        "bfaces": np.asarray(bfaces, dtype=np.int32).reshape(-1, 3),
+        "pfaces": np.asarray(pfaces, dtype=np.int32).reshape(-1, 4),
+        "ifaces_L": np.asarray(ifL, dtype=np.int32).reshape(-1, 2),
+        "ifaces_R": np.asarray(ifR, dtype=np.int32).reshape(-1, 2),
+        "center": mb.center.copy(),
+        "r_interface": float(r_interface),
+    }
+
+
+def _ring(mb, table, zone, inner_pts, outer_pts, nlayers, inner_is_arc, outer_is_arc):
+    """Structured ring between two closed point loops with equal point counts
+    (counter-clockwise).  Layer l sits at blend lambda_l between them.
+    Returns (cells, node ids of inner loop, node ids of outer loop)."""
+    m = len(inner_pts)
+    lam = np.linspace(0.0, 1.0, nlayers + 1)
+    ids = np.zeros((nlayers + 1, m), dtype=np.int64)
+    for l in range(nlayers + 1):
+        for k in range(m):
+            if l == 0:
+                x, y = inner_pts[k]
+            elif l == nlayers:
+                x, y = outer_pts[k]
+            else:
+                x = (1 - lam[l]) * inner_pts[k][0] + lam[l] * outer_pts[k][0]
+                y = (1 - lam[l]) * inner_pts[k][1] + lam[l] * outer_pts[k][1]
+            ids[l, k] = table.add(x, y)
+    look = _lookup(mb)
+    cells = []
+    for l in range(nlayers):
+        for k in range(m):
+            k1 = (k + 1) % m
+            a, b, c, d = ids[l, k], ids[l + 1, k], ids[l + 1, k1], ids[l, k1]
+            arcs = []
+            if l == 0 and inner_is_arc:
+                arcs.append((a, d))
+            if l == nlayers - 1 and outer_is_arc:
+                arcs.append((b, c))
+            cells.append(mb.add_cell(look, [a, b, c, d], zone, arcs))
+    return cells, ids[0], ids[nlayers]
+
+
+def _lookup(mb):
+    def f(n):
+        for z in mb.zones:
+            if z.offset <= n < z.offset + len(z.xy):
+                return z.xy[n - z.offset]
+        raise KeyError(n)
+    return f
+
+
+def _circle(center, r, m, phi0):
+    return [(center[0] + r * math.cos(phi0 + 2 * math.pi * k / m),
+             center[1] + r * math.sin(phi0 + 2 * math.pi * k / m)) for k in range(m)]
+
+
+def _square_loop(center, s, m_side):
+    """Counter-clockwise points on the square of half-width s, starting at the
+    lower-left corner, m_side segments per side."""
+    cx, cy = center
+    pts = []
+    for side in range(4):
+        for k in range(m_side):
+            t = k / m_side
+            if side == 0:
+                pts.append((cx - s + 2 * s * t, cy - s))
+            elif side == 1:
+                pts.append((cx + s, cy - s + 2 * s * t))
+            elif side == 2:
+                pts.append((cx + s - 2 * s * t, cy + s))
+            else:
+                pts.append((cx - s, cy + s - 2 * s * t))
+    return pts
+
+
+def _interface_faces(mb, cells, loop_ids):
+    """(elem, local face) of the cells whose edge joins consecutive loop nodes."""
+    out = []
+    m = len(loop_ids)
+    edge_to_cell = {}
+    for e in cells:
+        c = mb.cells[e]
+        for f, (i, j) in enumerate(FACE_CORNERS):
+            edge_to_cell[frozenset((c[i], c[j]))] = (e, f)
+    for k in range(m):
+        out.append(edge_to_cell[frozenset((int(loop_ids[k]), int(loop_ids[(k + 1) % m])))])
+    return out
+
+
+def couette_mesh(nr_in=4, nth_in=32, nr_out=4, nth_out=40, r_i=1.0, r_m=1.5, r_o=2.0,
+                 phi_in=0.0, phi_out=0.0) -> dict:
+    """Annulus r_i<=r<=r_o split at r_m: inner ring rotating (zone 1), outer
+    ring stationary, isothermal walls at r_i and r_o (Sec. 4.2).  Every
+    constant-radius edge is an exact arc, so all cells are annular sectors."""
+    mb = _MeshBuilder((0.0, 0.0))
+    c = (0.0, 0.0)
+    tin = mb.node_table()
+    cells_in, loop_i0, loop_i1 = _polar_ring(mb, tin, 1, c, np.linspace(r_i, r_m, nr_in + 1),
+                                             nth_in, phi_in)
+    tout = mb.node_table()
+    cells_out, loop_o0, loop_o1 = _polar_ring(mb, tout, 0, c, np.linspace(r_m, r_o, nr_out + 1),
+                                              nth_out, phi_out)
+    bfaces = []
+    for e, f in _interface_faces(mb, cells_in, loop_i0):
+        bfaces.append((e, f, BC_WALL))
+    for e, f in _interface_faces(mb, cells_out, loop_o1):
+        bfaces.append((e, f, BC_WALL))
+    ifL = _interface_faces(mb, cells_in, loop_i1)
+    ifR = _interface_faces(mb, cells_out, loop_o0)
+    return _finish(mb, bfaces, [], ifL, ifR, r_m)
+
+
+def _polar_ring(mb, table, zone, center, radii, nth, phi0):
+    nl = len(radii) - 1
+    ids = np.zeros((nl + 1, nth), dtype=np.int64)
+    for l in range(nl + 1):
+        for k in range(nth):
+            phi = phi0 + 2 * math.pi * k / nth
+            ids[l, k] = table.add(center[0] + radii[l] * math.cos(phi),
+                                  center[1] + radii[l] * math.sin(phi))
+    look = _lookup(mb)
+    cells = []
+    for l in range(nl):
+        for k in range(nth):
+            k1 = (k + 1) % nth
+            a, b, c, d = ids[l, k], ids[l + 1, k], ids[l + 1, k1], ids[l, k1]
+            cells.append(mb.add_cell(look, [a, b, c, d], zone, [(a, d), (b, c)]))
+    return cells, ids[0], ids[nl]
+
+
+def rotor_mesh(half_width=10.0, n_cart=64, n_hole=24, r_interface=3.0, n_core=24,
+               core_half=1.5, n_ring_in=16, n_ring_out=4, shift_L=0.0, shift_R=0.0) -> dict:
+    """Periodic square [-w,w]^2 with a rotating disk r<=r_interface (Sec. 4.1).
+
+    Rotating zone: a core square of n_core x n_core straight cells and an
+    O-ring of n_ring_in layers from the core square to the circle (4*n_core
+    interface faces).  Stationary zone: an O-ring of n_ring_out layers from
+    the circle (4*n_hole interface faces) out to a square hole of half-width
+    n_hole*h/2 cut from an n_cart x n_cart Cartesian grid of spacing
+    h = 2w/n_cart, periodic in x and y.  Only the edges lying on the circle
+    are arcs; every other edge is straight.  ``shift_L`` / ``shift_R`` turn the
+    circle nodes of either side by a small angle (the corner nodes of the
+    square loops stay put).
+    """
+    h = 2.0 * half_width / n_cart
+    b = n_hole * h / 2.0
+    if n_hole % 2 or (n_cart - n_hole) % 2:
+        raise ValueError("n_hole and n_cart - n_hole must be even")
+    if not (core_half * math.sqrt(2) < r_interface < b):
+        raise ValueError("need core square inside the circle inside the hole")
+    c = (0.0, 0.0)
+    mb = _MeshBuilder(c)
+    # rotating zone ------------------------------------------------------
+    tin = mb.node_table()
+    look = _lookup(mb)
+    core_ids = np.zeros((n_core + 1, n_core + 1), dtype=np.int64)
+    for i in range(n_core + 1):
+        for j in range(n_core + 1):
+            core_ids[i, j] = tin.add(-core_half + 2 * core_half * i / n_core,
+                                     -core_half + 2 * core_half * j / n_core)
+    for j in range(n_core):
+        for i in range(n_core):
+            mb.add_cell(look, [core_ids[i, j], core_ids[i + 1, j], core_ids[i + 1, j + 1],
+                               core_ids[i, j + 1]], 1)
+    m_in = 4 * n_core
+    phiL = -0.75 * math.pi + shift_L
+    sq = _square_loop(c, core_half, n_core)
+    circ_in = _circle(c, r_interface, m_in, phiL)
+    cells_in, _, loopL = _ring(mb, tin, 1, sq, circ_in, n_ring_in, False, True)
+    # stationary zone ----------------------------------------------------
+    tout = mb.node_table()
+    look = _lookup(mb)
+    m_out = 4 * n_hole
+    phiR = -0.75 * math.pi + shift_R
+    circ_out = _circle(c, r_interface, m_out, phiR)
+    hole = _square_loop(c, b, n_hole)
+    cells_out, loopR, _ = _ring(mb, tout, 0, circ_out, hole, n_ring_out, True, False)
+    cart = np.zeros((n_cart + 1, n_cart + 1), dtype=np.int64)
+    for i in range(n_cart + 1):
+        for j in range(n_cart + 1):
+            cart[i, j] = tout.add(-half_width + i * h, -half_width + j * h)
+    lo = (n_cart - n_hole) // 2
+    hi = lo + n_hole
+    cart_cell = {}
+    for j in range(n_cart):
+        for i in range(n_cart):
+            if lo <= i < hi and lo <= j < hi:
+                continue
+            cart_cell[(i, j)] = mb.add_cell(look, [cart[i, j], cart[i + 1, j],
+                                                   cart[i + 1, j + 1], cart[i, j + 1]], 0)
+    pf = []
+    for j in range(n_cart):
+        a, bb = cart_cell[(0, j)], cart_cell[(n_cart - 1, j)]
+        pf.append((a, _face_of(mb.cells[a], cart[0, j], cart[0, j + 1]),
+                   bb, _face_of(mb.cells[bb], cart[n_cart, j], cart[n_cart, j + 1])))
+    for i in range(n_cart):
+        a, bb = cart_cell[(i, 0)], cart_cell[(i, n_cart - 1)]
+        pf.append((a, _face_of(mb.cells[a], cart[i, 0], cart[i + 1, 0]),
+                   bb, _face_of(mb.cells[bb], cart[i, n_cart], cart[i + 1, n_cart])))
+    ifL = _interface_faces(mb, cells_in, loopL)
+    ifR = _interface_faces(mb, cells_out, loopR)
+    return _finish(mb, [], pf, ifL, ifR, r_interface)
+
+
+def periodic_box_mesh(n=4, half_width=1.0, rotating=False) -> dict:
+    """Plain periodic Cartesian box without an interface (small pin cases)."""
+    mb = _MeshBuilder((0.0, 0.0))
+    t = mb.node_table()
+    look = _lookup(mb)
+    h = 2 * half_width / n
+    ids = np.zeros((n + 1, n + 1), dtype=np.int64)
+    for i in range(n + 1):
+        for j in range(n + 1):
+            ids[i, j] = t.add(-half_width + i * h, -half_width + j * h)
+    cell = {}
+    for j in range(n):
+        for i in range(n):
+            cell[(i, j)] = mb.add_cell(look, [ids[i, j], ids[i + 1, j], ids[i + 1, j + 1],
+                                              ids[i, j + 1]], 1 if rotating else 0)
+    pf = []
+    for j in range(n):
+        a, bb = cell[(0, j)], cell[(n - 1, j)]
+        pf.append((a, _face_of(mb.cells[a], ids[0, j], ids[0, j + 1]),
+                   bb, _face_of(mb.cells[bb], ids[n, j], ids[n, j + 1])))
+    for i in range(n):
+        a, bb = cell[(i, 0)], cell[(i, n - 1)]
+        pf.append((a, _face_of(mb.cells[a], ids[i, 0], ids[i + 1, 0]),
+                   bb, _face_of(mb.cells[bb], ids[i, n], ids[i + 1, n])))
+    return _finish(mb, [], pf, [], [], 0.0)
+
+
+def perturb_nodes(mesh: dict, amplitude: float, seed: int = 1503) -> dict:
+    """Seeded random displacement of nodes that lie on no arc and on no
+    periodic or outer boundary (gives skewed straight-sided cells)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in mesh.items()}
+    xy = out["xy"]
+    fixed = np.zeros(len(xy), dtype=bool)
+    en, arc = mesh["elem_nodes"], mesh["edge_arc"]
+    for e in range(len(en)):
+        for f, (i, j) in enumerate(FACE_CORNERS):
+            if arc[e, f]:
+                fixed[en[e, i]] = fixed[en[e, j]] = True
+    for row in mesh["bfaces"]:
+        e, f = row[0], row[1]
+        i, j = FACE_CORNERS[f]
+        fixed[en[e, i]] = fixed[en[e, j]] = True
+    for row in mesh["pfaces"]:
+        for e, f in ((row[0], row[1]), (row[2], row[3])):
+            i, j = FACE_CORNERS[f]
+            fixed[en[e, i]] = fixed[en[e, j]] = True
+    # displacement bounded by a fraction of the shortest incident edge
+    hmin = np.full(len(xy), np.inf)
+    for e in range(len(en)):
+        for f, (i, j) in enumerate(FACE_CORNERS):
+            d = np.linalg.norm(xy[en[e, i]] - xy[en[e, j]])
+            hmin[en[e, i]] = min(hmin[en[e, i]], d)
+            hmin[en[e, j]] = min(hmin[en[e, j]], d)
+    disp = rng.uniform(-1.0, 1.0, size=xy.shape) * amplitude * hmin[:, None]
+    disp[fixed] = 0.0
+    out["xy"] = xy + disp
+    return out
+
+
+def mesh_stats(mesh: dict) -> dict:
+    return {
+        "elements": int(len(mesh["elem_nodes"])),
+        "rotating": int(mesh["elem_zone"].sum()),
+        "curved": int((mesh["edge_arc"].sum(axis=1) > 0).sum()),
+        "interface_L": int(len(mesh["ifaces_L"])),
+        "interface_R": int(len(mesh["ifaces_R"])),
+        "periodic_pairs": int(len(mesh["pfaces"])),
+        "boundary_faces": int(len(mesh["bfaces"])),
+    }
