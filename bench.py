@@ -1,0 +1,361 @@
+"""Benchmark of the sliding-mesh SD hot path: SSP-RK3 steps of the residual
+(SP->FP interpolation, ALE fluxes, Rusanov faces, curved dynamic mortars,
+divergence, RK update) on one GPU per rank, through the C ABI.
+
+Workload (default): vortex through a rotor -- periodic [-20,20]^2, rotating
+disk r<=4 at omega=0.5, 246,900 quads, N=6 (p=5), Euler, strength-5
+isentropic vortex; 8.9M solution points x 4 variables.  The state (284 MB)
+is larger than L2, so no flush is needed between steps.
+
+One step = three SSP-RK3 stages; metric = DOF-updates/s = E * N^2 * 4 *
+steps / time.  ``--impl reference`` times the plain C FP64 oracle on the host
+cores instead (a bounded sample of the same workload family).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from ssd_inputs import fields, meshes  # noqa: E402
+from ssd_inputs.workloads import FlowParams, build_workload  # noqa: E402
+
+METRIC = "DOF-updates/s (FP32 & batched vs FP64 GPU) at stated L2 error; % HBM roofline"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def volume_bytes_per_element(N, w_c):
+    """Algorithmic bytes one volume launch moves per element (see design
+    notes): FP64 state read + write, the Runge-Kutta base read on two of the
+    three stages, the common-flux read and the new traces written (16 N values
+    each in the compute word), 4 corner nodes (16 B each) and the zone tag."""
+    state = 4 * N * N * 8
+    return state * (2 + 2.0 / 3.0) + 2 * 16 * N * w_c + 4 * 16 + 4
+
+
+def launches_per_step(mesh):
+    """Kernels of one captured step: per stage the clock/merge kernel, the
+    conforming-face kernel, the wall kernel (if walls), the two mortar
+    kernels (if an interface) and the volume kernel; then the clock advance."""
+    per_stage = 1 + 1 + int(len(mesh["bfaces"]) > 0) + 2 * int(len(mesh["ifaces_L"]) > 0) + 1
+    return 3 * per_stage + 1
+
+
+SAMPLE_LADDER = (  # (n_cart, n_hole, n_core, n_ring_in, n_ring_out) of the rotor family
+    (90, 22, 10, 4, 2), (60, 16, 8, 3, 2), (40, 12, 6, 2, 2), (28, 10, 4, 2, 1))
+
+
+def sample_workload(level=0):
+    """Bounded sample of the rotor workload family for the CPU oracle: same
+    generator and N, coarser mesh (level 0: 7,950 quads)."""
+    nc, nh, nk, ri, ro = SAMPLE_LADDER[level]
+    return meshes.rotor_mesh(half_width=20.0, n_cart=nc, n_hole=nh, r_interface=4.0, n_core=nk,
+                             core_half=2.0, n_ring_in=ri, n_ring_out=ro)
+
+
+def cpu_oracle_rate(steps, warmup, dt, budget_s=None):
+    """Oracle SSP-RK3 steps on a sample mesh; with a time budget the sample
+    is the largest ladder mesh whose estimated (steps + warmup) time fits."""
+    import oracle
+    oracle.build()
+    w = build_workload("rotor_n6")
+    level = 0
+    if budget_s is not None:
+        probe = sample_workload(len(SAMPLE_LADDER) - 1)
+        op = oracle.Oracle(probe, w.N, w.params)
+        Qp = op.state_from(lambda x, y: fields.isentropic_vortex(x, y))
+        t0 = time.perf_counter()
+        op.step(Qp, 0.0, dt, 1)
+        per_elem = (time.perf_counter() - t0) / len(probe["elem_nodes"])
+        level = len(SAMPLE_LADDER) - 1
+        for lv in range(len(SAMPLE_LADDER)):
+            nc, nh = SAMPLE_LADDER[lv][0], SAMPLE_LADDER[lv][1]
+            est_E = nc * nc - nh * nh + 4 * nh * SAMPLE_LADDER[lv][4] + (SAMPLE_LADDER[lv][2] ** 2) * 5
+            if est_E * per_elem * (steps + warmup) <= budget_s:
+                level = lv
+                break
+    mesh = sample_workload(level)
+    orc = oracle.Oracle(mesh, w.N, w.params)
+    Q = orc.state_from(lambda x, y: fields.isentropic_vortex(x, y))
+    t = 0.0
+    for _ in range(warmup):
+        Q, t = orc.step(Q, t, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        Q, t = orc.step(Q, t, dt, 1)
+    el = time.perf_counter() - t0
+    E = len(mesh["elem_nodes"])
+    rate = E * w.N * w.N * 4 * steps / el
+    return rate, el, E
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = build_workload(args.workload)
+    rate, el, E = cpu_oracle_rate(args.steps, args.warmup, w.cfl_dt, budget_s=150.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "DOF-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "sample": f"same generator at {E} quads, N={w.N}"},
+        "cpu_baseline": {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} SSP-RK3 steps of the rotor family at {E} quads, N={w.N}"},
+        "e2e": {"value": rate, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rotor_n6")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1503_02198_gb300 as ssd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    ssd.build()
+
+    w = build_workload(args.workload)
+    N, dt = w.N, w.cfl_dt
+    prec = ssd.SD_PREC_FP32 if args.precision == "fp32" else ssd.SD_PREC_FP64
+    stream = torch.cuda.Stream()
+    solver = ssd.Solver(w.mesh, N - 1, w.params, precision=prec, stream=stream.cuda_stream)
+    Q0 = solver.state_from(lambda x, y: fields.isentropic_vortex(x, y))
+    solver.sd_set_state(Q0)
+    dofs = solver.n_dofs
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    solver.sd_step(dt, args.warmup)
+    solver.sd_sync()
+    barrier()
+    torch.cuda.synchronize()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.sd_step(dt, args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    solver.sd_sync()
+    barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * dofs * args.steps / (ms * 1e-3)
+
+    # accuracy at the final time: density L2 error against the exact vortex
+    t_end = solver.sd_get_time()
+    Q = solver.sd_get_state()
+    xy = solver.sd_sp_coords(t_end)
+    exact = np.moveaxis(fields.isentropic_vortex(xy[..., 0], xy[..., 1], t=t_end, period=(-20.0, 40.0)), -1, 1)
+    l2_rho = float(np.sqrt(np.mean((Q[:, 0] - exact[:, 0]) ** 2)))
+
+    # FP64 path on the same workload: throughput and FP32-vs-FP64 difference
+    fp64 = None
+    if prec == ssd.SD_PREC_FP32 and args.fp64_steps > 0:
+        s64 = ssd.Solver(w.mesh, N - 1, w.params, precision=ssd.SD_PREC_FP64, stream=stream.cuda_stream)
+        s64.sd_set_state(Q0)
+        s64.sd_step(dt, args.warmup)
+        s64.sd_sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s64.sd_step(dt, args.fp64_steps)
+        b.record(stream)
+        b.synchronize()
+        s64.sd_sync()
+        ms64 = a.elapsed_time(b)
+        # bring FP64 to the same step count as the FP32 run, compare states
+        rest = args.steps - args.fp64_steps
+        if rest > 0:
+            s64.sd_step(dt, rest)
+            s64.sd_sync()
+        Q64 = s64.sd_get_state()
+        rel = float(np.sqrt(np.sum((Q - Q64) ** 2) / np.sum(Q64 ** 2)))
+        fp64 = {"value": dofs * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
+                "fp32_rel_l2_vs_fp64": rel, "fp32_speedup": (dofs * args.steps / (ms * 1e-3)) /
+                (dofs * args.fp64_steps / (ms64 * 1e-3))}
+        try:
+            fp64["fma_peak_tflops"] = s64.sd_fma_peak(ssd.SD_PREC_FP64)
+        except Exception:
+            pass
+        s64.close()
+
+    # per-kernel timing (CUDA events on the handle's stream) -> roofline of the volume kernel
+    prof = solver.sd_profile_step(dt, reps=5)
+    w_c = 4 if prec == ssd.SD_PREC_FP32 else 8
+    E = solver.E
+    vol_bytes = volume_bytes_per_element(N, w_c) * E
+    peak, peak_src = _peaks()
+    achieved = vol_bytes / (prof["volume"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_volume", "peak_source": peak_src + " hbm_gbs (burst)",
+                "algorithmic_bytes_per_launch": vol_bytes}
+    try:
+        fp32_peak = solver.sd_fma_peak(ssd.SD_PREC_FP32)
+    except Exception:
+        fp32_peak = None
+
+    # end to end through the public API with host buffers: H2D state, one step, D2H state
+    pin_in = torch.empty(solver.shape, dtype=torch.float64, pin_memory=True)
+    pin_out = torch.empty(solver.shape, dtype=torch.float64, pin_memory=True)
+    pin_in.copy_(torch.from_numpy(Q))
+    solver.sd_set_state(pin_in)
+    solver.sd_step(dt, 1)
+    solver.sd_get_state(pin_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        solver.sd_set_state(pin_in)
+        solver.sd_step(dt, 1)
+        solver.sd_get_state(pin_out)
+    solver.sd_sync()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    state_bytes = dofs * 8
+    e2e = {"value": world * dofs * args.e2e_steps / e2e_s, "unit": "DOF-updates/s",
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, el, Es = cpu_oracle_rate(args.cpu_steps, 0, dt)
+        cpu = {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_steps} SSP-RK3 steps of the same rotor family at {Es} quads, N={N} "
+                         f"({el:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == ssd.SD_PREC_FP32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "elements": E, "N": N, "dofs": dofs, "dt": dt,
+                       "state_precision": "f64", "l2_flush": "state 284 MB > L2 (inputs larger than L2)",
+                       "parallelism": f"replicas x{world}", "description": w.description},
+            "l2_error_rho_vs_exact": l2_rho, "t_final": t_end,
+            "fp64": fp64,
+            "kernel_ms": prof,
+            "interface_fraction": prof["mortar"] * 3 / prof["step"],
+            "fp32_fma_peak_tflops": fp32_peak,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches_per_step(w.mesh) * args.steps,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * ssd.h -- C ABI of the GB300 sliding-mesh spectral difference (SSD) library.
+ *
+ * The library advances the two-dimensional compressible Euler / Navier-Stokes
+ * equations (Sec. 2 of Zhang & Liang, arXiv:1503.02198) on curvilinear
+ * quadrilaterals with one rotating zone coupled to one stationary zone through
+ * a curved sliding interface (Sec. 3.2), using the spectral difference method
+ * (Sec. 3.1) and explicit three-stage SSP Runge-Kutta (Sec. 3).  Every step of
+ * the residual and of the time step runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call:
+ *   - return value: SD_OK (0) or a negative SD_ERR_* code; sd_last_error()
+ *     gives a message for the last failure on a handle;
+ *   - the handle owns all device memory; input arrays are copied during the
+ *     call and stay owned by the caller;
+ *   - a state array is [E][4][N][N] doubles, element-major, then the
+ *     conservative variable (rho, rho u, rho v, E; Sec. 2.1 Eq. Q), then the
+ *     eta index j, then the xi index i of the solution point (X_i, X_j);
+ *     N = p + 1 points per direction;
+ *   - "on_device" = 1 means the pointer is CUDA device memory (for example a
+ *     torch tensor's data_ptr()), 0 means host memory;
+ *   - all work is queued on the stream given at creation; calls that return
+ *     data to the host synchronise that stream.
+ */
+#ifndef SSD_H
+#define SSD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SD_OK = 0,
+  SD_ERR_ARG = -1,         /* invalid argument (null pointer, bad p, dt <= 0 ...) */
+  SD_ERR_MESH = -2,        /* inconsistent mesh (unmatched face, folded cell ...) */
+  SD_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  SD_ERR_NONPHYSICAL = -4, /* a kernel met rho <= 0, p <= 0 or a non-finite value */
+  SD_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up */
+  SD_ERR_UNSUPPORTED = -6  /* valid request this build does not support (e.g. p) */
+};
+
+enum { SD_PREC_FP64 = 0, SD_PREC_FP32 = 1 };
+
+/* boundary tags of sd_mesh.bfaces */
+enum { SD_BC_WALL = 1 /* isothermal no-slip wall moving with its zone */ };
+
+/* Mesh (Sec. 3.1: every cell is mapped to the standard square [0,1]^2).
+ * Corners n0..n3 are counter-clockwise and map to (0,0), (1,0), (1,1), (0,1).
+ * Local face f: f0 = {eta=0} n0->n1, f1 = {xi=1} n1->n2, f2 = {eta=1} n3->n2,
+ * f3 = {xi=0} n0->n3 (the arrow is the direction of the face parameter).
+ * An edge flagged in edge_arc is the circular arc about `center` through its
+ * two corners (both at the same radius); other edges are straight.  The map of
+ * a cell is the transfinite interpolation of its four edges, i.e. the 4-node
+ * bilinear map when all edges are straight.  Faces shared by two cells of the
+ * same zone are found from their node pairs; every other face must appear in
+ * exactly one of bfaces, pfaces, iface_L, iface_R. */
+typedef struct {
+  int n_nodes;
+  const double *xy;        /* [n_nodes][2] */
+  int n_elems;
+  const int *elem_nodes;   /* [n_elems][4] */
+  const int *elem_zone;    /* [n_elems]: 0 stationary, 1 rotating (rigid rotation about center) */
+  const int *edge_arc;     /* [n_elems][4]: 1 if local face f is an arc */
+  int n_bfaces;
+  const int *bfaces;       /* [n_bfaces][3]: element, local face, SD_BC_* tag */
+  int n_pfaces;
+  const int *pfaces;       /* [n_pfaces][4]: periodic pair elemA, faceA, elemB, faceB */
+  int n_iface_L;
+  const int *iface_L;      /* [n][2]: element, local face on the interface, rotating side (Sec. 3.2 "left") */
+  int n_iface_R;
+  const int *iface_R;      /* [n][2]: stationary side ("right") */
+  double center[2];        /* rotation centre = centre of the interface circle */
+  double r_interface;      /* radius of the sliding interface */
+} sd_mesh;
+
+/* Gas, flow and run parameters (non-dimensional).  Viscous fluxes follow
+ * Sec. 2.1 with lambda = -2/3 mu and conductivity k = mu gamma Rgas /
+ * ((gamma - 1) prandtl). */
+typedef struct {
+  double gamma;     /* ratio of specific heats (Sec. 2.1: 1.4) */
+  double Rgas;      /* gas constant, p = rho Rgas T */
+  double mu;        /* dynamic viscosity (constant) */
+  double prandtl;   /* Prandtl number */
+  double omega;     /* angular velocity of the rotating zone (Sec. 2.2) */
+  double T_wall;    /* temperature of SD_BC_WALL faces */
+  int viscous;      /* 0 Euler, 1 Navier-Stokes */
+  int precision;    /* SD_PREC_FP64, or SD_PREC_FP32: FP32 interpolation, flux and
+                       divergence arithmetic; FP64 rotation angle, mortar geometry and
+                       projection weights, and FP64 state / Runge-Kutta accumulation */
+  void *stream;     /* cudaStream_t to queue work on; NULL = a non-blocking stream the handle creates */
+} sd_params;
+
+typedef struct sd_handle sd_handle;
+
+/* Build the solver for mesh m at polynomial degree p (N = p + 1 solution points
+ * per direction, Sec. 3.1; supported p = 2..5).  Validates the mesh, builds
+ * the face tables and the sorted interface lists, uploads the geometry and
+ * computes the t = 0 metrics on the device.  Time starts at 0 and the state
+ * is zero until sd_set_state.  On failure *out is NULL and the return code
+ * says why (the message is printed by sd_create_error()). */
+int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out);
+
+/* message of the last sd_create failure in this thread */
+const char *sd_create_error(void);
+
+/* Free the handle and its device memory (synchronises the stream first). */
+int sd_destroy(sd_handle *h);
+
+/* Message for the last failure on h (a static string owned by h). */
+const char *sd_last_error(const sd_handle *h);
+
+/* Sizes: number of elements, N, and number of conservative unknowns
+ * (E * 4 * N * N). Any pointer may be NULL. */
+int sd_info(const sd_handle *h, int *n_elems, int *N, long long *n_dofs);
+
+/* Copy the physical state Q (layout above) into the solver. */
+int sd_set_state(sd_handle *h, const double *Q, int on_device);
+
+/* Copy the current state out (synchronises). */
+int sd_get_state(sd_handle *h, double *Q, int on_device);
+
+/* Set / read the solution time t (the rotation angle is omega * t). */
+int sd_set_time(sd_handle *h, double t);
+int sd_get_time(sd_handle *h, double *t);
+
+/* Semi-discrete residual dQ/dt = -(dF~/dxi + dG~/deta) / |J| (Eq. computational
+ * with Eqs. Qt, Ft, Gt) at the current state and time, with the mortar
+ * coupling of Sec. 3.2 at the current rotation angle.  R has the state layout.
+ * Synchronises when R is host memory. */
+int sd_residual(sd_handle *h, double *R, int on_device);
+
+/* Advance nsteps steps of size dt with three-stage SSP Runge-Kutta (Sec. 3;
+ * stage times t, t + dt, t + dt/2; mortar connectivity rebuilt at every
+ * stage, Sec. 3.2).  Asynchronous: queued on the stream as CUDA-graph
+ * launches; errors detected on the device are reported by sd_sync. */
+int sd_step(sd_handle *h, double dt, int nsteps);
+
+/* Wait for queued work; returns SD_ERR_NONPHYSICAL if a stage produced
+ * rho <= 0, p <= 0 or a non-finite value since the last sd_sync. */
+int sd_sync(sd_handle *h);
+
+/* Physical coordinates of the solution points at time t, [E][N][N][2]. */
+int sd_sp_coords(sd_handle *h, double t, double *xy, int on_device);
+
+/* Measurement aid (the paper reports wall time split into interface and
+ * total time, Tables 3-10): runs reps steps outside the CUDA graph with CUDA
+ * events around each launch group on the handle's stream and writes the mean
+ * milliseconds per launch of ms[0] stage clock + mortar merge, ms[1]
+ * conforming, periodic and wall faces, ms[2] mortar projection + gather
+ * (the paper's "interface" work), ms[3] volume kernel (divergence, RK update,
+ * traces); ms[4] = mean milliseconds per whole step.  Advances the solution
+ * by reps steps; synchronises. */
+int sd_profile_step(sd_handle *h, double dt, int reps, double *ms);
+
+/* Measured FMA throughput of the current GPU in TFLOP/s (2 flops per FMA)
+ * for precision SD_PREC_FP64 or SD_PREC_FP32, from a probe kernel queued on
+ * the handle's stream; the denominator for FP64 / FP32 pipe utilisation.
+ * Synchronises. */
+int sd_fma_peak(sd_handle *h, int precision, double *tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSD_H */

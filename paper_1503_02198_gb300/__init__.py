@@ -1,0 +1,208 @@
+"""Thin Python binding of the C ABI in include/ssd.h (libssd.so).
+
+Argument marshalling only: every step of the residual and of the time step
+runs in the library's CUDA kernels.  Arrays may be numpy arrays (host memory)
+or CUDA torch tensors (device memory; passed by data pointer).  The library
+must have been built (``build()`` or ``__graft_entry__.build()``); importing
+this module never falls back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libssd.so")
+
+SD_OK = 0
+SD_ERR_ARG = -1
+SD_ERR_MESH = -2
+SD_ERR_CUDA = -3
+SD_ERR_NONPHYSICAL = -4
+SD_ERR_TIMEOUT = -5
+SD_ERR_UNSUPPORTED = -6
+SD_PREC_FP64 = 0
+SD_PREC_FP32 = 1
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+
+
+class sd_mesh(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int), ("xy", _c_dbl_p), ("n_elems", ctypes.c_int),
+                ("elem_nodes", _c_int_p), ("elem_zone", _c_int_p), ("edge_arc", _c_int_p),
+                ("n_bfaces", ctypes.c_int), ("bfaces", _c_int_p), ("n_pfaces", ctypes.c_int),
+                ("pfaces", _c_int_p), ("n_iface_L", ctypes.c_int), ("iface_L", _c_int_p),
+                ("n_iface_R", ctypes.c_int), ("iface_R", _c_int_p), ("center", ctypes.c_double * 2),
+                ("r_interface", ctypes.c_double)]
+
+
+class sd_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("Rgas", ctypes.c_double), ("mu", ctypes.c_double),
+                ("prandtl", ctypes.c_double), ("omega", ctypes.c_double), ("T_wall", ctypes.c_double),
+                ("viscous", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class SSDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"SSD error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    return _build_mod.build(force=force)
+
+
+def lib():
+    """Load libssd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first (build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.sd_create.argtypes = [ctypes.POINTER(sd_mesh), ctypes.c_int, ctypes.POINTER(sd_params),
+                                ctypes.POINTER(vp)]
+        L.sd_create_error.restype = ctypes.c_char_p
+        L.sd_destroy.argtypes = [vp]
+        L.sd_last_error.argtypes = [vp]
+        L.sd_last_error.restype = ctypes.c_char_p
+        L.sd_info.argtypes = [vp, _c_int_p, _c_int_p, ctypes.POINTER(ctypes.c_longlong)]
+        L.sd_set_state.argtypes = [vp, vp, ctypes.c_int]
+        L.sd_get_state.argtypes = [vp, vp, ctypes.c_int]
+        L.sd_set_time.argtypes = [vp, ctypes.c_double]
+        L.sd_get_time.argtypes = [vp, _c_dbl_p]
+        L.sd_residual.argtypes = [vp, vp, ctypes.c_int]
+        L.sd_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+        L.sd_sync.argtypes = [vp]
+        L.sd_sp_coords.argtypes = [vp, ctypes.c_double, vp, ctypes.c_int]
+        L.sd_profile_step.argtypes = [vp, ctypes.c_double, ctypes.c_int, _c_dbl_p]
+        L.sd_fma_peak.argtypes = [vp, ctypes.c_int, _c_dbl_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"need a C-contiguous {dtype} array")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    # torch tensor
+    if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+        raise ValueError("need a contiguous float64 tensor")
+    return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+class Solver:
+    """Owns one sd_handle; methods mirror the C ABI names."""
+
+    def __init__(self, mesh: dict, p: int, params, precision: int = SD_PREC_FP64, stream=None):
+        L = lib()
+        self._keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(x, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        xy = arr(mesh["xy"], np.float64)
+        en = arr(mesh["elem_nodes"], np.int32)
+        zone = arr(mesh["elem_zone"], np.int32)
+        arc = arr(mesh["edge_arc"], np.int32)
+        bf = arr(mesh["bfaces"], np.int32)
+        pf = arr(mesh["pfaces"], np.int32)
+        Lf = arr(mesh["ifaces_L"], np.int32)
+        Rf = arr(mesh["ifaces_R"], np.int32)
+
+        def ip(a):
+            return a.ctypes.data_as(_c_int_p)
+
+        m = sd_mesh(len(xy), xy.ctypes.data_as(_c_dbl_p), len(en), ip(en), ip(zone), ip(arc), len(bf), ip(bf),
+                    len(pf), ip(pf), len(Lf), ip(Lf), len(Rf), ip(Rf),
+                    (ctypes.c_double * 2)(float(mesh["center"][0]), float(mesh["center"][1])),
+                    float(mesh["r_interface"]))
+        prm = sd_params(params.gamma, params.Rgas, params.mu, params.prandtl, params.omega, params.T_wall,
+                        int(params.viscous), int(precision), ctypes.c_void_p(stream) if stream else None)
+        h = ctypes.c_void_p()
+        rc = L.sd_create(ctypes.byref(m), p, ctypes.byref(prm), ctypes.byref(h))
+        if rc != SD_OK:
+            raise SSDError(rc, L.sd_create_error().decode())
+        self._h = h
+        self.p, self.N = p, p + 1
+        E, N, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        L.sd_info(h, ctypes.byref(E), ctypes.byref(N), ctypes.byref(n))
+        self.E, self.n_dofs = E.value, n.value
+        self.shape = (self.E, 4, self.N, self.N)
+
+    def _check(self, rc):
+        if rc != SD_OK:
+            raise SSDError(rc, lib().sd_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def sd_set_state(self, Q):
+        p, dev = _ptr(Q, np.float64)
+        self._check(lib().sd_set_state(self._h, p, dev))
+
+    def sd_get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, dev = _ptr(out, np.float64)
+        self._check(lib().sd_get_state(self._h, p, dev))
+        return out
+
+    def sd_set_time(self, t):
+        self._check(lib().sd_set_time(self._h, float(t)))
+
+    def sd_get_time(self):
+        t = ctypes.c_double()
+        self._check(lib().sd_get_time(self._h, ctypes.byref(t)))
+        return t.value
+
+    def sd_residual(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        p, dev = _ptr(out, np.float64)
+        self._check(lib().sd_residual(self._h, p, dev))
+        return out
+
+    def sd_step(self, dt, nsteps=1):
+        self._check(lib().sd_step(self._h, float(dt), int(nsteps)))
+
+    def sd_sync(self):
+        self._check(lib().sd_sync(self._h))
+
+    def sd_sp_coords(self, t=0.0, out=None):
+        if out is None:
+            out = np.empty((self.E, self.N, self.N, 2))
+        p, dev = _ptr(out, np.float64)
+        self._check(lib().sd_sp_coords(self._h, float(t), p, dev))
+        return out
+
+    def sd_profile_step(self, dt, reps=1):
+        ms = (ctypes.c_double * 5)()
+        self._check(lib().sd_profile_step(self._h, float(dt), int(reps), ms))
+        return {"merge": ms[0], "faces": ms[1], "mortar": ms[2], "volume": ms[3], "step": ms[4]}
+
+    def sd_fma_peak(self, precision):
+        v = ctypes.c_double()
+        self._check(lib().sd_fma_peak(self._h, int(precision), ctypes.byref(v)))
+        return v.value
+
+    def state_from(self, field_fn, t=0.0):
+        xy = self.sd_sp_coords(t)
+        return np.ascontiguousarray(np.moveaxis(field_fn(xy[..., 0], xy[..., 1]), -1, 1))

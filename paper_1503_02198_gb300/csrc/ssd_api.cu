@@ -1,0 +1,797 @@
+// ssd_api.cu -- host driver behind the C ABI of include/ssd.h: mesh checks,
+// face tables, interface lists, device buffers, CUDA-graph step loop.  All
+// per-stage arithmetic runs in the kernels of ssd_engine.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ssd.h"
+#include "ssd_internal.h"
+
+using namespace ssd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr double kPi = 3.14159265358979323846264338328;
+
+// ---------------------------------------------------------------------------
+// basis of Sec. 3.1 for one N, in FP64
+// ---------------------------------------------------------------------------
+
+// Legendre P_n and P_n' by the Bonnet recurrence
+void legendre_pn(int n, double x, double &p, double &dp) {
+  double pm1 = 1.0, pc = x;
+  if (n == 0) {
+    p = 1.0;
+    dp = 0.0;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    const double pn = ((2 * k + 1) * x * pc - k * pm1) / (k + 1);
+    pm1 = pc;
+    pc = pn;
+  }
+  p = pc;
+  dp = n * (pm1 - x * pc) / (1.0 - x * x);
+}
+
+// Gauss-Legendre nodes and weights on [0,1], ascending
+void gauss_legendre01(int n, double *z, double *w) {
+  for (int k = 0; k < n; ++k) {
+    // Chebyshev-like initial guess for root k (descending), then Newton
+    double x = -std::cos(kPi * (k + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre_pn(n, x, p, dp);
+      const double dx = p / dp;
+      x -= dx;
+      if (std::fabs(dx) <= 1e-16 * std::max(1.0, std::fabs(x))) break;
+    }
+    double p, dp;
+    legendre_pn(n, x, p, dp);
+    z[k] = 0.5 * (x + 1.0);
+    w[k] = 1.0 / ((1.0 - x * x) * dp * dp);  // (2 / ((1-x^2) P'^2)) / 2 for [0,1]
+  }
+  // ascending order
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && z[j] < z[j - 1]; --j) {
+      std::swap(z[j], z[j - 1]);
+      std::swap(w[j], w[j - 1]);
+    }
+}
+
+// Lagrange basis on nodes xs[0..n-1] by barycentric weights
+struct Lagrange {
+  int n;
+  double x[kMaxN + 1], bw[kMaxN + 1];
+  Lagrange(const double *nodes, int n_) : n(n_) {
+    for (int i = 0; i < n; ++i) {
+      x[i] = nodes[i];
+      double d = 1.0;
+      for (int k = 0; k < n; ++k)
+        if (k != i) d *= nodes[i] - nodes[k];
+      bw[i] = 1.0 / d;
+    }
+  }
+  double value(int i, double t) const {
+    double v = bw[i];
+    for (int k = 0; k < n; ++k)
+      if (k != i) v *= t - x[k];
+    return v;
+  }
+  double deriv(int i, double t) const {
+    double s = 0.0;
+    for (int m = 0; m < n; ++m) {
+      if (m == i) continue;
+      double v = bw[i];
+      for (int k = 0; k < n; ++k)
+        if (k != i && k != m) v *= t - x[k];
+      s += v;
+    }
+    return s;
+  }
+};
+
+bool build_basis(int N, HostBasis &hb) {
+  std::memset(&hb, 0, sizeof hb);
+  hb.N = N;
+  for (int s = 0; s < N; ++s) hb.Xs[s] = 0.5 - 0.5 * std::cos(kPi * (2.0 * s + 1.0) / (2.0 * N));
+  double z[kMaxN], w[kMaxN];
+  gauss_legendre01(N - 1, z, w);
+  hb.Xf[0] = 0.0;
+  for (int k = 0; k < N - 1; ++k) hb.Xf[k + 1] = z[k];
+  hb.Xf[N] = 1.0;
+  Lagrange h(hb.Xs, N), l(hb.Xf, N + 1);
+  for (int i = 0; i <= N; ++i)
+    for (int k = 0; k < N; ++k) hb.Hf[i * N + k] = h.value(k, hb.Xf[i]);
+  for (int k = 0; k < N; ++k)
+    for (int i = 0; i <= N; ++i) hb.Dm[k * (N + 1) + i] = l.deriv(i, hb.Xs[k]);
+  for (int k = 0; k < N; ++k) {
+    hb.H0[k] = h.value(k, 0.0);
+    hb.H1[k] = h.value(k, 1.0);
+    hb.cden[k] = h.bw[k];
+  }
+  gauss_legendre01(N, hb.zq, hb.wq);
+  for (int q = 0; q < N; ++q)
+    for (int j = 0; j < N; ++j) hb.Hz[q * N + j] = h.value(j, hb.zq[q]);
+  // M_ij = sum_q w_q h_i(z_q) h_j(z_q); invert by Gauss-Jordan
+  double A[kMaxN][2 * kMaxN];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double m = 0.0;
+      for (int q = 0; q < N; ++q) m += hb.wq[q] * hb.Hz[q * N + i] * hb.Hz[q * N + j];
+      A[i][j] = m;
+      A[i][N + j] = i == j ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < N; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < N; ++r)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0) return false;
+    for (int j = 0; j < 2 * N; ++j) std::swap(A[c][j], A[piv][j]);
+    const double d = 1.0 / A[c][c];
+    for (int j = 0; j < 2 * N; ++j) A[c][j] *= d;
+    for (int r = 0; r < N; ++r) {
+      if (r == c) continue;
+      const double f = A[r][c];
+      if (f != 0.0)
+        for (int j = 0; j < 2 * N; ++j) A[r][j] -= f * A[c][j];
+    }
+  }
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) hb.Minv[i * N + j] = A[i][N + j];
+  return true;
+}
+
+// FMA throughput probe: 8 independent FMA chains per thread
+template <typename T>
+__global__ void k_fma_probe(T *out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  T acc = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc += x[k];
+  if (acc == (T)-1.2345) out[0] = acc;  // keeps the loop alive
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+
+struct sd_handle {
+  int N = 0, E = 0, precision = 0;
+  double center[2] = {0, 0};
+  sd_params prm{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Engine *eng = nullptr;
+  MeshDev md{};
+  std::vector<void *> allocs;
+  double *QA = nullptr, *QB = nullptr, *scratch = nullptr;
+  bool traces_valid = false;
+  cudaGraphExec_t step_exec = nullptr;
+  double graph_dt = 0.0;
+  double *h_pinned = nullptr;  // small pinned buffer for clock reads / writes
+  std::string err;
+};
+
+namespace {
+
+int fail(sd_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(sd_handle *h, cudaError_t e, const char *what) {
+  return fail(h, SD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename P>
+cudaError_t dalloc(sd_handle *h, P **ptr, size_t bytes) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e == cudaSuccess) {
+    h->allocs.push_back(p);
+    *ptr = (P *)p;
+  }
+  return e;
+}
+
+template <typename P>
+cudaError_t upload(sd_handle *h, P **ptr, const P *src, size_t count) {
+  cudaError_t e = dalloc(h, ptr, sizeof(P) * count);
+  if (e == cudaSuccess && count)
+    e = cudaMemcpyAsync(*ptr, src, sizeof(P) * count, cudaMemcpyHostToDevice, h->stream);
+  return e;
+}
+
+const int kFaceA[4] = {0, 1, 3, 0};  // start corner of the face parameter
+const int kFaceB[4] = {1, 2, 2, 3};  // end corner
+
+struct IfaceSide {
+  std::vector<int4> face;
+  std::vector<double> a, w, S;
+};
+
+int build_iface(sd_handle *h, const sd_mesh *m, int n, const int *lst, std::vector<int> &kind, int tag,
+                IfaceSide &out) {
+  struct Item { int ef, rev; double a, w, S; };
+  std::vector<Item> items;
+  const double cx = m->center[0], cy = m->center[1];
+  for (int k = 0; k < n; ++k) {
+    const int e = lst[2 * k], f = lst[2 * k + 1];
+    if (e < 0 || e >= m->n_elems || f < 0 || f > 3) return fail(h, SD_ERR_MESH, "interface face index out of range");
+    const int ef = 4 * e + f;
+    if (kind[ef] != -1) return fail(h, SD_ERR_MESH, "interface face listed twice or also a boundary");
+    kind[ef] = tag;
+    if (!m->edge_arc[ef]) return fail(h, SD_ERR_MESH, "interface face is not flagged as an arc");
+    const int na = m->elem_nodes[4 * e + kFaceA[f]], nb = m->elem_nodes[4 * e + kFaceB[f]];
+    const double ax = m->xy[2 * na] - cx, ay = m->xy[2 * na + 1] - cy;
+    const double bx = m->xy[2 * nb] - cx, by = m->xy[2 * nb + 1] - cy;
+    const double ra = std::hypot(ax, ay), rb = std::hypot(bx, by);
+    if (std::fabs(ra - m->r_interface) > 1e-9 * std::max(1.0, m->r_interface) ||
+        std::fabs(rb - m->r_interface) > 1e-9 * std::max(1.0, m->r_interface))
+      return fail(h, SD_ERR_MESH, "interface node not on the interface circle");
+    const double d = std::atan2(ax * by - ay * bx, ax * bx + ay * by);  // signed angle a -> b
+    Item it;
+    it.ef = ef;
+    double start = d > 0 ? std::atan2(ay, ax) : std::atan2(by, bx);
+    start = std::fmod(start, 2 * kPi);
+    if (start < 0) start += 2 * kPi;
+    it.a = start;
+    it.w = std::fabs(d);
+    it.rev = d > 0 ? 0 : 1;
+    it.S = ra * it.w;
+    items.push_back(it);
+  }
+  std::sort(items.begin(), items.end(), [](const Item &p, const Item &q) { return p.a < q.a; });
+  double total = 0.0;
+  for (int k = 0; k < n; ++k) {
+    total += items[k].w;
+    const Item &p = items[k], &q = items[(k + 1) % n];
+    double gap = std::fmod(q.a - (p.a + p.w) + 4 * kPi, 2 * kPi);
+    if (gap > kPi) gap -= 2 * kPi;
+    if (std::fabs(gap) > 1e-9) return fail(h, SD_ERR_MESH, "interface faces do not tile the circle");
+  }
+  if (n > 0 && std::fabs(total - 2 * kPi) > 1e-9) return fail(h, SD_ERR_MESH, "interface side does not close");
+  for (auto &it : items) {
+    out.face.push_back(make_int4(it.ef, it.rev, 0, 0));
+    out.a.push_back(it.a);
+    out.w.push_back(it.w);
+    out.S.push_back(it.S);
+  }
+  return SD_OK;
+}
+
+int build_mesh(sd_handle *h, const sd_mesh *m) {
+  const int E = m->n_elems;
+  if (E <= 0 || !m->xy || !m->elem_nodes || !m->elem_zone || !m->edge_arc || m->n_nodes <= 0)
+    return fail(h, SD_ERR_ARG, "mesh arrays missing");
+  for (int k = 0; k < 4 * E; ++k)
+    if (m->elem_nodes[k] < 0 || m->elem_nodes[k] >= m->n_nodes) return fail(h, SD_ERR_MESH, "node index out of range");
+  for (int e = 0; e < E; ++e)
+    if (m->elem_zone[e] != 0 && m->elem_zone[e] != 1) return fail(h, SD_ERR_MESH, "zone must be 0 or 1");
+  std::vector<int> kind(4 * E, -1);  // 0 conforming/periodic, 1 boundary, 2 L, 3 R
+  std::vector<int4> faces, bfaces;
+  // boundary faces
+  for (int k = 0; k < m->n_bfaces; ++k) {
+    const int e = m->bfaces[3 * k], f = m->bfaces[3 * k + 1], tag = m->bfaces[3 * k + 2];
+    if (e < 0 || e >= E || f < 0 || f > 3) return fail(h, SD_ERR_MESH, "boundary face index out of range");
+    if (tag != SD_BC_WALL) return fail(h, SD_ERR_UNSUPPORTED, "unsupported boundary tag");
+    if (kind[4 * e + f] != -1) return fail(h, SD_ERR_MESH, "boundary face listed twice");
+    kind[4 * e + f] = 1;
+    bfaces.push_back(make_int4(4 * e + f, tag, 0, 0));
+  }
+  // periodic pairs: orientation from the translation between the two faces
+  for (int k = 0; k < m->n_pfaces; ++k) {
+    const int *p = m->pfaces + 4 * k;
+    if (p[0] < 0 || p[0] >= E || p[2] < 0 || p[2] >= E || p[1] < 0 || p[1] > 3 || p[3] < 0 || p[3] > 3)
+      return fail(h, SD_ERR_MESH, "periodic face index out of range");
+    const int efA = 4 * p[0] + p[1], efB = 4 * p[2] + p[3];
+    if (kind[efA] != -1 || kind[efB] != -1) return fail(h, SD_ERR_MESH, "periodic face listed twice");
+    if (m->elem_zone[p[0]] != 0 || m->elem_zone[p[2]] != 0)
+      return fail(h, SD_ERR_MESH, "periodic faces must lie in the stationary zone");
+    kind[efA] = kind[efB] = 0;
+    const int a0 = m->elem_nodes[4 * p[0] + kFaceA[p[1]]], a1 = m->elem_nodes[4 * p[0] + kFaceB[p[1]]];
+    const int b0 = m->elem_nodes[4 * p[2] + kFaceA[p[3]]], b1 = m->elem_nodes[4 * p[2] + kFaceB[p[3]]];
+    const double tx = 0.5 * (m->xy[2 * b0] + m->xy[2 * b1] - m->xy[2 * a0] - m->xy[2 * a1]);
+    const double ty = 0.5 * (m->xy[2 * b0 + 1] + m->xy[2 * b1 + 1] - m->xy[2 * a0 + 1] - m->xy[2 * a1 + 1]);
+    const double same = std::hypot(m->xy[2 * a0] + tx - m->xy[2 * b0], m->xy[2 * a0 + 1] + ty - m->xy[2 * b0 + 1]);
+    const double flip = std::hypot(m->xy[2 * a0] + tx - m->xy[2 * b1], m->xy[2 * a0 + 1] + ty - m->xy[2 * b1 + 1]);
+    faces.push_back(make_int4(efA, efB, flip < same ? 1 : 0, 0));
+  }
+  IfaceSide L, R;
+  int rc;
+  if ((m->n_iface_L > 0) != (m->n_iface_R > 0)) return fail(h, SD_ERR_MESH, "interface needs both sides");
+  if ((rc = build_iface(h, m, m->n_iface_L, m->iface_L, kind, 2, L))) return rc;
+  if ((rc = build_iface(h, m, m->n_iface_R, m->iface_R, kind, 3, R))) return rc;
+  for (const int4 &f : L.face)
+    if (m->elem_zone[f.x / 4] != 1) return fail(h, SD_ERR_MESH, "rotating-side interface face not in zone 1");
+  for (const int4 &f : R.face)
+    if (m->elem_zone[f.x / 4] != 0) return fail(h, SD_ERR_MESH, "stationary-side interface face not in zone 0");
+  // conforming faces: shared node pairs
+  std::unordered_map<long long, int> open;
+  open.reserve(4 * (size_t)E);
+  for (int ef = 0; ef < 4 * E; ++ef) {
+    if (kind[ef] != -1) continue;
+    const int e = ef / 4, f = ef % 4;
+    const int a = m->elem_nodes[4 * e + kFaceA[f]], b = m->elem_nodes[4 * e + kFaceB[f]];
+    if (a == b) return fail(h, SD_ERR_MESH, "degenerate face");
+    const long long key = (long long)std::min(a, b) * m->n_nodes + std::max(a, b);
+    auto it = open.find(key);
+    if (it == open.end()) {
+      open.emplace(key, ef);
+    } else {
+      const int efA = it->second;
+      open.erase(it);
+      const int eA = efA / 4, fA = efA % 4;
+      if (m->elem_zone[eA] != m->elem_zone[e]) return fail(h, SD_ERR_MESH, "conforming face joins the two zones");
+      const int a0 = m->elem_nodes[4 * eA + kFaceA[fA]];
+      faces.push_back(make_int4(efA, ef, a0 == a ? 0 : 1, 0));
+      kind[efA] = kind[ef] = 0;
+    }
+  }
+  if (!open.empty()) {
+    const int ef = open.begin()->second;
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "face %d of element %d has no neighbour and no boundary condition", ef % 4, ef / 4);
+    return fail(h, SD_ERR_MESH, buf);
+  }
+  // device copies
+  MeshDev &md = h->md;
+  md.E = E;
+  md.N = h->N;
+  md.nF = (int)faces.size();
+  md.nB = (int)bfaces.size();
+  md.nL = (int)L.face.size();
+  md.nR = (int)R.face.size();
+  md.nM = md.nL + md.nR;
+  std::vector<double> corners(8 * (size_t)E);
+  std::vector<int> arcs(E);
+  for (int e = 0; e < E; ++e) {
+    for (int k = 0; k < 4; ++k) {
+      const int n = m->elem_nodes[4 * e + k];
+      corners[8 * (size_t)e + 2 * k] = m->xy[2 * n] - m->center[0];
+      corners[8 * (size_t)e + 2 * k + 1] = m->xy[2 * n + 1] - m->center[1];
+    }
+    int bits = 0;
+    for (int f = 0; f < 4; ++f)
+      if (m->edge_arc[4 * e + f]) {
+        bits |= 1 << f;
+        // both corners of an arc edge must sit at the same radius
+        const double *c = &corners[8 * (size_t)e];
+        const int ia = kFaceA[f], ib = kFaceB[f];
+        const double ra = std::hypot(c[2 * ia], c[2 * ia + 1]), rb = std::hypot(c[2 * ib], c[2 * ib + 1]);
+        if (std::fabs(ra - rb) > 1e-9 * std::max(1.0, ra)) return fail(h, SD_ERR_MESH, "arc edge corners at different radii");
+      }
+    arcs[e] = bits;
+  }
+  cudaError_t ce;
+  int4 *dfaces, *dbfaces, *dL, *dR;
+  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS;
+  int *darcs, *dzone;
+  if ((ce = upload(h, &dfaces, faces.data(), faces.size())) || (ce = upload(h, &dbfaces, bfaces.data(), bfaces.size())) ||
+      (ce = upload(h, &dL, L.face.data(), L.face.size())) || (ce = upload(h, &dR, R.face.data(), R.face.size())) ||
+      (ce = upload(h, &dLa, L.a.data(), L.a.size())) || (ce = upload(h, &dLw, L.w.data(), L.w.size())) ||
+      (ce = upload(h, &dLS, L.S.data(), L.S.size())) || (ce = upload(h, &dRa, R.a.data(), R.a.size())) ||
+      (ce = upload(h, &dRw, R.w.data(), R.w.size())) || (ce = upload(h, &dRS, R.S.data(), R.S.size())) ||
+      (ce = upload(h, &dcorn, corners.data(), corners.size())) || (ce = upload(h, &darcs, arcs.data(), arcs.size())) ||
+      (ce = upload(h, &dzone, m->elem_zone, (size_t)E)))
+    return cuda_fail(h, ce, "mesh upload");
+  md.faces = dfaces;
+  md.bfaces = dbfaces;
+  md.Lface = dL;
+  md.Rface = dR;
+  md.La = dLa;
+  md.Lw = dLw;
+  md.LS = dLS;
+  md.Ra = dRa;
+  md.Rw = dRw;
+  md.RS = dRS;
+  md.corners = dcorn;
+  md.arcs = darcs;
+  md.zone = dzone;
+  // (host vectors are released when this function returns: wait for the copies)
+  if ((ce = cudaStreamSynchronize(h->stream))) return cuda_fail(h, ce, "mesh upload");
+  return SD_OK;
+}
+
+cudaError_t alloc_buffers(sd_handle *h) {
+  MeshDev &md = h->md;
+  const size_t E = md.E, N = h->N, nb = md.nM;
+  const size_t w = h->eng->compute_word();
+  cudaError_t e;
+  double *bxy;
+  DevClock *clk;
+  if ((e = dalloc(h, &h->QA, sizeof(double) * E * 4 * N * N))) return e;
+  if ((e = dalloc(h, &h->QB, sizeof(double) * E * 4 * N * N))) return e;
+  if ((e = dalloc(h, &md.geo, w * E * h->eng->geo_words()))) return e;
+  if ((e = dalloc(h, &md.TR, w * E * 16 * N))) return e;
+  if ((e = dalloc(h, &md.CF, w * E * 16 * N))) return e;
+  if ((e = dalloc(h, &md.contrib, w * 2 * nb * 4 * N))) return e;
+  if ((e = dalloc(h, &md.mLf, sizeof(int) * nb))) return e;
+  if ((e = dalloc(h, &md.mRf, sizeof(int) * nb))) return e;
+  if ((e = dalloc(h, &md.mgeo, sizeof(double) * 6 * nb))) return e;
+  if ((e = dalloc(h, &md.Lstart, sizeof(int) * md.nL))) return e;
+  if ((e = dalloc(h, &md.Lcount, sizeof(int) * md.nL))) return e;
+  if ((e = dalloc(h, &md.Rstart, sizeof(int) * md.nR))) return e;
+  if ((e = dalloc(h, &md.Rcount, sizeof(int) * md.nR))) return e;
+  if ((e = dalloc(h, &bxy, sizeof(double) * 2 * N * md.nB))) return e;
+  if ((e = dalloc(h, &clk, sizeof(DevClock)))) return e;
+  md.bxy = bxy;
+  md.clk = clk;
+  if ((e = cudaMemsetAsync(h->QA, 0, sizeof(double) * E * 4 * N * N, h->stream))) return e;
+  if ((e = cudaMemsetAsync(clk, 0, sizeof(DevClock), h->stream))) return e;
+  if ((e = cudaMemsetAsync(md.CF, 0, w * E * 16 * N, h->stream))) return e;
+  return cudaSuccess;
+}
+
+int read_flags(sd_handle *h, int *flags, bool clear) {
+  cudaError_t e = cudaMemcpyAsync(h->h_pinned, &h->md.clk->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (e) return cuda_fail(h, e, "reading device flags");
+  std::memcpy(flags, h->h_pinned, sizeof(int));
+  if (clear && *flags) {
+    e = cudaMemsetAsync(&h->md.clk->flags, 0, sizeof(int), h->stream);
+    if (!e) e = cudaStreamSynchronize(h->stream);
+    if (e) return cuda_fail(h, e, "clearing device flags");
+  }
+  return SD_OK;
+}
+
+void free_handle(sd_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  delete h->eng;
+  for (void *p : h->allocs) cudaFree(p);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+// queue the three SSP-RK3 stages of one step (Shu-Osher form)
+void queue_step(sd_handle *h, double dt) {
+  MeshDev &md = h->md;
+  Engine *g = h->eng;
+  cudaStream_t s = h->stream;
+  g->couple(md, 0.0, dt, s);
+  g->volume(md, h->QA, nullptr, h->QB, nullptr, 0.0, 1.0, dt, MODE_RK, s);
+  g->couple(md, 1.0, dt, s);
+  g->volume(md, h->QB, h->QA, h->QB, nullptr, 0.75, 0.25, dt, MODE_RK, s);
+  g->couple(md, 0.5, dt, s);
+  g->volume(md, h->QB, h->QA, h->QA, nullptr, 1.0 / 3.0, 2.0 / 3.0, dt, MODE_RK, s);
+  g->advance(md, dt, s);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *sd_create_error(void) { return g_create_error.c_str(); }
+
+int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
+  g_create_error.clear();
+  if (!out) return SD_ERR_ARG;
+  *out = nullptr;
+  if (!m || !prm) {
+    g_create_error = "null mesh or params";
+    return SD_ERR_ARG;
+  }
+  const int N = p + 1;
+  if (N < 3 || N > 6) {
+    g_create_error = "supported polynomial degrees are p = 2..5";
+    return SD_ERR_UNSUPPORTED;
+  }
+  if (!(prm->gamma > 1.0) || !(prm->Rgas > 0.0) || !std::isfinite(prm->omega) ||
+      (prm->viscous && (!(prm->mu >= 0.0) || !(prm->prandtl > 0.0) || !(prm->T_wall > 0.0)))) {
+    g_create_error = "invalid gas / flow parameters";
+    return SD_ERR_ARG;
+  }
+  if (prm->viscous) {
+    g_create_error = "viscous fluxes are not built in this library version";
+    return SD_ERR_UNSUPPORTED;
+  }
+  if (prm->precision != SD_PREC_FP64 && prm->precision != SD_PREC_FP32) {
+    g_create_error = "unknown precision";
+    return SD_ERR_ARG;
+  }
+  sd_handle *h = new sd_handle();
+  h->N = N;
+  h->E = m->n_elems;
+  h->prm = *prm;
+  h->precision = prm->precision;
+  h->center[0] = m->center[0];
+  h->center[1] = m->center[1];
+  cudaError_t ce;
+  if (prm->stream) {
+    h->stream = (cudaStream_t)prm->stream;
+  } else {
+    if ((ce = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking))) {
+      g_create_error = std::string("stream: ") + cudaGetErrorString(ce);
+      free_handle(h);
+      return SD_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  int rc = SD_OK;
+  HostBasis hb;
+  if (!build_basis(N, hb)) rc = fail(h, SD_ERR_ARG, "singular mortar mass matrix");
+  if (!rc) rc = build_mesh(h, m);
+  if (!rc) {
+    h->eng = prm->precision == SD_PREC_FP64 ? make_engine_f64(N) : make_engine_f32(N);
+    if (!h->eng) rc = fail(h, SD_ERR_UNSUPPORTED, "no engine for this N");
+  }
+  if (!rc && (ce = cudaMallocHost(&h->h_pinned, 64))) rc = cuda_fail(h, ce, "pinned buffer");
+  if (!rc) {
+    MeshDev &md = h->md;
+    md.omega = prm->omega;
+    md.gamma = prm->gamma;
+    md.Rgas = prm->Rgas;
+    md.mu = prm->mu;
+    md.prandtl = prm->prandtl;
+    md.T_wall = prm->T_wall;
+    md.viscous = prm->viscous;
+    md.r_interface = m->r_interface;
+    if ((ce = alloc_buffers(h))) rc = cuda_fail(h, ce, "device buffers");
+  }
+  if (!rc && (ce = h->eng->init(hb, h->md, h->stream))) rc = cuda_fail(h, ce, "engine init");
+  if (!rc && (ce = cudaGetLastError())) rc = cuda_fail(h, ce, "geometry kernels");
+  if (!rc) {
+    int flags = 0;
+    rc = read_flags(h, &flags, false);
+    if (!rc && (flags & 2)) rc = fail(h, SD_ERR_MESH, "a cell has a non-positive Jacobian (folded or clockwise cell)");
+  }
+  if (rc) {
+    g_create_error = h->err;
+    free_handle(h);
+    return rc;
+  }
+  *out = h;
+  return SD_OK;
+}
+
+int sd_destroy(sd_handle *h) {
+  free_handle(h);
+  return SD_OK;
+}
+
+const char *sd_last_error(const sd_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+int sd_info(const sd_handle *h, int *n_elems, int *N, long long *n_dofs) {
+  if (!h) return SD_ERR_ARG;
+  if (n_elems) *n_elems = h->E;
+  if (N) *N = h->N;
+  if (n_dofs) *n_dofs = (long long)h->E * 4 * h->N * h->N;
+  return SD_OK;
+}
+
+static size_t state_bytes(const sd_handle *h) { return sizeof(double) * (size_t)h->E * 4 * h->N * h->N; }
+
+int sd_set_state(sd_handle *h, const double *Q, int on_device) {
+  if (!h || !Q) return fail(h, SD_ERR_ARG, "null argument");
+  cudaError_t e = cudaMemcpyAsync(h->QA, Q, state_bytes(h), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (!e && !on_device) e = cudaStreamSynchronize(h->stream);  // caller may reuse Q at once
+  if (e) return cuda_fail(h, e, "sd_set_state");
+  h->traces_valid = false;
+  return SD_OK;
+}
+
+int sd_get_state(sd_handle *h, double *Q, int on_device) {
+  if (!h || !Q) return fail(h, SD_ERR_ARG, "null argument");
+  cudaError_t e = cudaMemcpyAsync(Q, h->QA, state_bytes(h), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (e) return cuda_fail(h, e, "sd_get_state");
+  return SD_OK;
+}
+
+int sd_set_time(sd_handle *h, double t) {
+  if (!h || !std::isfinite(t)) return fail(h, SD_ERR_ARG, "bad time");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (!e) {
+    h->h_pinned[0] = t;
+    e = cudaMemcpyAsync(&h->md.clk->t_n, h->h_pinned, sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  }
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (e) return cuda_fail(h, e, "sd_set_time");
+  return SD_OK;
+}
+
+int sd_get_time(sd_handle *h, double *t) {
+  if (!h || !t) return fail(h, SD_ERR_ARG, "null argument");
+  cudaError_t e = cudaMemcpyAsync(h->h_pinned, &h->md.clk->t_n, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (e) return cuda_fail(h, e, "sd_get_time");
+  *t = h->h_pinned[0];
+  return SD_OK;
+}
+
+int sd_residual(sd_handle *h, double *R, int on_device) {
+  if (!h || !R) return fail(h, SD_ERR_ARG, "null argument");
+  double *dst = R;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    if (!h->scratch) e = dalloc(h, &h->scratch, state_bytes(h));
+    if (e) return cuda_fail(h, e, "residual scratch");
+    dst = h->scratch;
+  }
+  h->eng->trace(h->md, h->QA, h->stream);
+  h->eng->couple(h->md, 0.0, 0.0, h->stream);
+  h->eng->volume(h->md, h->QA, nullptr, nullptr, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
+  if ((e = cudaGetLastError())) return cuda_fail(h, e, "residual kernels");
+  h->traces_valid = true;
+  if (!on_device) {
+    e = cudaMemcpyAsync(R, dst, state_bytes(h), cudaMemcpyDeviceToHost, h->stream);
+    if (!e) e = cudaStreamSynchronize(h->stream);
+    if (e) return cuda_fail(h, e, "sd_residual copy");
+  }
+  return SD_OK;
+}
+
+int sd_step(sd_handle *h, double dt, int nsteps) {
+  if (!h) return SD_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(h, SD_ERR_ARG, "dt must be positive and nsteps >= 0");
+  if (nsteps == 0) return SD_OK;
+  cudaError_t e;
+  if (!h->traces_valid) {
+    h->eng->trace(h->md, h->QA, h->stream);
+    if ((e = cudaGetLastError())) return cuda_fail(h, e, "trace kernel");
+    h->traces_valid = true;
+  }
+  if (!h->step_exec || h->graph_dt != dt) {
+    if (h->step_exec) {
+      cudaGraphExecDestroy(h->step_exec);
+      h->step_exec = nullptr;
+    }
+    cudaGraph_t graph;
+    if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal))) return cuda_fail(h, e, "graph capture");
+    queue_step(h, dt);
+    cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (le) return cuda_fail(h, le, "graph capture (launch)");
+    if (e) return cuda_fail(h, e, "graph capture (end)");
+    e = cudaGraphInstantiate(&h->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e) return cuda_fail(h, e, "graph instantiate");
+    h->graph_dt = dt;
+  }
+  for (int k = 0; k < nsteps; ++k)
+    if ((e = cudaGraphLaunch(h->step_exec, h->stream))) return cuda_fail(h, e, "graph launch");
+  return SD_OK;
+}
+
+int sd_sync(sd_handle *h) {
+  if (!h) return SD_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return cuda_fail(h, e, "sd_sync");
+  int flags = 0;
+  int rc = read_flags(h, &flags, true);
+  if (rc) return rc;
+  if (flags & 1) return fail(h, SD_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite)");
+  return SD_OK;
+}
+
+int sd_sp_coords(sd_handle *h, double t, double *xy, int on_device) {
+  if (!h || !xy || !std::isfinite(t)) return fail(h, SD_ERR_ARG, "bad argument");
+  const size_t bytes = sizeof(double) * (size_t)h->E * h->N * h->N * 2;
+  double *dst = xy;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    e = cudaMalloc(&dst, bytes);
+    if (e) return cuda_fail(h, e, "coordinate buffer");
+  }
+  h->eng->sp_coords(h->md, t, h->center[0], h->center[1], dst, h->stream);
+  e = cudaGetLastError();
+  if (!e && !on_device) e = cudaMemcpyAsync(xy, dst, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (!on_device) cudaFree(dst);
+  if (e) return cuda_fail(h, e, "sd_sp_coords");
+  return SD_OK;
+}
+
+int sd_profile_step(sd_handle *h, double dt, int reps, double *ms) {
+  if (!h || !ms || reps <= 0 || !(dt > 0.0)) return fail(h, SD_ERR_ARG, "bad argument");
+  cudaError_t e;
+  cudaEvent_t ev[6];
+  for (int k = 0; k < 6; ++k)
+    if ((e = cudaEventCreate(&ev[k]))) return cuda_fail(h, e, "event");
+  if (!h->traces_valid) {
+    h->eng->trace(h->md, h->QA, h->stream);
+    h->traces_valid = true;
+  }
+  double acc[5] = {0, 0, 0, 0, 0};
+  const double cs[3] = {0.0, 1.0, 0.5}, al[3] = {0.0, 0.75, 1.0 / 3.0}, be[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int r = 0; r < reps && !e; ++r) {
+    float t;
+    cudaEventRecord(ev[5], h->stream);
+    for (int k = 0; k < 3; ++k) {
+      const double *qin = k == 0 ? h->QA : h->QB;
+      const double *qb = k == 0 ? nullptr : h->QA;
+      double *qo = k == 2 ? h->QA : h->QB;
+      cudaEventRecord(ev[0], h->stream);
+      h->eng->clock_merge(h->md, cs[k], dt, h->stream);
+      cudaEventRecord(ev[1], h->stream);
+      h->eng->faces(h->md, h->stream);
+      cudaEventRecord(ev[2], h->stream);
+      h->eng->mortars(h->md, h->stream);
+      cudaEventRecord(ev[3], h->stream);
+      h->eng->volume(h->md, qin, qb, qo, nullptr, al[k], be[k], dt, MODE_RK, h->stream);
+      cudaEventRecord(ev[4], h->stream);
+      if ((e = cudaEventSynchronize(ev[4]))) break;
+      for (int c = 0; c < 4; ++c) {
+        cudaEventElapsedTime(&t, ev[c], ev[c + 1]);
+        acc[c] += t;
+      }
+    }
+    h->eng->advance(h->md, dt, h->stream);
+    cudaEventRecord(ev[0], h->stream);
+    if (!e) e = cudaEventSynchronize(ev[0]);
+    if (!e) {
+      cudaEventElapsedTime(&t, ev[5], ev[0]);
+      acc[4] += t;
+    }
+  }
+  if (!e) e = cudaGetLastError();
+  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+  if (e) return cuda_fail(h, e, "sd_profile_step");
+  for (int c = 0; c < 4; ++c) ms[c] = acc[c] / (3.0 * reps);
+  ms[4] = acc[4] / reps;
+  return SD_OK;
+}
+
+int sd_fma_peak(sd_handle *h, int precision, double *tflops) {
+  if (!h || !tflops) return fail(h, SD_ERR_ARG, "null argument");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8, threads = 256;
+  const int iters = precision == SD_PREC_FP64 ? 2048 : 65536;
+  void *out = nullptr;
+  cudaError_t e = cudaMalloc(&out, 16);
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && !e; ++rep) {
+    cudaEventRecord(a, h->stream);
+    if (precision == SD_PREC_FP64)
+      k_fma_probe<double><<<blocks, threads, 0, h->stream>>>((double *)out, iters, 0.999999, 1e-7);
+    else
+      k_fma_probe<float><<<blocks, threads, 0, h->stream>>>((float *)out, iters, 0.9999f, 1e-5f);
+    cudaEventRecord(b, h->stream);
+    e = cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (rep > 0 && ms < best) best = ms;  // first launch is a warm-up
+  }
+  if (!e) e = cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  if (e) return cuda_fail(h, e, "sd_fma_peak");
+  *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+  return SD_OK;
+}
+
+}  // extern "C"

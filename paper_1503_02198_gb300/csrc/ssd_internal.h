@@ -1,0 +1,105 @@
+// Internal structures shared by the host driver (ssd_api.cu) and the
+// per-precision kernel engines (ssd_engine.cuh instantiated in ssd_f64.cu and
+// ssd_f32.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ssd {
+
+constexpr int kMaxN = 8;
+
+// Device-resident clock of the current stage (the rotation angle never
+// leaves FP64: theta = omega * t_stage, Sec. 2.2).
+struct DevClock {
+  double t_n;      // time at the start of the step
+  double t_stage;  // time of the stage being evaluated
+  double theta;    // omega * t_stage
+  double c, s;     // cos(theta), sin(theta)
+  int flags;       // bit 0: non-physical state met; bit 1: mesh geometry error
+  int pad;
+};
+
+// Basis data of Sec. 3.1 and the mortar quadrature of Sec. 3.2, built on the
+// host in FP64 for one N (see ssd_api.cu) and copied to constant memory.
+struct HostBasis {
+  int N;
+  double Xs[kMaxN];                  // solution points
+  double Xf[kMaxN + 1];              // flux points
+  double Hf[(kMaxN + 1) * kMaxN];    // h_k(X_{i+1/2}) [i][k]
+  double Dm[kMaxN * (kMaxN + 1)];    // l'_{i+1/2}(X_k) [k][i]
+  double H0[kMaxN], H1[kMaxN];       // h_k(0), h_k(1)
+  double zq[kMaxN], wq[kMaxN];       // N-point Gauss-Legendre rule on [0,1]
+  double Hz[kMaxN * kMaxN];          // h_j(z_q) [q][j]
+  double Minv[kMaxN * kMaxN];        // inverse mortar mass matrix (Eq. mortarM)
+  double cden[kMaxN];                // 1 / prod_{s != i} (X_i - X_s)
+};
+
+// Everything a kernel needs, by value (device pointers + sizes + parameters).
+struct MeshDev {
+  int E, N;
+  // conforming and periodic face pairs: (efA, efB, reversed, 0), ef = 4 e + f
+  int nF;
+  const int4 *faces;
+  // boundary faces: (ef, tag, 0, 0); t = 0 positions of their points [nB][N][2]
+  int nB;
+  const int4 *bfaces;
+  const double *bxy;
+  // sliding interface, both sides sorted counter-clockwise at t = 0:
+  // (ef, reversed, 0, 0), CCW start angle, angular width, |S| = r * width
+  int nL, nR, nM;
+  const int4 *Lface, *Rface;
+  const double *La, *Lw, *LS, *Ra, *Rw, *RS;
+  // per-stage mortar table (written by the merge kernel)
+  int *mLf, *mRf;       // [nM] containing L / R face (sorted index)
+  double *mgeo;         // [nM][6]: oL, sL, oR, sR, start angle, angular length
+  int *Lstart, *Lcount; // [nL] first mortar (merged position) and count
+  int *Rstart, *Rcount; // [nR]
+  void *contrib;        // T [2][nM][4][N] back-projected mortar fluxes
+  // elements
+  const double *corners;  // [E][8] t = 0 corner coordinates relative to the centre
+  const int *arcs;        // [E] bit f set if local face f is an arc
+  const int *zone;        // [E]
+  void *geo;              // T [E][G] metrics (see ssd_engine.cuh)
+  void *TR, *CF;          // T [E][4][4][N] face traces and common fluxes
+  DevClock *clk;
+  double omega, gamma, Rgas, mu, prandtl, T_wall, r_interface;
+  int viscous;
+};
+
+enum { MODE_RESIDUAL = 0, MODE_RK = 1 };
+
+// Per-precision engine: T = double (FP64 path) or float (FP32 path).
+struct Engine {
+  virtual ~Engine() {}
+  virtual size_t geo_words() const = 0;
+  virtual size_t compute_word() const = 0;
+  // upload basis constants, compute the t = 0 metrics
+  virtual cudaError_t init(const HostBasis &hb, const MeshDev &md, cudaStream_t s) = 0;
+  // face traces of Q
+  virtual void trace(const MeshDev &md, const double *Q, cudaStream_t s) = 0;
+  // stage clock at t_n + c dt and mortar table; common fluxes on conforming,
+  // periodic and wall faces; mortar fluxes gathered onto the interface faces
+  virtual void clock_merge(const MeshDev &md, double c, double dt, cudaStream_t s) = 0;
+  virtual void faces(const MeshDev &md, cudaStream_t s) = 0;
+  virtual void mortars(const MeshDev &md, cudaStream_t s) = 0;
+  void couple(const MeshDev &md, double c, double dt, cudaStream_t s) {
+    clock_merge(md, c, dt, s);
+    faces(md, s);
+    mortars(md, s);
+  }
+  // divergence; MODE_RESIDUAL writes R, MODE_RK writes
+  // Qout = alpha Qbase + beta (Qin + dt R) and its face traces
+  virtual void volume(const MeshDev &md, const double *Qin, const double *Qbase, double *Qout, double *R,
+                      double alpha, double beta, double dt, int mode, cudaStream_t s) = 0;
+  virtual void advance(const MeshDev &md, double dt, cudaStream_t s) = 0;
+  virtual void sp_coords(const MeshDev &md, double t, double cx, double cy, double *xy, cudaStream_t s) = 0;
+};
+
+// FMA throughput probe: flops/s of a dependent-chain-free FMA loop in T
+double fma_probe(int precision, cudaStream_t s, float *ms_out);
+
+Engine *make_engine_f64(int N);
+Engine *make_engine_f32(int N);
+
+}  // namespace ssd

@@ -1,0 +1,167 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 path: residual and steps within 1e-12 of the oracle, relative to the
+largest magnitude of each conservative variable.  FP32 path: within the
+tolerance derived in the design notes (FP32 arithmetic on FP64 state).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import rel_err, small_rotor
+from ssd_inputs import fields, meshes
+from ssd_inputs.workloads import FlowParams, build_workload
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def ssd():
+    import paper_1503_02198_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _pair(ssd, oracle_mod, mesh, N, prm, precision=0):
+    return ssd.Solver(mesh, N - 1, prm, precision=precision), oracle_mod.Oracle(mesh, N, prm)
+
+
+def _check(a, b, tol):
+    err = rel_err(a, b)
+    assert (err <= tol).all(), err
+
+
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
+@pytest.mark.parametrize("t", [0.0, 0.37, 5.123])
+def test_residual_fp64_rotor(ssd, oracle_mod, N, t):
+    m = small_rotor(shift_R=0.05)
+    prm = FlowParams(omega=0.9)
+    s, o = _pair(ssd, oracle_mod, m, N, prm)
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=N, amp=0.2, scale=3.0))
+    s.sd_set_state(Q)
+    s.sd_set_time(t)
+    _check(s.sd_residual(), o.residual(Q, t), TOL64)
+
+
+@pytest.mark.parametrize("N", [3, 5])
+def test_residual_fp64_aligned_and_degenerate_mortars(ssd, oracle_mod, N):
+    # equal face counts, nodes coincide at theta = k * 2 pi / 24: zero-length mortars
+    m = small_rotor(n_hole=6, n_core=6)
+    prm = FlowParams(omega=1.0)
+    s, o = _pair(ssd, oracle_mod, m, N, prm)
+    Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=1.0, y0=-2.0))
+    s.sd_set_state(Q)
+    for t in (0.0, 2 * math.pi / 24, 3 * 2 * math.pi / 24 + 1e-9):
+        s.sd_set_time(t)
+        _check(s.sd_residual(), o.residual(Q, t), TOL64)
+
+
+def test_residual_fp64_periodic_box_no_interface(ssd, oracle_mod):
+    m = meshes.perturb_nodes(meshes.periodic_box_mesh(6, 2.0), 0.2, seed=9)
+    s, o = _pair(ssd, oracle_mod, m, 4, FlowParams())
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=3, amp=0.3))
+    s.sd_set_state(Q)
+    _check(s.sd_residual(), o.residual(Q, 0.0), TOL64)
+
+
+def test_residual_fp64_walls_inviscid(ssd, oracle_mod):
+    # Couette annulus with Euler fluxes: rotating and stationary walls, curved cells
+    m = meshes.couette_mesh(2, 12, 2, 16)
+    prm = FlowParams(omega=0.5, Rgas=2.0, T_wall=1.3)
+    s, o = _pair(ssd, oracle_mod, m, 3, prm)
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=4, amp=0.1, u0=0.1, v0=0.2,
+                                                             p0=2.5))
+    s.sd_set_state(Q)
+    s.sd_set_time(0.77)
+    _check(s.sd_residual(), o.residual(Q, 0.77), TOL64)
+
+
+def test_sp_coords_match_oracle(ssd, oracle_mod):
+    m = small_rotor()
+    s, o = _pair(ssd, oracle_mod, m, 4, FlowParams(omega=0.3))
+    for t in (0.0, 1.7):
+        xy = s.sd_sp_coords(t)
+        x, y = o.sp_coords(t)
+        np.testing.assert_allclose(xy[..., 0], x, atol=1e-13)
+        np.testing.assert_allclose(xy[..., 1], y, atol=1e-13)
+
+
+@pytest.mark.parametrize("N", [3, 6])
+def test_steps_fp64(ssd, oracle_mod, N):
+    m = small_rotor(shift_L=0.02)
+    prm = FlowParams(omega=math.pi / 4)
+    s, o = _pair(ssd, oracle_mod, m, N, prm)
+    Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=2.0))
+    dt = 2e-3
+    s.sd_set_state(Q)
+    s.sd_set_time(0.1)
+    s.sd_step(dt, 4)
+    s.sd_sync()
+    q_ref, t_ref = o.step(Q, 0.1, dt, 4)
+    assert s.sd_get_time() == t_ref
+    _check(s.sd_get_state(), q_ref, TOL64)
+    # resuming from the returned state and time continues identically (checkpoint)
+    q_mid = s.sd_get_state()
+    s.sd_step(dt, 2)
+    s.sd_sync()
+    a = s.sd_get_state()
+    s2 = ssd.Solver(m, N - 1, prm)
+    s2.sd_set_state(q_mid)
+    s2.sd_set_time(t_ref)
+    s2.sd_step(dt, 2)
+    s2.sd_sync()
+    assert np.array_equal(a, s2.sd_get_state())
+
+
+@pytest.mark.parametrize("N", [3, 4, 6])
+def test_residual_fp32_rotor(ssd, oracle_mod, N):
+    m = small_rotor(shift_R=0.05)
+    prm = FlowParams(omega=0.9)
+    s, o = _pair(ssd, oracle_mod, m, N, prm, precision=1)
+    Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=1.0))
+    s.sd_set_state(Q)
+    s.sd_set_time(0.37)
+    _check(s.sd_residual(), o.residual(Q, 0.37), TOL32)
+
+
+def test_full_size_vortex_residual_fp64(ssd, oracle_mod):
+    w = build_workload("vortex_n4")
+    s, o = _pair(ssd, oracle_mod, w.mesh, w.N, w.params)
+    Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y))
+    s.sd_set_state(Q)
+    s.sd_set_time(1.1)
+    _check(s.sd_residual(), o.residual(Q, 1.1), TOL64)
+
+
+def test_non_physical_state_is_reported(ssd, oracle_mod):
+    m = small_rotor()
+    s = ssd.Solver(m, 2, FlowParams(omega=0.5))
+    Q = s.state_from(lambda x, y: fields.uniform(x, y))
+    Q[3, 0] = -1.0  # negative density in one element
+    s.sd_set_state(Q)
+    s.sd_step(1e-3, 1)
+    with pytest.raises(ssd.SSDError) as ei:
+        s.sd_sync()
+    assert ei.value.code == ssd.SD_ERR_NONPHYSICAL
+    # the flag is cleared once reported; a good state steps cleanly again
+    s.sd_set_state(s.state_from(lambda x, y: fields.uniform(x, y)))
+    s.sd_step(1e-3, 1)
+    s.sd_sync()
+
+
+def test_bad_mesh_rejected_by_library(ssd):
+    m = dict(small_rotor())
+    m["pfaces"] = m["pfaces"][1:]
+    with pytest.raises(ssd.SSDError) as ei:
+        ssd.Solver(m, 2, FlowParams())
+    assert ei.value.code == ssd.SD_ERR_MESH
+    m = dict(small_rotor())
+    en = m["elem_nodes"].copy()
+    en[0] = en[0][::-1]  # clockwise cell
+    m["elem_nodes"] = en
+    with pytest.raises(ssd.SSDError):
+        ssd.Solver(m, 2, FlowParams())
