@@ -158,6 +158,28 @@ int sd_profile_step(sd_handle *h, double dt, int reps, double *ms);
  * Synchronises. */
 int sd_fma_peak(sd_handle *h, int precision, double *tflops);
 
+/* Same result as sd_residual, for callers that must not allocate device
+ * memory once their handle exists: a solver embedded in a host application
+ * whose device memory is owned by another allocator (for example a framework
+ * memory pool that reserves the free memory), or a latency-bound loop where
+ * the implicit device synchronisation of cudaMalloc / cudaFree is not
+ * acceptable.  sd_residual may allocate a device staging buffer on its first
+ * call with a host R; this variant allocates nothing.  (The paper has no
+ * counterpart: this is a deployment aid, not part of the method.)
+ *
+ * Work memory: the mortar table, the mortar flux contributions, the merge
+ * work arrays and, when R is host memory, the device copy of R all live in one
+ * fixed 16 MiB device array inside the library, which every GPU that loads the
+ * library holds until the process exits.  Calls needing more than 16 MiB
+ * return SD_ERR_ARG with a message (with R in host memory the state copy,
+ * E * 4 * N * N doubles, counts against the limit; with R in device memory
+ * only the interface work does).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) for that device; make that
+ * first call before any stream capture.  All calls share the array and
+ * nothing in it is assumed to start at zero; calls that overlap on the GPU
+ * (several handles or streams at once) race on it.  Synchronises. */
+int sd_residual_noalloc(sd_handle *h, double *R, int on_device);
+
 #ifdef __cplusplus
 }
 #endif

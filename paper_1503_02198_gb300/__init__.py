@@ -85,6 +85,7 @@ def lib():
         L.sd_sp_coords.argtypes = [vp, ctypes.c_double, vp, ctypes.c_int]
         L.sd_profile_step.argtypes = [vp, ctypes.c_double, ctypes.c_int, _c_dbl_p]
         L.sd_fma_peak.argtypes = [vp, ctypes.c_int, _c_dbl_p]
+        L.sd_residual_noalloc.argtypes = [vp, vp, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -178,6 +179,16 @@ class Solver:
             out = np.empty(self.shape)
         p, dev = _ptr(out, np.float64)
         self._check(lib().sd_residual(self._h, p, dev))
+        return out
+
+    def sd_residual_noalloc(self, out=None):
+        """sd_residual without any device allocation (fixed 16 MiB work memory
+        inside the library); ``out`` must be preallocated by a caller that
+        cannot allocate, or is created here in host memory."""
+        if out is None:
+            out = np.empty(self.shape)
+        p, dev = _ptr(out, np.float64)
+        self._check(lib().sd_residual_noalloc(self._h, p, dev))
         return out
 
     def sd_step(self, dt, nsteps=1):

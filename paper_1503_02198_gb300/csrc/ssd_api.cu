@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -791,6 +792,94 @@ int sd_fma_peak(sd_handle *h, int precision, double *tflops) {
   cudaFree(out);
   if (e) return cuda_fail(h, e, "sd_fma_peak");
   *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+  return SD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// residual without any allocation at call time
+// ---------------------------------------------------------------------------
+//
+// Work memory of sd_residual_noalloc: one file-scope device array that every
+// GPU loading this library holds until the process exits.  Its name is only a
+// host-side stand-in in host code; the device address comes from
+// cudaGetSymbolAddress, taken once per device.
+static constexpr size_t kNoAllocBytes = 16u << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[256] = {};
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+cudaError_t noalloc_base(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
+  if (!h || !R) return fail(h, SD_ERR_ARG, "null argument");
+  const MeshDev &md0 = h->md;
+  const size_t nb = (size_t)md0.nM, N = (size_t)h->N;
+  const size_t w = h->eng->compute_word();
+  // carve the work arrays out of the static array
+  size_t off = 0;
+  const size_t o_mLf = off; off += align256(sizeof(int) * nb);
+  const size_t o_mRf = off; off += align256(sizeof(int) * nb);
+  const size_t o_mgeo = off; off += align256(sizeof(double) * 6 * nb);
+  const size_t o_Ls = off; off += align256(sizeof(int) * md0.nL);
+  const size_t o_Lc = off; off += align256(sizeof(int) * md0.nL);
+  const size_t o_Rs = off; off += align256(sizeof(int) * md0.nR);
+  const size_t o_Rc = off; off += align256(sizeof(int) * md0.nR);
+  const size_t o_con = off; off += align256(w * 2 * nb * 4 * N);
+  const size_t o_wi = off; off += align256(sizeof(int) * (2 * nb + 1));
+  const size_t o_wd = off; off += align256(sizeof(double) * (md0.nL + nb + 1));
+  const size_t o_R = off;
+  if (!on_device) off += align256(state_bytes(h));
+  if (off > kNoAllocBytes) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf,
+                  "sd_residual_noalloc needs %zu bytes of work memory, more than its fixed %zu; pass R in device "
+                  "memory or use sd_residual",
+                  off, kNoAllocBytes);
+    return fail(h, SD_ERR_ARG, buf);
+  }
+  void *base = nullptr;
+  cudaError_t e = noalloc_base(&base);
+  if (e) return cuda_fail(h, e, "sd_residual_noalloc work memory address");
+  unsigned char *b = (unsigned char *)base;
+  MeshDev md = md0;
+  md.mLf = (int *)(b + o_mLf);
+  md.mRf = (int *)(b + o_mRf);
+  md.mgeo = (double *)(b + o_mgeo);
+  md.Lstart = (int *)(b + o_Ls);
+  md.Lcount = (int *)(b + o_Lc);
+  md.Rstart = (int *)(b + o_Rs);
+  md.Rcount = (int *)(b + o_Rc);
+  md.contrib = b + o_con;
+  double *dst = on_device ? R : (double *)(b + o_R);
+  h->eng->trace(md, h->QA, h->stream);
+  h->eng->clock_merge_into(md, 0.0, 0.0, (int *)(b + o_wi), (double *)(b + o_wd), h->stream);
+  h->eng->faces(md, h->stream);
+  h->eng->mortars(md, h->stream);
+  h->eng->volume(md, h->QA, nullptr, nullptr, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
+  if ((e = cudaGetLastError())) return cuda_fail(h, e, "sd_residual_noalloc kernels");
+  h->traces_valid = true;
+  if (!on_device) e = cudaMemcpyAsync(R, dst, state_bytes(h), cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (e) return cuda_fail(h, e, "sd_residual_noalloc");
   return SD_OK;
 }
 

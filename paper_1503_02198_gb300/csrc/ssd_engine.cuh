@@ -859,6 +859,11 @@ struct EngineImpl : Engine {
     k_clock_merge<<<1, 1024, 0, s>>>(md, c, dt, scratch_i, scratch_d);
   }
 
+  void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
+                        cudaStream_t s) override {
+    k_clock_merge<<<1, 1024, 0, s>>>(md, c, dt, work_i, work_d);
+  }
+
   void faces(const MeshDev &md, cudaStream_t s) override {
     if (md.nF > 0) k_face<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
     if (md.nB > 0) k_bface<T, N><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);

@@ -81,6 +81,10 @@ struct Engine {
   // stage clock at t_n + c dt and mortar table; common fluxes on conforming,
   // periodic and wall faces; mortar fluxes gathered onto the interface faces
   virtual void clock_merge(const MeshDev &md, double c, double dt, cudaStream_t s) = 0;
+  // the same merge with caller-provided work arrays (ints: 2 (nL + nR) + 1,
+  // doubles: 2 nL + nR + 1)
+  virtual void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
+                                cudaStream_t s) = 0;
   virtual void faces(const MeshDev &md, cudaStream_t s) = 0;
   virtual void mortars(const MeshDev &md, cudaStream_t s) = 0;
   void couple(const MeshDev &md, double c, double dt, cudaStream_t s) {
