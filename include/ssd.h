@@ -35,7 +35,7 @@ enum {
   SD_ERR_MESH = -2,        /* inconsistent mesh (unmatched face, folded cell ...) */
   SD_ERR_CUDA = -3,        /* a CUDA runtime call failed */
   SD_ERR_NONPHYSICAL = -4, /* a kernel met rho <= 0, p <= 0 or a non-finite value */
-  SD_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up */
+  SD_ERR_TIMEOUT = -5,     /* a bounded device wait gave up (reported by sd_sync) */
   SD_ERR_UNSUPPORTED = -6  /* valid request this build does not support (e.g. p) */
 };
 

@@ -44,6 +44,7 @@ def lib():
                                 ctypes.c_double, ctypes.c_int, _dp, ctypes.c_char_p, ctypes.c_int]
         L.or_destroy.argtypes = [ctypes.c_void_p]
         L.or_residual.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
+        L.or_residual_ex.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, _dp]
         L.or_step.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_int]
         L.or_sp_coords.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp]
         L.or_sp_jacobian.argtypes = [ctypes.c_void_p, _dp]
@@ -155,6 +156,13 @@ class Oracle:
         R = np.zeros(self.shape)
         lib().or_residual(self._h, _d(Q), t, _d(R))
         return R
+
+    def residual_with_scale(self, Q, t: float = 0.0):
+        """Residual and, per point, the summed magnitude of its divergence terms."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(self.shape)
+        R, S = np.zeros(self.shape), np.zeros(self.shape)
+        lib().or_residual_ex(self._h, _d(Q), t, _d(R), _d(S))
+        return R, S
 
     def step(self, Q, t: float, dt: float, nsteps: int = 1):
         Q = np.array(Q, dtype=np.float64, order="C").reshape(self.shape)

@@ -152,12 +152,16 @@ static double lag_d(const double *nodes, int n, int i, double x) {
 static const int FACE_A[4] = {0, 1, 3, 0}; /* start corner of face f's parameter */
 static const int FACE_B[4] = {1, 2, 2, 3}; /* end corner */
 
-/* point and derivative of an edge curve from P to Q at parameter u */
+/* Edge curve from P to Q at parameter u: offset of the point from P, and the
+ * derivative.  An arc is written with the chord form
+ * e(phi0 + d) - e(phi0) = 2 sin(d/2) (-sin(phi0 + d/2), cos(phi0 + d/2)),
+ * so the offset keeps full relative precision for short arcs far from the
+ * centre. */
 static void edge_curve(const or_mesh *m, double px, double py, double qx, double qy, int arc, double u,
-                       double *x, double *y, double *dx, double *dy) {
+                       double *ox, double *oy, double *dx, double *dy) {
   if (!arc) {
-    *x = px + u * (qx - px);
-    *y = py + u * (qy - py);
+    *ox = u * (qx - px);
+    *oy = u * (qy - py);
     *dx = qx - px;
     *dy = qy - py;
     return;
@@ -166,16 +170,19 @@ static void edge_curve(const or_mesh *m, double px, double py, double qx, double
   double r = sqrt(ax * ax + ay * ay);
   double phi0 = atan2(ay, ax);
   double dphi = atan2(ax * by - ay * bx, ax * bx + ay * by);
+  double half = 0.5 * u * dphi, chord = 2.0 * r * sin(half);
+  *ox = -chord * sin(phi0 + half);
+  *oy = chord * cos(phi0 + half);
   double phi = phi0 + u * dphi;
-  *x = m->cx + r * cos(phi);
-  *y = m->cy + r * sin(phi);
   *dx = -r * dphi * sin(phi);
   *dy = r * dphi * cos(phi);
 }
 
 /* Transfinite (Coons) map of element e at (xi, eta) at t = 0: position and the
  * four derivatives.  With straight edges it is the 4-node bilinear map; an arc
- * edge is reproduced exactly. */
+ * edge is reproduced exactly.  It is evaluated about the cell's first corner
+ * (an exact shift in real arithmetic) so that the round-off of the metrics
+ * scales with the cell size rather than with the coordinates. */
 static void map_t0(const or_mesh *m, int e, double xi, double eta, double *g) {
   const int *n = m->en + 4 * e;
   double X[4], Y[4];
@@ -183,25 +190,29 @@ static void map_t0(const or_mesh *m, int e, double xi, double eta, double *g) {
     X[k] = m->xy[2 * n[k]];
     Y[k] = m->xy[2 * n[k] + 1];
   }
+  double U[4], V[4]; /* corners relative to corner 0 */
+  for (int k = 0; k < 4; ++k) {
+    U[k] = X[k] - X[0];
+    V[k] = Y[k] - Y[0];
+  }
   const int *a = m->arc + 4 * e;
   double Bx, By, dBx, dBy, Tx, Ty, dTx, dTy, Lx, Ly, dLx, dLy, Rx, Ry, dRx, dRy;
   edge_curve(m, X[0], Y[0], X[1], Y[1], a[0], xi, &Bx, &By, &dBx, &dBy);   /* f0, eta = 0 */
   edge_curve(m, X[1], Y[1], X[2], Y[2], a[1], eta, &Rx, &Ry, &dRx, &dRy);  /* f1, xi = 1 */
   edge_curve(m, X[3], Y[3], X[2], Y[2], a[2], xi, &Tx, &Ty, &dTx, &dTy);   /* f2, eta = 1 */
   edge_curve(m, X[0], Y[0], X[3], Y[3], a[3], eta, &Lx, &Ly, &dLx, &dLy);  /* f3, xi = 0 */
+  /* edge points relative to corner 0 */
+  Rx += U[1]; Ry += V[1];
+  Tx += U[3]; Ty += V[3];
   double x = (1 - eta) * Bx + eta * Tx + (1 - xi) * Lx + xi * Rx -
-             ((1 - xi) * (1 - eta) * X[0] + xi * (1 - eta) * X[1] + xi * eta * X[2] + (1 - xi) * eta * X[3]);
+             (xi * (1 - eta) * U[1] + xi * eta * U[2] + (1 - xi) * eta * U[3]);
   double y = (1 - eta) * By + eta * Ty + (1 - xi) * Ly + xi * Ry -
-             ((1 - xi) * (1 - eta) * Y[0] + xi * (1 - eta) * Y[1] + xi * eta * Y[2] + (1 - xi) * eta * Y[3]);
-  double x_xi = (1 - eta) * dBx + eta * dTx - Lx + Rx -
-                (-(1 - eta) * X[0] + (1 - eta) * X[1] + eta * X[2] - eta * X[3]);
-  double y_xi = (1 - eta) * dBy + eta * dTy - Ly + Ry -
-                (-(1 - eta) * Y[0] + (1 - eta) * Y[1] + eta * Y[2] - eta * Y[3]);
-  double x_eta = -Bx + Tx + (1 - xi) * dLx + xi * dRx -
-                 (-(1 - xi) * X[0] - xi * X[1] + xi * X[2] + (1 - xi) * X[3]);
-  double y_eta = -By + Ty + (1 - xi) * dLy + xi * dRy -
-                 (-(1 - xi) * Y[0] - xi * Y[1] + xi * Y[2] + (1 - xi) * Y[3]);
-  g[0] = x; g[1] = y; g[2] = x_xi; g[3] = y_xi; g[4] = x_eta; g[5] = y_eta;
+             (xi * (1 - eta) * V[1] + xi * eta * V[2] + (1 - xi) * eta * V[3]);
+  double x_xi = (1 - eta) * dBx + eta * dTx - Lx + Rx - ((1 - eta) * U[1] + eta * U[2] - eta * U[3]);
+  double y_xi = (1 - eta) * dBy + eta * dTy - Ly + Ry - ((1 - eta) * V[1] + eta * V[2] - eta * V[3]);
+  double x_eta = -Bx + Tx + (1 - xi) * dLx + xi * dRx - (-xi * U[1] + xi * U[2] + (1 - xi) * U[3]);
+  double y_eta = -By + Ty + (1 - xi) * dLy + xi * dRy - (-xi * V[1] + xi * V[2] + (1 - xi) * V[3]);
+  g[0] = X[0] + x; g[1] = Y[0] + y; g[2] = x_xi; g[3] = y_xi; g[4] = x_eta; g[5] = y_eta;
 }
 
 /* Map at time t: cells of the rotating zone are rotated rigidly about the
@@ -809,7 +820,14 @@ typedef struct {
   double *gxi, *geta;   /* physical gradient at FPs: [E][8][..] as two 4-var blocks */
 } or_work;
 
-int or_residual(or_mesh *m, const double *Q, double t, double *dQdt) {
+/* Residual; when scale is not NULL it also receives, per SP and variable,
+ * (sum_i |l'_i(X_k)| |F~_i| + sum_i |l'_i(X_j)| |G~_i|) / |J|: the magnitude of
+ * the terms the divergence adds up, which bounds its round-off. */
+int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *scale);
+
+int or_residual(or_mesh *m, const double *Q, double t, double *dQdt) { return or_residual_ex(m, Q, t, dQdt, NULL); }
+
+int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *scale) {
   int N = m->N, ne = m->ne;
   const or_params *P = &m->prm;
   size_t nxf = (size_t)ne * 4 * N * (N + 1);
@@ -1130,6 +1148,12 @@ int or_residual(or_mesh *m, const double *Q, double t, double *dQdt) {
             dG += Geta[IEF(e, v, i, k)] * dl[j * (N + 1) + i];
           }
           dQdt[IQ(e, v, j, k)] = -(dF + dG) / J;
+          if (scale) {
+            double a = 0.0;
+            for (int i = 0; i <= N; ++i)
+              a += fabs(Fxi[IXF(e, v, j, i)] * dl[k * (N + 1) + i]) + fabs(Geta[IEF(e, v, i, k)] * dl[j * (N + 1) + i]);
+            scale[IQ(e, v, j, k)] = a / fabs(J);
+          }
         }
       }
 

@@ -183,7 +183,9 @@ struct sd_handle {
   Engine *eng = nullptr;
   MeshDev md{};
   std::vector<void *> allocs;
-  double *QA = nullptr, *QB = nullptr, *scratch = nullptr;
+  std::vector<int> zone_v, curved_v;  // per element: zone, has an arc edge
+  double *stage = nullptr;    // FP64 staging of host states (FP32 path)
+  double *scratch = nullptr;  // device copy of a host residual
   bool traces_valid = false;
   cudaGraphExec_t step_exec = nullptr;
   double graph_dt = 0.0;
@@ -381,6 +383,8 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
         if (std::fabs(ra - rb) > 1e-9 * std::max(1.0, ra)) return fail(h, SD_ERR_MESH, "arc edge corners at different radii");
       }
     arcs[e] = bits;
+    h->zone_v.push_back(m->elem_zone[e]);
+    h->curved_v.push_back(bits != 0);
   }
   cudaError_t ce;
   int4 *dfaces, *dbfaces, *dL, *dR;
@@ -412,18 +416,41 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   return SD_OK;
 }
 
-cudaError_t alloc_buffers(sd_handle *h) {
+cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std::vector<int> &curved) {
   MeshDev &md = h->md;
   const size_t E = md.E, N = h->N, nb = md.nM;
   const size_t w = h->eng->compute_word();
   cudaError_t e;
   double *bxy;
   DevClock *clk;
-  if ((e = dalloc(h, &h->QA, sizeof(double) * E * 4 * N * N))) return e;
-  if ((e = dalloc(h, &h->QB, sizeof(double) * E * 4 * N * N))) return e;
-  if ((e = dalloc(h, &md.geo, w * E * h->eng->geo_words()))) return e;
-  if ((e = dalloc(h, &md.TR, w * E * 16 * N))) return e;
-  if ((e = dalloc(h, &md.CF, w * E * 16 * N))) return e;
+  // every per-element array holds a whole number of volume-kernel tiles
+  const int tile = h->eng->tile_elems();
+  const size_t Ep = (E + tile - 1) / tile * tile;
+  // metric tables: every cell on the FP64 path, arc cells only on the on-the-fly path
+  std::vector<int> eflag(Ep, 0), tab_elem;
+  const bool otf = h->eng->metrics_on_the_fly();
+  for (size_t k = 0; k < E; ++k) {
+    int f = zone[k] == 1 ? 1 : 0;
+    if (!otf || curved[k]) {
+      tab_elem.push_back((int)k);
+      f |= (int)tab_elem.size() << 1;
+    }
+    eflag[k] = f;
+  }
+  int *deflag, *dtab;
+  if ((e = upload(h, &deflag, eflag.data(), eflag.size()))) return e;
+  if ((e = upload(h, &dtab, tab_elem.data(), tab_elem.size()))) return e;
+  md.eflag = deflag;
+  md.tab_elem = dtab;
+  md.nTab = (int)tab_elem.size();
+  if ((e = h->eng->alloc_state((int)E, (int)Ep))) return e;
+  if (otf && (e = dalloc(h, &h->stage, sizeof(double) * E * 4 * N * N))) return e;
+  if ((e = dalloc(h, &md.geo, w * (tab_elem.size() ? tab_elem.size() : 1) * h->eng->geo_words()))) return e;
+  md.egeo = nullptr;
+  if (otf && (e = dalloc(h, &md.egeo, w * Ep * 8))) return e;
+  if (otf && (e = cudaMemsetAsync(md.egeo, 0, w * Ep * 8, h->stream))) return e;
+  if ((e = dalloc(h, &md.TR, w * Ep * 16 * N))) return e;
+  if ((e = dalloc(h, &md.CF, w * Ep * 16 * N))) return e;
   if ((e = dalloc(h, &md.contrib, w * 2 * nb * 4 * N))) return e;
   if ((e = dalloc(h, &md.mLf, sizeof(int) * nb))) return e;
   if ((e = dalloc(h, &md.mRf, sizeof(int) * nb))) return e;
@@ -436,10 +463,16 @@ cudaError_t alloc_buffers(sd_handle *h) {
   if ((e = dalloc(h, &clk, sizeof(DevClock)))) return e;
   md.bxy = bxy;
   md.clk = clk;
-  if ((e = cudaMemsetAsync(h->QA, 0, sizeof(double) * E * 4 * N * N, h->stream))) return e;
   if ((e = cudaMemsetAsync(clk, 0, sizeof(DevClock), h->stream))) return e;
-  if ((e = cudaMemsetAsync(md.CF, 0, w * E * 16 * N, h->stream))) return e;
-  return cudaSuccess;
+  if ((e = cudaMemsetAsync(md.CF, 0, w * Ep * 16 * N, h->stream))) return e;
+  // zero state
+  const StatePtr A = h->eng->A(), Bs = h->eng->B();
+  for (const StatePtr &q : {A, Bs}) {
+    if ((e = cudaMemsetAsync(q.hi, 0, w * Ep * 4 * N * N, h->stream))) return e;
+    if (q.lo && (e = cudaMemsetAsync(q.lo, 0, sizeof(float) * Ep * 4 * N * N, h->stream))) return e;
+  }
+  // the host vectors above go out of scope: wait for their copies
+  return cudaStreamSynchronize(h->stream);
 }
 
 int read_flags(sd_handle *h, int *flags, bool clear) {
@@ -471,12 +504,13 @@ void queue_step(sd_handle *h, double dt) {
   MeshDev &md = h->md;
   Engine *g = h->eng;
   cudaStream_t s = h->stream;
+  const StatePtr A = g->A(), B = g->B(), none{nullptr, nullptr};
   g->couple(md, 0.0, dt, s);
-  g->volume(md, h->QA, nullptr, h->QB, nullptr, 0.0, 1.0, dt, MODE_RK, s);
+  g->volume(md, A, none, B, nullptr, 0.0, 1.0, dt, MODE_RK, s);
   g->couple(md, 1.0, dt, s);
-  g->volume(md, h->QB, h->QA, h->QB, nullptr, 0.75, 0.25, dt, MODE_RK, s);
+  g->volume(md, B, A, B, nullptr, 0.75, 0.25, dt, MODE_RK, s);
   g->couple(md, 0.5, dt, s);
-  g->volume(md, h->QB, h->QA, h->QA, nullptr, 1.0 / 3.0, 2.0 / 3.0, dt, MODE_RK, s);
+  g->volume(md, B, A, A, nullptr, 1.0 / 3.0, 2.0 / 3.0, dt, MODE_RK, s);
   g->advance(md, dt, s);
 }
 
@@ -553,7 +587,7 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
     md.T_wall = prm->T_wall;
     md.viscous = prm->viscous;
     md.r_interface = m->r_interface;
-    if ((ce = alloc_buffers(h))) rc = cuda_fail(h, ce, "device buffers");
+    if ((ce = alloc_buffers(h, h->zone_v, h->curved_v))) rc = cuda_fail(h, ce, "device buffers");
   }
   if (!rc && (ce = h->eng->init(hb, h->md, h->stream))) rc = cuda_fail(h, ce, "engine init");
   if (!rc && (ce = cudaGetLastError())) rc = cuda_fail(h, ce, "geometry kernels");
@@ -590,8 +624,19 @@ static size_t state_bytes(const sd_handle *h) { return sizeof(double) * (size_t)
 
 int sd_set_state(sd_handle *h, const double *Q, int on_device) {
   if (!h || !Q) return fail(h, SD_ERR_ARG, "null argument");
-  cudaError_t e = cudaMemcpyAsync(h->QA, Q, state_bytes(h), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                  h->stream);
+  cudaError_t e = cudaSuccess;
+  if (!h->eng->metrics_on_the_fly()) {
+    e = cudaMemcpyAsync(h->eng->A().hi, Q, state_bytes(h),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+  } else {
+    const double *src = Q;
+    if (!on_device) {
+      e = cudaMemcpyAsync(h->stage, Q, state_bytes(h), cudaMemcpyHostToDevice, h->stream);
+      src = h->stage;
+    }
+    if (!e) h->eng->set_state(h->md, src, h->stream);
+    if (!e) e = cudaGetLastError();
+  }
   if (!e && !on_device) e = cudaStreamSynchronize(h->stream);  // caller may reuse Q at once
   if (e) return cuda_fail(h, e, "sd_set_state");
   h->traces_valid = false;
@@ -600,8 +645,16 @@ int sd_set_state(sd_handle *h, const double *Q, int on_device) {
 
 int sd_get_state(sd_handle *h, double *Q, int on_device) {
   if (!h || !Q) return fail(h, SD_ERR_ARG, "null argument");
-  cudaError_t e = cudaMemcpyAsync(Q, h->QA, state_bytes(h), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                  h->stream);
+  cudaError_t e = cudaSuccess;
+  if (!h->eng->metrics_on_the_fly()) {
+    e = cudaMemcpyAsync(Q, h->eng->A().hi, state_bytes(h),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  } else {
+    double *dst = on_device ? Q : h->stage;
+    h->eng->get_state(h->md, dst, h->stream);
+    e = cudaGetLastError();
+    if (!e && !on_device) e = cudaMemcpyAsync(Q, dst, state_bytes(h), cudaMemcpyDeviceToHost, h->stream);
+  }
   if (!e) e = cudaStreamSynchronize(h->stream);
   if (e) return cuda_fail(h, e, "sd_get_state");
   return SD_OK;
@@ -637,9 +690,10 @@ int sd_residual(sd_handle *h, double *R, int on_device) {
     if (e) return cuda_fail(h, e, "residual scratch");
     dst = h->scratch;
   }
-  h->eng->trace(h->md, h->QA, h->stream);
+  const StatePtr none{nullptr, nullptr};
+  h->eng->trace(h->md, h->eng->A(), h->stream);
   h->eng->couple(h->md, 0.0, 0.0, h->stream);
-  h->eng->volume(h->md, h->QA, nullptr, nullptr, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
+  h->eng->volume(h->md, h->eng->A(), none, none, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
   if ((e = cudaGetLastError())) return cuda_fail(h, e, "residual kernels");
   h->traces_valid = true;
   if (!on_device) {
@@ -656,7 +710,7 @@ int sd_step(sd_handle *h, double dt, int nsteps) {
   if (nsteps == 0) return SD_OK;
   cudaError_t e;
   if (!h->traces_valid) {
-    h->eng->trace(h->md, h->QA, h->stream);
+    h->eng->trace(h->md, h->eng->A(), h->stream);
     if ((e = cudaGetLastError())) return cuda_fail(h, e, "trace kernel");
     h->traces_valid = true;
   }
@@ -689,6 +743,7 @@ int sd_sync(sd_handle *h) {
   int flags = 0;
   int rc = read_flags(h, &flags, true);
   if (rc) return rc;
+  if (flags & 4) return fail(h, SD_ERR_TIMEOUT, "a bounded device wait gave up (tile copy did not arrive)");
   if (flags & 1) return fail(h, SD_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite)");
   return SD_OK;
 }
@@ -718,7 +773,7 @@ int sd_profile_step(sd_handle *h, double dt, int reps, double *ms) {
   for (int k = 0; k < 6; ++k)
     if ((e = cudaEventCreate(&ev[k]))) return cuda_fail(h, e, "event");
   if (!h->traces_valid) {
-    h->eng->trace(h->md, h->QA, h->stream);
+    h->eng->trace(h->md, h->eng->A(), h->stream);
     h->traces_valid = true;
   }
   double acc[5] = {0, 0, 0, 0, 0};
@@ -727,9 +782,10 @@ int sd_profile_step(sd_handle *h, double dt, int reps, double *ms) {
     float t;
     cudaEventRecord(ev[5], h->stream);
     for (int k = 0; k < 3; ++k) {
-      const double *qin = k == 0 ? h->QA : h->QB;
-      const double *qb = k == 0 ? nullptr : h->QA;
-      double *qo = k == 2 ? h->QA : h->QB;
+      const StatePtr A = h->eng->A(), B = h->eng->B(), none{nullptr, nullptr};
+      const StatePtr qin = k == 0 ? A : B;
+      const StatePtr qb = k == 0 ? none : A;
+      const StatePtr qo = k == 2 ? A : B;
       cudaEventRecord(ev[0], h->stream);
       h->eng->clock_merge(h->md, cs[k], dt, h->stream);
       cudaEventRecord(ev[1], h->stream);
@@ -870,11 +926,12 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   md.Rcount = (int *)(b + o_Rc);
   md.contrib = b + o_con;
   double *dst = on_device ? R : (double *)(b + o_R);
-  h->eng->trace(md, h->QA, h->stream);
+  const StatePtr none{nullptr, nullptr};
+  h->eng->trace(md, h->eng->A(), h->stream);
   h->eng->clock_merge_into(md, 0.0, 0.0, (int *)(b + o_wi), (double *)(b + o_wd), h->stream);
   h->eng->faces(md, h->stream);
   h->eng->mortars(md, h->stream);
-  h->eng->volume(md, h->QA, nullptr, nullptr, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
+  h->eng->volume(md, h->eng->A(), none, none, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
   if ((e = cudaGetLastError())) return cuda_fail(h, e, "sd_residual_noalloc kernels");
   h->traces_valid = true;
   if (!on_device) e = cudaMemcpyAsync(R, dst, state_bytes(h), cudaMemcpyDeviceToHost, h->stream);

@@ -1,9 +1,14 @@
 // ssd_engine.cuh -- sm_103a kernels of the sliding-mesh spectral difference
 // residual and its SSP Runge-Kutta stage update, templated on the compute
 // type T (double: FP64 path; float: FP32 path) and on N (solution points per
-// direction, Sec. 3.1).  The state and the Runge-Kutta accumulation are FP64
-// in both paths; so are the rotation angle, the mortar geometry and the
-// mortar projection weights (Sec. 3.2).
+// direction, Sec. 3.1).
+//
+// FP64 path: every value and every operation in double.  FP32 path: the
+// interpolation, flux and divergence arithmetic in float; the state is kept
+// as a double-float pair (hi + lo) and the Runge-Kutta accumulation uses exact
+// two-sum arithmetic on the FP32 pipe (GB300's FP64 pipe runs at 1/64 of the
+// FP32 rate); the rotation angle, the mortar geometry and the mortar
+// projection weights stay FP64 in both paths (Sec. 3.2).
 //
 // Per stage (stage time t_k):
 //   k_clock_merge   1 CTA: theta = omega t_k; merge of the rotated L node
@@ -26,6 +31,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "ssd_internal.h"
 
 namespace ssd {
@@ -39,6 +47,7 @@ struct VolBasis {
   T Hf[(N + 1) * N];  // h_k(X_{i+1/2}) [i][k]
   T Dm[N * (N + 1)];  // l'_{i+1/2}(X_k) [k][i]
   T H0[N], H1[N];     // h_k(0), h_k(1)
+  T Xs[N], Xf[N + 1]; // solution and flux points
 };
 
 template <int N>
@@ -55,14 +64,14 @@ __constant__ VolBasis<T, N> cVB;
 template <int N>
 __constant__ MortBasis<N> cMB;
 
-// metric table of one element, t = 0 (words of type T)
+// metric table of one element at t = 0 (words of type T)
 template <int N>
 struct GeoLayout {
   static constexpr int NF = N * (N + 1);
-  static constexpr int ax = 0, ay = NF, gx = 2 * NF;      // xi-FPs [j][i]: (y_eta, -x_eta), V_g . a
-  static constexpr int bx = 3 * NF, by = 4 * NF, gy = 5 * NF;  // eta-FPs [i'][i]: (-y_xi, x_xi), V_g . b
-  static constexpr int iJ = 6 * NF;                       // 1/|J| at SPs [j][i]
-  static constexpr int grad = 6 * NF + N * N;             // xi_x, xi_y, eta_x, eta_y at SPs [4][N*N]
+  static constexpr int ax = 0, ay = NF, gx = 2 * NF;           // xi-FPs [j][i]: (y_eta, -x_eta), V_g . a
+  static constexpr int bx = 3 * NF, by = 4 * NF, gy = 5 * NF;  // eta-FPs [l][i]: (-y_xi, x_xi), V_g . b
+  static constexpr int iJ = 6 * NF;                            // 1/|J| at SPs [j][i]
+  static constexpr int grad = 6 * NF + N * N;                  // xi_x, xi_y, eta_x, eta_y at SPs [4][N*N]
   static constexpr int G = 6 * NF + 5 * N * N;
 };
 
@@ -73,13 +82,16 @@ __device__ __forceinline__ double face_sigma(int f) { return (f == 1 || f == 2) 
 // geometry (Sec. 3.1 iso-parametric cells; Sec. 2.3 metrics)
 // ---------------------------------------------------------------------------
 
-// point and parameter derivative of the edge from P to Q at u in [0,1]; an arc
-// edge is the circle about the origin (coordinates are centre-relative)
-__device__ inline void edge_point(double px, double py, double qx, double qy, bool arc, double u, double &x,
-                                  double &y, double &dx, double &dy) {
+// Edge from P to Q at u in [0,1]: offset of the point from P and the
+// parameter derivative.  An arc edge is the circle about the origin
+// (coordinates are centre-relative); its offset uses the chord identity
+// e(phi0 + d) - e(phi0) = 2 sin(d/2) e_perp(phi0 + d/2), which keeps full
+// relative precision for short arcs far from the centre.
+__device__ inline void edge_offset(double px, double py, double qx, double qy, bool arc, double u, double &ox,
+                                   double &oy, double &dx, double &dy) {
   if (!arc) {
-    x = fma(u, qx - px, px);
-    y = fma(u, qy - py, py);
+    ox = u * (qx - px);
+    oy = u * (qy - py);
     dx = qx - px;
     dy = qy - py;
     return;
@@ -87,50 +99,63 @@ __device__ inline void edge_point(double px, double py, double qx, double qy, bo
   const double r = sqrt(px * px + py * py);
   const double phi0 = atan2(py, px);
   const double dphi = atan2(px * qy - py * qx, px * qx + py * qy);
-  double sn, cs;
-  sincos(fma(u, dphi, phi0), &sn, &cs);
-  x = r * cs;
-  y = r * sn;
+  const double half = 0.5 * u * dphi;
+  double sh, ch, sm, cm, sn, cs;
+  sincos(half, &sh, &ch);
+  sincos(phi0 + half, &sm, &cm);
+  const double chord = 2.0 * r * sh;
+  ox = -chord * sm;
+  oy = chord * cm;
+  sincos(phi0 + u * dphi, &sn, &cs);
   dx = -r * dphi * sn;
   dy = r * dphi * cs;
 }
 
-// transfinite map of a cell with corners c[8] (x0 y0 .. x3 y3) and arc bits
-// at (xi, eta): out = x, y, x_xi, y_xi, x_eta, y_eta
+// Transfinite map of a cell with corners c[8] (x0 y0 .. x3 y3, centre
+// relative) and arc bits at (xi, eta): out = x, y, x_xi, y_xi, x_eta, y_eta.
+// Evaluated about corner 0 (an exact shift in real arithmetic), so the
+// round-off of the metrics scales with the cell, not with the coordinates.
 __device__ inline void cell_map(const double *c, int arcs, double xi, double eta, double *out) {
+  const double u1 = c[2] - c[0], v1 = c[3] - c[1];
+  const double u2 = c[4] - c[0], v2 = c[5] - c[1];
+  const double u3 = c[6] - c[0], v3 = c[7] - c[1];
   double bx, by, dbx, dby, tx, ty, dtx, dty, lx, ly, dlx, dly, rx, ry, drx, dry;
-  edge_point(c[0], c[1], c[2], c[3], arcs & 1, xi, bx, by, dbx, dby);    // f0: n0 -> n1
-  edge_point(c[2], c[3], c[4], c[5], arcs & 2, eta, rx, ry, drx, dry);   // f1: n1 -> n2
-  edge_point(c[6], c[7], c[4], c[5], arcs & 4, xi, tx, ty, dtx, dty);    // f2: n3 -> n2
-  edge_point(c[0], c[1], c[6], c[7], arcs & 8, eta, lx, ly, dlx, dly);   // f3: n0 -> n3
+  edge_offset(c[0], c[1], c[2], c[3], arcs & 1, xi, bx, by, dbx, dby);    // f0: n0 -> n1
+  edge_offset(c[2], c[3], c[4], c[5], arcs & 2, eta, rx, ry, drx, dry);   // f1: n1 -> n2
+  edge_offset(c[6], c[7], c[4], c[5], arcs & 4, xi, tx, ty, dtx, dty);    // f2: n3 -> n2
+  edge_offset(c[0], c[1], c[6], c[7], arcs & 8, eta, lx, ly, dlx, dly);   // f3: n0 -> n3
+  rx += u1;
+  ry += v1;
+  tx += u3;
+  ty += v3;
   const double a = 1.0 - xi, b = 1.0 - eta;
-  // bilinear corner blend and its derivatives
-  const double cxv = a * b * c[0] + xi * b * c[2] + xi * eta * c[4] + a * eta * c[6];
-  const double cyv = a * b * c[1] + xi * b * c[3] + xi * eta * c[5] + a * eta * c[7];
-  const double cx_xi = -b * c[0] + b * c[2] + eta * c[4] - eta * c[6];
-  const double cy_xi = -b * c[1] + b * c[3] + eta * c[5] - eta * c[7];
-  const double cx_eta = -a * c[0] - xi * c[2] + xi * c[4] + a * c[6];
-  const double cy_eta = -a * c[1] - xi * c[3] + xi * c[5] + a * c[7];
-  out[0] = b * bx + eta * tx + a * lx + xi * rx - cxv;
-  out[1] = b * by + eta * ty + a * ly + xi * ry - cyv;
+  // bilinear corner blend (corner 0 at the origin) and its derivatives
+  const double cxv = xi * b * u1 + xi * eta * u2 + a * eta * u3;
+  const double cyv = xi * b * v1 + xi * eta * v2 + a * eta * v3;
+  const double cx_xi = b * u1 + eta * u2 - eta * u3;
+  const double cy_xi = b * v1 + eta * v2 - eta * v3;
+  const double cx_eta = -xi * u1 + xi * u2 + a * u3;
+  const double cy_eta = -xi * v1 + xi * v2 + a * v3;
+  out[0] = c[0] + (b * bx + eta * tx + a * lx + xi * rx - cxv);
+  out[1] = c[1] + (b * by + eta * ty + a * ly + xi * ry - cyv);
   out[2] = b * dbx + eta * dtx - lx + rx - cx_xi;
   out[3] = b * dby + eta * dty - ly + ry - cy_xi;
   out[4] = -bx + tx + a * dlx + xi * drx - cx_eta;
   out[5] = -by + ty + a * dly + xi * dry - cy_eta;
 }
 
-// t = 0 metric tables of every element (one thread per element)
+// t = 0 metric tables (one thread per table; table t belongs to element tab_elem[t])
 template <typename T, int N>
 __global__ void k_geo(MeshDev md, const double *__restrict__ Xs, const double *__restrict__ Xf) {
   using L = GeoLayout<N>;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= md.E) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= md.nTab) return;
+  const int e = md.tab_elem[t];
   double c[8];
   for (int k = 0; k < 8; ++k) c[k] = md.corners[(size_t)e * 8 + k];
   const int arcs = md.arcs[e];
   const double om = md.zone[e] == 1 ? md.omega : 0.0;
-  T *g = (T *)md.geo + (size_t)e * L::G;
-  bool bad = false;
+  T *g = (T *)md.geo + (size_t)t * L::G;
   double m[6];
   for (int j = 0; j < N; ++j)
     for (int i = 0; i <= N; ++i) {
@@ -140,27 +165,61 @@ __global__ void k_geo(MeshDev md, const double *__restrict__ Xs, const double *_
       g[L::ax + j * (N + 1) + i] = (T)ax;
       g[L::ay + j * (N + 1) + i] = (T)ay;
       g[L::gx + j * (N + 1) + i] = (T)(om * (-m[1] * ax + m[0] * ay));
-      bad |= !(m[2] * m[5] - m[4] * m[3] > 0.0);
       // eta-FP (X_j, X_{i+1/2}) stored at FP row i, column j
       cell_map(c, arcs, Xs[j], Xf[i], m);
       const double bx = -m[3], by = m[2];
       g[L::bx + i * N + j] = (T)bx;
       g[L::by + i * N + j] = (T)by;
       g[L::gy + i * N + j] = (T)(om * (-m[1] * bx + m[0] * by));
-      bad |= !(m[2] * m[5] - m[4] * m[3] > 0.0);
     }
   for (int j = 0; j < N; ++j)
     for (int i = 0; i < N; ++i) {
       cell_map(c, arcs, Xs[i], Xs[j], m);
       const double J = m[2] * m[5] - m[4] * m[3];
-      bad |= !(J > 0.0);
       g[L::iJ + j * N + i] = (T)(1.0 / J);
       g[L::grad + 0 * N * N + j * N + i] = (T)(m[5] / J);   // xi_x
       g[L::grad + 1 * N * N + j * N + i] = (T)(-m[4] / J);  // xi_y
       g[L::grad + 2 * N * N + j * N + i] = (T)(-m[3] / J);  // eta_x
       g[L::grad + 3 * N * N + j * N + i] = (T)(m[2] / J);   // eta_y
     }
+}
+
+// Every cell: positive Jacobian at all SPs and FPs (folded or clockwise cells
+// set flag bit 1), and the bilinear record x0, y0, e1 = x1 - x0, e3 = x3 - x0,
+// d = x2 - x1 - x3 + x0 (centre-relative, differences formed in FP64) used for
+// the on-the-fly metrics of straight cells.
+template <typename T, int N>
+__global__ void k_egeo(MeshDev md, const double *__restrict__ Xs, const double *__restrict__ Xf) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= md.E) return;
+  double c[8], m[6];
+  for (int k = 0; k < 8; ++k) c[k] = md.corners[(size_t)e * 8 + k];
+  const int arcs = md.arcs[e];
+  bool bad = false;
+  for (int j = 0; j < N; ++j) {
+    for (int i = 0; i <= N; ++i) {
+      cell_map(c, arcs, Xf[i], Xs[j], m);  // xi-FP
+      bad |= !(m[2] * m[5] - m[4] * m[3] > 0.0);
+      cell_map(c, arcs, Xs[j], Xf[i], m);  // eta-FP
+      bad |= !(m[2] * m[5] - m[4] * m[3] > 0.0);
+    }
+    for (int i = 0; i < N; ++i) {
+      cell_map(c, arcs, Xs[i], Xs[j], m);  // SP
+      bad |= !(m[2] * m[5] - m[4] * m[3] > 0.0);
+    }
+  }
   if (bad) atomicOr(&md.clk->flags, 2);
+  if (md.egeo) {
+    T *r = (T *)md.egeo + (size_t)e * 8;
+    r[0] = (T)c[0];
+    r[1] = (T)c[1];
+    r[2] = (T)(c[2] - c[0]);
+    r[3] = (T)(c[3] - c[1]);
+    r[4] = (T)(c[6] - c[0]);
+    r[5] = (T)(c[7] - c[1]);
+    r[6] = (T)((c[4] - c[2]) - (c[6] - c[0]));
+    r[7] = (T)((c[5] - c[3]) - (c[7] - c[1]));
+  }
 }
 
 // t = 0 positions of boundary-face points (wall velocity of the rotating zone)
@@ -196,6 +255,94 @@ __global__ void k_spxy(MeshDev md, const double *__restrict__ Xs, double t, doub
       out[(((size_t)e * N + j) * N + i) * 2 + 1] = cy + (sn * m[0] + cs * m[1]);
     }
 }
+
+// Metrics of one element at the current rotation (Sec. 2.3): either its t = 0
+// table rotated by R(theta), or, for a straight cell on the on-the-fly path,
+// the bilinear map from its rotated record.  The grid-velocity coefficient
+// V_g . a is rotation invariant.
+template <typename T, int N, bool OTF>
+struct ElemGeo {
+  using L = GeoLayout<N>;
+  const T *tab;
+  T c, s, om;
+  T x0, y0, e1x, e1y, e3x, e3y, dx, dy;
+
+  __device__ __forceinline__ void load(const MeshDev &md, int e, T cth, T sth) {
+    load_rec(md, e, md.eflag[e], OTF ? (const T *)md.egeo + (size_t)e * 8 : nullptr, cth, sth);
+  }
+  // the same with the flag and the bilinear record already at hand (e.g. in shared memory)
+  __device__ __forceinline__ void load_rec(const MeshDev &md, int e, int f, const T *r, T cth, T sth) {
+    const bool rot = f & 1;
+    c = rot ? cth : T(1);
+    s = rot ? sth : T(0);
+    om = rot ? (T)md.omega : T(0);
+    const int ti = (f >> 1) - 1;
+    if (OTF && ti < 0) {
+      tab = nullptr;
+      const T v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4], v5 = r[5], v6 = r[6], v7 = r[7];
+      x0 = c * v0 - s * v1;
+      y0 = s * v0 + c * v1;
+      e1x = c * v2 - s * v3;
+      e1y = s * v2 + c * v3;
+      e3x = c * v4 - s * v5;
+      e3y = s * v4 + c * v5;
+      dx = c * v6 - s * v7;
+      dy = s * v6 + c * v7;
+    } else {
+      tab = (const T *)md.geo + (size_t)ti * L::G;
+    }
+  }
+  // xi-FP (X_{i+1/2}, X_j): a = (y_eta, -x_eta) and V_g . a
+  __device__ __forceinline__ void xi_fp(int i, int j, T &vx, T &vy, T &g) const {
+    if (OTF && tab == nullptr) {
+      const T xi = cVB<T, N>.Xf[i], eta = cVB<T, N>.Xs[j];
+      const T xe = e3x + xi * dx, ye = e3y + xi * dy;
+      vx = ye;
+      vy = -xe;
+      const T px = x0 + xi * e1x + eta * xe, py = y0 + xi * e1y + eta * ye;
+      g = om * (px * vy - py * vx);
+    } else {
+      const int k = j * (N + 1) + i;
+      const T ax = tab[L::ax + k], ay = tab[L::ay + k];
+      vx = c * ax - s * ay;
+      vy = s * ax + c * ay;
+      g = tab[L::gx + k];
+    }
+  }
+  // eta-FP (X_i, X_{l+1/2}): b = (-y_xi, x_xi) and V_g . b
+  __device__ __forceinline__ void eta_fp(int i, int l, T &vx, T &vy, T &g) const {
+    if (OTF && tab == nullptr) {
+      const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xf[l];
+      const T xx = e1x + eta * dx, yx = e1y + eta * dy;
+      vx = -yx;
+      vy = xx;
+      const T px = x0 + eta * e3x + xi * xx, py = y0 + eta * e3y + xi * yx;
+      g = om * (px * vy - py * vx);
+    } else {
+      const int k = l * N + i;
+      const T bx = tab[L::bx + k], by = tab[L::by + k];
+      vx = c * bx - s * by;
+      vy = s * bx + c * by;
+      g = tab[L::gy + k];
+    }
+  }
+  // metric vector of the end FP at point j of face f
+  __device__ __forceinline__ void face(int f, int j, T &vx, T &vy, T &g) const {
+    if (f == 1) xi_fp(N, j, vx, vy, g);
+    else if (f == 3) xi_fp(0, j, vx, vy, g);
+    else if (f == 0) eta_fp(j, 0, vx, vy, g);
+    else eta_fp(j, N, vx, vy, g);
+  }
+  // 1 / |J| at SP (X_i, X_j)
+  __device__ __forceinline__ T inv_jac(int i, int j) const {
+    if (OTF && tab == nullptr) {
+      const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
+      const T xx = e1x + eta * dx, yx = e1y + eta * dy, xe = e3x + xi * dx, ye = e3y + xi * dy;
+      return T(1) / (xx * ye - xe * yx);
+    }
+    return tab[L::iJ + j * N + i];
+  }
+};
 
 // ---------------------------------------------------------------------------
 // physics (Sec. 2)
@@ -233,31 +380,10 @@ __device__ __forceinline__ void rusanov(const T *qL, const T *qR, T nx, T ny, T 
   for (int v = 0; v < 4; ++v) Fn[v] = T(0.5) * (fL[v] + fR[v]) - T(0.5) * lam * (qR[v] - qL[v]);
 }
 
-// metric vector of the end FP at face f, point j, of an element's table
-template <typename T, int N>
-__device__ __forceinline__ void end_metric(const T *__restrict__ g, int f, int j, T &vx, T &vy, T &vg) {
-  using L = GeoLayout<N>;
-  int o0, o1, o2, idx;
-  if (f == 1 || f == 3) {
-    o0 = L::ax; o1 = L::ay; o2 = L::gx;
-    idx = j * (N + 1) + (f == 1 ? N : 0);
-  } else {
-    o0 = L::bx; o1 = L::by; o2 = L::gy;
-    idx = (f == 2 ? N : 0) * N + j;
-  }
-  vx = g[o0 + idx];
-  vy = g[o1 + idx];
-  vg = g[o2 + idx];
-}
-
 // ---------------------------------------------------------------------------
 // per-stage coupling kernels
 // ---------------------------------------------------------------------------
 
-// Stage clock and mortar table (Sec. 3.2: connectivity updated at every
-// stage).  Mortar k is the interval between merged node positions k and k+1
-// (counter-clockwise, cyclic); nodes of both sides are sorted by angle, L
-// before R on ties.  One CTA; loops cover any interface size.
 __device__ __forceinline__ double wrap_2pi(double a) {
   const double tp = 6.283185307179586476925286766559;
   double r = fmod(a, tp);
@@ -269,7 +395,13 @@ __device__ __forceinline__ double wrap_pi(double a) {
   return wrap_2pi(a + pi) - pi;
 }
 
-static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *scratch_i, double *scratch_d) {
+// Stage clock and mortar table (Sec. 3.2: connectivity updated at every
+// stage).  Mortar k is the interval between merged node positions k and k+1
+// (counter-clockwise, cyclic); nodes of both sides sorted by angle, L before R
+// on ties.  One CTA; the node angles are searched in shared memory (dynamic,
+// (nL + nR) doubles); work_i / work_d hold the merged positions and angles.
+static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_i, double *work_d) {
+  extern __shared__ double s_ang[];  // [nL] rotated L angles, then [nR] R angles
   __shared__ double s_theta;
   __shared__ int s_k0;
   const int nL = md.nL, nR = md.nR, nb = nL + nR;
@@ -289,31 +421,29 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *scrat
   __syncthreads();
   if (nL == 0) return;
   const double th = s_theta;
-  // rotated L angles: a cyclic shift of an ascending list; k0 = index of the minimum
-  for (int k = threadIdx.x; k < nL; k += blockDim.x) {
-    const double a = wrap_2pi(md.La[k] + th);
-    scratch_d[k] = a;
-  }
+  double *sL = s_ang, *sR = s_ang + nL;
+  for (int k = threadIdx.x; k < nL; k += blockDim.x) sL[k] = wrap_2pi(md.La[k] + th);
+  for (int k = threadIdx.x; k < nR; k += blockDim.x) sR[k] = md.Ra[k];
   __syncthreads();
+  // rotated L angles are a cyclic shift of an ascending list; k0 = index of the minimum
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
     const int kp = k == 0 ? nL - 1 : k - 1;
-    if (scratch_d[k] < scratch_d[kp]) s_k0 = k;
+    if (sL[k] < sL[kp]) s_k0 = k;
   }
   __syncthreads();
   const int k0 = s_k0;
-  double *mAng = scratch_d + nL;  // [nb] merged angles
-  int *posL = scratch_i;          // [nL] merged position of L node k (t=0 index)
-  int *posR = scratch_i + nL;     // [nR]
-  int *otherL = scratch_i + nb;   // [nL] R face containing the mortar that starts at L node k
-  int *otherR = otherL + nL;      // [nR] L face (t=0 index) containing the mortar starting at R node k
+  double *mAng = work_d;          // [nb] merged angles
+  int *posL = work_i;             // [nL] merged position of L node k (t = 0 index)
+  int *posR = work_i + nL;        // [nR]
+  int *otherL = work_i + nb;      // [nL] R face containing the mortar that starts at L node k
+  int *otherR = otherL + nL;      // [nR] L face containing the mortar that starts at R node k
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
-    const double a = scratch_d[k];
+    const double a = sL[k];
     const int rank = (k - k0 + nL) % nL;
-    // number of R angles strictly below a
-    int lo = 0, hi = nR;
+    int lo = 0, hi = nR;  // number of R angles strictly below a
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (md.Ra[mid] < a) lo = mid + 1; else hi = mid;
+      if (sR[mid] < a) lo = mid + 1; else hi = mid;
     }
     const int p = rank + lo;
     posL[k] = p;
@@ -321,12 +451,13 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *scrat
     otherL[k] = lo == 0 ? nR - 1 : lo - 1;
   }
   for (int k = threadIdx.x; k < nR; k += blockDim.x) {
-    const double a = md.Ra[k];
-    // number of rotated L angles <= a (L first on ties)
-    int lo = 0, hi = nL;
+    const double a = sR[k];
+    int lo = 0, hi = nL;  // number of rotated L angles <= a (L first on ties)
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (scratch_d[(k0 + mid) % nL] <= a) lo = mid + 1; else hi = mid;
+      int idx = k0 + mid;
+      if (idx >= nL) idx -= nL;
+      if (sL[idx] <= a) lo = mid + 1; else hi = mid;
     }
     const int p = k + lo;
     posR[k] = p;
@@ -334,12 +465,11 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *scrat
     otherR[k] = lo == 0 ? (k0 + nL - 1) % nL : (k0 + lo - 1) % nL;
   }
   __syncthreads();
-  const double tp = 6.283185307179586476925286766559;
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
     const int p = posL[k];
     md.mLf[p] = k;
     md.mRf[p] = otherL[k];
-    const int cnt = (posL[(k + 1) % nL] - p + nb) % nb;
+    const int cnt = (posL[k + 1 == nL ? 0 : k + 1] - p + nb) % nb;
     md.Lstart[k] = p;
     md.Lcount[k] = cnt == 0 ? nb : cnt;
   }
@@ -347,21 +477,21 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *scrat
     const int p = posR[k];
     md.mRf[p] = k;
     md.mLf[p] = otherR[k];
-    const int cnt = (posR[(k + 1) % nR] - p + nb) % nb;
+    const int cnt = (posR[k + 1 == nR ? 0 : k + 1] - p + nb) % nb;
     md.Rstart[k] = p;
     md.Rcount[k] = cnt == 0 ? nb : cnt;
   }
   __syncthreads();
+  const double tp = 6.283185307179586476925286766559;
   for (int p = threadIdx.x; p < nb; p += blockDim.x) {
     const double a = mAng[p];
     const double b = p + 1 < nb ? mAng[p + 1] : mAng[0] + tp;
     const double d = b - a;
     const int fl = md.mLf[p], fr = md.mRf[p];
-    const double aL = wrap_2pi(md.La[fl] + th);
     double *g = md.mgeo + (size_t)p * 6;
-    g[0] = wrap_pi(a - aL) / md.Lw[fl];
+    g[0] = wrap_pi(a - sL[fl]) / md.Lw[fl];
     g[1] = d / md.Lw[fl];
-    g[2] = wrap_pi(a - md.Ra[fr]) / md.Rw[fr];
+    g[2] = wrap_pi(a - sR[fr]) / md.Rw[fr];
     g[3] = d / md.Rw[fr];
     g[4] = a;
     g[5] = d;
@@ -369,9 +499,8 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *scrat
 }
 
 // Conforming and periodic faces: one thread per face point.
-template <typename T, int N>
+template <typename T, int N, bool OTF>
 __global__ void k_face(MeshDev md) {
-  using L = GeoLayout<N>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= md.nF * N) return;
   const int fi = t / N, j = t - fi * N;
@@ -385,17 +514,13 @@ __global__ void k_face(MeshDev md) {
     qA[v] = TR[((size_t)efA * 4 + v) * N + j];
     qB[v] = TR[((size_t)efB * 4 + v) * N + jB];
   }
-  const T *gA = (const T *)md.geo + (size_t)eA * L::G;
-  const T *gB = (const T *)md.geo + (size_t)eB * L::G;
+  const T cth = (T)md.clk->c, sth = (T)md.clk->s;
+  ElemGeo<T, N, OTF> GA, GB;
+  GA.load(md, eA, cth, sth);
+  GB.load(md, eB, cth, sth);
   T ax, ay, ag, bx, by, bg;
-  end_metric<T, N>(gA, fA, j, ax, ay, ag);
-  end_metric<T, N>(gB, fB, jB, bx, by, bg);
-  if (md.zone[eA] == 1) {
-    const T c = (T)md.clk->c, s = (T)md.clk->s;
-    const T rx = c * ax - s * ay, ry = s * ax + c * ay;
-    ax = rx;
-    ay = ry;
-  }
+  GA.face(fA, j, ax, ay, ag);
+  GB.face(fB, jB, bx, by, bg);
   const T SA = sqrt(ax * ax + ay * ay), SB = sqrt(bx * bx + by * by);
   const T sgA = (T)face_sigma(fA), sgB = (T)face_sigma(fB);
   const T nx = sgA * ax / SA, ny = sgA * ay / SA, vgn = sgA * ag / SA;
@@ -411,9 +536,8 @@ __global__ void k_face(MeshDev md) {
 
 // Isothermal no-slip walls moving with their zone: Rusanov through a ghost
 // state with velocity 2 V_w - V, the wall temperature and the interior pressure.
-template <typename T, int N>
+template <typename T, int N, bool OTF>
 __global__ void k_bface(MeshDev md) {
-  using L = GeoLayout<N>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= md.nB * N) return;
   const int b = t / N, j = t - b * N;
@@ -422,15 +546,13 @@ __global__ void k_bface(MeshDev md) {
   T q[4], qg[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) q[v] = TR[((size_t)ef * 4 + v) * N + j];
-  const T *g = (const T *)md.geo + (size_t)e * L::G;
+  const double c = md.clk->c, s = md.clk->s;
+  ElemGeo<T, N, OTF> G;
+  G.load(md, e, (T)c, (T)s);
   T ax, ay, ag;
-  end_metric<T, N>(g, f, j, ax, ay, ag);
+  G.face(f, j, ax, ay, ag);
   double uw = 0.0, vw = 0.0;
-  if (md.zone[e] == 1) {
-    const double c = md.clk->c, s = md.clk->s;
-    const T rx = (T)c * ax - (T)s * ay, ry = (T)s * ax + (T)c * ay;
-    ax = rx;
-    ay = ry;
+  if (md.eflag[e] & 1) {
     const double x0 = md.bxy[((size_t)b * N + j) * 2], y0 = md.bxy[((size_t)b * N + j) * 2 + 1];
     const double x = c * x0 - s * y0, y = s * x0 + c * y0;
     uw = -md.omega * y;
@@ -623,69 +745,202 @@ __global__ void k_mortar_gather(MeshDev md) {
 }
 
 // ---------------------------------------------------------------------------
-// traces of a state (used before the first stage and by the residual call)
+// state conversion and traces
 // ---------------------------------------------------------------------------
+
+// FP64 state -> double-float pair (hi = round(x), lo = round(x - hi))
+static __global__ void k_split(const double *__restrict__ Q, float *hi, float *lo, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = Q[i];
+  const float h = __double2float_rn(x);
+  hi[i] = h;
+  lo[i] = __double2float_rn(x - (double)h);
+}
+
+static __global__ void k_join(const float *__restrict__ hi, const float *__restrict__ lo, double *Q, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Q[i] = (double)hi[i] + (double)lo[i];
+}
+
+// face traces [E][4][4][N] of a state (compute-precision values)
 template <typename T, int N>
-__global__ void k_trace(MeshDev md, const double *__restrict__ Q) {
+__global__ void k_trace(MeshDev md, const T *__restrict__ Q) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= md.E * 16 * N) return;
   const int e = t / (16 * N);
   const int r = t - e * 16 * N;
   const int f = r / (4 * N), v = (r / N) & 3, j = r % N;
   const VolBasis<T, N> &B = cVB<T, N>;
-  const double *q = Q + ((size_t)e * 4 + v) * N * N;
+  const T *q = Q + ((size_t)e * 4 + v) * N * N;
   T acc = 0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     // f0 eta=0 / f2 eta=1: column j; f1 xi=1 / f3 xi=0: row j
-    const T qk = (T)((f == 0 || f == 2) ? q[k * N + j] : q[j * N + k]);
+    const T qk = (f == 0 || f == 2) ? q[k * N + j] : q[j * N + k];
     acc += qk * ((f == 1 || f == 2) ? B.H1[k] : B.H0[k]);
   }
   ((T *)md.TR)[t] = acc;
 }
 
 // ---------------------------------------------------------------------------
-// volume kernel
+// volume kernel: persistent CTAs stream element tiles through shared memory
+// with 1-D bulk TMA copies (cp.async.bulk + mbarrier), two stages deep, so the
+// next tile's state, base state, common fluxes and cell records load while
+// the current tile computes.  Every per-element array is padded to a whole
+// number of tiles, so each copy is a full, 16-byte-aligned tile.
 // ---------------------------------------------------------------------------
-template <int N>
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait: gives up after a fixed number of polls (each poll may suspend
+// the thread for a hardware-defined time), so a lost copy cannot hang the GPU
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// exact sum s + e = a + b (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <typename T, int N, bool OTF>
 struct VolCfg {
-  static constexpr int EPB = (128 / (2 * N)) > 0 ? 128 / (2 * N) : 1;  // elements per CTA
-  static constexpr int THREADS = EPB * 2 * N;                          // one thread per line
+  static constexpr int NN = N * N;
+  static constexpr bool FF = std::is_same<T, float>::value;  // double-float state
+  static constexpr int EPB = N == 3 ? 16 : (N == 6 ? 8 : 12);  // elements per tile (multiple of 4)
+  static constexpr int THREADS = EPB * 2 * N;                  // one thread per SP line
+  // one stage: state (hi, lo), base state (hi, lo), common fluxes, cell records, flags
+  static constexpr int QHI = EPB * 4 * NN * (int)sizeof(T);
+  static constexpr int QLO = FF ? EPB * 4 * NN * 4 : 0;
+  static constexpr int CFB = EPB * 16 * N * (int)sizeof(T);
+  static constexpr int EGB = OTF ? EPB * 8 * (int)sizeof(T) : 0;
+  static constexpr int EFB = EPB * 4;
+  static constexpr int O_QHI = 0, O_QLO = O_QHI + QHI, O_NHI = O_QLO + QLO, O_NLO = O_NHI + QHI,
+                       O_CF = O_NLO + QLO, O_EG = O_CF + CFB, O_EF = O_EG + EGB;
+  static constexpr int STAGE = ((O_EF + EFB) + 127) / 128 * 128;
+  // work arrays after the two stages
+  static constexpr int O_RF = 2 * STAGE, O_RG = O_RF + QHI, O_IJ = O_RG + QHI;
+  static constexpr int O_BAR = ((O_IJ + EPB * NN * (int)sizeof(T)) + 15) / 16 * 16;
+  static constexpr int SMEM = O_BAR + 16;
 };
 
-template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(VolCfg<N>::THREADS)
-    k_volume(MeshDev md, const double *Qin, const double *Qbase, double *Qout, double *Rout, double alpha,
-             double beta, double dt) {
-  using L = GeoLayout<N>;
-  constexpr int EPB = VolCfg<N>::EPB, NT = VolCfg<N>::THREADS, NN = N * N;
-  __shared__ T sQ[EPB][4][NN];
-  __shared__ T sCF[EPB][16 * N];
-  __shared__ T sRF[EPB][4][NN];
-  __shared__ T sRG[EPB][4][NN];
+template <typename T, int N, int MODE, bool OTF>
+__global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
+    k_volume(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, double alpha, double beta,
+             double dt, int ntiles) {
+  using C = VolCfg<T, N, OTF>;
+  constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
+  constexpr bool FF = C::FF;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = (uint64_t *)(smem + C::O_BAR);
+  T(*sRF)[4][NN] = (T(*)[4][NN])(smem + C::O_RF);
+  T(*sRG)[4][NN] = (T(*)[4][NN])(smem + C::O_RG);
+  T(*sIJ)[NN] = (T(*)[NN])(smem + C::O_IJ);
   const VolBasis<T, N> &B = cVB<T, N>;
-  const int e0 = blockIdx.x * EPB;
-  const int ne = min(EPB, md.E - e0);
-  // coalesced tile loads
-  {
-    const double *src = Qin + (size_t)e0 * 4 * NN;
-    T *dst = &sQ[0][0][0];
-    for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) dst[i] = (T)src[i];
-    const T *cf = (const T *)md.CF + (size_t)e0 * 16 * N;
-    T *dcf = &sCF[0][0];
-    for (int i = threadIdx.x; i < ne * 16 * N; i += NT) dcf[i] = cf[i];
+  const bool use_base = MODE == MODE_RK && alpha != 0.0;
+  const uint32_t tx_bytes = C::QHI + C::QLO + C::CFB + C::EGB + C::EFB + (use_base ? C::QHI + C::QLO : 0);
+  const T cth = (T)md.clk->c, sth = (T)md.clk->s;
+  const T gm1 = (T)(md.gamma - 1.0);
+  // stage constants, converted once per thread
+  const T bdt = (T)(beta * dt), af = (T)alpha;
+
+  auto issue = [&](int tl, int st) {
+    unsigned char *sb = smem + st * C::STAGE;
+    const size_t e0 = (size_t)tl * EPB;
+    mbar_expect_tx(&bar[st], tx_bytes);
+    bulk_g2s(sb + C::O_QHI, (const T *)in.hi + e0 * 4 * NN, C::QHI, &bar[st]);
+    if (FF) bulk_g2s(sb + C::O_QLO, (const float *)in.lo + e0 * 4 * NN, C::QLO, &bar[st]);
+    if (use_base) {
+      bulk_g2s(sb + C::O_NHI, (const T *)base.hi + e0 * 4 * NN, C::QHI, &bar[st]);
+      if (FF) bulk_g2s(sb + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QLO, &bar[st]);
+    }
+    bulk_g2s(sb + C::O_CF, (const T *)md.CF + e0 * 16 * N, C::CFB, &bar[st]);
+    if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, C::EGB, &bar[st]);
+    bulk_g2s(sb + C::O_EF, md.eflag + e0, C::EFB, &bar[st]);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
   }
   __syncthreads();
-  const T cth = (T)md.clk->c, sth = (T)md.clk->s;
-  const T gam = (T)md.gamma, gm1 = (T)(md.gamma - 1.0);
-  {
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  bool bad = false;
+  int it = 0;
+  for (; tile < ntiles; tile += gridDim.x, ++it) {
+    const int st = it & 1;
+    const int next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles) {
+      // the other stage was last read in the previous iteration (before its
+      // closing barrier); order those generic reads before the async refill
+      fence_proxy_async_smem();
+      issue(next, st ^ 1);
+    }
+    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1));
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(&md.clk->flags, 4);
+        // let the prefetch of the next tile land before the CTA exits
+        if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+      }
+      return;
+    }
+    unsigned char *sb = smem + st * C::STAGE;
+    T(*sQ)[4][NN] = (T(*)[4][NN])(sb + C::O_QHI);
+    const T(*sCF)[16 * N] = (const T(*)[16 * N])(sb + C::O_CF);
+    const int *sEF = (const int *)(sb + C::O_EF);
+    const T *sEG = (const T *)(sb + C::O_EG);
+    const int e0 = tile * EPB;
+    const int ne = min(EPB, md.E - e0);
+    // ---- phase 1: one thread per SP line (xi lines, then eta lines) ----
     const int le = threadIdx.x / (2 * N);
     const int r = threadIdx.x - le * 2 * N;
     const int d = r / N, mline = r - d * N;
     if (le < ne) {
-      const int e = e0 + le;
-      const bool rot = md.zone[e] == 1;
-      const T *g = (const T *)md.geo + (size_t)e * L::G;
+      ElemGeo<T, N, OTF> G;
+      G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, cth, sth);
       T q[4][N];
 #pragma unroll
       for (int k = 0; k < N; ++k)
@@ -712,15 +967,9 @@ __global__ void __launch_bounds__(VolCfg<N>::THREADS)
             for (int k = 0; k < N; ++k) s += q[v][k] * B.Hf[i * N + k];
             qf[v] = s;
           }
-          const int gi = d == 0 ? mline * (N + 1) + i : i * N + mline;
-          T vx = g[(d == 0 ? L::ax : L::bx) + gi];
-          T vy = g[(d == 0 ? L::ay : L::by) + gi];
-          const T vg = g[(d == 0 ? L::gx : L::gy) + gi];
-          if (rot) {
-            const T rx = cth * vx - sth * vy, ry = sth * vx + cth * vy;
-            vx = rx;
-            vy = ry;
-          }
+          T vx, vy, vg;
+          if (d == 0) G.xi_fp(i, mline, vx, vy, vg);
+          else G.eta_fp(mline, i, vx, vy, vg);
           const T p = pressure_of(qf, gm1);
           normal_flux(qf, p, vx, vy, vg, f);
         }
@@ -733,9 +982,11 @@ __global__ void __launch_bounds__(VolCfg<N>::THREADS)
       }
       if (d == 0) {
 #pragma unroll
-        for (int k = 0; k < N; ++k)
+        for (int k = 0; k < N; ++k) {
 #pragma unroll
           for (int v = 0; v < 4; ++v) sRF[le][v][mline * N + k] = acc[v][k];
+          sIJ[le][mline * N + k] = G.inv_jac(k, mline);
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < N; ++k)
@@ -743,56 +994,89 @@ __global__ void __launch_bounds__(VolCfg<N>::THREADS)
           for (int v = 0; v < 4; ++v) sRG[le][v][k * N + mline] = acc[v][k];
       }
     }
-  }
-  __syncthreads();
-  // divergence -> dQ/dt at the SPs; one thread per SP (all four variables)
-  bool bad = false;
-  for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
-    const int le = idx / NN, sp = idx - le * NN;
-    const int e = e0 + le;
-    const T *g = (const T *)md.geo + (size_t)e * L::G;
-    const T iJ = g[L::iJ + sp];
-    const size_t base = (size_t)e * 4 * NN + sp;
-    if (MODE == MODE_RESIDUAL) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Rout[base + v * NN] = -(double)((sRF[le][v][sp] + sRG[le][v][sp]) * iJ);
-    } else {
-      double qn[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const double R = -(double)((sRF[le][v][sp] + sRG[le][v][sp]) * iJ);
-        const double qk = Qin[base + v * NN];
-        double val = beta * (qk + dt * R);
-        if (alpha != 0.0) val = alpha * Qbase[base + v * NN] + val;
-        qn[v] = val;
-      }
-      const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
-      bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        Qout[base + v * NN] = qn[v];
-        sQ[le][v][sp] = (T)qn[v];
-      }
-    }
-  }
-  if (MODE == MODE_RK) {
-    if (bad) atomicOr(&md.clk->flags, 1);
     __syncthreads();
-    // face traces of the new state, coalesced [E][4][4][N]
-    T *tr = (T *)md.TR + (size_t)e0 * 16 * N;
-    for (int idx = threadIdx.x; idx < ne * 16 * N; idx += NT) {
-      const int le = idx / (16 * N);
-      const int r = idx - le * 16 * N;
-      const int f = r / (4 * N), v = (r / N) & 3, j = r % N;
-      T acc = 0;
+    // ---- phase 2: dQ/dt at the SPs and the Runge-Kutta combination ----
+    for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
+      const int l2 = idx / NN, sp = idx - l2 * NN;
+      const T iJ = sIJ[l2][sp];
+      const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
+      if (MODE == MODE_RESIDUAL) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const T qk = (f == 0 || f == 2) ? sQ[le][v][k * N + j] : sQ[le][v][j * N + k];
-        acc += qk * ((f == 1 || f == 2) ? B.H1[k] : B.H0[k]);
+        for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+      } else if (!FF) {
+        // FP64: Shu-Osher combination alpha Q_n + beta (Q_k + dt R)
+        const double(*sN)[4][NN] = (const double(*)[4][NN])(sb + C::O_NHI);
+        double *qo = (double *)out.hi;
+        double qn[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+          double val = beta * ((double)sQ[l2][v][sp] + dt * R);
+          if (use_base) val = alpha * sN[l2][v][sp] + val;
+          qn[v] = val;
+        }
+        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
+        bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          qo[gi + v * NN] = qn[v];
+          sQ[l2][v][sp] = (T)qn[v];
+        }
+      } else {
+        // FP32 with a double-float state: the same combination written as
+        // Q_k + [alpha (Q_n - Q_k) + beta dt R] (alpha + beta = 1); the bracket
+        // is an O(dt) increment formed in float, added to Q_k exactly (two-sum)
+        const float(*sKL)[4][NN] = (const float(*)[4][NN])(sb + C::O_QLO);
+        const float(*sNH)[4][NN] = (const float(*)[4][NN])(sb + C::O_NHI);
+        const float(*sNL)[4][NN] = (const float(*)[4][NN])(sb + C::O_NLO);
+        float *oh = (float *)out.hi, *ol = (float *)out.lo;
+        float hv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+          const float h = (float)sQ[l2][v][sp], l = sKL[l2][v][sp];
+          float inc = (float)bdt * R;
+          if (use_base) inc = fmaf((float)af, (sNH[l2][v][sp] - h) + (sNL[l2][v][sp] - l), inc);
+          float sum, err;
+          two_sum(h, inc, sum, err);
+          err += l;
+          const float H = sum + err;
+          oh[gi + v * NN] = H;
+          ol[gi + v * NN] = err - (H - sum);
+          hv[v] = H;
+        }
+        const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
+        bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sQ[l2][v][sp] = (T)hv[v];
       }
-      tr[idx] = acc;
     }
+    if (MODE == MODE_RK) {
+      __syncthreads();
+      // ---- phase 3: face traces of the new state, one thread per SP line:
+      // xi line j -> faces 3 (xi = 0) and 1 (xi = 1) at point j; eta line i ->
+      // faces 0 (eta = 0) and 2 (eta = 1) at point i ----
+      if (le < ne) {
+        T *tr = (T *)md.TR + (size_t)(e0 + le) * 16 * N;
+        const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          T a0 = 0, a1 = 0;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const T qk = d == 0 ? sQ[le][v][mline * N + k] : sQ[le][v][k * N + mline];
+            a0 += qk * B.H0[k];
+            a1 += qk * B.H1[k];
+          }
+          tr[(fa * 4 + v) * N + mline] = a0;
+          tr[(fb * 4 + v) * N + mline] = a1;
+        }
+      }
+    }
+    // every read of this stage is done before it is refilled next iteration
+    __syncthreads();
   }
+  if (MODE == MODE_RK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&md.clk->flags, 1);
 }
 
 static __global__ void k_advance(DevClock *clk, double dt) { clk->t_n = clk->t_n + dt; }
@@ -802,18 +1086,56 @@ static __global__ void k_advance(DevClock *clk, double dt) { clk->t_n = clk->t_n
 // ---------------------------------------------------------------------------
 template <typename T, int N>
 struct EngineImpl : Engine {
+  static constexpr bool OTF = std::is_same<T, float>::value;
   double *dXs = nullptr, *dXf = nullptr;
   int *scratch_i = nullptr;
   double *scratch_d = nullptr;
+  void *sA[2] = {nullptr, nullptr}, *sB[2] = {nullptr, nullptr};
+  size_t nval = 0;
+  int merge_smem = 0;
+  int grid_res = 1, grid_rk = 1;  // persistent grid sizes of the volume kernel
 
   ~EngineImpl() override {
     cudaFree(dXs);
     cudaFree(dXf);
     cudaFree(scratch_i);
     cudaFree(scratch_d);
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(sA[k]);
+      cudaFree(sB[k]);
+    }
   }
   size_t geo_words() const override { return GeoLayout<N>::G; }
   size_t compute_word() const override { return sizeof(T); }
+  bool metrics_on_the_fly() const override { return OTF; }
+
+  cudaError_t alloc_state(int E, int Epad) override {
+    nval = (size_t)E * 4 * N * N;
+    const size_t nalloc = (size_t)Epad * 4 * N * N;
+    cudaError_t e;
+    if ((e = cudaMalloc(&sA[0], sizeof(T) * nalloc))) return e;
+    if ((e = cudaMalloc(&sB[0], sizeof(T) * nalloc))) return e;
+    if (OTF) {
+      if ((e = cudaMalloc(&sA[1], sizeof(float) * nalloc))) return e;
+      if ((e = cudaMalloc(&sB[1], sizeof(float) * nalloc))) return e;
+    }
+    return cudaSuccess;
+  }
+  StatePtr A() const override { return StatePtr{sA[0], sA[1]}; }
+  StatePtr B() const override { return StatePtr{sB[0], sB[1]}; }
+
+  void set_state(const MeshDev &, const double *Q, cudaStream_t s) override {
+    if (OTF)
+      k_split<<<(unsigned)((nval + 255) / 256), 256, 0, s>>>(Q, (float *)sA[0], (float *)sA[1], nval);
+    else
+      cudaMemcpyAsync(sA[0], Q, sizeof(double) * nval, cudaMemcpyDeviceToDevice, s);
+  }
+  void get_state(const MeshDev &, double *Q, cudaStream_t s) override {
+    if (OTF)
+      k_join<<<(unsigned)((nval + 255) / 256), 256, 0, s>>>((const float *)sA[0], (const float *)sA[1], Q, nval);
+    else
+      cudaMemcpyAsync(Q, sA[0], sizeof(double) * nval, cudaMemcpyDeviceToDevice, s);
+  }
 
   cudaError_t init(const HostBasis &hb, const MeshDev &md, cudaStream_t s) override {
     VolBasis<T, N> vb;
@@ -825,11 +1147,13 @@ struct EngineImpl : Engine {
     for (int k = 0; k < N; ++k) {
       vb.H0[k] = (T)hb.H0[k];
       vb.H1[k] = (T)hb.H1[k];
+      vb.Xs[k] = (T)hb.Xs[k];
       mb.zq[k] = hb.zq[k];
       mb.wq[k] = hb.wq[k];
       mb.Xs[k] = hb.Xs[k];
       mb.cden[k] = hb.cden[k];
     }
+    for (int k = 0; k <= N; ++k) vb.Xf[k] = (T)hb.Xf[k];
     for (int k = 0; k < N * N; ++k) {
       mb.Hz[k] = hb.Hz[k];
       mb.Minv[k] = hb.Minv[k];
@@ -844,29 +1168,55 @@ struct EngineImpl : Engine {
     const int nb = md.nL + md.nR;
     if ((err = cudaMalloc(&scratch_i, sizeof(int) * (2 * nb + 1)))) return err;
     if ((err = cudaMalloc(&scratch_d, sizeof(double) * (md.nL + nb + 1)))) return err;
-    k_geo<T, N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
+    merge_smem = (int)(sizeof(double) * (nb > 0 ? nb : 1));
+    if (merge_smem > 48 * 1024) {
+      if ((err = cudaFuncSetAttribute(k_clock_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, merge_smem)))
+        return err;
+    }
+    {
+      // persistent volume kernel: as many CTAs as fit on the GPU at once
+      using C = VolCfg<T, N, OTF>;
+      int dev = 0, sms = 0, occ0 = 0, occ1 = 0;
+      if ((err = cudaGetDevice(&dev))) return err;
+      if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return err;
+      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RESIDUAL, OTF>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)))
+        return err;
+      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      C::SMEM)))
+        return err;
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_volume<T, N, MODE_RESIDUAL, OTF>, C::THREADS,
+                                                               C::SMEM)))
+        return err;
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_volume<T, N, MODE_RK, OTF>, C::THREADS,
+                                                               C::SMEM)))
+        return err;
+      grid_res = std::max(1, occ0) * sms;
+      grid_rk = std::max(1, occ1) * sms;
+    }
+    if (md.nTab > 0) k_geo<T, N><<<(md.nTab + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
+    k_egeo<T, N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
     if (md.nB > 0) k_bgeo<N><<<(md.nB + 127) / 128, 128, 0, s>>>(md, dXs, (double *)md.bxy);
-    // the stream synchronises in the caller before the geometry flag is read
-    return cudaSuccess;
+    return cudaGetLastError();
   }
 
-  void trace(const MeshDev &md, const double *Q, cudaStream_t s) override {
+  void trace(const MeshDev &md, StatePtr q, cudaStream_t s) override {
     const int n = md.E * 16 * N;
-    k_trace<T, N><<<(n + 255) / 256, 256, 0, s>>>(md, Q);
+    k_trace<T, N><<<(n + 255) / 256, 256, 0, s>>>(md, (const T *)q.hi);
   }
 
   void clock_merge(const MeshDev &md, double c, double dt, cudaStream_t s) override {
-    k_clock_merge<<<1, 1024, 0, s>>>(md, c, dt, scratch_i, scratch_d);
+    k_clock_merge<<<1, 1024, merge_smem, s>>>(md, c, dt, scratch_i, scratch_d);
   }
 
   void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                         cudaStream_t s) override {
-    k_clock_merge<<<1, 1024, 0, s>>>(md, c, dt, work_i, work_d);
+    k_clock_merge<<<1, 1024, merge_smem, s>>>(md, c, dt, work_i, work_d);
   }
 
   void faces(const MeshDev &md, cudaStream_t s) override {
-    if (md.nF > 0) k_face<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
-    if (md.nB > 0) k_bface<T, N><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
+    if (md.nF > 0) k_face<T, N, OTF><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
+    if (md.nB > 0) k_bface<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
   }
 
   void mortars(const MeshDev &md, cudaStream_t s) override {
@@ -878,15 +1228,19 @@ struct EngineImpl : Engine {
     }
   }
 
-  void volume(const MeshDev &md, const double *Qin, const double *Qbase, double *Qout, double *R, double alpha,
-              double beta, double dt, int mode, cudaStream_t s) override {
-    constexpr int EPB = VolCfg<N>::EPB;
-    const int grid = (md.E + EPB - 1) / EPB;
+  void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, double alpha, double beta,
+              double dt, int mode, cudaStream_t s) override {
+    using C = VolCfg<T, N, OTF>;
+    const int ntiles = (md.E + C::EPB - 1) / C::EPB;
     if (mode == MODE_RESIDUAL)
-      k_volume<T, N, MODE_RESIDUAL><<<grid, VolCfg<N>::THREADS, 0, s>>>(md, Qin, Qbase, Qout, R, alpha, beta, dt);
+      k_volume<T, N, MODE_RESIDUAL, OTF><<<std::min(ntiles, grid_res), C::THREADS, C::SMEM, s>>>(
+          md, in, base, out, R, alpha, beta, dt, ntiles);
     else
-      k_volume<T, N, MODE_RK><<<grid, VolCfg<N>::THREADS, 0, s>>>(md, Qin, Qbase, Qout, R, alpha, beta, dt);
+      k_volume<T, N, MODE_RK, OTF><<<std::min(ntiles, grid_rk), C::THREADS, C::SMEM, s>>>(md, in, base, out, R, alpha,
+                                                                                         beta, dt, ntiles);
   }
+
+  int tile_elems() const override { return VolCfg<T, N, OTF>::EPB; }
 
   void advance(const MeshDev &md, double dt, cudaStream_t s) override { k_advance<<<1, 1, 0, s>>>(md.clk, dt); }
 

@@ -16,7 +16,7 @@ struct DevClock {
   double t_stage;  // time of the stage being evaluated
   double theta;    // omega * t_stage
   double c, s;     // cos(theta), sin(theta)
-  int flags;       // bit 0: non-physical state met; bit 1: mesh geometry error
+  int flags;       // bit 0: non-physical state; bit 1: mesh geometry error; bit 2: a bounded device wait gave up
   int pad;
 };
 
@@ -33,6 +33,14 @@ struct HostBasis {
   double Hz[kMaxN * kMaxN];          // h_j(z_q) [q][j]
   double Minv[kMaxN * kMaxN];        // inverse mortar mass matrix (Eq. mortarM)
   double cden[kMaxN];                // 1 / prod_{s != i} (X_i - X_s)
+};
+
+// A solution state in device memory.  FP64 path: hi = double[E][4][N][N],
+// lo = nullptr.  FP32 path: the value is hi + lo with hi, lo float[E][4][N][N]
+// (a double-float pair, about 48 significant bits).
+struct StatePtr {
+  void *hi;
+  void *lo;
 };
 
 // Everything a kernel needs, by value (device pointers + sizes + parameters).
@@ -60,7 +68,13 @@ struct MeshDev {
   const double *corners;  // [E][8] t = 0 corner coordinates relative to the centre
   const int *arcs;        // [E] bit f set if local face f is an arc
   const int *zone;        // [E]
-  void *geo;              // T [E][G] metrics (see ssd_engine.cuh)
+  // eflag[e]: bit 0 = rotating zone; (table index + 1) << 1, or 0 for a
+  // straight cell whose bilinear metrics are computed on the fly
+  const int *eflag;
+  int nTab;               // number of metric tables
+  const int *tab_elem;    // [nTab] element of each table
+  void *geo;              // T [nTab][G] metric tables (see ssd_engine.cuh)
+  void *egeo;             // T [E][8] bilinear record x0, y0, e1, e3, d of each cell
   void *TR, *CF;          // T [E][4][4][N] face traces and common fluxes
   DevClock *clk;
   double omega, gamma, Rgas, mu, prandtl, T_wall, r_interface;
@@ -74,15 +88,27 @@ struct Engine {
   virtual ~Engine() {}
   virtual size_t geo_words() const = 0;
   virtual size_t compute_word() const = 0;
+  // true: straight cells get their metrics on the fly (tables only for arc cells)
+  virtual bool metrics_on_the_fly() const = 0;
+  // elements per volume-kernel tile; every per-element device array holds a
+  // whole number of tiles (padding elements are never computed on)
+  virtual int tile_elems() const = 0;
+  // the two state buffers A and B: E elements, storage for Epad >= E
+  virtual cudaError_t alloc_state(int E, int Epad) = 0;
+  virtual StatePtr A() const = 0;
+  virtual StatePtr B() const = 0;
+  // copy an FP64 state (device memory) into A, or A out as FP64 (device memory)
+  virtual void set_state(const MeshDev &md, const double *Q, cudaStream_t s) = 0;
+  virtual void get_state(const MeshDev &md, double *Q, cudaStream_t s) = 0;
   // upload basis constants, compute the t = 0 metrics
   virtual cudaError_t init(const HostBasis &hb, const MeshDev &md, cudaStream_t s) = 0;
-  // face traces of Q
-  virtual void trace(const MeshDev &md, const double *Q, cudaStream_t s) = 0;
+  // face traces of a state
+  virtual void trace(const MeshDev &md, StatePtr q, cudaStream_t s) = 0;
   // stage clock at t_n + c dt and mortar table; common fluxes on conforming,
   // periodic and wall faces; mortar fluxes gathered onto the interface faces
   virtual void clock_merge(const MeshDev &md, double c, double dt, cudaStream_t s) = 0;
   // the same merge with caller-provided work arrays (ints: 2 (nL + nR) + 1,
-  // doubles: 2 nL + nR + 1)
+  // doubles: nL + (nL + nR) + 1)
   virtual void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                                 cudaStream_t s) = 0;
   virtual void faces(const MeshDev &md, cudaStream_t s) = 0;
@@ -92,16 +118,13 @@ struct Engine {
     faces(md, s);
     mortars(md, s);
   }
-  // divergence; MODE_RESIDUAL writes R, MODE_RK writes
+  // divergence; MODE_RESIDUAL writes R (FP64), MODE_RK writes the stage
   // Qout = alpha Qbase + beta (Qin + dt R) and its face traces
-  virtual void volume(const MeshDev &md, const double *Qin, const double *Qbase, double *Qout, double *R,
-                      double alpha, double beta, double dt, int mode, cudaStream_t s) = 0;
+  virtual void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, double alpha,
+                      double beta, double dt, int mode, cudaStream_t s) = 0;
   virtual void advance(const MeshDev &md, double dt, cudaStream_t s) = 0;
   virtual void sp_coords(const MeshDev &md, double t, double cx, double cy, double *xy, cudaStream_t s) = 0;
 };
-
-// FMA throughput probe: flops/s of a dependent-chain-free FMA loop in T
-double fma_probe(int precision, cudaStream_t s, float *ms_out);
 
 Engine *make_engine_f64(int N);
 Engine *make_engine_f32(int N);

@@ -186,3 +186,51 @@ def test_bad_mesh_rejected_by_library(ssd):
     m["elem_nodes"] = en
     with pytest.raises(ssd.SSDError):
         ssd.Solver(m, 2, FlowParams())
+
+
+@pytest.fixture(scope="module")
+def rotor_full(oracle_mod):
+    w = build_workload("rotor_n6")
+    o = oracle_mod.Oracle(w.mesh, w.N, w.params)
+    Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=3.0, y0=1.0))
+    return w, o, Q
+
+
+def test_full_size_rotor_residual_fp64(ssd, rotor_full):
+    # the bench workload at full size (246,900 quads, N = 6); a state whose
+    # residual is O(1) everywhere (with the vortex most of the domain is free
+    # stream, where the true residual is below round-off and no relative
+    # measure is meaningful)
+    # At h = 0.08 and N = 6 each SP residual is a weighted difference of flux
+    # values up to ~1e3 times larger than itself, so two independent FP64
+    # evaluations differ by ~3e-12 relative L2 (the round-off floor).  Where
+    # the divergence terms do not cancel among themselves (straight cells of
+    # the stationary zone) the arithmetic bounds the difference per point:
+    # |dR| <= c u S with S = sum of the magnitudes of the divergence terms (from
+    # the oracle), u = 2^-53, c = 128 (2(N+1) terms, each flux value carrying a
+    # few tens of u, two independent evaluations).
+    w, o, _ = rotor_full
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=21, amp=0.2, scale=4.0))
+    s = ssd.Solver(w.mesh, w.N - 1, w.params)
+    s.sd_set_state(Q)
+    s.sd_set_time(0.8)
+    R = s.sd_residual()
+    Rr, S = o.residual_with_scale(Q, 0.8)
+    m = w.mesh
+    plain = (m["edge_arc"].sum(axis=1) == 0) & (m["elem_zone"] == 0)
+    ratio = np.abs(R - Rr)[plain] / (2.0 ** -53 * S[plain])
+    assert ratio.max() <= 128.0, ratio.max()
+    _check(R, Rr, (1e-11, 1e-11))
+    s.close()
+
+
+def test_full_size_rotor_step_fp32(ssd, rotor_full):
+    # one captured-graph SSP-RK3 step of the FP32 path, as the benchmark times it
+    w, o, Q = rotor_full
+    s = ssd.Solver(w.mesh, w.N - 1, w.params, precision=1)
+    s.sd_set_state(Q)
+    s.sd_step(w.cfl_dt, 1)
+    s.sd_sync()
+    q_ref, _ = o.step(Q, 0.0, w.cfl_dt, 1)
+    _check(s.sd_get_state(), q_ref, TOL32_STATE)
+    s.close()
