@@ -228,7 +228,7 @@ const int kFaceB[4] = {1, 2, 2, 3};  // end corner
 
 struct IfaceSide {
   std::vector<int4> face;
-  std::vector<double> a, w, S;
+  std::vector<double> a, w, S, iw;
 };
 
 int build_iface(sd_handle *h, const sd_mesh *m, int n, const int *lst, std::vector<int> &kind, int tag,
@@ -277,6 +277,7 @@ int build_iface(sd_handle *h, const sd_mesh *m, int n, const int *lst, std::vect
     out.a.push_back(it.a);
     out.w.push_back(it.w);
     out.S.push_back(it.S);
+    out.iw.push_back(1.0 / it.w);
   }
   return SD_OK;
 }
@@ -388,13 +389,14 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   }
   cudaError_t ce;
   int4 *dfaces, *dbfaces, *dL, *dR;
-  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS;
+  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS, *dLiW, *dRiW;
   int *darcs, *dzone;
   if ((ce = upload(h, &dfaces, faces.data(), faces.size())) || (ce = upload(h, &dbfaces, bfaces.data(), bfaces.size())) ||
       (ce = upload(h, &dL, L.face.data(), L.face.size())) || (ce = upload(h, &dR, R.face.data(), R.face.size())) ||
       (ce = upload(h, &dLa, L.a.data(), L.a.size())) || (ce = upload(h, &dLw, L.w.data(), L.w.size())) ||
       (ce = upload(h, &dLS, L.S.data(), L.S.size())) || (ce = upload(h, &dRa, R.a.data(), R.a.size())) ||
       (ce = upload(h, &dRw, R.w.data(), R.w.size())) || (ce = upload(h, &dRS, R.S.data(), R.S.size())) ||
+      (ce = upload(h, &dLiW, L.iw.data(), L.iw.size())) || (ce = upload(h, &dRiW, R.iw.data(), R.iw.size())) ||
       (ce = upload(h, &dcorn, corners.data(), corners.size())) || (ce = upload(h, &darcs, arcs.data(), arcs.size())) ||
       (ce = upload(h, &dzone, m->elem_zone, (size_t)E)))
     return cuda_fail(h, ce, "mesh upload");
@@ -408,6 +410,8 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   md.Ra = dRa;
   md.Rw = dRw;
   md.RS = dRS;
+  md.LiW = dLiW;
+  md.RiW = dRiW;
   md.corners = dcorn;
   md.arcs = darcs;
   md.zone = dzone;
@@ -454,7 +458,8 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   if ((e = dalloc(h, &md.contrib, w * 2 * nb * 4 * N))) return e;
   if ((e = dalloc(h, &md.mLf, sizeof(int) * nb))) return e;
   if ((e = dalloc(h, &md.mRf, sizeof(int) * nb))) return e;
-  if ((e = dalloc(h, &md.mgeo, sizeof(double) * 6 * nb))) return e;
+  if ((e = dalloc(h, &md.mgeo, sizeof(double) * 2 * nb))) return e;
+  if ((e = dalloc(h, &md.fgeo, w * 5 * N * (md.nF ? md.nF : 1)))) return e;
   if ((e = dalloc(h, &md.Lstart, sizeof(int) * md.nL))) return e;
   if ((e = dalloc(h, &md.Lcount, sizeof(int) * md.nL))) return e;
   if ((e = dalloc(h, &md.Rstart, sizeof(int) * md.nR))) return e;
@@ -894,7 +899,7 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   size_t off = 0;
   const size_t o_mLf = off; off += align256(sizeof(int) * nb);
   const size_t o_mRf = off; off += align256(sizeof(int) * nb);
-  const size_t o_mgeo = off; off += align256(sizeof(double) * 6 * nb);
+  const size_t o_mgeo = off; off += align256(sizeof(double) * 2 * nb);
   const size_t o_Ls = off; off += align256(sizeof(int) * md0.nL);
   const size_t o_Lc = off; off += align256(sizeof(int) * md0.nL);
   const size_t o_Rs = off; off += align256(sizeof(int) * md0.nR);

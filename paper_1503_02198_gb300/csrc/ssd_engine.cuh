@@ -400,29 +400,36 @@ __device__ __forceinline__ double wrap_pi(double a) {
 // (counter-clockwise, cyclic); nodes of both sides sorted by angle, L before R
 // on ties.  One CTA; the node angles are searched in shared memory (dynamic,
 // (nL + nR) doubles); work_i / work_d hold the merged positions and angles.
+// The offsets and scales of Eq. xz are formed per mortar in k_mortar_flux.
 static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_i, double *work_d) {
   extern __shared__ double s_ang[];  // [nL] rotated L angles, then [nR] R angles
-  __shared__ double s_theta;
+  __shared__ double s_th2;
   __shared__ int s_k0;
   const int nL = md.nL, nR = md.nR, nb = nL + nR;
+  const double tp = 6.283185307179586476925286766559;
   if (threadIdx.x == 0) {
     DevClock *k = md.clk;
     const double ts = k->t_n + c * dt;
     const double th = md.omega * ts;
+    const double th2 = wrap_2pi(th);
     k->t_stage = ts;
     k->theta = th;
+    k->theta2 = th2;
     double sn, cs;
     sincos(th, &sn, &cs);
     k->c = cs;
     k->s = sn;
-    s_theta = th;
+    s_th2 = th2;
     s_k0 = 0;
   }
   __syncthreads();
   if (nL == 0) return;
-  const double th = s_theta;
+  const double th2 = s_th2;
   double *sL = s_ang, *sR = s_ang + nL;
-  for (int k = threadIdx.x; k < nL; k += blockDim.x) sL[k] = wrap_2pi(md.La[k] + th);
+  for (int k = threadIdx.x; k < nL; k += blockDim.x) {
+    const double a = md.La[k] + th2;
+    sL[k] = a >= tp ? a - tp : a;
+  }
   for (int k = threadIdx.x; k < nR; k += blockDim.x) sR[k] = md.Ra[k];
   __syncthreads();
   // rotated L angles are a cyclic shift of an ascending list; k0 = index of the minimum
@@ -482,23 +489,40 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_
     md.Rcount[k] = cnt == 0 ? nb : cnt;
   }
   __syncthreads();
-  const double tp = 6.283185307179586476925286766559;
   for (int p = threadIdx.x; p < nb; p += blockDim.x) {
     const double a = mAng[p];
     const double b = p + 1 < nb ? mAng[p + 1] : mAng[0] + tp;
-    const double d = b - a;
-    const int fl = md.mLf[p], fr = md.mRf[p];
-    double *g = md.mgeo + (size_t)p * 6;
-    g[0] = wrap_pi(a - sL[fl]) / md.Lw[fl];
-    g[1] = d / md.Lw[fl];
-    g[2] = wrap_pi(a - sR[fr]) / md.Rw[fr];
-    g[3] = d / md.Rw[fr];
-    g[4] = a;
-    g[5] = d;
+    md.mgeo[2 * p] = a;
+    md.mgeo[2 * p + 1] = b - a;
   }
 }
 
-// Conforming and periodic faces: one thread per face point.
+// t = 0 geometry of every conforming / periodic face point (one thread per point)
+template <typename T, int N, bool OTF>
+__global__ void k_fgeo(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= md.nF * N) return;
+  const int fi = t / N, j = t - fi * N;
+  const int4 fc = md.faces[fi];
+  const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
+  ElemGeo<T, N, OTF> GA, GB;
+  GA.load(md, efA >> 2, T(1), T(0));
+  GB.load(md, efB >> 2, T(1), T(0));
+  T ax, ay, ag, bx, by, bg;
+  GA.face(efA & 3, j, ax, ay, ag);
+  GB.face(efB & 3, jB, bx, by, bg);
+  const T SA = sqrt(ax * ax + ay * ay), SB = sqrt(bx * bx + by * by);
+  const T sgA = (T)face_sigma(efA & 3), sgB = (T)face_sigma(efB & 3);
+  T *g = (T *)md.fgeo + (size_t)fi * 5 * N;
+  g[0 * N + j] = sgA * ax / SA;
+  g[1 * N + j] = sgA * ay / SA;
+  g[2 * N + j] = sgA * SA;
+  g[3 * N + j] = sgB * SB;
+  g[4 * N + j] = sgA * ag / SA;
+}
+
+// Conforming and periodic faces: one thread per face point; geometry from the
+// t = 0 face table, the normal turned by R(theta) on the rotating zone.
 template <typename T, int N, bool OTF>
 __global__ void k_face(MeshDev md) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -506,7 +530,6 @@ __global__ void k_face(MeshDev md) {
   const int fi = t / N, j = t - fi * N;
   const int4 fc = md.faces[fi];
   const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
-  const int eA = efA >> 2, fA = efA & 3, eB = efB >> 2, fB = efB & 3;
   const T *TR = (const T *)md.TR;
   T qA[4], qB[4];
 #pragma unroll
@@ -514,23 +537,22 @@ __global__ void k_face(MeshDev md) {
     qA[v] = TR[((size_t)efA * 4 + v) * N + j];
     qB[v] = TR[((size_t)efB * 4 + v) * N + jB];
   }
-  const T cth = (T)md.clk->c, sth = (T)md.clk->s;
-  ElemGeo<T, N, OTF> GA, GB;
-  GA.load(md, eA, cth, sth);
-  GB.load(md, eB, cth, sth);
-  T ax, ay, ag, bx, by, bg;
-  GA.face(fA, j, ax, ay, ag);
-  GB.face(fB, jB, bx, by, bg);
-  const T SA = sqrt(ax * ax + ay * ay), SB = sqrt(bx * bx + by * by);
-  const T sgA = (T)face_sigma(fA), sgB = (T)face_sigma(fB);
-  const T nx = sgA * ax / SA, ny = sgA * ay / SA, vgn = sgA * ag / SA;
+  const T *g = (const T *)md.fgeo + (size_t)fi * 5 * N;
+  T nx = g[j], ny = g[N + j];
+  const T sA = g[2 * N + j], sB = g[3 * N + j], vgn = g[4 * N + j];
+  if (md.eflag[efA >> 2] & 1) {
+    const T c = (T)md.clk->c, s = (T)md.clk->s;
+    const T rx = c * nx - s * ny, ry = s * nx + c * ny;
+    nx = rx;
+    ny = ry;
+  }
   T Fn[4];
   rusanov(qA, qB, nx, ny, vgn, (T)md.gamma, Fn);
   T *CF = (T *)md.CF;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    CF[((size_t)efA * 4 + v) * N + j] = sgA * SA * Fn[v];
-    CF[((size_t)efB * 4 + v) * N + jB] = -sgB * SB * Fn[v];
+    CF[((size_t)efA * 4 + v) * N + j] = sA * Fn[v];
+    CF[((size_t)efB * 4 + v) * N + jB] = -sB * Fn[v];
   }
 }
 
@@ -602,11 +624,22 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
   const MortBasis<N> &B = cMB<N>;
   double o = 0.0, s = 0.0;
   int ef = 0, rev = 0;
+  double m0 = 0.0, dm = 0.0;
   if (act) {
-    const double *g = md.mgeo + (size_t)m * 6;
-    o = g[sd ? 2 : 0];
-    s = g[sd ? 3 : 1];
-    const int4 fc = sd ? md.Rface[md.mRf[m]] : md.Lface[md.mLf[m]];
+    // Eq. xz: offset and scale of this mortar against its face on side sd
+    m0 = md.mgeo[2 * m];
+    dm = md.mgeo[2 * m + 1];
+    const double tp = 6.283185307179586476925286766559, pi = 0.5 * tp;
+    const int fq = sd ? md.mRf[m] : md.mLf[m];
+    double fa = sd ? md.Ra[fq] : md.La[fq] + md.clk->theta2;
+    if (fa >= tp) fa -= tp;
+    double off = m0 - fa;
+    if (off > pi) off -= tp;
+    if (off <= -pi) off += tp;
+    const double iw = sd ? md.RiW[fq] : md.LiW[fq];
+    o = off * iw;
+    s = dm * iw;
+    const int4 fc = sd ? md.Rface[fq] : md.Lface[fq];
     ef = fc.x;
     rev = fc.y;
     const T *TR = (const T *)md.TR;
@@ -663,9 +696,8 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
   // (D) Rusanov at mortar SP p with the radial normal (the grid velocity of
   // a rotation about the circle's centre is tangential: v_g . n = 0)
   if (act && sd == 0) {
-    const double *g = md.mgeo + (size_t)m * 6;
     double sn, cs;
-    sincos(fma(B.Xs[p], g[5], g[4]), &sn, &cs);
+    sincos(fma(B.Xs[p], dm, m0), &sn, &cs);
     T qL[4], qR[4], Fn[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -1196,6 +1228,7 @@ struct EngineImpl : Engine {
     }
     if (md.nTab > 0) k_geo<T, N><<<(md.nTab + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
     k_egeo<T, N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
+    if (md.nF > 0) k_fgeo<T, N, OTF><<<(md.nF * N + 127) / 128, 128, 0, s>>>(md);
     if (md.nB > 0) k_bgeo<N><<<(md.nB + 127) / 128, 128, 0, s>>>(md, dXs, (double *)md.bxy);
     return cudaGetLastError();
   }

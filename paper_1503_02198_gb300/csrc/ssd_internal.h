@@ -15,6 +15,7 @@ struct DevClock {
   double t_n;      // time at the start of the step
   double t_stage;  // time of the stage being evaluated
   double theta;    // omega * t_stage
+  double theta2;   // theta reduced to [0, 2 pi)
   double c, s;     // cos(theta), sin(theta)
   int flags;       // bit 0: non-physical state; bit 1: mesh geometry error; bit 2: a bounded device wait gave up
   int pad;
@@ -58,9 +59,10 @@ struct MeshDev {
   int nL, nR, nM;
   const int4 *Lface, *Rface;
   const double *La, *Lw, *LS, *Ra, *Rw, *RS;
+  const double *LiW, *RiW;  // 1 / angular width
   // per-stage mortar table (written by the merge kernel)
   int *mLf, *mRf;       // [nM] containing L / R face (sorted index)
-  double *mgeo;         // [nM][6]: oL, sL, oR, sR, start angle, angular length
+  double *mgeo;         // [nM][2]: start angle, angular length
   int *Lstart, *Lcount; // [nL] first mortar (merged position) and count
   int *Rstart, *Rcount; // [nR]
   void *contrib;        // T [2][nM][4][N] back-projected mortar fluxes
@@ -76,6 +78,8 @@ struct MeshDev {
   void *geo;              // T [nTab][G] metric tables (see ssd_engine.cuh)
   void *egeo;             // T [E][8] bilinear record x0, y0, e1, e3, d of each cell
   void *TR, *CF;          // T [E][4][4][N] face traces and common fluxes
+  void *fgeo;             // T [nF][5][N] conforming-face geometry at t = 0: unit normal
+                          // (x, y) out of side A, sigma_A |S_A|, sigma_B |S_B|, V_g . n
   DevClock *clk;
   double omega, gamma, Rgas, mu, prandtl, T_wall, r_interface;
   int viscous;
