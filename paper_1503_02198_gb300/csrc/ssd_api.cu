@@ -455,6 +455,11 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   if (otf && (e = cudaMemsetAsync(md.egeo, 0, w * Ep * 8, h->stream))) return e;
   if ((e = dalloc(h, &md.TR, w * Ep * 16 * N))) return e;
   if ((e = dalloc(h, &md.CF, w * Ep * 16 * N))) return e;
+  md.CQ = md.GTR = nullptr;
+  if (md.viscous) {
+    if ((e = dalloc(h, &md.CQ, w * Ep * 16 * N))) return e;
+    if ((e = dalloc(h, &md.GTR, w * Ep * 32 * N))) return e;
+  }
   if ((e = dalloc(h, &md.contrib, w * 2 * nb * 4 * N))) return e;
   if ((e = dalloc(h, &md.mLf, sizeof(int) * nb))) return e;
   if ((e = dalloc(h, &md.mRf, sizeof(int) * nb))) return e;
@@ -510,11 +515,11 @@ void queue_step(sd_handle *h, double dt) {
   Engine *g = h->eng;
   cudaStream_t s = h->stream;
   const StatePtr A = g->A(), B = g->B(), none{nullptr, nullptr};
-  g->couple(md, 0.0, dt, s);
+  g->couple(md, A, 0.0, dt, s);
   g->volume(md, A, none, B, nullptr, 0.0, 1.0, dt, MODE_RK, s);
-  g->couple(md, 1.0, dt, s);
+  g->couple(md, B, 1.0, dt, s);
   g->volume(md, B, A, B, nullptr, 0.75, 0.25, dt, MODE_RK, s);
-  g->couple(md, 0.5, dt, s);
+  g->couple(md, B, 0.5, dt, s);
   g->volume(md, B, A, A, nullptr, 1.0 / 3.0, 2.0 / 3.0, dt, MODE_RK, s);
   g->advance(md, dt, s);
 }
@@ -546,10 +551,6 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
       (prm->viscous && (!(prm->mu >= 0.0) || !(prm->prandtl > 0.0) || !(prm->T_wall > 0.0)))) {
     g_create_error = "invalid gas / flow parameters";
     return SD_ERR_ARG;
-  }
-  if (prm->viscous) {
-    g_create_error = "viscous fluxes are not built in this library version";
-    return SD_ERR_UNSUPPORTED;
   }
   if (prm->precision != SD_PREC_FP64 && prm->precision != SD_PREC_FP32) {
     g_create_error = "unknown precision";
@@ -697,7 +698,7 @@ int sd_residual(sd_handle *h, double *R, int on_device) {
   }
   const StatePtr none{nullptr, nullptr};
   h->eng->trace(h->md, h->eng->A(), h->stream);
-  h->eng->couple(h->md, 0.0, 0.0, h->stream);
+  h->eng->couple(h->md, h->eng->A(), 0.0, 0.0, h->stream);
   h->eng->volume(h->md, h->eng->A(), none, none, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
   if ((e = cudaGetLastError())) return cuda_fail(h, e, "residual kernels");
   h->traces_valid = true;
@@ -794,7 +795,7 @@ int sd_profile_step(sd_handle *h, double dt, int reps, double *ms) {
       cudaEventRecord(ev[0], h->stream);
       h->eng->clock_merge(h->md, cs[k], dt, h->stream);
       cudaEventRecord(ev[1], h->stream);
-      h->eng->faces(h->md, h->stream);
+      h->eng->faces(h->md, qin, h->stream);
       cudaEventRecord(ev[2], h->stream);
       h->eng->mortars(h->md, h->stream);
       cudaEventRecord(ev[3], h->stream);
@@ -934,7 +935,7 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   const StatePtr none{nullptr, nullptr};
   h->eng->trace(md, h->eng->A(), h->stream);
   h->eng->clock_merge_into(md, 0.0, 0.0, (int *)(b + o_wi), (double *)(b + o_wd), h->stream);
-  h->eng->faces(md, h->stream);
+  h->eng->faces(md, h->eng->A(), h->stream);
   h->eng->mortars(md, h->stream);
   h->eng->volume(md, h->eng->A(), none, none, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
   if ((e = cudaGetLastError())) return cuda_fail(h, e, "sd_residual_noalloc kernels");

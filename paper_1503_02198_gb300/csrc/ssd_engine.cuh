@@ -342,6 +342,26 @@ struct ElemGeo {
     }
     return tab[L::iJ + j * N + i];
   }
+  // gradients of xi and eta at SP (X_i, X_j): (xi_x, xi_y), (eta_x, eta_y)
+  __device__ __forceinline__ void sp_grad(int i, int j, T &xix, T &xiy, T &etx, T &ety) const {
+    if (OTF && tab == nullptr) {
+      const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
+      const T xx = e1x + eta * dx, yx = e1y + eta * dy, xe = e3x + xi * dx, ye = e3y + xi * dy;
+      const T iJ = T(1) / (xx * ye - xe * yx);
+      xix = ye * iJ;
+      xiy = -xe * iJ;
+      etx = -yx * iJ;
+      ety = xx * iJ;
+    } else {
+      const int k = j * N + i;
+      const T a = tab[L::grad + k], b = tab[L::grad + N * N + k];
+      const T c2 = tab[L::grad + 2 * N * N + k], d2 = tab[L::grad + 3 * N * N + k];
+      xix = c * a - s * b;
+      xiy = s * a + c * b;
+      etx = c * c2 - s * d2;
+      ety = s * c2 + c * d2;
+    }
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -607,7 +627,9 @@ struct MortCfg {
   static constexpr int THREADS = MPB * 2 * N;
 };
 
-template <typename T, int N>
+enum { MORTAR_RUSANOV = 0, MORTAR_AVG_Q = 1, MORTAR_AVG_FV = 2 };
+
+template <typename T, int N, int MMODE>
 __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md) {
   constexpr int MPB = MortCfg<N>::MPB;
   __shared__ double sH[MPB][2][N][N];  // h_i(o + s z_q) [q][i]
@@ -642,9 +664,29 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     const int4 fc = sd ? md.Rface[fq] : md.Lface[fq];
     ef = fc.x;
     rev = fc.y;
-    const T *TR = (const T *)md.TR;
+    const int jj = rev ? N - 1 - p : p;
+    if (MMODE == MORTAR_AVG_FV) {
+      // viscous normal flux of this face point with the common solution and
+      // the face's own gradient, along the radial normal (from L to R)
+      const T *CQ = (const T *)md.CQ, *GT = (const T *)md.GTR;
+      T q[4], g8[8], fn[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) sQf[lm][sd][v][p] = TR[((size_t)ef * 4 + v) * N + (rev ? N - 1 - p : p)];
+      for (int v = 0; v < 4; ++v) q[v] = CQ[((size_t)ef * 4 + v) * N + jj];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) g8[c] = GT[((size_t)ef * 8 + c) * N + jj];
+      const double tp = 6.283185307179586476925286766559;
+      double fa = sd ? md.Ra[fq] : md.La[fq] + md.clk->theta2;
+      if (fa >= tp) fa -= tp;
+      double sn, cs;
+      sincos(fa + B.Xs[p] * (sd ? md.Rw[fq] : md.Lw[fq]), &sn, &cs);
+      viscous_normal(q, g8, (T)cs, (T)sn, md, fn);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sQf[lm][sd][v][p] = fn[v];
+    } else {
+      const T *TR = (const T *)md.TR;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sQf[lm][sd][v][p] = TR[((size_t)ef * 4 + v) * N + jj];
+    }
     // Lagrange values at the mapped quadrature point x = o + s z_p
     const double x = fma(s, B.zq[p], o);
     double dif[N];
@@ -696,17 +738,23 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
   // (D) Rusanov at mortar SP p with the radial normal (the grid velocity of
   // a rotation about the circle's centre is tangential: v_g . n = 0)
   if (act && sd == 0) {
-    double sn, cs;
-    sincos(fma(B.Xs[p], dm, m0), &sn, &cs);
-    T qL[4], qR[4], Fn[4];
+    if (MMODE == MORTAR_RUSANOV) {
+      double sn, cs;
+      sincos(fma(B.Xs[p], dm, m0), &sn, &cs);
+      T qL[4], qR[4], Fn[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      qL[v] = sA[lm][0][v][p];
-      qR[v] = sA[lm][1][v][p];
+      for (int v = 0; v < 4; ++v) {
+        qL[v] = sA[lm][0][v][p];
+        qR[v] = sA[lm][1][v][p];
+      }
+      rusanov(qL, qR, (T)cs, (T)sn, T(0), (T)md.gamma, Fn);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sF[lm][v][p] = Fn[v];
+    } else {
+      // common value on the mortar: average of both sides (Sec. 3.2)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sF[lm][v][p] = T(0.5) * (sA[lm][0][v][p] + sA[lm][1][v][p]);
     }
-    rusanov(qL, qR, (T)cs, (T)sn, T(0), (T)md.gamma, Fn);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) sF[lm][v][p] = Fn[v];
   }
   __syncthreads();
   // (E) mortar flux polynomial at the quadrature points
@@ -748,7 +796,9 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
 // face's mortars in counter-clockwise order), written as the face's common
 // flux F~_end = sigma_f |S| F.n_out (n from L to R is outward for L, inward
 // for R).  One thread per (side, face, point).
-template <typename T, int N>
+enum { GATHER_FLUX = 0, GATHER_Q = 1, GATHER_FLUX_ADD = 2 };
+
+template <typename T, int N, int GMODE>
 __global__ void k_mortar_gather(MeshDev md) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int nLR = md.nL + md.nR;
@@ -769,11 +819,20 @@ __global__ void k_mortar_gather(MeshDev md) {
   }
   const int ef = fc.x, f = ef & 3;
   const int j = fc.y ? N - 1 - p : p;
+  if (GMODE == GATHER_Q) {
+    T *CQ = (T *)md.CQ;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) CQ[((size_t)ef * 4 + v) * N + j] = acc[v];
+    return;
+  }
   const T S = (T)(sd ? md.RS[k] : md.LS[k]);
   const T sc = (T)face_sigma(f) * S * (sd ? T(-1) : T(1));
   T *CF = (T *)md.CF;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sc * acc[v];
+  for (int v = 0; v < 4; ++v) {
+    const size_t i = ((size_t)ef * 4 + v) * N + j;
+    CF[i] = GMODE == GATHER_FLUX_ADD ? CF[i] + sc * acc[v] : sc * acc[v];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1111,6 +1170,12 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
   if (MODE == MODE_RK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&md.clk->flags, 1);
 }
 
+}  // namespace ssd
+
+#include "ssd_viscous.cuh"
+
+namespace ssd {
+
 static __global__ void k_advance(DevClock *clk, double dt) { clk->t_n = clk->t_n + dt; }
 
 // ---------------------------------------------------------------------------
@@ -1247,17 +1312,34 @@ struct EngineImpl : Engine {
     k_clock_merge<<<1, 1024, merge_smem, s>>>(md, c, dt, work_i, work_d);
   }
 
-  void faces(const MeshDev &md, cudaStream_t s) override {
-    if (md.nF > 0) k_face<T, N, OTF><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
-    if (md.nB > 0) k_bface<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
+  template <int MMODE, int GMODE>
+  void mortar_pass(const MeshDev &md, cudaStream_t s) {
+    constexpr int MPB = MortCfg<N>::MPB;
+    k_mortar_flux<T, N, MMODE><<<(md.nM + MPB - 1) / MPB, MortCfg<N>::THREADS, 0, s>>>(md);
+    const int n = (md.nL + md.nR) * N;
+    k_mortar_gather<T, N, GMODE><<<(n + 127) / 128, 128, 0, s>>>(md);
+  }
+
+  void faces(const MeshDev &md, StatePtr q, cudaStream_t s) override {
+    if (!md.viscous) {
+      if (md.nF > 0) k_face<T, N, OTF><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
+      if (md.nB > 0) k_bface<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
+      return;
+    }
+    // common solution, gradient traces, then common inviscid + viscous fluxes
+    if (md.nF > 0) k_face_cq<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
+    if (md.nB > 0) k_bface_cq<T, N><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
+    if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
+    constexpr int EPBv = VisCfg<N>::EPB;
+    k_grad_trace<T, N, OTF><<<(md.E + EPBv - 1) / EPBv, VisCfg<N>::THREADS, 0, s>>>(md, (const T *)q.hi);
+    if (md.nF > 0) k_face_visc<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
+    if (md.nB > 0) k_bface_visc<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
   }
 
   void mortars(const MeshDev &md, cudaStream_t s) override {
     if (md.nL > 0) {
-      constexpr int MPB = MortCfg<N>::MPB;
-      k_mortar_flux<T, N><<<(md.nM + MPB - 1) / MPB, MortCfg<N>::THREADS, 0, s>>>(md);
-      const int n = (md.nL + md.nR) * N;
-      k_mortar_gather<T, N><<<(n + 127) / 128, 128, 0, s>>>(md);
+      mortar_pass<MORTAR_RUSANOV, GATHER_FLUX>(md, s);
+      if (md.viscous) mortar_pass<MORTAR_AVG_FV, GATHER_FLUX_ADD>(md, s);
     }
   }
 
@@ -1265,6 +1347,17 @@ struct EngineImpl : Engine {
               double dt, int mode, cudaStream_t s) override {
     using C = VolCfg<T, N, OTF>;
     const int ntiles = (md.E + C::EPB - 1) / C::EPB;
+    if (md.viscous) {
+      constexpr int EPBv = VisCfg<N>::EPB;
+      const int grid = (md.E + EPBv - 1) / EPBv;
+      if (mode == MODE_RESIDUAL)
+        k_volume_visc<T, N, MODE_RESIDUAL, OTF><<<grid, VisCfg<N>::THREADS, 0, s>>>(md, in, base, out, R, alpha,
+                                                                                    beta, dt);
+      else
+        k_volume_visc<T, N, MODE_RK, OTF><<<grid, VisCfg<N>::THREADS, 0, s>>>(md, in, base, out, R, alpha, beta,
+                                                                              dt);
+      return;
+    }
     if (mode == MODE_RESIDUAL)
       k_volume<T, N, MODE_RESIDUAL, OTF><<<std::min(ntiles, grid_res), C::THREADS, C::SMEM, s>>>(
           md, in, base, out, R, alpha, beta, dt, ntiles);

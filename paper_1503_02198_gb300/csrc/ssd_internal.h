@@ -78,6 +78,7 @@ struct MeshDev {
   void *geo;              // T [nTab][G] metric tables (see ssd_engine.cuh)
   void *egeo;             // T [E][8] bilinear record x0, y0, e1, e3, d of each cell
   void *TR, *CF;          // T [E][4][4][N] face traces and common fluxes
+  void *CQ, *GTR;         // viscous: T [E][4][4][N] common solution, [E][4][8][N] gradient traces
   void *fgeo;             // T [nF][5][N] conforming-face geometry at t = 0: unit normal
                           // (x, y) out of side A, sigma_A |S_A|, sigma_B |S_B|, V_g . n
   DevClock *clk;
@@ -115,11 +116,12 @@ struct Engine {
   // doubles: nL + (nL + nR) + 1)
   virtual void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                                 cudaStream_t s) = 0;
-  virtual void faces(const MeshDev &md, cudaStream_t s) = 0;
+  // q: the stage's state (the viscous chain needs its gradients)
+  virtual void faces(const MeshDev &md, StatePtr q, cudaStream_t s) = 0;
   virtual void mortars(const MeshDev &md, cudaStream_t s) = 0;
-  void couple(const MeshDev &md, double c, double dt, cudaStream_t s) {
+  void couple(const MeshDev &md, StatePtr q, double c, double dt, cudaStream_t s) {
     clock_merge(md, c, dt, s);
-    faces(md, s);
+    faces(md, q, s);
     mortars(md, s);
   }
   // divergence; MODE_RESIDUAL writes R (FP64), MODE_RK writes the stage

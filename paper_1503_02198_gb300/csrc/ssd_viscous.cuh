@@ -1,0 +1,464 @@
+// ssd_viscous.cuh -- viscous chain of the sliding-mesh SD residual (Sec. 2.1
+// viscous fluxes; Sec. 3.1 common solution / common viscous flux on cell
+// faces; Sec. 3.2 viscous mortar procedure).  Included by ssd_engine.cuh.
+//
+// Per stage, after the stage clock and mortar merge:
+//   k_face_cq / k_bface_cq     common solution Q_c on conforming faces (average)
+//                              and walls (wall state)
+//   k_mortar_flux<MORTAR_AVG_Q> + gather   Q_c on the interface: both sides
+//                              projected to the mortars, averaged, projected back
+//   k_grad_trace               gradients of the conservative variables at the
+//                              SPs (derivative of the degree-N polynomial through
+//                              the FP values with Q_c at the end FPs, chain rule
+//                              with the SP metrics), interpolated to the faces
+//   k_face_visc / k_bface_visc Rusanov + average of both sides' viscous normal
+//                              flux evaluated with Q_c (walls: wall state,
+//                              interior gradient)
+//   k_mortar_flux<MORTAR_RUSANOV> + gather, then <MORTAR_AVG_FV> + gather-add:
+//                              inviscid mortar flux, then the viscous normal flux
+//                              of both sides projected, averaged, projected back
+//   k_volume_visc              inviscid + viscous fluxes at interior FPs,
+//                              divergence, Runge-Kutta update, traces
+#pragma once
+
+namespace ssd {
+
+// viscous fluxes of Sec. 2.1 (with the paper's leading minus sign) from Q and
+// the physical gradients of the conservative variables
+template <typename T>
+__device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *qy, const MeshDev &md, T *F, T *G) {
+  const T gm1 = (T)(md.gamma - 1.0), Rg = (T)md.Rgas, mu = (T)md.mu;
+  const T kc = (T)(md.mu * md.gamma * md.Rgas / ((md.gamma - 1.0) * md.prandtl));
+  const T ir = T(1) / q[0];
+  const T u = q[1] * ir, v = q[2] * ir;
+  const T ux = (qx[1] - u * qx[0]) * ir, uy = (qy[1] - u * qy[0]) * ir;
+  const T vx = (qx[2] - v * qx[0]) * ir, vy = (qy[2] - v * qy[0]) * ir;
+  const T ke = T(0.5) * (u * u + v * v);
+  const T p = gm1 * (q[3] - ke * q[0]);
+  const T Tt = p * ir / Rg;
+  const T px = gm1 * (qx[3] - (u * qx[1] + v * qx[2] - ke * qx[0]));
+  const T py = gm1 * (qy[3] - (u * qy[1] + v * qy[2] - ke * qy[0]));
+  const T Tx = (px - Rg * Tt * qx[0]) * ir / Rg, Ty = (py - Rg * Tt * qy[0]) * ir / Rg;
+  const T lam = T(-2) / T(3) * mu, dv = ux + vy;
+  const T txx = T(2) * mu * ux + lam * dv, tyy = T(2) * mu * vy + lam * dv, txy = mu * (uy + vx);
+  F[0] = 0;
+  F[1] = -txx;
+  F[2] = -txy;
+  F[3] = -(u * txx + v * txy + kc * Tx);
+  G[0] = 0;
+  G[1] = -txy;
+  G[2] = -tyy;
+  G[3] = -(u * txy + v * tyy + kc * Ty);
+}
+
+// wall state of an isothermal no-slip wall: interior pressure, wall
+// temperature, wall velocity (uw, vw)
+template <typename T>
+__device__ __forceinline__ void wall_state(const T *q, T uw, T vw, const MeshDev &md, T *qw) {
+  const T gm1 = (T)(md.gamma - 1.0);
+  const T p = pressure_of(q, gm1);
+  const T rho = p / (T)(md.Rgas * md.T_wall);
+  qw[0] = rho;
+  qw[1] = rho * uw;
+  qw[2] = rho * vw;
+  qw[3] = p / gm1 + T(0.5) * rho * (uw * uw + vw * vw);
+}
+
+// wall velocity at boundary point (b, j): the grid velocity of a rotating wall
+template <int N>
+__device__ __forceinline__ void wall_velocity(const MeshDev &md, int b, int j, double &uw, double &vw) {
+  uw = vw = 0.0;
+  const int e = md.bfaces[b].x >> 2;
+  if (md.eflag[e] & 1) {
+    const double c = md.clk->c, s = md.clk->s;
+    const double x0 = md.bxy[((size_t)b * N + j) * 2], y0 = md.bxy[((size_t)b * N + j) * 2 + 1];
+    uw = -md.omega * (s * x0 + c * y0);
+    vw = md.omega * (c * x0 - s * y0);
+  }
+}
+
+// ---- common solution -------------------------------------------------------
+
+template <typename T, int N>
+__global__ void k_face_cq(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= md.nF * N) return;
+  const int fi = t / N, j = t - fi * N;
+  const int4 fc = md.faces[fi];
+  const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
+  const T *TR = (const T *)md.TR;
+  T *CQ = (T *)md.CQ;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const T c = T(0.5) * (TR[((size_t)efA * 4 + v) * N + j] + TR[((size_t)efB * 4 + v) * N + jB]);
+    CQ[((size_t)efA * 4 + v) * N + j] = c;
+    CQ[((size_t)efB * 4 + v) * N + jB] = c;
+  }
+}
+
+template <typename T, int N>
+__global__ void k_bface_cq(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= md.nB * N) return;
+  const int b = t / N, j = t - b * N;
+  const int ef = md.bfaces[b].x;
+  const T *TR = (const T *)md.TR;
+  T q[4], qw[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) q[v] = TR[((size_t)ef * 4 + v) * N + j];
+  double uw, vw;
+  wall_velocity<N>(md, b, j, uw, vw);
+  wall_state(q, (T)uw, (T)vw, md, qw);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) ((T *)md.CQ)[((size_t)ef * 4 + v) * N + j] = qw[v];
+}
+
+// ---- gradients ---------------------------------------------------------------
+
+template <int N>
+struct VisCfg {
+  static constexpr int EPB = N <= 4 ? 8 : 4;
+  static constexpr int THREADS = EPB * 2 * N;
+};
+
+// Gradients at the SPs of a tile (thread per SP line, then per SP): on
+// return sDx / sDe hold Q_x / Q_y.  The caller synchronises before and after.
+template <typename T, int N, bool OTF>
+__device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne, T (*sQ)[4][N * N],
+                                               T (*sCQ)[16 * N], T (*sDx)[4][N * N], T (*sDe)[4][N * N], T cth,
+                                               T sth) {
+  constexpr int NN = N * N, NT = VisCfg<N>::THREADS;
+  const VolBasis<T, N> &B = cVB<T, N>;
+  const int le = threadIdx.x / (2 * N);
+  const int r = threadIdx.x - le * 2 * N;
+  const int d = r / N, m = r - d * N;
+  if (le < ne) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      T val[N + 1];
+      val[0] = sCQ[le][((d == 0 ? 3 : 0) * 4 + v) * N + m];
+      val[N] = sCQ[le][((d == 0 ? 1 : 2) * 4 + v) * N + m];
+#pragma unroll
+      for (int i = 1; i < N; ++i) {
+        T acc = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc += (d == 0 ? sQ[le][v][m * N + k] : sQ[le][v][k * N + m]) * B.Hf[i * N + k];
+        val[i] = acc;
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        T acc = 0;
+#pragma unroll
+        for (int i = 0; i <= N; ++i) acc += B.Dm[k * (N + 1) + i] * val[i];
+        if (d == 0) sDx[le][v][m * N + k] = acc;   // d/dxi at SP (k, m)
+        else sDe[le][v][k * N + m] = acc;          // d/deta at SP (m, k)
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
+    const int l2 = idx / NN, sp = idx - l2 * NN;
+    ElemGeo<T, N, OTF> G;
+    G.load(md, e0 + l2, cth, sth);
+    T xix, xiy, etx, ety;
+    G.sp_grad(sp % N, sp / N, xix, xiy, etx, ety);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const T a = sDx[l2][v][sp], b = sDe[l2][v][sp];
+      sDx[l2][v][sp] = xix * a + etx * b;
+      sDe[l2][v][sp] = xiy * a + ety * b;
+    }
+  }
+}
+
+// gradient traces GTR [E][4 faces][8][N]: component v = dQ_v/dx, 4 + v = dQ_v/dy
+template <typename T, int N, bool OTF>
+__global__ void __launch_bounds__(VisCfg<N>::THREADS) k_grad_trace(MeshDev md, const T *__restrict__ Q) {
+  constexpr int EPB = VisCfg<N>::EPB, NT = VisCfg<N>::THREADS, NN = N * N;
+  __shared__ T sQ[EPB][4][NN];
+  __shared__ T sCQ[EPB][16 * N];
+  __shared__ T sDx[EPB][4][NN];
+  __shared__ T sDe[EPB][4][NN];
+  const int e0 = blockIdx.x * EPB;
+  const int ne = min(EPB, md.E - e0);
+  for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) (&sQ[0][0][0])[i] = Q[(size_t)e0 * 4 * NN + i];
+  for (int i = threadIdx.x; i < ne * 16 * N; i += NT) (&sCQ[0][0])[i] = ((const T *)md.CQ)[(size_t)e0 * 16 * N + i];
+  __syncthreads();
+  tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, (T)md.clk->c, (T)md.clk->s);
+  __syncthreads();
+  const VolBasis<T, N> &B = cVB<T, N>;
+  const int le = threadIdx.x / (2 * N);
+  const int r = threadIdx.x - le * 2 * N;
+  const int d = r / N, m = r - d * N;
+  if (le < ne) {
+    T *g = (T *)md.GTR + (size_t)(e0 + le) * 32 * N;
+    const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int v = c & 3;
+      T a0 = 0, a1 = 0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int sp = d == 0 ? m * N + k : k * N + m;
+        const T val = c < 4 ? sDx[le][v][sp] : sDe[le][v][sp];
+        a0 += val * B.H0[k];
+        a1 += val * B.H1[k];
+      }
+      g[(fa * 8 + c) * N + m] = a0;
+      g[(fb * 8 + c) * N + m] = a1;
+    }
+  }
+}
+
+// ---- common fluxes -------------------------------------------------------------
+
+// normal viscous flux F_vis . n from Q and the 8 gradient components
+template <typename T>
+__device__ __forceinline__ void viscous_normal(const T *q, const T *g8, T nx, T ny, const MeshDev &md, T *fn) {
+  T F[4], G[4];
+  viscous_flux(q, g8, g8 + 4, md, F, G);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) fn[v] = F[v] * nx + G[v] * ny;
+}
+
+template <typename T, int N>
+__global__ void k_face_visc(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= md.nF * N) return;
+  const int fi = t / N, j = t - fi * N;
+  const int4 fc = md.faces[fi];
+  const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
+  const T *TR = (const T *)md.TR, *CQ = (const T *)md.CQ, *GT = (const T *)md.GTR;
+  T qA[4], qB[4], qc[4], gA[8], gB[8];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    qA[v] = TR[((size_t)efA * 4 + v) * N + j];
+    qB[v] = TR[((size_t)efB * 4 + v) * N + jB];
+    qc[v] = CQ[((size_t)efA * 4 + v) * N + j];
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    gA[c] = GT[((size_t)efA * 8 + c) * N + j];
+    gB[c] = GT[((size_t)efB * 8 + c) * N + jB];
+  }
+  const T *g = (const T *)md.fgeo + (size_t)fi * 5 * N;
+  T nx = g[j], ny = g[N + j];
+  const T sA = g[2 * N + j], sB = g[3 * N + j], vgn = g[4 * N + j];
+  if (md.eflag[efA >> 2] & 1) {
+    const T c = (T)md.clk->c, s = (T)md.clk->s;
+    const T rx = c * nx - s * ny, ry = s * nx + c * ny;
+    nx = rx;
+    ny = ry;
+  }
+  T Fn[4], va[4], vb[4];
+  rusanov(qA, qB, nx, ny, vgn, (T)md.gamma, Fn);
+  viscous_normal(qc, gA, nx, ny, md, va);
+  viscous_normal(qc, gB, nx, ny, md, vb);
+  T *CF = (T *)md.CF;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const T f = Fn[v] + T(0.5) * (va[v] + vb[v]);
+    CF[((size_t)efA * 4 + v) * N + j] = sA * f;
+    CF[((size_t)efB * 4 + v) * N + jB] = -sB * f;
+  }
+}
+
+template <typename T, int N, bool OTF>
+__global__ void k_bface_visc(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= md.nB * N) return;
+  const int b = t / N, j = t - b * N;
+  const int ef = md.bfaces[b].x, e = ef >> 2, f = ef & 3;
+  const T *TR = (const T *)md.TR, *GT = (const T *)md.GTR;
+  T q[4], qg[4], qw[4], g8[8];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) q[v] = TR[((size_t)ef * 4 + v) * N + j];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) g8[c] = GT[((size_t)ef * 8 + c) * N + j];
+  ElemGeo<T, N, OTF> G;
+  G.load(md, e, (T)md.clk->c, (T)md.clk->s);
+  T ax, ay, ag;
+  G.face(f, j, ax, ay, ag);
+  double uw, vw;
+  wall_velocity<N>(md, b, j, uw, vw);
+  const T S = sqrt(ax * ax + ay * ay), sg = (T)face_sigma(f);
+  const T nx = sg * ax / S, ny = sg * ay / S, vgn = sg * ag / S;
+  const T gm1 = (T)(md.gamma - 1.0);
+  const T p = pressure_of(q, gm1);
+  const T rho = p / (T)(md.Rgas * md.T_wall);
+  const T gu = T(2) * (T)uw - q[1] / q[0], gv = T(2) * (T)vw - q[2] / q[0];
+  qg[0] = rho;
+  qg[1] = rho * gu;
+  qg[2] = rho * gv;
+  qg[3] = p / gm1 + T(0.5) * rho * (gu * gu + gv * gv);
+  T Fn[4], fv[4];
+  rusanov(q, qg, nx, ny, vgn, (T)md.gamma, Fn);
+  wall_state(q, (T)uw, (T)vw, md, qw);
+  viscous_normal(qw, g8, nx, ny, md, fv);
+  T *CF = (T *)md.CF;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sg * S * (Fn[v] + fv[v]);
+}
+
+// ---- volume ------------------------------------------------------------------
+
+template <typename T, int N, int MODE, bool OTF>
+__global__ void __launch_bounds__(VisCfg<N>::THREADS)
+    k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, double alpha, double beta,
+                  double dt) {
+  constexpr int EPB = VisCfg<N>::EPB, NT = VisCfg<N>::THREADS, NN = N * N;
+  constexpr bool FF = std::is_same<T, float>::value;
+  __shared__ T sQ[EPB][4][NN];
+  __shared__ T sCQ[EPB][16 * N];
+  __shared__ T sCF[EPB][16 * N];
+  __shared__ T sDx[EPB][4][NN];
+  __shared__ T sDe[EPB][4][NN];
+  __shared__ T sRF[EPB][4][NN];
+  __shared__ T sRG[EPB][4][NN];
+  const VolBasis<T, N> &B = cVB<T, N>;
+  const int e0 = blockIdx.x * EPB;
+  const int ne = min(EPB, md.E - e0);
+  for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) (&sQ[0][0][0])[i] = ((const T *)in.hi)[(size_t)e0 * 4 * NN + i];
+  for (int i = threadIdx.x; i < ne * 16 * N; i += NT) {
+    (&sCQ[0][0])[i] = ((const T *)md.CQ)[(size_t)e0 * 16 * N + i];
+    (&sCF[0][0])[i] = ((const T *)md.CF)[(size_t)e0 * 16 * N + i];
+  }
+  __syncthreads();
+  const T cth = (T)md.clk->c, sth = (T)md.clk->s;
+  tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, cth, sth);
+  __syncthreads();
+  const T gm1 = (T)(md.gamma - 1.0);
+  const int le = threadIdx.x / (2 * N);
+  const int r = threadIdx.x - le * 2 * N;
+  const int d = r / N, m = r - d * N;
+  if (le < ne) {
+    ElemGeo<T, N, OTF> G;
+    G.load(md, e0 + le, cth, sth);
+    T acc[4][N];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v][k] = 0;
+#pragma unroll
+    for (int i = 0; i <= N; ++i) {
+      T f[4];
+      if (i == 0 || i == N) {
+        const int face = d == 0 ? (i == 0 ? 3 : 1) : (i == 0 ? 0 : 2);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) f[v] = sCF[le][(face * 4 + v) * N + m];
+      } else {
+        T qf[4], g8[8];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          T a = 0, bx = 0, by = 0;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const int sp = d == 0 ? m * N + k : k * N + m;
+            const T h = B.Hf[i * N + k];
+            a += sQ[le][v][sp] * h;
+            bx += sDx[le][v][sp] * h;
+            by += sDe[le][v][sp] * h;
+          }
+          qf[v] = a;
+          g8[v] = bx;
+          g8[4 + v] = by;
+        }
+        T vx, vy, vg;
+        if (d == 0) G.xi_fp(i, m, vx, vy, vg);
+        else G.eta_fp(m, i, vx, vy, vg);
+        const T p = pressure_of(qf, gm1);
+        normal_flux(qf, p, vx, vy, vg, f);
+        T Fv[4], Gv[4];
+        viscous_flux(qf, g8, g8 + 4, md, Fv, Gv);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) f[v] += vx * Fv[v] + vy * Gv[v];
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T w = B.Dm[k * (N + 1) + i];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v][k] += w * f[v];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        if (d == 0) sRF[le][v][m * N + k] = acc[v][k];
+        else sRG[le][v][k * N + m] = acc[v][k];
+      }
+  }
+  __syncthreads();
+  bool bad = false;
+  const T bdt = (T)(beta * dt), af = (T)alpha;
+  for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
+    const int l2 = idx / NN, sp = idx - l2 * NN;
+    ElemGeo<T, N, OTF> G;
+    G.load(md, e0 + l2, cth, sth);
+    const T iJ = G.inv_jac(sp % N, sp / N);
+    const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
+    if (MODE == MODE_RESIDUAL) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+    } else if (!FF) {
+      double qn[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+        double val = beta * ((double)sQ[l2][v][sp] + dt * R);
+        if (alpha != 0.0) val = alpha * ((const double *)base.hi)[gi + v * NN] + val;
+        qn[v] = val;
+      }
+      const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
+      bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        ((double *)out.hi)[gi + v * NN] = qn[v];
+        sQ[l2][v][sp] = (T)qn[v];
+      }
+    } else {
+      float hv[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const size_t ii = gi + v * NN;
+        const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+        const float h = (float)sQ[l2][v][sp], l = ((const float *)in.lo)[ii];
+        float inc = (float)bdt * R;
+        if (alpha != 0.0)
+          inc = fmaf((float)af, (((const float *)base.hi)[ii] - h) + (((const float *)base.lo)[ii] - l), inc);
+        float sum, err;
+        two_sum(h, inc, sum, err);
+        err += l;
+        const float H = sum + err;
+        ((float *)out.hi)[ii] = H;
+        ((float *)out.lo)[ii] = err - (H - sum);
+        hv[v] = H;
+      }
+      const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
+      bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sQ[l2][v][sp] = (T)hv[v];
+    }
+  }
+  if (MODE == MODE_RK) {
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&md.clk->flags, 1);
+    if (le < ne) {
+      T *tr = (T *)md.TR + (size_t)(e0 + le) * 16 * N;
+      const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        T a0 = 0, a1 = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const T qk = d == 0 ? sQ[le][v][m * N + k] : sQ[le][v][k * N + m];
+          a0 += qk * B.H0[k];
+          a1 += qk * B.H1[k];
+        }
+        tr[(fa * 4 + v) * N + m] = a0;
+        tr[(fb * 4 + v) * N + m] = a1;
+      }
+    }
+  }
+}
+
+}  // namespace ssd
