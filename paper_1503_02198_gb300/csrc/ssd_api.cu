@@ -586,6 +586,8 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
   if (!rc) {
     MeshDev &md = h->md;
     md.omega = prm->omega;
+    md.omega_f = (float)prm->omega;
+    md.gamma_f = (float)prm->gamma;
     md.gamma = prm->gamma;
     md.Rgas = prm->Rgas;
     md.mu = prm->mu;

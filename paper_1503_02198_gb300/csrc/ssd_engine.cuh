@@ -75,6 +75,14 @@ struct GeoLayout {
   static constexpr int G = 6 * NF + 5 * N * N;
 };
 
+// a parameter in the compute type, taken from its float copy on the FP32
+// path so that no FP64 instruction runs there
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f) {
+  if constexpr (std::is_same<T, float>::value) return f;
+  else return (T)d;
+}
+
 // face f of an element: sign sigma_f with F~_end = sigma_f |S| F.n_out
 __device__ __forceinline__ double face_sigma(int f) { return (f == 1 || f == 2) ? 1.0 : -1.0; }
 
@@ -275,7 +283,7 @@ struct ElemGeo {
     const bool rot = f & 1;
     c = rot ? cth : T(1);
     s = rot ? sth : T(0);
-    om = rot ? (T)md.omega : T(0);
+    om = rot ? pick<T>(md.omega, md.omega_f) : T(0);
     const int ti = (f >> 1) - 1;
     if (OTF && ti < 0) {
       tab = nullptr;
@@ -439,6 +447,8 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_
     sincos(th, &sn, &cs);
     k->c = cs;
     k->s = sn;
+    k->cf = (float)cs;
+    k->sf = (float)sn;
     s_th2 = th2;
     s_k0 = 0;
   }
@@ -561,13 +571,13 @@ __global__ void k_face(MeshDev md) {
   T nx = g[j], ny = g[N + j];
   const T sA = g[2 * N + j], sB = g[3 * N + j], vgn = g[4 * N + j];
   if (md.eflag[efA >> 2] & 1) {
-    const T c = (T)md.clk->c, s = (T)md.clk->s;
+    const T c = pick<T>(md.clk->c, md.clk->cf), s = pick<T>(md.clk->s, md.clk->sf);
     const T rx = c * nx - s * ny, ry = s * nx + c * ny;
     nx = rx;
     ny = ry;
   }
   T Fn[4];
-  rusanov(qA, qB, nx, ny, vgn, (T)md.gamma, Fn);
+  rusanov(qA, qB, nx, ny, vgn, pick<T>(md.gamma, md.gamma_f), Fn);
   T *CF = (T *)md.CF;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -958,7 +968,7 @@ struct VolCfg {
 template <typename T, int N, int MODE, bool OTF>
 __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
     k_volume(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, double alpha, double beta,
-             double dt, int ntiles) {
+             double dt, int ntiles, float af, float bdt) {
   using C = VolCfg<T, N, OTF>;
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
   constexpr bool FF = C::FF;
@@ -970,10 +980,8 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
   const VolBasis<T, N> &B = cVB<T, N>;
   const bool use_base = MODE == MODE_RK && alpha != 0.0;
   const uint32_t tx_bytes = C::QHI + C::QLO + C::CFB + C::EGB + C::EFB + (use_base ? C::QHI + C::QLO : 0);
-  const T cth = (T)md.clk->c, sth = (T)md.clk->s;
-  const T gm1 = (T)(md.gamma - 1.0);
-  // stage constants, converted once per thread
-  const T bdt = (T)(beta * dt), af = (T)alpha;
+  const T cth = pick<T>(md.clk->c, md.clk->cf), sth = pick<T>(md.clk->s, md.clk->sf);
+  const T gm1 = pick<T>(md.gamma, md.gamma_f) - T(1);
 
   auto issue = [&](int tl, int st) {
     unsigned char *sb = smem + st * C::STAGE;
@@ -1126,8 +1134,8 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
         for (int v = 0; v < 4; ++v) {
           const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
           const float h = (float)sQ[l2][v][sp], l = sKL[l2][v][sp];
-          float inc = (float)bdt * R;
-          if (use_base) inc = fmaf((float)af, (sNH[l2][v][sp] - h) + (sNL[l2][v][sp] - l), inc);
+          float inc = bdt * R;
+          if (use_base) inc = fmaf(af, (sNH[l2][v][sp] - h) + (sNL[l2][v][sp] - l), inc);
           float sum, err;
           two_sum(h, inc, sum, err);
           err += l;
@@ -1360,10 +1368,10 @@ struct EngineImpl : Engine {
     }
     if (mode == MODE_RESIDUAL)
       k_volume<T, N, MODE_RESIDUAL, OTF><<<std::min(ntiles, grid_res), C::THREADS, C::SMEM, s>>>(
-          md, in, base, out, R, alpha, beta, dt, ntiles);
+          md, in, base, out, R, alpha, beta, dt, ntiles, (float)alpha, (float)(beta * dt));
     else
-      k_volume<T, N, MODE_RK, OTF><<<std::min(ntiles, grid_rk), C::THREADS, C::SMEM, s>>>(md, in, base, out, R, alpha,
-                                                                                         beta, dt, ntiles);
+      k_volume<T, N, MODE_RK, OTF><<<std::min(ntiles, grid_rk), C::THREADS, C::SMEM, s>>>(
+          md, in, base, out, R, alpha, beta, dt, ntiles, (float)alpha, (float)(beta * dt));
   }
 
   int tile_elems() const override { return VolCfg<T, N, OTF>::EPB; }

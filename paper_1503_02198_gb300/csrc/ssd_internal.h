@@ -17,6 +17,7 @@ struct DevClock {
   double theta;    // omega * t_stage
   double theta2;   // theta reduced to [0, 2 pi)
   double c, s;     // cos(theta), sin(theta)
+  float cf, sf;    // the same rounded to float (FP32 path)
   int flags;       // bit 0: non-physical state; bit 1: mesh geometry error; bit 2: a bounded device wait gave up
   int pad;
 };
@@ -83,6 +84,7 @@ struct MeshDev {
                           // (x, y) out of side A, sigma_A |S_A|, sigma_B |S_B|, V_g . n
   DevClock *clk;
   double omega, gamma, Rgas, mu, prandtl, T_wall, r_interface;
+  float omega_f, gamma_f;  // the same rounded to float (FP32 path)
   int viscous;
 };
 
