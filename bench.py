@@ -160,6 +160,22 @@ def cpu_oracle_rate(steps, warmup, dt, budget_s=None):
     return rate, el, E
 
 
+def aggregate_ranks(ms, work):
+    """Replicas: every rank advances its own copy of the workload.  Returns
+    (max elapsed ms over ranks, total work over ranks); plain values on one
+    process, all-reduces over torch.distributed when a group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(work)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -179,6 +195,49 @@ def run_reference(args):
     return 0
 
 
+def run_batched(ssd, ncases, steps):
+    """Batched form: a seeded mix of independent cases (rotor and Couette
+    families, 1k-8k cells, p = 2..5, omega in [0.1, 1], FP32 path) advanced by
+    one CUDA-graph launch per step, against the same cases stepped one after
+    another with their own graphs.  Wall-clock time around synchronised
+    calls."""
+    from ssd_inputs.workloads import batch_cases
+    cases = batch_cases(ncases)
+    b = ssd.Batch([c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases],
+                  precision=ssd.SD_PREC_FP32, tune_dt=1e-5)
+    states = []
+    for k, (name, mesh, p, prm, dt) in enumerate(cases):
+        if prm.viscous:
+            q = b.cases[k].state_from(lambda x, y, prm=prm: fields.uniform(x, y, rho=1.0, p=prm.Rgas))
+        else:
+            q = b.cases[k].state_from(lambda x, y: fields.isentropic_vortex(x, y))
+        states.append(q)
+        b.cases[k].sd_set_state(q)
+    dts = [c[4] for c in cases]
+    dofs = sum(c.n_dofs for c in b.cases)
+    b.sd_batch_step(dts, 5)
+    b.sd_batch_sync()
+    t0 = time.perf_counter()
+    b.sd_batch_step(dts, steps)
+    b.sd_batch_sync()
+    el = time.perf_counter() - t0
+    # the same cases, one after another, each with its own graph
+    for k, c in enumerate(b.cases):
+        c.sd_set_state(states[k])
+    t1 = time.perf_counter()
+    for k, c in enumerate(b.cases):
+        c.sd_step(dts[k], steps)
+    for c in b.cases:
+        c.sd_sync()
+    el_sep = time.perf_counter() - t1
+    b.close()
+    return {"value": dofs * steps / el, "unit": "DOF-updates/s", "cases": len(cases), "dofs": dofs,
+            "cells": int(sum(len(c[1]["elem_nodes"]) for c in cases)), "steps": steps,
+            "ms_per_step": el / steps * 1e3, "separate_ms_per_step": el_sep / steps * 1e3,
+            "speedup_vs_separate": el_sep / el, "precision": "f32", "autotuned": True,
+            "timing": "wall clock around synchronised calls"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,6 +250,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-cases", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=50)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -242,12 +303,8 @@ def main():
     solver.sd_sync()
     barrier()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * dofs * args.steps / (ms * 1e-3)
+    ms, work = aggregate_ranks(e0.elapsed_time(e1), dofs * args.steps)
+    value = work / (ms * 1e-3)
 
     # accuracy at the final time: density L2 error against the exact vortex
     t_end = solver.sd_get_time()
@@ -315,14 +372,12 @@ def main():
         solver.sd_step(dt, 1)
         solver.sd_get_state(pin_out)
     solver.sd_sync()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s, e2e_work = aggregate_ranks(time.perf_counter() - t0, dofs * args.e2e_steps)
     state_bytes = dofs * 8
-    e2e = {"value": world * dofs * args.e2e_steps / e2e_s, "unit": "DOF-updates/s",
+    e2e = {"value": e2e_work / e2e_s if e2e_s > 0 else 0.0, "unit": "DOF-updates/s",
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
+
+    batched = run_batched(ssd, args.batch_cases, args.batch_steps) if args.batch_cases > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -342,6 +397,7 @@ def main():
                        "parallelism": f"replicas x{world}", "description": w.description},
             "l2_error_rho_vs_exact": l2_rho, "t_final": t_end,
             "fp64": fp64,
+            "batched": batched,
             "kernel_ms": prof,
             "interface_fraction": prof["mortar"] * 3 / prof["step"],
             "fp32_fma_peak_tflops": fp32_peak,

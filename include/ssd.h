@@ -142,6 +142,35 @@ int sd_sync(sd_handle *h);
 /* Physical coordinates of the solution points at time t, [E][N][N][2]. */
 int sd_sp_coords(sd_handle *h, double t, double *xy, int on_device);
 
+/* ---- batched form: many independent cases, one CUDA-graph launch per step ----
+ * Each case has its own mesh, polynomial degree and parameters (its own
+ * rotation rate).  sd_batch_step advances every case by nsteps steps with one
+ * graph launch per step; the graph holds one branch per case, so the small
+ * kernels of different cases run concurrently.  With tune_dt > 0 the batch
+ * autotunes each case's launch shapes (persistent volume CTAs per SM, face
+ * kernel block size) at creation by timing a few steps of size tune_dt from
+ * a uniform state; the state and time are reset to zero afterwards. */
+typedef struct sd_batch sd_batch;
+
+int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_params *prm, double tune_dt,
+                    sd_batch **out);
+int sd_batch_destroy(sd_batch *b);
+int sd_batch_size(const sd_batch *b);
+
+/* Handle of case i (owned by the batch): use it with sd_set_state,
+ * sd_get_state, sd_set_time, sd_get_time, sd_residual; work queued on it is
+ * ordered after the batch's earlier steps.  NULL if i is out of range. */
+sd_handle *sd_batch_case(sd_batch *b, int i);
+
+/* Advance every case by nsteps steps; dt[i] is case i's step (the graph is
+ * captured again when a dt changes).  Asynchronous; errors of any case are
+ * reported by sd_batch_sync. */
+int sd_batch_step(sd_batch *b, const double *dt, int nsteps);
+
+/* Wait for the batch; returns the first case error (SD_ERR_NONPHYSICAL ...). */
+int sd_batch_sync(sd_batch *b);
+const char *sd_batch_last_error(const sd_batch *b);
+
 /* Measurement aid (the paper reports wall time split into interface and
  * total time, Tables 3-10): runs reps steps outside the CUDA graph with CUDA
  * events around each launch group on the handle's stream and writes the mean

@@ -86,6 +86,16 @@ def lib():
         L.sd_profile_step.argtypes = [vp, ctypes.c_double, ctypes.c_int, _c_dbl_p]
         L.sd_fma_peak.argtypes = [vp, ctypes.c_int, _c_dbl_p]
         L.sd_residual_noalloc.argtypes = [vp, vp, ctypes.c_int]
+        L.sd_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.POINTER(sd_mesh)), _c_int_p,
+                                      ctypes.POINTER(sd_params), ctypes.c_double, ctypes.POINTER(vp)]
+        L.sd_batch_destroy.argtypes = [vp]
+        L.sd_batch_size.argtypes = [vp]
+        L.sd_batch_case.argtypes = [vp, ctypes.c_int]
+        L.sd_batch_case.restype = vp
+        L.sd_batch_step.argtypes = [vp, _c_dbl_p, ctypes.c_int]
+        L.sd_batch_sync.argtypes = [vp]
+        L.sd_batch_last_error.argtypes = [vp]
+        L.sd_batch_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -102,55 +112,75 @@ def _ptr(a, dtype):
     return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
 
 
+def _mesh_struct(mesh: dict, keep: list) -> sd_mesh:
+    def arr(x, dt):
+        a = np.ascontiguousarray(x, dtype=dt)
+        keep.append(a)
+        return a
+
+    xy = arr(mesh["xy"], np.float64)
+    en = arr(mesh["elem_nodes"], np.int32)
+    zone = arr(mesh["elem_zone"], np.int32)
+    arc = arr(mesh["edge_arc"], np.int32)
+    bf = arr(mesh["bfaces"], np.int32)
+    pf = arr(mesh["pfaces"], np.int32)
+    Lf = arr(mesh["ifaces_L"], np.int32)
+    Rf = arr(mesh["ifaces_R"], np.int32)
+
+    def ip(a):
+        return a.ctypes.data_as(_c_int_p)
+
+    return sd_mesh(len(xy), xy.ctypes.data_as(_c_dbl_p), len(en), ip(en), ip(zone), ip(arc), len(bf), ip(bf),
+                   len(pf), ip(pf), len(Lf), ip(Lf), len(Rf), ip(Rf),
+                   (ctypes.c_double * 2)(float(mesh["center"][0]), float(mesh["center"][1])),
+                   float(mesh["r_interface"]))
+
+
+def _params_struct(params, precision, stream=None) -> sd_params:
+    return sd_params(params.gamma, params.Rgas, params.mu, params.prandtl, params.omega, params.T_wall,
+                     int(params.viscous), int(precision), ctypes.c_void_p(stream) if stream else None)
+
+
 class Solver:
-    """Owns one sd_handle; methods mirror the C ABI names."""
+    """Owns one sd_handle (or wraps a batch's case); methods mirror the C ABI names."""
+
+    @classmethod
+    def _wrap(cls, handle, owner):
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p(handle)
+        self._owner = owner
+        self._owned = False
+        self._init_sizes()
+        return self
+
+    def _init_sizes(self):
+        E, N, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        lib().sd_info(self._h, ctypes.byref(E), ctypes.byref(N), ctypes.byref(n))
+        self.E, self.N, self.n_dofs = E.value, N.value, n.value
+        self.p = self.N - 1
+        self.shape = (self.E, 4, self.N, self.N)
 
     def __init__(self, mesh: dict, p: int, params, precision: int = SD_PREC_FP64, stream=None):
         L = lib()
         self._keep = []
-
-        def arr(x, dt):
-            a = np.ascontiguousarray(x, dtype=dt)
-            self._keep.append(a)
-            return a
-
-        xy = arr(mesh["xy"], np.float64)
-        en = arr(mesh["elem_nodes"], np.int32)
-        zone = arr(mesh["elem_zone"], np.int32)
-        arc = arr(mesh["edge_arc"], np.int32)
-        bf = arr(mesh["bfaces"], np.int32)
-        pf = arr(mesh["pfaces"], np.int32)
-        Lf = arr(mesh["ifaces_L"], np.int32)
-        Rf = arr(mesh["ifaces_R"], np.int32)
-
-        def ip(a):
-            return a.ctypes.data_as(_c_int_p)
-
-        m = sd_mesh(len(xy), xy.ctypes.data_as(_c_dbl_p), len(en), ip(en), ip(zone), ip(arc), len(bf), ip(bf),
-                    len(pf), ip(pf), len(Lf), ip(Lf), len(Rf), ip(Rf),
-                    (ctypes.c_double * 2)(float(mesh["center"][0]), float(mesh["center"][1])),
-                    float(mesh["r_interface"]))
-        prm = sd_params(params.gamma, params.Rgas, params.mu, params.prandtl, params.omega, params.T_wall,
-                        int(params.viscous), int(precision), ctypes.c_void_p(stream) if stream else None)
+        self._owned = True
+        m = _mesh_struct(mesh, self._keep)
+        prm = _params_struct(params, precision, stream)
         h = ctypes.c_void_p()
         rc = L.sd_create(ctypes.byref(m), p, ctypes.byref(prm), ctypes.byref(h))
         if rc != SD_OK:
             raise SSDError(rc, L.sd_create_error().decode())
         self._h = h
-        self.p, self.N = p, p + 1
-        E, N, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
-        L.sd_info(h, ctypes.byref(E), ctypes.byref(N), ctypes.byref(n))
-        self.E, self.n_dofs = E.value, n.value
-        self.shape = (self.E, 4, self.N, self.N)
+        self._init_sizes()
 
     def _check(self, rc):
         if rc != SD_OK:
             raise SSDError(rc, lib().sd_last_error(self._h).decode())
 
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and getattr(self, "_owned", True):
             lib().sd_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         self.close()
@@ -217,3 +247,45 @@ class Solver:
     def state_from(self, field_fn, t=0.0):
         xy = self.sd_sp_coords(t)
         return np.ascontiguousarray(np.moveaxis(field_fn(xy[..., 0], xy[..., 1]), -1, 1))
+
+
+class Batch:
+    """Owns one sd_batch: independent cases (mesh, p, params each) advanced
+    together with one CUDA-graph launch per step."""
+
+    def __init__(self, meshes, ps, params, precision=SD_PREC_FP64, tune_dt=0.0):
+        L = lib()
+        n = len(meshes)
+        self._keep = []
+        structs = [_mesh_struct(m, self._keep) for m in meshes]
+        self._keep.append(structs)
+        mptrs = (ctypes.POINTER(sd_mesh) * n)(*[ctypes.pointer(x) for x in structs])
+        parr = (ctypes.c_int * n)(*[int(p) for p in ps])
+        prms = (sd_params * n)(*[_params_struct(pr, precision) for pr in params])
+        b = ctypes.c_void_p()
+        rc = L.sd_batch_create(n, mptrs, parr, prms, float(tune_dt), ctypes.byref(b))
+        if rc != SD_OK:
+            raise SSDError(rc, L.sd_create_error().decode())
+        self._b = b
+        self.cases = [Solver._wrap(L.sd_batch_case(b, i), self) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            for c in self.cases:
+                c._h = None
+            lib().sd_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, rc):
+        if rc != SD_OK:
+            raise SSDError(rc, lib().sd_batch_last_error(self._b).decode())
+
+    def sd_batch_step(self, dts, nsteps=1):
+        arr = (ctypes.c_double * len(self.cases))(*[float(d) for d in dts])
+        self._check(lib().sd_batch_step(self._b, arr, int(nsteps)))
+
+    def sd_batch_sync(self):
+        self._check(lib().sd_batch_sync(self._b))

@@ -860,6 +860,235 @@ int sd_fma_peak(sd_handle *h, int precision, double *tflops) {
 }
 
 // ---------------------------------------------------------------------------
+// batched form: independent cases advanced by one graph launch per step
+// ---------------------------------------------------------------------------
+
+struct sd_batch {
+  std::vector<sd_handle *> cases;
+  std::vector<double> dt;      // dt of the captured graph, per case
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev; // fork / join events (one per case + origin)
+  std::string err;
+};
+
+namespace {
+
+void free_batch(sd_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  for (sd_handle *h : b->cases) free_handle(h);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// Autotuner: for one case, time a few SSP-RK3 steps of each candidate launch
+// shape (volume CTAs per SM x face block size) from a uniform state and keep
+// the fastest.  The case's state and time are reset afterwards.
+int tune_case(sd_handle *h, double dt) {
+  int maxc = 1, cur = 0, fb = 0;
+  h->eng->tuning(&cur, &maxc, &fb);
+  const int fblocks[3] = {128, 256, 512};
+  cudaEvent_t a, z;
+  cudaEventCreate(&a);
+  cudaEventCreate(&z);
+  float best = 1e30f;
+  int best_c = cur, best_f = fb;
+  // uniform state: rho = 1, p = 1, at rest
+  const size_t n = (size_t)h->E * 4 * h->N * h->N, nn = (size_t)h->N * h->N;
+  std::vector<double> q(n, 0.0);
+  const double e0 = 1.0 / (h->prm.gamma - 1.0);
+  for (int e = 0; e < h->E; ++e)
+    for (size_t k = 0; k < nn; ++k) {
+      q[((size_t)e * 4 + 0) * nn + k] = 1.0;
+      q[((size_t)e * 4 + 3) * nn + k] = e0;
+    }
+  int rc = SD_OK;
+  for (int c = 1; c <= maxc && !rc; ++c)
+    for (int f = 0; f < 3 && !rc; ++f) {
+      int cc = c, ff = fblocks[f];
+      h->eng->tuning(&cc, nullptr, &ff);
+      if ((rc = sd_set_state(h, q.data(), 0))) break;
+      const StatePtr A = h->eng->A();
+      h->eng->trace(h->md, A, h->stream);
+      queue_step(h, dt);  // warm-up
+      cudaEventRecord(a, h->stream);
+      for (int k = 0; k < 3; ++k) queue_step(h, dt);
+      cudaEventRecord(z, h->stream);
+      cudaError_t e = cudaEventSynchronize(z);
+      if (e) rc = cuda_fail(h, e, "autotuner");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, z);
+      if (!rc && ms < best) {
+        best = ms;
+        best_c = cc;
+        best_f = ff;
+      }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(z);
+  h->eng->tuning(&best_c, nullptr, &best_f);
+  if (!rc) {
+    std::fill(q.begin(), q.end(), 0.0);
+    rc = sd_set_state(h, q.data(), 0);
+  }
+  if (!rc) rc = sd_set_time(h, 0.0);
+  int flags = 0;
+  if (!rc) rc = read_flags(h, &flags, true);
+  return rc;
+}
+
+}  // namespace
+
+int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_params *prm, double tune_dt,
+                    sd_batch **out) {
+  g_create_error.clear();
+  if (!out) return SD_ERR_ARG;
+  *out = nullptr;
+  if (n <= 0 || !meshes || !p || !prm) {
+    g_create_error = "bad batch arguments";
+    return SD_ERR_ARG;
+  }
+  sd_batch *b = new sd_batch();
+  cudaError_t ce = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (ce) {
+    g_create_error = std::string("batch stream: ") + cudaGetErrorString(ce);
+    free_batch(b);
+    return SD_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    sd_params pi = prm[i];
+    pi.stream = nullptr;  // every case gets its own stream (a branch of the step graph)
+    sd_handle *h = nullptr;
+    int rc = sd_create(meshes[i], p[i], &pi, &h);
+    if (rc) {
+      g_create_error = "case " + std::to_string(i) + ": " + g_create_error;
+      free_batch(b);
+      return rc;
+    }
+    b->cases.push_back(h);
+    if (tune_dt > 0.0 && (rc = tune_case(h, tune_dt))) {
+      g_create_error = "case " + std::to_string(i) + " autotuner: " + h->err;
+      free_batch(b);
+      return rc;
+    }
+  }
+  b->ev.resize(n + 1);
+  for (auto &e : b->ev)
+    if ((ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) {
+      g_create_error = std::string("batch events: ") + cudaGetErrorString(ce);
+      free_batch(b);
+      return SD_ERR_CUDA;
+    }
+  *out = b;
+  return SD_OK;
+}
+
+int sd_batch_destroy(sd_batch *b) {
+  free_batch(b);
+  return SD_OK;
+}
+
+int sd_batch_size(const sd_batch *b) { return b ? (int)b->cases.size() : 0; }
+
+sd_handle *sd_batch_case(sd_batch *b, int i) {
+  if (!b || i < 0 || i >= (int)b->cases.size()) return nullptr;
+  return b->cases[i];
+}
+
+const char *sd_batch_last_error(const sd_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+int sd_batch_step(sd_batch *b, const double *dt, int nsteps) {
+  if (!b || !dt || nsteps < 0) return SD_ERR_ARG;
+  const int n = (int)b->cases.size();
+  for (int i = 0; i < n; ++i)
+    if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) {
+      b->err = "dt must be positive";
+      return SD_ERR_ARG;
+    }
+  if (nsteps == 0) return SD_OK;
+  cudaError_t e;
+  // every case's earlier work (state copies, traces) is ordered before the graph
+  for (int i = 0; i < n; ++i) {
+    sd_handle *h = b->cases[i];
+    if (!h->traces_valid) {
+      h->eng->trace(h->md, h->eng->A(), h->stream);
+      h->traces_valid = true;
+    }
+    if ((e = cudaEventRecord(b->ev[i], h->stream)) || (e = cudaStreamWaitEvent(b->stream, b->ev[i], 0))) {
+      b->err = std::string("batch ordering: ") + cudaGetErrorString(e);
+      return SD_ERR_CUDA;
+    }
+  }
+  bool same = b->exec && (int)b->dt.size() == n;
+  for (int i = 0; same && i < n; ++i) same = b->dt[i] == dt[i];
+  if (!same) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    // one graph per step: a branch per case, forked from and joined to the batch stream
+    cudaGraph_t g;
+    if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal))) {
+      b->err = std::string("batch capture: ") + cudaGetErrorString(e);
+      return SD_ERR_CUDA;
+    }
+    cudaEventRecord(b->ev[n], b->stream);
+    for (int i = 0; i < n; ++i) {
+      sd_handle *h = b->cases[i];
+      cudaStreamWaitEvent(h->stream, b->ev[n], 0);
+      queue_step(h, dt[i]);
+      cudaEventRecord(b->ev[i], h->stream);
+      cudaStreamWaitEvent(b->stream, b->ev[i], 0);
+    }
+    cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (le || e) {
+      b->err = std::string("batch capture: ") + cudaGetErrorString(le ? le : e);
+      if (!e) cudaGraphDestroy(g);
+      return SD_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e) {
+      b->err = std::string("batch instantiate: ") + cudaGetErrorString(e);
+      return SD_ERR_CUDA;
+    }
+    b->dt.assign(dt, dt + n);
+  }
+  for (int k = 0; k < nsteps; ++k)
+    if ((e = cudaGraphLaunch(b->exec, b->stream))) {
+      b->err = std::string("batch launch: ") + cudaGetErrorString(e);
+      return SD_ERR_CUDA;
+    }
+  // later per-case calls run on the case streams: order them after the steps
+  if ((e = cudaEventRecord(b->ev[n], b->stream))) return SD_ERR_CUDA;
+  for (int i = 0; i < n; ++i)
+    if ((e = cudaStreamWaitEvent(b->cases[i]->stream, b->ev[n], 0))) return SD_ERR_CUDA;
+  return SD_OK;
+}
+
+int sd_batch_sync(sd_batch *b) {
+  if (!b) return SD_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e) {
+    b->err = std::string("sd_batch_sync: ") + cudaGetErrorString(e);
+    return SD_ERR_CUDA;
+  }
+  int worst = SD_OK;
+  for (size_t i = 0; i < b->cases.size(); ++i) {
+    const int rc = sd_sync(b->cases[i]);
+    if (rc && worst == SD_OK) {
+      worst = rc;
+      b->err = "case " + std::to_string(i) + ": " + b->cases[i]->err;
+    }
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
 // residual without any allocation at call time
 // ---------------------------------------------------------------------------
 //

@@ -1199,6 +1199,8 @@ struct EngineImpl : Engine {
   size_t nval = 0;
   int merge_smem = 0;
   int grid_res = 1, grid_rk = 1;  // persistent grid sizes of the volume kernel
+  int sms = 1, occ_rk = 1;         // SM count, resident volume CTAs per SM
+  int face_block = 256;            // block size of the conforming-face kernel
 
   ~EngineImpl() override {
     cudaFree(dXs);
@@ -1281,7 +1283,7 @@ struct EngineImpl : Engine {
     {
       // persistent volume kernel: as many CTAs as fit on the GPU at once
       using C = VolCfg<T, N, OTF>;
-      int dev = 0, sms = 0, occ0 = 0, occ1 = 0;
+      int dev = 0, occ0 = 0, occ1 = 0;
       if ((err = cudaGetDevice(&dev))) return err;
       if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return err;
       if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RESIDUAL, OTF>,
@@ -1297,7 +1299,8 @@ struct EngineImpl : Engine {
                                                                C::SMEM)))
         return err;
       grid_res = std::max(1, occ0) * sms;
-      grid_rk = std::max(1, occ1) * sms;
+      occ_rk = std::max(1, occ1);
+      grid_rk = occ_rk * sms;
     }
     if (md.nTab > 0) k_geo<T, N><<<(md.nTab + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
     k_egeo<T, N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
@@ -1330,7 +1333,7 @@ struct EngineImpl : Engine {
 
   void faces(const MeshDev &md, StatePtr q, cudaStream_t s) override {
     if (!md.viscous) {
-      if (md.nF > 0) k_face<T, N, OTF><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
+      if (md.nF > 0) k_face<T, N, OTF><<<(md.nF * N + face_block - 1) / face_block, face_block, 0, s>>>(md);
       if (md.nB > 0) k_bface<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
       return;
     }
@@ -1375,6 +1378,20 @@ struct EngineImpl : Engine {
   }
 
   int tile_elems() const override { return VolCfg<T, N, OTF>::EPB; }
+
+  // launch shapes chosen by the batch autotuner: volume CTAs per SM (capped
+  // by occupancy; 0 keeps the current value) and the face-kernel block size
+  void tuning(int *vol_ctas_per_sm, int *max_ctas_per_sm, int *fblock) override {
+    if (max_ctas_per_sm) *max_ctas_per_sm = occ_rk;
+    if (vol_ctas_per_sm) {
+      if (*vol_ctas_per_sm > 0) grid_rk = std::min(*vol_ctas_per_sm, occ_rk) * sms;
+      *vol_ctas_per_sm = grid_rk / sms;
+    }
+    if (fblock) {
+      if (*fblock > 0) face_block = *fblock;
+      *fblock = face_block;
+    }
+  }
 
   void advance(const MeshDev &md, double dt, cudaStream_t s) override { k_advance<<<1, 1, 0, s>>>(md.clk, dt); }
 

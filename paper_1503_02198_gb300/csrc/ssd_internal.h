@@ -100,6 +100,8 @@ struct Engine {
   // elements per volume-kernel tile; every per-element device array holds a
   // whole number of tiles (padding elements are never computed on)
   virtual int tile_elems() const = 0;
+  // get / set the tunable launch shapes (see EngineImpl::tuning)
+  virtual void tuning(int *vol_ctas_per_sm, int *max_ctas_per_sm, int *face_block) = 0;
   // the two state buffers A and B: E elements, storage for Epad >= E
   virtual cudaError_t alloc_state(int E, int Epad) = 0;
   virtual StatePtr A() const = 0;

@@ -90,3 +90,61 @@ def build_workload(name: str) -> Workload:
 
 
 WORKLOADS = ("couette_n3", "vortex_n4", "vortex_n5", "rotor_n6")
+
+
+def min_edge(mesh) -> float:
+    import numpy as np
+    xy, en = mesh["xy"], mesh["elem_nodes"]
+    d = [np.linalg.norm(xy[en[:, a]] - xy[en[:, b]], axis=1) for a, b in ((0, 1), (1, 2), (2, 3), (3, 0))]
+    return float(np.min(d))
+
+
+def stable_dt(mesh, N, prm, speed, cfl=0.1):
+    """Explicit step from the smallest edge: acoustic/convective limit
+    h / (speed N^2), and for viscous flow the diffusive limit h^2 / (nu N^4)."""
+    h = min_edge(mesh)
+    dt = cfl * h / (speed * N * N)
+    if prm.viscous and prm.mu > 0:
+        dt = min(dt, 0.25 * cfl * h * h / (prm.mu * N ** 4))
+    return dt
+
+
+def batch_cases(n=64, seed=1503, min_cells=1000, max_cells=8000):
+    """Seeded mix of independent cases for the batched form: rotor-family
+    (Euler vortex through a rotating disk) and Couette-family (viscous,
+    walls) meshes with log-uniform cell counts, p in {2,..,5}, omega in
+    U[0.1, 1].  Returns a list of (name, mesh, p, FlowParams, dt)."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(n):
+        target = math.exp(rng.uniform(math.log(min_cells), math.log(max_cells)))
+        p = int(rng.integers(2, 6))
+        omega = float(rng.uniform(0.1, 1.0))
+        N = p + 1
+        if rng.uniform() < 0.75:
+            # rotor family: about 6016 s^2 cells
+            s = math.sqrt(target / 6016.0)
+            nh = max(4, 2 * int(round(12 * s)))
+            nc = max(nh + 6, 2 * int(round(32 * s)))
+            if (nc - nh) % 2:
+                nc += 1
+            mesh = meshes.rotor_mesh(half_width=10.0, n_cart=nc, n_hole=nh, r_interface=3.0,
+                                     n_core=max(2, int(round(24 * s))), core_half=1.5,
+                                     n_ring_in=max(2, int(round(16 * s))),
+                                     n_ring_out=max(2, int(round(4 * s))))
+            prm = FlowParams(gamma=1.4, Rgas=1.0, omega=omega, viscous=0)
+            dt = stable_dt(mesh, N, prm, 2.0 + math.sqrt(1.4) + 3.0 * omega)
+            out.append((f"rotor{k}", mesh, p, prm, dt))
+        else:
+            # Couette family: nr x 8m rotating + nr x 10m stationary cells
+            nr = max(2, int(round(math.sqrt(target / 72.0))))
+            mm = max(1, int(round(target / (18.0 * nr))))
+            mesh = meshes.couette_mesh(nr, 8 * mm, nr, 10 * mm)
+            U = omega
+            c = U / 0.1
+            prm = FlowParams(gamma=1.4, Rgas=c * c / 1.4, mu=U / 10.0, prandtl=0.72, omega=omega, viscous=1,
+                             T_wall=1.0)
+            dt = stable_dt(mesh, N, prm, c + U)
+            out.append((f"couette{k}", mesh, p, prm, dt))
+    return out
