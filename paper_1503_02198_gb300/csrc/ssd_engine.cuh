@@ -950,79 +950,118 @@ struct VolCfg {
   static constexpr bool FF = std::is_same<T, float>::value;  // double-float state
   static constexpr int EPB = N == 3 ? 16 : (N == 6 ? 8 : 12);  // elements per tile (multiple of 4)
   static constexpr int THREADS = EPB * 2 * N;                  // one thread per SP line
-  // one stage: state (hi, lo), base state (hi, lo), common fluxes, cell records, flags
+  // double-buffered part of a tile (needed by the flux phase): state hi,
+  // common fluxes, cell records, flags
   static constexpr int QHI = EPB * 4 * NN * (int)sizeof(T);
   static constexpr int QLO = FF ? EPB * 4 * NN * 4 : 0;
   static constexpr int CFB = EPB * 16 * N * (int)sizeof(T);
   static constexpr int EGB = OTF ? EPB * 8 * (int)sizeof(T) : 0;
   static constexpr int EFB = EPB * 4;
-  static constexpr int O_QHI = 0, O_QLO = O_QHI + QHI, O_NHI = O_QLO + QLO, O_NLO = O_NHI + QHI,
-                       O_CF = O_NLO + QLO, O_EG = O_CF + CFB, O_EF = O_EG + EGB;
+  static constexpr int O_QHI = 0, O_CF = O_QHI + QHI, O_EG = O_CF + CFB, O_EF = O_EG + EGB;
   static constexpr int STAGE = ((O_EF + EFB) + 127) / 128 * 128;
-  // work arrays after the two stages
-  static constexpr int O_RF = 2 * STAGE, O_RG = O_RF + QHI, O_IJ = O_RG + QHI;
+  // single-buffered part (needed only by the Runge-Kutta phase): state lo,
+  // base state hi and lo; loaded at the start of each tile behind the flux phase
+  static constexpr int O_QLO = 2 * STAGE, O_NHI = O_QLO + QLO, O_NLO = O_NHI + QHI;
+  static constexpr int SINGLE_END = ((O_NLO + QLO) + 127) / 128 * 128;
+  // work arrays
+  static constexpr int O_RF = SINGLE_END, O_RG = O_RF + QHI, O_IJ = O_RG + QHI;
   static constexpr int O_BAR = ((O_IJ + EPB * NN * (int)sizeof(T)) + 15) / 16 * 16;
-  static constexpr int SMEM = O_BAR + 16;
+  static constexpr int SMEM = O_BAR + 3 * 8;
+  // resident CTAs per SM the register budget is set for
+  static constexpr int MINB = (200 * 1024 / SMEM) < 8 ? (200 * 1024 / SMEM) : 8;
 };
 
+// 1 / x: one correctly rounded reciprocal on the FP32 path, a division in FP64
+template <typename T>
+__device__ __forceinline__ T recip(T x) {
+  if constexpr (std::is_same<T, float>::value) return __frcp_rn(x);
+  else return T(1) / x;
+}
+
+// transformed ALE inviscid flux at one flux point: a.(F, G) - (V_g . a) Q
+template <typename T>
+__device__ __forceinline__ void point_flux(const T *q, T vx, T vy, T vg, T gm1, T *f) {
+  const T ir = recip(q[0]);
+  const T p = gm1 * (q[3] - T(0.5) * (q[1] * q[1] + q[2] * q[2]) * ir);
+  const T un = (q[1] * vx + q[2] * vy) * ir;
+  f[0] = q[0] * un - vg * q[0];
+  f[1] = q[1] * un + p * vx - vg * q[1];
+  f[2] = q[2] * un + p * vy - vg * q[2];
+  f[3] = (q[3] + p) * un - vg * q[3];
+}
+
+// bounded wait by warp 0 only; the other warps wait at the barrier without issuing
+__device__ __forceinline__ bool cta_wait(uint64_t *bar, uint32_t parity) {
+  bool ok = true;
+  if (threadIdx.x < 32) ok = mbar_wait_bounded(bar, parity);
+  return __syncthreads_and(ok) != 0;
+}
+
 template <typename T, int N, int MODE, bool OTF>
-__global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
+__global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS, VolCfg<T, N, OTF>::MINB)
     k_volume(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, double alpha, double beta,
              double dt, int ntiles, float af, float bdt) {
   using C = VolCfg<T, N, OTF>;
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
   constexpr bool FF = C::FF;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bar = (uint64_t *)(smem + C::O_BAR);
+  uint64_t *bar = (uint64_t *)(smem + C::O_BAR);  // [0], [1]: double-buffered part; [2]: single part
   T(*sRF)[4][NN] = (T(*)[4][NN])(smem + C::O_RF);
   T(*sRG)[4][NN] = (T(*)[4][NN])(smem + C::O_RG);
   T(*sIJ)[NN] = (T(*)[NN])(smem + C::O_IJ);
   const VolBasis<T, N> &B = cVB<T, N>;
   const bool use_base = MODE == MODE_RK && alpha != 0.0;
-  const uint32_t tx_bytes = C::QHI + C::QLO + C::CFB + C::EGB + C::EFB + (use_base ? C::QHI + C::QLO : 0);
+  const uint32_t txA = C::QHI + C::CFB + C::EGB + C::EFB;
+  const uint32_t txB = MODE == MODE_RK ? C::QLO + (use_base ? C::QHI + C::QLO : 0) : 0;
   const T cth = pick<T>(md.clk->c, md.clk->cf), sth = pick<T>(md.clk->s, md.clk->sf);
   const T gm1 = pick<T>(md.gamma, md.gamma_f) - T(1);
 
-  auto issue = [&](int tl, int st) {
+  auto issueA = [&](int tl, int st) {
     unsigned char *sb = smem + st * C::STAGE;
     const size_t e0 = (size_t)tl * EPB;
-    mbar_expect_tx(&bar[st], tx_bytes);
+    mbar_expect_tx(&bar[st], txA);
     bulk_g2s(sb + C::O_QHI, (const T *)in.hi + e0 * 4 * NN, C::QHI, &bar[st]);
-    if (FF) bulk_g2s(sb + C::O_QLO, (const float *)in.lo + e0 * 4 * NN, C::QLO, &bar[st]);
-    if (use_base) {
-      bulk_g2s(sb + C::O_NHI, (const T *)base.hi + e0 * 4 * NN, C::QHI, &bar[st]);
-      if (FF) bulk_g2s(sb + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QLO, &bar[st]);
-    }
     bulk_g2s(sb + C::O_CF, (const T *)md.CF + e0 * 16 * N, C::CFB, &bar[st]);
     if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, C::EGB, &bar[st]);
     bulk_g2s(sb + C::O_EF, md.eflag + e0, C::EFB, &bar[st]);
+  };
+  auto issueB = [&](int tl) {
+    const size_t e0 = (size_t)tl * EPB;
+    mbar_expect_tx(&bar[2], txB);
+    if (FF) bulk_g2s(smem + C::O_QLO, (const float *)in.lo + e0 * 4 * NN, C::QLO, &bar[2]);
+    if (use_base) {
+      bulk_g2s(smem + C::O_NHI, (const T *)base.hi + e0 * 4 * NN, C::QHI, &bar[2]);
+      if (FF) bulk_g2s(smem + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QLO, &bar[2]);
+    }
   };
 
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
     fence_mbar_init();
   }
   __syncthreads();
   int tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  if (threadIdx.x == 0 && tile < ntiles) issueA(tile, 0);
   bool bad = false;
   int it = 0;
   for (; tile < ntiles; tile += gridDim.x, ++it) {
     const int st = it & 1;
     const int next = tile + gridDim.x;
-    if (threadIdx.x == 0 && next < ntiles) {
-      // the other stage was last read in the previous iteration (before its
-      // closing barrier); order those generic reads before the async refill
+    if (threadIdx.x == 0) {
+      // both refilled regions were last read before the previous iteration's
+      // closing barrier; order those generic reads before the async writes
       fence_proxy_async_smem();
-      issue(next, st ^ 1);
+      if (next < ntiles) issueA(next, st ^ 1);
+      if (txB) issueB(tile);
     }
-    const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it >> 1) & 1));
-    if (!__syncthreads_and(ok)) {
+    if (!cta_wait(&bar[st], (uint32_t)((it >> 1) & 1))) {
       if (threadIdx.x == 0) {
         atomicOr(&md.clk->flags, 4);
-        // let the prefetch of the next tile land before the CTA exits
+        // let the copies in flight land before the CTA exits
         if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        if (txB) mbar_wait_bounded(&bar[2], (uint32_t)(it & 1));
       }
       return;
     }
@@ -1069,8 +1108,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
           T vx, vy, vg;
           if (d == 0) G.xi_fp(i, mline, vx, vy, vg);
           else G.eta_fp(mline, i, vx, vy, vg);
-          const T p = pressure_of(qf, gm1);
-          normal_flux(qf, p, vx, vy, vg, f);
+          point_flux(qf, vx, vy, vg, gm1, f);
         }
 #pragma unroll
         for (int k = 0; k < N; ++k) {
@@ -1093,7 +1131,18 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
           for (int v = 0; v < 4; ++v) sRG[le][v][k * N + mline] = acc[v][k];
       }
     }
-    __syncthreads();
+    // the single-buffered part (state lo, base state) must have landed too
+    if (txB) {
+      if (!cta_wait(&bar[2], (uint32_t)(it & 1))) {
+        if (threadIdx.x == 0) {
+          atomicOr(&md.clk->flags, 4);
+          if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        }
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
     // ---- phase 2: dQ/dt at the SPs and the Runge-Kutta combination ----
     for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
       const int l2 = idx / NN, sp = idx - l2 * NN;
@@ -1104,7 +1153,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
         for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
       } else if (!FF) {
         // FP64: Shu-Osher combination alpha Q_n + beta (Q_k + dt R)
-        const double(*sN)[4][NN] = (const double(*)[4][NN])(sb + C::O_NHI);
+        const double(*sN)[4][NN] = (const double(*)[4][NN])(smem + C::O_NHI);
         double *qo = (double *)out.hi;
         double qn[4];
 #pragma unroll
@@ -1125,9 +1174,9 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
         // FP32 with a double-float state: the same combination written as
         // Q_k + [alpha (Q_n - Q_k) + beta dt R] (alpha + beta = 1); the bracket
         // is an O(dt) increment formed in float, added to Q_k exactly (two-sum)
-        const float(*sKL)[4][NN] = (const float(*)[4][NN])(sb + C::O_QLO);
-        const float(*sNH)[4][NN] = (const float(*)[4][NN])(sb + C::O_NHI);
-        const float(*sNL)[4][NN] = (const float(*)[4][NN])(sb + C::O_NLO);
+        const float(*sKL)[4][NN] = (const float(*)[4][NN])(smem + C::O_QLO);
+        const float(*sNH)[4][NN] = (const float(*)[4][NN])(smem + C::O_NHI);
+        const float(*sNL)[4][NN] = (const float(*)[4][NN])(smem + C::O_NLO);
         float *oh = (float *)out.hi, *ol = (float *)out.lo;
         float hv[4];
 #pragma unroll
@@ -1144,7 +1193,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
           ol[gi + v * NN] = err - (H - sum);
           hv[v] = H;
         }
-        const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
+        const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) * __frcp_rn(hv[0]));
         bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) sQ[l2][v][sp] = (T)hv[v];
@@ -1172,7 +1221,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS)
         }
       }
     }
-    // every read of this stage is done before it is refilled next iteration
+    // every read of this tile's buffers is done before they are refilled
     __syncthreads();
   }
   if (MODE == MODE_RK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&md.clk->flags, 1);
