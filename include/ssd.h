@@ -88,6 +88,8 @@ typedef struct {
                        divergence arithmetic; FP64 rotation angle, mortar geometry and
                        projection weights, and FP64 state / Runge-Kutta accumulation */
   void *stream;     /* cudaStream_t to queue work on; NULL = a non-blocking stream the handle creates */
+  int rk_stages;    /* time integrator: 0 or 3 = three-stage SSP-RK3 (Shu-Osher); 5 = the
+                       five-stage fourth-order SSP-RK of Sec. 4 (Spiteri-Ruuth coefficients) */
 } sd_params;
 
 typedef struct sd_handle sd_handle;
@@ -129,9 +131,9 @@ int sd_get_time(sd_handle *h, double *t);
  * Synchronises when R is host memory. */
 int sd_residual(sd_handle *h, double *R, int on_device);
 
-/* Advance nsteps steps of size dt with three-stage SSP Runge-Kutta (Sec. 3;
- * stage times t, t + dt, t + dt/2; mortar connectivity rebuilt at every
- * stage, Sec. 3.2).  Asynchronous: queued on the stream as CUDA-graph
+/* Advance nsteps steps of size dt with the SSP Runge-Kutta scheme chosen by
+ * sd_params.rk_stages (Sec. 3: three stages at t, t + dt, t + dt/2; Sec. 4:
+ * five stages); the mortar connectivity is rebuilt at every stage (Sec. 3.2).  Asynchronous: queued on the stream as CUDA-graph
  * launches; errors detected on the device are reported by sd_sync. */
 int sd_step(sd_handle *h, double dt, int nsteps);
 

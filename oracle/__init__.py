@@ -46,6 +46,8 @@ def lib():
         L.or_residual.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
         L.or_residual_ex.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, _dp]
         L.or_step.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_int]
+        L.or_step_rk54.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_int]
+        L.or_rk54_tableau.argtypes = [_dp, _dp, _dp]
         L.or_sp_coords.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp]
         L.or_sp_jacobian.argtypes = [ctypes.c_void_p, _dp]
         L.or_points.argtypes = [ctypes.c_int, _dp, _dp]
@@ -93,6 +95,12 @@ def projection(N: int, o: float, s: float):
     Pf, Pb = np.zeros((N, N)), np.zeros((N, N))
     lib().or_projection(N, o, s, _d(Pf), _d(Pb))
     return Pf, Pb
+
+
+def rk54_tableau():
+    A, b, c = np.zeros((5, 5)), np.zeros(5), np.zeros(5)
+    lib().or_rk54_tableau(_d(A), _d(b), _d(c))
+    return A, b, c
 
 
 def params_array(params) -> np.ndarray:
@@ -164,10 +172,12 @@ class Oracle:
         lib().or_residual_ex(self._h, _d(Q), t, _d(R), _d(S))
         return R, S
 
-    def step(self, Q, t: float, dt: float, nsteps: int = 1):
+    def step(self, Q, t: float, dt: float, nsteps: int = 1, rk_stages: int = 3):
+        """rk_stages 3: SSP-RK3 (Shu-Osher); 5: the five-stage fourth-order SSP-RK."""
         Q = np.array(Q, dtype=np.float64, order="C").reshape(self.shape)
         tt = np.array([t], dtype=np.float64)
-        lib().or_step(self._h, _d(Q), _d(tt), dt, nsteps)
+        fn = lib().or_step_rk54 if rk_stages == 5 else lib().or_step
+        fn(self._h, _d(Q), _d(tt), dt, nsteps)
         return Q, float(tt[0])
 
     def face_info(self):

@@ -1181,6 +1181,76 @@ int or_step(or_mesh *m, double *Q, double *t, double dt, int nsteps) {
   return 0;
 }
 
+/* Five-stage, fourth-order SSP Runge-Kutta (the integrator of Sec. 4; the
+ * paper cites Spiteri & Ruuth for it without printing coefficients).  Shu-Osher
+ * form with the published coefficients:
+ *   u1 = u + c10 dt L(u)
+ *   u2 = a20 u + a21 u1 + c21 dt L(u1)
+ *   u3 = a30 u + a32 u2 + c32 dt L(u2)
+ *   u4 = a40 u + a43 u3 + c43 dt L(u3)
+ *   u+ = a52 u2 + a53 u3 + c53 dt L(u3) + a54 u4 + c54 dt L(u4)
+ * Stage times follow from the coefficients (or_rk54_tableau). */
+static const double RK54_C10 = 0.391752226571890;
+static const double RK54_A20 = 0.444370493651235, RK54_A21 = 0.555629506348765, RK54_C21 = 0.368410593050371;
+static const double RK54_A30 = 0.620101851488403, RK54_A32 = 0.379898148511597, RK54_C32 = 0.251891774271694;
+static const double RK54_A40 = 0.178079954393132, RK54_A43 = 0.821920045606868, RK54_C43 = 0.544974750228521;
+static const double RK54_A52 = 0.517231671970585, RK54_A53 = 0.096059710526147, RK54_C53 = 0.063692468666290;
+static const double RK54_A54 = 0.386708617503269, RK54_C54 = 0.226007483236906;
+
+/* Butcher tableau (A 5x5 row-major, b 5, c 5) of the scheme above, for tests:
+ * every stage value is expanded as u + dt sum_j A_ij k_j with k_j = L(stage j). */
+void or_rk54_tableau(double *A, double *b, double *c) {
+  /* coefficient of dt k_j in stage i (stage 1 = u) */
+  double S[6][5];
+  memset(S, 0, sizeof S);
+  /* S[1] = u1 */
+  S[1][0] = RK54_C10;
+  for (int j = 0; j < 5; ++j) S[2][j] = RK54_A21 * S[1][j];
+  S[2][1] += RK54_C21;
+  for (int j = 0; j < 5; ++j) S[3][j] = RK54_A32 * S[2][j];
+  S[3][2] += RK54_C32;
+  for (int j = 0; j < 5; ++j) S[4][j] = RK54_A43 * S[3][j];
+  S[4][3] += RK54_C43;
+  for (int j = 0; j < 5; ++j) S[5][j] = RK54_A52 * S[2][j] + RK54_A53 * S[3][j] + RK54_A54 * S[4][j];
+  S[5][3] += RK54_C53;
+  S[5][4] += RK54_C54;
+  memset(A, 0, sizeof(double) * 25);
+  for (int i = 0; i < 5; ++i) {
+    double ci = 0.0;
+    for (int j = 0; j < 5; ++j) {
+      A[i * 5 + j] = i == 0 ? 0.0 : S[i][j];
+      ci += A[i * 5 + j];
+    }
+    c[i] = ci;
+  }
+  for (int j = 0; j < 5; ++j) b[j] = S[5][j];
+}
+
+int or_step_rk54(or_mesh *m, double *Q, double *t, double dt, int nsteps) {
+  size_t n = (size_t)m->ne * 4 * m->N * m->N;
+  double *u1 = malloc(n * sizeof(double)), *u2 = malloc(n * sizeof(double)), *u3 = malloc(n * sizeof(double));
+  double *u4 = malloc(n * sizeof(double)), *r = malloc(n * sizeof(double)), *r3 = malloc(n * sizeof(double));
+  double A[25], b[5], c[5];
+  or_rk54_tableau(A, b, c);
+  for (int s = 0; s < nsteps; ++s) {
+    double tn = *t;
+    or_residual(m, Q, tn + c[0] * dt, r);
+    for (size_t i = 0; i < n; ++i) u1[i] = Q[i] + RK54_C10 * dt * r[i];
+    or_residual(m, u1, tn + c[1] * dt, r);
+    for (size_t i = 0; i < n; ++i) u2[i] = RK54_A20 * Q[i] + RK54_A21 * u1[i] + RK54_C21 * dt * r[i];
+    or_residual(m, u2, tn + c[2] * dt, r);
+    for (size_t i = 0; i < n; ++i) u3[i] = RK54_A30 * Q[i] + RK54_A32 * u2[i] + RK54_C32 * dt * r[i];
+    or_residual(m, u3, tn + c[3] * dt, r3);
+    for (size_t i = 0; i < n; ++i) u4[i] = RK54_A40 * Q[i] + RK54_A43 * u3[i] + RK54_C43 * dt * r3[i];
+    or_residual(m, u4, tn + c[4] * dt, r);
+    for (size_t i = 0; i < n; ++i)
+      Q[i] = RK54_A52 * u2[i] + RK54_A53 * u3[i] + RK54_C53 * dt * r3[i] + RK54_A54 * u4[i] + RK54_C54 * dt * r[i];
+    *t = tn + dt;
+  }
+  free(u1); free(u2); free(u3); free(u4); free(r); free(r3);
+  return 0;
+}
+
 /* mortar list at time t, for tests: returns the number of mortars; arrays must
  * hold nL + nR entries */
 int or_mortar_list(const or_mesh *m, double t, int *lf, int *rf, double *oL, double *sL, double *oR, double *sR) {

@@ -44,7 +44,8 @@ class sd_mesh(ctypes.Structure):
 class sd_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("Rgas", ctypes.c_double), ("mu", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("omega", ctypes.c_double), ("T_wall", ctypes.c_double),
-                ("viscous", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("viscous", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("rk_stages", ctypes.c_int)]
 
 
 class SSDError(RuntimeError):
@@ -138,7 +139,8 @@ def _mesh_struct(mesh: dict, keep: list) -> sd_mesh:
 
 def _params_struct(params, precision, stream=None) -> sd_params:
     return sd_params(params.gamma, params.Rgas, params.mu, params.prandtl, params.omega, params.T_wall,
-                     int(params.viscous), int(precision), ctypes.c_void_p(stream) if stream else None)
+                     int(params.viscous), int(precision), ctypes.c_void_p(stream) if stream else None,
+                     int(getattr(params, "rk_stages", 3)))
 
 
 class Solver:

@@ -509,18 +509,85 @@ void free_handle(sd_handle *h) {
   delete h;
 }
 
-// queue the three SSP-RK3 stages of one step (Shu-Osher form)
+// Five-stage fourth-order SSP Runge-Kutta (the integrator of Sec. 4), the
+// published Shu-Osher coefficients:
+//   u1 = u + c10 dt L(u);  u2 = a20 u + a21 u1 + c21 dt L(u1);
+//   u3 = a30 u + a32 u2 + c32 dt L(u2);  u4 = a40 u + a43 u3 + c43 dt L(u3);
+//   u+ = a52 u2 + a53 u3 + c53 dt L(u3) + a54 u4 + c54 dt L(u4).
+struct Rk54 {
+  static constexpr double c10 = 0.391752226571890;
+  static constexpr double a20 = 0.444370493651235, a21 = 0.555629506348765, c21 = 0.368410593050371;
+  static constexpr double a30 = 0.620101851488403, a32 = 0.379898148511597, c32 = 0.251891774271694;
+  static constexpr double a40 = 0.178079954393132, a43 = 0.821920045606868, c43 = 0.544974750228521;
+  static constexpr double a52 = 0.517231671970585, a53 = 0.096059710526147, c53 = 0.063692468666290;
+  static constexpr double a54 = 0.386708617503269, c54 = 0.226007483236906;
+};
+
+// stage times of the five-stage scheme (row sums of its Butcher matrix)
+void rk54_times(double *c) {
+  // dt-coefficients of L(stage j) inside stage i
+  double s1[5] = {Rk54::c10, 0, 0, 0, 0}, s2[5], s3[5], s4[5];
+  for (int j = 0; j < 5; ++j) s2[j] = Rk54::a21 * s1[j];
+  s2[1] += Rk54::c21;
+  for (int j = 0; j < 5; ++j) s3[j] = Rk54::a32 * s2[j];
+  s3[2] += Rk54::c32;
+  for (int j = 0; j < 5; ++j) s4[j] = Rk54::a43 * s3[j];
+  s4[3] += Rk54::c43;
+  const double *rows[4] = {s1, s2, s3, s4};
+  c[0] = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < 5; ++j) acc += rows[i][j];
+    c[i + 1] = acc;
+  }
+}
+
+// queue the stages of one step; every stage is  out = in + a0 (base - in) +
+// w_in + bdt L(in)  (RkArgs), which is the Shu-Osher form rewritten around
+// the stage input (the weights of a Shu-Osher stage sum to one)
 void queue_step(sd_handle *h, double dt) {
   MeshDev &md = h->md;
   Engine *g = h->eng;
   cudaStream_t s = h->stream;
   const StatePtr A = g->A(), B = g->B(), none{nullptr, nullptr};
-  g->couple(md, A, 0.0, dt, s);
-  g->volume(md, A, none, B, nullptr, 0.0, 1.0, dt, MODE_RK, s);
-  g->couple(md, B, 1.0, dt, s);
-  g->volume(md, B, A, B, nullptr, 0.75, 0.25, dt, MODE_RK, s);
-  g->couple(md, B, 0.5, dt, s);
-  g->volume(md, B, A, A, nullptr, 1.0 / 3.0, 2.0 / 3.0, dt, MODE_RK, s);
+  if (h->prm.rk_stages != 5) {
+    // SSP-RK3: Q1 = Qn + dt L(Qn); Q2 = 3/4 Qn + 1/4 (Q1 + dt L(Q1));
+    // Qn+1 = 1/3 Qn + 2/3 (Q2 + dt L(Q2)); stage times 0, 1, 1/2
+    RkArgs r1, r2, r3;
+    r1.bdt = dt;
+    r2.has_base = 1, r2.a0 = 0.75, r2.bdt = 0.25 * dt;
+    r3.has_base = 1, r3.a0 = 1.0 / 3.0, r3.bdt = 2.0 / 3.0 * dt;
+    g->couple(md, A, 0.0, dt, s);
+    g->volume(md, A, none, B, nullptr, r1, MODE_RK, s);
+    g->couple(md, B, 1.0, dt, s);
+    g->volume(md, B, A, B, nullptr, r2, MODE_RK, s);
+    g->couple(md, B, 0.5, dt, s);
+    g->volume(md, B, A, A, nullptr, r3, MODE_RK, s);
+  } else {
+    // u -> A, u1 -> B, u2 -> C, u3 -> B, u4 -> A (u is not needed after the
+    // fourth stage), u+ -> A; W carries a53 (u3 - u4) + c53 dt L(u3)
+    const StatePtr Cs = g->C();
+    void *W = g->W();
+    double c[5];
+    rk54_times(c);
+    RkArgs r1, r2, r3, r4, r5;
+    r1.bdt = Rk54::c10 * dt;
+    r2.has_base = 1, r2.a0 = Rk54::a20, r2.bdt = Rk54::c21 * dt;
+    r3.has_base = 1, r3.a0 = Rk54::a30, r3.bdt = Rk54::c32 * dt;
+    r4.has_base = 1, r4.a0 = Rk54::a40, r4.bdt = Rk54::c43 * dt, r4.g = Rk54::a53, r4.ddt = Rk54::c53 * dt;
+    r4.w_out = W;
+    r5.has_base = 1, r5.a0 = Rk54::a52, r5.bdt = Rk54::c54 * dt, r5.w_in = W;
+    g->couple(md, A, c[0], dt, s);
+    g->volume(md, A, none, B, nullptr, r1, MODE_RK, s);
+    g->couple(md, B, c[1], dt, s);
+    g->volume(md, B, A, Cs, nullptr, r2, MODE_RK, s);
+    g->couple(md, Cs, c[2], dt, s);
+    g->volume(md, Cs, A, B, nullptr, r3, MODE_RK, s);
+    g->couple(md, B, c[3], dt, s);
+    g->volume(md, B, A, A, nullptr, r4, MODE_RK, s);
+    g->couple(md, A, c[4], dt, s);
+    g->volume(md, A, Cs, A, nullptr, r5, MODE_RK, s);
+  }
   g->advance(md, dt, s);
 }
 
@@ -550,6 +617,10 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
   if (!(prm->gamma > 1.0) || !(prm->Rgas > 0.0) || !std::isfinite(prm->omega) ||
       (prm->viscous && (!(prm->mu >= 0.0) || !(prm->prandtl > 0.0) || !(prm->T_wall > 0.0)))) {
     g_create_error = "invalid gas / flow parameters";
+    return SD_ERR_ARG;
+  }
+  if (prm->rk_stages != 0 && prm->rk_stages != 3 && prm->rk_stages != 5) {
+    g_create_error = "rk_stages must be 0 or 3 (SSP-RK3) or 5 (SSP-RK(5,4))";
     return SD_ERR_ARG;
   }
   if (prm->precision != SD_PREC_FP64 && prm->precision != SD_PREC_FP32) {
@@ -596,6 +667,7 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
     md.viscous = prm->viscous;
     md.r_interface = m->r_interface;
     if ((ce = alloc_buffers(h, h->zone_v, h->curved_v))) rc = cuda_fail(h, ce, "device buffers");
+    if (!rc && prm->rk_stages == 5 && (ce = h->eng->alloc_rk54())) rc = cuda_fail(h, ce, "stage buffers");
   }
   if (!rc && (ce = h->eng->init(hb, h->md, h->stream))) rc = cuda_fail(h, ce, "engine init");
   if (!rc && (ce = cudaGetLastError())) rc = cuda_fail(h, ce, "geometry kernels");
@@ -701,7 +773,7 @@ int sd_residual(sd_handle *h, double *R, int on_device) {
   const StatePtr none{nullptr, nullptr};
   h->eng->trace(h->md, h->eng->A(), h->stream);
   h->eng->couple(h->md, h->eng->A(), 0.0, 0.0, h->stream);
-  h->eng->volume(h->md, h->eng->A(), none, none, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
+  h->eng->volume(h->md, h->eng->A(), none, none, dst, RkArgs(), MODE_RESIDUAL, h->stream);
   if ((e = cudaGetLastError())) return cuda_fail(h, e, "residual kernels");
   h->traces_valid = true;
   if (!on_device) {
@@ -801,7 +873,11 @@ int sd_profile_step(sd_handle *h, double dt, int reps, double *ms) {
       cudaEventRecord(ev[2], h->stream);
       h->eng->mortars(h->md, h->stream);
       cudaEventRecord(ev[3], h->stream);
-      h->eng->volume(h->md, qin, qb, qo, nullptr, al[k], be[k], dt, MODE_RK, h->stream);
+      RkArgs rk;
+      rk.has_base = k > 0;
+      rk.a0 = al[k];
+      rk.bdt = be[k] * dt;
+      h->eng->volume(h->md, qin, qb, qo, nullptr, rk, MODE_RK, h->stream);
       cudaEventRecord(ev[4], h->stream);
       if ((e = cudaEventSynchronize(ev[4]))) break;
       for (int c = 0; c < 4; ++c) {
@@ -1168,7 +1244,7 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   h->eng->clock_merge_into(md, 0.0, 0.0, (int *)(b + o_wi), (double *)(b + o_wd), h->stream);
   h->eng->faces(md, h->eng->A(), h->stream);
   h->eng->mortars(md, h->stream);
-  h->eng->volume(md, h->eng->A(), none, none, dst, 0.0, 1.0, 0.0, MODE_RESIDUAL, h->stream);
+  h->eng->volume(md, h->eng->A(), none, none, dst, RkArgs(), MODE_RESIDUAL, h->stream);
   if ((e = cudaGetLastError())) return cuda_fail(h, e, "sd_residual_noalloc kernels");
   h->traces_valid = true;
   if (!on_device) e = cudaMemcpyAsync(R, dst, state_bytes(h), cudaMemcpyDeviceToHost, h->stream);

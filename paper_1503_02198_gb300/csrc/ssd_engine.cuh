@@ -944,7 +944,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-template <typename T, int N, bool OTF>
+template <typename T, int N, bool OTF, bool AUX = false>
 struct VolCfg {
   static constexpr int NN = N * N;
   static constexpr bool FF = std::is_same<T, float>::value;  // double-float state
@@ -961,8 +961,9 @@ struct VolCfg {
   static constexpr int STAGE = ((O_EF + EFB) + 127) / 128 * 128;
   // single-buffered part (needed only by the Runge-Kutta phase): state lo,
   // base state hi and lo; loaded at the start of each tile behind the flux phase
-  static constexpr int O_QLO = 2 * STAGE, O_NHI = O_QLO + QLO, O_NLO = O_NHI + QHI;
-  static constexpr int SINGLE_END = ((O_NLO + QLO) + 127) / 128 * 128;
+  static constexpr int AUXB = AUX ? QHI : 0;  // increment carried from an earlier stage
+  static constexpr int O_QLO = 2 * STAGE, O_NHI = O_QLO + QLO, O_NLO = O_NHI + QHI, O_AUX = O_NLO + QLO;
+  static constexpr int SINGLE_END = ((O_AUX + AUXB) + 127) / 128 * 128;
   // work arrays
   static constexpr int O_RF = SINGLE_END, O_RG = O_RF + QHI, O_IJ = O_RG + QHI;
   static constexpr int O_BAR = ((O_IJ + EPB * NN * (int)sizeof(T)) + 15) / 16 * 16;
@@ -997,11 +998,17 @@ __device__ __forceinline__ bool cta_wait(uint64_t *bar, uint32_t parity) {
   return __syncthreads_and(ok) != 0;
 }
 
-template <typename T, int N, int MODE, bool OTF>
-__global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS, VolCfg<T, N, OTF>::MINB)
-    k_volume(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, double alpha, double beta,
-             double dt, int ntiles, float af, float bdt) {
-  using C = VolCfg<T, N, OTF>;
+// stage coefficients in the compute type
+template <typename T>
+struct RkCoef {
+  T a0, bdt, g, ddt;
+};
+
+template <typename T, int N, int MODE, bool OTF, bool AUX>
+__global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, OTF, AUX>::MINB)
+    k_volume(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
+             T *w_out, const T *w_in, int ntiles) {
+  using C = VolCfg<T, N, OTF, AUX>;
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
   constexpr bool FF = C::FF;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1010,9 +1017,9 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS, VolCfg<T, N, OTF>:
   T(*sRG)[4][NN] = (T(*)[4][NN])(smem + C::O_RG);
   T(*sIJ)[NN] = (T(*)[NN])(smem + C::O_IJ);
   const VolBasis<T, N> &B = cVB<T, N>;
-  const bool use_base = MODE == MODE_RK && alpha != 0.0;
+  const bool use_base = MODE == MODE_RK && has_base;
   const uint32_t txA = C::QHI + C::CFB + C::EGB + C::EFB;
-  const uint32_t txB = MODE == MODE_RK ? C::QLO + (use_base ? C::QHI + C::QLO : 0) : 0;
+  const uint32_t txB = MODE == MODE_RK ? C::QLO + (use_base ? C::QHI + C::QLO : 0) + C::AUXB : 0;
   const T cth = pick<T>(md.clk->c, md.clk->cf), sth = pick<T>(md.clk->s, md.clk->sf);
   const T gm1 = pick<T>(md.gamma, md.gamma_f) - T(1);
 
@@ -1033,6 +1040,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS, VolCfg<T, N, OTF>:
       bulk_g2s(smem + C::O_NHI, (const T *)base.hi + e0 * 4 * NN, C::QHI, &bar[2]);
       if (FF) bulk_g2s(smem + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QLO, &bar[2]);
     }
+    if (AUX) bulk_g2s(smem + C::O_AUX, w_in + e0 * 4 * NN, C::AUXB, &bar[2]);
   };
 
   if (threadIdx.x == 0) {
@@ -1152,16 +1160,20 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS, VolCfg<T, N, OTF>:
 #pragma unroll
         for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
       } else if (!FF) {
-        // FP64: Shu-Osher combination alpha Q_n + beta (Q_k + dt R)
+        // FP64: inc = a0 (Q_base - Q_k) + w_in + bdt R;  Q_out = Q_k + inc
         const double(*sN)[4][NN] = (const double(*)[4][NN])(smem + C::O_NHI);
+        const double(*sW)[4][NN] = (const double(*)[4][NN])(smem + C::O_AUX);
         double *qo = (double *)out.hi;
         double qn[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-          double val = beta * ((double)sQ[l2][v][sp] + dt * R);
-          if (use_base) val = alpha * sN[l2][v][sp] + val;
-          qn[v] = val;
+          const double qk = (double)sQ[l2][v][sp];
+          double inc = (double)rk.bdt * R;
+          if (use_base) inc += (double)rk.a0 * (sN[l2][v][sp] - qk);
+          if (AUX) inc += sW[l2][v][sp];
+          qn[v] = qk + inc;
+          if (w_out) w_out[gi + v * NN] = (T)((double)rk.ddt * R - (double)rk.g * inc);
         }
         const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
         bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
@@ -1171,20 +1183,22 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS, VolCfg<T, N, OTF>:
           sQ[l2][v][sp] = (T)qn[v];
         }
       } else {
-        // FP32 with a double-float state: the same combination written as
-        // Q_k + [alpha (Q_n - Q_k) + beta dt R] (alpha + beta = 1); the bracket
-        // is an O(dt) increment formed in float, added to Q_k exactly (two-sum)
+        // FP32 with a double-float state: the O(dt) increment
+        // inc = a0 (Q_base - Q_k) + w_in + bdt R is formed in float and added to
+        // Q_k exactly (two-sum), so the state keeps ~48 significant bits
         const float(*sKL)[4][NN] = (const float(*)[4][NN])(smem + C::O_QLO);
         const float(*sNH)[4][NN] = (const float(*)[4][NN])(smem + C::O_NHI);
         const float(*sNL)[4][NN] = (const float(*)[4][NN])(smem + C::O_NLO);
+        const float(*sW)[4][NN] = (const float(*)[4][NN])(smem + C::O_AUX);
         float *oh = (float *)out.hi, *ol = (float *)out.lo;
         float hv[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
           const float h = (float)sQ[l2][v][sp], l = sKL[l2][v][sp];
-          float inc = bdt * R;
-          if (use_base) inc = fmaf(af, (sNH[l2][v][sp] - h) + (sNL[l2][v][sp] - l), inc);
+          float inc = (float)rk.bdt * R;
+          if (use_base) inc = fmaf((float)rk.a0, (sNH[l2][v][sp] - h) + (sNL[l2][v][sp] - l), inc);
+          if (AUX) inc += sW[l2][v][sp];
           float sum, err;
           two_sum(h, inc, sum, err);
           err += l;
@@ -1192,6 +1206,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF>::THREADS, VolCfg<T, N, OTF>:
           oh[gi + v * NN] = H;
           ol[gi + v * NN] = err - (H - sum);
           hv[v] = H;
+          if (w_out) w_out[gi + v * NN] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
         }
         const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) * __frcp_rn(hv[0]));
         bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
@@ -1244,10 +1259,11 @@ struct EngineImpl : Engine {
   double *dXs = nullptr, *dXf = nullptr;
   int *scratch_i = nullptr;
   double *scratch_d = nullptr;
-  void *sA[2] = {nullptr, nullptr}, *sB[2] = {nullptr, nullptr};
-  size_t nval = 0;
+  void *sA[2] = {nullptr, nullptr}, *sB[2] = {nullptr, nullptr}, *sC[2] = {nullptr, nullptr};
+  void *sW = nullptr;
+  size_t nval = 0, nalloc_vals = 0;
   int merge_smem = 0;
-  int grid_res = 1, grid_rk = 1;  // persistent grid sizes of the volume kernel
+  int grid_res = 1, grid_rk = 1, grid_aux = 1;  // persistent grid sizes of the volume kernel
   int sms = 1, occ_rk = 1;         // SM count, resident volume CTAs per SM
   int face_block = 256;            // block size of the conforming-face kernel
 
@@ -1259,7 +1275,9 @@ struct EngineImpl : Engine {
     for (int k = 0; k < 2; ++k) {
       cudaFree(sA[k]);
       cudaFree(sB[k]);
+      cudaFree(sC[k]);
     }
+    cudaFree(sW);
   }
   size_t geo_words() const override { return GeoLayout<N>::G; }
   size_t compute_word() const override { return sizeof(T); }
@@ -1268,6 +1286,7 @@ struct EngineImpl : Engine {
   cudaError_t alloc_state(int E, int Epad) override {
     nval = (size_t)E * 4 * N * N;
     const size_t nalloc = (size_t)Epad * 4 * N * N;
+    nalloc_vals = nalloc;
     cudaError_t e;
     if ((e = cudaMalloc(&sA[0], sizeof(T) * nalloc))) return e;
     if ((e = cudaMalloc(&sB[0], sizeof(T) * nalloc))) return e;
@@ -1335,21 +1354,29 @@ struct EngineImpl : Engine {
       int dev = 0, occ0 = 0, occ1 = 0;
       if ((err = cudaGetDevice(&dev))) return err;
       if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return err;
-      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RESIDUAL, OTF>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)))
+      int occ2 = 0;
+      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RESIDUAL, OTF, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, VolCfg<T, N, OTF, false>::SMEM)))
         return err;
-      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      C::SMEM)))
+      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      VolCfg<T, N, OTF, false>::SMEM)))
         return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_volume<T, N, MODE_RESIDUAL, OTF>, C::THREADS,
-                                                               C::SMEM)))
+      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      VolCfg<T, N, OTF, true>::SMEM)))
         return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_volume<T, N, MODE_RK, OTF>, C::THREADS,
-                                                               C::SMEM)))
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_volume<T, N, MODE_RESIDUAL, OTF, false>,
+                                                               C::THREADS, VolCfg<T, N, OTF, false>::SMEM)))
+        return err;
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_volume<T, N, MODE_RK, OTF, false>, C::THREADS,
+                                                               VolCfg<T, N, OTF, false>::SMEM)))
+        return err;
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_volume<T, N, MODE_RK, OTF, true>, C::THREADS,
+                                                               VolCfg<T, N, OTF, true>::SMEM)))
         return err;
       grid_res = std::max(1, occ0) * sms;
       occ_rk = std::max(1, occ1);
       grid_rk = occ_rk * sms;
+      grid_aux = std::max(1, occ2) * sms;
     }
     if (md.nTab > 0) k_geo<T, N><<<(md.nTab + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
     k_egeo<T, N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
@@ -1403,28 +1430,46 @@ struct EngineImpl : Engine {
     }
   }
 
-  void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, double alpha, double beta,
-              double dt, int mode, cudaStream_t s) override {
-    using C = VolCfg<T, N, OTF>;
+  template <int MODE, bool AUX>
+  void launch_volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk,
+                     int grid, cudaStream_t s) {
+    using C = VolCfg<T, N, OTF, AUX>;
     const int ntiles = (md.E + C::EPB - 1) / C::EPB;
+    const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
+    k_volume<T, N, MODE, OTF, AUX><<<std::min(ntiles, grid), C::THREADS, C::SMEM, s>>>(
+        md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
+  }
+
+  void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk, int mode,
+              cudaStream_t s) override {
     if (md.viscous) {
       constexpr int EPBv = VisCfg<N>::EPB;
       const int grid = (md.E + EPBv - 1) / EPBv;
+      const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
       if (mode == MODE_RESIDUAL)
-        k_volume_visc<T, N, MODE_RESIDUAL, OTF><<<grid, VisCfg<N>::THREADS, 0, s>>>(md, in, base, out, R, alpha,
-                                                                                    beta, dt);
+        k_volume_visc<T, N, MODE_RESIDUAL, OTF><<<grid, VisCfg<N>::THREADS, 0, s>>>(
+            md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
       else
-        k_volume_visc<T, N, MODE_RK, OTF><<<grid, VisCfg<N>::THREADS, 0, s>>>(md, in, base, out, R, alpha, beta,
-                                                                              dt);
+        k_volume_visc<T, N, MODE_RK, OTF><<<grid, VisCfg<N>::THREADS, 0, s>>>(
+            md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
       return;
     }
-    if (mode == MODE_RESIDUAL)
-      k_volume<T, N, MODE_RESIDUAL, OTF><<<std::min(ntiles, grid_res), C::THREADS, C::SMEM, s>>>(
-          md, in, base, out, R, alpha, beta, dt, ntiles, (float)alpha, (float)(beta * dt));
-    else
-      k_volume<T, N, MODE_RK, OTF><<<std::min(ntiles, grid_rk), C::THREADS, C::SMEM, s>>>(
-          md, in, base, out, R, alpha, beta, dt, ntiles, (float)alpha, (float)(beta * dt));
+    if (mode == MODE_RESIDUAL) launch_volume<MODE_RESIDUAL, false>(md, in, base, out, R, rk, grid_res, s);
+    else if (rk.w_in) launch_volume<MODE_RK, true>(md, in, base, out, R, rk, grid_aux, s);
+    else launch_volume<MODE_RK, false>(md, in, base, out, R, rk, grid_rk, s);
   }
+
+  cudaError_t alloc_rk54() override {
+    if (sC[0]) return cudaSuccess;
+    const size_t nalloc = nalloc_vals;
+    cudaError_t e;
+    if ((e = cudaMalloc(&sC[0], sizeof(T) * nalloc))) return e;
+    if (OTF && (e = cudaMalloc(&sC[1], sizeof(float) * nalloc))) return e;
+    if ((e = cudaMalloc(&sW, sizeof(T) * nalloc))) return e;
+    return cudaSuccess;
+  }
+  StatePtr C() const override { return StatePtr{sC[0], sC[1]}; }
+  void *W() const override { return sW; }
 
   int tile_elems() const override { return VolCfg<T, N, OTF>::EPB; }
 

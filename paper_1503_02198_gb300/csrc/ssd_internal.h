@@ -90,6 +90,17 @@ struct MeshDev {
 
 enum { MODE_RESIDUAL = 0, MODE_RK = 1 };
 
+// One Runge-Kutta stage in increment form: with R = L(in),
+//   inc = a0 (base - in) + w_in + bdt R,   out = in + inc,
+//   w_out = -g inc + ddt R   (an O(dt) increment kept for a later stage).
+// SSP-RK3 and the five-stage SSP-RK(5,4) are sequences of such stages.
+struct RkArgs {
+  double a0 = 0.0, bdt = 0.0, g = 0.0, ddt = 0.0;
+  int has_base = 0;
+  const void *w_in = nullptr;  // compute-precision [E][4][N][N] or null
+  void *w_out = nullptr;       // compute-precision [E][4][N][N] or null
+};
+
 // Per-precision engine: T = double (FP64 path) or float (FP32 path).
 struct Engine {
   virtual ~Engine() {}
@@ -129,9 +140,13 @@ struct Engine {
     mortars(md, s);
   }
   // divergence; MODE_RESIDUAL writes R (FP64), MODE_RK writes the stage
-  // Qout = alpha Qbase + beta (Qin + dt R) and its face traces
-  virtual void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, double alpha,
-                      double beta, double dt, int mode, cudaStream_t s) = 0;
+  // described by rk (see RkArgs) and the face traces of its result
+  virtual void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk,
+                      int mode, cudaStream_t s) = 0;
+  // the extra buffers of the five-stage scheme: a third state and an increment
+  virtual cudaError_t alloc_rk54() = 0;
+  virtual StatePtr C() const = 0;
+  virtual void *W() const = 0;
   virtual void advance(const MeshDev &md, double dt, cudaStream_t s) = 0;
   virtual void sp_coords(const MeshDev &md, double t, double cx, double cy, double *xy, cudaStream_t s) = 0;
 };

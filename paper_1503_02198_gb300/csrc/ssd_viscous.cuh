@@ -304,8 +304,8 @@ __global__ void k_bface_visc(MeshDev md) {
 
 template <typename T, int N, int MODE, bool OTF>
 __global__ void __launch_bounds__(VisCfg<N>::THREADS)
-    k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, double alpha, double beta,
-                  double dt) {
+    k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
+                  T *w_out, const T *w_in) {
   constexpr int EPB = VisCfg<N>::EPB, NT = VisCfg<N>::THREADS, NN = N * N;
   constexpr bool FF = std::is_same<T, float>::value;
   __shared__ T sQ[EPB][4][NN];
@@ -390,7 +390,6 @@ __global__ void __launch_bounds__(VisCfg<N>::THREADS)
   }
   __syncthreads();
   bool bad = false;
-  const T bdt = (T)(beta * dt), af = (T)alpha;
   for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
     const int l2 = idx / NN, sp = idx - l2 * NN;
     ElemGeo<T, N, OTF> G;
@@ -404,10 +403,14 @@ __global__ void __launch_bounds__(VisCfg<N>::THREADS)
       double qn[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
+        const size_t ii = gi + v * NN;
         const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-        double val = beta * ((double)sQ[l2][v][sp] + dt * R);
-        if (alpha != 0.0) val = alpha * ((const double *)base.hi)[gi + v * NN] + val;
-        qn[v] = val;
+        const double qk = (double)sQ[l2][v][sp];
+        double inc = (double)rk.bdt * R;
+        if (has_base) inc += (double)rk.a0 * (((const double *)base.hi)[ii] - qk);
+        if (w_in) inc += (double)w_in[ii];
+        qn[v] = qk + inc;
+        if (w_out) w_out[ii] = (T)((double)rk.ddt * R - (double)rk.g * inc);
       }
       const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
       bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
@@ -423,9 +426,10 @@ __global__ void __launch_bounds__(VisCfg<N>::THREADS)
         const size_t ii = gi + v * NN;
         const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
         const float h = (float)sQ[l2][v][sp], l = ((const float *)in.lo)[ii];
-        float inc = (float)bdt * R;
-        if (alpha != 0.0)
-          inc = fmaf((float)af, (((const float *)base.hi)[ii] - h) + (((const float *)base.lo)[ii] - l), inc);
+        float inc = (float)rk.bdt * R;
+        if (has_base)
+          inc = fmaf((float)rk.a0, (((const float *)base.hi)[ii] - h) + (((const float *)base.lo)[ii] - l), inc);
+        if (w_in) inc += (float)w_in[ii];
         float sum, err;
         two_sum(h, inc, sum, err);
         err += l;
@@ -433,6 +437,7 @@ __global__ void __launch_bounds__(VisCfg<N>::THREADS)
         ((float *)out.hi)[ii] = H;
         ((float *)out.lo)[ii] = err - (H - sum);
         hv[v] = H;
+        if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
       }
       const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
       bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);

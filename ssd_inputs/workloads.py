@@ -21,6 +21,7 @@ class FlowParams:
     omega: float = 0.0
     viscous: int = 0
     T_wall: float = 1.0
+    rk_stages: int = 3
 
 
 @dataclass

@@ -234,3 +234,20 @@ def test_full_size_rotor_step_fp32(ssd, rotor_full):
     q_ref, _ = o.step(Q, 0.0, w.cfl_dt, 1)
     _check(s.sd_get_state(), q_ref, TOL32_STATE)
     s.close()
+
+
+@pytest.mark.parametrize("precision,N", [(0, 3), (0, 5), (1, 4)])
+def test_steps_rk54(ssd, oracle_mod, precision, N):
+    # the five-stage fourth-order SSP Runge-Kutta of Sec. 4
+    m = small_rotor(shift_L=0.02)
+    prm = FlowParams(omega=math.pi / 4, rk_stages=5)
+    s, o = _pair(ssd, oracle_mod, m, N, prm, precision=precision)
+    Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=2.0))
+    dt = 2e-3
+    s.sd_set_state(Q)
+    s.sd_set_time(0.05)
+    s.sd_step(dt, 4)
+    s.sd_sync()
+    q_ref, t_ref = o.step(Q, 0.05, dt, 4, rk_stages=5)
+    assert abs(s.sd_get_time() - t_ref) < 1e-15
+    _check(s.sd_get_state(), q_ref, TOL64 if precision == 0 else TOL32_STATE)

@@ -110,3 +110,17 @@ def test_couette_accuracy_order(ssd):
         errs.append(err)
     order = math.log2(errs[0] / errs[1])
     assert order > N - 0.5, (errs, order)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_couette_rk54_steps(ssd, oracle_mod, precision):
+    w = build_workload("couette_n3")
+    prm = w.params
+    prm.rk_stages = 5
+    s, o = ssd.Solver(w.mesh, w.N - 1, prm, precision=precision), oracle_mod.Oracle(w.mesh, w.N, prm)
+    Q = o.state_from(lambda x, y: fields.uniform(x, y, rho=1.0, p=prm.Rgas * prm.T_wall))
+    s.sd_set_state(Q)
+    s.sd_step(w.cfl_dt, 20)
+    s.sd_sync()
+    q_ref, _ = o.step(Q, 0.0, w.cfl_dt, 20, rk_stages=5)
+    _check(s.sd_get_state(), q_ref, TOL64 if precision == 0 else TOL32_STATE)

@@ -228,3 +228,41 @@ def test_ssp_rk3_is_third_order_in_time(oracle_mod):
         errs.append(np.abs(q - ref).max())
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert (rates > 2.7).all(), (errs, rates)
+
+
+def test_ssp_rk54_order_conditions(oracle_mod):
+    # Sec. 4 uses a five-stage fourth-order SSP Runge-Kutta method; its
+    # coefficients (not printed in the paper) must satisfy the eight Butcher
+    # order conditions up to order four.
+    A, b, c = oracle_mod.rk54_tableau()
+    assert np.allclose(A.sum(axis=1), c, atol=1e-15)
+    assert np.allclose(np.triu(A), 0.0)  # explicit
+    conds = [
+        (b.sum(), 1.0),
+        (b @ c, 1 / 2),
+        (b @ c ** 2, 1 / 3),
+        (b @ (A @ c), 1 / 6),
+        (b @ c ** 3, 1 / 4),
+        (b @ (c * (A @ c)), 1 / 8),
+        (b @ (A @ c ** 2), 1 / 12),
+        (b @ (A @ (A @ c)), 1 / 24),
+    ]
+    for got, want in conds:
+        assert abs(got - want) < 5e-14, (got, want)
+    # SSP: all Shu-Osher weights are non-negative, i.e. b >= 0 and A >= 0
+    assert (b >= 0).all() and (A >= -1e-15).all()
+
+
+def test_ssp_rk54_is_fourth_order_in_time(oracle_mod):
+    m = small_rotor()
+    o = oracle_mod.Oracle(m, 3, FlowParams(omega=1.3))
+    Q0 = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=2.0))
+    T = 0.032
+    ref, _ = o.step(Q0, 0.0, T / 64, 64, rk_stages=5)
+    errs = []
+    for n in (2, 4, 8):
+        q, t = o.step(Q0, 0.0, T / n, n, rk_stages=5)
+        assert abs(t - T) < 1e-15
+        errs.append(np.abs(q - ref).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert (rates > 3.6).all(), (errs, rates)
