@@ -95,6 +95,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic of k_volume per launch (read + write, averaged over the three
+# stage launches) from the ncu capture summarised in
+# profiles/k_volume_fp32_rotor_n6.md; valid only for the kernel source it was
+# taken on (SHA-256 of csrc/ssd_engine.cuh), otherwise reported as null.
+PROFILED_TRAFFIC = {"bytes": (389.09e6 + 327.88e6 + 673.48e6 + 330.19e6 + 673.48e6 + 329.34e6) / 3,
+                    "engine_sha256": "abb8dae592ed5f8414889d2549d4bf22e936237da6b5470d87fc79c80ff663a0"}
+
+
+def profiled_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1503_02198_gb300", "csrc", "ssd_engine.cuh")
+    try:
+        h = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return PROFILED_TRAFFIC["bytes"] if h == PROFILED_TRAFFIC["engine_sha256"] else None
+
+
 def volume_bytes_per_element(N, w_c):
     """Algorithmic bytes one volume launch moves per element (see design
     notes): FP64 state read + write, the Runge-Kutta base read on two of the
@@ -350,8 +368,9 @@ def main():
     vol_bytes = volume_bytes_per_element(N, w_c) * E
     peak, peak_src = _peaks()
     achieved = vol_bytes / (prof["volume"] * 1e-3) / 1e9
+    traffic = profiled_traffic() if (args.workload == "rotor_n6" and prec == ssd.SD_PREC_FP32) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_volume", "peak_source": peak_src + " hbm_gbs (burst)",
+                "traffic": traffic, "kernel": "k_volume", "peak_source": peak_src + " hbm_gbs (burst)",
                 "algorithmic_bytes_per_launch": vol_bytes}
     try:
         fp32_peak = solver.sd_fma_peak(ssd.SD_PREC_FP32)

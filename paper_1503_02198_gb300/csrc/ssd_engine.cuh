@@ -48,6 +48,8 @@ struct VolBasis {
   T Dm[N * (N + 1)];  // l'_{i+1/2}(X_k) [k][i]
   T H0[N], H1[N];     // h_k(0), h_k(1)
   T Xs[N], Xf[N + 1]; // solution and flux points
+  // the same weights duplicated into float pairs for packed FP32x2 FMAs
+  float2 Hf2[(N + 1) * N], Dm2[N * (N + 1)], H02[N], H12[N];
 };
 
 template <int N>
@@ -1087,6 +1089,70 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
     if (le < ne) {
       ElemGeo<T, N, OTF> G;
       G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, cth, sth);
+      if constexpr (FF) {
+        // FP32: variables packed in pairs (rho, rho u), (rho v, E); every
+        // interpolation and divergence FMA is a packed FP32x2 FMA
+        float2 q2[2][N], acc2[2][N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const int sp = d == 0 ? mline * N + k : k * N + mline;
+          q2[0][k] = make_float2(sQ[le][0][sp], sQ[le][1][sp]);
+          q2[1][k] = make_float2(sQ[le][2][sp], sQ[le][3][sp]);
+          acc2[0][k] = make_float2(0.f, 0.f);
+          acc2[1][k] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i <= N; ++i) {
+          float2 f01, f23;
+          if (i == 0 || i == N) {
+            const int face = d == 0 ? (i == 0 ? 3 : 1) : (i == 0 ? 0 : 2);
+            f01 = make_float2(sCF[le][(face * 4 + 0) * N + mline], sCF[le][(face * 4 + 1) * N + mline]);
+            f23 = make_float2(sCF[le][(face * 4 + 2) * N + mline], sCF[le][(face * 4 + 3) * N + mline]);
+          } else {
+            float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              const float2 h = B.Hf2[i * N + k];
+              s01 = __ffma2_rn(q2[0][k], h, s01);
+              s23 = __ffma2_rn(q2[1][k], h, s23);
+            }
+            const float qf[4] = {s01.x, s01.y, s23.x, s23.y};
+            T vx, vy, vg;
+            if (d == 0) G.xi_fp(i, mline, vx, vy, vg);
+            else G.eta_fp(mline, i, vx, vy, vg);
+            float f[4];
+            point_flux(qf, (float)vx, (float)vy, (float)vg, (float)gm1, f);
+            f01 = make_float2(f[0], f[1]);
+            f23 = make_float2(f[2], f[3]);
+          }
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const float2 w = B.Dm2[k * (N + 1) + i];
+            acc2[0][k] = __ffma2_rn(w, f01, acc2[0][k]);
+            acc2[1][k] = __ffma2_rn(w, f23, acc2[1][k]);
+          }
+        }
+        if (d == 0) {
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const int sp = mline * N + k;
+            sRF[le][0][sp] = acc2[0][k].x;
+            sRF[le][1][sp] = acc2[0][k].y;
+            sRF[le][2][sp] = acc2[1][k].x;
+            sRF[le][3][sp] = acc2[1][k].y;
+            sIJ[le][sp] = G.inv_jac(k, mline);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const int sp = k * N + mline;
+            sRG[le][0][sp] = acc2[0][k].x;
+            sRG[le][1][sp] = acc2[0][k].y;
+            sRG[le][2][sp] = acc2[1][k].x;
+            sRG[le][3][sp] = acc2[1][k].y;
+          }
+        }
+      } else {
       T q[4][N];
 #pragma unroll
       for (int k = 0; k < N; ++k)
@@ -1137,6 +1203,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
         for (int k = 0; k < N; ++k)
 #pragma unroll
           for (int v = 0; v < 4; ++v) sRG[le][v][k * N + mline] = acc[v][k];
+      }
       }
     }
     // the single-buffered part (state lo, base state) must have landed too
@@ -1222,17 +1289,35 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
       if (le < ne) {
         T *tr = (T *)md.TR + (size_t)(e0 + le) * 16 * N;
         const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+        if constexpr (FF) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          T a0 = 0, a1 = 0;
+          for (int vp = 0; vp < 2; ++vp) {
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const T qk = d == 0 ? sQ[le][v][mline * N + k] : sQ[le][v][k * N + mline];
-            a0 += qk * B.H0[k];
-            a1 += qk * B.H1[k];
+            for (int k = 0; k < N; ++k) {
+              const int sp = d == 0 ? mline * N + k : k * N + mline;
+              const float2 qk = make_float2(sQ[le][2 * vp][sp], sQ[le][2 * vp + 1][sp]);
+              a0 = __ffma2_rn(qk, B.H02[k], a0);
+              a1 = __ffma2_rn(qk, B.H12[k], a1);
+            }
+            tr[(fa * 4 + 2 * vp) * N + mline] = a0.x;
+            tr[(fa * 4 + 2 * vp + 1) * N + mline] = a0.y;
+            tr[(fb * 4 + 2 * vp) * N + mline] = a1.x;
+            tr[(fb * 4 + 2 * vp + 1) * N + mline] = a1.y;
           }
-          tr[(fa * 4 + v) * N + mline] = a0;
-          tr[(fb * 4 + v) * N + mline] = a1;
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            T a0 = 0, a1 = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              const T qk = d == 0 ? sQ[le][v][mline * N + k] : sQ[le][v][k * N + mline];
+              a0 += qk * B.H0[k];
+              a1 += qk * B.H1[k];
+            }
+            tr[(fa * 4 + v) * N + mline] = a0;
+            tr[(fb * 4 + v) * N + mline] = a1;
+          }
         }
       }
     }
@@ -1329,6 +1414,14 @@ struct EngineImpl : Engine {
       mb.cden[k] = hb.cden[k];
     }
     for (int k = 0; k <= N; ++k) vb.Xf[k] = (T)hb.Xf[k];
+    for (int k = 0; k < (N + 1) * N; ++k) {
+      vb.Hf2[k] = make_float2((float)hb.Hf[k], (float)hb.Hf[k]);
+      vb.Dm2[k] = make_float2((float)hb.Dm[k], (float)hb.Dm[k]);
+    }
+    for (int k = 0; k < N; ++k) {
+      vb.H02[k] = make_float2((float)hb.H0[k], (float)hb.H0[k]);
+      vb.H12[k] = make_float2((float)hb.H1[k], (float)hb.H1[k]);
+    }
     for (int k = 0; k < N * N; ++k) {
       mb.Hz[k] = hb.Hz[k];
       mb.Minv[k] = hb.Minv[k];
