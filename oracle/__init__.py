@@ -39,7 +39,7 @@ def lib():
         build()
         L = ctypes.CDLL(_LIB_PATH)
         L.or_create.restype = ctypes.c_void_p
-        L.or_create.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _ip, ctypes.c_int, _ip, ctypes.c_int,
+        L.or_create.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _ip, _ip, ctypes.c_int, _ip, ctypes.c_int,
                                 _ip, ctypes.c_int, _ip, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_int, _dp, ctypes.c_char_p, ctypes.c_int]
         L.or_destroy.argtypes = [ctypes.c_void_p]
@@ -105,7 +105,8 @@ def rk54_tableau():
 
 def params_array(params) -> np.ndarray:
     return np.array([params.gamma, params.Rgas, params.mu, params.prandtl, params.omega,
-                     float(params.viscous), params.T_wall], dtype=np.float64)
+                     float(params.viscous), params.T_wall, params.rho_inf, params.u_inf, params.v_inf,
+                     params.p_inf], dtype=np.float64)
 
 
 class Oracle:
@@ -127,13 +128,15 @@ class Oracle:
         en = arr(mesh["elem_nodes"], np.int32)
         zone = arr(mesh["elem_zone"], np.int32)
         arc = arr(mesh["edge_arc"], np.int32)
+        enode = arr(mesh["edge_nodes"], np.int32) if "edge_nodes" in mesh else None
         bf = arr(mesh["bfaces"], np.int32)
         pf = arr(mesh["pfaces"], np.int32)
         Lf = arr(mesh["ifaces_L"], np.int32)
         Rf = arr(mesh["ifaces_R"], np.int32)
         prm = arr(params_array(params), np.float64)
         err = ctypes.create_string_buffer(256)
-        self._h = L.or_create(len(xy), _d(xy), self.E, _i(en), _i(zone), _i(arc), len(bf), _i(bf), len(pf),
+        self._h = L.or_create(len(xy), _d(xy), self.E, _i(en), _i(zone), _i(arc),
+                              _i(enode) if enode is not None else None, len(bf), _i(bf), len(pf),
                               _i(pf), len(Lf), _i(Lf), len(Rf), _i(Rf), float(mesh["center"][0]),
                               float(mesh["center"][1]), float(mesh["r_interface"]), N, _d(prm), err, 256)
         if not self._h:

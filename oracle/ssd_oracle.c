@@ -36,7 +36,20 @@
  *   - conforming viscous coupling: common Q = average, common viscous flux =
  *     average of both sides' viscous flux evaluated with the common Q;
  *   - isothermal moving walls through a ghost state (velocity 2 V_w - V,
- *     wall temperature, interior pressure).
+ *     wall temperature, interior pressure);
+ *   - the boundary conditions of the elliptic-cylinder case of Sec. 4
+ *     (slip walls, Dirichlet inlet, fixed-pressure outlet) through ghost
+ *     states as well: slip mirrors the velocity relative to the wall in the
+ *     normal direction, the inlet ghost is the free stream, the outlet ghost is
+ *     the interior state with the free-stream pressure.  For the viscous
+ *     fluxes the common solution at a boundary point is the state on the
+ *     boundary itself (slip: interior density and pressure with the normal
+ *     relative velocity removed; inlet, outlet: the ghost state) and the
+ *     viscous flux uses the interior gradient;
+ *   - curved cells with 12 nodes (Sec. 3.1): an edge may be the cubic
+ *     through its two corners and two edge nodes at face parameter 1/3 and
+ *     2/3; the transfinite map with such edges spans exactly the 12-node
+ *     serendipity cubic element.
  */
 #include <math.h>
 #include <stdio.h>
@@ -53,7 +66,13 @@
 typedef struct {
   double gamma, Rgas, mu, prandtl, omega, T_wall;
   int viscous;
+  double rho_inf, u_inf, v_inf, p_inf; /* free stream (inlet state, outlet pressure) */
 } or_params;
+
+/* boundary tags */
+enum { BC_WALL = 1, BC_SLIP = 2, BC_INLET = 3, BC_OUTLET = 4 };
+/* edge kinds */
+enum { EDGE_STRAIGHT = 0, EDGE_ARC = 1, EDGE_CUBIC = 2 };
 
 enum { FK_NONE = -1, FK_CONF = 0, FK_PERIODIC = 1, FK_BOUNDARY = 2, FK_IFACE_L = 3, FK_IFACE_R = 4 };
 
@@ -65,6 +84,7 @@ typedef struct {
   int nn, ne;
   double *xy;
   int *en, *zone, *arc;
+  int *enode; /* [E][4][2]: edge nodes at face parameter 1/3, 2/3 of cubic edges, or NULL */
   double cx, cy, rI;
   /* per element face e*4+f */
   int *fkind, *fnbr, *frev, *ftag;
@@ -157,8 +177,24 @@ static const int FACE_B[4] = {1, 2, 2, 3}; /* end corner */
  * e(phi0 + d) - e(phi0) = 2 sin(d/2) (-sin(phi0 + d/2), cos(phi0 + d/2)),
  * so the offset keeps full relative precision for short arcs far from the
  * centre. */
-static void edge_curve(const or_mesh *m, double px, double py, double qx, double qy, int arc, double u,
-                       double *ox, double *oy, double *dx, double *dy) {
+static void edge_curve(const or_mesh *m, double px, double py, double qx, double qy, int arc, const int *mid,
+                       double u, double *ox, double *oy, double *dx, double *dy) {
+  if (arc == EDGE_CUBIC) {
+    /* cubic Lagrange interpolation through P, M1, M2, Q at u = 0, 1/3, 2/3, 1,
+     * written as offsets from P */
+    static const double un[4] = {0.0, 1.0 / 3.0, 2.0 / 3.0, 1.0};
+    double Dx[4] = {0.0, m->xy[2 * mid[0]] - px, m->xy[2 * mid[1]] - px, qx - px};
+    double Dy[4] = {0.0, m->xy[2 * mid[0] + 1] - py, m->xy[2 * mid[1] + 1] - py, qy - py};
+    *ox = *oy = *dx = *dy = 0.0;
+    for (int k = 1; k < 4; ++k) {
+      double l = lag(un, 4, k, u), ld = lag_d(un, 4, k, u);
+      *ox += l * Dx[k];
+      *oy += l * Dy[k];
+      *dx += ld * Dx[k];
+      *dy += ld * Dy[k];
+    }
+    return;
+  }
   if (!arc) {
     *ox = u * (qx - px);
     *oy = u * (qy - py);
@@ -196,11 +232,12 @@ static void map_t0(const or_mesh *m, int e, double xi, double eta, double *g) {
     V[k] = Y[k] - Y[0];
   }
   const int *a = m->arc + 4 * e;
+  const int *md = m->enode ? m->enode + 8 * e : NULL;
   double Bx, By, dBx, dBy, Tx, Ty, dTx, dTy, Lx, Ly, dLx, dLy, Rx, Ry, dRx, dRy;
-  edge_curve(m, X[0], Y[0], X[1], Y[1], a[0], xi, &Bx, &By, &dBx, &dBy);   /* f0, eta = 0 */
-  edge_curve(m, X[1], Y[1], X[2], Y[2], a[1], eta, &Rx, &Ry, &dRx, &dRy);  /* f1, xi = 1 */
-  edge_curve(m, X[3], Y[3], X[2], Y[2], a[2], xi, &Tx, &Ty, &dTx, &dTy);   /* f2, eta = 1 */
-  edge_curve(m, X[0], Y[0], X[3], Y[3], a[3], eta, &Lx, &Ly, &dLx, &dLy);  /* f3, xi = 0 */
+  edge_curve(m, X[0], Y[0], X[1], Y[1], a[0], md ? md + 0 : NULL, xi, &Bx, &By, &dBx, &dBy);  /* f0, eta = 0 */
+  edge_curve(m, X[1], Y[1], X[2], Y[2], a[1], md ? md + 2 : NULL, eta, &Rx, &Ry, &dRx, &dRy); /* f1, xi = 1 */
+  edge_curve(m, X[3], Y[3], X[2], Y[2], a[2], md ? md + 4 : NULL, xi, &Tx, &Ty, &dTx, &dTy);  /* f2, eta = 1 */
+  edge_curve(m, X[0], Y[0], X[3], Y[3], a[3], md ? md + 6 : NULL, eta, &Lx, &Ly, &dLx, &dLy); /* f3, xi = 0 */
   /* edge points relative to corner 0 */
   Rx += U[1]; Ry += V[1];
   Tx += U[3]; Ty += V[3];
@@ -464,7 +501,10 @@ static int setup_interface_side(or_mesh *m, int n, const int *faces, int kind, i
   return 0;
 }
 
-or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *zone, const int *arc, int nb,
+void or_destroy(or_mesh *m);
+
+or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *zone, const int *arc,
+                   const int *enode, int nb,
                    const int *bfaces, int np, const int *pfaces, int nL, const int *Lf, int nR, const int *Rf,
                    double cx, double cy, double rI, int N, const double *prm_in, char *err, int errlen) {
   or_mesh *m = calloc(1, sizeof(or_mesh));
@@ -480,6 +520,11 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
   memcpy(m->zone, zone, sizeof(int) * ne);
   m->arc = malloc(sizeof(int) * 4 * ne);
   memcpy(m->arc, arc, sizeof(int) * 4 * ne);
+  m->enode = NULL;
+  if (enode) {
+    m->enode = malloc(sizeof(int) * 8 * ne);
+    memcpy(m->enode, enode, sizeof(int) * 8 * ne);
+  }
   m->cx = cx;
   m->cy = cy;
   m->rI = rI;
@@ -490,6 +535,10 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
   m->prm.omega = prm_in[4];
   m->prm.viscous = (int)prm_in[5];
   m->prm.T_wall = prm_in[6];
+  m->prm.rho_inf = prm_in[7];
+  m->prm.u_inf = prm_in[8];
+  m->prm.v_inf = prm_in[9];
+  m->prm.p_inf = prm_in[10];
   int nf = 4 * ne;
   m->fkind = malloc(sizeof(int) * nf);
   m->fnbr = malloc(sizeof(int) * nf);
@@ -497,9 +546,22 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
   m->ftag = malloc(sizeof(int) * nf);
   for (int k = 0; k < nf; ++k) { m->fkind[k] = FK_NONE; m->fnbr[k] = -1; m->frev[k] = 0; m->ftag[k] = 0; }
   int rc = 0;
+  /* edge kinds: a cubic edge needs its two edge nodes */
+  for (int k = 0; k < 4 * ne && !rc; ++k) {
+    if (arc[k] < EDGE_STRAIGHT || arc[k] > EDGE_CUBIC) {
+      snprintf(m->err, sizeof m->err, "unknown edge kind");
+      rc = -1;
+    } else if (arc[k] == EDGE_CUBIC &&
+               (!enode || enode[2 * k] < 0 || enode[2 * k] >= nn || enode[2 * k + 1] < 0 || enode[2 * k + 1] >= nn)) {
+      snprintf(m->err, sizeof m->err, "cubic edge without valid edge nodes");
+      rc = -1;
+    }
+  }
   /* boundary faces */
   for (int k = 0; k < nb && !rc; ++k) {
     int ef = 4 * bfaces[3 * k] + bfaces[3 * k + 1];
+    int tag = bfaces[3 * k + 2];
+    if (tag < BC_WALL || tag > BC_OUTLET) { snprintf(m->err, sizeof m->err, "unknown boundary tag"); rc = -1; }
     if (m->fkind[ef] != FK_NONE) { snprintf(m->err, sizeof m->err, "boundary face repeated"); rc = -1; }
     m->fkind[ef] = FK_BOUNDARY;
     m->ftag[ef] = bfaces[3 * k + 2];
@@ -556,6 +618,19 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
         m->fnbr[efA] = efB;
         m->fnbr[efB] = efA;
         m->frev[efA] = m->frev[efB] = (a0 != b0);
+        /* both sides must describe the same curve */
+        int kA = m->arc[efA], kB = m->arc[efB];
+        if (kA != kB) {
+          snprintf(m->err, sizeof m->err, "edge kinds differ across a conforming face");
+          rc = -1;
+        } else if (kA == EDGE_CUBIC) {
+          const int *pA = m->enode + 2 * efA, *pB = m->enode + 2 * efB;
+          int same = m->frev[efA] ? (pA[0] == pB[1] && pA[1] == pB[0]) : (pA[0] == pB[0] && pA[1] == pB[1]);
+          if (!same) {
+            snprintf(m->err, sizeof m->err, "cubic edge nodes differ across a conforming face");
+            rc = -1;
+          }
+        }
         if (m->zone[efA / 4] != m->zone[efB / 4]) {
           snprintf(m->err, sizeof m->err, "conforming face joins two zones");
           rc = -1;
@@ -569,8 +644,16 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
     }
     free(keys);
   }
+  for (int ef = 0; ef < nf && !rc; ++ef) {
+    int k = m->fkind[ef];
+    if ((k == FK_PERIODIC || k == FK_IFACE_L || k == FK_IFACE_R) && m->arc[ef] == EDGE_CUBIC) {
+      snprintf(m->err, sizeof m->err, "periodic and interface faces cannot be cubic edges");
+      rc = -1;
+    }
+  }
   if (rc) {
     if (err) snprintf(err, errlen, "%s", m->err);
+    or_destroy(m);
     return NULL;
   }
   return m;
@@ -578,7 +661,7 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
 
 void or_destroy(or_mesh *m) {
   if (!m) return;
-  free(m->xy); free(m->en); free(m->zone); free(m->arc);
+  free(m->xy); free(m->en); free(m->zone); free(m->arc); free(m->enode);
   free(m->fkind); free(m->fnbr); free(m->frev); free(m->ftag);
   free(m->Lef); free(m->La); free(m->Lw); free(m->Lrev);
   free(m->Ref); free(m->Ra); free(m->Rw); free(m->Rrev);
@@ -802,15 +885,44 @@ static void mortar_couple(const or_mesh *m, const or_mortars *mo, int mode, cons
   }
 }
 
-/* wall state of an isothermal no-slip wall moving with velocity (uw, vw):
- * interior pressure, wall temperature (boundary condition reading) */
-static void wall_state(const or_params *p, const double *qi, double uw, double vw, double *qw) {
-  double pr = pressure(p, qi);
-  double rho = pr / (p->Rgas * p->T_wall);
-  qw[0] = rho;
-  qw[1] = rho * uw;
-  qw[2] = rho * vw;
-  qw[3] = pr / (p->gamma - 1.0) + 0.5 * rho * (uw * uw + vw * vw);
+/* conservative state from density, velocity and pressure */
+static void from_primitive(const or_params *p, double rho, double u, double v, double pr, double *q) {
+  q[0] = rho;
+  q[1] = rho * u;
+  q[2] = rho * v;
+  q[3] = pr / (p->gamma - 1.0) + 0.5 * rho * (u * u + v * v);
+}
+
+/* Boundary conditions (readings; the paper names them only): the ghost state
+ * qg that enters the Rusanov flux and the state qb on the boundary itself,
+ * which is the common solution of the viscous terms.  (ug, vg) is the grid
+ * velocity at the point, (nx, ny) the outward unit normal.
+ *   wall   (isothermal, no slip, moving with its zone): ghost velocity
+ *          2 V_g - V, wall temperature, interior pressure; on the wall V_g;
+ *   slip:  ghost velocity with the normal velocity relative to the wall
+ *          mirrored, interior density and pressure; on the wall that
+ *          normal component is zero;
+ *   inlet  (Dirichlet): the free stream;
+ *   outlet (fixed pressure): interior density and velocity, free-stream
+ *          pressure. */
+static void boundary_states(const or_params *p, int tag, const double *qi, double ug, double vg, double nx,
+                            double ny, double *qg, double *qb) {
+  double pr = pressure(p, qi), u = qi[1] / qi[0], v = qi[2] / qi[0];
+  if (tag == BC_WALL) {
+    double rho = pr / (p->Rgas * p->T_wall);
+    from_primitive(p, rho, 2.0 * ug - u, 2.0 * vg - v, pr, qg);
+    from_primitive(p, rho, ug, vg, pr, qb);
+  } else if (tag == BC_SLIP) {
+    double wn = (u - ug) * nx + (v - vg) * ny;
+    from_primitive(p, qi[0], u - 2.0 * wn * nx, v - 2.0 * wn * ny, pr, qg);
+    from_primitive(p, qi[0], u - wn * nx, v - wn * ny, pr, qb);
+  } else if (tag == BC_INLET) {
+    from_primitive(p, p->rho_inf, p->u_inf, p->v_inf, p->p_inf, qg);
+    from_primitive(p, p->rho_inf, p->u_inf, p->v_inf, p->p_inf, qb);
+  } else {
+    from_primitive(p, qi[0], u, v, p->p_inf, qg);
+    from_primitive(p, qi[0], u, v, p->p_inf, qb);
+  }
 }
 
 typedef struct {
@@ -911,10 +1023,10 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
               qc[v] = 0.5 * (qi[v] + qo);
             }
           } else if (kind == FK_BOUNDARY) {
-            double nx, ny, S, x, y, ug, vg;
+            double nx, ny, S, x, y, ug, vg, qg[4];
             face_geom(m, e, f, j, t, &nx, &ny, &S, &x, &y);
             grid_velocity(m, e, x, y, &ug, &vg);
-            wall_state(P, qi, ug, vg, qc);
+            boundary_states(P, m->ftag[ef], qi, ug, vg, nx, ny, qg, qc);
           } else {
             continue; /* interface: below */
           }
@@ -1088,14 +1200,8 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
             qo[v] = (fb == 1 || fb == 3) ? Qxi[id] : Qeta[id];
           }
         } else {
-          /* isothermal no-slip wall moving with the grid: ghost state */
-          double pr = pressure(P, qi), rho = pr / (P->Rgas * P->T_wall);
-          double u = qi[1] / qi[0], v = qi[2] / qi[0];
-          double gu = 2.0 * ug - u, gv = 2.0 * vg - v;
-          qo[0] = rho;
-          qo[1] = rho * gu;
-          qo[2] = rho * gv;
-          qo[3] = pr / (P->gamma - 1.0) + 0.5 * rho * (gu * gu + gv * gv);
+          double qb[4];
+          boundary_states(P, m->ftag[ef], qi, ug, vg, nx, ny, qo, qb);
         }
         rusanov(P, qi, qo, nx, ny, vgn, Fn);
         for (int v = 0; v < 4; ++v) {

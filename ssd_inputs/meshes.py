@@ -13,8 +13,12 @@ CUDA library):
 ``xy``          float64 (n_nodes, 2)  node coordinates
 ``elem_nodes``  int32 (E, 4)          corners n0..n3, counter-clockwise
 ``elem_zone``   int32 (E,)            0 stationary, 1 rotating
-``edge_arc``    int32 (E, 4)          1 if local face f is a circular arc about
-                                      ``center`` (else a straight segment)
+``edge_arc``    int32 (E, 4)          edge kind of local face f: 0 straight,
+                                      1 circular arc about ``center``, 2 cubic
+                                      through the corners and two edge nodes
+``edge_nodes``  int32 (E, 4, 2)       (only when some edge is cubic) nodes at
+                                      face parameter 1/3 and 2/3 of each cubic
+                                      edge, -1 elsewhere
 ``bfaces``      int32 (nb, 3)         (elem, local face, bc tag)
 ``pfaces``      int32 (np, 4)         periodic pairs (eA, fA, eB, fB)
 ``ifaces_L``    int32 (nL, 2)         interface faces of the rotating zone
@@ -26,7 +30,12 @@ Local faces follow the reference square [0,1]^2 with n0=(0,0), n1=(1,0),
 n2=(1,1), n3=(0,1): f0 is eta=0 (n0->n1), f1 is xi=1 (n1->n2), f2 is eta=1
 (n3->n2), f3 is xi=0 (n0->n3).
 
-Boundary tags: 1 isothermal no-slip wall (moving with its zone).
+Boundary tags: 1 isothermal no-slip wall (moving with its zone), 2 slip wall,
+3 inlet (free stream imposed), 4 outlet (free-stream pressure imposed).
+
+A cell whose edges are cubic is the paper's 12-node cubic cell (corners plus
+two nodes per edge): the transfinite map through its four edges is the
+12-node serendipity map.
 """
 from __future__ import annotations
 
@@ -35,6 +44,11 @@ import math
 import numpy as np
 
 BC_WALL = 1
+BC_SLIP = 2
+BC_INLET = 3
+BC_OUTLET = 4
+
+EDGE_STRAIGHT, EDGE_ARC, EDGE_CUBIC = 0, 1, 2
 
 # corner pairs of the four local faces, in the order of their face parameter
 FACE_CORNERS = ((0, 1), (1, 2), (3, 2), (0, 3))
@@ -66,6 +80,7 @@ class _MeshBuilder:
         self.cells: list[list[int]] = []
         self.zone_of: list[int] = []
         self.arcs: list[list[int]] = []
+        self.enodes: list[list[list[int]]] = []
 
     def node_table(self) -> _NodeTable:
         off = sum(len(z.xy) for z in self.zones)
@@ -77,9 +92,11 @@ class _MeshBuilder:
         pts = [p for z in self.zones for p in z.xy]
         return np.asarray(pts, dtype=np.float64).reshape(-1, 2)
 
-    def add_cell(self, xy_lookup, corners, zone, arc_edges=()):
+    def add_cell(self, xy_lookup, corners, zone, arc_edges=(), cubic_edges=None):
         """Add a quad given 4 node ids in either orientation.  ``arc_edges``
-        lists unordered node-id pairs whose edge is a circular arc."""
+        lists unordered node-id pairs whose edge is a circular arc;
+        ``cubic_edges`` maps an ordered corner pair (a, b) to the edge nodes
+        at 1/3 and 2/3 of the way from a to b."""
         c = list(corners)
         p = np.array([xy_lookup(n) for n in c])
         area2 = 0.0
@@ -91,9 +108,22 @@ class _MeshBuilder:
             c = [c[0], c[3], c[2], c[1]]
         arcset = {frozenset(e) for e in arc_edges}
         arc = [1 if frozenset((c[a], c[b])) in arcset else 0 for a, b in FACE_CORNERS]
+        en = [[-1, -1] for _ in range(4)]
+        for f, (a, b) in enumerate(FACE_CORNERS):
+            if not cubic_edges:
+                break
+            if (c[a], c[b]) in cubic_edges:
+                m1, m2 = cubic_edges[(c[a], c[b])]
+            elif (c[b], c[a]) in cubic_edges:
+                m2, m1 = cubic_edges[(c[b], c[a])]
+            else:
+                continue
+            arc[f] = EDGE_CUBIC
+            en[f] = [int(m1), int(m2)]
         self.cells.append(c)
         self.zone_of.append(zone)
         self.arcs.append(arc)
+        self.enodes.append(en)
         return len(self.cells) - 1
 
 
@@ -105,7 +135,7 @@ def _face_of(cell: list[int], a: int, b: int) -> int:
 
 
 def _finish(mb: _MeshBuilder, bfaces, pfaces, ifL, ifR, r_interface) -> dict:
-    return {
+    out = {
         "xy": mb.all_xy(),
         "elem_nodes": np.asarray(mb.cells, dtype=np.int32).reshape(-1, 4),
         "elem_zone": np.asarray(mb.zone_of, dtype=np.int32),
@@ -117,6 +147,9 @@ def _finish(mb: _MeshBuilder, bfaces, pfaces, ifL, ifR, r_interface) -> dict:
         "center": mb.center.copy(),
         "r_interface": float(r_interface),
     }
+    if any(k == EDGE_CUBIC for row in mb.arcs for k in row):
+        out["edge_nodes"] = np.asarray(mb.enodes, dtype=np.int32).reshape(-1, 4, 2)
+    return out
 
 
 def _ring(mb, table, zone, inner_pts, outer_pts, nlayers, inner_is_arc, outer_is_arc):
@@ -352,6 +385,9 @@ def perturb_nodes(mesh: dict, amplitude: float, seed: int = 1503) -> dict:
         for f, (i, j) in enumerate(FACE_CORNERS):
             if arc[e, f]:
                 fixed[en[e, i]] = fixed[en[e, j]] = True
+    if "edge_nodes" in mesh:
+        enodes = mesh["edge_nodes"]
+        fixed[enodes[enodes >= 0]] = True
     for row in mesh["bfaces"]:
         e, f = row[0], row[1]
         i, j = FACE_CORNERS[f]
@@ -383,3 +419,166 @@ def mesh_stats(mesh: dict) -> dict:
         "periodic_pairs": int(len(mesh["pfaces"])),
         "boundary_faces": int(len(mesh["bfaces"])),
     }
+
+
+def _geometric(n: int, ratio: float) -> np.ndarray:
+    """n + 1 increasing values from 0 to 1 whose steps grow by ``ratio``."""
+    if abs(ratio - 1.0) < 1e-12:
+        return np.linspace(0.0, 1.0, n + 1)
+    k = np.arange(n + 1, dtype=np.float64)
+    return (ratio ** k - 1.0) / (ratio ** n - 1.0)
+
+
+def ellipse_mesh(a=0.5, b=0.1, r_interface=2.0, n_theta=128, n_inner=40, n_outer=117,
+                 box=(-10.0, 30.0, -10.0, 10.0), inner_ratio=1.08, outer_ratio=1.01,
+                 shift_L=0.0) -> dict:
+    """Flow past a rotating elliptic cylinder (Sec. 4: rotating disk inside a
+    rectangular channel).
+
+    Rotating zone: an O-grid of ``n_theta`` x ``n_inner`` cells between the
+    ellipse x = a cos t, y = b sin t and the circle r = r_interface; its grid
+    lines are the linear blends (1 - s) E(t) + s C(t), i.e. ellipses of
+    semi-axes (1-s) a + s r, (1-s) b + s r, every one of them represented by
+    cubic edges (12-node cells); the layer spacing grows geometrically from
+    the body.  Stationary zone: an O-grid of ``n_theta`` x ``n_outer`` cells
+    from the circle to the rectangle ``box`` = (x0, x1, y0, y1); the corners
+    of the rectangle are nodes, and the circle nodes of each side of the
+    rectangle are spaced uniformly in angle within that side's angular range,
+    so the two sides of the interface never match node for node.  Tags: the
+    ellipse is an isothermal wall moving with the zone, x = x0 the inlet,
+    x = x1 the outlet, y = y0 and y = y1 slip walls.
+    """
+    x0, x1, y0, y1 = box
+    c = (0.0, 0.0)
+    if not (max(a, b) < r_interface < min(-x0, x1, -y0, y1)):
+        raise ValueError("need the ellipse inside the disk inside the box")
+    mb = _MeshBuilder(c)
+    # rotating zone ----------------------------------------------------------
+    tin = mb.node_table()
+    look = _lookup(mb)
+    s_in = _geometric(n_inner, inner_ratio)
+
+    def ring_pt(k, t):
+        A = (1.0 - s_in[k]) * a + s_in[k] * r_interface
+        B = (1.0 - s_in[k]) * b + s_in[k] * r_interface
+        return A * math.cos(t), B * math.sin(t)
+
+    dt = 2.0 * math.pi / n_theta
+    ids = np.zeros((n_inner + 1, n_theta), dtype=np.int64)
+    for k in range(n_inner + 1):
+        for i in range(n_theta):
+            ids[k, i] = tin.add(*ring_pt(k, shift_L + i * dt))
+    cubic = {}
+    for k in range(n_inner):
+        for i in range(n_theta):
+            t0 = shift_L + i * dt
+            m1 = tin.add(*ring_pt(k, t0 + dt / 3.0))
+            m2 = tin.add(*ring_pt(k, t0 + 2.0 * dt / 3.0))
+            cubic[(int(ids[k, i]), int(ids[k, (i + 1) % n_theta]))] = (m1, m2)
+    cells_in = []
+    for k in range(n_inner):
+        for i in range(n_theta):
+            i1 = (i + 1) % n_theta
+            p, q, r, s = ids[k, i], ids[k + 1, i], ids[k + 1, i1], ids[k, i1]
+            arcs = [(q, r)] if k == n_inner - 1 else []
+            cells_in.append(mb.add_cell(look, [p, q, r, s], 1, arcs, cubic))
+    # stationary zone --------------------------------------------------------
+    tout = mb.node_table()
+    look = _lookup(mb)
+    corners = [(x1, y0), (x1, y1), (x0, y1), (x0, y0)]  # counter-clockwise from lower right
+    ang = [math.atan2(y, x) for x, y in corners]
+    ang = [ang[0]] + [ang[0] + ((ang[j] - ang[0]) % (2 * math.pi)) for j in (1, 2, 3)] + [ang[0] + 2 * math.pi]
+    span = [ang[j + 1] - ang[j] for j in range(4)]
+    # nodes per rectangle side in proportion to its angular range (largest remainders)
+    raw = [n_theta * sp / (2 * math.pi) for sp in span]
+    cnt = [max(1, int(math.floor(v))) for v in raw]
+    order = sorted(range(4), key=lambda j: raw[j] - math.floor(raw[j]), reverse=True)
+    j = 0
+    while sum(cnt) < n_theta:
+        cnt[order[j % 4]] += 1
+        j += 1
+    while sum(cnt) > n_theta:
+        jm = max(range(4), key=lambda q: cnt[q])
+        cnt[jm] -= 1
+    circ, rect, side_of = [], [], []
+    for sd in range(4):
+        pa, pb = corners[sd], corners[(sd + 1) % 4]
+        for q in range(cnt[sd]):
+            f = q / cnt[sd]
+            t = ang[sd] + f * span[sd]
+            circ.append((r_interface * math.cos(t), r_interface * math.sin(t)))
+            rect.append((pa[0] + f * (pb[0] - pa[0]), pa[1] + f * (pb[1] - pa[1])))
+            side_of.append(sd)
+    s_out = _geometric(n_outer, outer_ratio)
+    oid = np.zeros((n_outer + 1, n_theta), dtype=np.int64)
+    for k in range(n_outer + 1):
+        for i in range(n_theta):
+            if k == 0:
+                x, y = circ[i]
+            elif k == n_outer:
+                x, y = rect[i]
+            else:
+                x = (1 - s_out[k]) * circ[i][0] + s_out[k] * rect[i][0]
+                y = (1 - s_out[k]) * circ[i][1] + s_out[k] * rect[i][1]
+            oid[k, i] = tout.add(x, y)
+    cells_out = []
+    for k in range(n_outer):
+        for i in range(n_theta):
+            i1 = (i + 1) % n_theta
+            p, q, r, s = oid[k, i], oid[k + 1, i], oid[k + 1, i1], oid[k, i1]
+            arcs = [(p, s)] if k == 0 else []
+            cells_out.append(mb.add_cell(look, [p, q, r, s], 0, arcs))
+    # boundaries -------------------------------------------------------------
+    bfaces = [(e, f, BC_WALL) for e, f in _interface_faces(mb, cells_in, ids[0])]
+    side_tag = (BC_OUTLET, BC_SLIP, BC_INLET, BC_SLIP)
+    for i, (e, f) in enumerate(_interface_faces(mb, cells_out, oid[n_outer])):
+        bfaces.append((e, f, side_tag[side_of[i]]))
+    ifL = _interface_faces(mb, cells_in, ids[n_inner])
+    ifR = _interface_faces(mb, cells_out, oid[0])
+    return _finish(mb, bfaces, [], ifL, ifR, r_interface)
+
+
+def channel_mesh(nx=6, ny=4, lx=3.0, ly=2.0, tags=(BC_INLET, BC_OUTLET, BC_SLIP, BC_SLIP),
+                 mapping=None, cubic=False) -> dict:
+    """Stationary rectangle [0, lx] x [0, ly] of nx x ny cells with boundary
+    tags (left, right, bottom, top).  ``mapping`` (x, y) -> (X, Y) moves every
+    node; with ``cubic`` each edge also gets the mapped points at 1/3 and 2/3
+    of its length, i.e. the cells are 12-node cubic cells, and a mapping whose
+    components are in the cubic serendipity span (x^a y^b with a + b <= 3, or
+    x^3 y, x y^3) is then reproduced exactly by every cell."""
+    mb = _MeshBuilder((0.0, 0.0))
+    t = mb.node_table()
+    look = _lookup(mb)
+    fmap = mapping if mapping is not None else (lambda x, y: (x, y))
+    hx, hy = lx / nx, ly / ny
+    ids = np.zeros((nx + 1, ny + 1), dtype=np.int64)
+    for i in range(nx + 1):
+        for j in range(ny + 1):
+            ids[i, j] = t.add(*fmap(i * hx, j * hy))
+    cub = {}
+    if cubic:
+        for i in range(nx + 1):
+            for j in range(ny + 1):
+                if i < nx:  # edge (i, j) -> (i + 1, j)
+                    cub[(int(ids[i, j]), int(ids[i + 1, j]))] = (
+                        t.add(*fmap((i + 1.0 / 3.0) * hx, j * hy)), t.add(*fmap((i + 2.0 / 3.0) * hx, j * hy)))
+                if j < ny:  # edge (i, j) -> (i, j + 1)
+                    cub[(int(ids[i, j]), int(ids[i, j + 1]))] = (
+                        t.add(*fmap(i * hx, (j + 1.0 / 3.0) * hy)), t.add(*fmap(i * hx, (j + 2.0 / 3.0) * hy)))
+    cell = {}
+    for j in range(ny):
+        for i in range(nx):
+            cell[(i, j)] = mb.add_cell(look, [ids[i, j], ids[i + 1, j], ids[i + 1, j + 1], ids[i, j + 1]], 0,
+                                       (), cub)
+    bf = []
+    for j in range(ny):
+        e = cell[(0, j)]
+        bf.append((e, _face_of(mb.cells[e], ids[0, j], ids[0, j + 1]), tags[0]))
+        e = cell[(nx - 1, j)]
+        bf.append((e, _face_of(mb.cells[e], ids[nx, j], ids[nx, j + 1]), tags[1]))
+    for i in range(nx):
+        e = cell[(i, 0)]
+        bf.append((e, _face_of(mb.cells[e], ids[i, 0], ids[i + 1, 0]), tags[2]))
+        e = cell[(i, ny - 1)]
+        bf.append((e, _face_of(mb.cells[e], ids[i, ny], ids[i + 1, ny]), tags[3]))
+    return _finish(mb, bf, [], [], [], 0.0)

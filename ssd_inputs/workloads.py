@@ -22,6 +22,11 @@ class FlowParams:
     viscous: int = 0
     T_wall: float = 1.0
     rk_stages: int = 3
+    # free stream: the inlet state and the outlet pressure
+    rho_inf: float = 1.0
+    u_inf: float = 0.0
+    v_inf: float = 0.0
+    p_inf: float = 1.0
 
 
 @dataclass
