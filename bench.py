@@ -214,18 +214,21 @@ def run_reference(args):
 
 
 def run_batched(ssd, ncases, steps):
-    """Batched form: a seeded mix of independent cases (rotor and Couette
-    families, 1k-8k cells, p = 2..5, omega in [0.1, 1], FP32 path) advanced by
-    one CUDA-graph launch per step, against the same cases stepped one after
-    another with their own graphs.  Wall-clock time around synchronised
-    calls."""
+    """Batched form: a seeded mix of independent cases (Couette, rotor and
+    rotating-ellipse families, 1k-8k cells, p = 2..5, omega in [0.1, 1], FP32
+    path) advanced by one CUDA-graph launch per step, against the same cases
+    stepped one after another with their own graphs.  Wall-clock time around
+    synchronised calls."""
     from ssd_inputs.workloads import batch_cases
     cases = batch_cases(ncases)
     b = ssd.Batch([c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases],
                   precision=ssd.SD_PREC_FP32, tune_dt=1e-5)
     states = []
     for k, (name, mesh, p, prm, dt) in enumerate(cases):
-        if prm.viscous:
+        if name.startswith("ellipse"):
+            q = b.cases[k].state_from(lambda x, y, prm=prm: fields.uniform(x, y, rho=prm.rho_inf, u=prm.u_inf,
+                                                                          v=prm.v_inf, p=prm.p_inf))
+        elif prm.viscous:
             q = b.cases[k].state_from(lambda x, y, prm=prm: fields.uniform(x, y, rho=1.0, p=prm.Rgas))
         else:
             q = b.cases[k].state_from(lambda x, y: fields.isentropic_vortex(x, y))
@@ -256,6 +259,44 @@ def run_batched(ssd, ncases, steps):
             "timing": "wall clock around synchronised calls"}
 
 
+def run_ellipse(ssd, stream, steps, warmup):
+    """Flow past the rotating ellipse (20096 cells, N = 5, Navier-Stokes,
+    slip / inlet / outlet, cubic cells): FP32 and FP64 paths from the same
+    impulsively started free stream, CUDA-event throughput of each over
+    ``steps`` steps and the FP32-vs-FP64 state difference after them."""
+    import torch
+    w = build_workload("ellipse_n5")
+    prm = w.params
+    out = {"workload": w.name, "elements": int(len(w.mesh["elem_nodes"])), "N": w.N, "steps": steps,
+           "dt": w.cfl_dt}
+    states = {}
+    for name, prec in (("fp32", ssd.SD_PREC_FP32), ("fp64", ssd.SD_PREC_FP64)):
+        s = ssd.Solver(w.mesh, w.N - 1, prm, precision=prec, stream=stream.cuda_stream)
+        q0 = s.state_from(lambda x, y: fields.uniform(x, y, rho=prm.rho_inf, u=prm.u_inf, v=prm.v_inf,
+                                                      p=prm.p_inf))
+        s.sd_set_state(q0)
+        s.sd_step(w.cfl_dt, warmup)
+        s.sd_sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.sd_step(w.cfl_dt, steps)
+        b.record(stream)
+        b.synchronize()
+        s.sd_sync()
+        ms = a.elapsed_time(b)
+        out[name] = {"value": s.n_dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s", "ms_per_step": ms / steps}
+        if name == "fp32":
+            prof = s.sd_profile_step(w.cfl_dt, reps=5)
+            out["fp32"]["kernel_ms"] = prof
+            out["fp32"]["interface_fraction"] = prof["mortar"] * 3 / prof["step"]
+        states[name] = s.sd_get_state()
+        s.close()
+    q32, q64 = states["fp32"], states["fp64"]
+    out["fp32_rel_l2_vs_fp64"] = float(np.sqrt(np.sum((q32 - q64) ** 2) / np.sum(q64 ** 2)))
+    out["fp32_speedup"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -270,6 +311,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--ellipse-steps", type=int, default=200)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -397,6 +439,7 @@ def main():
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
 
     batched = run_batched(ssd, args.batch_cases, args.batch_steps) if args.batch_cases > 0 else None
+    ellipse = run_ellipse(ssd, stream, args.ellipse_steps, 5) if args.ellipse_steps > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -417,6 +460,7 @@ def main():
             "l2_error_rho_vs_exact": l2_rho, "t_final": t_end,
             "fp64": fp64,
             "batched": batched,
+            "ellipse": ellipse,
             "kernel_ms": prof,
             "interface_fraction": prof["mortar"] * 3 / prof["step"],
             "fp32_fma_peak_tflops": fp32_peak,

@@ -41,26 +41,48 @@ enum {
 
 enum { SD_PREC_FP64 = 0, SD_PREC_FP32 = 1 };
 
-/* boundary tags of sd_mesh.bfaces */
-enum { SD_BC_WALL = 1 /* isothermal no-slip wall moving with its zone */ };
+/* Boundary tags of sd_mesh.bfaces.  Each acts through a ghost state in the
+ * Rusanov flux; the state on the boundary is the common solution of the
+ * viscous terms, whose flux uses the interior gradient (the paper names these
+ * conditions, Secs. 4.2-4.3, without formulas; these are the readings):
+ *   WALL   ghost velocity 2 V_g - V, temperature T_wall, interior pressure;
+ *          on the wall the velocity is V_g (the grid velocity of the zone);
+ *   SLIP   ghost velocity with the normal component of V - V_g mirrored,
+ *          interior density and pressure; on the wall that component is 0;
+ *   INLET  ghost = the free stream (rho_inf, u_inf, v_inf, p_inf);
+ *   OUTLET ghost = interior density and velocity with pressure p_inf. */
+enum {
+  SD_BC_WALL = 1,  /* isothermal no-slip wall moving with its zone */
+  SD_BC_SLIP = 2,  /* slip (inviscid) wall */
+  SD_BC_INLET = 3, /* Dirichlet inflow of the free stream */
+  SD_BC_OUTLET = 4 /* fixed-pressure outflow */
+};
+
+/* edge kinds of sd_mesh.edge_arc */
+enum { SD_EDGE_STRAIGHT = 0, SD_EDGE_ARC = 1, SD_EDGE_CUBIC = 2 };
 
 /* Mesh (Sec. 3.1: every cell is mapped to the standard square [0,1]^2).
  * Corners n0..n3 are counter-clockwise and map to (0,0), (1,0), (1,1), (0,1).
  * Local face f: f0 = {eta=0} n0->n1, f1 = {xi=1} n1->n2, f2 = {eta=1} n3->n2,
  * f3 = {xi=0} n0->n3 (the arrow is the direction of the face parameter).
- * An edge flagged in edge_arc is the circular arc about `center` through its
- * two corners (both at the same radius); other edges are straight.  The map of
- * a cell is the transfinite interpolation of its four edges, i.e. the 4-node
- * bilinear map when all edges are straight.  Faces shared by two cells of the
- * same zone are found from their node pairs; every other face must appear in
- * exactly one of bfaces, pfaces, iface_L, iface_R. */
+ * An SD_EDGE_ARC edge is the circular arc about `center` through its two
+ * corners (both at the same radius); an SD_EDGE_CUBIC edge is the cubic
+ * through its corners and the two edge nodes edge_nodes[e][f][0..1] at face
+ * parameter 1/3 and 2/3 (Sec. 3.1's 12-node cubic cells); other edges are
+ * straight.  The map of a cell is the transfinite interpolation of its four
+ * edges: the 4-node bilinear map when all edges are straight, the 12-node
+ * serendipity map when all are cubic.  Faces shared by two cells of the same
+ * zone are found from their node pairs and must have the same edge kind (and,
+ * if cubic, the same edge nodes); periodic and interface faces cannot be
+ * cubic.  Every other face must appear in exactly one of bfaces, pfaces,
+ * iface_L, iface_R. */
 typedef struct {
   int n_nodes;
   const double *xy;        /* [n_nodes][2] */
   int n_elems;
   const int *elem_nodes;   /* [n_elems][4] */
   const int *elem_zone;    /* [n_elems]: 0 stationary, 1 rotating (rigid rotation about center) */
-  const int *edge_arc;     /* [n_elems][4]: 1 if local face f is an arc */
+  const int *edge_arc;     /* [n_elems][4]: SD_EDGE_* kind of local face f */
   int n_bfaces;
   const int *bfaces;       /* [n_bfaces][3]: element, local face, SD_BC_* tag */
   int n_pfaces;
@@ -71,6 +93,8 @@ typedef struct {
   const int *iface_R;      /* [n][2]: stationary side ("right") */
   double center[2];        /* rotation centre = centre of the interface circle */
   double r_interface;      /* radius of the sliding interface */
+  const int *edge_nodes;   /* [n_elems][4][2] node indices of cubic edges (-1 elsewhere);
+                              may be NULL when no edge is cubic */
 } sd_mesh;
 
 /* Gas, flow and run parameters (non-dimensional).  Viscous fluxes follow
@@ -90,6 +114,8 @@ typedef struct {
   void *stream;     /* cudaStream_t to queue work on; NULL = a non-blocking stream the handle creates */
   int rk_stages;    /* time integrator: 0 or 3 = three-stage SSP-RK3 (Shu-Osher); 5 = the
                        five-stage fourth-order SSP-RK of Sec. 4 (Spiteri-Ruuth coefficients) */
+  double rho_inf, u_inf, v_inf, p_inf; /* free stream: SD_BC_INLET state, SD_BC_OUTLET pressure
+                                          (read only when the mesh has such faces) */
 } sd_params;
 
 typedef struct sd_handle sd_handle;

@@ -38,14 +38,15 @@ class sd_mesh(ctypes.Structure):
                 ("n_bfaces", ctypes.c_int), ("bfaces", _c_int_p), ("n_pfaces", ctypes.c_int),
                 ("pfaces", _c_int_p), ("n_iface_L", ctypes.c_int), ("iface_L", _c_int_p),
                 ("n_iface_R", ctypes.c_int), ("iface_R", _c_int_p), ("center", ctypes.c_double * 2),
-                ("r_interface", ctypes.c_double)]
+                ("r_interface", ctypes.c_double), ("edge_nodes", _c_int_p)]
 
 
 class sd_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("Rgas", ctypes.c_double), ("mu", ctypes.c_double),
                 ("prandtl", ctypes.c_double), ("omega", ctypes.c_double), ("T_wall", ctypes.c_double),
                 ("viscous", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("rk_stages", ctypes.c_int)]
+                ("rk_stages", ctypes.c_int), ("rho_inf", ctypes.c_double), ("u_inf", ctypes.c_double),
+                ("v_inf", ctypes.c_double), ("p_inf", ctypes.c_double)]
 
 
 class SSDError(RuntimeError):
@@ -127,6 +128,7 @@ def _mesh_struct(mesh: dict, keep: list) -> sd_mesh:
     pf = arr(mesh["pfaces"], np.int32)
     Lf = arr(mesh["ifaces_L"], np.int32)
     Rf = arr(mesh["ifaces_R"], np.int32)
+    enode = arr(mesh["edge_nodes"], np.int32) if "edge_nodes" in mesh else None
 
     def ip(a):
         return a.ctypes.data_as(_c_int_p)
@@ -134,13 +136,15 @@ def _mesh_struct(mesh: dict, keep: list) -> sd_mesh:
     return sd_mesh(len(xy), xy.ctypes.data_as(_c_dbl_p), len(en), ip(en), ip(zone), ip(arc), len(bf), ip(bf),
                    len(pf), ip(pf), len(Lf), ip(Lf), len(Rf), ip(Rf),
                    (ctypes.c_double * 2)(float(mesh["center"][0]), float(mesh["center"][1])),
-                   float(mesh["r_interface"]))
+                   float(mesh["r_interface"]), ip(enode) if enode is not None else None)
 
 
 def _params_struct(params, precision, stream=None) -> sd_params:
     return sd_params(params.gamma, params.Rgas, params.mu, params.prandtl, params.omega, params.T_wall,
                      int(params.viscous), int(precision), ctypes.c_void_p(stream) if stream else None,
-                     int(getattr(params, "rk_stages", 3)))
+                     int(getattr(params, "rk_stages", 3)), float(getattr(params, "rho_inf", 1.0)),
+                     float(getattr(params, "u_inf", 0.0)), float(getattr(params, "v_inf", 0.0)),
+                     float(getattr(params, "p_inf", 1.0)))
 
 
 class Solver:

@@ -290,13 +290,27 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
     if (m->elem_nodes[k] < 0 || m->elem_nodes[k] >= m->n_nodes) return fail(h, SD_ERR_MESH, "node index out of range");
   for (int e = 0; e < E; ++e)
     if (m->elem_zone[e] != 0 && m->elem_zone[e] != 1) return fail(h, SD_ERR_MESH, "zone must be 0 or 1");
+  bool any_cubic = false;
+  for (int k = 0; k < 4 * E; ++k) {
+    const int kind = m->edge_arc[k];
+    if (kind < SD_EDGE_STRAIGHT || kind > SD_EDGE_CUBIC) return fail(h, SD_ERR_MESH, "unknown edge kind");
+    if (kind == SD_EDGE_CUBIC) {
+      if (!m->edge_nodes) return fail(h, SD_ERR_MESH, "cubic edge without edge_nodes");
+      for (int q = 0; q < 2; ++q)
+        if (m->edge_nodes[2 * k + q] < 0 || m->edge_nodes[2 * k + q] >= m->n_nodes)
+          return fail(h, SD_ERR_MESH, "cubic edge node index out of range");
+      any_cubic = true;
+    }
+  }
+  bool any_farfield = false;
   std::vector<int> kind(4 * E, -1);  // 0 conforming/periodic, 1 boundary, 2 L, 3 R
   std::vector<int4> faces, bfaces;
   // boundary faces
   for (int k = 0; k < m->n_bfaces; ++k) {
     const int e = m->bfaces[3 * k], f = m->bfaces[3 * k + 1], tag = m->bfaces[3 * k + 2];
     if (e < 0 || e >= E || f < 0 || f > 3) return fail(h, SD_ERR_MESH, "boundary face index out of range");
-    if (tag != SD_BC_WALL) return fail(h, SD_ERR_UNSUPPORTED, "unsupported boundary tag");
+    if (tag < SD_BC_WALL || tag > SD_BC_OUTLET) return fail(h, SD_ERR_MESH, "unknown boundary tag");
+    any_farfield |= tag == SD_BC_INLET || tag == SD_BC_OUTLET;
     if (kind[4 * e + f] != -1) return fail(h, SD_ERR_MESH, "boundary face listed twice");
     kind[4 * e + f] = 1;
     bfaces.push_back(make_int4(4 * e + f, tag, 0, 0));
@@ -308,6 +322,8 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
       return fail(h, SD_ERR_MESH, "periodic face index out of range");
     const int efA = 4 * p[0] + p[1], efB = 4 * p[2] + p[3];
     if (kind[efA] != -1 || kind[efB] != -1) return fail(h, SD_ERR_MESH, "periodic face listed twice");
+    if (m->edge_arc[efA] == SD_EDGE_CUBIC || m->edge_arc[efB] == SD_EDGE_CUBIC)
+      return fail(h, SD_ERR_MESH, "periodic and interface faces cannot be cubic edges");
     if (m->elem_zone[p[0]] != 0 || m->elem_zone[p[2]] != 0)
       return fail(h, SD_ERR_MESH, "periodic faces must lie in the stationary zone");
     kind[efA] = kind[efB] = 0;
@@ -346,10 +362,20 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
       const int eA = efA / 4, fA = efA % 4;
       if (m->elem_zone[eA] != m->elem_zone[e]) return fail(h, SD_ERR_MESH, "conforming face joins the two zones");
       const int a0 = m->elem_nodes[4 * eA + kFaceA[fA]];
+      // both sides must describe the same curve
+      if (m->edge_arc[efA] != m->edge_arc[ef]) return fail(h, SD_ERR_MESH, "edge kinds differ across a conforming face");
+      if (m->edge_arc[ef] == SD_EDGE_CUBIC) {
+        const int *pA = m->edge_nodes + 2 * efA, *pB = m->edge_nodes + 2 * ef;
+        const bool same = a0 == a ? (pA[0] == pB[0] && pA[1] == pB[1]) : (pA[0] == pB[1] && pA[1] == pB[0]);
+        if (!same) return fail(h, SD_ERR_MESH, "cubic edge nodes differ across a conforming face");
+      }
       faces.push_back(make_int4(efA, ef, a0 == a ? 0 : 1, 0));
       kind[efA] = kind[ef] = 0;
     }
   }
+  for (int ef = 0; ef < 4 * E; ++ef)
+    if ((kind[ef] == 2 || kind[ef] == 3) && m->edge_arc[ef] == SD_EDGE_CUBIC)
+      return fail(h, SD_ERR_MESH, "periodic and interface faces cannot be cubic edges");
   if (!open.empty()) {
     const int ef = open.begin()->second;
     char buf[160];
@@ -367,6 +393,7 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   md.nM = md.nL + md.nR;
   std::vector<double> corners(8 * (size_t)E);
   std::vector<int> arcs(E);
+  std::vector<double> cubic(any_cubic ? 16 * (size_t)E : 0, 0.0);
   for (int e = 0; e < E; ++e) {
     for (int k = 0; k < 4; ++k) {
       const int n = m->elem_nodes[4 * e + k];
@@ -375,7 +402,14 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
     }
     int bits = 0;
     for (int f = 0; f < 4; ++f)
-      if (m->edge_arc[4 * e + f]) {
+      if (m->edge_arc[4 * e + f] == SD_EDGE_CUBIC) {
+        bits |= 16 << f;
+        for (int q = 0; q < 2; ++q) {
+          const int n = m->edge_nodes[2 * (4 * e + f) + q];
+          cubic[16 * (size_t)e + 4 * f + 2 * q] = m->xy[2 * n] - m->center[0];
+          cubic[16 * (size_t)e + 4 * f + 2 * q + 1] = m->xy[2 * n + 1] - m->center[1];
+        }
+      } else if (m->edge_arc[4 * e + f] == SD_EDGE_ARC) {
         bits |= 1 << f;
         // both corners of an arc edge must sit at the same radius
         const double *c = &corners[8 * (size_t)e];
@@ -389,7 +423,7 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   }
   cudaError_t ce;
   int4 *dfaces, *dbfaces, *dL, *dR;
-  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS, *dLiW, *dRiW;
+  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS, *dLiW, *dRiW, *dcub = nullptr;
   int *darcs, *dzone;
   if ((ce = upload(h, &dfaces, faces.data(), faces.size())) || (ce = upload(h, &dbfaces, bfaces.data(), bfaces.size())) ||
       (ce = upload(h, &dL, L.face.data(), L.face.size())) || (ce = upload(h, &dR, R.face.data(), R.face.size())) ||
@@ -398,8 +432,11 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
       (ce = upload(h, &dRw, R.w.data(), R.w.size())) || (ce = upload(h, &dRS, R.S.data(), R.S.size())) ||
       (ce = upload(h, &dLiW, L.iw.data(), L.iw.size())) || (ce = upload(h, &dRiW, R.iw.data(), R.iw.size())) ||
       (ce = upload(h, &dcorn, corners.data(), corners.size())) || (ce = upload(h, &darcs, arcs.data(), arcs.size())) ||
-      (ce = upload(h, &dzone, m->elem_zone, (size_t)E)))
+      (ce = upload(h, &dzone, m->elem_zone, (size_t)E)) ||
+      (any_cubic && (ce = upload(h, &dcub, cubic.data(), cubic.size()))))
     return cuda_fail(h, ce, "mesh upload");
+  md.cubic = dcub;
+  md.any_farfield = any_farfield;
   md.faces = dfaces;
   md.bfaces = dbfaces;
   md.Lface = dL;
@@ -665,6 +702,16 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
     md.prandtl = prm->prandtl;
     md.T_wall = prm->T_wall;
     md.viscous = prm->viscous;
+    md.rho_inf = prm->rho_inf;
+    md.u_inf = prm->u_inf;
+    md.v_inf = prm->v_inf;
+    md.p_inf = prm->p_inf;
+    if (md.any_farfield && (!(prm->rho_inf > 0.0) || !(prm->p_inf > 0.0) || !std::isfinite(prm->u_inf) ||
+                            !std::isfinite(prm->v_inf)))
+      rc = fail(h, SD_ERR_ARG, "inlet / outlet faces need a free stream with rho_inf > 0 and p_inf > 0");
+  }
+  if (!rc) {
+    MeshDev &md = h->md;
     md.r_interface = m->r_interface;
     if ((ce = alloc_buffers(h, h->zone_v, h->curved_v))) rc = cuda_fail(h, ce, "device buffers");
     if (!rc && prm->rk_stages == 5 && (ce = h->eng->alloc_rk54())) rc = cuda_fail(h, ce, "stage buffers");

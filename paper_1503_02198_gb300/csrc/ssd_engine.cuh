@@ -15,7 +15,7 @@
 //                   angles with the R node angles -> mortars, (o, s) of each
 //                   mortar against its L and R face (Eq. xz), face ranges
 //   k_face          conforming and periodic faces: Rusanov common flux
-//   k_bface         isothermal wall faces: Rusanov through a ghost state
+//   k_bface         boundary faces (wall, slip, inlet, outlet): Rusanov through a ghost state
 //   k_mortar_flux   per mortar: L2 projection of both sides' face traces
 //                   (Eq. prjQ2), Rusanov at the mortar SPs, back-projection
 //                   weights of the common flux (Eq. prjF2)
@@ -35,6 +35,7 @@
 #include <type_traits>
 
 #include "ssd_internal.h"
+#include "../../include/ssd.h"
 
 namespace ssd {
 
@@ -85,6 +86,13 @@ __device__ __forceinline__ T pick(double d, float f) {
   else return (T)d;
 }
 
+// 1 / x: one correctly rounded reciprocal on the FP32 path, a division in FP64
+template <typename T>
+__device__ __forceinline__ T recip(T x) {
+  if constexpr (std::is_same<T, float>::value) return __frcp_rn(x);
+  else return T(1) / x;
+}
+
 // face f of an element: sign sigma_f with F~_end = sigma_f |S| F.n_out
 __device__ __forceinline__ double face_sigma(int f) { return (f == 1 || f == 2) ? 1.0 : -1.0; }
 
@@ -121,19 +129,44 @@ __device__ inline void edge_offset(double px, double py, double qx, double qy, b
   dy = r * dphi * cs;
 }
 
+// Cubic edge (Sec. 3.1's 12-node cells) through P, M1, M2, Q at u = 0, 1/3,
+// 2/3, 1: offset from P and derivative, with the cubic Lagrange basis in
+// closed form, l1 = 27/2 u (u - 2/3)(u - 1), l2 = -27/2 u (u - 1/3)(u - 1),
+// l3 = 9/2 u (u - 1/3)(u - 2/3).
+__device__ inline void cubic_offset(double px, double py, const double *mid, double qx, double qy, double u,
+                                    double &ox, double &oy, double &dx, double &dy) {
+  const double a = u - 1.0 / 3.0, b = u - 2.0 / 3.0, c = u - 1.0;
+  const double l1 = 13.5 * u * b * c, l2 = -13.5 * u * a * c, l3 = 4.5 * u * a * b;
+  const double d1 = 13.5 * (b * c + u * c + u * b), d2 = -13.5 * (a * c + u * c + u * a),
+               d3 = 4.5 * (a * b + u * b + u * a);
+  const double x1 = mid[0] - px, y1 = mid[1] - py, x2 = mid[2] - px, y2 = mid[3] - py, x3 = qx - px, y3 = qy - py;
+  ox = l1 * x1 + l2 * x2 + l3 * x3;
+  oy = l1 * y1 + l2 * y2 + l3 * y3;
+  dx = d1 * x1 + d2 * x2 + d3 * x3;
+  dy = d1 * y1 + d2 * y2 + d3 * y3;
+}
+
+// edge f of a cell: cubic (bit 4 + f, edge nodes in cub[4 f ..]), arc (bit f) or straight
+__device__ inline void cell_edge(int arcs, const double *cub, int f, double px, double py, double qx, double qy,
+                                 double u, double &ox, double &oy, double &dx, double &dy) {
+  if (arcs & (16 << f)) cubic_offset(px, py, cub + 4 * f, qx, qy, u, ox, oy, dx, dy);
+  else edge_offset(px, py, qx, qy, arcs & (1 << f), u, ox, oy, dx, dy);
+}
+
 // Transfinite map of a cell with corners c[8] (x0 y0 .. x3 y3, centre
-// relative) and arc bits at (xi, eta): out = x, y, x_xi, y_xi, x_eta, y_eta.
-// Evaluated about corner 0 (an exact shift in real arithmetic), so the
-// round-off of the metrics scales with the cell, not with the coordinates.
-__device__ inline void cell_map(const double *c, int arcs, double xi, double eta, double *out) {
+// relative), edge kind bits and cubic edge nodes (or null) at (xi, eta):
+// out = x, y, x_xi, y_xi, x_eta, y_eta.  Evaluated about corner 0 (an exact
+// shift in real arithmetic), so the round-off of the metrics scales with the
+// cell, not with the coordinates.
+__device__ inline void cell_map(const double *c, int arcs, const double *cub, double xi, double eta, double *out) {
   const double u1 = c[2] - c[0], v1 = c[3] - c[1];
   const double u2 = c[4] - c[0], v2 = c[5] - c[1];
   const double u3 = c[6] - c[0], v3 = c[7] - c[1];
   double bx, by, dbx, dby, tx, ty, dtx, dty, lx, ly, dlx, dly, rx, ry, drx, dry;
-  edge_offset(c[0], c[1], c[2], c[3], arcs & 1, xi, bx, by, dbx, dby);    // f0: n0 -> n1
-  edge_offset(c[2], c[3], c[4], c[5], arcs & 2, eta, rx, ry, drx, dry);   // f1: n1 -> n2
-  edge_offset(c[6], c[7], c[4], c[5], arcs & 4, xi, tx, ty, dtx, dty);    // f2: n3 -> n2
-  edge_offset(c[0], c[1], c[6], c[7], arcs & 8, eta, lx, ly, dlx, dly);   // f3: n0 -> n3
+  cell_edge(arcs, cub, 0, c[0], c[1], c[2], c[3], xi, bx, by, dbx, dby);   // f0: n0 -> n1
+  cell_edge(arcs, cub, 1, c[2], c[3], c[4], c[5], eta, rx, ry, drx, dry);  // f1: n1 -> n2
+  cell_edge(arcs, cub, 2, c[6], c[7], c[4], c[5], xi, tx, ty, dtx, dty);   // f2: n3 -> n2
+  cell_edge(arcs, cub, 3, c[0], c[1], c[6], c[7], eta, lx, ly, dlx, dly);  // f3: n0 -> n3
   rx += u1;
   ry += v1;
   tx += u3;
@@ -163,6 +196,7 @@ __global__ void k_geo(MeshDev md, const double *__restrict__ Xs, const double *_
   const int e = md.tab_elem[t];
   double c[8];
   for (int k = 0; k < 8; ++k) c[k] = md.corners[(size_t)e * 8 + k];
+  const double *cub = md.cubic ? md.cubic + (size_t)e * 16 : nullptr;
   const int arcs = md.arcs[e];
   const double om = md.zone[e] == 1 ? md.omega : 0.0;
   T *g = (T *)md.geo + (size_t)t * L::G;
@@ -170,13 +204,13 @@ __global__ void k_geo(MeshDev md, const double *__restrict__ Xs, const double *_
   for (int j = 0; j < N; ++j)
     for (int i = 0; i <= N; ++i) {
       // xi-FP (X_{i+1/2}, X_j)
-      cell_map(c, arcs, Xf[i], Xs[j], m);
+      cell_map(c, arcs, cub, Xf[i], Xs[j], m);
       const double ax = m[5], ay = -m[4];
       g[L::ax + j * (N + 1) + i] = (T)ax;
       g[L::ay + j * (N + 1) + i] = (T)ay;
       g[L::gx + j * (N + 1) + i] = (T)(om * (-m[1] * ax + m[0] * ay));
       // eta-FP (X_j, X_{i+1/2}) stored at FP row i, column j
-      cell_map(c, arcs, Xs[j], Xf[i], m);
+      cell_map(c, arcs, cub, Xs[j], Xf[i], m);
       const double bx = -m[3], by = m[2];
       g[L::bx + i * N + j] = (T)bx;
       g[L::by + i * N + j] = (T)by;
@@ -184,7 +218,7 @@ __global__ void k_geo(MeshDev md, const double *__restrict__ Xs, const double *_
     }
   for (int j = 0; j < N; ++j)
     for (int i = 0; i < N; ++i) {
-      cell_map(c, arcs, Xs[i], Xs[j], m);
+      cell_map(c, arcs, cub, Xs[i], Xs[j], m);
       const double J = m[2] * m[5] - m[4] * m[3];
       g[L::iJ + j * N + i] = (T)(1.0 / J);
       g[L::grad + 0 * N * N + j * N + i] = (T)(m[5] / J);   // xi_x
@@ -204,17 +238,18 @@ __global__ void k_egeo(MeshDev md, const double *__restrict__ Xs, const double *
   if (e >= md.E) return;
   double c[8], m[6];
   for (int k = 0; k < 8; ++k) c[k] = md.corners[(size_t)e * 8 + k];
+  const double *cub = md.cubic ? md.cubic + (size_t)e * 16 : nullptr;
   const int arcs = md.arcs[e];
   bool bad = false;
   for (int j = 0; j < N; ++j) {
     for (int i = 0; i <= N; ++i) {
-      cell_map(c, arcs, Xf[i], Xs[j], m);  // xi-FP
+      cell_map(c, arcs, cub, Xf[i], Xs[j], m);  // xi-FP
       bad |= !(m[2] * m[5] - m[4] * m[3] > 0.0);
-      cell_map(c, arcs, Xs[j], Xf[i], m);  // eta-FP
+      cell_map(c, arcs, cub, Xs[j], Xf[i], m);  // eta-FP
       bad |= !(m[2] * m[5] - m[4] * m[3] > 0.0);
     }
     for (int i = 0; i < N; ++i) {
-      cell_map(c, arcs, Xs[i], Xs[j], m);  // SP
+      cell_map(c, arcs, cub, Xs[i], Xs[j], m);  // SP
       bad |= !(m[2] * m[5] - m[4] * m[3] > 0.0);
     }
   }
@@ -240,10 +275,11 @@ __global__ void k_bgeo(MeshDev md, const double *__restrict__ Xs, double *bxy) {
   const int ef = md.bfaces[b].x, e = ef >> 2, f = ef & 3;
   double c[8], m[6];
   for (int k = 0; k < 8; ++k) c[k] = md.corners[(size_t)e * 8 + k];
+  const double *cub = md.cubic ? md.cubic + (size_t)e * 16 : nullptr;
   for (int j = 0; j < N; ++j) {
     const double xi = (f == 0 || f == 2) ? Xs[j] : (f == 1 ? 1.0 : 0.0);
     const double eta = (f == 1 || f == 3) ? Xs[j] : (f == 2 ? 1.0 : 0.0);
-    cell_map(c, md.arcs[e], xi, eta, m);
+    cell_map(c, md.arcs[e], cub, xi, eta, m);
     bxy[((size_t)b * N + j) * 2] = m[0];
     bxy[((size_t)b * N + j) * 2 + 1] = m[1];
   }
@@ -256,11 +292,12 @@ __global__ void k_spxy(MeshDev md, const double *__restrict__ Xs, double t, doub
   if (e >= md.E) return;
   double c[8], m[6];
   for (int k = 0; k < 8; ++k) c[k] = md.corners[(size_t)e * 8 + k];
+  const double *cub = md.cubic ? md.cubic + (size_t)e * 16 : nullptr;
   double cs = 1.0, sn = 0.0;
   if (md.zone[e] == 1) sincos(md.omega * t, &sn, &cs);
   for (int j = 0; j < N; ++j)
     for (int i = 0; i < N; ++i) {
-      cell_map(c, md.arcs[e], Xs[i], Xs[j], m);
+      cell_map(c, md.arcs[e], cub, Xs[i], Xs[j], m);
       out[(((size_t)e * N + j) * N + i) * 2] = cx + (cs * m[0] - sn * m[1]);
       out[(((size_t)e * N + j) * N + i) * 2 + 1] = cy + (sn * m[0] + cs * m[1]);
     }
@@ -309,8 +346,11 @@ struct ElemGeo {
       const T xe = e3x + xi * dx, ye = e3y + xi * dy;
       vx = ye;
       vy = -xe;
-      const T px = x0 + xi * e1x + eta * xe, py = y0 + xi * e1y + eta * ye;
-      g = om * (px * vy - py * vx);
+      g = T(0);
+      if (om != T(0)) {
+        const T px = x0 + xi * e1x + eta * xe, py = y0 + xi * e1y + eta * ye;
+        g = om * (px * vy - py * vx);
+      }
     } else {
       const int k = j * (N + 1) + i;
       const T ax = tab[L::ax + k], ay = tab[L::ay + k];
@@ -326,8 +366,11 @@ struct ElemGeo {
       const T xx = e1x + eta * dx, yx = e1y + eta * dy;
       vx = -yx;
       vy = xx;
-      const T px = x0 + eta * e3x + xi * xx, py = y0 + eta * e3y + xi * yx;
-      g = om * (px * vy - py * vx);
+      g = T(0);
+      if (om != T(0)) {
+        const T px = x0 + eta * e3x + xi * xx, py = y0 + eta * e3y + xi * yx;
+        g = om * (px * vy - py * vx);
+      }
     } else {
       const int k = l * N + i;
       const T bx = tab[L::bx + k], by = tab[L::by + k];
@@ -348,9 +391,20 @@ struct ElemGeo {
     if (OTF && tab == nullptr) {
       const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
       const T xx = e1x + eta * dx, yx = e1y + eta * dy, xe = e3x + xi * dx, ye = e3y + xi * dy;
-      return T(1) / (xx * ye - xe * yx);
+      return recip(xx * ye - xe * yx);
     }
     return tab[L::iJ + j * N + i];
+  }
+  // 1 / |J| at SP (X_i, X_j) straight from the cell flag and the unrotated
+  // record or table (|J| does not change under the rotation)
+  static __device__ __forceinline__ T inv_jac_t0(const MeshDev &md, int f, const T *r, int i, int j) {
+    const int ti = (f >> 1) - 1;
+    if (OTF && ti < 0) {
+      const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
+      const T xx = r[2] + eta * r[6], yx = r[3] + eta * r[7], xe = r[4] + xi * r[6], ye = r[5] + xi * r[7];
+      return recip(xx * ye - xe * yx);
+    }
+    return ((const T *)md.geo + (size_t)ti * L::G)[L::iJ + j * N + i];
   }
   // gradients of xi and eta at SP (X_i, X_j): (xi_x, xi_y), (eta_x, eta_y)
   __device__ __forceinline__ void sp_grad(int i, int j, T &xix, T &xiy, T &etx, T &ety) const {
@@ -588,18 +642,54 @@ __global__ void k_face(MeshDev md) {
   }
 }
 
-// Isothermal no-slip walls moving with their zone: Rusanov through a ghost
-// state with velocity 2 V_w - V, the wall temperature and the interior pressure.
+// conservative state from density, velocity and pressure
+template <typename T>
+__device__ __forceinline__ void from_primitive(T rho, T u, T v, T p, T gm1, T *q) {
+  q[0] = rho;
+  q[1] = rho * u;
+  q[2] = rho * v;
+  q[3] = p / gm1 + T(0.5) * rho * (u * u + v * v);
+}
+
+// Boundary conditions (Secs. 4.2-4.3 name them; these are the readings): the
+// ghost state qg entering the Rusanov flux and the state qb on the boundary,
+// the common solution of the viscous terms.  (ug, vg) is the grid velocity at
+// the point, (nx, ny) the outward unit normal.
+//   WALL   ghost velocity 2 V_g - V, wall temperature, interior pressure; qb has V_g
+//   SLIP   normal velocity relative to the wall mirrored (qb: removed),
+//          interior density and pressure
+//   INLET  the free stream
+//   OUTLET interior density and velocity, free-stream pressure
+template <typename T>
+__device__ __forceinline__ void boundary_states(const MeshDev &md, int tag, const T *q, T ug, T vg, T nx, T ny, T *qg,
+                                                T *qb) {
+  const T gm1 = (T)(md.gamma - 1.0);
+  const T p = pressure_of(q, gm1);
+  const T u = q[1] / q[0], v = q[2] / q[0];
+  if (tag == SD_BC_WALL) {
+    const T rho = p / (T)(md.Rgas * md.T_wall);
+    from_primitive(rho, T(2) * ug - u, T(2) * vg - v, p, gm1, qg);
+    from_primitive(rho, ug, vg, p, gm1, qb);
+  } else if (tag == SD_BC_SLIP) {
+    const T wn = (u - ug) * nx + (v - vg) * ny;
+    from_primitive(q[0], u - T(2) * wn * nx, v - T(2) * wn * ny, p, gm1, qg);
+    from_primitive(q[0], u - wn * nx, v - wn * ny, p, gm1, qb);
+  } else if (tag == SD_BC_INLET) {
+    from_primitive((T)md.rho_inf, (T)md.u_inf, (T)md.v_inf, (T)md.p_inf, gm1, qg);
+    from_primitive((T)md.rho_inf, (T)md.u_inf, (T)md.v_inf, (T)md.p_inf, gm1, qb);
+  } else {
+    from_primitive(q[0], u, v, (T)md.p_inf, gm1, qg);
+    from_primitive(q[0], u, v, (T)md.p_inf, gm1, qb);
+  }
+}
+
+// Geometry of boundary point (b, j) at the current rotation: outward unit
+// normal, |S| with the face sign, normal grid velocity and the grid velocity
+// (from the t = 0 position of the point, rotated).
 template <typename T, int N, bool OTF>
-__global__ void k_bface(MeshDev md) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= md.nB * N) return;
-  const int b = t / N, j = t - b * N;
+__device__ __forceinline__ void bface_geom(const MeshDev &md, int b, int j, T &nx, T &ny, T &sS, T &vgn, T &ug,
+                                           T &vg) {
   const int ef = md.bfaces[b].x, e = ef >> 2, f = ef & 3;
-  const T *TR = (const T *)md.TR;
-  T q[4], qg[4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) q[v] = TR[((size_t)ef * 4 + v) * N + j];
   const double c = md.clk->c, s = md.clk->s;
   ElemGeo<T, N, OTF> G;
   G.load(md, e, (T)c, (T)s);
@@ -608,25 +698,38 @@ __global__ void k_bface(MeshDev md) {
   double uw = 0.0, vw = 0.0;
   if (md.eflag[e] & 1) {
     const double x0 = md.bxy[((size_t)b * N + j) * 2], y0 = md.bxy[((size_t)b * N + j) * 2 + 1];
-    const double x = c * x0 - s * y0, y = s * x0 + c * y0;
-    uw = -md.omega * y;
-    vw = md.omega * x;
+    uw = -md.omega * (s * x0 + c * y0);
+    vw = md.omega * (c * x0 - s * y0);
   }
   const T S = sqrt(ax * ax + ay * ay), sg = (T)face_sigma(f);
-  const T nx = sg * ax / S, ny = sg * ay / S, vgn = sg * ag / S;
-  const T gm1 = (T)(md.gamma - 1.0);
-  const T p = pressure_of(q, gm1);
-  const T rho = p / (T)(md.Rgas * md.T_wall);
-  const T gu = T(2) * (T)uw - q[1] / q[0], gv = T(2) * (T)vw - q[2] / q[0];
-  qg[0] = rho;
-  qg[1] = rho * gu;
-  qg[2] = rho * gv;
-  qg[3] = p / gm1 + T(0.5) * rho * (gu * gu + gv * gv);
+  nx = sg * ax / S;
+  ny = sg * ay / S;
+  vgn = sg * ag / S;
+  sS = sg * S;
+  ug = (T)uw;
+  vg = (T)vw;
+}
+
+// Boundary faces: Rusanov through the ghost state of the face's condition.
+template <typename T, int N, bool OTF>
+__global__ void k_bface(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= md.nB * N) return;
+  const int b = t / N, j = t - b * N;
+  const int4 bf = md.bfaces[b];
+  const int ef = bf.x;
+  const T *TR = (const T *)md.TR;
+  T q[4], qg[4], qb[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) q[v] = TR[((size_t)ef * 4 + v) * N + j];
+  T nx, ny, sS, vgn, ug, vg;
+  bface_geom<T, N, OTF>(md, b, j, nx, ny, sS, vgn, ug, vg);
+  boundary_states(md, bf.y, q, ug, vg, nx, ny, qg, qb);
   T Fn[4];
   rusanov(q, qg, nx, ny, vgn, (T)md.gamma, Fn);
   T *CF = (T *)md.CF;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sg * S * Fn[v];
+  for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sS * Fn[v];
 }
 
 // Mortar coupling of Sec. 3.2.  Thread (mortar, side, p): p is a quadrature
@@ -967,19 +1070,12 @@ struct VolCfg {
   static constexpr int O_QLO = 2 * STAGE, O_NHI = O_QLO + QLO, O_NLO = O_NHI + QHI, O_AUX = O_NLO + QLO;
   static constexpr int SINGLE_END = ((O_AUX + AUXB) + 127) / 128 * 128;
   // work arrays
-  static constexpr int O_RF = SINGLE_END, O_RG = O_RF + QHI, O_IJ = O_RG + QHI;
-  static constexpr int O_BAR = ((O_IJ + EPB * NN * (int)sizeof(T)) + 15) / 16 * 16;
+  static constexpr int O_RF = SINGLE_END, O_RG = O_RF + QHI;
+  static constexpr int O_BAR = ((O_RG + QHI) + 15) / 16 * 16;
   static constexpr int SMEM = O_BAR + 3 * 8;
   // resident CTAs per SM the register budget is set for
   static constexpr int MINB = (200 * 1024 / SMEM) < 8 ? (200 * 1024 / SMEM) : 8;
 };
-
-// 1 / x: one correctly rounded reciprocal on the FP32 path, a division in FP64
-template <typename T>
-__device__ __forceinline__ T recip(T x) {
-  if constexpr (std::is_same<T, float>::value) return __frcp_rn(x);
-  else return T(1) / x;
-}
 
 // transformed ALE inviscid flux at one flux point: a.(F, G) - (V_g . a) Q
 template <typename T>
@@ -1017,7 +1113,6 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
   uint64_t *bar = (uint64_t *)(smem + C::O_BAR);  // [0], [1]: double-buffered part; [2]: single part
   T(*sRF)[4][NN] = (T(*)[4][NN])(smem + C::O_RF);
   T(*sRG)[4][NN] = (T(*)[4][NN])(smem + C::O_RG);
-  T(*sIJ)[NN] = (T(*)[NN])(smem + C::O_IJ);
   const VolBasis<T, N> &B = cVB<T, N>;
   const bool use_base = MODE == MODE_RK && has_base;
   const uint32_t txA = C::QHI + C::CFB + C::EGB + C::EFB;
@@ -1082,10 +1177,11 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
     const T *sEG = (const T *)(sb + C::O_EG);
     const int e0 = tile * EPB;
     const int ne = min(EPB, md.E - e0);
-    // ---- phase 1: one thread per SP line (xi lines, then eta lines) ----
-    const int le = threadIdx.x / (2 * N);
-    const int r = threadIdx.x - le * 2 * N;
-    const int d = r / N, mline = r - d * N;
+    // ---- phase 1: one thread per SP line: threads [0, EPB N) take the xi
+    // lines, the rest the eta lines, so that most warps run one direction ----
+    const int d = threadIdx.x >= EPB * N ? 1 : 0;
+    const int tl = threadIdx.x - d * EPB * N;
+    const int le = tl / N, mline = tl - le * N;
     if (le < ne) {
       ElemGeo<T, N, OTF> G;
       G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, cth, sth);
@@ -1140,7 +1236,6 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
             sRF[le][1][sp] = acc2[0][k].y;
             sRF[le][2][sp] = acc2[1][k].x;
             sRF[le][3][sp] = acc2[1][k].y;
-            sIJ[le][sp] = G.inv_jac(k, mline);
           }
         } else {
 #pragma unroll
@@ -1193,11 +1288,9 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
       }
       if (d == 0) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
+        for (int k = 0; k < N; ++k)
 #pragma unroll
           for (int v = 0; v < 4; ++v) sRF[le][v][mline * N + k] = acc[v][k];
-          sIJ[le][mline * N + k] = G.inv_jac(k, mline);
-        }
       } else {
 #pragma unroll
         for (int k = 0; k < N; ++k)
@@ -1221,7 +1314,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
     // ---- phase 2: dQ/dt at the SPs and the Runge-Kutta combination ----
     for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
       const int l2 = idx / NN, sp = idx - l2 * NN;
-      const T iJ = sIJ[l2][sp];
+      const T iJ = ElemGeo<T, N, OTF>::inv_jac_t0(md, sEF[l2], sEG + l2 * 8, sp % N, sp / N);
       const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
       if (MODE == MODE_RESIDUAL) {
 #pragma unroll
@@ -1508,7 +1601,7 @@ struct EngineImpl : Engine {
     }
     // common solution, gradient traces, then common inviscid + viscous fluxes
     if (md.nF > 0) k_face_cq<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
-    if (md.nB > 0) k_bface_cq<T, N><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
+    if (md.nB > 0) k_bface_cq<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
     if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
     constexpr int EPBv = VisCfg<N>::EPB;
     k_grad_trace<T, N, OTF><<<(md.E + EPBv - 1) / EPBv, VisCfg<N>::THREADS, 0, s>>>(md, (const T *)q.hi);

@@ -69,7 +69,9 @@ struct MeshDev {
   void *contrib;        // T [2][nM][4][N] back-projected mortar fluxes
   // elements
   const double *corners;  // [E][8] t = 0 corner coordinates relative to the centre
-  const int *arcs;        // [E] bit f set if local face f is an arc
+  const int *arcs;        // [E] bit f: local face f is an arc; bit 4 + f: it is a cubic
+  const double *cubic;    // [E][4][4] edge nodes (x, y at 1/3, x, y at 2/3) of cubic
+                          // edges, centre relative; null when the mesh has none
   const int *zone;        // [E]
   // eflag[e]: bit 0 = rotating zone; (table index + 1) << 1, or 0 for a
   // straight cell whose bilinear metrics are computed on the fly
@@ -84,6 +86,8 @@ struct MeshDev {
                           // (x, y) out of side A, sigma_A |S_A|, sigma_B |S_B|, V_g . n
   DevClock *clk;
   double omega, gamma, Rgas, mu, prandtl, T_wall, r_interface;
+  double rho_inf, u_inf, v_inf, p_inf;  // free stream (inlet state, outlet pressure)
+  int any_farfield;                     // the mesh has inlet or outlet faces
   float omega_f, gamma_f;  // the same rounded to float (FP32 path)
   int viscous;
 };

@@ -4,7 +4,7 @@
 //
 // Per stage, after the stage clock and mortar merge:
 //   k_face_cq / k_bface_cq     common solution Q_c on conforming faces (average)
-//                              and walls (wall state)
+//                              and boundaries (the state on the boundary)
 //   k_mortar_flux<MORTAR_AVG_Q> + gather   Q_c on the interface: both sides
 //                              projected to the mortars, averaged, projected back
 //   k_grad_trace               gradients of the conservative variables at the
@@ -12,7 +12,7 @@
 //                              the FP values with Q_c at the end FPs, chain rule
 //                              with the SP metrics), interpolated to the faces
 //   k_face_visc / k_bface_visc Rusanov + average of both sides' viscous normal
-//                              flux evaluated with Q_c (walls: wall state,
+//                              flux evaluated with Q_c (boundaries: boundary state,
 //                              interior gradient)
 //   k_mortar_flux<MORTAR_RUSANOV> + gather, then <MORTAR_AVG_FV> + gather-add:
 //                              inviscid mortar flux, then the viscous normal flux
@@ -51,32 +51,6 @@ __device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *q
   G[3] = -(u * txy + v * tyy + kc * Ty);
 }
 
-// wall state of an isothermal no-slip wall: interior pressure, wall
-// temperature, wall velocity (uw, vw)
-template <typename T>
-__device__ __forceinline__ void wall_state(const T *q, T uw, T vw, const MeshDev &md, T *qw) {
-  const T gm1 = (T)(md.gamma - 1.0);
-  const T p = pressure_of(q, gm1);
-  const T rho = p / (T)(md.Rgas * md.T_wall);
-  qw[0] = rho;
-  qw[1] = rho * uw;
-  qw[2] = rho * vw;
-  qw[3] = p / gm1 + T(0.5) * rho * (uw * uw + vw * vw);
-}
-
-// wall velocity at boundary point (b, j): the grid velocity of a rotating wall
-template <int N>
-__device__ __forceinline__ void wall_velocity(const MeshDev &md, int b, int j, double &uw, double &vw) {
-  uw = vw = 0.0;
-  const int e = md.bfaces[b].x >> 2;
-  if (md.eflag[e] & 1) {
-    const double c = md.clk->c, s = md.clk->s;
-    const double x0 = md.bxy[((size_t)b * N + j) * 2], y0 = md.bxy[((size_t)b * N + j) * 2 + 1];
-    uw = -md.omega * (s * x0 + c * y0);
-    vw = md.omega * (c * x0 - s * y0);
-  }
-}
-
 // ---- common solution -------------------------------------------------------
 
 template <typename T, int N>
@@ -96,21 +70,23 @@ __global__ void k_face_cq(MeshDev md) {
   }
 }
 
-template <typename T, int N>
+// boundary faces: the common solution is the state on the boundary
+template <typename T, int N, bool OTF>
 __global__ void k_bface_cq(MeshDev md) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= md.nB * N) return;
   const int b = t / N, j = t - b * N;
-  const int ef = md.bfaces[b].x;
+  const int4 bf = md.bfaces[b];
+  const int ef = bf.x;
   const T *TR = (const T *)md.TR;
-  T q[4], qw[4];
+  T q[4], qg[4], qb[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) q[v] = TR[((size_t)ef * 4 + v) * N + j];
-  double uw, vw;
-  wall_velocity<N>(md, b, j, uw, vw);
-  wall_state(q, (T)uw, (T)vw, md, qw);
+  T nx, ny, sS, vgn, ug, vg;
+  bface_geom<T, N, OTF>(md, b, j, nx, ny, sS, vgn, ug, vg);
+  boundary_states(md, bf.y, q, ug, vg, nx, ny, qg, qb);
 #pragma unroll
-  for (int v = 0; v < 4; ++v) ((T *)md.CQ)[((size_t)ef * 4 + v) * N + j] = qw[v];
+  for (int v = 0; v < 4; ++v) ((T *)md.CQ)[((size_t)ef * 4 + v) * N + j] = qb[v];
 }
 
 // ---- gradients ---------------------------------------------------------------
@@ -263,41 +239,30 @@ __global__ void k_face_visc(MeshDev md) {
   }
 }
 
+// boundary faces: Rusanov through the ghost state plus the viscous flux of the
+// boundary state with the interior gradient
 template <typename T, int N, bool OTF>
 __global__ void k_bface_visc(MeshDev md) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= md.nB * N) return;
   const int b = t / N, j = t - b * N;
-  const int ef = md.bfaces[b].x, e = ef >> 2, f = ef & 3;
+  const int4 bf = md.bfaces[b];
+  const int ef = bf.x;
   const T *TR = (const T *)md.TR, *GT = (const T *)md.GTR;
-  T q[4], qg[4], qw[4], g8[8];
+  T q[4], qg[4], qb[4], g8[8];
 #pragma unroll
   for (int v = 0; v < 4; ++v) q[v] = TR[((size_t)ef * 4 + v) * N + j];
 #pragma unroll
   for (int c = 0; c < 8; ++c) g8[c] = GT[((size_t)ef * 8 + c) * N + j];
-  ElemGeo<T, N, OTF> G;
-  G.load(md, e, (T)md.clk->c, (T)md.clk->s);
-  T ax, ay, ag;
-  G.face(f, j, ax, ay, ag);
-  double uw, vw;
-  wall_velocity<N>(md, b, j, uw, vw);
-  const T S = sqrt(ax * ax + ay * ay), sg = (T)face_sigma(f);
-  const T nx = sg * ax / S, ny = sg * ay / S, vgn = sg * ag / S;
-  const T gm1 = (T)(md.gamma - 1.0);
-  const T p = pressure_of(q, gm1);
-  const T rho = p / (T)(md.Rgas * md.T_wall);
-  const T gu = T(2) * (T)uw - q[1] / q[0], gv = T(2) * (T)vw - q[2] / q[0];
-  qg[0] = rho;
-  qg[1] = rho * gu;
-  qg[2] = rho * gv;
-  qg[3] = p / gm1 + T(0.5) * rho * (gu * gu + gv * gv);
+  T nx, ny, sS, vgn, ug, vg;
+  bface_geom<T, N, OTF>(md, b, j, nx, ny, sS, vgn, ug, vg);
+  boundary_states(md, bf.y, q, ug, vg, nx, ny, qg, qb);
   T Fn[4], fv[4];
   rusanov(q, qg, nx, ny, vgn, (T)md.gamma, Fn);
-  wall_state(q, (T)uw, (T)vw, md, qw);
-  viscous_normal(qw, g8, nx, ny, md, fv);
+  viscous_normal(qb, g8, nx, ny, md, fv);
   T *CF = (T *)md.CF;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sg * S * (Fn[v] + fv[v]);
+  for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sS * (Fn[v] + fv[v]);
 }
 
 // ---- volume ------------------------------------------------------------------

@@ -77,6 +77,27 @@ def _rotor_large(N=6):
     return mesh, prm, dt
 
 
+def ellipse_params(omega=0.3, mach=0.2, re=1000.0):
+    """Free stream rho = U = T = 1 along +x at Mach M: p_inf = R = 1/(gamma M^2);
+    mu from Re on the major axis (length 1); isothermal body at T = 1."""
+    gamma = 1.4
+    p_inf = 1.0 / (gamma * mach * mach)
+    return FlowParams(gamma=gamma, Rgas=p_inf, mu=1.0 / re, prandtl=0.72, omega=omega, viscous=1, T_wall=1.0,
+                      rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=p_inf)
+
+
+def _ellipse(N=5, scale=1.0, omega=0.3, **mesh_kw):
+    if scale != 1.0:
+        mesh_kw.setdefault("n_theta", max(16, 4 * int(round(32 * scale))))
+        mesh_kw.setdefault("n_inner", max(3, int(round(40 * scale))))
+        mesh_kw.setdefault("n_outer", max(4, int(round(117 * scale))))
+    mesh = meshes.ellipse_mesh(**mesh_kw)
+    prm = ellipse_params(omega=omega)
+    c = math.sqrt(prm.gamma * prm.p_inf / prm.rho_inf)
+    dt = stable_dt(mesh, N, prm, 1.0 + c + 2.0 * omega)
+    return mesh, prm, dt
+
+
 def build_workload(name: str) -> Workload:
     if name == "couette_n3":
         mesh, prm, dt = _couette()
@@ -88,6 +109,11 @@ def build_workload(name: str) -> Workload:
         mesh, prm, dt = _vortex(N)
         return Workload(name, f"isentropic vortex (strength 5) on periodic [-10,10]^2, rotating "
                         f"disk r<=3 at omega=pi/4, N={N} (p={N-1}), Euler", mesh, N, prm, dt, 100)
+    if name == "ellipse_n5":
+        mesh, prm, dt = _ellipse(5)
+        return Workload(name, "Navier-Stokes flow past a rotating ellipse (axes 1:0.2), Re=1000, Mach 0.2, "
+                        "rotating disk r<=2 at omega=0.3, 20096 curvilinear quads (12-node cubic cells "
+                        "around the body), N=5 (p=4)", mesh, 5, prm, dt, 10000)
     if name == "rotor_n6":
         mesh, prm, dt = _rotor_large(6)
         return Workload(name, "vortex through rotor: periodic [-20,20]^2, rotating disk r<=4, "
@@ -95,7 +121,7 @@ def build_workload(name: str) -> Workload:
     raise KeyError(name)
 
 
-WORKLOADS = ("couette_n3", "vortex_n4", "vortex_n5", "rotor_n6")
+WORKLOADS = ("couette_n3", "vortex_n4", "vortex_n5", "ellipse_n5", "rotor_n6")
 
 
 def min_edge(mesh) -> float:
@@ -116,9 +142,10 @@ def stable_dt(mesh, N, prm, speed, cfl=0.1):
 
 
 def batch_cases(n=64, seed=1503, min_cells=1000, max_cells=8000):
-    """Seeded mix of independent cases for the batched form: rotor-family
-    (Euler vortex through a rotating disk) and Couette-family (viscous,
-    walls) meshes with log-uniform cell counts, p in {2,..,5}, omega in
+    """Seeded mix of independent cases for the batched form, drawn uniformly
+    from three families: Couette (viscous, walls), rotor (Euler vortex
+    through a rotating disk) and rotating ellipse (viscous, slip / inlet /
+    outlet, cubic cells); log-uniform cell counts, p in {2,..,5}, omega in
     U[0.1, 1].  Returns a list of (name, mesh, p, FlowParams, dt)."""
     import numpy as np
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -128,7 +155,12 @@ def batch_cases(n=64, seed=1503, min_cells=1000, max_cells=8000):
         p = int(rng.integers(2, 6))
         omega = float(rng.uniform(0.1, 1.0))
         N = p + 1
-        if rng.uniform() < 0.75:
+        family = rng.uniform()
+        if family >= 2.0 / 3.0:
+            # ellipse family: about 20096 s^2 cells
+            mesh, prm, dt = _ellipse(N, scale=math.sqrt(target / 20096.0), omega=omega)
+            out.append((f"ellipse{k}", mesh, p, prm, dt))
+        elif family >= 1.0 / 3.0:
             # rotor family: about 6016 s^2 cells
             s = math.sqrt(target / 6016.0)
             nh = max(4, 2 * int(round(12 * s)))
