@@ -95,30 +95,45 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM traffic of k_volume per launch (read + write, averaged over the three
-# stage launches) from the ncu capture summarised in
+# DRAM bytes (read + write) per launch of the FP32 volume kernel (mean of the
+# three stage launches) from the ncu capture summarised in
 # profiles/k_volume_fp32_rotor_n6.md; valid only for the kernel source it was
-# taken on (SHA-256 of csrc/ssd_engine.cuh), otherwise reported as null.
-PROFILED_TRAFFIC = {"bytes": (389.09e6 + 327.88e6 + 673.48e6 + 330.19e6 + 673.48e6 + 329.34e6) / 3,
-                    "engine_sha256": "abb8dae592ed5f8414889d2549d4bf22e936237da6b5470d87fc79c80ff663a0"}
+# taken on: SHA-256 of the engine text that k_volume is built from (the
+# ElemGeo metrics and VolCfg through the end of k_volume); otherwise null.
+PROFILED_TRAFFIC = {"bytes": (389.16e6 + 328.36e6 + 673.57e6 + 330.60e6 + 673.47e6 + 329.89e6) / 3,
+                    "kernel_sha256": "7df48af09167ef4d2b7ff5c2a9fc923c258c086079b4abce0db10cb0a8b10729"}
+
+
+def volume_kernel_source():
+    path = os.path.join(ROOT, "paper_1503_02198_gb300", "csrc", "ssd_engine.cuh")
+    try:
+        text = open(path, encoding="utf-8").read()
+    except OSError:
+        return None
+    a = text.index("struct ElemGeo {")
+    b = text.index("\n};\n", a)
+    c = text.index("struct VolCfg {")
+    d = text.index('#include "ssd_viscous.cuh"')
+    return text[a:b] + text[c:d]
 
 
 def profiled_traffic():
     import hashlib
-    path = os.path.join(ROOT, "paper_1503_02198_gb300", "csrc", "ssd_engine.cuh")
-    try:
-        h = hashlib.sha256(open(path, "rb").read()).hexdigest()
-    except OSError:
+    src = volume_kernel_source()
+    if src is None:
         return None
-    return PROFILED_TRAFFIC["bytes"] if h == PROFILED_TRAFFIC["engine_sha256"] else None
+    h = hashlib.sha256(src.encode("utf-8")).hexdigest()
+    return PROFILED_TRAFFIC["bytes"] if h == PROFILED_TRAFFIC["kernel_sha256"] else None
 
 
-def volume_bytes_per_element(N, w_c):
+def volume_bytes_per_element(N, w_c, w_s=8):
     """Algorithmic bytes one volume launch moves per element (see design
-    notes): FP64 state read + write, the Runge-Kutta base read on two of the
-    three stages, the common-flux read and the new traces written (16 N values
-    each in the compute word), 4 corner nodes (16 B each) and the zone tag."""
-    state = 4 * N * N * 8
+    notes): state read + write (w_s bytes per value: 8 for the FP64 or
+    double-float state, 4 for FP32 state storage), the Runge-Kutta base read
+    on two of the three stages, the common-flux read and the new traces
+    written (16 N values each in the compute word), 4 corner nodes (16 B each)
+    and the zone tag."""
+    state = 4 * N * N * w_s
     return state * (2 + 2.0 / 3.0) + 2 * 16 * N * w_c + 4 * 16 + 4
 
 
@@ -259,42 +274,79 @@ def run_batched(ssd, ncases, steps):
             "timing": "wall clock around synchronised calls"}
 
 
-def run_ellipse(ssd, stream, steps, warmup):
-    """Flow past the rotating ellipse (20096 cells, N = 5, Navier-Stokes,
-    slip / inlet / outlet, cubic cells): FP32 and FP64 paths from the same
-    impulsively started free stream, CUDA-event throughput of each over
-    ``steps`` steps and the FP32-vs-FP64 state difference after them."""
+def run_config(ssd, stream, name, steps, warmup, start, start_label, other_start=None):
+    """One of the paper's named configurations at full size: FP32 and FP64
+    paths over ``steps`` steps from ``start`` (CUDA-event throughput of each,
+    per-kernel times of the FP32 step, FP32-vs-FP64 state difference after the
+    steps) and, if given, the same difference from ``other_start``."""
     import torch
-    w = build_workload("ellipse_n5")
+    w = build_workload(name)
     prm = w.params
     out = {"workload": w.name, "elements": int(len(w.mesh["elem_nodes"])), "N": w.N, "steps": steps,
-           "dt": w.cfl_dt}
-    states = {}
-    for name, prec in (("fp32", ssd.SD_PREC_FP32), ("fp64", ssd.SD_PREC_FP64)):
+           "dt": w.cfl_dt, "start": start_label}
+
+    def run(prec, q_fn, timed):
         s = ssd.Solver(w.mesh, w.N - 1, prm, precision=prec, stream=stream.cuda_stream)
-        q0 = s.state_from(lambda x, y: fields.uniform(x, y, rho=prm.rho_inf, u=prm.u_inf, v=prm.v_inf,
-                                                      p=prm.p_inf))
-        s.sd_set_state(q0)
-        s.sd_step(w.cfl_dt, warmup)
-        s.sd_sync()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        s.sd_step(w.cfl_dt, steps)
-        b.record(stream)
-        b.synchronize()
-        s.sd_sync()
-        ms = a.elapsed_time(b)
-        out[name] = {"value": s.n_dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s", "ms_per_step": ms / steps}
-        if name == "fp32":
-            prof = s.sd_profile_step(w.cfl_dt, reps=5)
-            out["fp32"]["kernel_ms"] = prof
-            out["fp32"]["interface_fraction"] = prof["mortar"] * 3 / prof["step"]
-        states[name] = s.sd_get_state()
+        s.sd_set_state(s.state_from(q_fn))
+        res = {}
+        if timed:
+            s.sd_step(w.cfl_dt, warmup)
+            s.sd_sync()
+            s.sd_set_state(s.state_from(q_fn))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.sd_step(w.cfl_dt, steps)
+            b.record(stream)
+            b.synchronize()
+            s.sd_sync()
+            ms = a.elapsed_time(b)
+            res = {"value": s.n_dofs * steps / (ms * 1e-3), "unit": "DOF-updates/s", "ms_per_step": ms / steps}
+            q = s.sd_get_state()  # before sd_profile_step, which advances the solution
+            if prec == ssd.SD_PREC_FP32:
+                prof = s.sd_profile_step(w.cfl_dt, reps=5)
+                res["kernel_ms"] = prof
+                res["interface_fraction"] = prof["mortar"] * 3 / prof["step"]
+        else:
+            s.sd_step(w.cfl_dt, steps)
+            s.sd_sync()
+            q = s.sd_get_state()
         s.close()
-    q32, q64 = states["fp32"], states["fp64"]
-    out["fp32_rel_l2_vs_fp64"] = float(np.sqrt(np.sum((q32 - q64) ** 2) / np.sum(q64 ** 2)))
+        return res, q
+
+    def rel(a, b):
+        return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+    out["fp32"], q32 = run(ssd.SD_PREC_FP32, start, True)
+    out["fp64"], q64 = run(ssd.SD_PREC_FP64, start, True)
+    out["fp32_rel_l2_vs_fp64"] = rel(q32, q64)
     out["fp32_speedup"] = out["fp32"]["value"] / out["fp64"]["value"]
+    if other_start is not None:
+        label, fn = other_start
+        _, i32 = run(ssd.SD_PREC_FP32, fn, False)
+        _, i64 = run(ssd.SD_PREC_FP64, fn, False)
+        out[label + "_fp32_rel_l2_vs_fp64"] = rel(i32, i64)
     return out
+
+
+def run_ellipse(ssd, stream, steps, warmup):
+    """Flow past the rotating ellipse (20096 cells, N = 5, Navier-Stokes,
+    slip / inlet / outlet, cubic cells) from a smooth start that meets the
+    no-slip condition, and the FP32-vs-FP64 difference from the impulsively
+    started free stream."""
+    prm = build_workload("ellipse_n5").params
+    smooth = lambda x, y: fields.ellipse_start(x, y, prm.rho_inf, prm.u_inf, prm.v_inf, prm.p_inf, prm.omega,
+                                               gamma=prm.gamma)
+    impulsive = lambda x, y: fields.uniform(x, y, rho=prm.rho_inf, u=prm.u_inf, v=prm.v_inf, p=prm.p_inf)
+    return run_config(ssd, stream, "ellipse_n5", steps, warmup, smooth,
+                      "free stream blended to the body rotation (no-slip at t = 0)", ("impulsive_start", impulsive))
+
+
+def run_tank(ssd, stream, steps, warmup):
+    """Stirred tank (14752 cells, N = 4, Navier-Stokes, rotating hub and
+    adiabatic blades, baffles) started at rest, as in Sec. 4."""
+    prm = build_workload("tank_n4").params
+    rest = lambda x, y: fields.uniform(x, y, rho=1.0, p=prm.Rgas)
+    return run_config(ssd, stream, "tank_n4", steps, warmup, rest, "uniform fluid at rest (Sec. 4)")
 
 
 def main():
@@ -304,7 +356,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rotor_n6")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32s"])
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=12)
@@ -312,6 +364,8 @@ def main():
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--ellipse-steps", type=int, default=200)
+    ap.add_argument("--tank-steps", type=int, default=200)
+    ap.add_argument("--fp32s-steps", type=int, default=-1, help="FP32-state leg steps (-1: same as --steps)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -331,7 +385,7 @@ def main():
 
     w = build_workload(args.workload)
     N, dt = w.N, w.cfl_dt
-    prec = ssd.SD_PREC_FP32 if args.precision == "fp32" else ssd.SD_PREC_FP64
+    prec = {"fp32": ssd.SD_PREC_FP32, "fp64": ssd.SD_PREC_FP64, "fp32s": ssd.SD_PREC_FP32S}[args.precision]
     stream = torch.cuda.Stream()
     solver = ssd.Solver(w.mesh, N - 1, w.params, precision=prec, stream=stream.cuda_stream)
     Q0 = solver.state_from(lambda x, y: fields.isentropic_vortex(x, y))
@@ -403,11 +457,42 @@ def main():
             pass
         s64.close()
 
+    # FP32 state storage on the same workload: throughput, volume-kernel
+    # roofline and state difference from the FP64 path after the same steps
+    fp32s = None
+    if args.fp32s_steps < 0:
+        args.fp32s_steps = args.steps
+    if prec == ssd.SD_PREC_FP32 and args.fp32s_steps > 0:
+        s3 = ssd.Solver(w.mesh, N - 1, w.params, precision=ssd.SD_PREC_FP32S, stream=stream.cuda_stream)
+        s3.sd_set_state(Q0)
+        s3.sd_step(dt, args.warmup)
+        s3.sd_sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s3.sd_step(dt, args.fp32s_steps)
+        b.record(stream)
+        b.synchronize()
+        s3.sd_sync()
+        ms3 = a.elapsed_time(b)
+        fp32s = {"value": dofs * args.fp32s_steps / (ms3 * 1e-3), "unit": "DOF-updates/s",
+                 "ms_per_step": ms3 / args.fp32s_steps, "steps": args.fp32s_steps, "state_bytes_per_value": 4}
+        if fp64 is not None and args.fp32s_steps == args.steps:
+            Q3 = s3.sd_get_state()
+            fp32s["rel_l2_vs_fp64"] = float(np.sqrt(np.sum((Q3 - Q64) ** 2) / np.sum(Q64 ** 2)))
+        prof3 = s3.sd_profile_step(dt, reps=5)
+        vb3 = volume_bytes_per_element(N, 4, 4) * s3.E
+        ach3 = vb3 / (prof3["volume"] * 1e-3) / 1e9
+        pk, _ = _peaks()
+        fp32s["kernel_ms"] = prof3
+        fp32s["roofline"] = {"bound": "hbm", "achieved": ach3, "peak": pk, "unit": "GB/s", "frac": ach3 / pk,
+                             "kernel": "k_volume", "algorithmic_bytes_per_launch": vb3}
+        s3.close()
+
     # per-kernel timing (CUDA events on the handle's stream) -> roofline of the volume kernel
     prof = solver.sd_profile_step(dt, reps=5)
-    w_c = 4 if prec == ssd.SD_PREC_FP32 else 8
+    w_c = 8 if prec == ssd.SD_PREC_FP64 else 4
     E = solver.E
-    vol_bytes = volume_bytes_per_element(N, w_c) * E
+    vol_bytes = volume_bytes_per_element(N, w_c, 4 if prec == ssd.SD_PREC_FP32S else 8) * E
     peak, peak_src = _peaks()
     achieved = vol_bytes / (prof["volume"] * 1e-3) / 1e9
     traffic = profiled_traffic() if (args.workload == "rotor_n6" and prec == ssd.SD_PREC_FP32) else None
@@ -440,6 +525,7 @@ def main():
 
     batched = run_batched(ssd, args.batch_cases, args.batch_steps) if args.batch_cases > 0 else None
     ellipse = run_ellipse(ssd, stream, args.ellipse_steps, 5) if args.ellipse_steps > 0 else None
+    tank = run_tank(ssd, stream, args.tank_steps, 5) if args.tank_steps > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -452,15 +538,17 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == ssd.SD_PREC_FP32 else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == ssd.SD_PREC_FP64 else "f32",
             "data": "synthetic",
             "config": {"workload": w.name, "elements": E, "N": N, "dofs": dofs, "dt": dt,
-                       "state_precision": "f64", "l2_flush": "state 284 MB > L2 (inputs larger than L2)",
+                       "state_precision": "f32" if prec == ssd.SD_PREC_FP32S else "f64", "l2_flush": "state 284 MB > L2 (inputs larger than L2)",
                        "parallelism": f"replicas x{world}", "description": w.description},
             "l2_error_rho_vs_exact": l2_rho, "t_final": t_end,
             "fp64": fp64,
+            "fp32_state": fp32s,
             "batched": batched,
             "ellipse": ellipse,
+            "tank": tank,
             "kernel_ms": prof,
             "interface_fraction": prof["mortar"] * 3 / prof["step"],
             "fp32_fma_peak_tflops": fp32_peak,

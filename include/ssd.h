@@ -39,7 +39,7 @@ enum {
   SD_ERR_UNSUPPORTED = -6  /* valid request this build does not support (e.g. p) */
 };
 
-enum { SD_PREC_FP64 = 0, SD_PREC_FP32 = 1 };
+enum { SD_PREC_FP64 = 0, SD_PREC_FP32 = 1, SD_PREC_FP32S = 2 };
 
 /* Boundary tags of sd_mesh.bfaces.  Each acts through a ghost state in the
  * Rusanov flux; the state on the boundary is the common solution of the
@@ -50,12 +50,16 @@ enum { SD_PREC_FP64 = 0, SD_PREC_FP32 = 1 };
  *   SLIP   ghost velocity with the normal component of V - V_g mirrored,
  *          interior density and pressure; on the wall that component is 0;
  *   INLET  ghost = the free stream (rho_inf, u_inf, v_inf, p_inf);
- *   OUTLET ghost = interior density and velocity with pressure p_inf. */
+ *   OUTLET ghost = interior density and velocity with pressure p_inf;
+ *   ADIABATIC  as WALL with the interior temperature (density) instead of
+ *          T_wall; its viscous flux has no heat conduction (Sec. 4's stirred
+ *          tank blades). */
 enum {
-  SD_BC_WALL = 1,  /* isothermal no-slip wall moving with its zone */
-  SD_BC_SLIP = 2,  /* slip (inviscid) wall */
-  SD_BC_INLET = 3, /* Dirichlet inflow of the free stream */
-  SD_BC_OUTLET = 4 /* fixed-pressure outflow */
+  SD_BC_WALL = 1,     /* isothermal no-slip wall moving with its zone */
+  SD_BC_SLIP = 2,     /* slip (inviscid) wall */
+  SD_BC_INLET = 3,    /* Dirichlet inflow of the free stream */
+  SD_BC_OUTLET = 4,   /* fixed-pressure outflow */
+  SD_BC_ADIABATIC = 5 /* adiabatic no-slip wall moving with its zone */
 };
 
 /* edge kinds of sd_mesh.edge_arc */
@@ -110,7 +114,11 @@ typedef struct {
   int viscous;      /* 0 Euler, 1 Navier-Stokes */
   int precision;    /* SD_PREC_FP64, or SD_PREC_FP32: FP32 interpolation, flux and
                        divergence arithmetic; FP64 rotation angle, mortar geometry and
-                       projection weights, and FP64 state / Runge-Kutta accumulation */
+                       projection weights, and FP64 state / Runge-Kutta accumulation
+                       (a double-float pair per value); or SD_PREC_FP32S: as SD_PREC_FP32
+                       with the state stored as one float per value, each Runge-Kutta
+                       stage result rounded to float (half the state bytes; the state
+                       carries float round-off, about 6e-8 relative per stage) */
   void *stream;     /* cudaStream_t to queue work on; NULL = a non-blocking stream the handle creates */
   int rk_stages;    /* time integrator: 0 or 3 = three-stage SSP-RK3 (Shu-Osher); 5 = the
                        five-stage fourth-order SSP-RK of Sec. 4 (Spiteri-Ruuth coefficients) */

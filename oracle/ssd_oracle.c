@@ -70,7 +70,7 @@ typedef struct {
 } or_params;
 
 /* boundary tags */
-enum { BC_WALL = 1, BC_SLIP = 2, BC_INLET = 3, BC_OUTLET = 4 };
+enum { BC_WALL = 1, BC_SLIP = 2, BC_INLET = 3, BC_OUTLET = 4, BC_ADIABATIC = 5 };
 /* edge kinds */
 enum { EDGE_STRAIGHT = 0, EDGE_ARC = 1, EDGE_CUBIC = 2 };
 
@@ -333,6 +333,19 @@ static void viscous_flux(const or_params *p, const double *q, const double *qx, 
   G[3] = -(u * txy + v * tyy + kc * Ty);
 }
 
+/* conductive heat flux -k grad T from Q and its gradients (the part of the
+ * energy viscous flux an adiabatic wall removes): returns k T_x, k T_y */
+static void conduction(const or_params *p, const double *q, const double *qx, const double *qy, double *kTx,
+                       double *kTy) {
+  double rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  double T = pressure(p, q) / (rho * p->Rgas);
+  double px = (p->gamma - 1.0) * (qx[3] - (u * qx[1] + v * qx[2] - 0.5 * (u * u + v * v) * qx[0]));
+  double py = (p->gamma - 1.0) * (qy[3] - (u * qy[1] + v * qy[2] - 0.5 * (u * u + v * v) * qy[0]));
+  double kc = p->mu * p->gamma * p->Rgas / ((p->gamma - 1.0) * p->prandtl);
+  *kTx = kc * (px - p->Rgas * T * qx[0]) / (rho * p->Rgas);
+  *kTy = kc * (py - p->Rgas * T * qy[0]) / (rho * p->Rgas);
+}
+
 /* Rusanov common normal flux (Sec. 3.1) across a face with unit normal n
  * pointing from L to R; vgn is the grid velocity normal to the face. */
 static void rusanov(const or_params *p, const double *qL, const double *qR, double nx, double ny, double vgn,
@@ -561,7 +574,7 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
   for (int k = 0; k < nb && !rc; ++k) {
     int ef = 4 * bfaces[3 * k] + bfaces[3 * k + 1];
     int tag = bfaces[3 * k + 2];
-    if (tag < BC_WALL || tag > BC_OUTLET) { snprintf(m->err, sizeof m->err, "unknown boundary tag"); rc = -1; }
+    if (tag < BC_WALL || tag > BC_ADIABATIC) { snprintf(m->err, sizeof m->err, "unknown boundary tag"); rc = -1; }
     if (m->fkind[ef] != FK_NONE) { snprintf(m->err, sizeof m->err, "boundary face repeated"); rc = -1; }
     m->fkind[ef] = FK_BOUNDARY;
     m->ftag[ef] = bfaces[3 * k + 2];
@@ -899,6 +912,10 @@ static void from_primitive(const or_params *p, double rho, double u, double v, d
  * velocity at the point, (nx, ny) the outward unit normal.
  *   wall   (isothermal, no slip, moving with its zone): ghost velocity
  *          2 V_g - V, wall temperature, interior pressure; on the wall V_g;
+ *   adiabatic wall (no slip, moving with its zone; the stirred tank's
+ *          blades, Sec. 4): as the isothermal wall with the interior
+ *          temperature (interior density) instead of the wall temperature;
+ *          its viscous flux carries no heat conduction;
  *   slip:  ghost velocity with the normal velocity relative to the wall
  *          mirrored, interior density and pressure; on the wall that
  *          normal component is zero;
@@ -912,6 +929,9 @@ static void boundary_states(const or_params *p, int tag, const double *qi, doubl
     double rho = pr / (p->Rgas * p->T_wall);
     from_primitive(p, rho, 2.0 * ug - u, 2.0 * vg - v, pr, qg);
     from_primitive(p, rho, ug, vg, pr, qb);
+  } else if (tag == BC_ADIABATIC) {
+    from_primitive(p, qi[0], 2.0 * ug - u, 2.0 * vg - v, pr, qg);
+    from_primitive(p, qi[0], ug, vg, pr, qb);
   } else if (tag == BC_SLIP) {
     double wn = (u - ug) * nx + (v - vg) * ny;
     from_primitive(p, qi[0], u - 2.0 * wn * nx, v - 2.0 * wn * ny, pr, qg);
@@ -1142,6 +1162,12 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
             viscous_flux(P, qc, gbx, gby, Fb, Gb);
             for (int v = 0; v < 4; ++v) Fv_face[((size_t)ef * 4 + v) * N + j] = 0.5 * (fo[v] + Fb[v] * nx + Gb[v] * ny);
           } else if (kind == FK_BOUNDARY) {
+            if (m->ftag[ef] == BC_ADIABATIC) {
+              /* no heat through the wall: remove the conduction term of the energy flux */
+              double kTx, kTy;
+              conduction(P, qc, gx, gy, &kTx, &kTy);
+              fo[3] += kTx * nx + kTy * ny;
+            }
             for (int v = 0; v < 4; ++v) Fv_face[((size_t)ef * 4 + v) * N + j] = fo[v];
           } else {
             /* interface: store F_vis . n with n oriented from L to R, in the

@@ -27,6 +27,7 @@ SD_ERR_TIMEOUT = -5
 SD_ERR_UNSUPPORTED = -6
 SD_PREC_FP64 = 0
 SD_PREC_FP32 = 1
+SD_PREC_FP32S = 2
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)

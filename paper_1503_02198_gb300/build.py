@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libssd.so")
-SOURCES = ["ssd_api.cu", "ssd_f64.cu", "ssd_f32.cu"]
+SOURCES = ["ssd_api.cu", "ssd_f64.cu", "ssd_f32.cu", "ssd_f32s.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

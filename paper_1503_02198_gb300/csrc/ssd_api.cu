@@ -309,7 +309,7 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   for (int k = 0; k < m->n_bfaces; ++k) {
     const int e = m->bfaces[3 * k], f = m->bfaces[3 * k + 1], tag = m->bfaces[3 * k + 2];
     if (e < 0 || e >= E || f < 0 || f > 3) return fail(h, SD_ERR_MESH, "boundary face index out of range");
-    if (tag < SD_BC_WALL || tag > SD_BC_OUTLET) return fail(h, SD_ERR_MESH, "unknown boundary tag");
+    if (tag < SD_BC_WALL || tag > SD_BC_ADIABATIC) return fail(h, SD_ERR_MESH, "unknown boundary tag");
     any_farfield |= tag == SD_BC_INLET || tag == SD_BC_OUTLET;
     if (kind[4 * e + f] != -1) return fail(h, SD_ERR_MESH, "boundary face listed twice");
     kind[4 * e + f] = 1;
@@ -660,7 +660,7 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
     g_create_error = "rk_stages must be 0 or 3 (SSP-RK3) or 5 (SSP-RK(5,4))";
     return SD_ERR_ARG;
   }
-  if (prm->precision != SD_PREC_FP64 && prm->precision != SD_PREC_FP32) {
+  if (prm->precision != SD_PREC_FP64 && prm->precision != SD_PREC_FP32 && prm->precision != SD_PREC_FP32S) {
     g_create_error = "unknown precision";
     return SD_ERR_ARG;
   }
@@ -687,7 +687,9 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
   if (!build_basis(N, hb)) rc = fail(h, SD_ERR_ARG, "singular mortar mass matrix");
   if (!rc) rc = build_mesh(h, m);
   if (!rc) {
-    h->eng = prm->precision == SD_PREC_FP64 ? make_engine_f64(N) : make_engine_f32(N);
+    h->eng = prm->precision == SD_PREC_FP64   ? make_engine_f64(N)
+             : prm->precision == SD_PREC_FP32 ? make_engine_f32(N)
+                                              : make_engine_f32s(N);
     if (!h->eng) rc = fail(h, SD_ERR_UNSUPPORTED, "no engine for this N");
   }
   if (!rc && (ce = cudaMallocHost(&h->h_pinned, 64))) rc = cuda_fail(h, ce, "pinned buffer");

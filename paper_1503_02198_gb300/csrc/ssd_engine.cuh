@@ -656,6 +656,8 @@ __device__ __forceinline__ void from_primitive(T rho, T u, T v, T p, T gm1, T *q
 // the common solution of the viscous terms.  (ug, vg) is the grid velocity at
 // the point, (nx, ny) the outward unit normal.
 //   WALL   ghost velocity 2 V_g - V, wall temperature, interior pressure; qb has V_g
+//   ADIABATIC  the same with the interior temperature; its viscous flux
+//          carries no heat conduction
 //   SLIP   normal velocity relative to the wall mirrored (qb: removed),
 //          interior density and pressure
 //   INLET  the free stream
@@ -666,8 +668,8 @@ __device__ __forceinline__ void boundary_states(const MeshDev &md, int tag, cons
   const T gm1 = (T)(md.gamma - 1.0);
   const T p = pressure_of(q, gm1);
   const T u = q[1] / q[0], v = q[2] / q[0];
-  if (tag == SD_BC_WALL) {
-    const T rho = p / (T)(md.Rgas * md.T_wall);
+  if (tag == SD_BC_WALL || tag == SD_BC_ADIABATIC) {
+    const T rho = tag == SD_BC_WALL ? p / (T)(md.Rgas * md.T_wall) : q[0];
     from_primitive(rho, T(2) * ug - u, T(2) * vg - v, p, gm1, qg);
     from_primitive(rho, ug, vg, p, gm1, qb);
   } else if (tag == SD_BC_SLIP) {
@@ -961,13 +963,13 @@ static __global__ void k_split(const double *__restrict__ Q, float *hi, float *l
   const double x = Q[i];
   const float h = __double2float_rn(x);
   hi[i] = h;
-  lo[i] = __double2float_rn(x - (double)h);
+  if (lo) lo[i] = __double2float_rn(x - (double)h);
 }
 
 static __global__ void k_join(const float *__restrict__ hi, const float *__restrict__ lo, double *Q, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  Q[i] = (double)hi[i] + (double)lo[i];
+  Q[i] = lo ? (double)hi[i] + (double)lo[i] : (double)hi[i];
 }
 
 // face traces [E][4][4][N] of a state (compute-precision values)
@@ -1049,16 +1051,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-template <typename T, int N, bool OTF, bool AUX = false>
+template <typename T, int N, bool OTF, bool AUX = false, bool LO = true>
 struct VolCfg {
   static constexpr int NN = N * N;
-  static constexpr bool FF = std::is_same<T, float>::value;  // double-float state
+  static constexpr bool FF = std::is_same<T, float>::value;  // FP32 arithmetic (packed pairs)
+  static constexpr bool DF = FF && LO;                       // double-float state (hi + lo planes)
   static constexpr int EPB = N == 3 ? 16 : (N == 6 ? 8 : 12);  // elements per tile (multiple of 4)
   static constexpr int THREADS = EPB * 2 * N;                  // one thread per SP line
   // double-buffered part of a tile (needed by the flux phase): state hi,
   // common fluxes, cell records, flags
   static constexpr int QHI = EPB * 4 * NN * (int)sizeof(T);
-  static constexpr int QLO = FF ? EPB * 4 * NN * 4 : 0;
+  static constexpr int QLO = DF ? EPB * 4 * NN * 4 : 0;
   static constexpr int CFB = EPB * 16 * N * (int)sizeof(T);
   static constexpr int EGB = OTF ? EPB * 8 * (int)sizeof(T) : 0;
   static constexpr int EFB = EPB * 4;
@@ -1102,13 +1105,13 @@ struct RkCoef {
   T a0, bdt, g, ddt;
 };
 
-template <typename T, int N, int MODE, bool OTF, bool AUX>
-__global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, OTF, AUX>::MINB)
+template <typename T, int N, int MODE, bool OTF, bool AUX, bool LO>
+__global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T, N, OTF, AUX, LO>::MINB)
     k_volume(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
              T *w_out, const T *w_in, int ntiles) {
-  using C = VolCfg<T, N, OTF, AUX>;
+  using C = VolCfg<T, N, OTF, AUX, LO>;
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
-  constexpr bool FF = C::FF;
+  constexpr bool FF = C::FF, DF = C::DF;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = (uint64_t *)(smem + C::O_BAR);  // [0], [1]: double-buffered part; [2]: single part
   T(*sRF)[4][NN] = (T(*)[4][NN])(smem + C::O_RF);
@@ -1132,10 +1135,10 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
   auto issueB = [&](int tl) {
     const size_t e0 = (size_t)tl * EPB;
     mbar_expect_tx(&bar[2], txB);
-    if (FF) bulk_g2s(smem + C::O_QLO, (const float *)in.lo + e0 * 4 * NN, C::QLO, &bar[2]);
+    if (DF) bulk_g2s(smem + C::O_QLO, (const float *)in.lo + e0 * 4 * NN, C::QLO, &bar[2]);
     if (use_base) {
       bulk_g2s(smem + C::O_NHI, (const T *)base.hi + e0 * 4 * NN, C::QHI, &bar[2]);
-      if (FF) bulk_g2s(smem + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QLO, &bar[2]);
+      if (DF) bulk_g2s(smem + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QLO, &bar[2]);
     }
     if (AUX) bulk_g2s(smem + C::O_AUX, w_in + e0 * 4 * NN, C::AUXB, &bar[2]);
   };
@@ -1343,9 +1346,9 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
           sQ[l2][v][sp] = (T)qn[v];
         }
       } else {
-        // FP32 with a double-float state: the O(dt) increment
-        // inc = a0 (Q_base - Q_k) + w_in + bdt R is formed in float and added to
-        // Q_k exactly (two-sum), so the state keeps ~48 significant bits
+        // FP32: the O(dt) increment inc = a0 (Q_base - Q_k) + w_in + bdt R is
+        // formed in float; with a double-float state it is added to Q_k exactly
+        // (two-sum), so the state keeps ~48 significant bits
         const float(*sKL)[4][NN] = (const float(*)[4][NN])(smem + C::O_QLO);
         const float(*sNH)[4][NN] = (const float(*)[4][NN])(smem + C::O_NHI);
         const float(*sNL)[4][NN] = (const float(*)[4][NN])(smem + C::O_NLO);
@@ -1355,17 +1358,27 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX>::THREADS, VolCfg<T, N, 
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-          const float h = (float)sQ[l2][v][sp], l = sKL[l2][v][sp];
+          const float h = (float)sQ[l2][v][sp];
           float inc = (float)rk.bdt * R;
-          if (use_base) inc = fmaf((float)rk.a0, (sNH[l2][v][sp] - h) + (sNL[l2][v][sp] - l), inc);
-          if (AUX) inc += sW[l2][v][sp];
-          float sum, err;
-          two_sum(h, inc, sum, err);
-          err += l;
-          const float H = sum + err;
-          oh[gi + v * NN] = H;
-          ol[gi + v * NN] = err - (H - sum);
-          hv[v] = H;
+          if constexpr (DF) {
+            const float l = sKL[l2][v][sp];
+            if (use_base) inc = fmaf((float)rk.a0, (sNH[l2][v][sp] - h) + (sNL[l2][v][sp] - l), inc);
+            if (AUX) inc += sW[l2][v][sp];
+            float sum, err;
+            two_sum(h, inc, sum, err);
+            err += l;
+            const float H = sum + err;
+            oh[gi + v * NN] = H;
+            ol[gi + v * NN] = err - (H - sum);
+            hv[v] = H;
+          } else {
+            // single-float state: the stage result is rounded to float once
+            if (use_base) inc = fmaf((float)rk.a0, sNH[l2][v][sp] - h, inc);
+            if (AUX) inc += sW[l2][v][sp];
+            const float H = h + inc;
+            oh[gi + v * NN] = H;
+            hv[v] = H;
+          }
           if (w_out) w_out[gi + v * NN] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
         }
         const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) * __frcp_rn(hv[0]));
@@ -1431,9 +1444,12 @@ static __global__ void k_advance(DevClock *clk, double dt) { clk->t_n = clk->t_n
 // ---------------------------------------------------------------------------
 // engine
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+// LO: FP32 path with a double-float state (hi + lo planes); false: one float
+// per value (FP32 state storage)
+template <typename T, int N, bool LO = true>
 struct EngineImpl : Engine {
   static constexpr bool OTF = std::is_same<T, float>::value;
+  static constexpr bool DF = OTF && LO;
   double *dXs = nullptr, *dXf = nullptr;
   int *scratch_i = nullptr;
   double *scratch_d = nullptr;
@@ -1468,7 +1484,7 @@ struct EngineImpl : Engine {
     cudaError_t e;
     if ((e = cudaMalloc(&sA[0], sizeof(T) * nalloc))) return e;
     if ((e = cudaMalloc(&sB[0], sizeof(T) * nalloc))) return e;
-    if (OTF) {
+    if (DF) {
       if ((e = cudaMalloc(&sA[1], sizeof(float) * nalloc))) return e;
       if ((e = cudaMalloc(&sB[1], sizeof(float) * nalloc))) return e;
     }
@@ -1478,8 +1494,10 @@ struct EngineImpl : Engine {
   StatePtr B() const override { return StatePtr{sB[0], sB[1]}; }
 
   void set_state(const MeshDev &, const double *Q, cudaStream_t s) override {
-    if (OTF)
+    if (DF)
       k_split<<<(unsigned)((nval + 255) / 256), 256, 0, s>>>(Q, (float *)sA[0], (float *)sA[1], nval);
+    else if (OTF)
+      k_split<<<(unsigned)((nval + 255) / 256), 256, 0, s>>>(Q, (float *)sA[0], nullptr, nval);
     else
       cudaMemcpyAsync(sA[0], Q, sizeof(double) * nval, cudaMemcpyDeviceToDevice, s);
   }
@@ -1536,28 +1554,28 @@ struct EngineImpl : Engine {
     }
     {
       // persistent volume kernel: as many CTAs as fit on the GPU at once
-      using C = VolCfg<T, N, OTF>;
+      using C = VolCfg<T, N, OTF, false, LO>;
       int dev = 0, occ0 = 0, occ1 = 0;
       if ((err = cudaGetDevice(&dev))) return err;
       if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return err;
       int occ2 = 0;
-      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RESIDUAL, OTF, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, VolCfg<T, N, OTF, false>::SMEM)))
+      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RESIDUAL, OTF, false, LO>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, VolCfg<T, N, OTF, false, LO>::SMEM)))
         return err;
-      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      VolCfg<T, N, OTF, false>::SMEM)))
+      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF, false, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      VolCfg<T, N, OTF, false, LO>::SMEM)))
         return err;
-      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      VolCfg<T, N, OTF, true>::SMEM)))
+      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF, true, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      VolCfg<T, N, OTF, true, LO>::SMEM)))
         return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_volume<T, N, MODE_RESIDUAL, OTF, false>,
-                                                               C::THREADS, VolCfg<T, N, OTF, false>::SMEM)))
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_volume<T, N, MODE_RESIDUAL, OTF, false, LO>,
+                                                               C::THREADS, VolCfg<T, N, OTF, false, LO>::SMEM)))
         return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_volume<T, N, MODE_RK, OTF, false>, C::THREADS,
-                                                               VolCfg<T, N, OTF, false>::SMEM)))
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_volume<T, N, MODE_RK, OTF, false, LO>, C::THREADS,
+                                                               VolCfg<T, N, OTF, false, LO>::SMEM)))
         return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_volume<T, N, MODE_RK, OTF, true>, C::THREADS,
-                                                               VolCfg<T, N, OTF, true>::SMEM)))
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_volume<T, N, MODE_RK, OTF, true, LO>, C::THREADS,
+                                                               VolCfg<T, N, OTF, true, LO>::SMEM)))
         return err;
       grid_res = std::max(1, occ0) * sms;
       occ_rk = std::max(1, occ1);
@@ -1619,10 +1637,10 @@ struct EngineImpl : Engine {
   template <int MODE, bool AUX>
   void launch_volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk,
                      int grid, cudaStream_t s) {
-    using C = VolCfg<T, N, OTF, AUX>;
+    using C = VolCfg<T, N, OTF, AUX, LO>;
     const int ntiles = (md.E + C::EPB - 1) / C::EPB;
     const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
-    k_volume<T, N, MODE, OTF, AUX><<<std::min(ntiles, grid), C::THREADS, C::SMEM, s>>>(
+    k_volume<T, N, MODE, OTF, AUX, LO><<<std::min(ntiles, grid), C::THREADS, C::SMEM, s>>>(
         md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
   }
 
@@ -1633,10 +1651,10 @@ struct EngineImpl : Engine {
       const int grid = (md.E + EPBv - 1) / EPBv;
       const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
       if (mode == MODE_RESIDUAL)
-        k_volume_visc<T, N, MODE_RESIDUAL, OTF><<<grid, VisCfg<N>::THREADS, 0, s>>>(
+        k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO><<<grid, VisCfg<N>::THREADS, 0, s>>>(
             md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
       else
-        k_volume_visc<T, N, MODE_RK, OTF><<<grid, VisCfg<N>::THREADS, 0, s>>>(
+        k_volume_visc<T, N, MODE_RK, OTF, LO><<<grid, VisCfg<N>::THREADS, 0, s>>>(
             md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
       return;
     }
@@ -1650,14 +1668,14 @@ struct EngineImpl : Engine {
     const size_t nalloc = nalloc_vals;
     cudaError_t e;
     if ((e = cudaMalloc(&sC[0], sizeof(T) * nalloc))) return e;
-    if (OTF && (e = cudaMalloc(&sC[1], sizeof(float) * nalloc))) return e;
+    if (DF && (e = cudaMalloc(&sC[1], sizeof(float) * nalloc))) return e;
     if ((e = cudaMalloc(&sW, sizeof(T) * nalloc))) return e;
     return cudaSuccess;
   }
   StatePtr C() const override { return StatePtr{sC[0], sC[1]}; }
   void *W() const override { return sW; }
 
-  int tile_elems() const override { return VolCfg<T, N, OTF>::EPB; }
+  int tile_elems() const override { return VolCfg<T, N, OTF, false, LO>::EPB; }
 
   // launch shapes chosen by the batch autotuner: volume CTAs per SM (capped
   // by occupancy; 0 keeps the current value) and the face-kernel block size
@@ -1680,13 +1698,13 @@ struct EngineImpl : Engine {
   }
 };
 
-template <typename T>
+template <typename T, bool LO = true>
 Engine *make_engine_t(int N) {
   switch (N) {
-    case 3: return new EngineImpl<T, 3>();
-    case 4: return new EngineImpl<T, 4>();
-    case 5: return new EngineImpl<T, 5>();
-    case 6: return new EngineImpl<T, 6>();
+    case 3: return new EngineImpl<T, 3, LO>();
+    case 4: return new EngineImpl<T, 4, LO>();
+    case 5: return new EngineImpl<T, 5, LO>();
+    case 6: return new EngineImpl<T, 6, LO>();
     default: return nullptr;
   }
 }

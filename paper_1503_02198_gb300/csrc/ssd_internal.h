@@ -157,5 +157,6 @@ struct Engine {
 
 Engine *make_engine_f64(int N);
 Engine *make_engine_f32(int N);
+Engine *make_engine_f32s(int N);
 
 }  // namespace ssd

@@ -24,11 +24,13 @@
 namespace ssd {
 
 // viscous fluxes of Sec. 2.1 (with the paper's leading minus sign) from Q and
-// the physical gradients of the conservative variables
+// the physical gradients of the conservative variables; conduct = false drops
+// the heat conduction (adiabatic walls)
 template <typename T>
-__device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *qy, const MeshDev &md, T *F, T *G) {
+__device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *qy, const MeshDev &md, T *F, T *G,
+                                             bool conduct = true) {
   const T gm1 = (T)(md.gamma - 1.0), Rg = (T)md.Rgas, mu = (T)md.mu;
-  const T kc = (T)(md.mu * md.gamma * md.Rgas / ((md.gamma - 1.0) * md.prandtl));
+  const T kc = conduct ? (T)(md.mu * md.gamma * md.Rgas / ((md.gamma - 1.0) * md.prandtl)) : T(0);
   const T ir = T(1) / q[0];
   const T u = q[1] * ir, v = q[2] * ir;
   const T ux = (qx[1] - u * qx[0]) * ir, uy = (qy[1] - u * qy[0]) * ir;
@@ -190,9 +192,10 @@ __global__ void __launch_bounds__(VisCfg<N>::THREADS) k_grad_trace(MeshDev md, c
 
 // normal viscous flux F_vis . n from Q and the 8 gradient components
 template <typename T>
-__device__ __forceinline__ void viscous_normal(const T *q, const T *g8, T nx, T ny, const MeshDev &md, T *fn) {
+__device__ __forceinline__ void viscous_normal(const T *q, const T *g8, T nx, T ny, const MeshDev &md, T *fn,
+                                               bool conduct = true) {
   T F[4], G[4];
-  viscous_flux(q, g8, g8 + 4, md, F, G);
+  viscous_flux(q, g8, g8 + 4, md, F, G, conduct);
 #pragma unroll
   for (int v = 0; v < 4; ++v) fn[v] = F[v] * nx + G[v] * ny;
 }
@@ -259,7 +262,7 @@ __global__ void k_bface_visc(MeshDev md) {
   boundary_states(md, bf.y, q, ug, vg, nx, ny, qg, qb);
   T Fn[4], fv[4];
   rusanov(q, qg, nx, ny, vgn, (T)md.gamma, Fn);
-  viscous_normal(qb, g8, nx, ny, md, fv);
+  viscous_normal(qb, g8, nx, ny, md, fv, bf.y != SD_BC_ADIABATIC);
   T *CF = (T *)md.CF;
 #pragma unroll
   for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sS * (Fn[v] + fv[v]);
@@ -267,7 +270,7 @@ __global__ void k_bface_visc(MeshDev md) {
 
 // ---- volume ------------------------------------------------------------------
 
-template <typename T, int N, int MODE, bool OTF>
+template <typename T, int N, int MODE, bool OTF, bool LO>
 __global__ void __launch_bounds__(VisCfg<N>::THREADS)
     k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
                   T *w_out, const T *w_in) {
@@ -390,18 +393,28 @@ __global__ void __launch_bounds__(VisCfg<N>::THREADS)
       for (int v = 0; v < 4; ++v) {
         const size_t ii = gi + v * NN;
         const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-        const float h = (float)sQ[l2][v][sp], l = ((const float *)in.lo)[ii];
+        const float h = (float)sQ[l2][v][sp];
         float inc = (float)rk.bdt * R;
-        if (has_base)
-          inc = fmaf((float)rk.a0, (((const float *)base.hi)[ii] - h) + (((const float *)base.lo)[ii] - l), inc);
-        if (w_in) inc += (float)w_in[ii];
-        float sum, err;
-        two_sum(h, inc, sum, err);
-        err += l;
-        const float H = sum + err;
-        ((float *)out.hi)[ii] = H;
-        ((float *)out.lo)[ii] = err - (H - sum);
-        hv[v] = H;
+        if constexpr (LO) {
+          const float l = ((const float *)in.lo)[ii];
+          if (has_base)
+            inc = fmaf((float)rk.a0, (((const float *)base.hi)[ii] - h) + (((const float *)base.lo)[ii] - l), inc);
+          if (w_in) inc += (float)w_in[ii];
+          float sum, err;
+          two_sum(h, inc, sum, err);
+          err += l;
+          const float H = sum + err;
+          ((float *)out.hi)[ii] = H;
+          ((float *)out.lo)[ii] = err - (H - sum);
+          hv[v] = H;
+        } else {
+          // single-float state: the stage result is rounded to float once
+          if (has_base) inc = fmaf((float)rk.a0, ((const float *)base.hi)[ii] - h, inc);
+          if (w_in) inc += (float)w_in[ii];
+          const float H = h + inc;
+          ((float *)out.hi)[ii] = H;
+          hv[v] = H;
+        }
         if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
       }
       const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);

@@ -146,3 +146,20 @@ def random_smooth_state(x, y, seed=1503, amp=0.05, rho0=1.0, p0=1.0, u0=0.3, v0=
 def noise(shape, seed=1503, amp=1e-3):
     rng = np.random.Generator(np.random.PCG64(seed))
     return amp * rng.standard_normal(shape)
+
+
+def ellipse_start(x, y, rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=1.0, omega=0.0, a=0.5, b=0.1, width=1.0,
+                  gamma=1.4):
+    """Uniform density and pressure with a velocity that is the free stream far
+    from the ellipse x^2/a^2 + y^2/b^2 = 1 and the body's rigid rotation
+    omega x r on it: V = phi V_inf + (1 - phi) omega x r with
+    phi = 1 - exp(-(s / width)^2), s = sqrt(x^2/a^2 + y^2/b^2) - 1.  A smooth
+    start that already meets the no-slip condition (unlike the impulsively
+    started free stream)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    s = np.sqrt((x / a) ** 2 + (y / b) ** 2) - 1.0
+    phi = 1.0 - np.exp(-(np.maximum(s, 0.0) / width) ** 2)
+    u = phi * u_inf - (1.0 - phi) * omega * y
+    v = phi * v_inf + (1.0 - phi) * omega * x
+    return conservative(np.full(x.shape, rho_inf), u, v, np.full(x.shape, p_inf), gamma)

@@ -31,7 +31,8 @@ n2=(1,1), n3=(0,1): f0 is eta=0 (n0->n1), f1 is xi=1 (n1->n2), f2 is eta=1
 (n3->n2), f3 is xi=0 (n0->n3).
 
 Boundary tags: 1 isothermal no-slip wall (moving with its zone), 2 slip wall,
-3 inlet (free stream imposed), 4 outlet (free-stream pressure imposed).
+3 inlet (free stream imposed), 4 outlet (free-stream pressure imposed),
+5 adiabatic no-slip wall (moving with its zone).
 
 A cell whose edges are cubic is the paper's 12-node cubic cell (corners plus
 two nodes per edge): the transfinite map through its four edges is the
@@ -47,6 +48,7 @@ BC_WALL = 1
 BC_SLIP = 2
 BC_INLET = 3
 BC_OUTLET = 4
+BC_ADIABATIC = 5
 
 EDGE_STRAIGHT, EDGE_ARC, EDGE_CUBIC = 0, 1, 2
 
@@ -539,9 +541,9 @@ def ellipse_mesh(a=0.5, b=0.1, r_interface=2.0, n_theta=128, n_inner=40, n_outer
 
 
 def channel_mesh(nx=6, ny=4, lx=3.0, ly=2.0, tags=(BC_INLET, BC_OUTLET, BC_SLIP, BC_SLIP),
-                 mapping=None, cubic=False) -> dict:
-    """Stationary rectangle [0, lx] x [0, ly] of nx x ny cells with boundary
-    tags (left, right, bottom, top).  ``mapping`` (x, y) -> (X, Y) moves every
+                 mapping=None, cubic=False, zone=0) -> dict:
+    """Rectangle [0, lx] x [0, ly] of nx x ny cells (all in ``zone``; zone 1
+    rotates about the origin) with boundary tags (left, right, bottom, top).  ``mapping`` (x, y) -> (X, Y) moves every
     node; with ``cubic`` each edge also gets the mapped points at 1/3 and 2/3
     of its length, i.e. the cells are 12-node cubic cells, and a mapping whose
     components are in the cubic serendipity span (x^a y^b with a + b <= 3, or
@@ -568,7 +570,7 @@ def channel_mesh(nx=6, ny=4, lx=3.0, ly=2.0, tags=(BC_INLET, BC_OUTLET, BC_SLIP,
     cell = {}
     for j in range(ny):
         for i in range(nx):
-            cell[(i, j)] = mb.add_cell(look, [ids[i, j], ids[i + 1, j], ids[i + 1, j + 1], ids[i, j + 1]], 0,
+            cell[(i, j)] = mb.add_cell(look, [ids[i, j], ids[i + 1, j], ids[i + 1, j + 1], ids[i, j + 1]], zone,
                                        (), cub)
     bf = []
     for j in range(ny):
@@ -582,3 +584,109 @@ def channel_mesh(nx=6, ny=4, lx=3.0, ly=2.0, tags=(BC_INLET, BC_OUTLET, BC_SLIP,
         e = cell[(i, ny - 1)]
         bf.append((e, _face_of(mb.cells[e], ids[i, ny], ids[i + 1, ny]), tags[3]))
     return _finish(mb, bf, [], [], [], 0.0)
+
+
+def _radii(segments):
+    """Concatenate radial node lists: segments of (r0, r1, layers, ratio);
+    ratio > 1 grows the spacing from r0, ratio < 1 shrinks it towards r1."""
+    out = [segments[0][0]]
+    for r0, r1, n, ratio in segments:
+        if ratio >= 1.0:
+            f = _geometric(n, ratio)
+        else:
+            f = 1.0 - _geometric(n, 1.0 / ratio)[::-1]
+        out.extend(list(r0 + (r1 - r0) * f[1:]))
+    return np.asarray(out)
+
+
+def stirred_tank_mesh(r_hub=0.5, r_interface=3.0, r_tank=5.0, n_blades=6, blade_r=(1.0, 2.0), blade_t=0.1,
+                      n_baffles=4, baffle_h=1.0, baffle_t=0.1, n_theta_in=168, n_theta_out=200,
+                      layers_in=(10, 16, 14), layers_out=(20, 22), shift_L=0.0) -> dict:
+    """Two-dimensional stirred tank (Sec. 4): a rotating hub wall r = r_hub with
+    ``n_blades`` flat blades (radial extent ``blade_r``, thickness ``blade_t``),
+    a sliding interface at r = r_interface, and a stationary tank wall r = r_tank
+    carrying ``n_baffles`` flat baffles (height ``baffle_h``, thickness
+    ``baffle_t``).  Polar grids in both zones (layers refined towards the hub
+    and the tank wall); a blade or baffle removes the two cells on either side
+    of its axis over its radial extent, and the grid lines that bound it are
+    moved onto the plate's faces (offset +-t/2 from the axis), so blades and
+    baffles are exact rectangles.  Tags: hub and tank wall and baffles
+    isothermal walls moving with their zone, blades adiabatic walls."""
+    c = (0.0, 0.0)
+    if n_theta_in % n_blades or n_theta_out % n_baffles:
+        raise ValueError("theta counts must be multiples of the blade / baffle counts")
+    mb = _MeshBuilder(c)
+
+    def zone_grid(table, zone, radii, n_theta, phi0, plates, lo, hi, on_circle_top):
+        """plates: list of axis line indices; the plate spans layers lo..hi."""
+        dth = 2.0 * math.pi / n_theta
+        nl = len(radii) - 1
+        axes = {j: phi0 + j * dth for j in plates}
+        ids = np.zeros((nl + 1, n_theta), dtype=np.int64)
+        for k in range(nl + 1):
+            for j in range(n_theta):
+                r, phi = radii[k], phi0 + j * dth
+                x, y = r * math.cos(phi), r * math.sin(phi)
+                for ja, th in axes.items():
+                    side = (j - ja) % n_theta
+                    if lo <= k <= hi and side in (1, n_theta - 1):
+                        sgn = 1.0 if side == 1 else -1.0
+                        h = 0.5 * (baffle_t if zone == 0 else blade_t)
+                        along = math.sqrt(r * r - h * h) if (on_circle_top and k == nl) else r
+                        x = along * math.cos(th) - sgn * h * math.sin(th)
+                        y = along * math.sin(th) + sgn * h * math.cos(th)
+                ids[k, j] = table.add(x, y)
+        look = _lookup(mb)
+        cells = []
+        for k in range(nl):
+            for j in range(n_theta):
+                if lo <= k < hi and any((j - ja) % n_theta in (0, n_theta - 1) for ja in plates):
+                    continue
+                j1 = (j + 1) % n_theta
+                p, q, r_, s = ids[k, j], ids[k + 1, j], ids[k + 1, j1], ids[k, j1]
+                arcs = []
+                if k == 0:
+                    arcs.append((p, s))
+                if k == nl - 1:
+                    arcs.append((q, r_))
+                cells.append(mb.add_cell(look, [p, q, r_, s], zone, arcs))
+        return cells, ids
+
+    def single_edges(cells):
+        count = {}
+        for e in cells:
+            cl = mb.cells[e]
+            for f, (i, j) in enumerate(FACE_CORNERS):
+                count.setdefault(frozenset((cl[i], cl[j])), []).append((e, f))
+        return {k: v[0] for k, v in count.items() if len(v) == 1}
+
+    # rotating zone: hub .. blade root .. blade tip .. interface
+    rin = _radii([(r_hub, blade_r[0], layers_in[0], 1.15), (blade_r[0], blade_r[1], layers_in[1], 1.0),
+                  (blade_r[1], r_interface, layers_in[2], 1.0)])
+    kb0, kb1 = layers_in[0], layers_in[0] + layers_in[1]
+    tin = mb.node_table()
+    blades = [b * (n_theta_in // n_blades) for b in range(n_blades)]
+    cells_in, ids_in = zone_grid(tin, 1, rin, n_theta_in, shift_L, blades, kb0, kb1, False)
+    # stationary zone: interface .. baffle root .. tank wall
+    rout = _radii([(r_interface, r_tank - baffle_h, layers_out[0], 1.0),
+                   (r_tank - baffle_h, r_tank, layers_out[1], 1.0 / 1.12)])
+    tout = mb.node_table()
+    baffles = [b * (n_theta_out // n_baffles) + n_theta_out // (2 * n_baffles) for b in range(n_baffles)]
+    nlo = len(rout) - 1
+    cells_out, ids_out = zone_grid(tout, 0, rout, n_theta_out, 0.0, baffles, layers_out[0], nlo, True)
+    # boundaries: every unshared edge that is not on the interface
+    ifL = _interface_faces(mb, cells_in, ids_in[-1])
+    ifR = _interface_faces(mb, cells_out, ids_out[0])
+    iface = set(map(tuple, ifL)) | set(map(tuple, ifR))
+    bfaces = []
+    hub = {int(n) for n in ids_in[0]}
+    for edge, (e, f) in single_edges(cells_in).items():
+        if (e, f) in iface:
+            continue
+        bfaces.append((e, f, BC_WALL if edge <= hub else BC_ADIABATIC))
+    for edge, (e, f) in single_edges(cells_out).items():
+        if (e, f) in iface:
+            continue
+        bfaces.append((e, f, BC_WALL))
+    bfaces.sort()
+    return _finish(mb, bfaces, [], ifL, ifR, r_interface)

@@ -98,6 +98,26 @@ def _ellipse(N=5, scale=1.0, omega=0.3, **mesh_kw):
     return mesh, prm, dt
 
 
+def tank_params(omega=1.0, mach=0.1, re=100.0, r_hub=0.5):
+    """Stirred tank: velocity scale = hub wall speed U = omega r_hub at Mach M
+    (R = (U/M)^2 / (gamma T) with T = 1), Re on the hub diameter 2 r_hub,
+    isothermal walls at T = 1; the tank starts at rest."""
+    gamma = 1.4
+    U = omega * r_hub
+    c = U / mach
+    return FlowParams(gamma=gamma, Rgas=c * c / gamma, mu=U * 2.0 * r_hub / re, prandtl=0.72, omega=omega,
+                      viscous=1, T_wall=1.0)
+
+
+def _tank(N=4, **mesh_kw):
+    mesh = meshes.stirred_tank_mesh(**mesh_kw)
+    prm = tank_params()
+    c = math.sqrt(prm.gamma * prm.Rgas)
+    # the paper's step is 1e-4; the explicit limit of this mesh at this N is smaller
+    dt = min(1e-4, stable_dt(mesh, N, prm, c + prm.omega * 3.0))
+    return mesh, prm, dt
+
+
 def build_workload(name: str) -> Workload:
     if name == "couette_n3":
         mesh, prm, dt = _couette()
@@ -114,6 +134,12 @@ def build_workload(name: str) -> Workload:
         return Workload(name, "Navier-Stokes flow past a rotating ellipse (axes 1:0.2), Re=1000, Mach 0.2, "
                         "rotating disk r<=2 at omega=0.3, 20096 curvilinear quads (12-node cubic cells "
                         "around the body), N=5 (p=4)", mesh, 5, prm, dt, 10000)
+    if name == "tank_n4":
+        mesh, prm, dt = _tank(4)
+        return Workload(name, "2D stirred tank: rotating hub r=0.5 with 6 adiabatic blades (r 1-2, "
+                        "thickness 0.1), sliding interface r=3, isothermal tank wall r=5 with 4 baffles "
+                        "(height 1, thickness 0.1); omega=1, Re=100, Mach 0.1 at the hub; 14752 quads, "
+                        "N=4 (p=3)", mesh, 4, prm, dt, 1000)
     if name == "rotor_n6":
         mesh, prm, dt = _rotor_large(6)
         return Workload(name, "vortex through rotor: periodic [-20,20]^2, rotating disk r<=4, "
@@ -121,7 +147,7 @@ def build_workload(name: str) -> Workload:
     raise KeyError(name)
 
 
-WORKLOADS = ("couette_n3", "vortex_n4", "vortex_n5", "ellipse_n5", "rotor_n6")
+WORKLOADS = ("couette_n3", "vortex_n4", "vortex_n5", "ellipse_n5", "tank_n4", "rotor_n6")
 
 
 def min_edge(mesh) -> float:

@@ -1,14 +1,15 @@
 """Parity of the CUDA path with the FP64 oracle on 12-node cubic cells and the
-boundary conditions of the elliptic-cylinder case (Sec. 4: slip walls,
-Dirichlet inlet, fixed-pressure outlet, isothermal no-slip rotating body),
-through the C ABI.  Tolerances as in test_gpu_parity."""
+boundary conditions of Sec. 4's elliptic-cylinder case (slip walls, Dirichlet
+inlet, fixed-pressure outlet, isothermal no-slip rotating body) and stirred
+tank (adiabatic rotating blades, baffles), through the C ABI.  Tolerances as
+in test_gpu_parity."""
 import numpy as np
 import pytest
 
 from helpers import rel_err
 from ssd_inputs import fields, meshes
-from ssd_inputs.meshes import BC_INLET, BC_OUTLET, BC_SLIP
-from ssd_inputs.workloads import FlowParams, build_workload, ellipse_params
+from ssd_inputs.meshes import BC_ADIABATIC, BC_INLET, BC_OUTLET, BC_SLIP
+from ssd_inputs.workloads import FlowParams, build_workload, ellipse_params, tank_params
 
 pytestmark = pytest.mark.gpu
 
@@ -145,3 +146,70 @@ def test_curved_mesh_errors(ssd):
         ssd.Solver(bad, 3, prm)
     with pytest.raises(ssd.SSDError, match="free stream"):
         ssd.Solver(m, 3, FlowParams(rho_inf=0.0, p_inf=1.0))
+
+
+@pytest.mark.parametrize("N", [3, 5])
+@pytest.mark.parametrize("zone", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residual_adiabatic_box(ssd, oracle_mod, N, zone, precision):
+    # closed box of adiabatic no-slip walls, stationary or rotating with the box
+    m = meshes.channel_mesh(4, 3, 3.0, 2.0, tags=(BC_ADIABATIC,) * 4, mapping=_mapping, cubic=True, zone=zone)
+    prm = FlowParams(gamma=1.4, Rgas=1.0, mu=0.05, viscous=1, T_wall=1.3, omega=0.8 * zone)
+    s, o = ssd.Solver(m, N - 1, prm, precision=precision), oracle_mod.Oracle(m, N, prm)
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=12, amp=0.2, scale=1.5))
+    s.sd_set_state(Q)
+    s.sd_set_time(0.3)
+    _check(s.sd_residual(), o.residual(Q, 0.3), TOL32_RESIDUAL if precision else TOL64)
+
+
+def _small_tank():
+    return meshes.stirred_tank_mesh(n_theta_in=48, n_theta_out=40, layers_in=(3, 4, 3), layers_out=(3, 4))
+
+
+def _tank_state(prm, seed):
+    return lambda x, y: fields.random_smooth_state(x, y, seed=seed, amp=0.05, scale=2.0, p0=prm.Rgas, u0=0.1,
+                                                   v0=-0.1, gamma=prm.gamma)
+
+
+@pytest.mark.parametrize("N", [3, 4, 6])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residual_small_tank(ssd, oracle_mod, N, precision):
+    m = _small_tank()
+    prm = tank_params()
+    s, o = ssd.Solver(m, N - 1, prm, precision=precision), oracle_mod.Oracle(m, N, prm)
+    Q = o.state_from(_tank_state(prm, 21))
+    s.sd_set_state(Q)
+    s.sd_set_time(0.77)
+    _check(s.sd_residual(), o.residual(Q, 0.77), TOL32_RESIDUAL if precision else TOL64)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_steps_small_tank(ssd, oracle_mod, precision):
+    # the tank starts at rest; the hub and blades set it moving
+    m = _small_tank()
+    prm = tank_params()
+    s, o = ssd.Solver(m, 3, prm, precision=precision), oracle_mod.Oracle(m, 4, prm)
+    Q = o.state_from(lambda x, y: fields.uniform(x, y, rho=1.0, p=prm.Rgas))
+    dt, n = 5e-5, 10
+    s.sd_set_state(Q)
+    s.sd_step(dt, n)
+    s.sd_sync()
+    Qo, _ = o.step(Q, 0.0, dt, n)
+    Qg = s.sd_get_state()
+    if precision:
+        # the momentum starts at zero (see test_steps_small_ellipse)
+        whole = np.sqrt(((Qg - Qo) ** 2).sum() / (Qo ** 2).sum())
+        assert whole <= TOL32_STATE[0], whole
+        assert (rel_err(Qg, Qo) <= TOL32_STATE[1]).all(), rel_err(Qg, Qo)
+    else:
+        _check(Qg, Qo, TOL64)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residual_full_tank_config(ssd, oracle_mod, precision):
+    w = build_workload("tank_n4")
+    s, o = ssd.Solver(w.mesh, w.N - 1, w.params, precision=precision), oracle_mod.Oracle(w.mesh, w.N, w.params)
+    Q = o.state_from(_tank_state(w.params, 22))
+    s.sd_set_state(Q)
+    s.sd_set_time(2.5)
+    _check(s.sd_residual(), o.residual(Q, 2.5), TOL32_RESIDUAL if precision else TOL64)

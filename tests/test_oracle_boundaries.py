@@ -13,7 +13,11 @@ fixed-pressure outlet), against what geometry and conservation fix:
 - the outlet ghost keeps the interior density and velocity, so the mass
   leaving through it is exactly the integral of rho u . n, which is known in
   closed form for a polynomial state;
-- the free-stream values enter only through the inlet and outlet faces.
+- the free-stream values enter only through the inlet and outlet faces;
+- an adiabatic no-slip wall passes no mass and, at rest, no energy (no work,
+  no heat), so a closed adiabatic box conserves both to round-off, viscous
+  terms included, while an isothermal box exchanges heat; moving adiabatic
+  walls (the stirred tank's blades) still pass no mass.
 """
 import math
 
@@ -22,7 +26,7 @@ import pytest
 
 from helpers import sp_weights
 from ssd_inputs import fields, meshes
-from ssd_inputs.meshes import BC_INLET, BC_OUTLET, BC_SLIP, BC_WALL
+from ssd_inputs.meshes import BC_ADIABATIC, BC_INLET, BC_OUTLET, BC_SLIP, BC_WALL
 from ssd_inputs.workloads import FlowParams
 
 
@@ -198,3 +202,58 @@ def test_ellipse_mesh_is_valid(oracle_mod):
     body = [int(e) for e, f, t in m["bfaces"] if t == BC_WALL]
     r_body = np.hypot(x[body] / 0.5, y[body] / 0.1)
     assert r_body.min() > 1.0  # the SPs lie outside the ellipse
+
+
+def _closed_box_totals(oracle_mod, tag, N=4, zone=0, omega=0.0, seed=12):
+    m = meshes.channel_mesh(4, 3, 3.0, 2.0, tags=(tag,) * 4, mapping=_in_span, cubic=True, zone=zone)
+    prm = FlowParams(gamma=1.4, Rgas=1.0, mu=0.05, viscous=1, T_wall=1.3, omega=omega)
+    o = oracle_mod.Oracle(m, N, prm)
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=seed, amp=0.2, scale=1.5))
+    R = o.residual(Q, 0.3)
+    w = sp_weights(oracle_mod, N)
+    J = o.sp_jacobian()
+    total = np.einsum("evji,eji,j,i->v", R, J, w, w)
+    scale = np.einsum("evji,eji,j,i->v", np.abs(R), J, w, w)
+    return total / scale
+
+
+@pytest.mark.parametrize("N", [3, 5])
+def test_closed_adiabatic_box_conserves_mass_and_energy(oracle_mod, N):
+    rel = _closed_box_totals(oracle_mod, BC_ADIABATIC, N)
+    assert abs(rel[0]) < 1e-13 and abs(rel[3]) < 1e-13, rel
+
+
+def test_closed_isothermal_box_exchanges_heat(oracle_mod):
+    # control: the same box with isothermal walls at a different temperature
+    rel = _closed_box_totals(oracle_mod, BC_WALL)
+    assert abs(rel[3]) > 1e-6, rel
+
+
+def test_moving_adiabatic_walls_pass_no_mass(oracle_mod):
+    # the whole box rotates; its walls move normal to themselves
+    rel = _closed_box_totals(oracle_mod, BC_ADIABATIC, zone=1, omega=0.8)
+    assert abs(rel[0]) < 1e-13, rel
+    assert abs(rel[3]) > 1e-6  # moving walls do work
+
+
+def test_stirred_tank_mesh_is_valid(oracle_mod):
+    m = meshes.stirred_tank_mesh(n_theta_in=48, n_theta_out=40, layers_in=(3, 4, 3), layers_out=(3, 4))
+    tags = np.bincount(m["bfaces"][:, 2], minlength=6)
+    # 6 blades x (2 x 4 long faces + 2 x 2 end faces) adiabatic
+    assert tags[BC_ADIABATIC] == 6 * (2 * 4 + 4)
+    o = oracle_mod.Oracle(m, 4, FlowParams(omega=1.0, viscous=1, mu=0.01, Rgas=25 / 1.4))
+    assert o.sp_jacobian().min() > 0
+    # blades are exact rectangles: every adiabatic face point lies on a plate face
+    x, y = o.sp_coords()
+    for e, f, t in m["bfaces"]:
+        if t != BC_ADIABATIC:
+            continue
+        xe, ye = x[e].mean(), y[e].mean()
+        th = round(math.atan2(ye, xe) / (2 * math.pi / 6)) * (2 * math.pi / 6)
+        en = m["elem_nodes"][e]
+        i, j = meshes.FACE_CORNERS[f]
+        for n in (en[i], en[j]):
+            along = m["xy"][n, 0] * math.cos(th) + m["xy"][n, 1] * math.sin(th)
+            perp = -m["xy"][n, 0] * math.sin(th) + m["xy"][n, 1] * math.cos(th)
+            assert (abs(abs(perp) - 0.05) < 1e-12 and 1.0 - 1e-12 <= along <= 2.0 + 1e-12) or \
+                (abs(perp) <= 0.05 + 1e-12 and min(abs(along - 1.0), abs(along - 2.0)) < 1e-12)
