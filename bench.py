@@ -100,8 +100,8 @@ class ClockSampler:
 # profiles/k_volume_fp32_rotor_n6.md; valid only for the kernel source it was
 # taken on: SHA-256 of the engine text that k_volume is built from (the
 # ElemGeo metrics and VolCfg through the end of k_volume); otherwise null.
-PROFILED_TRAFFIC = {"bytes": (389.16e6 + 328.36e6 + 673.57e6 + 330.60e6 + 673.47e6 + 329.89e6) / 3,
-                    "kernel_sha256": "7df48af09167ef4d2b7ff5c2a9fc923c258c086079b4abce0db10cb0a8b10729"}
+PROFILED_TRAFFIC = {"bytes": (389.06e6 + 328.68e6 + 673.47e6 + 330.91e6 + 673.47e6 + 329.55e6) / 3,
+                    "kernel_sha256": "40f2b8abc1ae603b69139f7534110a2c937e428ce36cf9d0d4e43a1a0714dcd4"}
 
 
 def volume_kernel_source():

@@ -379,6 +379,35 @@ struct ElemGeo {
       g = tab[L::gy + k];
     }
   }
+  // Metric vectors and V_g . a at the interior FPs 1..N-1 of SP line m in
+  // direction d (0: xi line at eta = X_m, 1: eta line at xi = X_m), into
+  // vx/vy/vg[1..N-1].  On straight cells both directions share one form:
+  // with the line's coordinate u = X_{i+1/2}, the tangent of the cross
+  // direction is t = A + u d (A = e3 for xi lines, e1 for eta lines), the
+  // vector is (t_y, -t_x) or (-t_y, t_x), and the point is x0 + u B + X_m t
+  // (B = e1 or e3); no branch depends on the FP.
+  __device__ __forceinline__ void line_metrics(int d, int m, T *vx, T *vy, T *vg) const {
+    if (OTF && tab == nullptr) {
+      const T Ax = d == 0 ? e3x : e1x, Ay = d == 0 ? e3y : e1y;
+      const T Bx = d == 0 ? e1x : e3x, By = d == 0 ? e1y : e3y;
+      const T sg = d == 0 ? T(1) : T(-1), w = cVB<T, N>.Xs[m];
+#pragma unroll
+      for (int i = 1; i < N; ++i) {
+        const T u = cVB<T, N>.Xf[i];
+        const T tx = Ax + u * dx, ty = Ay + u * dy;
+        vx[i] = sg * ty;
+        vy[i] = -sg * tx;
+        const T px = x0 + u * Bx + w * tx, py = y0 + u * By + w * ty;
+        vg[i] = om * (px * vy[i] - py * vx[i]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 1; i < N; ++i) {
+        if (d == 0) xi_fp(i, m, vx[i], vy[i], vg[i]);
+        else eta_fp(m, i, vx[i], vy[i], vg[i]);
+      }
+    }
+  }
   // metric vector of the end FP at point j of face f
   __device__ __forceinline__ void face(int f, int j, T &vx, T &vy, T &g) const {
     if (f == 1) xi_fp(N, j, vx, vy, g);
@@ -1058,26 +1087,43 @@ struct VolCfg {
   static constexpr bool DF = FF && LO;                       // double-float state (hi + lo planes)
   static constexpr int EPB = N == 3 ? 16 : (N == 6 ? 8 : 12);  // elements per tile (multiple of 4)
   static constexpr int THREADS = EPB * 2 * N;                  // one thread per SP line
+  // element strides (values) of the tiles in shared memory: padded so that
+  // the elements of a tile start in different banks (a stride of 4 N^2 or 16 N
+  // words put the SP lines of neighbouring elements on the same banks); every
+  // stride is a multiple of 16 bytes, as a bulk copy's destination must be
+  static constexpr int PADQ = N == 3 ? 8 : (N == 4 ? 16 : (N == 5 ? 24 : 20));
+  static constexpr int SE = 4 * NN + PADQ;  // state hi tile, work arrays
+  static constexpr int SC = 16 * N + 8;     // common-flux tile
+  // bytes one element moves per array
+  static constexpr int QE = 4 * NN * (int)sizeof(T), CE = 16 * N * (int)sizeof(T);
   // double-buffered part of a tile (needed by the flux phase): state hi,
   // common fluxes, cell records, flags
-  static constexpr int QHI = EPB * 4 * NN * (int)sizeof(T);
-  static constexpr int QLO = DF ? EPB * 4 * NN * 4 : 0;
-  static constexpr int CFB = EPB * 16 * N * (int)sizeof(T);
+  static constexpr int QHI = EPB * SE * (int)sizeof(T);
+  static constexpr int CFB = EPB * SC * (int)sizeof(T);
   static constexpr int EGB = OTF ? EPB * 8 * (int)sizeof(T) : 0;
   static constexpr int EFB = EPB * 4;
   static constexpr int O_QHI = 0, O_CF = O_QHI + QHI, O_EG = O_CF + CFB, O_EF = O_EG + EGB;
   static constexpr int STAGE = ((O_EF + EFB) + 127) / 128 * 128;
   // single-buffered part (needed only by the Runge-Kutta phase): state lo,
-  // base state hi and lo; loaded at the start of each tile behind the flux phase
-  static constexpr int AUXB = AUX ? QHI : 0;  // increment carried from an earlier stage
-  static constexpr int O_QLO = 2 * STAGE, O_NHI = O_QLO + QLO, O_NLO = O_NHI + QHI, O_AUX = O_NLO + QLO;
+  // base state hi and lo, carried increment; loaded at the start of each tile
+  // behind the flux phase, unpadded (one copy per array lands sooner than one
+  // per element; its reads are plain runs of consecutive words)
+  static constexpr int QB = EPB * 4 * NN * (int)sizeof(T), QBL = DF ? EPB * 4 * NN * 4 : 0;
+  static constexpr int AUXB = AUX ? QB : 0;  // increment carried from an earlier stage
+  static constexpr int O_QLO = 2 * STAGE, O_NHI = O_QLO + QBL, O_NLO = O_NHI + QB, O_AUX = O_NLO + QBL;
   static constexpr int SINGLE_END = ((O_AUX + AUXB) + 127) / 128 * 128;
   // work arrays
   static constexpr int O_RF = SINGLE_END, O_RG = O_RF + QHI;
   static constexpr int O_BAR = ((O_RG + QHI) + 15) / 16 * 16;
   static constexpr int SMEM = O_BAR + 3 * 8;
-  // resident CTAs per SM the register budget is set for
-  static constexpr int MINB = (200 * 1024 / SMEM) < 8 ? (200 * 1024 / SMEM) : 8;
+  // transaction bytes of the two barriers' copies
+  static constexpr int TX_QHI = EPB * QE, TX_CF = EPB * CE;
+  static_assert((SE * (int)sizeof(T)) % 16 == 0 && (SC * (int)sizeof(T)) % 16 == 0, "bulk-copy alignment");
+  static_assert(QE % 16 == 0 && CE % 16 == 0 && QB % 16 == 0, "bulk-copy sizes");
+  static_assert(EPB <= 32, "one warp-0 lane per element");
+  // resident CTAs per SM the register budget is set for (228 KB of shared
+  // memory per SM, 1 KB of it reserved per CTA)
+  static constexpr int MINB = (228 * 1024 / (SMEM + 1024)) < 8 ? (228 * 1024 / (SMEM + 1024)) : 8;
 };
 
 // transformed ALE inviscid flux at one flux point: a.(F, G) - (V_g . a) Q
@@ -1114,31 +1160,38 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
   constexpr bool FF = C::FF, DF = C::DF;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = (uint64_t *)(smem + C::O_BAR);  // [0], [1]: double-buffered part; [2]: single part
-  T(*sRF)[4][NN] = (T(*)[4][NN])(smem + C::O_RF);
-  T(*sRG)[4][NN] = (T(*)[4][NN])(smem + C::O_RG);
+  T(*sRF)[C::SE] = (T(*)[C::SE])(smem + C::O_RF);
+  T(*sRG)[C::SE] = (T(*)[C::SE])(smem + C::O_RG);
   const VolBasis<T, N> &B = cVB<T, N>;
   const bool use_base = MODE == MODE_RK && has_base;
-  const uint32_t txA = C::QHI + C::CFB + C::EGB + C::EFB;
-  const uint32_t txB = MODE == MODE_RK ? C::QLO + (use_base ? C::QHI + C::QLO : 0) + C::AUXB : 0;
+  const uint32_t txA = C::TX_QHI + C::TX_CF + C::EGB + C::EFB;
+  const uint32_t txB = MODE == MODE_RK ? C::QBL + (use_base ? C::QB + C::QBL : 0) + C::AUXB : 0;
   const T cth = pick<T>(md.clk->c, md.clk->cf), sth = pick<T>(md.clk->s, md.clk->sf);
   const T gm1 = pick<T>(md.gamma, md.gamma_f) - T(1);
 
-  auto issueA = [&](int tl, int st) {
+  // copies are issued by the lanes of warp 0, one element each, into the
+  // padded tile; lane 0 first arms the barrier with the whole byte count
+  auto issueA = [&](int tl, int st, int lane) {
     unsigned char *sb = smem + st * C::STAGE;
     const size_t e0 = (size_t)tl * EPB;
-    mbar_expect_tx(&bar[st], txA);
-    bulk_g2s(sb + C::O_QHI, (const T *)in.hi + e0 * 4 * NN, C::QHI, &bar[st]);
-    bulk_g2s(sb + C::O_CF, (const T *)md.CF + e0 * 16 * N, C::CFB, &bar[st]);
-    if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, C::EGB, &bar[st]);
-    bulk_g2s(sb + C::O_EF, md.eflag + e0, C::EFB, &bar[st]);
+    if (lane == 0) mbar_expect_tx(&bar[st], txA);
+    __syncwarp();
+    if (lane < EPB) {
+      bulk_g2s(sb + C::O_QHI + lane * C::SE * sizeof(T), (const T *)in.hi + (e0 + lane) * 4 * NN, C::QE, &bar[st]);
+      bulk_g2s(sb + C::O_CF + lane * C::SC * sizeof(T), (const T *)md.CF + (e0 + lane) * 16 * N, C::CE, &bar[st]);
+    }
+    if (lane == 0) {
+      if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, C::EGB, &bar[st]);
+      bulk_g2s(sb + C::O_EF, md.eflag + e0, C::EFB, &bar[st]);
+    }
   };
   auto issueB = [&](int tl) {
     const size_t e0 = (size_t)tl * EPB;
     mbar_expect_tx(&bar[2], txB);
-    if (DF) bulk_g2s(smem + C::O_QLO, (const float *)in.lo + e0 * 4 * NN, C::QLO, &bar[2]);
+    if (DF) bulk_g2s(smem + C::O_QLO, (const float *)in.lo + e0 * 4 * NN, C::QBL, &bar[2]);
     if (use_base) {
-      bulk_g2s(smem + C::O_NHI, (const T *)base.hi + e0 * 4 * NN, C::QHI, &bar[2]);
-      if (DF) bulk_g2s(smem + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QLO, &bar[2]);
+      bulk_g2s(smem + C::O_NHI, (const T *)base.hi + e0 * 4 * NN, C::QB, &bar[2]);
+      if (DF) bulk_g2s(smem + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QBL, &bar[2]);
     }
     if (AUX) bulk_g2s(smem + C::O_AUX, w_in + e0 * 4 * NN, C::AUXB, &bar[2]);
   };
@@ -1151,18 +1204,18 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
   }
   __syncthreads();
   int tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) issueA(tile, 0);
+  if (threadIdx.x < 32 && tile < ntiles) issueA(tile, 0, threadIdx.x);
   bool bad = false;
   int it = 0;
   for (; tile < ntiles; tile += gridDim.x, ++it) {
     const int st = it & 1;
     const int next = tile + gridDim.x;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       // both refilled regions were last read before the previous iteration's
       // closing barrier; order those generic reads before the async writes
       fence_proxy_async_smem();
-      if (next < ntiles) issueA(next, st ^ 1);
-      if (txB) issueB(tile);
+      if (next < ntiles) issueA(next, st ^ 1, threadIdx.x);
+      if (txB && threadIdx.x == 0) issueB(tile);
     }
     if (!cta_wait(&bar[st], (uint32_t)((it >> 1) & 1))) {
       if (threadIdx.x == 0) {
@@ -1174,8 +1227,8 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
       return;
     }
     unsigned char *sb = smem + st * C::STAGE;
-    T(*sQ)[4][NN] = (T(*)[4][NN])(sb + C::O_QHI);
-    const T(*sCF)[16 * N] = (const T(*)[16 * N])(sb + C::O_CF);
+    T(*sQ)[C::SE] = (T(*)[C::SE])(sb + C::O_QHI);
+    const T(*sCF)[C::SC] = (const T(*)[C::SC])(sb + C::O_CF);
     const int *sEF = (const int *)(sb + C::O_EF);
     const T *sEG = (const T *)(sb + C::O_EG);
     const int e0 = tile * EPB;
@@ -1188,6 +1241,8 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
     if (le < ne) {
       ElemGeo<T, N, OTF> G;
       G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, cth, sth);
+      T mvx[N + 1], mvy[N + 1], mvg[N + 1];
+      G.line_metrics(d, mline, mvx, mvy, mvg);
       if constexpr (FF) {
         // FP32: variables packed in pairs (rho, rho u), (rho v, E); every
         // interpolation and divergence FMA is a packed FP32x2 FMA
@@ -1195,8 +1250,8 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           const int sp = d == 0 ? mline * N + k : k * N + mline;
-          q2[0][k] = make_float2(sQ[le][0][sp], sQ[le][1][sp]);
-          q2[1][k] = make_float2(sQ[le][2][sp], sQ[le][3][sp]);
+          q2[0][k] = make_float2(sQ[le][(0) * NN + sp], sQ[le][(1) * NN + sp]);
+          q2[1][k] = make_float2(sQ[le][(2) * NN + sp], sQ[le][(3) * NN + sp]);
           acc2[0][k] = make_float2(0.f, 0.f);
           acc2[1][k] = make_float2(0.f, 0.f);
         }
@@ -1216,11 +1271,8 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
               s23 = __ffma2_rn(q2[1][k], h, s23);
             }
             const float qf[4] = {s01.x, s01.y, s23.x, s23.y};
-            T vx, vy, vg;
-            if (d == 0) G.xi_fp(i, mline, vx, vy, vg);
-            else G.eta_fp(mline, i, vx, vy, vg);
             float f[4];
-            point_flux(qf, (float)vx, (float)vy, (float)vg, (float)gm1, f);
+            point_flux(qf, (float)mvx[i], (float)mvy[i], (float)mvg[i], (float)gm1, f);
             f01 = make_float2(f[0], f[1]);
             f23 = make_float2(f[2], f[3]);
           }
@@ -1235,19 +1287,19 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
 #pragma unroll
           for (int k = 0; k < N; ++k) {
             const int sp = mline * N + k;
-            sRF[le][0][sp] = acc2[0][k].x;
-            sRF[le][1][sp] = acc2[0][k].y;
-            sRF[le][2][sp] = acc2[1][k].x;
-            sRF[le][3][sp] = acc2[1][k].y;
+            sRF[le][(0) * NN + sp] = acc2[0][k].x;
+            sRF[le][(1) * NN + sp] = acc2[0][k].y;
+            sRF[le][(2) * NN + sp] = acc2[1][k].x;
+            sRF[le][(3) * NN + sp] = acc2[1][k].y;
           }
         } else {
 #pragma unroll
           for (int k = 0; k < N; ++k) {
             const int sp = k * N + mline;
-            sRG[le][0][sp] = acc2[0][k].x;
-            sRG[le][1][sp] = acc2[0][k].y;
-            sRG[le][2][sp] = acc2[1][k].x;
-            sRG[le][3][sp] = acc2[1][k].y;
+            sRG[le][(0) * NN + sp] = acc2[0][k].x;
+            sRG[le][(1) * NN + sp] = acc2[0][k].y;
+            sRG[le][(2) * NN + sp] = acc2[1][k].x;
+            sRG[le][(3) * NN + sp] = acc2[1][k].y;
           }
         }
       } else {
@@ -1255,7 +1307,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
 #pragma unroll
       for (int k = 0; k < N; ++k)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) q[v][k] = d == 0 ? sQ[le][v][mline * N + k] : sQ[le][v][k * N + mline];
+        for (int v = 0; v < 4; ++v) q[v][k] = d == 0 ? sQ[le][(v) * NN + mline * N + k] : sQ[le][(v) * NN + k * N + mline];
       T acc[4][N];
 #pragma unroll
       for (int k = 0; k < N; ++k)
@@ -1277,10 +1329,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
             for (int k = 0; k < N; ++k) s += q[v][k] * B.Hf[i * N + k];
             qf[v] = s;
           }
-          T vx, vy, vg;
-          if (d == 0) G.xi_fp(i, mline, vx, vy, vg);
-          else G.eta_fp(mline, i, vx, vy, vg);
-          point_flux(qf, vx, vy, vg, gm1, f);
+          point_flux(qf, mvx[i], mvy[i], mvg[i], gm1, f);
         }
 #pragma unroll
         for (int k = 0; k < N; ++k) {
@@ -1293,12 +1342,12 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
 #pragma unroll
         for (int k = 0; k < N; ++k)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) sRF[le][v][mline * N + k] = acc[v][k];
+          for (int v = 0; v < 4; ++v) sRF[le][(v) * NN + mline * N + k] = acc[v][k];
       } else {
 #pragma unroll
         for (int k = 0; k < N; ++k)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) sRG[le][v][k * N + mline] = acc[v][k];
+          for (int v = 0; v < 4; ++v) sRG[le][(v) * NN + k * N + mline] = acc[v][k];
       }
       }
     }
@@ -1321,20 +1370,20 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
       const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
       if (MODE == MODE_RESIDUAL) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+        for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
       } else if (!FF) {
         // FP64: inc = a0 (Q_base - Q_k) + w_in + bdt R;  Q_out = Q_k + inc
-        const double(*sN)[4][NN] = (const double(*)[4][NN])(smem + C::O_NHI);
-        const double(*sW)[4][NN] = (const double(*)[4][NN])(smem + C::O_AUX);
+        const double(*sN)[4 * NN] = (const double(*)[4 * NN])(smem + C::O_NHI);
+        const double(*sW)[4 * NN] = (const double(*)[4 * NN])(smem + C::O_AUX);
         double *qo = (double *)out.hi;
         double qn[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-          const double qk = (double)sQ[l2][v][sp];
+          const double R = -(double)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
+          const double qk = (double)sQ[l2][(v) * NN + sp];
           double inc = (double)rk.bdt * R;
-          if (use_base) inc += (double)rk.a0 * (sN[l2][v][sp] - qk);
-          if (AUX) inc += sW[l2][v][sp];
+          if (use_base) inc += (double)rk.a0 * (sN[l2][(v) * NN + sp] - qk);
+          if (AUX) inc += sW[l2][(v) * NN + sp];
           qn[v] = qk + inc;
           if (w_out) w_out[gi + v * NN] = (T)((double)rk.ddt * R - (double)rk.g * inc);
         }
@@ -1343,27 +1392,27 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           qo[gi + v * NN] = qn[v];
-          sQ[l2][v][sp] = (T)qn[v];
+          sQ[l2][(v) * NN + sp] = (T)qn[v];
         }
       } else {
         // FP32: the O(dt) increment inc = a0 (Q_base - Q_k) + w_in + bdt R is
         // formed in float; with a double-float state it is added to Q_k exactly
         // (two-sum), so the state keeps ~48 significant bits
-        const float(*sKL)[4][NN] = (const float(*)[4][NN])(smem + C::O_QLO);
-        const float(*sNH)[4][NN] = (const float(*)[4][NN])(smem + C::O_NHI);
-        const float(*sNL)[4][NN] = (const float(*)[4][NN])(smem + C::O_NLO);
-        const float(*sW)[4][NN] = (const float(*)[4][NN])(smem + C::O_AUX);
+        const float(*sKL)[4 * NN] = (const float(*)[4 * NN])(smem + C::O_QLO);
+        const float(*sNH)[4 * NN] = (const float(*)[4 * NN])(smem + C::O_NHI);
+        const float(*sNL)[4 * NN] = (const float(*)[4 * NN])(smem + C::O_NLO);
+        const float(*sW)[4 * NN] = (const float(*)[4 * NN])(smem + C::O_AUX);
         float *oh = (float *)out.hi, *ol = (float *)out.lo;
         float hv[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-          const float h = (float)sQ[l2][v][sp];
+          const float R = -(float)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
+          const float h = (float)sQ[l2][(v) * NN + sp];
           float inc = (float)rk.bdt * R;
           if constexpr (DF) {
-            const float l = sKL[l2][v][sp];
-            if (use_base) inc = fmaf((float)rk.a0, (sNH[l2][v][sp] - h) + (sNL[l2][v][sp] - l), inc);
-            if (AUX) inc += sW[l2][v][sp];
+            const float l = sKL[l2][(v) * NN + sp];
+            if (use_base) inc = fmaf((float)rk.a0, (sNH[l2][(v) * NN + sp] - h) + (sNL[l2][(v) * NN + sp] - l), inc);
+            if (AUX) inc += sW[l2][(v) * NN + sp];
             float sum, err;
             two_sum(h, inc, sum, err);
             err += l;
@@ -1373,8 +1422,8 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
             hv[v] = H;
           } else {
             // single-float state: the stage result is rounded to float once
-            if (use_base) inc = fmaf((float)rk.a0, sNH[l2][v][sp] - h, inc);
-            if (AUX) inc += sW[l2][v][sp];
+            if (use_base) inc = fmaf((float)rk.a0, sNH[l2][(v) * NN + sp] - h, inc);
+            if (AUX) inc += sW[l2][(v) * NN + sp];
             const float H = h + inc;
             oh[gi + v * NN] = H;
             hv[v] = H;
@@ -1384,7 +1433,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
         const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) * __frcp_rn(hv[0]));
         bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) sQ[l2][v][sp] = (T)hv[v];
+        for (int v = 0; v < 4; ++v) sQ[l2][(v) * NN + sp] = (T)hv[v];
       }
     }
     if (MODE == MODE_RK) {
@@ -1402,7 +1451,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
 #pragma unroll
             for (int k = 0; k < N; ++k) {
               const int sp = d == 0 ? mline * N + k : k * N + mline;
-              const float2 qk = make_float2(sQ[le][2 * vp][sp], sQ[le][2 * vp + 1][sp]);
+              const float2 qk = make_float2(sQ[le][(2 * vp) * NN + sp], sQ[le][(2 * vp + 1) * NN + sp]);
               a0 = __ffma2_rn(qk, B.H02[k], a0);
               a1 = __ffma2_rn(qk, B.H12[k], a1);
             }
@@ -1417,7 +1466,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
             T a0 = 0, a1 = 0;
 #pragma unroll
             for (int k = 0; k < N; ++k) {
-              const T qk = d == 0 ? sQ[le][v][mline * N + k] : sQ[le][v][k * N + mline];
+              const T qk = d == 0 ? sQ[le][(v) * NN + mline * N + k] : sQ[le][(v) * NN + k * N + mline];
               a0 += qk * B.H0[k];
               a1 += qk * B.H1[k];
             }
