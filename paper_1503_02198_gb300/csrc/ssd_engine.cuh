@@ -1509,6 +1509,7 @@ struct EngineImpl : Engine {
   int grid_res = 1, grid_rk = 1, grid_aux = 1;  // persistent grid sizes of the volume kernel
   int sms = 1, occ_rk = 1;         // SM count, resident volume CTAs per SM
   int face_block = 256;            // block size of the conforming-face kernel
+  int face_block_max = 256;        // the most threads per block its registers allow
 
   ~EngineImpl() override {
     cudaFree(dXs);
@@ -1631,6 +1632,12 @@ struct EngineImpl : Engine {
       grid_rk = occ_rk * sms;
       grid_aux = std::max(1, occ2) * sms;
     }
+    {
+      cudaFuncAttributes fa;
+      if ((err = cudaFuncGetAttributes(&fa, k_face<T, N, OTF>))) return err;
+      face_block_max = fa.maxThreadsPerBlock / 32 * 32;
+      face_block = std::min(face_block, face_block_max);
+    }
     if (md.nTab > 0) k_geo<T, N><<<(md.nTab + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
     k_egeo<T, N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, dXf);
     if (md.nF > 0) k_fgeo<T, N, OTF><<<(md.nF * N + 127) / 128, 128, 0, s>>>(md);
@@ -1670,8 +1677,8 @@ struct EngineImpl : Engine {
     if (md.nF > 0) k_face_cq<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
     if (md.nB > 0) k_bface_cq<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
     if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
-    constexpr int EPBv = VisCfg<N>::EPB;
-    k_grad_trace<T, N, OTF><<<(md.E + EPBv - 1) / EPBv, VisCfg<N>::THREADS, 0, s>>>(md, (const T *)q.hi);
+    constexpr int EPBv = VisCfg<T, N>::EPB;
+    k_grad_trace<T, N, OTF><<<(md.E + EPBv - 1) / EPBv, VisCfg<T, N>::THREADS, 0, s>>>(md, (const T *)q.hi);
     if (md.nF > 0) k_face_visc<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
     if (md.nB > 0) k_bface_visc<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
   }
@@ -1696,14 +1703,14 @@ struct EngineImpl : Engine {
   void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk, int mode,
               cudaStream_t s) override {
     if (md.viscous) {
-      constexpr int EPBv = VisCfg<N>::EPB;
+      constexpr int EPBv = VisCfg<T, N>::EPB;
       const int grid = (md.E + EPBv - 1) / EPBv;
       const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
       if (mode == MODE_RESIDUAL)
-        k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO><<<grid, VisCfg<N>::THREADS, 0, s>>>(
+        k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO><<<grid, VisCfg<T, N>::THREADS, 0, s>>>(
             md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
       else
-        k_volume_visc<T, N, MODE_RK, OTF, LO><<<grid, VisCfg<N>::THREADS, 0, s>>>(
+        k_volume_visc<T, N, MODE_RK, OTF, LO><<<grid, VisCfg<T, N>::THREADS, 0, s>>>(
             md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
       return;
     }
@@ -1735,7 +1742,7 @@ struct EngineImpl : Engine {
       *vol_ctas_per_sm = grid_rk / sms;
     }
     if (fblock) {
-      if (*fblock > 0) face_block = *fblock;
+      if (*fblock > 0) face_block = std::min(*fblock, face_block_max);
       *fblock = face_block;
     }
   }

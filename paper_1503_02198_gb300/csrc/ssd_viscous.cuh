@@ -93,10 +93,16 @@ __global__ void k_bface_cq(MeshDev md) {
 
 // ---- gradients ---------------------------------------------------------------
 
-template <int N>
+// Elements per block of the viscous kernels (two threads per SP line pair:
+// 2 N threads per element): chosen so that a block is whole warps where the
+// 48 KB of static shared memory of k_volume_visc (20 N^2 + 32 N values per
+// element) allows it.
+template <typename T, int N>
 struct VisCfg {
-  static constexpr int EPB = N <= 4 ? 8 : 4;
+  static constexpr bool F = sizeof(T) == 4;
+  static constexpr int EPB = N == 3 ? 16 : (N == 4 ? 8 : (N == 5 ? (F ? 16 : 8) : (F ? 8 : 4)));
   static constexpr int THREADS = EPB * 2 * N;
+  static_assert(EPB * (20 * N * N + 32 * N) * (int)sizeof(T) <= 48 * 1024, "static shared memory");
 };
 
 // Gradients at the SPs of a tile (thread per SP line, then per SP): on
@@ -105,7 +111,7 @@ template <typename T, int N, bool OTF>
 __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne, T (*sQ)[4][N * N],
                                                T (*sCQ)[16 * N], T (*sDx)[4][N * N], T (*sDe)[4][N * N], T cth,
                                                T sth) {
-  constexpr int NN = N * N, NT = VisCfg<N>::THREADS;
+  constexpr int NN = N * N, NT = VisCfg<T, N>::THREADS;
   const VolBasis<T, N> &B = cVB<T, N>;
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
@@ -151,8 +157,8 @@ __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne
 
 // gradient traces GTR [E][4 faces][8][N]: component v = dQ_v/dx, 4 + v = dQ_v/dy
 template <typename T, int N, bool OTF>
-__global__ void __launch_bounds__(VisCfg<N>::THREADS) k_grad_trace(MeshDev md, const T *__restrict__ Q) {
-  constexpr int EPB = VisCfg<N>::EPB, NT = VisCfg<N>::THREADS, NN = N * N;
+__global__ void __launch_bounds__(VisCfg<T, N>::THREADS) k_grad_trace(MeshDev md, const T *__restrict__ Q) {
+  constexpr int EPB = VisCfg<T, N>::EPB, NT = VisCfg<T, N>::THREADS, NN = N * N;
   __shared__ T sQ[EPB][4][NN];
   __shared__ T sCQ[EPB][16 * N];
   __shared__ T sDx[EPB][4][NN];
@@ -271,10 +277,10 @@ __global__ void k_bface_visc(MeshDev md) {
 // ---- volume ------------------------------------------------------------------
 
 template <typename T, int N, int MODE, bool OTF, bool LO>
-__global__ void __launch_bounds__(VisCfg<N>::THREADS)
+__global__ void __launch_bounds__(VisCfg<T, N>::THREADS)
     k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
                   T *w_out, const T *w_in) {
-  constexpr int EPB = VisCfg<N>::EPB, NT = VisCfg<N>::THREADS, NN = N * N;
+  constexpr int EPB = VisCfg<T, N>::EPB, NT = VisCfg<T, N>::THREADS, NN = N * N;
   constexpr bool FF = std::is_same<T, float>::value;
   __shared__ T sQ[EPB][4][NN];
   __shared__ T sCQ[EPB][16 * N];
