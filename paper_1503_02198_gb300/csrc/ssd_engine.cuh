@@ -14,8 +14,9 @@
 //   k_clock_merge   1 CTA: theta = omega t_k; merge of the rotated L node
 //                   angles with the R node angles -> mortars, (o, s) of each
 //                   mortar against its L and R face (Eq. xz), face ranges
-//   k_face          conforming and periodic faces: Rusanov common flux
-//   k_bface         boundary faces (wall, slip, inlet, outlet): Rusanov through a ghost state
+//   k_faces         one launch for every face point: conforming and periodic
+//                   faces (Rusanov common flux), then boundary faces (wall,
+//                   slip, inlet, outlet, adiabatic: Rusanov through a ghost state)
 //   k_mortar_flux   per mortar: L2 projection of both sides' face traces
 //                   (Eq. prjQ2), Rusanov at the mortar SPs, back-projection
 //                   weights of the common flux (Eq. prjF2)
@@ -639,9 +640,7 @@ __global__ void k_fgeo(MeshDev md) {
 // Conforming and periodic faces: one thread per face point; geometry from the
 // t = 0 face table, the normal turned by R(theta) on the rotating zone.
 template <typename T, int N, bool OTF>
-__global__ void k_face(MeshDev md) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= md.nF * N) return;
+__device__ __forceinline__ void k_face_point(const MeshDev &md, int t) {
   const int fi = t / N, j = t - fi * N;
   const int4 fc = md.faces[fi];
   const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
@@ -743,9 +742,7 @@ __device__ __forceinline__ void bface_geom(const MeshDev &md, int b, int j, T &n
 
 // Boundary faces: Rusanov through the ghost state of the face's condition.
 template <typename T, int N, bool OTF>
-__global__ void k_bface(MeshDev md) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= md.nB * N) return;
+__device__ __forceinline__ void k_bface_point(const MeshDev &md, int t) {
   const int b = t / N, j = t - b * N;
   const int4 bf = md.bfaces[b];
   const int ef = bf.x;
@@ -761,6 +758,15 @@ __global__ void k_bface(MeshDev md) {
   T *CF = (T *)md.CF;
 #pragma unroll
   for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sS * Fn[v];
+}
+
+// One launch for all face points of a stage: threads [0, nF N) take the
+// conforming and periodic faces, the next nB N threads the boundary faces.
+template <typename T, int N, bool OTF>
+__global__ void k_faces(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < md.nF * N) k_face_point<T, N, OTF>(md, t);
+  else if (t < (md.nF + md.nB) * N) k_bface_point<T, N, OTF>(md, t - md.nF * N);
 }
 
 // Mortar coupling of Sec. 3.2.  Thread (mortar, side, p): p is a quadrature
@@ -1634,7 +1640,7 @@ struct EngineImpl : Engine {
     }
     {
       cudaFuncAttributes fa;
-      if ((err = cudaFuncGetAttributes(&fa, k_face<T, N, OTF>))) return err;
+      if ((err = cudaFuncGetAttributes(&fa, k_faces<T, N, OTF>))) return err;
       face_block_max = fa.maxThreadsPerBlock / 32 * 32;
       face_block = std::min(face_block, face_block_max);
     }
@@ -1668,19 +1674,17 @@ struct EngineImpl : Engine {
   }
 
   void faces(const MeshDev &md, StatePtr q, cudaStream_t s) override {
+    const int np = (md.nF + md.nB) * N;
     if (!md.viscous) {
-      if (md.nF > 0) k_face<T, N, OTF><<<(md.nF * N + face_block - 1) / face_block, face_block, 0, s>>>(md);
-      if (md.nB > 0) k_bface<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
+      if (np > 0) k_faces<T, N, OTF><<<(np + face_block - 1) / face_block, face_block, 0, s>>>(md);
       return;
     }
     // common solution, gradient traces, then common inviscid + viscous fluxes
-    if (md.nF > 0) k_face_cq<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
-    if (md.nB > 0) k_bface_cq<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
+    if (np > 0) k_faces_cq<T, N, OTF><<<(np + 255) / 256, 256, 0, s>>>(md);
     if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
     constexpr int EPBv = VisCfg<T, N>::EPB;
     k_grad_trace<T, N, OTF><<<(md.E + EPBv - 1) / EPBv, VisCfg<T, N>::THREADS, 0, s>>>(md, (const T *)q.hi);
-    if (md.nF > 0) k_face_visc<T, N><<<(md.nF * N + 255) / 256, 256, 0, s>>>(md);
-    if (md.nB > 0) k_bface_visc<T, N, OTF><<<(md.nB * N + 127) / 128, 128, 0, s>>>(md);
+    if (np > 0) k_faces_visc<T, N, OTF><<<(np + 255) / 256, 256, 0, s>>>(md);
   }
 
   void mortars(const MeshDev &md, cudaStream_t s) override {

@@ -3,7 +3,7 @@
 // faces; Sec. 3.2 viscous mortar procedure).  Included by ssd_engine.cuh.
 //
 // Per stage, after the stage clock and mortar merge:
-//   k_face_cq / k_bface_cq     common solution Q_c on conforming faces (average)
+//   k_faces_cq                 common solution Q_c on conforming faces (average)
 //                              and boundaries (the state on the boundary)
 //   k_mortar_flux<MORTAR_AVG_Q> + gather   Q_c on the interface: both sides
 //                              projected to the mortars, averaged, projected back
@@ -11,7 +11,7 @@
 //                              SPs (derivative of the degree-N polynomial through
 //                              the FP values with Q_c at the end FPs, chain rule
 //                              with the SP metrics), interpolated to the faces
-//   k_face_visc / k_bface_visc Rusanov + average of both sides' viscous normal
+//   k_faces_visc               Rusanov + average of both sides' viscous normal
 //                              flux evaluated with Q_c (boundaries: boundary state,
 //                              interior gradient)
 //   k_mortar_flux<MORTAR_RUSANOV> + gather, then <MORTAR_AVG_FV> + gather-add:
@@ -56,9 +56,7 @@ __device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *q
 // ---- common solution -------------------------------------------------------
 
 template <typename T, int N>
-__global__ void k_face_cq(MeshDev md) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= md.nF * N) return;
+__device__ __forceinline__ void k_face_cq_point(const MeshDev &md, int t) {
   const int fi = t / N, j = t - fi * N;
   const int4 fc = md.faces[fi];
   const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
@@ -74,9 +72,7 @@ __global__ void k_face_cq(MeshDev md) {
 
 // boundary faces: the common solution is the state on the boundary
 template <typename T, int N, bool OTF>
-__global__ void k_bface_cq(MeshDev md) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= md.nB * N) return;
+__device__ __forceinline__ void k_bface_cq_point(const MeshDev &md, int t) {
   const int b = t / N, j = t - b * N;
   const int4 bf = md.bfaces[b];
   const int ef = bf.x;
@@ -89,6 +85,14 @@ __global__ void k_bface_cq(MeshDev md) {
   boundary_states(md, bf.y, q, ug, vg, nx, ny, qg, qb);
 #pragma unroll
   for (int v = 0; v < 4; ++v) ((T *)md.CQ)[((size_t)ef * 4 + v) * N + j] = qb[v];
+}
+
+// common solution at all face points of a stage (conforming, then boundary)
+template <typename T, int N, bool OTF>
+__global__ void k_faces_cq(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < md.nF * N) k_face_cq_point<T, N>(md, t);
+  else if (t < (md.nF + md.nB) * N) k_bface_cq_point<T, N, OTF>(md, t - md.nF * N);
 }
 
 // ---- gradients ---------------------------------------------------------------
@@ -207,9 +211,7 @@ __device__ __forceinline__ void viscous_normal(const T *q, const T *g8, T nx, T 
 }
 
 template <typename T, int N>
-__global__ void k_face_visc(MeshDev md) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= md.nF * N) return;
+__device__ __forceinline__ void k_face_visc_point(const MeshDev &md, int t) {
   const int fi = t / N, j = t - fi * N;
   const int4 fc = md.faces[fi];
   const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
@@ -251,9 +253,7 @@ __global__ void k_face_visc(MeshDev md) {
 // boundary faces: Rusanov through the ghost state plus the viscous flux of the
 // boundary state with the interior gradient
 template <typename T, int N, bool OTF>
-__global__ void k_bface_visc(MeshDev md) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= md.nB * N) return;
+__device__ __forceinline__ void k_bface_visc_point(const MeshDev &md, int t) {
   const int b = t / N, j = t - b * N;
   const int4 bf = md.bfaces[b];
   const int ef = bf.x;
@@ -272,6 +272,14 @@ __global__ void k_bface_visc(MeshDev md) {
   T *CF = (T *)md.CF;
 #pragma unroll
   for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sS * (Fn[v] + fv[v]);
+}
+
+// common inviscid + viscous fluxes at all face points of a stage
+template <typename T, int N, bool OTF>
+__global__ void k_faces_visc(MeshDev md) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < md.nF * N) k_face_visc_point<T, N>(md, t);
+  else if (t < (md.nF + md.nB) * N) k_bface_visc_point<T, N, OTF>(md, t - md.nF * N);
 }
 
 // ---- volume ------------------------------------------------------------------
