@@ -341,6 +341,14 @@ def run_ellipse(ssd, stream, steps, warmup):
                       "free stream blended to the body rotation (no-slip at t = 0)", ("impulsive_start", impulsive))
 
 
+def run_couette(ssd, stream, steps, warmup):
+    """Taylor-Couette flow (288 cells, N = 3, Navier-Stokes, rotating inner
+    wall) for the configuration's 200 steps from the quiescent uniform state."""
+    prm = build_workload("couette_n3").params
+    rest = lambda x, y: fields.uniform(x, y, rho=1.0, p=prm.Rgas)
+    return run_config(ssd, stream, "couette_n3", steps, warmup, rest, "uniform fluid at rest, T = T_wall")
+
+
 def run_tank(ssd, stream, steps, warmup):
     """Stirred tank (14752 cells, N = 4, Navier-Stokes, rotating hub and
     adiabatic blades, baffles) started at rest, as in Sec. 4."""
@@ -365,6 +373,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=50)
     ap.add_argument("--ellipse-steps", type=int, default=200)
     ap.add_argument("--tank-steps", type=int, default=200)
+    ap.add_argument("--couette-steps", type=int, default=200)
     ap.add_argument("--fp32s-steps", type=int, default=-1, help="FP32-state leg steps (-1: same as --steps)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -526,6 +535,7 @@ def main():
     batched = run_batched(ssd, args.batch_cases, args.batch_steps) if args.batch_cases > 0 else None
     ellipse = run_ellipse(ssd, stream, args.ellipse_steps, 5) if args.ellipse_steps > 0 else None
     tank = run_tank(ssd, stream, args.tank_steps, 5) if args.tank_steps > 0 else None
+    couette = run_couette(ssd, stream, args.couette_steps, 5) if args.couette_steps > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -549,6 +559,7 @@ def main():
             "batched": batched,
             "ellipse": ellipse,
             "tank": tank,
+            "couette": couette,
             "kernel_ms": prof,
             "interface_fraction": prof["mortar"] * 3 / prof["step"],
             "fp32_fma_peak_tflops": fp32_peak,

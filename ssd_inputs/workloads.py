@@ -57,10 +57,16 @@ def _couette(scale=1, N=3, omega=0.5, mach=0.1, re=10.0):
     return mesh, prm, dt
 
 
+def vortex_family(N=4, scale=1):
+    """The vortex configuration's mesh refined ``scale`` times (h / scale),
+    its flow parameters and a stable step: (mesh, FlowParams, dt)."""
+    return _vortex(N, scale)
+
+
 def _vortex(N=4, scale=1):
-    mesh = meshes.rotor_mesh(half_width=10.0, n_cart=64 * scale, n_hole=24 * scale,
-                             r_interface=3.0, n_core=24 * scale, core_half=1.5,
-                             n_ring_in=16 * scale, n_ring_out=4 * scale)
+    mesh = meshes.rotor_mesh(half_width=10.0, n_cart=int(round(64 * scale)), n_hole=int(round(24 * scale)),
+                             r_interface=3.0, n_core=int(round(24 * scale)), core_half=1.5,
+                             n_ring_in=int(round(16 * scale)), n_ring_out=max(1, int(round(4 * scale))))
     prm = FlowParams(gamma=1.4, Rgas=1.0, omega=math.pi / 4, viscous=0)
     h = 3.0 / 24 / scale
     dt = 0.1 * h / ((1.0 + math.sqrt(1.4) + 3.0 * math.pi / 4 * 0 + 2.0) * N * N)
