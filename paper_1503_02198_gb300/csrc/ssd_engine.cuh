@@ -779,15 +779,20 @@ struct MortCfg {
   static constexpr int THREADS = MPB * 2 * N;
 };
 
-enum { MORTAR_RUSANOV = 0, MORTAR_AVG_Q = 1, MORTAR_AVG_FV = 2 };
+// RUSANOV: inviscid common flux; AVG_Q: common solution (average); RUSANOV_FV:
+// the inviscid common flux plus the average of both sides' viscous normal
+// fluxes, both projected in one pass and back-projected as one sum (the
+// back-projection is linear, Eq. prjF2)
+enum { MORTAR_RUSANOV = 0, MORTAR_AVG_Q = 1, MORTAR_RUSANOV_FV = 2 };
 
 template <typename T, int N, int MMODE>
 __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md) {
   constexpr int MPB = MortCfg<N>::MPB;
+  constexpr int NV = MMODE == MORTAR_RUSANOV_FV ? 8 : 4;  // projected values per point
   __shared__ double sH[MPB][2][N][N];  // h_i(o + s z_q) [q][i]
-  __shared__ T sQf[MPB][2][4][N];      // face values, CCW order
-  __shared__ T sA[MPB][2][4][N];       // work arrays
-  __shared__ T sB[MPB][2][4][N];
+  __shared__ T sQf[MPB][2][NV][N];     // face values, CCW order (+ viscous normal flux)
+  __shared__ T sA[MPB][2][NV][N];      // work arrays
+  __shared__ T sB[MPB][2][NV][N];
   __shared__ T sF[MPB][4][N];          // common mortar flux at mortar SPs
   __shared__ T sFz[MPB][4][N];         // common flux at quadrature points
   const int lm = threadIdx.x / (2 * N);
@@ -817,7 +822,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     ef = fc.x;
     rev = fc.y;
     const int jj = rev ? N - 1 - p : p;
-    if (MMODE == MORTAR_AVG_FV) {
+    if (MMODE == MORTAR_RUSANOV_FV) {
       // viscous normal flux of this face point with the common solution and
       // the face's own gradient, along the radial normal (from L to R)
       const T *CQ = (const T *)md.CQ, *GT = (const T *)md.GTR;
@@ -833,8 +838,9 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
       sincos(fa + B.Xs[p] * (sd ? md.Rw[fq] : md.Lw[fq]), &sn, &cs);
       viscous_normal(q, g8, (T)cs, (T)sn, md, fn);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) sQf[lm][sd][v][p] = fn[v];
-    } else {
+      for (int v = 0; v < 4; ++v) sQf[lm][sd][NV - 4 + v][p] = fn[v];
+    }
+    {
       const T *TR = (const T *)md.TR;
 #pragma unroll
       for (int v = 0; v < 4; ++v) sQf[lm][sd][v][p] = TR[((size_t)ef * 4 + v) * N + jj];
@@ -857,7 +863,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
   // (A) face polynomial at the mapped quadrature points
   if (act) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < NV; ++v) {
       T acc = 0;
 #pragma unroll
       for (int i = 0; i < N; ++i) acc += sQf[lm][sd][v][i] * (T)sH[lm][sd][p][i];
@@ -868,7 +874,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
   // (B) right-hand side of Eq. prjQ1: (S^T Q)_p = sum_q w_q h_p(z_q) Q(o + s z_q)
   if (act) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < NV; ++v) {
       T acc = 0;
 #pragma unroll
       for (int q = 0; q < N; ++q) acc += (T)(B.wq[q] * B.Hz[q * N + p]) * sA[lm][sd][v][q];
@@ -879,7 +885,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
   // (C) Q^Xi = M^{-1} S^T Q^Omega (Eq. prjQ2)
   if (act) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < NV; ++v) {
       T acc = 0;
 #pragma unroll
       for (int k = 0; k < N; ++k) acc += (T)B.Minv[p * N + k] * sB[lm][sd][v][k];
@@ -890,7 +896,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
   // (D) Rusanov at mortar SP p with the radial normal (the grid velocity of
   // a rotation about the circle's centre is tangential: v_g . n = 0)
   if (act && sd == 0) {
-    if (MMODE == MORTAR_RUSANOV) {
+    if (MMODE != MORTAR_AVG_Q) {
       double sn, cs;
       sincos(fma(B.Xs[p], dm, m0), &sn, &cs);
       T qL[4], qR[4], Fn[4];
@@ -901,7 +907,9 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
       }
       rusanov(qL, qR, (T)cs, (T)sn, T(0), (T)md.gamma, Fn);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) sF[lm][v][p] = Fn[v];
+      for (int v = 0; v < 4; ++v)
+        sF[lm][v][p] = MMODE == MORTAR_RUSANOV_FV ? Fn[v] + T(0.5) * (sA[lm][0][4 + v][p] + sA[lm][1][4 + v][p])
+                                                  : Fn[v];
     } else {
       // common value on the mortar: average of both sides (Sec. 3.2)
 #pragma unroll
@@ -948,7 +956,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
 // face's mortars in counter-clockwise order), written as the face's common
 // flux F~_end = sigma_f |S| F.n_out (n from L to R is outward for L, inward
 // for R).  One thread per (side, face, point).
-enum { GATHER_FLUX = 0, GATHER_Q = 1, GATHER_FLUX_ADD = 2 };
+enum { GATHER_FLUX = 0, GATHER_Q = 1 };
 
 template <typename T, int N, int GMODE>
 __global__ void k_mortar_gather(MeshDev md) {
@@ -983,7 +991,7 @@ __global__ void k_mortar_gather(MeshDev md) {
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const size_t i = ((size_t)ef * 4 + v) * N + j;
-    CF[i] = GMODE == GATHER_FLUX_ADD ? CF[i] + sc * acc[v] : sc * acc[v];
+    CF[i] = sc * acc[v];
   }
 }
 
@@ -1689,8 +1697,8 @@ struct EngineImpl : Engine {
 
   void mortars(const MeshDev &md, cudaStream_t s) override {
     if (md.nL > 0) {
-      mortar_pass<MORTAR_RUSANOV, GATHER_FLUX>(md, s);
-      if (md.viscous) mortar_pass<MORTAR_AVG_FV, GATHER_FLUX_ADD>(md, s);
+      if (md.viscous) mortar_pass<MORTAR_RUSANOV_FV, GATHER_FLUX>(md, s);
+      else mortar_pass<MORTAR_RUSANOV, GATHER_FLUX>(md, s);
     }
   }
 

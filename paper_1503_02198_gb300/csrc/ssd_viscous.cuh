@@ -14,9 +14,10 @@
 //   k_faces_visc               Rusanov + average of both sides' viscous normal
 //                              flux evaluated with Q_c (boundaries: boundary state,
 //                              interior gradient)
-//   k_mortar_flux<MORTAR_RUSANOV> + gather, then <MORTAR_AVG_FV> + gather-add:
-//                              inviscid mortar flux, then the viscous normal flux
-//                              of both sides projected, averaged, projected back
+//   k_mortar_flux<MORTAR_RUSANOV_FV> + gather: traces and the viscous normal
+//                              flux of both sides projected to the mortars in one
+//                              pass, Rusanov + average of the viscous fluxes,
+//                              projected back as one sum
 //   k_volume_visc              inviscid + viscous fluxes at interior FPs,
 //                              divergence, Runge-Kutta update, traces
 #pragma once
