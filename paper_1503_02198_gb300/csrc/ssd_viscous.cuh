@@ -107,6 +107,8 @@ struct VisCfg {
   static constexpr bool F = sizeof(T) == 4;
   static constexpr int EPB = N == 3 ? 16 : (N == 4 ? 8 : (N == 5 ? (F ? 16 : 8) : (F ? 8 : 4)));
   static constexpr int THREADS = EPB * 2 * N;
+  // resident blocks per SM the register budget is set for: about 16 warps
+  static constexpr int MINB = 16 / ((THREADS + 31) / 32) > 0 ? 16 / ((THREADS + 31) / 32) : 1;
   static_assert(EPB * (20 * N * N + 32 * N) * (int)sizeof(T) <= 48 * 1024, "static shared memory");
 };
 
@@ -286,7 +288,7 @@ __global__ void k_faces_visc(MeshDev md) {
 // ---- volume ------------------------------------------------------------------
 
 template <typename T, int N, int MODE, bool OTF, bool LO>
-__global__ void __launch_bounds__(VisCfg<T, N>::THREADS)
+__global__ void __launch_bounds__(VisCfg<T, N>::THREADS, VisCfg<T, N>::MINB)
     k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
                   T *w_out, const T *w_in) {
   constexpr int EPB = VisCfg<T, N>::EPB, NT = VisCfg<T, N>::THREADS, NN = N * N;
