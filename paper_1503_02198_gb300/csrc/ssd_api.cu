@@ -708,6 +708,18 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
     md.u_inf = prm->u_inf;
     md.v_inf = prm->v_inf;
     md.p_inf = prm->p_inf;
+    md.gm1 = prm->gamma - 1.0;
+    md.kc = prm->mu * prm->gamma * prm->Rgas / ((prm->gamma - 1.0) * prm->prandtl);
+    md.RTw = prm->Rgas * prm->T_wall;
+    md.gm1_f = (float)md.gm1;
+    md.Rgas_f = (float)prm->Rgas;
+    md.mu_f = (float)prm->mu;
+    md.kc_f = (float)md.kc;
+    md.RTw_f = (float)md.RTw;
+    md.rho_inf_f = (float)prm->rho_inf;
+    md.u_inf_f = (float)prm->u_inf;
+    md.v_inf_f = (float)prm->v_inf;
+    md.p_inf_f = (float)prm->p_inf;
     if (md.any_farfield && (!(prm->rho_inf > 0.0) || !(prm->p_inf > 0.0) || !std::isfinite(prm->u_inf) ||
                             !std::isfinite(prm->v_inf)))
       rc = fail(h, SD_ERR_ARG, "inlet / outlet faces need a free stream with rho_inf > 0 and p_inf > 0");

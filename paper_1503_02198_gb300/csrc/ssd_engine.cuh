@@ -693,11 +693,11 @@ __device__ __forceinline__ void from_primitive(T rho, T u, T v, T p, T gm1, T *q
 template <typename T>
 __device__ __forceinline__ void boundary_states(const MeshDev &md, int tag, const T *q, T ug, T vg, T nx, T ny, T *qg,
                                                 T *qb) {
-  const T gm1 = (T)(md.gamma - 1.0);
+  const T gm1 = pick<T>(md.gm1, md.gm1_f);
   const T p = pressure_of(q, gm1);
   const T u = q[1] / q[0], v = q[2] / q[0];
   if (tag == SD_BC_WALL || tag == SD_BC_ADIABATIC) {
-    const T rho = tag == SD_BC_WALL ? p / (T)(md.Rgas * md.T_wall) : q[0];
+    const T rho = tag == SD_BC_WALL ? p / pick<T>(md.RTw, md.RTw_f) : q[0];
     from_primitive(rho, T(2) * ug - u, T(2) * vg - v, p, gm1, qg);
     from_primitive(rho, ug, vg, p, gm1, qb);
   } else if (tag == SD_BC_SLIP) {
@@ -705,11 +705,13 @@ __device__ __forceinline__ void boundary_states(const MeshDev &md, int tag, cons
     from_primitive(q[0], u - T(2) * wn * nx, v - T(2) * wn * ny, p, gm1, qg);
     from_primitive(q[0], u - wn * nx, v - wn * ny, p, gm1, qb);
   } else if (tag == SD_BC_INLET) {
-    from_primitive((T)md.rho_inf, (T)md.u_inf, (T)md.v_inf, (T)md.p_inf, gm1, qg);
-    from_primitive((T)md.rho_inf, (T)md.u_inf, (T)md.v_inf, (T)md.p_inf, gm1, qb);
+    const T ri = pick<T>(md.rho_inf, md.rho_inf_f), ui = pick<T>(md.u_inf, md.u_inf_f);
+    const T vi = pick<T>(md.v_inf, md.v_inf_f), pi = pick<T>(md.p_inf, md.p_inf_f);
+    from_primitive(ri, ui, vi, pi, gm1, qg);
+    from_primitive(ri, ui, vi, pi, gm1, qb);
   } else {
-    from_primitive(q[0], u, v, (T)md.p_inf, gm1, qg);
-    from_primitive(q[0], u, v, (T)md.p_inf, gm1, qb);
+    from_primitive(q[0], u, v, pick<T>(md.p_inf, md.p_inf_f), gm1, qg);
+    from_primitive(q[0], u, v, pick<T>(md.p_inf, md.p_inf_f), gm1, qb);
   }
 }
 
@@ -754,7 +756,7 @@ __device__ __forceinline__ void k_bface_point(const MeshDev &md, int t) {
   bface_geom<T, N, OTF>(md, b, j, nx, ny, sS, vgn, ug, vg);
   boundary_states(md, bf.y, q, ug, vg, nx, ny, qg, qb);
   T Fn[4];
-  rusanov(q, qg, nx, ny, vgn, (T)md.gamma, Fn);
+  rusanov(q, qg, nx, ny, vgn, pick<T>(md.gamma, md.gamma_f), Fn);
   T *CF = (T *)md.CF;
 #pragma unroll
   for (int v = 0; v < 4; ++v) CF[((size_t)ef * 4 + v) * N + j] = sS * Fn[v];
@@ -905,7 +907,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
         qL[v] = sA[lm][0][v][p];
         qR[v] = sA[lm][1][v][p];
       }
-      rusanov(qL, qR, (T)cs, (T)sn, T(0), (T)md.gamma, Fn);
+      rusanov(qL, qR, (T)cs, (T)sn, T(0), pick<T>(md.gamma, md.gamma_f), Fn);
 #pragma unroll
       for (int v = 0; v < 4; ++v)
         sF[lm][v][p] = MMODE == MORTAR_RUSANOV_FV ? Fn[v] + T(0.5) * (sA[lm][0][4 + v][p] + sA[lm][1][4 + v][p])

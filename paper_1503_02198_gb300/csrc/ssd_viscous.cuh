@@ -30,8 +30,8 @@ namespace ssd {
 template <typename T>
 __device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *qy, const MeshDev &md, T *F, T *G,
                                              bool conduct = true) {
-  const T gm1 = (T)(md.gamma - 1.0), Rg = (T)md.Rgas, mu = (T)md.mu;
-  const T kc = conduct ? (T)(md.mu * md.gamma * md.Rgas / ((md.gamma - 1.0) * md.prandtl)) : T(0);
+  const T gm1 = pick<T>(md.gm1, md.gm1_f), Rg = pick<T>(md.Rgas, md.Rgas_f), mu = pick<T>(md.mu, md.mu_f);
+  const T kc = conduct ? pick<T>(md.kc, md.kc_f) : T(0);
   const T ir = T(1) / q[0];
   const T u = q[1] * ir, v = q[2] * ir;
   const T ux = (qx[1] - u * qx[0]) * ir, uy = (qy[1] - u * qy[0]) * ir;
@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(VisCfg<T, N>::THREADS) k_grad_trace(MeshDev md
   for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) (&sQ[0][0][0])[i] = Q[(size_t)e0 * 4 * NN + i];
   for (int i = threadIdx.x; i < ne * 16 * N; i += NT) (&sCQ[0][0])[i] = ((const T *)md.CQ)[(size_t)e0 * 16 * N + i];
   __syncthreads();
-  tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, (T)md.clk->c, (T)md.clk->s);
+  tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, pick<T>(md.clk->c, md.clk->cf),
+                            pick<T>(md.clk->s, md.clk->sf));
   __syncthreads();
   const VolBasis<T, N> &B = cVB<T, N>;
   const int le = threadIdx.x / (2 * N);
@@ -235,13 +236,13 @@ __device__ __forceinline__ void k_face_visc_point(const MeshDev &md, int t) {
   T nx = g[j], ny = g[N + j];
   const T sA = g[2 * N + j], sB = g[3 * N + j], vgn = g[4 * N + j];
   if (md.eflag[efA >> 2] & 1) {
-    const T c = (T)md.clk->c, s = (T)md.clk->s;
+    const T c = pick<T>(md.clk->c, md.clk->cf), s = pick<T>(md.clk->s, md.clk->sf);
     const T rx = c * nx - s * ny, ry = s * nx + c * ny;
     nx = rx;
     ny = ry;
   }
   T Fn[4], va[4], vb[4];
-  rusanov(qA, qB, nx, ny, vgn, (T)md.gamma, Fn);
+  rusanov(qA, qB, nx, ny, vgn, pick<T>(md.gamma, md.gamma_f), Fn);
   viscous_normal(qc, gA, nx, ny, md, va);
   viscous_normal(qc, gB, nx, ny, md, vb);
   T *CF = (T *)md.CF;
@@ -270,7 +271,7 @@ __device__ __forceinline__ void k_bface_visc_point(const MeshDev &md, int t) {
   bface_geom<T, N, OTF>(md, b, j, nx, ny, sS, vgn, ug, vg);
   boundary_states(md, bf.y, q, ug, vg, nx, ny, qg, qb);
   T Fn[4], fv[4];
-  rusanov(q, qg, nx, ny, vgn, (T)md.gamma, Fn);
+  rusanov(q, qg, nx, ny, vgn, pick<T>(md.gamma, md.gamma_f), Fn);
   viscous_normal(qb, g8, nx, ny, md, fv, bf.y != SD_BC_ADIABATIC);
   T *CF = (T *)md.CF;
 #pragma unroll
@@ -309,10 +310,10 @@ __global__ void __launch_bounds__(VisCfg<T, N>::THREADS, VisCfg<T, N>::MINB)
     (&sCF[0][0])[i] = ((const T *)md.CF)[(size_t)e0 * 16 * N + i];
   }
   __syncthreads();
-  const T cth = (T)md.clk->c, sth = (T)md.clk->s;
+  const T cth = pick<T>(md.clk->c, md.clk->cf), sth = pick<T>(md.clk->s, md.clk->sf);
   tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, cth, sth);
   __syncthreads();
-  const T gm1 = (T)(md.gamma - 1.0);
+  const T gm1 = pick<T>(md.gm1, md.gm1_f);
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
   const int d = r / N, m = r - d * N;
