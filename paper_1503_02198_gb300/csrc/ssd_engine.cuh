@@ -58,9 +58,12 @@ template <int N>
 struct MortBasis {
   double zq[N], wq[N];  // Gauss-Legendre on [0,1]
   double Hz[N * N];     // h_j(z_q) [q][j]
+  double wHz[N * N];    // w_q h_j(z_q) [q][j]
   double Minv[N * N];   // M^{-1}
   double Xs[N];         // solution points
   double cden[N];       // 1 / prod_{s != i}(X_i - X_s)
+  // the same rounded to float, for the FP32 contractions
+  float Hz_f[N * N], wHz_f[N * N], Minv_f[N * N];
 };
 
 template <typename T, int N>
@@ -791,7 +794,10 @@ template <typename T, int N, int MMODE>
 __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md) {
   constexpr int MPB = MortCfg<N>::MPB;
   constexpr int NV = MMODE == MORTAR_RUSANOV_FV ? 8 : 4;  // projected values per point
-  __shared__ double sH[MPB][2][N][N];  // h_i(o + s z_q) [q][i]
+  // h_i(o + s z_q) and w_q h_i(o + s z_q) [q][i]: formed in FP64, stored in
+  // the compute type once
+  __shared__ T sH[MPB][2][N][N];
+  __shared__ T sWH[MPB][2][N][N];
   __shared__ T sQf[MPB][2][NV][N];     // face values, CCW order (+ viscous normal flux)
   __shared__ T sA[MPB][2][NV][N];      // work arrays
   __shared__ T sB[MPB][2][NV][N];
@@ -858,7 +864,8 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
 #pragma unroll
       for (int k = 0; k < N; ++k)
         if (k != i) h *= dif[k];
-      sH[lm][sd][p][i] = h;
+      sH[lm][sd][p][i] = (T)h;
+      sWH[lm][sd][p][i] = (T)(B.wq[p] * h);
     }
   }
   __syncthreads();
@@ -868,7 +875,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     for (int v = 0; v < NV; ++v) {
       T acc = 0;
 #pragma unroll
-      for (int i = 0; i < N; ++i) acc += sQf[lm][sd][v][i] * (T)sH[lm][sd][p][i];
+      for (int i = 0; i < N; ++i) acc += sQf[lm][sd][v][i] * sH[lm][sd][p][i];
       sA[lm][sd][v][p] = acc;
     }
   }
@@ -879,7 +886,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     for (int v = 0; v < NV; ++v) {
       T acc = 0;
 #pragma unroll
-      for (int q = 0; q < N; ++q) acc += (T)(B.wq[q] * B.Hz[q * N + p]) * sA[lm][sd][v][q];
+      for (int q = 0; q < N; ++q) acc += pick<T>(B.wHz[q * N + p], B.wHz_f[q * N + p]) * sA[lm][sd][v][q];
       sB[lm][sd][v][p] = acc;
     }
   }
@@ -890,7 +897,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     for (int v = 0; v < NV; ++v) {
       T acc = 0;
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc += (T)B.Minv[p * N + k] * sB[lm][sd][v][k];
+      for (int k = 0; k < N; ++k) acc += pick<T>(B.Minv[p * N + k], B.Minv_f[p * N + k]) * sB[lm][sd][v][k];
       sA[lm][sd][v][p] = acc;
     }
   }
@@ -925,7 +932,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     for (int v = 0; v < 4; ++v) {
       T acc = 0;
 #pragma unroll
-      for (int j = 0; j < N; ++j) acc += (T)B.Hz[p * N + j] * sF[lm][v][j];
+      for (int j = 0; j < N; ++j) acc += pick<T>(B.Hz[p * N + j], B.Hz_f[p * N + j]) * sF[lm][v][j];
       sFz[lm][v][p] = acc;
     }
   }
@@ -936,7 +943,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     for (int v = 0; v < 4; ++v) {
       T acc = 0;
 #pragma unroll
-      for (int q = 0; q < N; ++q) acc += (T)(B.wq[q] * sH[lm][sd][q][p]) * sFz[lm][v][q];
+      for (int q = 0; q < N; ++q) acc += sWH[lm][sd][q][p] * sFz[lm][v][q];
       sB[lm][sd][v][p] = acc;
     }
   }
@@ -948,7 +955,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     for (int v = 0; v < 4; ++v) {
       T acc = 0;
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc += (T)B.Minv[p * N + k] * sB[lm][sd][v][k];
+      for (int k = 0; k < N; ++k) acc += pick<T>(B.Minv[p * N + k], B.Minv_f[p * N + k]) * sB[lm][sd][v][k];
       out[v * N + p] = (T)s * acc;
     }
   }
@@ -1602,6 +1609,10 @@ struct EngineImpl : Engine {
     for (int k = 0; k < N * N; ++k) {
       mb.Hz[k] = hb.Hz[k];
       mb.Minv[k] = hb.Minv[k];
+      mb.wHz[k] = hb.wq[k / N] * hb.Hz[k];
+      mb.Hz_f[k] = (float)mb.Hz[k];
+      mb.wHz_f[k] = (float)mb.wHz[k];
+      mb.Minv_f[k] = (float)mb.Minv[k];
     }
     cudaError_t err;
     if ((err = cudaMemcpyToSymbolAsync(cVB<T, N>, &vb, sizeof vb, 0, cudaMemcpyHostToDevice, s))) return err;
