@@ -492,10 +492,11 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   if (otf && (e = cudaMemsetAsync(md.egeo, 0, w * Ep * 8, h->stream))) return e;
   if ((e = dalloc(h, &md.TR, w * Ep * 16 * N))) return e;
   if ((e = dalloc(h, &md.CF, w * Ep * 16 * N))) return e;
-  md.CQ = md.GTR = nullptr;
+  md.CQ = md.GTR = md.GSP = nullptr;
   if (md.viscous) {
     if ((e = dalloc(h, &md.CQ, w * Ep * 16 * N))) return e;
     if ((e = dalloc(h, &md.GTR, w * Ep * 32 * N))) return e;
+    if ((e = dalloc(h, &md.GSP, w * Ep * 8 * N * N))) return e;
   }
   if ((e = dalloc(h, &md.contrib, w * 2 * nb * 4 * N))) return e;
   if ((e = dalloc(h, &md.mLf, sizeof(int) * nb))) return e;

@@ -82,6 +82,7 @@ struct MeshDev {
   void *egeo;             // T [E][8] bilinear record x0, y0, e1, e3, d of each cell
   void *TR, *CF;          // T [E][4][4][N] face traces and common fluxes
   void *CQ, *GTR;         // viscous: T [E][4][4][N] common solution, [E][4][8][N] gradient traces
+  void *GSP;              // viscous: T [E][8][N][N] gradients at the SPs (x then y, 4 variables each)
   void *fgeo;             // T [nF][5][N] conforming-face geometry at t = 0: unit normal
                           // (x, y) out of side A, sigma_A |S_A|, sigma_B |S_B|, V_g . n
   DevClock *clk;

@@ -10,7 +10,8 @@
 //   k_grad_trace               gradients of the conservative variables at the
 //                              SPs (derivative of the degree-N polynomial through
 //                              the FP values with Q_c at the end FPs, chain rule
-//                              with the SP metrics), interpolated to the faces
+//                              with the SP metrics), stored for k_volume_visc and
+//                              interpolated to the faces
 //   k_faces_visc               Rusanov + average of both sides' viscous normal
 //                              flux evaluated with Q_c (boundaries: boundary state,
 //                              interior gradient)
@@ -18,8 +19,9 @@
 //                              flux of both sides projected to the mortars in one
 //                              pass, Rusanov + average of the viscous fluxes,
 //                              projected back as one sum
-//   k_volume_visc              inviscid + viscous fluxes at interior FPs,
-//                              divergence, Runge-Kutta update, traces
+//   k_volume_visc              inviscid + viscous fluxes at interior FPs (with
+//                              the stored SP gradients), divergence, Runge-Kutta
+//                              update, traces
 #pragma once
 
 namespace ssd {
@@ -100,7 +102,7 @@ __global__ void k_faces_cq(MeshDev md) {
 
 // Elements per block of the viscous kernels (two threads per SP line pair:
 // 2 N threads per element): chosen so that a block is whole warps where the
-// 48 KB of static shared memory of k_volume_visc (20 N^2 + 32 N values per
+// 48 KB of static shared memory of k_volume_visc (20 N^2 + 16 N values per
 // element) allows it.
 template <typename T, int N>
 struct VisCfg {
@@ -109,7 +111,7 @@ struct VisCfg {
   static constexpr int THREADS = EPB * 2 * N;
   // resident blocks per SM the register budget is set for: about 16 warps
   static constexpr int MINB = 16 / ((THREADS + 31) / 32) > 0 ? 16 / ((THREADS + 31) / 32) : 1;
-  static_assert(EPB * (20 * N * N + 32 * N) * (int)sizeof(T) <= 48 * 1024, "static shared memory");
+  static_assert(EPB * (20 * N * N + 16 * N) * (int)sizeof(T) <= 48 * 1024, "static shared memory");
 };
 
 // Gradients at the SPs of a tile (thread per SP line, then per SP): on
@@ -178,6 +180,13 @@ __global__ void __launch_bounds__(VisCfg<T, N>::THREADS) k_grad_trace(MeshDev md
   tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, pick<T>(md.clk->c, md.clk->cf),
                             pick<T>(md.clk->s, md.clk->sf));
   __syncthreads();
+  // the SP gradients for the volume kernel of this stage
+  for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) {
+    const int l2 = i / (4 * NN), r = i - l2 * 4 * NN;
+    T *gs = (T *)md.GSP + (size_t)(e0 + l2) * 8 * NN;
+    gs[r] = (&sDx[0][0][0])[i];
+    gs[4 * NN + r] = (&sDe[0][0][0])[i];
+  }
   const VolBasis<T, N> &B = cVB<T, N>;
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
@@ -295,7 +304,6 @@ __global__ void __launch_bounds__(VisCfg<T, N>::THREADS, VisCfg<T, N>::MINB)
   constexpr int EPB = VisCfg<T, N>::EPB, NT = VisCfg<T, N>::THREADS, NN = N * N;
   constexpr bool FF = std::is_same<T, float>::value;
   __shared__ T sQ[EPB][4][NN];
-  __shared__ T sCQ[EPB][16 * N];
   __shared__ T sCF[EPB][16 * N];
   __shared__ T sDx[EPB][4][NN];
   __shared__ T sDe[EPB][4][NN];
@@ -304,15 +312,18 @@ __global__ void __launch_bounds__(VisCfg<T, N>::THREADS, VisCfg<T, N>::MINB)
   const VolBasis<T, N> &B = cVB<T, N>;
   const int e0 = blockIdx.x * EPB;
   const int ne = min(EPB, md.E - e0);
-  for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) (&sQ[0][0][0])[i] = ((const T *)in.hi)[(size_t)e0 * 4 * NN + i];
-  for (int i = threadIdx.x; i < ne * 16 * N; i += NT) {
-    (&sCQ[0][0])[i] = ((const T *)md.CQ)[(size_t)e0 * 16 * N + i];
-    (&sCF[0][0])[i] = ((const T *)md.CF)[(size_t)e0 * 16 * N + i];
+  // the state, the common fluxes and the SP gradients that k_grad_trace
+  // formed from this state in this stage
+  const T *gsp = (const T *)md.GSP + (size_t)e0 * 8 * NN;
+  for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) {
+    (&sQ[0][0][0])[i] = ((const T *)in.hi)[(size_t)e0 * 4 * NN + i];
+    const int l2 = i / (4 * NN), r = i - l2 * 4 * NN;
+    (&sDx[0][0][0])[i] = gsp[(size_t)l2 * 8 * NN + r];
+    (&sDe[0][0][0])[i] = gsp[(size_t)l2 * 8 * NN + 4 * NN + r];
   }
+  for (int i = threadIdx.x; i < ne * 16 * N; i += NT) (&sCF[0][0])[i] = ((const T *)md.CF)[(size_t)e0 * 16 * N + i];
   __syncthreads();
   const T cth = pick<T>(md.clk->c, md.clk->cf), sth = pick<T>(md.clk->s, md.clk->sf);
-  tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, cth, sth);
-  __syncthreads();
   const T gm1 = pick<T>(md.gm1, md.gm1_f);
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
