@@ -190,6 +190,7 @@ struct sd_handle {
   cudaGraphExec_t step_exec = nullptr;
   double graph_dt = 0.0;
   double *h_pinned = nullptr;  // small pinned buffer for clock reads / writes
+  StageMerge sm{};             // per-stage clocks, mortar tables and merge work arrays
   std::string err;
 };
 
@@ -512,6 +513,23 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   md.bxy = bxy;
   md.clk = clk;
   if ((e = cudaMemsetAsync(clk, 0, sizeof(DevClock), h->stream))) return e;
+  // the stage records of a time step (see StageMerge)
+  DevClock *sclk;
+  if ((e = dalloc(h, &sclk, sizeof(DevClock) * kMaxStages))) return e;
+  if ((e = cudaMemsetAsync(sclk, 0, sizeof(DevClock) * kMaxStages, h->stream))) return e;
+  for (int k = 0; k < kMaxStages; ++k) {
+    StageMerge &sm = h->sm;
+    sm.clk[k] = sclk + k;
+    if ((e = dalloc(h, &sm.mLf[k], sizeof(int) * nb))) return e;
+    if ((e = dalloc(h, &sm.mRf[k], sizeof(int) * nb))) return e;
+    if ((e = dalloc(h, &sm.mgeo[k], sizeof(double) * 2 * nb))) return e;
+    if ((e = dalloc(h, &sm.Lstart[k], sizeof(int) * md.nL))) return e;
+    if ((e = dalloc(h, &sm.Lcount[k], sizeof(int) * md.nL))) return e;
+    if ((e = dalloc(h, &sm.Rstart[k], sizeof(int) * md.nR))) return e;
+    if ((e = dalloc(h, &sm.Rcount[k], sizeof(int) * md.nR))) return e;
+    if ((e = dalloc(h, &sm.work_i[k], sizeof(int) * (2 * nb + 1)))) return e;
+    if ((e = dalloc(h, &sm.work_d[k], sizeof(double) * (md.nL + nb + 1)))) return e;
+  }
   if ((e = cudaMemsetAsync(md.CF, 0, w * Ep * 16 * N, h->stream))) return e;
   // zero state
   const StatePtr A = h->eng->A(), Bs = h->eng->B();
@@ -523,13 +541,23 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   return cudaStreamSynchronize(h->stream);
 }
 
+// device flags: the OR of the primary clock's and the stage records' (the
+// kernels of a step raise them on their stage's record)
 int read_flags(sd_handle *h, int *flags, bool clear) {
-  cudaError_t e = cudaMemcpyAsync(h->h_pinned, &h->md.clk->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  int *hp = (int *)h->h_pinned;
+  DevClock *rec[1 + kMaxStages] = {h->md.clk};
+  for (int k = 0; k < kMaxStages; ++k) rec[1 + k] = h->sm.clk[k];
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 1 + kMaxStages && !e; ++k)
+    if (rec[k]) e = cudaMemcpyAsync(hp + k, &rec[k]->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (!e) e = cudaStreamSynchronize(h->stream);
   if (e) return cuda_fail(h, e, "reading device flags");
-  std::memcpy(flags, h->h_pinned, sizeof(int));
+  *flags = 0;
+  for (int k = 0; k < 1 + kMaxStages; ++k)
+    if (rec[k]) *flags |= hp[k];
   if (clear && *flags) {
-    e = cudaMemsetAsync(&h->md.clk->flags, 0, sizeof(int), h->stream);
+    for (int k = 0; k < 1 + kMaxStages && !e; ++k)
+      if (rec[k]) e = cudaMemsetAsync(&rec[k]->flags, 0, sizeof(int), h->stream);
     if (!e) e = cudaStreamSynchronize(h->stream);
     if (e) return cuda_fail(h, e, "clearing device flags");
   }
@@ -583,6 +611,30 @@ void rk54_times(double *c) {
 // queue the stages of one step; every stage is  out = in + a0 (base - in) +
 // w_in + bdt L(in)  (RkArgs), which is the Shu-Osher form rewritten around
 // the stage input (the weights of a Shu-Osher stage sum to one)
+// the MeshDev a stage's kernels see: its own clock and mortar table
+MeshDev stage_view(const sd_handle *h, int k) {
+  MeshDev m = h->md;
+  const StageMerge &sm = h->sm;
+  m.clk = sm.clk[k];
+  m.mLf = sm.mLf[k];
+  m.mRf = sm.mRf[k];
+  m.mgeo = sm.mgeo[k];
+  m.Lstart = sm.Lstart[k];
+  m.Lcount = sm.Lcount[k];
+  m.Rstart = sm.Rstart[k];
+  m.Rcount = sm.Rcount[k];
+  return m;
+}
+
+// one stage after the step's merge: common fluxes of the stage's state q,
+// then the volume kernel (divergence, Runge-Kutta combination, traces)
+void queue_stage(sd_handle *h, int k, StatePtr q, StatePtr base, StatePtr out, const RkArgs &rk) {
+  const MeshDev m = stage_view(h, k);
+  h->eng->faces(m, q, h->stream);
+  h->eng->mortars(m, h->stream);
+  h->eng->volume(m, q, base, out, nullptr, rk, MODE_RK, h->stream);
+}
+
 void queue_step(sd_handle *h, double dt) {
   MeshDev &md = h->md;
   Engine *g = h->eng;
@@ -595,12 +647,13 @@ void queue_step(sd_handle *h, double dt) {
     r1.bdt = dt;
     r2.has_base = 1, r2.a0 = 0.75, r2.bdt = 0.25 * dt;
     r3.has_base = 1, r3.a0 = 1.0 / 3.0, r3.bdt = 2.0 / 3.0 * dt;
-    g->couple(md, A, 0.0, dt, s);
-    g->volume(md, A, none, B, nullptr, r1, MODE_RK, s);
-    g->couple(md, B, 1.0, dt, s);
-    g->volume(md, B, A, B, nullptr, r2, MODE_RK, s);
-    g->couple(md, B, 0.5, dt, s);
-    g->volume(md, B, A, A, nullptr, r3, MODE_RK, s);
+    StageMerge &sm = h->sm;
+    sm.n = 3;
+    sm.c[0] = 0.0, sm.c[1] = 1.0, sm.c[2] = 0.5;
+    g->merge_stages(md, sm, dt, s);
+    queue_stage(h, 0, A, none, B, r1);
+    queue_stage(h, 1, B, A, B, r2);
+    queue_stage(h, 2, B, A, A, r3);
   } else {
     // u -> A, u1 -> B, u2 -> C, u3 -> B, u4 -> A (u is not needed after the
     // fourth stage), u+ -> A; W carries a53 (u3 - u4) + c53 dt L(u3)
@@ -615,16 +668,15 @@ void queue_step(sd_handle *h, double dt) {
     r4.has_base = 1, r4.a0 = Rk54::a40, r4.bdt = Rk54::c43 * dt, r4.g = Rk54::a53, r4.ddt = Rk54::c53 * dt;
     r4.w_out = W;
     r5.has_base = 1, r5.a0 = Rk54::a52, r5.bdt = Rk54::c54 * dt, r5.w_in = W;
-    g->couple(md, A, c[0], dt, s);
-    g->volume(md, A, none, B, nullptr, r1, MODE_RK, s);
-    g->couple(md, B, c[1], dt, s);
-    g->volume(md, B, A, Cs, nullptr, r2, MODE_RK, s);
-    g->couple(md, Cs, c[2], dt, s);
-    g->volume(md, Cs, A, B, nullptr, r3, MODE_RK, s);
-    g->couple(md, B, c[3], dt, s);
-    g->volume(md, B, A, A, nullptr, r4, MODE_RK, s);
-    g->couple(md, A, c[4], dt, s);
-    g->volume(md, A, Cs, A, nullptr, r5, MODE_RK, s);
+    StageMerge &sm = h->sm;
+    sm.n = 5;
+    for (int k = 0; k < 5; ++k) sm.c[k] = c[k];
+    g->merge_stages(md, sm, dt, s);
+    queue_stage(h, 0, A, none, B, r1);
+    queue_stage(h, 1, B, A, Cs, r2);
+    queue_stage(h, 2, Cs, A, B, r3);
+    queue_stage(h, 3, B, A, A, r4);
+    queue_stage(h, 4, A, Cs, A, r5);
   }
   g->advance(md, dt, s);
 }

@@ -10,10 +10,13 @@
 // FP32 rate); the rotation angle, the mortar geometry and the mortar
 // projection weights stay FP64 in both paths (Sec. 3.2).
 //
-// Per stage (stage time t_k):
-//   k_clock_merge   1 CTA: theta = omega t_k; merge of the rotated L node
-//                   angles with the R node angles -> mortars, (o, s) of each
-//                   mortar against its L and R face (Eq. xz), face ranges
+// Per step, once: k_clock_merge_stages, one CTA per stage (stage time t_k):
+//                   theta = omega t_k; merge of the rotated L node angles
+//                   with the R node angles -> mortars, (o, s) of each mortar
+//                   against its L and R face (Eq. xz), face ranges, into the
+//                   stage's own clock record and mortar table
+//                   (k_clock_merge: the same for one stage, e.g. a residual)
+// Per stage:
 //   k_faces         one launch for every face point: conforming and periodic
 //                   faces (Rusanov common flux), then boundary faces (wall,
 //                   slip, inlet, outlet, adiabatic: Rusanov through a ghost state)
@@ -518,7 +521,10 @@ __device__ __forceinline__ double wrap_pi(double a) {
 // on ties.  One CTA; the node angles are searched in shared memory (dynamic,
 // (nL + nR) doubles); work_i / work_d hold the merged positions and angles.
 // The offsets and scales of Eq. xz are formed per mortar in k_mortar_flux.
-static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_i, double *work_d) {
+// The step's start time t_n is read from *tsrc; the stage clock and the table
+// are written through md.
+static __device__ void clock_merge_body(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
+                                        const DevClock *tsrc) {
   extern __shared__ double s_ang[];  // [nL] rotated L angles, then [nR] R angles
   __shared__ double s_th2;
   __shared__ int s_k0;
@@ -526,7 +532,7 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_
   const double tp = 6.283185307179586476925286766559;
   if (threadIdx.x == 0) {
     DevClock *k = md.clk;
-    const double ts = k->t_n + c * dt;
+    const double ts = tsrc->t_n + c * dt;
     const double th = md.omega * ts;
     const double th2 = wrap_2pi(th);
     k->t_stage = ts;
@@ -614,6 +620,25 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_
     md.mgeo[2 * p] = a;
     md.mgeo[2 * p + 1] = b - a;
   }
+}
+
+static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_i, double *work_d) {
+  clock_merge_body(md, c, dt, work_i, work_d, md.clk);
+}
+
+// block b: the clock and mortar table of stage b of a step
+static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt) {
+  const int b = blockIdx.x;
+  MeshDev m = md;
+  m.clk = sm.clk[b];
+  m.mLf = sm.mLf[b];
+  m.mRf = sm.mRf[b];
+  m.Lstart = sm.Lstart[b];
+  m.Lcount = sm.Lcount[b];
+  m.Rstart = sm.Rstart[b];
+  m.Rcount = sm.Rcount[b];
+  m.mgeo = sm.mgeo[b];
+  clock_merge_body(m, sm.c[b], dt, sm.work_i[b], sm.work_d[b], md.clk);
 }
 
 // t = 0 geometry of every conforming / periodic face point (one thread per point)
@@ -1628,6 +1653,9 @@ struct EngineImpl : Engine {
     if (merge_smem > 48 * 1024) {
       if ((err = cudaFuncSetAttribute(k_clock_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, merge_smem)))
         return err;
+      if ((err = cudaFuncSetAttribute(k_clock_merge_stages, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      merge_smem)))
+        return err;
     }
     {
       // persistent volume kernel: as many CTAs as fit on the GPU at once
@@ -1684,6 +1712,10 @@ struct EngineImpl : Engine {
   void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                         cudaStream_t s) override {
     k_clock_merge<<<1, 1024, merge_smem, s>>>(md, c, dt, work_i, work_d);
+  }
+
+  void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, cudaStream_t s) override {
+    k_clock_merge_stages<<<sm.n, 1024, merge_smem, s>>>(md, sm, dt);
   }
 
   template <int MMODE, int GMODE>

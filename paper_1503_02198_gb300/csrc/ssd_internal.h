@@ -100,6 +100,22 @@ struct MeshDev {
 
 enum { MODE_RESIDUAL = 0, MODE_RK = 1 };
 
+// Stage clocks and mortar tables of every stage of one time step, filled by
+// one merge launch at the start of the step (one block per stage; the stage
+// times t_n + c_k dt are known there).  Each stage's kernels then see a
+// MeshDev whose clock and mortar-table pointers are that stage's.
+constexpr int kMaxStages = 5;
+struct StageMerge {
+  int n;
+  double c[kMaxStages];
+  DevClock *clk[kMaxStages];
+  int *mLf[kMaxStages], *mRf[kMaxStages];
+  int *Lstart[kMaxStages], *Lcount[kMaxStages], *Rstart[kMaxStages], *Rcount[kMaxStages];
+  double *mgeo[kMaxStages];
+  int *work_i[kMaxStages];
+  double *work_d[kMaxStages];
+};
+
 // One Runge-Kutta stage in increment form: with R = L(in),
 //   inc = a0 (base - in) + w_in + bdt R,   out = in + inc,
 //   w_out = -g inc + ddt R   (an O(dt) increment kept for a later stage).
@@ -141,6 +157,9 @@ struct Engine {
   // doubles: nL + (nL + nR) + 1)
   virtual void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                                 cudaStream_t s) = 0;
+  // the clocks and mortar tables of all stages of a step in one launch (the
+  // step's start time t_n is read from md.clk)
+  virtual void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, cudaStream_t s) = 0;
   // q: the stage's state (the viscous chain needs its gradients)
   virtual void faces(const MeshDev &md, StatePtr q, cudaStream_t s) = 0;
   virtual void mortars(const MeshDev &md, cudaStream_t s) = 0;
