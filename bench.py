@@ -386,7 +386,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32s"])
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=50)

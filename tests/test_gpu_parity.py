@@ -251,3 +251,43 @@ def test_steps_rk54(ssd, oracle_mod, precision, N):
     q_ref, t_ref = o.step(Q, 0.05, dt, 4, rk_stages=5)
     assert abs(s.sd_get_time() - t_ref) < 1e-15
     _check(s.sd_get_state(), q_ref, TOL64 if precision == 0 else TOL32_STATE)
+
+
+@pytest.mark.parametrize("omega,t", [(0.9, 100.0), (-0.7, 123.4), (0.0, 3.0)])
+def test_residual_fp64_many_turns_clockwise_and_still(ssd, oracle_mod, omega, t):
+    # rotation angles of many turns (theta = 90 rad), clockwise rotation
+    # (theta = -86 rad) and a sliding interface that does not move
+    m = small_rotor(shift_R=0.05)
+    prm = FlowParams(omega=omega)
+    s, o = _pair(ssd, oracle_mod, m, 4, prm)
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=31, amp=0.2, scale=3.0))
+    s.sd_set_state(Q)
+    s.sd_set_time(t)
+    _check(s.sd_residual(), o.residual(Q, t), TOL64)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_steps_clockwise_from_late_time(ssd, oracle_mod, precision):
+    m = small_rotor(shift_L=0.03)
+    prm = FlowParams(omega=-0.8)
+    s, o = _pair(ssd, oracle_mod, m, 5, prm, precision=precision)
+    Q = o.state_from(lambda x, y: fields.isentropic_vortex(x, y, x0=-1.0, y0=0.5))
+    t0, dt, n = 50.0, 0.004, 10
+    s.sd_set_state(Q)
+    s.sd_set_time(t0)
+    s.sd_step(dt, n)
+    s.sd_sync()
+    Qo, t = o.step(Q, t0, dt, n)
+    _check(s.sd_get_state(), Qo, TOL32_STATE if precision else TOL64)
+    assert abs(s.sd_get_time() - t) < 1e-12
+
+
+def test_zero_steps_change_nothing(ssd, oracle_mod):
+    m = small_rotor()
+    s, o = _pair(ssd, oracle_mod, m, 3, FlowParams(omega=0.5))
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=4, amp=0.1, scale=3.0))
+    s.sd_set_state(Q)
+    s.sd_set_time(1.5)
+    s.sd_step(0.01, 0)
+    s.sd_sync()
+    assert np.array_equal(s.sd_get_state(), Q) and s.sd_get_time() == 1.5
