@@ -1303,34 +1303,47 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
           acc2[0][k] = make_float2(0.f, 0.f);
           acc2[1][k] = make_float2(0.f, 0.f);
         }
+        // Q at every interior FP of the line at once (the SP index outermost,
+        // so the 2 (N - 1) sums are independent chains), then the fluxes, then
+        // the divergence; each sum keeps its order
+        float2 s01[N + 1], s23[N + 1];
 #pragma unroll
-        for (int i = 0; i <= N; ++i) {
-          float2 f01, f23;
-          if (i == 0 || i == N) {
-            const int face = d == 0 ? (i == 0 ? 3 : 1) : (i == 0 ? 0 : 2);
-            f01 = make_float2(sCF[le][(face * 4 + 0) * N + mline], sCF[le][(face * 4 + 1) * N + mline]);
-            f23 = make_float2(sCF[le][(face * 4 + 2) * N + mline], sCF[le][(face * 4 + 3) * N + mline]);
-          } else {
-            float2 s01 = make_float2(0.f, 0.f), s23 = make_float2(0.f, 0.f);
+        for (int i = 1; i < N; ++i) {
+          s01[i] = make_float2(0.f, 0.f);
+          s23[i] = make_float2(0.f, 0.f);
+        }
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
-              const float2 h = B.Hf2[i * N + k];
-              s01 = __ffma2_rn(q2[0][k], h, s01);
-              s23 = __ffma2_rn(q2[1][k], h, s23);
-            }
-            const float qf[4] = {s01.x, s01.y, s23.x, s23.y};
-            float f[4];
-            point_flux(qf, (float)mvx[i], (float)mvy[i], (float)mvg[i], (float)gm1, f);
-            f01 = make_float2(f[0], f[1]);
-            f23 = make_float2(f[2], f[3]);
+        for (int k = 0; k < N; ++k)
+#pragma unroll
+          for (int i = 1; i < N; ++i) {
+            const float2 h = B.Hf2[i * N + k];
+            s01[i] = __ffma2_rn(q2[0][k], h, s01[i]);
+            s23[i] = __ffma2_rn(q2[1][k], h, s23[i]);
           }
+        float2 f01[N + 1], f23[N + 1];
+        {
+          const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+          f01[0] = make_float2(sCF[le][(fa * 4 + 0) * N + mline], sCF[le][(fa * 4 + 1) * N + mline]);
+          f23[0] = make_float2(sCF[le][(fa * 4 + 2) * N + mline], sCF[le][(fa * 4 + 3) * N + mline]);
+          f01[N] = make_float2(sCF[le][(fb * 4 + 0) * N + mline], sCF[le][(fb * 4 + 1) * N + mline]);
+          f23[N] = make_float2(sCF[le][(fb * 4 + 2) * N + mline], sCF[le][(fb * 4 + 3) * N + mline]);
+        }
+#pragma unroll
+        for (int i = 1; i < N; ++i) {
+          const float qf[4] = {s01[i].x, s01[i].y, s23[i].x, s23[i].y};
+          float f[4];
+          point_flux(qf, (float)mvx[i], (float)mvy[i], (float)mvg[i], (float)gm1, f);
+          f01[i] = make_float2(f[0], f[1]);
+          f23[i] = make_float2(f[2], f[3]);
+        }
+#pragma unroll
+        for (int i = 0; i <= N; ++i)
 #pragma unroll
           for (int k = 0; k < N; ++k) {
             const float2 w = B.Dm2[k * (N + 1) + i];
-            acc2[0][k] = __ffma2_rn(w, f01, acc2[0][k]);
-            acc2[1][k] = __ffma2_rn(w, f23, acc2[1][k]);
+            acc2[0][k] = __ffma2_rn(w, f01[i], acc2[0][k]);
+            acc2[1][k] = __ffma2_rn(w, f23[i], acc2[1][k]);
           }
-        }
         if (d == 0) {
 #pragma unroll
           for (int k = 0; k < N; ++k) {
