@@ -100,8 +100,8 @@ class ClockSampler:
 # profiles/k_volume_fp32_rotor_n6.md; valid only for the kernel source it was
 # taken on: SHA-256 of the engine text that k_volume is built from (the
 # ElemGeo metrics and VolCfg through the end of k_volume); otherwise null.
-PROFILED_TRAFFIC = {"bytes": (389.06e6 + 328.68e6 + 673.47e6 + 330.91e6 + 673.47e6 + 329.55e6) / 3,
-                    "kernel_sha256": "40f2b8abc1ae603b69139f7534110a2c937e428ce36cf9d0d4e43a1a0714dcd4"}
+PROFILED_TRAFFIC = {"bytes": (389.07e6 + 328.85e6 + 673.48e6 + 331.02e6 + 673.47e6 + 329.73e6) / 3,
+                    "kernel_sha256": "ae1f4e35b72381ac79256414963982e9a4c2a4fc8690384eead960d67f90039a"}
 
 
 def volume_kernel_source():
