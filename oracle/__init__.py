@@ -41,7 +41,8 @@ def lib():
         L.or_create.restype = ctypes.c_void_p
         L.or_create.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _ip, _ip, ctypes.c_int, _ip, ctypes.c_int,
                                 _ip, ctypes.c_int, _ip, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double,
-                                ctypes.c_double, ctypes.c_int, _dp, ctypes.c_char_p, ctypes.c_int]
+                                ctypes.c_double, ctypes.c_int, _dp, ctypes.c_int, _dp, _ip, _ip, _ip,
+                                ctypes.c_char_p, ctypes.c_int]
         L.or_destroy.argtypes = [ctypes.c_void_p]
         L.or_residual.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp]
         L.or_residual_ex.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, _dp, _dp]
@@ -58,6 +59,9 @@ def lib():
         L.or_face_info.argtypes = [ctypes.c_void_p, _ip, _ip, _ip]
         L.or_mortar_list.restype = ctypes.c_int
         L.or_mortar_list.argtypes = [ctypes.c_void_p, ctypes.c_double, _ip, _ip, _dp, _dp, _dp, _dp]
+        L.or_mortar_list_zone.restype = ctypes.c_int
+        L.or_mortar_list_zone.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _ip, _ip, _dp, _dp,
+                                          _dp, _dp]
         _lib = L
     return _lib
 
@@ -134,11 +138,22 @@ class Oracle:
         Lf = arr(mesh["ifaces_L"], np.int32)
         Rf = arr(mesh["ifaces_R"], np.int32)
         prm = arr(params_array(params), np.float64)
+        # further rotating zones 2, 3, ...: centre, radius, angular velocity, interface lists
+        extra = mesh.get("zones", [])
+        xz = arr(np.array([[z["center"][0], z["center"][1], z["r_interface"], z["omega"]] for z in extra],
+                          dtype=np.float64).reshape(-1, 4), np.float64)
+        xcnt = arr(np.array([[len(z["ifaces_L"]), len(z["ifaces_R"])] for z in extra],
+                            dtype=np.int32).reshape(-1, 2), np.int32)
+        xfaces = arr(np.concatenate([np.asarray(z[k], dtype=np.int32).reshape(-1, 2) for z in extra
+                                     for k in ("ifaces_L", "ifaces_R")] + [np.zeros((1, 2), np.int32)]),
+                     np.int32)
+        azone = arr(mesh["elem_arc_zone"], np.int32) if "elem_arc_zone" in mesh else None
         err = ctypes.create_string_buffer(256)
         self._h = L.or_create(len(xy), _d(xy), self.E, _i(en), _i(zone), _i(arc),
                               _i(enode) if enode is not None else None, len(bf), _i(bf), len(pf),
                               _i(pf), len(Lf), _i(Lf), len(Rf), _i(Rf), float(mesh["center"][0]),
-                              float(mesh["center"][1]), float(mesh["r_interface"]), N, _d(prm), err, 256)
+                              float(mesh["center"][1]), float(mesh["r_interface"]), N, _d(prm), len(extra),
+                              _d(xz), _i(xcnt), _i(xfaces), _i(azone) if azone is not None else None, err, 256)
         if not self._h:
             raise ValueError("oracle mesh set-up failed: " + err.value.decode())
 
@@ -189,11 +204,14 @@ class Oracle:
         lib().or_face_info(self._h, _i(kind), _i(nbr), _i(rev))
         return kind, nbr, rev
 
-    def mortars(self, t: float):
-        n = len(self.mesh["ifaces_L"]) + len(self.mesh["ifaces_R"])
-        lf, rf = np.zeros(n, np.int32), np.zeros(n, np.int32)
-        oL, sL, oR, sR = (np.zeros(n) for _ in range(4))
-        k = lib().or_mortar_list(self._h, t, _i(lf), _i(rf), _d(oL), _d(sL), _d(oR), _d(sR))
+    def mortars(self, t: float, zone: int = 1):
+        """Mortars of rotating zone ``zone``'s interface at time t (lf / rf index
+        that interface's sorted L / R lists)."""
+        z = self.mesh if zone == 1 else self.mesh["zones"][zone - 2]
+        n = len(z["ifaces_L"]) + len(z["ifaces_R"])
+        lf, rf = np.zeros(max(n, 1), np.int32), np.zeros(max(n, 1), np.int32)
+        oL, sL, oR, sR = (np.zeros(max(n, 1)) for _ in range(4))
+        k = lib().or_mortar_list_zone(self._h, zone, t, _i(lf), _i(rf), _d(oL), _d(sL), _d(oR), _d(sR))
         return {"lf": lf[:k], "rf": rf[:k], "oL": oL[:k], "sL": sL[:k], "oR": oR[:k], "sR": sR[:k]}
 
     def state_from(self, field_fn, t: float = 0.0):

@@ -49,7 +49,11 @@
  *   - curved cells with 12 nodes (Sec. 3.1): an edge may be the cubic
  *     through its two corners and two edge nodes at face parameter 1/3 and
  *     2/3; the transfinite map with such edges spans exactly the 12-node
- *     serendipity cubic element.
+ *     serendipity cubic element;
+ *   - several rotating zones (the paper has one per case): zone z >= 1 turns
+ *     rigidly about its own centre at its own angular velocity and meets the
+ *     stationary zone 0 across its own circular sliding interface; every
+ *     interface is coupled by the procedure of Sec. 3.2 on its own.
  */
 #include <math.h>
 #include <stdio.h>
@@ -58,6 +62,7 @@
 
 #define OR_MAXN 12
 #define OR_PI 3.14159265358979323846
+#define OR_MAXZ 4 /* rotating zones */
 
 /* ------------------------------------------------------------------------ */
 /* parameters and mesh                                                       */
@@ -76,6 +81,17 @@ enum { EDGE_STRAIGHT = 0, EDGE_ARC = 1, EDGE_CUBIC = 2 };
 
 enum { FK_NONE = -1, FK_CONF = 0, FK_PERIODIC = 1, FK_BOUNDARY = 2, FK_IFACE_L = 3, FK_IFACE_R = 4 };
 
+/* A rotating zone z >= 1: rigid rotation theta = omega t about its centre
+ * (Sec. 2.2), and its circular sliding interface of radius rI with the
+ * stationary zone 0 (Sec. 3.2), the rotating cells being the L side. */
+typedef struct {
+  double cx, cy, rI, omega;
+  int nL, nR;                /* interface faces, sorted counter-clockwise */
+  int *Lef, *Ref;            /* element-face index */
+  double *La, *Lw, *Ra, *Rw; /* CCW start angle at t = 0 (in [0, 2pi)) and angular width */
+  int *Lrev, *Rrev;          /* 1 if the face parameter runs clockwise */
+} or_iface;
+
 typedef struct {
   int N;
   double Xs[OR_MAXN];     /* solution points X_s, s = 1..N (stored 0-based) */
@@ -85,14 +101,11 @@ typedef struct {
   double *xy;
   int *en, *zone, *arc;
   int *enode; /* [E][4][2]: edge nodes at face parameter 1/3, 2/3 of cubic edges, or NULL */
-  double cx, cy, rI;
+  int *azone; /* [E]: the zone whose centre the cell's arc edges are drawn about */
   /* per element face e*4+f */
   int *fkind, *fnbr, *frev, *ftag;
-  /* interface faces, sorted counter-clockwise */
-  int nL, nR;
-  int *Lef, *Ref;           /* element-face index */
-  double *La, *Lw, *Ra, *Rw; /* CCW start angle at t = 0 (in [0, 2pi)) and angular width */
-  int *Lrev, *Rrev;         /* 1 if the face parameter runs clockwise */
+  int nz;               /* rotating zones 1..nz */
+  or_iface zi[OR_MAXZ]; /* zi[z - 1]: zone z */
   or_params prm;
   char err[256];
 } or_mesh;
@@ -173,12 +186,12 @@ static const int FACE_A[4] = {0, 1, 3, 0}; /* start corner of face f's parameter
 static const int FACE_B[4] = {1, 2, 2, 3}; /* end corner */
 
 /* Edge curve from P to Q at parameter u: offset of the point from P, and the
- * derivative.  An arc is written with the chord form
+ * derivative.  An arc is about the centre (cx, cy); it is written with the chord form
  * e(phi0 + d) - e(phi0) = 2 sin(d/2) (-sin(phi0 + d/2), cos(phi0 + d/2)),
  * so the offset keeps full relative precision for short arcs far from the
  * centre. */
-static void edge_curve(const or_mesh *m, double px, double py, double qx, double qy, int arc, const int *mid,
-                       double u, double *ox, double *oy, double *dx, double *dy) {
+static void edge_curve(const or_mesh *m, double cx, double cy, double px, double py, double qx, double qy, int arc,
+                       const int *mid, double u, double *ox, double *oy, double *dx, double *dy) {
   if (arc == EDGE_CUBIC) {
     /* cubic Lagrange interpolation through P, M1, M2, Q at u = 0, 1/3, 2/3, 1,
      * written as offsets from P */
@@ -202,7 +215,7 @@ static void edge_curve(const or_mesh *m, double px, double py, double qx, double
     *dy = qy - py;
     return;
   }
-  double ax = px - m->cx, ay = py - m->cy, bx = qx - m->cx, by = qy - m->cy;
+  double ax = px - cx, ay = py - cy, bx = qx - cx, by = qy - cy;
   double r = sqrt(ax * ax + ay * ay);
   double phi0 = atan2(ay, ax);
   double dphi = atan2(ax * by - ay * bx, ax * bx + ay * by);
@@ -233,11 +246,12 @@ static void map_t0(const or_mesh *m, int e, double xi, double eta, double *g) {
   }
   const int *a = m->arc + 4 * e;
   const int *md = m->enode ? m->enode + 8 * e : NULL;
+  const double cx = m->zi[m->azone[e] - 1].cx, cy = m->zi[m->azone[e] - 1].cy; /* centre of arc edges */
   double Bx, By, dBx, dBy, Tx, Ty, dTx, dTy, Lx, Ly, dLx, dLy, Rx, Ry, dRx, dRy;
-  edge_curve(m, X[0], Y[0], X[1], Y[1], a[0], md ? md + 0 : NULL, xi, &Bx, &By, &dBx, &dBy);  /* f0, eta = 0 */
-  edge_curve(m, X[1], Y[1], X[2], Y[2], a[1], md ? md + 2 : NULL, eta, &Rx, &Ry, &dRx, &dRy); /* f1, xi = 1 */
-  edge_curve(m, X[3], Y[3], X[2], Y[2], a[2], md ? md + 4 : NULL, xi, &Tx, &Ty, &dTx, &dTy);  /* f2, eta = 1 */
-  edge_curve(m, X[0], Y[0], X[3], Y[3], a[3], md ? md + 6 : NULL, eta, &Lx, &Ly, &dLx, &dLy); /* f3, xi = 0 */
+  edge_curve(m, cx, cy, X[0], Y[0], X[1], Y[1], a[0], md ? md + 0 : NULL, xi, &Bx, &By, &dBx, &dBy);  /* f0 */
+  edge_curve(m, cx, cy, X[1], Y[1], X[2], Y[2], a[1], md ? md + 2 : NULL, eta, &Rx, &Ry, &dRx, &dRy); /* f1 */
+  edge_curve(m, cx, cy, X[3], Y[3], X[2], Y[2], a[2], md ? md + 4 : NULL, xi, &Tx, &Ty, &dTx, &dTy);  /* f2 */
+  edge_curve(m, cx, cy, X[0], Y[0], X[3], Y[3], a[3], md ? md + 6 : NULL, eta, &Lx, &Ly, &dLx, &dLy); /* f3 */
   /* edge points relative to corner 0 */
   Rx += U[1]; Ry += V[1];
   Tx += U[3]; Ty += V[3];
@@ -252,15 +266,17 @@ static void map_t0(const or_mesh *m, int e, double xi, double eta, double *g) {
   g[0] = X[0] + x; g[1] = Y[0] + y; g[2] = x_xi; g[3] = y_xi; g[4] = x_eta; g[5] = y_eta;
 }
 
-/* Map at time t: cells of the rotating zone are rotated rigidly about the
- * centre by theta = omega t (Sec. 2.2: coordinates updated analytically). */
+/* Map at time t: cells of rotating zone z are rotated rigidly about the
+ * zone's centre by theta = omega_z t (Sec. 2.2: coordinates updated
+ * analytically). */
 static void map_at(const or_mesh *m, int e, double xi, double eta, double t, double *g) {
   map_t0(m, e, xi, eta, g);
-  if (m->zone[e] == 1) {
-    double th = m->prm.omega * t, c = cos(th), s = sin(th);
-    double dx = g[0] - m->cx, dy = g[1] - m->cy;
-    g[0] = m->cx + c * dx - s * dy;
-    g[1] = m->cy + s * dx + c * dy;
+  if (m->zone[e] >= 1) {
+    const or_iface *Z = &m->zi[m->zone[e] - 1];
+    double th = Z->omega * t, c = cos(th), s = sin(th);
+    double dx = g[0] - Z->cx, dy = g[1] - Z->cy;
+    g[0] = Z->cx + c * dx - s * dy;
+    g[1] = Z->cy + s * dx + c * dy;
     for (int k = 2; k < 6; k += 2) {
       double vx = g[k], vy = g[k + 1];
       g[k] = c * vx - s * vy;
@@ -269,11 +285,12 @@ static void map_at(const or_mesh *m, int e, double xi, double eta, double t, dou
   }
 }
 
-/* grid velocity (u_g, v_g) = omega x r on the rotating zone, 0 elsewhere */
+/* grid velocity (u_g, v_g) = omega_z x (r - centre_z) on rotating zone z, 0 elsewhere */
 static void grid_velocity(const or_mesh *m, int e, double x, double y, double *ug, double *vg) {
-  if (m->zone[e] == 1) {
-    *ug = -m->prm.omega * (y - m->cy);
-    *vg = m->prm.omega * (x - m->cx);
+  if (m->zone[e] >= 1) {
+    const or_iface *Z = &m->zi[m->zone[e] - 1];
+    *ug = -Z->omega * (y - Z->cy);
+    *vg = Z->omega * (x - Z->cx);
   } else {
     *ug = 0.0;
     *vg = 0.0;
@@ -469,8 +486,8 @@ static double wrap_pi(double a) {
   return r;
 }
 
-static int setup_interface_side(or_mesh *m, int n, const int *faces, int kind, int **ef_out, double **a_out,
-                                double **w_out, int **rev_out) {
+static int setup_interface_side(or_mesh *m, const or_iface *I, int n, const int *faces, int kind, int **ef_out,
+                                double **a_out, double **w_out, int **rev_out) {
   int *ef = malloc(sizeof(int) * (n > 0 ? n : 1));
   double *a = malloc(sizeof(double) * (n > 0 ? n : 1)), *w = malloc(sizeof(double) * (n > 0 ? n : 1));
   int *rv = malloc(sizeof(int) * (n > 0 ? n : 1));
@@ -478,8 +495,8 @@ static int setup_interface_side(or_mesh *m, int n, const int *faces, int kind, i
     int e = faces[2 * k], f = faces[2 * k + 1], na, nb;
     ef[k] = 4 * e + f;
     face_nodes(m, ef[k], &na, &nb);
-    double pa = atan2(m->xy[2 * na + 1] - m->cy, m->xy[2 * na] - m->cx);
-    double pb = atan2(m->xy[2 * nb + 1] - m->cy, m->xy[2 * nb] - m->cx);
+    double pa = atan2(m->xy[2 * na + 1] - I->cy, m->xy[2 * na] - I->cx);
+    double pb = atan2(m->xy[2 * nb + 1] - I->cy, m->xy[2 * nb] - I->cx);
     double d = wrap_pi(pb - pa);
     if (d > 0) {
       a[k] = wrap2pi(pa);
@@ -492,6 +509,7 @@ static int setup_interface_side(or_mesh *m, int n, const int *faces, int kind, i
     }
     if (m->fkind[ef[k]] != FK_NONE) {
       snprintf(m->err, sizeof m->err, "interface face %d/%d already classified", e, f);
+      *ef_out = ef; *a_out = a; *w_out = w; *rev_out = rv;
       return -1;
     }
     m->fkind[ef[k]] = kind;
@@ -506,6 +524,7 @@ static int setup_interface_side(or_mesh *m, int n, const int *faces, int kind, i
     }
   double total = 0.0;
   for (int k = 0; k < n; ++k) total += w[k];
+  *ef_out = ef; *a_out = a; *w_out = w; *rev_out = rv;
   if (n > 0 && fabs(total - 2.0 * OR_PI) > 1e-9) {
     snprintf(m->err, sizeof m->err, "interface side does not close (%.12f)", total);
     return -1;
@@ -516,10 +535,16 @@ static int setup_interface_side(or_mesh *m, int n, const int *faces, int kind, i
 
 void or_destroy(or_mesh *m);
 
+/* Zone 1 is given by (cx, cy, rI), prm_in's omega and the interface lists
+ * Lf / Rf; zones 2 .. nxz + 1 by xz[k] = (cx, cy, rI, omega), xcnt[k] =
+ * (nL, nR) and their lists, concatenated in xfaces (L then R, zone by zone).
+ * azone (or NULL: the cell's own zone, zone 1 for stationary cells) names the
+ * zone whose centre a cell's arc edges are drawn about. */
 or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *zone, const int *arc,
                    const int *enode, int nb,
                    const int *bfaces, int np, const int *pfaces, int nL, const int *Lf, int nR, const int *Rf,
-                   double cx, double cy, double rI, int N, const double *prm_in, char *err, int errlen) {
+                   double cx, double cy, double rI, int N, const double *prm_in, int nxz, const double *xz,
+                   const int *xcnt, const int *xfaces, const int *azone, char *err, int errlen) {
   or_mesh *m = calloc(1, sizeof(or_mesh));
   m->N = N;
   make_points(N, m->Xs, m->Xf);
@@ -538,9 +563,6 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
     m->enode = malloc(sizeof(int) * 8 * ne);
     memcpy(m->enode, enode, sizeof(int) * 8 * ne);
   }
-  m->cx = cx;
-  m->cy = cy;
-  m->rI = rI;
   m->prm.gamma = prm_in[0];
   m->prm.Rgas = prm_in[1];
   m->prm.mu = prm_in[2];
@@ -552,13 +574,41 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
   m->prm.u_inf = prm_in[8];
   m->prm.v_inf = prm_in[9];
   m->prm.p_inf = prm_in[10];
+  int rc = 0;
+  if (nxz < 0 || nxz + 1 > OR_MAXZ) {
+    snprintf(m->err, sizeof m->err, "at most %d rotating zones", OR_MAXZ);
+    rc = -1;
+    nxz = 0;
+  }
+  m->nz = 1 + nxz;
+  m->zi[0].cx = cx;
+  m->zi[0].cy = cy;
+  m->zi[0].rI = rI;
+  m->zi[0].omega = m->prm.omega;
+  for (int k = 0; k < nxz; ++k) {
+    m->zi[1 + k].cx = xz[4 * k];
+    m->zi[1 + k].cy = xz[4 * k + 1];
+    m->zi[1 + k].rI = xz[4 * k + 2];
+    m->zi[1 + k].omega = xz[4 * k + 3];
+  }
+  m->azone = malloc(sizeof(int) * (ne > 0 ? ne : 1));
+  for (int e = 0; e < ne; ++e) {
+    m->azone[e] = azone ? azone[e] : (zone[e] >= 1 ? zone[e] : 1);
+    if (zone[e] < 0 || zone[e] > m->nz) {
+      snprintf(m->err, sizeof m->err, "zone of element %d out of range", e);
+      rc = -1;
+    } else if (m->azone[e] < 1 || m->azone[e] > m->nz || (zone[e] >= 1 && m->azone[e] != zone[e])) {
+      snprintf(m->err, sizeof m->err, "arc zone of element %d invalid", e);
+      rc = -1;
+    }
+  }
+  if (rc) m->nz = 0; /* nothing of the interfaces is allocated */
   int nf = 4 * ne;
   m->fkind = malloc(sizeof(int) * nf);
   m->fnbr = malloc(sizeof(int) * nf);
   m->frev = malloc(sizeof(int) * nf);
   m->ftag = malloc(sizeof(int) * nf);
   for (int k = 0; k < nf; ++k) { m->fkind[k] = FK_NONE; m->fnbr[k] = -1; m->frev[k] = 0; m->ftag[k] = 0; }
-  int rc = 0;
   /* edge kinds: a cubic edge needs its two edge nodes */
   for (int k = 0; k < 4 * ne && !rc; ++k) {
     if (arc[k] < EDGE_STRAIGHT || arc[k] > EDGE_CUBIC) {
@@ -599,10 +649,34 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
     m->fnbr[efB] = efA;
     m->frev[efA] = m->frev[efB] = rev;
   }
-  if (!rc) rc = setup_interface_side(m, nL, Lf, FK_IFACE_L, &m->Lef, &m->La, &m->Lw, &m->Lrev);
-  if (!rc) rc = setup_interface_side(m, nR, Rf, FK_IFACE_R, &m->Ref, &m->Ra, &m->Rw, &m->Rrev);
-  m->nL = nL;
-  m->nR = nR;
+  /* interfaces: the L side of zone z's interface lies in zone z, the R side in zone 0 */
+  const int *xf = xfaces;
+  for (int z = 1; z <= m->nz; ++z) {
+    or_iface *I = &m->zi[z - 1];
+    const int *fl = z == 1 ? Lf : xf, *fr;
+    I->nL = z == 1 ? nL : xcnt[2 * (z - 2)];
+    I->nR = z == 1 ? nR : xcnt[2 * (z - 2) + 1];
+    if (z > 1) xf += 2 * I->nL;
+    fr = z == 1 ? Rf : xf;
+    if (z > 1) xf += 2 * I->nR;
+    if (rc) continue;
+    rc = setup_interface_side(m, I, I->nL, fl, FK_IFACE_L, &I->Lef, &I->La, &I->Lw, &I->Lrev);
+    if (!rc) rc = setup_interface_side(m, I, I->nR, fr, FK_IFACE_R, &I->Ref, &I->Ra, &I->Rw, &I->Rrev);
+    for (int k = 0; k < I->nL && !rc; ++k)
+      if (zone[I->Lef[k] / 4] != z) {
+        snprintf(m->err, sizeof m->err, "rotating-side face of interface %d not in zone %d", z, z);
+        rc = -1;
+      }
+    for (int k = 0; k < I->nR && !rc; ++k)
+      if (zone[I->Ref[k] / 4] != 0) {
+        snprintf(m->err, sizeof m->err, "stationary-side face of interface %d not in zone 0", z);
+        rc = -1;
+      }
+    if (!rc && (I->nL == 0) != (I->nR == 0)) {
+      snprintf(m->err, sizeof m->err, "interface %d has faces on one side only", z);
+      rc = -1;
+    }
+  }
   /* conforming faces by shared node pairs */
   if (!rc) {
     edge_key *keys = malloc(sizeof(edge_key) * nf);
@@ -674,10 +748,13 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
 
 void or_destroy(or_mesh *m) {
   if (!m) return;
-  free(m->xy); free(m->en); free(m->zone); free(m->arc); free(m->enode);
+  free(m->xy); free(m->en); free(m->zone); free(m->arc); free(m->enode); free(m->azone);
   free(m->fkind); free(m->fnbr); free(m->frev); free(m->ftag);
-  free(m->Lef); free(m->La); free(m->Lw); free(m->Lrev);
-  free(m->Ref); free(m->Ra); free(m->Rw); free(m->Rrev);
+  for (int z = 0; z < m->nz; ++z) {
+    or_iface *I = &m->zi[z];
+    free(I->Lef); free(I->La); free(I->Lw); free(I->Lrev);
+    free(I->Ref); free(I->Ra); free(I->Rw); free(I->Rrev);
+  }
   free(m);
 }
 
@@ -779,22 +856,23 @@ typedef struct {
   double *oL, *sL, *oR, *sR, *m0, *dm;
 } or_mortars;
 
-/* Sec. 3.2: mortars at stage time t.  The rotating (L) side is turned by
- * theta = omega t; the mortars are the intervals between consecutive node
- * angles of both sides, in counter-clockwise order. */
-static void build_mortars(const or_mesh *m, double t, or_mortars *mo) {
-  int nL = m->nL, nR = m->nR, nb = nL + nR;
-  double th = m->prm.omega * t;
-  double *ang = malloc(sizeof(double) * nb);
-  for (int k = 0; k < nL; ++k) ang[k] = wrap2pi(m->La[k] + th);
-  for (int k = 0; k < nR; ++k) ang[nL + k] = m->Ra[k];
+/* Sec. 3.2: mortars of interface I at stage time t.  Its rotating (L) side
+ * is turned by theta = omega t; the mortars are the intervals between
+ * consecutive node angles of both sides, in counter-clockwise order. */
+static void build_mortars(const or_iface *I, double t, or_mortars *mo) {
+  int nL = I->nL, nR = I->nR, nb = nL + nR;
+  double th = I->omega * t;
+  double *ang = malloc(sizeof(double) * (nb > 0 ? nb : 1));
+  for (int k = 0; k < nL; ++k) ang[k] = wrap2pi(I->La[k] + th);
+  for (int k = 0; k < nR; ++k) ang[nL + k] = I->Ra[k];
   for (int i = 1; i < nb; ++i)
     for (int j = i; j > 0 && ang[j] < ang[j - 1]; --j) { double tt = ang[j]; ang[j] = ang[j - 1]; ang[j - 1] = tt; }
   mo->nm = 0;
-  mo->lf = malloc(sizeof(int) * nb); mo->rf = malloc(sizeof(int) * nb);
-  mo->oL = malloc(sizeof(double) * nb); mo->sL = malloc(sizeof(double) * nb);
-  mo->oR = malloc(sizeof(double) * nb); mo->sR = malloc(sizeof(double) * nb);
-  mo->m0 = malloc(sizeof(double) * nb); mo->dm = malloc(sizeof(double) * nb);
+  int na = nb > 0 ? nb : 1;
+  mo->lf = malloc(sizeof(int) * na); mo->rf = malloc(sizeof(int) * na);
+  mo->oL = malloc(sizeof(double) * na); mo->sL = malloc(sizeof(double) * na);
+  mo->oR = malloc(sizeof(double) * na); mo->sR = malloc(sizeof(double) * na);
+  mo->m0 = malloc(sizeof(double) * na); mo->dm = malloc(sizeof(double) * na);
   for (int k = 0; k < nb; ++k) {
     double a = ang[k], b = (k + 1 < nb) ? ang[k + 1] : ang[0] + 2.0 * OR_PI;
     double d = b - a;
@@ -803,22 +881,22 @@ static void build_mortars(const or_mesh *m, double t, or_mortars *mo) {
     int fl = -1, fr = -1;
     double oL = 0, oR = 0;
     for (int q = 0; q < nL; ++q) {
-      double st = wrap2pi(m->La[q] + th);
+      double st = wrap2pi(I->La[q] + th);
       double off = wrap2pi(mid - st);
-      if (off < m->Lw[q]) { fl = q; oL = wrap_pi(a - st); break; }
+      if (off < I->Lw[q]) { fl = q; oL = wrap_pi(a - st); break; }
     }
     for (int q = 0; q < nR; ++q) {
-      double off = wrap2pi(mid - m->Ra[q]);
-      if (off < m->Rw[q]) { fr = q; oR = wrap_pi(a - m->Ra[q]); break; }
+      double off = wrap2pi(mid - I->Ra[q]);
+      if (off < I->Rw[q]) { fr = q; oR = wrap_pi(a - I->Ra[q]); break; }
     }
     if (fl < 0 || fr < 0) continue;
     int n = mo->nm++;
     mo->lf[n] = fl;
     mo->rf[n] = fr;
-    mo->oL[n] = oL / m->Lw[fl];
-    mo->sL[n] = d / m->Lw[fl];
-    mo->oR[n] = oR / m->Rw[fr];
-    mo->sR[n] = d / m->Rw[fr];
+    mo->oL[n] = oL / I->Lw[fl];
+    mo->sL[n] = d / I->Lw[fl];
+    mo->oR[n] = oR / I->Rw[fr];
+    mo->sR[n] = d / I->Rw[fr];
     mo->m0[n] = a;
     mo->dm[n] = d;
   }
@@ -851,12 +929,12 @@ static void gather_ccw(const or_mesh *m, const double *arr_xi, const double *arr
  *           face point in Lval / Rval), average both sides, project back.
  * Lin/Rin: per sorted L/R face, nv*N values in CCW order.  Lout/Rout receive the
  * projected-back values in CCW order. */
-static void mortar_couple(const or_mesh *m, const or_mortars *mo, int mode, const double *Lin, const double *Rin,
-                          double *Lout, double *Rout) {
+static void mortar_couple(const or_mesh *m, const or_iface *I, const or_mortars *mo, int mode, const double *Lin,
+                          const double *Rin, double *Lout, double *Rout) {
   int N = m->N;
   int nv = 4;
-  memset(Lout, 0, sizeof(double) * m->nL * nv * N);
-  memset(Rout, 0, sizeof(double) * m->nR * nv * N);
+  memset(Lout, 0, sizeof(double) * I->nL * nv * N);
+  memset(Rout, 0, sizeof(double) * I->nR * nv * N);
   double PfL[OR_MAXN * OR_MAXN], PbL[OR_MAXN * OR_MAXN], PfR[OR_MAXN * OR_MAXN], PbR[OR_MAXN * OR_MAXN];
   for (int k = 0; k < mo->nm; ++k) {
     int fl = mo->lf[k], fr = mo->rf[k];
@@ -878,7 +956,7 @@ static void mortar_couple(const or_mesh *m, const or_mortars *mo, int mode, cons
         double phi = mo->m0[k] + m->Xs[i] * mo->dm[k];
         double a[4], b[4], Fn[4];
         for (int v = 0; v < 4; ++v) { a[v] = qL[v * N + i]; b[v] = qR[v * N + i]; }
-        /* on a circle about the rotation centre the grid velocity is tangential */
+        /* on a circle about its zone's centre the grid velocity is tangential */
         rusanov(&m->prm, a, b, cos(phi), sin(phi), 0.0, Fn);
         for (int v = 0; v < 4; ++v) fm[v * N + i] = Fn[v];
       }
@@ -1005,17 +1083,19 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
         for (int v = 0; v < 4; ++v) Geta[IEF(e, v, i, j)] = -g[3] * F[v] + g[2] * G[v];
       }
 
-  /* mortars at this stage time */
-  or_mortars mo;
-  memset(&mo, 0, sizeof mo);
-  int nL = m->nL, nR = m->nR;
-  double *Lin = NULL, *Rin = NULL, *Lout = NULL, *Rout = NULL;
-  if (nL > 0) {
-    build_mortars(m, t, &mo);
-    Lin = malloc(sizeof(double) * nL * 4 * N);
-    Rin = malloc(sizeof(double) * nR * 4 * N);
-    Lout = malloc(sizeof(double) * nL * 4 * N);
-    Rout = malloc(sizeof(double) * nR * 4 * N);
+  /* mortars of every interface at this stage time */
+  or_mortars mos[OR_MAXZ];
+  double *Lins[OR_MAXZ], *Rins[OR_MAXZ], *Louts[OR_MAXZ], *Routs[OR_MAXZ];
+  memset(mos, 0, sizeof mos);
+  for (int z = 0; z < m->nz; ++z) {
+    const or_iface *I = &m->zi[z];
+    Lins[z] = Rins[z] = Louts[z] = Routs[z] = NULL;
+    if (I->nL == 0) continue;
+    build_mortars(I, t, &mos[z]);
+    Lins[z] = malloc(sizeof(double) * I->nL * 4 * N);
+    Rins[z] = malloc(sizeof(double) * I->nR * 4 * N);
+    Louts[z] = malloc(sizeof(double) * I->nL * 4 * N);
+    Routs[z] = malloc(sizeof(double) * I->nR * 4 * N);
   }
 
   /* viscous: common solution, gradients, viscous fluxes at the FPs */
@@ -1056,14 +1136,19 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
           }
         }
       }
-    if (nL > 0) {
-      for (int k = 0; k < nL; ++k) gather_ccw(m, Qxi, Qeta, m->Lef[k], m->Lrev[k], 4, Lin + (size_t)k * 4 * N);
-      for (int k = 0; k < nR; ++k) gather_ccw(m, Qxi, Qeta, m->Ref[k], m->Rrev[k], 4, Rin + (size_t)k * 4 * N);
-      mortar_couple(m, &mo, 1, Lin, Rin, Lout, Rout);
+    for (int z = 0; z < m->nz; ++z) {
+      const or_iface *I = &m->zi[z];
+      const int nL = I->nL, nR = I->nR;
+      double *Lin = Lins[z], *Rin = Rins[z], *Lout = Louts[z], *Rout = Routs[z];
+      const or_mortars *mo = &mos[z];
+      if (nL == 0) continue;
+      for (int k = 0; k < nL; ++k) gather_ccw(m, Qxi, Qeta, I->Lef[k], I->Lrev[k], 4, Lin + (size_t)k * 4 * N);
+      for (int k = 0; k < nR; ++k) gather_ccw(m, Qxi, Qeta, I->Ref[k], I->Rrev[k], 4, Rin + (size_t)k * 4 * N);
+      mortar_couple(m, I, mo, 1, Lin, Rin, Lout, Rout);
       for (int side = 0; side < 2; ++side) {
         int n = side ? nR : nL;
         for (int k = 0; k < n; ++k) {
-          int ef = side ? m->Ref[k] : m->Lef[k], rev = side ? m->Rrev[k] : m->Lrev[k];
+          int ef = side ? I->Ref[k] : I->Lef[k], rev = side ? I->Rrev[k] : I->Lrev[k];
           const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
           int e = ef / 4, f = ef % 4;
           for (int v = 0; v < 4; ++v)
@@ -1133,8 +1218,6 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
         }
     /* (e) common viscous normal flux at the face points */
     Fv_face = calloc((size_t)ne * 4 * 4 * N, sizeof(double));
-    double *vL = NULL, *vR = NULL;
-    if (nL > 0) { vL = calloc((size_t)nL * 4 * N, sizeof(double)); vR = calloc((size_t)nR * 4 * N, sizeof(double)); }
     for (int e = 0; e < ne; ++e)
       for (int f = 0; f < 4; ++f) {
         int ef = 4 * e + f, kind = m->fkind[ef];
@@ -1177,21 +1260,27 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
           }
         }
       }
-    if (nL > 0) {
+    for (int z = 0; z < m->nz; ++z) {
+      const or_iface *I = &m->zi[z];
+      const int nL = I->nL, nR = I->nR;
+      double *Lout = Louts[z], *Rout = Routs[z];
+      const or_mortars *mo = &mos[z];
+      if (nL == 0) continue;
+      double *vL = calloc((size_t)nL * 4 * N, sizeof(double)), *vR = calloc((size_t)nR * 4 * N, sizeof(double));
       for (int side = 0; side < 2; ++side) {
         int n = side ? nR : nL;
         for (int k = 0; k < n; ++k) {
-          int ef = side ? m->Ref[k] : m->Lef[k], rev = side ? m->Rrev[k] : m->Lrev[k];
+          int ef = side ? I->Ref[k] : I->Lef[k], rev = side ? I->Rrev[k] : I->Lrev[k];
           double *dst = (side ? vR : vL) + (size_t)k * 4 * N;
           for (int v = 0; v < 4; ++v)
             for (int j = 0; j < N; ++j) dst[v * N + j] = Fv_face[((size_t)ef * 4 + v) * N + (rev ? N - 1 - j : j)];
         }
       }
-      mortar_couple(m, &mo, 2, vL, vR, Lout, Rout);
+      mortar_couple(m, I, mo, 2, vL, vR, Lout, Rout);
       for (int side = 0; side < 2; ++side) {
         int n = side ? nR : nL;
         for (int k = 0; k < n; ++k) {
-          int ef = side ? m->Ref[k] : m->Lef[k], rev = side ? m->Rrev[k] : m->Lrev[k];
+          int ef = side ? I->Ref[k] : I->Lef[k], rev = side ? I->Rrev[k] : I->Lrev[k];
           const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
           double sgn = side ? -1.0 : 1.0; /* back to outward orientation */
           for (int v = 0; v < 4; ++v)
@@ -1239,14 +1328,19 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
       }
     }
   /* sliding interface: Eqs. prjQ2 -> Rusanov -> prjF2 */
-  if (nL > 0) {
-    for (int k = 0; k < nL; ++k) gather_ccw(m, Qxi, Qeta, m->Lef[k], m->Lrev[k], 4, Lin + (size_t)k * 4 * N);
-    for (int k = 0; k < nR; ++k) gather_ccw(m, Qxi, Qeta, m->Ref[k], m->Rrev[k], 4, Rin + (size_t)k * 4 * N);
-    mortar_couple(m, &mo, 0, Lin, Rin, Lout, Rout);
+  for (int z = 0; z < m->nz; ++z) {
+    const or_iface *I = &m->zi[z];
+    const int nL = I->nL, nR = I->nR;
+    double *Lin = Lins[z], *Rin = Rins[z], *Lout = Louts[z], *Rout = Routs[z];
+    const or_mortars *mo = &mos[z];
+    if (nL == 0) continue;
+    for (int k = 0; k < nL; ++k) gather_ccw(m, Qxi, Qeta, I->Lef[k], I->Lrev[k], 4, Lin + (size_t)k * 4 * N);
+    for (int k = 0; k < nR; ++k) gather_ccw(m, Qxi, Qeta, I->Ref[k], I->Rrev[k], 4, Rin + (size_t)k * 4 * N);
+    mortar_couple(m, I, mo, 0, Lin, Rin, Lout, Rout);
     for (int side = 0; side < 2; ++side) {
       int n = side ? nR : nL;
       for (int k = 0; k < n; ++k) {
-        int ef = side ? m->Ref[k] : m->Lef[k], rev = side ? m->Rrev[k] : m->Lrev[k];
+        int ef = side ? I->Ref[k] : I->Lef[k], rev = side ? I->Rrev[k] : I->Lrev[k];
         int e = ef / 4, f = ef % 4;
         const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
         double sgn = side ? -1.0 : 1.0; /* L -> R normal is outward for L, inward for R */
@@ -1291,7 +1385,8 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
 
   free(Qxi); free(Qeta); free(Fxi); free(Geta);
   free(cQxi); free(cQeta); free(Gxx); free(Gxy); free(Gex); free(Gey); free(Fv_face);
-  if (nL > 0) { free(Lin); free(Rin); free(Lout); free(Rout); free_mortars(&mo); }
+  for (int z = 0; z < m->nz; ++z)
+    if (m->zi[z].nL > 0) { free(Lins[z]); free(Rins[z]); free(Louts[z]); free(Routs[z]); free_mortars(&mos[z]); }
   return 0;
 }
 
@@ -1383,15 +1478,22 @@ int or_step_rk54(or_mesh *m, double *Q, double *t, double dt, int nsteps) {
   return 0;
 }
 
-/* mortar list at time t, for tests: returns the number of mortars; arrays must
- * hold nL + nR entries */
-int or_mortar_list(const or_mesh *m, double t, int *lf, int *rf, double *oL, double *sL, double *oR, double *sR) {
+/* mortar list of zone z's interface at time t, for tests: returns the number
+ * of mortars (-1 for no such zone); arrays must hold nL + nR entries */
+int or_mortar_list_zone(const or_mesh *m, int z, double t, int *lf, int *rf, double *oL, double *sL, double *oR,
+                        double *sR) {
+  if (z < 1 || z > m->nz) return -1;
   or_mortars mo;
-  build_mortars(m, t, &mo);
+  build_mortars(&m->zi[z - 1], t, &mo);
   for (int k = 0; k < mo.nm; ++k) {
     lf[k] = mo.lf[k]; rf[k] = mo.rf[k]; oL[k] = mo.oL[k]; sL[k] = mo.sL[k]; oR[k] = mo.oR[k]; sR[k] = mo.sR[k];
   }
   int n = mo.nm;
   free_mortars(&mo);
   return n;
+}
+
+/* the same for zone 1 */
+int or_mortar_list(const or_mesh *m, double t, int *lf, int *rf, double *oL, double *sL, double *oR, double *sR) {
+  return or_mortar_list_zone(m, 1, t, lf, rf, oL, sL, oR, sR);
 }

@@ -12,9 +12,10 @@ CUDA library):
 
 ``xy``          float64 (n_nodes, 2)  node coordinates
 ``elem_nodes``  int32 (E, 4)          corners n0..n3, counter-clockwise
-``elem_zone``   int32 (E,)            0 stationary, 1 rotating
+``elem_zone``   int32 (E,)            0 stationary, z >= 1 rotating zone z
 ``edge_arc``    int32 (E, 4)          edge kind of local face f: 0 straight,
-                                      1 circular arc about ``center``, 2 cubic
+                                      1 circular arc about the centre of the
+                                      cell's arc zone, 2 cubic
                                       through the corners and two edge nodes
 ``edge_nodes``  int32 (E, 4, 2)       (only when some edge is cubic) nodes at
                                       face parameter 1/3 and 2/3 of each cubic
@@ -23,8 +24,18 @@ CUDA library):
 ``pfaces``      int32 (np, 4)         periodic pairs (eA, fA, eB, fB)
 ``ifaces_L``    int32 (nL, 2)         interface faces of the rotating zone
 ``ifaces_R``    int32 (nR, 2)         interface faces of the stationary zone
-``center``      float64 (2,)          rotation centre (also every arc's centre)
-``r_interface`` float                 radius of the sliding interface
+``center``      float64 (2,)          rotation centre of zone 1 (the centre of its
+                                      interface circle)
+``r_interface`` float                 radius of zone 1's sliding interface
+``zones``       list (optional)       rotating zones 2, 3, ...: dicts with
+                                      ``center``, ``r_interface``, ``omega``
+                                      (its angular velocity), ``ifaces_L``,
+                                      ``ifaces_R`` as above for that zone's
+                                      own interface with zone 0
+``elem_arc_zone`` int32 (E,) (optional) zone whose centre the cell's arc
+                                      edges are drawn about (default: the
+                                      cell's own zone, zone 1 for stationary
+                                      cells)
 
 Local faces follow the reference square [0,1]^2 with n0=(0,0), n1=(1,0),
 n2=(1,1), n3=(0,1): f0 is eta=0 (n0->n1), f1 is xi=1 (n1->n2), f2 is eta=1
@@ -136,7 +147,7 @@ def _face_of(cell: list[int], a: int, b: int) -> int:
     raise ValueError("edge not in cell")
 
 
-def _finish(mb: _MeshBuilder, bfaces, pfaces, ifL, ifR, r_interface) -> dict:
+def _finish(mb: _MeshBuilder, bfaces, pfaces, ifL, ifR, r_interface, zones=None, arc_zone=None) -> dict:
     out = {
         "xy": mb.all_xy(),
         "elem_nodes": np.asarray(mb.cells, dtype=np.int32).reshape(-1, 4),
@@ -151,6 +162,14 @@ def _finish(mb: _MeshBuilder, bfaces, pfaces, ifL, ifR, r_interface) -> dict:
     }
     if any(k == EDGE_CUBIC for row in mb.arcs for k in row):
         out["edge_nodes"] = np.asarray(mb.enodes, dtype=np.int32).reshape(-1, 4, 2)
+    if zones:
+        out["zones"] = [{"center": np.asarray(z["center"], dtype=np.float64),
+                         "r_interface": float(z["r_interface"]), "omega": float(z["omega"]),
+                         "ifaces_L": np.asarray(z["ifaces_L"], dtype=np.int32).reshape(-1, 2),
+                         "ifaces_R": np.asarray(z["ifaces_R"], dtype=np.int32).reshape(-1, 2)}
+                        for z in zones]
+    if arc_zone is not None:
+        out["elem_arc_zone"] = np.asarray(arc_zone, dtype=np.int32)
     return out
 
 
@@ -274,6 +293,64 @@ def _polar_ring(mb, table, zone, center, radii, nth, phi0):
     return cells, ids[0], ids[nl]
 
 
+def _rotor_disk(mb, table, zone, c, core_half, n_core, r_interface, n_ring_in, phi):
+    """Rotating disk about c: a core square of n_core x n_core straight cells
+    and an O-ring of n_ring_in layers from the core square to the circle
+    (4 n_core arcs starting at angle phi).  Returns (ring cells, circle nodes)."""
+    look = _lookup(mb)
+    core_ids = np.zeros((n_core + 1, n_core + 1), dtype=np.int64)
+    for i in range(n_core + 1):
+        for j in range(n_core + 1):
+            core_ids[i, j] = table.add(c[0] - core_half + 2 * core_half * i / n_core,
+                                       c[1] - core_half + 2 * core_half * j / n_core)
+    for j in range(n_core):
+        for i in range(n_core):
+            mb.add_cell(look, [core_ids[i, j], core_ids[i + 1, j], core_ids[i + 1, j + 1],
+                               core_ids[i, j + 1]], zone)
+    sq = _square_loop(c, core_half, n_core)
+    circ_in = _circle(c, r_interface, 4 * n_core, phi)
+    cells_in, _, loopL = _ring(mb, table, zone, sq, circ_in, n_ring_in, False, True)
+    return cells_in, loopL
+
+
+def _hole_ring(mb, table, c, r_interface, m_out, half, n_hole, n_ring_out, phi):
+    """Stationary O-ring of n_ring_out layers from the circle about c (m_out
+    arcs starting at angle phi) out to the square hole of half-width ``half``.
+    Returns (ring cells, circle nodes)."""
+    circ_out = _circle(c, r_interface, m_out, phi)
+    hole = _square_loop(c, half, n_hole)
+    cells_out, loopR, _ = _ring(mb, table, 0, circ_out, hole, n_ring_out, True, False)
+    return cells_out, loopR
+
+
+def _cartesian_with_holes(mb, table, x0, y0, h, nx, ny, holes):
+    """nx x ny Cartesian cells of spacing h from (x0, y0), periodic in x and y,
+    without the cells (i, j) inside any hole (ilo, ihi, jlo, jhi).  Returns the
+    periodic face pairs."""
+    look = _lookup(mb)
+    cart = np.zeros((nx + 1, ny + 1), dtype=np.int64)
+    for i in range(nx + 1):
+        for j in range(ny + 1):
+            cart[i, j] = table.add(x0 + i * h, y0 + j * h)
+    cart_cell = {}
+    for j in range(ny):
+        for i in range(nx):
+            if any(ilo <= i < ihi and jlo <= j < jhi for ilo, ihi, jlo, jhi in holes):
+                continue
+            cart_cell[(i, j)] = mb.add_cell(look, [cart[i, j], cart[i + 1, j],
+                                                   cart[i + 1, j + 1], cart[i, j + 1]], 0)
+    pf = []
+    for j in range(ny):
+        a, bb = cart_cell[(0, j)], cart_cell[(nx - 1, j)]
+        pf.append((a, _face_of(mb.cells[a], cart[0, j], cart[0, j + 1]),
+                   bb, _face_of(mb.cells[bb], cart[nx, j], cart[nx, j + 1])))
+    for i in range(nx):
+        a, bb = cart_cell[(i, 0)], cart_cell[(i, ny - 1)]
+        pf.append((a, _face_of(mb.cells[a], cart[i, 0], cart[i + 1, 0]),
+                   bb, _face_of(mb.cells[bb], cart[i, ny], cart[i + 1, ny])))
+    return pf
+
+
 def rotor_mesh(half_width=10.0, n_cart=64, n_hole=24, r_interface=3.0, n_core=24,
                core_half=1.5, n_ring_in=16, n_ring_out=4, shift_L=0.0, shift_R=0.0) -> dict:
     """Periodic square [-w,w]^2 with a rotating disk r<=r_interface (Sec. 4.1).
@@ -296,56 +373,69 @@ def rotor_mesh(half_width=10.0, n_cart=64, n_hole=24, r_interface=3.0, n_core=24
         raise ValueError("need core square inside the circle inside the hole")
     c = (0.0, 0.0)
     mb = _MeshBuilder(c)
-    # rotating zone ------------------------------------------------------
     tin = mb.node_table()
-    look = _lookup(mb)
-    core_ids = np.zeros((n_core + 1, n_core + 1), dtype=np.int64)
-    for i in range(n_core + 1):
-        for j in range(n_core + 1):
-            core_ids[i, j] = tin.add(-core_half + 2 * core_half * i / n_core,
-                                     -core_half + 2 * core_half * j / n_core)
-    for j in range(n_core):
-        for i in range(n_core):
-            mb.add_cell(look, [core_ids[i, j], core_ids[i + 1, j], core_ids[i + 1, j + 1],
-                               core_ids[i, j + 1]], 1)
-    m_in = 4 * n_core
-    phiL = -0.75 * math.pi + shift_L
-    sq = _square_loop(c, core_half, n_core)
-    circ_in = _circle(c, r_interface, m_in, phiL)
-    cells_in, _, loopL = _ring(mb, tin, 1, sq, circ_in, n_ring_in, False, True)
-    # stationary zone ----------------------------------------------------
+    cells_in, loopL = _rotor_disk(mb, tin, 1, c, core_half, n_core, r_interface, n_ring_in,
+                                  -0.75 * math.pi + shift_L)
     tout = mb.node_table()
-    look = _lookup(mb)
-    m_out = 4 * n_hole
-    phiR = -0.75 * math.pi + shift_R
-    circ_out = _circle(c, r_interface, m_out, phiR)
-    hole = _square_loop(c, b, n_hole)
-    cells_out, loopR, _ = _ring(mb, tout, 0, circ_out, hole, n_ring_out, True, False)
-    cart = np.zeros((n_cart + 1, n_cart + 1), dtype=np.int64)
-    for i in range(n_cart + 1):
-        for j in range(n_cart + 1):
-            cart[i, j] = tout.add(-half_width + i * h, -half_width + j * h)
+    cells_out, loopR = _hole_ring(mb, tout, c, r_interface, 4 * n_hole, b, n_hole, n_ring_out,
+                                  -0.75 * math.pi + shift_R)
     lo = (n_cart - n_hole) // 2
-    hi = lo + n_hole
-    cart_cell = {}
-    for j in range(n_cart):
-        for i in range(n_cart):
-            if lo <= i < hi and lo <= j < hi:
-                continue
-            cart_cell[(i, j)] = mb.add_cell(look, [cart[i, j], cart[i + 1, j],
-                                                   cart[i + 1, j + 1], cart[i, j + 1]], 0)
-    pf = []
-    for j in range(n_cart):
-        a, bb = cart_cell[(0, j)], cart_cell[(n_cart - 1, j)]
-        pf.append((a, _face_of(mb.cells[a], cart[0, j], cart[0, j + 1]),
-                   bb, _face_of(mb.cells[bb], cart[n_cart, j], cart[n_cart, j + 1])))
-    for i in range(n_cart):
-        a, bb = cart_cell[(i, 0)], cart_cell[(i, n_cart - 1)]
-        pf.append((a, _face_of(mb.cells[a], cart[i, 0], cart[i + 1, 0]),
-                   bb, _face_of(mb.cells[bb], cart[i, n_cart], cart[i + 1, n_cart])))
+    pf = _cartesian_with_holes(mb, tout, -half_width, -half_width, h, n_cart, n_cart,
+                               [(lo, lo + n_hole, lo, lo + n_hole)])
     ifL = _interface_faces(mb, cells_in, loopL)
     ifR = _interface_faces(mb, cells_out, loopR)
     return _finish(mb, [], pf, ifL, ifR, r_interface)
+
+
+def twin_rotor_mesh(half_width=10.0, n_cart=64, n_hole=24, r_interface=3.0, n_core=24,
+                    core_half=1.5, n_ring_in=16, n_ring_out=4, omega2=-math.pi / 4,
+                    shift_L=0.0, shift_R=0.0, n_core2=None) -> dict:
+    """Two rotating disks in one periodic box (several rotating zones, each
+    with its own sliding interface; Sec. 3.2 applied per interface).
+
+    The box [-2w, 2w] x [-w, w] is a 2 n_cart x n_cart Cartesian grid of
+    spacing h = 2w/n_cart, periodic in x and y, with two square holes of
+    n_hole x n_hole cells centred at (-w, 0) and (w, 0).  Each hole holds the
+    disk and the stationary O-ring of ``rotor_mesh``: zone 1 about (-w, 0)
+    (its angular velocity is the flow parameter omega) and zone 2 about
+    (w, 0) with angular velocity ``omega2``.  Disk 2 has 4 n_core2 interface
+    faces (default n_core); with n_core2 = n_core the mesh is symmetric under
+    the half turn about the origin.  The stationary ring cells about disk 2
+    draw their arcs about its centre (``elem_arc_zone`` = 2).
+    """
+    n_core2 = n_core if n_core2 is None else n_core2
+    h = 2.0 * half_width / n_cart
+    b = n_hole * h / 2.0
+    if n_hole % 2 or n_cart % 2 or (n_cart - n_hole) % 2:
+        raise ValueError("n_cart, n_hole and n_cart - n_hole must be even")
+    if not (core_half * math.sqrt(2) < r_interface < b):
+        raise ValueError("need core square inside the circle inside the hole")
+    c1, c2 = (-half_width, 0.0), (half_width, 0.0)
+    mb = _MeshBuilder(c1)
+    t1 = mb.node_table()
+    cells1, loopL1 = _rotor_disk(mb, t1, 1, c1, core_half, n_core, r_interface, n_ring_in,
+                                 -0.75 * math.pi + shift_L)
+    t2 = mb.node_table()
+    cells2, loopL2 = _rotor_disk(mb, t2, 2, c2, core_half, n_core2, r_interface, n_ring_in,
+                                 -0.75 * math.pi + shift_L)
+    tout = mb.node_table()
+    out1, loopR1 = _hole_ring(mb, tout, c1, r_interface, 4 * n_hole, b, n_hole, n_ring_out,
+                              -0.75 * math.pi + shift_R)
+    first2 = len(mb.cells)
+    out2, loopR2 = _hole_ring(mb, tout, c2, r_interface, 4 * n_hole, b, n_hole, n_ring_out,
+                              -0.75 * math.pi + shift_R)
+    arc_zone = np.array([z if z else 1 for z in mb.zone_of], dtype=np.int32)
+    arc_zone[first2:len(mb.cells)] = 2
+    lo = n_cart // 2 - n_hole // 2
+    pf = _cartesian_with_holes(mb, tout, -2.0 * half_width, -half_width, h, 2 * n_cart, n_cart,
+                               [(lo, lo + n_hole, lo, lo + n_hole),
+                                (lo + n_cart, lo + n_cart + n_hole, lo, lo + n_hole)])
+    arc_zone = np.concatenate([arc_zone, np.ones(len(mb.cells) - len(arc_zone), dtype=np.int32)])
+    zone2 = {"center": c2, "r_interface": r_interface, "omega": omega2,
+             "ifaces_L": _interface_faces(mb, cells2, loopL2),
+             "ifaces_R": _interface_faces(mb, out2, loopR2)}
+    return _finish(mb, [], pf, _interface_faces(mb, cells1, loopL1), _interface_faces(mb, out1, loopR1),
+                   r_interface, zones=[zone2], arc_zone=arc_zone)
 
 
 def periodic_box_mesh(n=4, half_width=1.0, rotating=False) -> dict:
@@ -414,7 +504,7 @@ def perturb_nodes(mesh: dict, amplitude: float, seed: int = 1503) -> dict:
 def mesh_stats(mesh: dict) -> dict:
     return {
         "elements": int(len(mesh["elem_nodes"])),
-        "rotating": int(mesh["elem_zone"].sum()),
+        "rotating": int((mesh["elem_zone"] > 0).sum()),
         "curved": int((mesh["edge_arc"].sum(axis=1) > 0).sum()),
         "interface_L": int(len(mesh["ifaces_L"])),
         "interface_R": int(len(mesh["ifaces_R"])),
