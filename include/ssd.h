@@ -65,12 +65,33 @@ enum {
 /* edge kinds of sd_mesh.edge_arc */
 enum { SD_EDGE_STRAIGHT = 0, SD_EDGE_ARC = 1, SD_EDGE_CUBIC = 2 };
 
+/* rotating zones per mesh (zone 1 plus at most SD_MAX_ZONES - 1 further zones) */
+#define SD_MAX_ZONES 4
+
+/* A further rotating zone (the paper has one per case; Sec. 2.2 applies to
+ * each zone and Sec. 3.2 to each interface on its own).  Zone k + 2, the k-th
+ * entry of sd_mesh.zones, turns rigidly about `center` at angular velocity
+ * `omega` and meets the stationary zone 0 across its own circular sliding
+ * interface of radius r_interface about `center`: iface_L lists its faces on
+ * the zone's side, iface_R those on the stationary side, both as
+ * [n][2] (element, local face).  The arrays are copied by sd_create. */
+typedef struct {
+  double center[2];
+  double r_interface;
+  double omega;
+  int n_iface_L;
+  const int *iface_L;
+  int n_iface_R;
+  const int *iface_R;
+} sd_zone;
+
 /* Mesh (Sec. 3.1: every cell is mapped to the standard square [0,1]^2).
  * Corners n0..n3 are counter-clockwise and map to (0,0), (1,0), (1,1), (0,1).
  * Local face f: f0 = {eta=0} n0->n1, f1 = {xi=1} n1->n2, f2 = {eta=1} n3->n2,
  * f3 = {xi=0} n0->n3 (the arrow is the direction of the face parameter).
- * An SD_EDGE_ARC edge is the circular arc about `center` through its two
- * corners (both at the same radius); an SD_EDGE_CUBIC edge is the cubic
+ * An SD_EDGE_ARC edge is the circular arc through its two corners (both at
+ * the same radius) about the centre of the cell's arc zone (elem_arc_zone:
+ * zone 1's centre is `center`); an SD_EDGE_CUBIC edge is the cubic
  * through its corners and the two edge nodes edge_nodes[e][f][0..1] at face
  * parameter 1/3 and 2/3 (Sec. 3.1's 12-node cubic cells); other edges are
  * straight.  The map of a cell is the transfinite interpolation of its four
@@ -79,13 +100,15 @@ enum { SD_EDGE_STRAIGHT = 0, SD_EDGE_ARC = 1, SD_EDGE_CUBIC = 2 };
  * zone are found from their node pairs and must have the same edge kind (and,
  * if cubic, the same edge nodes); periodic and interface faces cannot be
  * cubic.  Every other face must appear in exactly one of bfaces, pfaces,
- * iface_L, iface_R. */
+ * iface_L, iface_R and the interface lists of the further zones.  A
+ * conforming face joins two cells of one zone; periodic faces lie in zone 0. */
 typedef struct {
   int n_nodes;
   const double *xy;        /* [n_nodes][2] */
   int n_elems;
   const int *elem_nodes;   /* [n_elems][4] */
-  const int *elem_zone;    /* [n_elems]: 0 stationary, 1 rotating (rigid rotation about center) */
+  const int *elem_zone;    /* [n_elems]: 0 stationary, z >= 1 rotating zone z (zone 1: rigid
+                              rotation about center at sd_params.omega; zone z >= 2: zones[z - 2]) */
   const int *edge_arc;     /* [n_elems][4]: SD_EDGE_* kind of local face f */
   int n_bfaces;
   const int *bfaces;       /* [n_bfaces][3]: element, local face, SD_BC_* tag */
@@ -95,10 +118,15 @@ typedef struct {
   const int *iface_L;      /* [n][2]: element, local face on the interface, rotating side (Sec. 3.2 "left") */
   int n_iface_R;
   const int *iface_R;      /* [n][2]: stationary side ("right") */
-  double center[2];        /* rotation centre = centre of the interface circle */
-  double r_interface;      /* radius of the sliding interface */
+  double center[2];        /* zone 1: rotation centre = centre of its interface circle */
+  double r_interface;      /* radius of zone 1's sliding interface */
   const int *edge_nodes;   /* [n_elems][4][2] node indices of cubic edges (-1 elsewhere);
                               may be NULL when no edge is cubic */
+  int n_zones;             /* further rotating zones (0 .. SD_MAX_ZONES - 1) */
+  const sd_zone *zones;    /* [n_zones] zones 2, 3, ...; may be NULL when n_zones = 0 */
+  const int *elem_arc_zone; /* [n_elems] zone (>= 1) whose centre the cell's arc edges are
+                              drawn about; a rotating cell's must be its own zone.  NULL: the
+                              cell's own zone, zone 1 for stationary cells */
 } sd_mesh;
 
 /* Gas, flow and run parameters (non-dimensional).  Viscous fluxes follow
@@ -109,7 +137,7 @@ typedef struct {
   double Rgas;      /* gas constant, p = rho Rgas T */
   double mu;        /* dynamic viscosity (constant) */
   double prandtl;   /* Prandtl number */
-  double omega;     /* angular velocity of the rotating zone (Sec. 2.2) */
+  double omega;     /* angular velocity of rotating zone 1 (Sec. 2.2) */
   double T_wall;    /* temperature of SD_BC_WALL faces */
   int viscous;      /* 0 Euler, 1 Navier-Stokes */
   int precision;    /* SD_PREC_FP64, or SD_PREC_FP32: FP32 interpolation, flux and

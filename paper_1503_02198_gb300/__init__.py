@@ -33,13 +33,23 @@ _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
 
 
+SD_MAX_ZONES = 4
+
+
+class sd_zone(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_double * 2), ("r_interface", ctypes.c_double), ("omega", ctypes.c_double),
+                ("n_iface_L", ctypes.c_int), ("iface_L", _c_int_p), ("n_iface_R", ctypes.c_int),
+                ("iface_R", _c_int_p)]
+
+
 class sd_mesh(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int), ("xy", _c_dbl_p), ("n_elems", ctypes.c_int),
                 ("elem_nodes", _c_int_p), ("elem_zone", _c_int_p), ("edge_arc", _c_int_p),
                 ("n_bfaces", ctypes.c_int), ("bfaces", _c_int_p), ("n_pfaces", ctypes.c_int),
                 ("pfaces", _c_int_p), ("n_iface_L", ctypes.c_int), ("iface_L", _c_int_p),
                 ("n_iface_R", ctypes.c_int), ("iface_R", _c_int_p), ("center", ctypes.c_double * 2),
-                ("r_interface", ctypes.c_double), ("edge_nodes", _c_int_p)]
+                ("r_interface", ctypes.c_double), ("edge_nodes", _c_int_p), ("n_zones", ctypes.c_int),
+                ("zones", ctypes.POINTER(sd_zone)), ("elem_arc_zone", _c_int_p)]
 
 
 class sd_params(ctypes.Structure):
@@ -130,14 +140,24 @@ def _mesh_struct(mesh: dict, keep: list) -> sd_mesh:
     Lf = arr(mesh["ifaces_L"], np.int32)
     Rf = arr(mesh["ifaces_R"], np.int32)
     enode = arr(mesh["edge_nodes"], np.int32) if "edge_nodes" in mesh else None
+    azone = arr(mesh["elem_arc_zone"], np.int32) if "elem_arc_zone" in mesh else None
 
     def ip(a):
         return a.ctypes.data_as(_c_int_p)
 
+    # further rotating zones 2, 3, ... (each with its own interface)
+    extra = mesh.get("zones", [])
+    zones = (sd_zone * max(len(extra), 1))()
+    keep.append(zones)
+    for k, z in enumerate(extra):
+        zl, zr = arr(z["ifaces_L"], np.int32).reshape(-1, 2), arr(z["ifaces_R"], np.int32).reshape(-1, 2)
+        zones[k] = sd_zone((ctypes.c_double * 2)(float(z["center"][0]), float(z["center"][1])),
+                           float(z["r_interface"]), float(z["omega"]), len(zl), ip(zl), len(zr), ip(zr))
     return sd_mesh(len(xy), xy.ctypes.data_as(_c_dbl_p), len(en), ip(en), ip(zone), ip(arc), len(bf), ip(bf),
                    len(pf), ip(pf), len(Lf), ip(Lf), len(Rf), ip(Rf),
                    (ctypes.c_double * 2)(float(mesh["center"][0]), float(mesh["center"][1])),
-                   float(mesh["r_interface"]), ip(enode) if enode is not None else None)
+                   float(mesh["r_interface"]), ip(enode) if enode is not None else None, len(extra),
+                   zones, ip(azone) if azone is not None else None)
 
 
 def _params_struct(params, precision, stream=None) -> sd_params:

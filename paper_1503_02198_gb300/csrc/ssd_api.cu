@@ -176,7 +176,7 @@ __global__ void k_fma_probe(T *out, int iters, T a, T b) {
 
 struct sd_handle {
   int N = 0, E = 0, precision = 0;
-  double center[2] = {0, 0};
+  std::vector<double> zpar;  // [kZT][4] per zone: centre x, y, omega, interface radius
   sd_params prm{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -232,11 +232,13 @@ struct IfaceSide {
   std::vector<double> a, w, S, iw;
 };
 
-int build_iface(sd_handle *h, const sd_mesh *m, int n, const int *lst, std::vector<int> &kind, int tag,
-                IfaceSide &out) {
+// one side of the interface of circle (cx, cy, r), appended to out sorted
+// counter-clockwise
+int build_iface(sd_handle *h, const sd_mesh *m, double cx, double cy, double r_if, int n, const int *lst,
+                std::vector<int> &kind, int tag, IfaceSide &out) {
   struct Item { int ef, rev; double a, w, S; };
   std::vector<Item> items;
-  const double cx = m->center[0], cy = m->center[1];
+  if (n > 0 && !lst) return fail(h, SD_ERR_ARG, "interface face list missing");
   for (int k = 0; k < n; ++k) {
     const int e = lst[2 * k], f = lst[2 * k + 1];
     if (e < 0 || e >= m->n_elems || f < 0 || f > 3) return fail(h, SD_ERR_MESH, "interface face index out of range");
@@ -248,8 +250,7 @@ int build_iface(sd_handle *h, const sd_mesh *m, int n, const int *lst, std::vect
     const double ax = m->xy[2 * na] - cx, ay = m->xy[2 * na + 1] - cy;
     const double bx = m->xy[2 * nb] - cx, by = m->xy[2 * nb + 1] - cy;
     const double ra = std::hypot(ax, ay), rb = std::hypot(bx, by);
-    if (std::fabs(ra - m->r_interface) > 1e-9 * std::max(1.0, m->r_interface) ||
-        std::fabs(rb - m->r_interface) > 1e-9 * std::max(1.0, m->r_interface))
+    if (std::fabs(ra - r_if) > 1e-9 * std::max(1.0, r_if) || std::fabs(rb - r_if) > 1e-9 * std::max(1.0, r_if))
       return fail(h, SD_ERR_MESH, "interface node not on the interface circle");
     const double d = std::atan2(ax * by - ay * bx, ax * bx + ay * by);  // signed angle a -> b
     Item it;
@@ -283,14 +284,37 @@ int build_iface(sd_handle *h, const sd_mesh *m, int n, const int *lst, std::vect
   return SD_OK;
 }
 
-int build_mesh(sd_handle *h, const sd_mesh *m) {
+// omega1: angular velocity of zone 1 (the flow parameter)
+int build_mesh(sd_handle *h, const sd_mesh *m, double omega1) {
   const int E = m->n_elems;
   if (E <= 0 || !m->xy || !m->elem_nodes || !m->elem_zone || !m->edge_arc || m->n_nodes <= 0)
     return fail(h, SD_ERR_ARG, "mesh arrays missing");
+  if (m->n_zones < 0 || m->n_zones > kMaxZones - 1 || (m->n_zones > 0 && !m->zones))
+    return fail(h, SD_ERR_ARG, "n_zones must be 0 .. SD_MAX_ZONES - 1 with a zones array");
+  const int nZ = 1 + m->n_zones;  // rotating zones
+  // per zone: centre x, y, omega, interface radius (zone 0: zeros)
+  std::vector<double> zpar(4 * kZT, 0.0);
+  for (int z = 1; z <= nZ; ++z) {
+    const double *c = z == 1 ? m->center : m->zones[z - 2].center;
+    zpar[4 * z] = c[0];
+    zpar[4 * z + 1] = c[1];
+    zpar[4 * z + 2] = z == 1 ? omega1 : m->zones[z - 2].omega;
+    zpar[4 * z + 3] = z == 1 ? m->r_interface : m->zones[z - 2].r_interface;
+    if (!std::isfinite(zpar[4 * z]) || !std::isfinite(zpar[4 * z + 1]) || !std::isfinite(zpar[4 * z + 2]) ||
+        !std::isfinite(zpar[4 * z + 3]))
+      return fail(h, SD_ERR_ARG, "zone centre, angular velocity and radius must be finite");
+  }
   for (int k = 0; k < 4 * E; ++k)
     if (m->elem_nodes[k] < 0 || m->elem_nodes[k] >= m->n_nodes) return fail(h, SD_ERR_MESH, "node index out of range");
-  for (int e = 0; e < E; ++e)
-    if (m->elem_zone[e] != 0 && m->elem_zone[e] != 1) return fail(h, SD_ERR_MESH, "zone must be 0 or 1");
+  // frame zone of each cell: its own zone if rotating, else its arc zone
+  std::vector<int> frame(E);
+  for (int e = 0; e < E; ++e) {
+    const int z = m->elem_zone[e];
+    if (z < 0 || z > nZ) return fail(h, SD_ERR_MESH, "zone out of range (0 .. 1 + n_zones)");
+    const int a = m->elem_arc_zone ? m->elem_arc_zone[e] : (z ? z : 1);
+    if (a < 1 || a > nZ || (z && a != z)) return fail(h, SD_ERR_MESH, "invalid arc zone (a rotating cell's is its own zone)");
+    frame[e] = a;
+  }
   bool any_cubic = false;
   for (int k = 0; k < 4 * E; ++k) {
     const int kind = m->edge_arc[k];
@@ -336,15 +360,36 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
     const double flip = std::hypot(m->xy[2 * a0] + tx - m->xy[2 * b1], m->xy[2 * a0 + 1] + ty - m->xy[2 * b1 + 1]);
     faces.push_back(make_int4(efA, efB, flip < same ? 1 : 0, 0));
   }
+  // the interfaces, zone by zone, their lists concatenated
   IfaceSide L, R;
-  int rc;
-  if ((m->n_iface_L > 0) != (m->n_iface_R > 0)) return fail(h, SD_ERR_MESH, "interface needs both sides");
-  if ((rc = build_iface(h, m, m->n_iface_L, m->iface_L, kind, 2, L))) return rc;
-  if ((rc = build_iface(h, m, m->n_iface_R, m->iface_R, kind, 3, R))) return rc;
-  for (const int4 &f : L.face)
-    if (m->elem_zone[f.x / 4] != 1) return fail(h, SD_ERR_MESH, "rotating-side interface face not in zone 1");
-  for (const int4 &f : R.face)
-    if (m->elem_zone[f.x / 4] != 0) return fail(h, SD_ERR_MESH, "stationary-side interface face not in zone 0");
+  std::vector<int> zoff(2 * kZT, 0), ifzL, ifzR;
+  int nbmax = 0;
+  for (int z = 1; z <= nZ; ++z) {
+    const int nLz = z == 1 ? m->n_iface_L : m->zones[z - 2].n_iface_L;
+    const int nRz = z == 1 ? m->n_iface_R : m->zones[z - 2].n_iface_R;
+    const int *lL = z == 1 ? m->iface_L : m->zones[z - 2].iface_L;
+    const int *lR = z == 1 ? m->iface_R : m->zones[z - 2].iface_R;
+    if (nLz < 0 || nRz < 0 || (nLz > 0) != (nRz > 0)) return fail(h, SD_ERR_MESH, "interface needs both sides");
+    const size_t l0 = L.face.size(), r0 = R.face.size();
+    int rc;
+    if ((rc = build_iface(h, m, zpar[4 * z], zpar[4 * z + 1], zpar[4 * z + 3], nLz, lL, kind, 2, L))) return rc;
+    if ((rc = build_iface(h, m, zpar[4 * z], zpar[4 * z + 1], zpar[4 * z + 3], nRz, lR, kind, 3, R))) return rc;
+    for (size_t k = l0; k < L.face.size(); ++k)
+      if (m->elem_zone[L.face[k].x / 4] != z) return fail(h, SD_ERR_MESH, "rotating-side interface face not in its zone");
+    for (size_t k = r0; k < R.face.size(); ++k)
+      if (m->elem_zone[R.face[k].x / 4] != 0) return fail(h, SD_ERR_MESH, "stationary-side interface face not in zone 0");
+    zoff[z] = (int)L.face.size();
+    zoff[kZT + z] = (int)R.face.size();
+    ifzL.insert(ifzL.end(), (size_t)nLz, z - 1);
+    ifzR.insert(ifzR.end(), (size_t)nRz, z - 1);
+    nbmax = std::max(nbmax, nLz + nRz);
+  }
+  for (int z = nZ + 1; z < kZT; ++z) {
+    zoff[z] = zoff[nZ];
+    zoff[kZT + z] = zoff[kZT + nZ];
+  }
+  std::vector<int> ifz(ifzL);
+  ifz.insert(ifz.end(), ifzR.begin(), ifzR.end());
   // conforming faces: shared node pairs
   std::unordered_map<long long, int> open;
   open.reserve(4 * (size_t)E);
@@ -392,14 +437,18 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   md.nL = (int)L.face.size();
   md.nR = (int)R.face.size();
   md.nM = md.nL + md.nR;
+  md.nI = nZ;
+  md.nbmax = nbmax;
   std::vector<double> corners(8 * (size_t)E);
   std::vector<int> arcs(E);
   std::vector<double> cubic(any_cubic ? 16 * (size_t)E : 0, 0.0);
   for (int e = 0; e < E; ++e) {
+    // coordinates relative to the centre of the cell's frame zone
+    const double fx = zpar[4 * frame[e]], fy = zpar[4 * frame[e] + 1];
     for (int k = 0; k < 4; ++k) {
       const int n = m->elem_nodes[4 * e + k];
-      corners[8 * (size_t)e + 2 * k] = m->xy[2 * n] - m->center[0];
-      corners[8 * (size_t)e + 2 * k + 1] = m->xy[2 * n + 1] - m->center[1];
+      corners[8 * (size_t)e + 2 * k] = m->xy[2 * n] - fx;
+      corners[8 * (size_t)e + 2 * k + 1] = m->xy[2 * n + 1] - fy;
     }
     int bits = 0;
     for (int f = 0; f < 4; ++f)
@@ -407,8 +456,8 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
         bits |= 16 << f;
         for (int q = 0; q < 2; ++q) {
           const int n = m->edge_nodes[2 * (4 * e + f) + q];
-          cubic[16 * (size_t)e + 4 * f + 2 * q] = m->xy[2 * n] - m->center[0];
-          cubic[16 * (size_t)e + 4 * f + 2 * q + 1] = m->xy[2 * n + 1] - m->center[1];
+          cubic[16 * (size_t)e + 4 * f + 2 * q] = m->xy[2 * n] - fx;
+          cubic[16 * (size_t)e + 4 * f + 2 * q + 1] = m->xy[2 * n + 1] - fy;
         }
       } else if (m->edge_arc[4 * e + f] == SD_EDGE_ARC) {
         bits |= 1 << f;
@@ -424,8 +473,8 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   }
   cudaError_t ce;
   int4 *dfaces, *dbfaces, *dL, *dR;
-  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS, *dLiW, *dRiW, *dcub = nullptr;
-  int *darcs, *dzone;
+  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS, *dLiW, *dRiW, *dcub = nullptr, *dzpar;
+  int *darcs, *dzone, *dframe, *dzoff, *difz;
   if ((ce = upload(h, &dfaces, faces.data(), faces.size())) || (ce = upload(h, &dbfaces, bfaces.data(), bfaces.size())) ||
       (ce = upload(h, &dL, L.face.data(), L.face.size())) || (ce = upload(h, &dR, R.face.data(), R.face.size())) ||
       (ce = upload(h, &dLa, L.a.data(), L.a.size())) || (ce = upload(h, &dLw, L.w.data(), L.w.size())) ||
@@ -433,7 +482,9 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
       (ce = upload(h, &dRw, R.w.data(), R.w.size())) || (ce = upload(h, &dRS, R.S.data(), R.S.size())) ||
       (ce = upload(h, &dLiW, L.iw.data(), L.iw.size())) || (ce = upload(h, &dRiW, R.iw.data(), R.iw.size())) ||
       (ce = upload(h, &dcorn, corners.data(), corners.size())) || (ce = upload(h, &darcs, arcs.data(), arcs.size())) ||
-      (ce = upload(h, &dzone, m->elem_zone, (size_t)E)) ||
+      (ce = upload(h, &dzone, m->elem_zone, (size_t)E)) || (ce = upload(h, &dframe, frame.data(), frame.size())) ||
+      (ce = upload(h, &dzpar, zpar.data(), zpar.size())) || (ce = upload(h, &dzoff, zoff.data(), zoff.size())) ||
+      (ce = upload(h, &difz, ifz.data(), ifz.size())) ||
       (any_cubic && (ce = upload(h, &dcub, cubic.data(), cubic.size()))))
     return cuda_fail(h, ce, "mesh upload");
   md.cubic = dcub;
@@ -453,6 +504,11 @@ int build_mesh(sd_handle *h, const sd_mesh *m) {
   md.corners = dcorn;
   md.arcs = darcs;
   md.zone = dzone;
+  md.frame = dframe;
+  md.zpar = dzpar;
+  md.zoff = dzoff;
+  md.ifz = difz;
+  h->zpar = zpar;
   // (host vectors are released when this function returns: wait for the copies)
   if ((ce = cudaStreamSynchronize(h->stream))) return cuda_fail(h, ce, "mesh upload");
   return SD_OK;
@@ -472,10 +528,10 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   std::vector<int> eflag(Ep, 0), tab_elem;
   const bool otf = h->eng->metrics_on_the_fly();
   for (size_t k = 0; k < E; ++k) {
-    int f = zone[k] == 1 ? 1 : 0;
+    int f = zone[k];  // bits 0-2
     if (!otf || curved[k]) {
       tab_elem.push_back((int)k);
-      f |= (int)tab_elem.size() << 1;
+      f |= (int)tab_elem.size() << 3;
     }
     eflag[k] = f;
   }
@@ -513,6 +569,20 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   md.bxy = bxy;
   md.clk = clk;
   if ((e = cudaMemsetAsync(clk, 0, sizeof(DevClock), h->stream))) return e;
+  // the t = 0 clock: identity rotations, each zone's angular velocity
+  {
+    DevClock c0{};
+    for (int z = 0; z < kZT; ++z) {
+      c0.c[z] = 1.0;
+      c0.cf[z] = 1.0f;
+      c0.om[z] = h->zpar[4 * z + 2];
+      c0.omf[z] = (float)c0.om[z];
+    }
+    DevClock *dc0;
+    if ((e = upload(h, &dc0, &c0, 1))) return e;
+    if ((e = cudaStreamSynchronize(h->stream))) return e;  // c0 leaves scope
+    md.clk0 = dc0;
+  }
   // the stage records of a time step (see StageMerge)
   DevClock *sclk;
   if ((e = dalloc(h, &sclk, sizeof(DevClock) * kMaxStages))) return e;
@@ -722,8 +792,6 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
   h->E = m->n_elems;
   h->prm = *prm;
   h->precision = prm->precision;
-  h->center[0] = m->center[0];
-  h->center[1] = m->center[1];
   cudaError_t ce;
   if (prm->stream) {
     h->stream = (cudaStream_t)prm->stream;
@@ -738,7 +806,7 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
   int rc = SD_OK;
   HostBasis hb;
   if (!build_basis(N, hb)) rc = fail(h, SD_ERR_ARG, "singular mortar mass matrix");
-  if (!rc) rc = build_mesh(h, m);
+  if (!rc) rc = build_mesh(h, m, prm->omega);
   if (!rc) {
     h->eng = prm->precision == SD_PREC_FP64   ? make_engine_f64(N)
              : prm->precision == SD_PREC_FP32 ? make_engine_f32(N)
@@ -748,8 +816,6 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
   if (!rc && (ce = cudaMallocHost(&h->h_pinned, 64))) rc = cuda_fail(h, ce, "pinned buffer");
   if (!rc) {
     MeshDev &md = h->md;
-    md.omega = prm->omega;
-    md.omega_f = (float)prm->omega;
     md.gamma_f = (float)prm->gamma;
     md.gamma = prm->gamma;
     md.Rgas = prm->Rgas;
@@ -778,8 +844,6 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
       rc = fail(h, SD_ERR_ARG, "inlet / outlet faces need a free stream with rho_inf > 0 and p_inf > 0");
   }
   if (!rc) {
-    MeshDev &md = h->md;
-    md.r_interface = m->r_interface;
     if ((ce = alloc_buffers(h, h->zone_v, h->curved_v))) rc = cuda_fail(h, ce, "device buffers");
     if (!rc && prm->rk_stages == 5 && (ce = h->eng->alloc_rk54())) rc = cuda_fail(h, ce, "stage buffers");
   }
@@ -951,7 +1015,7 @@ int sd_sp_coords(sd_handle *h, double t, double *xy, int on_device) {
     e = cudaMalloc(&dst, bytes);
     if (e) return cuda_fail(h, e, "coordinate buffer");
   }
-  h->eng->sp_coords(h->md, t, h->center[0], h->center[1], dst, h->stream);
+  h->eng->sp_coords(h->md, t, dst, h->stream);
   e = cudaGetLastError();
   if (!e && !on_device) e = cudaMemcpyAsync(xy, dst, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (!e) e = cudaStreamSynchronize(h->stream);

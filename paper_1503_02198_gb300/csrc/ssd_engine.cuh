@@ -10,9 +10,10 @@
 // FP32 rate); the rotation angle, the mortar geometry and the mortar
 // projection weights stay FP64 in both paths (Sec. 3.2).
 //
-// Per step, once: k_clock_merge_stages, one CTA per stage (stage time t_k):
-//                   theta = omega t_k; merge of the rotated L node angles
-//                   with the R node angles -> mortars, (o, s) of each mortar
+// Per step, once: k_clock_merge_stages, one CTA per stage (stage time t_k)
+//                   and interface: theta_z = omega_z t_k of every rotating
+//                   zone; merge of the interface's rotated L node angles
+//                   with its R node angles -> mortars, (o, s) of each mortar
 //                   against its L and R face (Eq. xz), face ranges, into the
 //                   stage's own clock record and mortar table
 //                   (k_clock_merge: the same for one stage, e.g. a residual)
@@ -205,7 +206,7 @@ __global__ void k_geo(MeshDev md, const double *__restrict__ Xs, const double *_
   for (int k = 0; k < 8; ++k) c[k] = md.corners[(size_t)e * 8 + k];
   const double *cub = md.cubic ? md.cubic + (size_t)e * 16 : nullptr;
   const int arcs = md.arcs[e];
-  const double om = md.zone[e] == 1 ? md.omega : 0.0;
+  const double om = md.clk0->om[md.zone[e]];
   T *g = (T *)md.geo + (size_t)t * L::G;
   double m[6];
   for (int j = 0; j < N; ++j)
@@ -294,14 +295,16 @@ __global__ void k_bgeo(MeshDev md, const double *__restrict__ Xs, double *bxy) {
 
 // physical SP coordinates at time t, [E][N][N][2]
 template <int N>
-__global__ void k_spxy(MeshDev md, const double *__restrict__ Xs, double t, double cx, double cy, double *out) {
+__global__ void k_spxy(MeshDev md, const double *__restrict__ Xs, double t, double *out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= md.E) return;
   double c[8], m[6];
   for (int k = 0; k < 8; ++k) c[k] = md.corners[(size_t)e * 8 + k];
   const double *cub = md.cubic ? md.cubic + (size_t)e * 16 : nullptr;
+  const int z = md.zone[e], fz = md.frame[e];
+  const double cx = md.zpar[4 * fz], cy = md.zpar[4 * fz + 1];
   double cs = 1.0, sn = 0.0;
-  if (md.zone[e] == 1) sincos(md.omega * t, &sn, &cs);
+  if (z) sincos(md.zpar[4 * z + 2] * t, &sn, &cs);
   for (int j = 0; j < N; ++j)
     for (int i = 0; i < N; ++i) {
       cell_map(c, md.arcs[e], cub, Xs[i], Xs[j], m);
@@ -310,10 +313,18 @@ __global__ void k_spxy(MeshDev md, const double *__restrict__ Xs, double t, doub
     }
 }
 
-// Metrics of one element at the current rotation (Sec. 2.3): either its t = 0
-// table rotated by R(theta), or, for a straight cell on the on-the-fly path,
-// the bilinear map from its rotated record.  The grid-velocity coefficient
-// V_g . a is rotation invariant.
+// The zone table [3][kZT] of a clock record in the compute type: cos theta_z,
+// sin theta_z, omega_z of every zone (zone 0: 1, 0, 0).
+template <typename T>
+__device__ __forceinline__ const T *zone_tab(const DevClock *k) {
+  if constexpr (std::is_same<T, double>::value) return k->c;
+  else return k->cf;
+}
+
+// Metrics of one element at the current rotation of its zone (Sec. 2.3):
+// either its t = 0 table rotated by R(theta_z), or, for a straight cell on the
+// on-the-fly path, the bilinear map from its rotated record.  The
+// grid-velocity coefficient V_g . a is rotation invariant.
 template <typename T, int N, bool OTF>
 struct ElemGeo {
   using L = GeoLayout<N>;
@@ -321,16 +332,17 @@ struct ElemGeo {
   T c, s, om;
   T x0, y0, e1x, e1y, e3x, e3y, dx, dy;
 
-  __device__ __forceinline__ void load(const MeshDev &md, int e, T cth, T sth) {
-    load_rec(md, e, md.eflag[e], OTF ? (const T *)md.egeo + (size_t)e * 8 : nullptr, cth, sth);
+  // zt: a zone table (zone_tab of the stage's clock, or of the t = 0 clock)
+  __device__ __forceinline__ void load(const MeshDev &md, int e, const T *zt) {
+    load_rec(md, e, md.eflag[e], OTF ? (const T *)md.egeo + (size_t)e * 8 : nullptr, zt);
   }
   // the same with the flag and the bilinear record already at hand (e.g. in shared memory)
-  __device__ __forceinline__ void load_rec(const MeshDev &md, int e, int f, const T *r, T cth, T sth) {
-    const bool rot = f & 1;
-    c = rot ? cth : T(1);
-    s = rot ? sth : T(0);
-    om = rot ? pick<T>(md.omega, md.omega_f) : T(0);
-    const int ti = (f >> 1) - 1;
+  __device__ __forceinline__ void load_rec(const MeshDev &md, int e, int f, const T *r, const T *zt) {
+    const int z = f & 7;
+    c = zt[z];
+    s = zt[kZT + z];
+    om = zt[2 * kZT + z];
+    const int ti = (f >> 3) - 1;
     if (OTF && ti < 0) {
       tab = nullptr;
       const T v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4], v5 = r[5], v6 = r[6], v7 = r[7];
@@ -515,36 +527,48 @@ __device__ __forceinline__ double wrap_pi(double a) {
   return wrap_2pi(a + pi) - pi;
 }
 
-// Stage clock and mortar table (Sec. 3.2: connectivity updated at every
-// stage).  Mortar k is the interval between merged node positions k and k+1
-// (counter-clockwise, cyclic); nodes of both sides sorted by angle, L before R
-// on ties.  One CTA; the node angles are searched in shared memory (dynamic,
-// (nL + nR) doubles); work_i / work_d hold the merged positions and angles.
+// Stage clock and mortar table of interface ii (Sec. 3.2: connectivity
+// updated at every stage).  Its mortar k is the interval between merged node
+// positions k and k+1 (counter-clockwise, cyclic); nodes of both sides sorted
+// by angle, L before R on ties.  One CTA per interface; the node angles are
+// searched in shared memory (dynamic, (nL + nR) doubles of the interface);
+// work_i / work_d hold the merged positions and angles.  The CTA of interface
+// 0 also writes the stage clock of every zone: theta_z = omega_z t_stage.
 // The offsets and scales of Eq. xz are formed per mortar in k_mortar_flux.
 // The step's start time t_n is read from *tsrc; the stage clock and the table
 // are written through md.
-static __device__ void clock_merge_body(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
-                                        const DevClock *tsrc) {
+static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, double dt, int *work_i,
+                                        double *work_d, const DevClock *tsrc) {
   extern __shared__ double s_ang[];  // [nL] rotated L angles, then [nR] R angles
   __shared__ double s_th2;
   __shared__ int s_k0;
-  const int nL = md.nL, nR = md.nR, nb = nL + nR;
   const double tp = 6.283185307179586476925286766559;
-  if (threadIdx.x == 0) {
+  const double ts = tsrc->t_n + c * dt;
+  if (ii == 0 && threadIdx.x < kZT) {
     DevClock *k = md.clk;
-    const double ts = tsrc->t_n + c * dt;
-    const double th = md.omega * ts;
-    const double th2 = wrap_2pi(th);
-    k->t_stage = ts;
-    k->theta = th;
-    k->theta2 = th2;
-    double sn, cs;
-    sincos(th, &sn, &cs);
-    k->c = cs;
-    k->s = sn;
-    k->cf = (float)cs;
-    k->sf = (float)sn;
-    s_th2 = th2;
+    const int z = threadIdx.x;
+    const double om = z ? md.zpar[4 * z + 2] : 0.0;
+    double sn = 0.0, cs = 1.0, th2 = 0.0;
+    if (z) {
+      const double th = om * ts;
+      th2 = wrap_2pi(th);
+      sincos(th, &sn, &cs);
+    } else {
+      k->t_stage = ts;
+    }
+    k->theta2[z] = th2;
+    k->c[z] = cs;
+    k->s[z] = sn;
+    k->om[z] = om;
+    k->cf[z] = (float)cs;
+    k->sf[z] = (float)sn;
+    k->omf[z] = (float)om;
+  }
+  const int Lo = md.zoff[ii], Ro = md.zoff[kZT + ii];
+  const int nL = md.zoff[ii + 1] - Lo, nR = md.zoff[kZT + ii + 1] - Ro, nb = nL + nR;
+  const int Mo = Lo + Ro;
+  if (threadIdx.x == 0) {
+    s_th2 = wrap_2pi(md.zpar[4 * (ii + 1) + 2] * ts);
     s_k0 = 0;
   }
   __syncthreads();
@@ -552,10 +576,10 @@ static __device__ void clock_merge_body(const MeshDev &md, double c, double dt, 
   const double th2 = s_th2;
   double *sL = s_ang, *sR = s_ang + nL;
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
-    const double a = md.La[k] + th2;
+    const double a = md.La[Lo + k] + th2;
     sL[k] = a >= tp ? a - tp : a;
   }
-  for (int k = threadIdx.x; k < nR; k += blockDim.x) sR[k] = md.Ra[k];
+  for (int k = threadIdx.x; k < nR; k += blockDim.x) sR[k] = md.Ra[Ro + k];
   __syncthreads();
   // rotated L angles are a cyclic shift of an ascending list; k0 = index of the minimum
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
@@ -564,10 +588,10 @@ static __device__ void clock_merge_body(const MeshDev &md, double c, double dt, 
   }
   __syncthreads();
   const int k0 = s_k0;
-  double *mAng = work_d;          // [nb] merged angles
-  int *posL = work_i;             // [nL] merged position of L node k (t = 0 index)
-  int *posR = work_i + nL;        // [nR]
-  int *otherL = work_i + nb;      // [nL] R face containing the mortar that starts at L node k
+  double *mAng = work_d + Mo;     // [nb] merged angles
+  int *posL = work_i + 2 * Mo;    // [nL] merged position of L node k (t = 0 index)
+  int *posR = posL + nL;          // [nR]
+  int *otherL = posL + nb;        // [nL] R face containing the mortar that starts at L node k
   int *otherR = otherL + nL;      // [nR] L face containing the mortar that starts at R node k
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
     const double a = sL[k];
@@ -599,34 +623,35 @@ static __device__ void clock_merge_body(const MeshDev &md, double c, double dt, 
   __syncthreads();
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
     const int p = posL[k];
-    md.mLf[p] = k;
-    md.mRf[p] = otherL[k];
+    md.mLf[Mo + p] = Lo + k;
+    md.mRf[Mo + p] = Ro + otherL[k];
     const int cnt = (posL[k + 1 == nL ? 0 : k + 1] - p + nb) % nb;
-    md.Lstart[k] = p;
-    md.Lcount[k] = cnt == 0 ? nb : cnt;
+    md.Lstart[Lo + k] = Mo + p;
+    md.Lcount[Lo + k] = cnt == 0 ? nb : cnt;
   }
   for (int k = threadIdx.x; k < nR; k += blockDim.x) {
     const int p = posR[k];
-    md.mRf[p] = k;
-    md.mLf[p] = otherR[k];
+    md.mRf[Mo + p] = Ro + k;
+    md.mLf[Mo + p] = Lo + otherR[k];
     const int cnt = (posR[k + 1 == nR ? 0 : k + 1] - p + nb) % nb;
-    md.Rstart[k] = p;
-    md.Rcount[k] = cnt == 0 ? nb : cnt;
+    md.Rstart[Ro + k] = Mo + p;
+    md.Rcount[Ro + k] = cnt == 0 ? nb : cnt;
   }
   __syncthreads();
   for (int p = threadIdx.x; p < nb; p += blockDim.x) {
     const double a = mAng[p];
     const double b = p + 1 < nb ? mAng[p + 1] : mAng[0] + tp;
-    md.mgeo[2 * p] = a;
-    md.mgeo[2 * p + 1] = b - a;
+    md.mgeo[2 * (Mo + p)] = a;
+    md.mgeo[2 * (Mo + p) + 1] = b - a;
   }
 }
 
+// block (0, ii): interface ii of one stage
 static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_i, double *work_d) {
-  clock_merge_body(md, c, dt, work_i, work_d, md.clk);
+  clock_merge_body(md, blockIdx.y, c, dt, work_i, work_d, md.clk);
 }
 
-// block b: the clock and mortar table of stage b of a step
+// block (b, ii): the clock and interface ii's mortar table of stage b of a step
 static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt) {
   const int b = blockIdx.x;
   MeshDev m = md;
@@ -638,7 +663,7 @@ static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt
   m.Rstart = sm.Rstart[b];
   m.Rcount = sm.Rcount[b];
   m.mgeo = sm.mgeo[b];
-  clock_merge_body(m, sm.c[b], dt, sm.work_i[b], sm.work_d[b], md.clk);
+  clock_merge_body(m, blockIdx.y, sm.c[b], dt, sm.work_i[b], sm.work_d[b], md.clk);
 }
 
 // t = 0 geometry of every conforming / periodic face point (one thread per point)
@@ -650,8 +675,8 @@ __global__ void k_fgeo(MeshDev md) {
   const int4 fc = md.faces[fi];
   const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
   ElemGeo<T, N, OTF> GA, GB;
-  GA.load(md, efA >> 2, T(1), T(0));
-  GB.load(md, efB >> 2, T(1), T(0));
+  GA.load(md, efA >> 2, zone_tab<T>(md.clk0));
+  GB.load(md, efB >> 2, zone_tab<T>(md.clk0));
   T ax, ay, ag, bx, by, bg;
   GA.face(efA & 3, j, ax, ay, ag);
   GB.face(efB & 3, jB, bx, by, bg);
@@ -666,7 +691,8 @@ __global__ void k_fgeo(MeshDev md) {
 }
 
 // Conforming and periodic faces: one thread per face point; geometry from the
-// t = 0 face table, the normal turned by R(theta) on the rotating zone.
+// t = 0 face table, the normal turned by R(theta_z) on rotating zone z (both
+// sides of a conforming face lie in one zone).
 template <typename T, int N, bool OTF>
 __device__ __forceinline__ void k_face_point(const MeshDev &md, int t) {
   const int fi = t / N, j = t - fi * N;
@@ -682,8 +708,10 @@ __device__ __forceinline__ void k_face_point(const MeshDev &md, int t) {
   const T *g = (const T *)md.fgeo + (size_t)fi * 5 * N;
   T nx = g[j], ny = g[N + j];
   const T sA = g[2 * N + j], sB = g[3 * N + j], vgn = g[4 * N + j];
-  if (md.eflag[efA >> 2] & 1) {
-    const T c = pick<T>(md.clk->c, md.clk->cf), s = pick<T>(md.clk->s, md.clk->sf);
+  const int z = md.eflag[efA >> 2] & 7;
+  if (z) {
+    const T *zt = zone_tab<T>(md.clk);
+    const T c = zt[z], s = zt[kZT + z];
     const T rx = c * nx - s * ny, ry = s * nx + c * ny;
     nx = rx;
     ny = ry;
@@ -750,16 +778,18 @@ template <typename T, int N, bool OTF>
 __device__ __forceinline__ void bface_geom(const MeshDev &md, int b, int j, T &nx, T &ny, T &sS, T &vgn, T &ug,
                                            T &vg) {
   const int ef = md.bfaces[b].x, e = ef >> 2, f = ef & 3;
-  const double c = md.clk->c, s = md.clk->s;
   ElemGeo<T, N, OTF> G;
-  G.load(md, e, (T)c, (T)s);
+  G.load(md, e, zone_tab<T>(md.clk));
   T ax, ay, ag;
   G.face(f, j, ax, ay, ag);
   double uw = 0.0, vw = 0.0;
-  if (md.eflag[e] & 1) {
+  const int z = md.eflag[e] & 7;
+  if (z) {
+    // wall velocity omega_z x (R(theta_z) x0), x0 relative to the zone's centre
+    const double c = md.clk->c[z], s = md.clk->s[z], om = md.clk->om[z];
     const double x0 = md.bxy[((size_t)b * N + j) * 2], y0 = md.bxy[((size_t)b * N + j) * 2 + 1];
-    uw = -md.omega * (s * x0 + c * y0);
-    vw = md.omega * (c * x0 - s * y0);
+    uw = -om * (s * x0 + c * y0);
+    vw = om * (c * x0 - s * y0);
   }
   const T S = sqrt(ax * ax + ay * ay), sg = (T)face_sigma(f);
   nx = sg * ax / S;
@@ -843,7 +873,9 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
     dm = md.mgeo[2 * m + 1];
     const double tp = 6.283185307179586476925286766559, pi = 0.5 * tp;
     const int fq = sd ? md.mRf[m] : md.mLf[m];
-    double fa = sd ? md.Ra[fq] : md.La[fq] + md.clk->theta2;
+    // the L side turns with its zone (interface ifz[fq] belongs to zone ifz[fq] + 1)
+    const double th2 = sd ? 0.0 : md.clk->theta2[md.ifz[fq] + 1];
+    double fa = sd ? md.Ra[fq] : md.La[fq] + th2;
     if (fa >= tp) fa -= tp;
     double off = m0 - fa;
     if (off > pi) off -= tp;
@@ -865,7 +897,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
 #pragma unroll
       for (int c = 0; c < 8; ++c) g8[c] = GT[((size_t)ef * 8 + c) * N + jj];
       const double tp = 6.283185307179586476925286766559;
-      double fa = sd ? md.Ra[fq] : md.La[fq] + md.clk->theta2;
+      double fa = sd ? md.Ra[fq] : md.La[fq] + th2;
       if (fa >= tp) fa -= tp;
       double sn, cs;
       sincos(fa + B.Xs[p] * (sd ? md.Rw[fq] : md.Lw[fq]), &sn, &cs);
@@ -1004,12 +1036,15 @@ __global__ void k_mortar_gather(MeshDev md) {
   const int cnt = sd ? md.Rcount[k] : md.Lcount[k];
   const int4 fc = sd ? md.Rface[k] : md.Lface[k];
   const T *cb = (const T *)md.contrib + (size_t)sd * md.nM * 4 * N;
+  // the face's mortars run cyclically through its interface's mortar range [m0, m1)
+  const int ii = md.ifz[fq];
+  const int m0 = md.zoff[ii] + md.zoff[kZT + ii], m1 = md.zoff[ii + 1] + md.zoff[kZT + ii + 1];
   T acc[4] = {0, 0, 0, 0};
   int mi = start;
   for (int c = 0; c < cnt; ++c) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v] += cb[((size_t)mi * 4 + v) * N + p];
-    mi = mi + 1 == md.nM ? 0 : mi + 1;
+    mi = mi + 1 == m1 ? m0 : mi + 1;
   }
   const int ef = fc.x, f = ef & 3;
   const int j = fc.y ? N - 1 - p : p;
@@ -1163,7 +1198,9 @@ struct VolCfg {
   // work arrays
   static constexpr int O_RF = SINGLE_END, O_RG = O_RF + QHI;
   static constexpr int O_BAR = ((O_RG + QHI) + 15) / 16 * 16;
-  static constexpr int SMEM = O_BAR + 3 * 8;
+  // the stage's zone table [3][kZT] (cos theta_z, sin theta_z, omega_z)
+  static constexpr int O_ZT = O_BAR + 32;
+  static constexpr int SMEM = O_ZT + 3 * kZT * (int)sizeof(T);
   // transaction bytes of the two barriers' copies
   static constexpr int TX_QHI = EPB * QE, TX_CF = EPB * CE;
   static_assert((SE * (int)sizeof(T)) % 16 == 0 && (SC * (int)sizeof(T)) % 16 == 0, "bulk-copy alignment");
@@ -1214,7 +1251,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
   const bool use_base = MODE == MODE_RK && has_base;
   const uint32_t txA = C::TX_QHI + C::TX_CF + C::EGB + C::EFB;
   const uint32_t txB = MODE == MODE_RK ? C::QBL + (use_base ? C::QB + C::QBL : 0) + C::AUXB : 0;
-  const T cth = pick<T>(md.clk->c, md.clk->cf), sth = pick<T>(md.clk->s, md.clk->sf);
+  T *sZT = (T *)(smem + C::O_ZT);
   const T gm1 = pick<T>(md.gamma, md.gamma_f) - T(1);
 
   // copies are issued by the lanes of warp 0, one element each, into the
@@ -1250,6 +1287,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
     mbar_init(&bar[2], 1);
     fence_mbar_init();
   }
+  if (threadIdx.x < 3 * kZT) sZT[threadIdx.x] = zone_tab<T>(md.clk)[threadIdx.x];
   __syncthreads();
   int tile = blockIdx.x;
   if (threadIdx.x < 32 && tile < ntiles) issueA(tile, 0, threadIdx.x);
@@ -1288,7 +1326,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
     const int le = tl / N, mline = tl - le * N;
     if (le < ne) {
       ElemGeo<T, N, OTF> G;
-      G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, cth, sth);
+      G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, sZT);
       T mvx[N + 1], mvy[N + 1], mvg[N + 1];
       G.line_metrics(d, mline, mvx, mvy, mvg);
       if constexpr (FF) {
@@ -1662,7 +1700,7 @@ struct EngineImpl : Engine {
     const int nb = md.nL + md.nR;
     if ((err = cudaMalloc(&scratch_i, sizeof(int) * (2 * nb + 1)))) return err;
     if ((err = cudaMalloc(&scratch_d, sizeof(double) * (md.nL + nb + 1)))) return err;
-    merge_smem = (int)(sizeof(double) * (nb > 0 ? nb : 1));
+    merge_smem = (int)(sizeof(double) * (md.nbmax > 0 ? md.nbmax : 1));  // one interface's angles
     if (merge_smem > 48 * 1024) {
       if ((err = cudaFuncSetAttribute(k_clock_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, merge_smem)))
         return err;
@@ -1719,16 +1757,16 @@ struct EngineImpl : Engine {
   }
 
   void clock_merge(const MeshDev &md, double c, double dt, cudaStream_t s) override {
-    k_clock_merge<<<1, 1024, merge_smem, s>>>(md, c, dt, scratch_i, scratch_d);
+    k_clock_merge<<<dim3(1, md.nI), 1024, merge_smem, s>>>(md, c, dt, scratch_i, scratch_d);
   }
 
   void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                         cudaStream_t s) override {
-    k_clock_merge<<<1, 1024, merge_smem, s>>>(md, c, dt, work_i, work_d);
+    k_clock_merge<<<dim3(1, md.nI), 1024, merge_smem, s>>>(md, c, dt, work_i, work_d);
   }
 
   void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, cudaStream_t s) override {
-    k_clock_merge_stages<<<sm.n, 1024, merge_smem, s>>>(md, sm, dt);
+    k_clock_merge_stages<<<dim3(sm.n, md.nI), 1024, merge_smem, s>>>(md, sm, dt);
   }
 
   template <int MMODE, int GMODE>
@@ -1819,8 +1857,8 @@ struct EngineImpl : Engine {
 
   void advance(const MeshDev &md, double dt, cudaStream_t s) override { k_advance<<<1, 1, 0, s>>>(md.clk, dt); }
 
-  void sp_coords(const MeshDev &md, double t, double cx, double cy, double *xy, cudaStream_t s) override {
-    k_spxy<N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, t, cx, cy, xy);
+  void sp_coords(const MeshDev &md, double t, double *xy, cudaStream_t s) override {
+    k_spxy<N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, t, xy);
   }
 };
 

@@ -8,17 +8,23 @@
 namespace ssd {
 
 constexpr int kMaxN = 8;
+// rotating zones per mesh (zone 0 is the stationary zone; zone z >= 1 turns
+// rigidly about its own centre and has its own sliding interface)
+constexpr int kMaxZones = 4;
+constexpr int kZT = kMaxZones + 1;  // per-zone table entries, zone 0 included
 
-// Device-resident clock of the current stage (the rotation angle never
-// leaves FP64: theta = omega * t_stage, Sec. 2.2).
+// Device-resident clock of the current stage (the rotation angles never
+// leave FP64: theta_z = omega_z * t_stage, Sec. 2.2).  Per zone z: the
+// rotation R(theta_z) as (c, s) and the angular velocity om; zone 0 holds
+// (1, 0, 0).  c, s, om follow each other so that c points at the zone table
+// [3][kZT] a kernel reads (likewise cf, sf, omf on the FP32 path).
 struct DevClock {
-  double t_n;      // time at the start of the step
-  double t_stage;  // time of the stage being evaluated
-  double theta;    // omega * t_stage
-  double theta2;   // theta reduced to [0, 2 pi)
-  double c, s;     // cos(theta), sin(theta)
-  float cf, sf;    // the same rounded to float (FP32 path)
-  int flags;       // bit 0: non-physical state; bit 1: mesh geometry error; bit 2: a bounded device wait gave up
+  double t_n;           // time at the start of the step
+  double t_stage;       // time of the stage being evaluated
+  double theta2[kZT];   // theta_z reduced to [0, 2 pi)
+  double c[kZT], s[kZT], om[kZT];
+  float cf[kZT], sf[kZT], omf[kZT];
+  int flags;  // bit 0: non-physical state; bit 1: mesh geometry error; bit 2: a bounded device wait gave up
   int pad;
 };
 
@@ -55,9 +61,16 @@ struct MeshDev {
   int nB;
   const int4 *bfaces;
   const double *bxy;
-  // sliding interface, both sides sorted counter-clockwise at t = 0:
-  // (ef, reversed, 0, 0), CCW start angle, angular width, |S| = r * width
+  // sliding interfaces, both sides of each sorted counter-clockwise at t = 0
+  // about its zone's centre: (ef, reversed, 0, 0), CCW start angle, angular
+  // width, |S| = r * width.  The lists of all interfaces are concatenated:
+  // interface i (of zone i + 1) owns L faces [zoff[i], zoff[i + 1]), R faces
+  // [zoff[kZT + i], zoff[kZT + i + 1]) and mortars [zoff[i] + zoff[kZT + i], ...)
   int nL, nR, nM;
+  int nI;                   // interfaces (rotating zones) of the mesh, at least 1
+  int nbmax;                // the largest nL + nR of one interface
+  const int *zoff;          // [2][kZT] prefix sums of the L and R list lengths
+  const int *ifz;           // [nL + nR] interface of each L, then R, face
   const int4 *Lface, *Rface;
   const double *La, *Lw, *LS, *Ra, *Rw, *RS;
   const double *LiW, *RiW;  // 1 / angular width
@@ -68,13 +81,17 @@ struct MeshDev {
   int *Rstart, *Rcount; // [nR]
   void *contrib;        // T [2][nM][4][N] back-projected mortar fluxes
   // elements
-  const double *corners;  // [E][8] t = 0 corner coordinates relative to the centre
+  // each cell's coordinates are relative to the centre of its frame zone:
+  // its own zone if rotating, else the zone its arc edges are drawn about
+  const double *corners;  // [E][8] t = 0 corner coordinates relative to the frame centre
   const int *arcs;        // [E] bit f: local face f is an arc; bit 4 + f: it is a cubic
   const double *cubic;    // [E][4][4] edge nodes (x, y at 1/3, x, y at 2/3) of cubic
                           // edges, centre relative; null when the mesh has none
   const int *zone;        // [E]
-  // eflag[e]: bit 0 = rotating zone; (table index + 1) << 1, or 0 for a
-  // straight cell whose bilinear metrics are computed on the fly
+  const int *frame;       // [E] frame zone
+  const double *zpar;     // [kZT][4] per zone: centre x, y, omega, interface radius
+  // eflag[e]: bits 0-2 = zone; (table index + 1) << 3, or 0 for a straight
+  // cell whose bilinear metrics are computed on the fly
   const int *eflag;
   int nTab;               // number of metric tables
   const int *tab_elem;    // [nTab] element of each table
@@ -86,7 +103,8 @@ struct MeshDev {
   void *fgeo;             // T [nF][5][N] conforming-face geometry at t = 0: unit normal
                           // (x, y) out of side A, sigma_A |S_A|, sigma_B |S_B|, V_g . n
   DevClock *clk;
-  double omega, gamma, Rgas, mu, prandtl, T_wall, r_interface;
+  const DevClock *clk0;   // t = 0: the identity rotation with each zone's omega
+  double gamma, Rgas, mu, prandtl, T_wall;
   double rho_inf, u_inf, v_inf, p_inf;  // free stream (inlet state, outlet pressure)
   // derived constants, computed once on the host in double, with float copies
   // for the FP32 kernels (no double arithmetic or conversion per point there):
@@ -94,15 +112,15 @@ struct MeshDev {
   double gm1, kc, RTw;
   float gm1_f, Rgas_f, mu_f, kc_f, RTw_f, rho_inf_f, u_inf_f, v_inf_f, p_inf_f;
   int any_farfield;                     // the mesh has inlet or outlet faces
-  float omega_f, gamma_f;  // the same rounded to float (FP32 path)
+  float gamma_f;  // the same rounded to float (FP32 path)
   int viscous;
 };
 
 enum { MODE_RESIDUAL = 0, MODE_RK = 1 };
 
 // Stage clocks and mortar tables of every stage of one time step, filled by
-// one merge launch at the start of the step (one block per stage; the stage
-// times t_n + c_k dt are known there).  Each stage's kernels then see a
+// one merge launch at the start of the step (one block per stage and
+// interface; the stage times t_n + c_k dt are known there).  Each stage's kernels then see a
 // MeshDev whose clock and mortar-table pointers are that stage's.
 constexpr int kMaxStages = 5;
 struct StageMerge {
@@ -177,7 +195,7 @@ struct Engine {
   virtual StatePtr C() const = 0;
   virtual void *W() const = 0;
   virtual void advance(const MeshDev &md, double dt, cudaStream_t s) = 0;
-  virtual void sp_coords(const MeshDev &md, double t, double cx, double cy, double *xy, cudaStream_t s) = 0;
+  virtual void sp_coords(const MeshDev &md, double t, double *xy, cudaStream_t s) = 0;
 };
 
 Engine *make_engine_f64(int N);

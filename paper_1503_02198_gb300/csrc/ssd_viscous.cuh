@@ -118,8 +118,8 @@ struct VisCfg {
 // return sDx / sDe hold Q_x / Q_y.  The caller synchronises before and after.
 template <typename T, int N, bool OTF>
 __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne, T (*sQ)[4][N * N],
-                                               T (*sCQ)[16 * N], T (*sDx)[4][N * N], T (*sDe)[4][N * N], T cth,
-                                               T sth) {
+                                               T (*sCQ)[16 * N], T (*sDx)[4][N * N], T (*sDe)[4][N * N],
+                                               const T *zt) {
   constexpr int NN = N * N, NT = VisCfg<T, N>::THREADS;
   const VolBasis<T, N> &B = cVB<T, N>;
   const int le = threadIdx.x / (2 * N);
@@ -152,7 +152,7 @@ __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne
   for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
     const int l2 = idx / NN, sp = idx - l2 * NN;
     ElemGeo<T, N, OTF> G;
-    G.load(md, e0 + l2, cth, sth);
+    G.load(md, e0 + l2, zt);
     T xix, xiy, etx, ety;
     G.sp_grad(sp % N, sp / N, xix, xiy, etx, ety);
 #pragma unroll
@@ -177,8 +177,7 @@ __global__ void __launch_bounds__(VisCfg<T, N>::THREADS) k_grad_trace(MeshDev md
   for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) (&sQ[0][0][0])[i] = Q[(size_t)e0 * 4 * NN + i];
   for (int i = threadIdx.x; i < ne * 16 * N; i += NT) (&sCQ[0][0])[i] = ((const T *)md.CQ)[(size_t)e0 * 16 * N + i];
   __syncthreads();
-  tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, pick<T>(md.clk->c, md.clk->cf),
-                            pick<T>(md.clk->s, md.clk->sf));
+  tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, zone_tab<T>(md.clk));
   __syncthreads();
   // the SP gradients for the volume kernel of this stage
   for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) {
@@ -244,8 +243,10 @@ __device__ __forceinline__ void k_face_visc_point(const MeshDev &md, int t) {
   const T *g = (const T *)md.fgeo + (size_t)fi * 5 * N;
   T nx = g[j], ny = g[N + j];
   const T sA = g[2 * N + j], sB = g[3 * N + j], vgn = g[4 * N + j];
-  if (md.eflag[efA >> 2] & 1) {
-    const T c = pick<T>(md.clk->c, md.clk->cf), s = pick<T>(md.clk->s, md.clk->sf);
+  const int z = md.eflag[efA >> 2] & 7;
+  if (z) {
+    const T *zt = zone_tab<T>(md.clk);
+    const T c = zt[z], s = zt[kZT + z];
     const T rx = c * nx - s * ny, ry = s * nx + c * ny;
     nx = rx;
     ny = ry;
@@ -323,14 +324,14 @@ __global__ void __launch_bounds__(VisCfg<T, N>::THREADS, VisCfg<T, N>::MINB)
   }
   for (int i = threadIdx.x; i < ne * 16 * N; i += NT) (&sCF[0][0])[i] = ((const T *)md.CF)[(size_t)e0 * 16 * N + i];
   __syncthreads();
-  const T cth = pick<T>(md.clk->c, md.clk->cf), sth = pick<T>(md.clk->s, md.clk->sf);
+  const T *zt = zone_tab<T>(md.clk);
   const T gm1 = pick<T>(md.gm1, md.gm1_f);
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
   const int d = r / N, m = r - d * N;
   if (le < ne) {
     ElemGeo<T, N, OTF> G;
-    G.load(md, e0 + le, cth, sth);
+    G.load(md, e0 + le, zt);
     T acc[4][N];
 #pragma unroll
     for (int k = 0; k < N; ++k)
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(VisCfg<T, N>::THREADS, VisCfg<T, N>::MINB)
   for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
     const int l2 = idx / NN, sp = idx - l2 * NN;
     ElemGeo<T, N, OTF> G;
-    G.load(md, e0 + l2, cth, sth);
+    G.load(md, e0 + l2, zt);
     const T iJ = G.inv_jac(sp % N, sp / N);
     const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
     if (MODE == MODE_RESIDUAL) {

@@ -387,55 +387,68 @@ def rotor_mesh(half_width=10.0, n_cart=64, n_hole=24, r_interface=3.0, n_core=24
     return _finish(mb, [], pf, ifL, ifR, r_interface)
 
 
-def twin_rotor_mesh(half_width=10.0, n_cart=64, n_hole=24, r_interface=3.0, n_core=24,
-                    core_half=1.5, n_ring_in=16, n_ring_out=4, omega2=-math.pi / 4,
-                    shift_L=0.0, shift_R=0.0, n_core2=None) -> dict:
-    """Two rotating disks in one periodic box (several rotating zones, each
-    with its own sliding interface; Sec. 3.2 applied per interface).
+def rotor_row_mesh(n_rotors=2, half_width=10.0, n_cart=64, n_hole=24, r_interface=3.0, n_core=24,
+                   core_half=1.5, n_ring_in=16, n_ring_out=4, omegas=(-math.pi / 4,),
+                   shift_L=0.0, shift_R=0.0, n_cores=None) -> dict:
+    """A row of rotating disks in one periodic box (several rotating zones,
+    each with its own sliding interface; Sec. 3.2 applied per interface).
 
-    The box [-2w, 2w] x [-w, w] is a 2 n_cart x n_cart Cartesian grid of
-    spacing h = 2w/n_cart, periodic in x and y, with two square holes of
-    n_hole x n_hole cells centred at (-w, 0) and (w, 0).  Each hole holds the
-    disk and the stationary O-ring of ``rotor_mesh``: zone 1 about (-w, 0)
-    (its angular velocity is the flow parameter omega) and zone 2 about
-    (w, 0) with angular velocity ``omega2``.  Disk 2 has 4 n_core2 interface
-    faces (default n_core); with n_core2 = n_core the mesh is symmetric under
-    the half turn about the origin.  The stationary ring cells about disk 2
-    draw their arcs about its centre (``elem_arc_zone`` = 2).
+    The box [-n w, n w] x [-w, w] (n = n_rotors) is an n n_cart x n_cart
+    Cartesian grid of spacing h = 2w/n_cart, periodic in x and y, with n
+    square holes of n_hole x n_hole cells centred at (-n w + (2k + 1) w, 0).
+    Each hole holds the disk and the stationary O-ring of ``rotor_mesh``:
+    zone k + 1 about the k-th centre.  Zone 1's angular velocity is the flow
+    parameter omega; zones 2 .. n turn at ``omegas``.  Disk k has
+    4 n_cores[k] interface faces (default n_core for all).  The stationary
+    ring cells about disk k draw their arcs about its centre
+    (``elem_arc_zone`` = k + 1).
     """
-    n_core2 = n_core if n_core2 is None else n_core2
+    n = n_rotors
+    cores = [n_core] * n if n_cores is None else list(n_cores)
+    if len(omegas) != n - 1 or len(cores) != n:
+        raise ValueError("need n_rotors - 1 angular velocities and n_rotors core sizes")
     h = 2.0 * half_width / n_cart
     b = n_hole * h / 2.0
     if n_hole % 2 or n_cart % 2 or (n_cart - n_hole) % 2:
         raise ValueError("n_cart, n_hole and n_cart - n_hole must be even")
     if not (core_half * math.sqrt(2) < r_interface < b):
         raise ValueError("need core square inside the circle inside the hole")
-    c1, c2 = (-half_width, 0.0), (half_width, 0.0)
-    mb = _MeshBuilder(c1)
-    t1 = mb.node_table()
-    cells1, loopL1 = _rotor_disk(mb, t1, 1, c1, core_half, n_core, r_interface, n_ring_in,
-                                 -0.75 * math.pi + shift_L)
-    t2 = mb.node_table()
-    cells2, loopL2 = _rotor_disk(mb, t2, 2, c2, core_half, n_core2, r_interface, n_ring_in,
-                                 -0.75 * math.pi + shift_L)
+    centres = [(-n * half_width + (2 * k + 1) * half_width, 0.0) for k in range(n)]
+    mb = _MeshBuilder(centres[0])
+    disks = []
+    for k in range(n):
+        t = mb.node_table()
+        disks.append(_rotor_disk(mb, t, k + 1, centres[k], core_half, cores[k], r_interface, n_ring_in,
+                                 -0.75 * math.pi + shift_L))
     tout = mb.node_table()
-    out1, loopR1 = _hole_ring(mb, tout, c1, r_interface, 4 * n_hole, b, n_hole, n_ring_out,
-                              -0.75 * math.pi + shift_R)
-    first2 = len(mb.cells)
-    out2, loopR2 = _hole_ring(mb, tout, c2, r_interface, 4 * n_hole, b, n_hole, n_ring_out,
-                              -0.75 * math.pi + shift_R)
-    arc_zone = np.array([z if z else 1 for z in mb.zone_of], dtype=np.int32)
-    arc_zone[first2:len(mb.cells)] = 2
+    arc_zone = [z if z else 1 for z in mb.zone_of]
+    rings = []
+    for k in range(n):
+        first = len(mb.cells)
+        rings.append(_hole_ring(mb, tout, centres[k], r_interface, 4 * n_hole, b, n_hole, n_ring_out,
+                                -0.75 * math.pi + shift_R))
+        arc_zone += [k + 1] * (len(mb.cells) - first)
     lo = n_cart // 2 - n_hole // 2
-    pf = _cartesian_with_holes(mb, tout, -2.0 * half_width, -half_width, h, 2 * n_cart, n_cart,
-                               [(lo, lo + n_hole, lo, lo + n_hole),
-                                (lo + n_cart, lo + n_cart + n_hole, lo, lo + n_hole)])
-    arc_zone = np.concatenate([arc_zone, np.ones(len(mb.cells) - len(arc_zone), dtype=np.int32)])
-    zone2 = {"center": c2, "r_interface": r_interface, "omega": omega2,
-             "ifaces_L": _interface_faces(mb, cells2, loopL2),
-             "ifaces_R": _interface_faces(mb, out2, loopR2)}
-    return _finish(mb, [], pf, _interface_faces(mb, cells1, loopL1), _interface_faces(mb, out1, loopR1),
-                   r_interface, zones=[zone2], arc_zone=arc_zone)
+    pf = _cartesian_with_holes(mb, tout, -n * half_width, -half_width, h, n * n_cart, n_cart,
+                               [(lo + k * n_cart, lo + k * n_cart + n_hole, lo, lo + n_hole) for k in range(n)])
+    arc_zone += [1] * (len(mb.cells) - len(arc_zone))
+    faces = [(_interface_faces(mb, disks[k][0], disks[k][1]), _interface_faces(mb, rings[k][0], rings[k][1]))
+             for k in range(n)]
+    zones = [{"center": centres[k], "r_interface": r_interface, "omega": omegas[k - 1],
+              "ifaces_L": faces[k][0], "ifaces_R": faces[k][1]} for k in range(1, n)]
+    return _finish(mb, [], pf, faces[0][0], faces[0][1], r_interface, zones=zones, arc_zone=arc_zone)
+
+
+def twin_rotor_mesh(half_width=10.0, n_cart=64, n_hole=24, r_interface=3.0, n_core=24,
+                    core_half=1.5, n_ring_in=16, n_ring_out=4, omega2=-math.pi / 4,
+                    shift_L=0.0, shift_R=0.0, n_core2=None) -> dict:
+    """Two disks (``rotor_row_mesh`` with n_rotors = 2) about (-w, 0) and
+    (w, 0); zone 2 turns at ``omega2`` and has 4 n_core2 interface faces
+    (default n_core).  With n_core2 = n_core the mesh is symmetric under the
+    half turn about the origin."""
+    return rotor_row_mesh(2, half_width, n_cart, n_hole, r_interface, n_core, core_half, n_ring_in,
+                          n_ring_out, (omega2,), shift_L, shift_R,
+                          None if n_core2 is None else (n_core, n_core2))
 
 
 def periodic_box_mesh(n=4, half_width=1.0, rotating=False) -> dict:

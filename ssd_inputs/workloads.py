@@ -83,6 +83,17 @@ def _rotor_large(N=6):
     return mesh, prm, dt
 
 
+def _twin_rotor(N=6):
+    # [-20,20] x [-10,10], h = 0.08, two disks r = 2 about (-10, 0) and (10, 0)
+    # turning in opposite senses: 123,450 quads
+    mesh = meshes.twin_rotor_mesh(half_width=10.0, n_cart=250, n_hole=60, r_interface=2.0, n_core=25,
+                                  core_half=1.0, n_ring_in=10, n_ring_out=5, omega2=-0.5)
+    prm = FlowParams(gamma=1.4, Rgas=1.0, omega=0.5, viscous=0)
+    h = 0.04
+    dt = 0.1 * h / ((1.0 + math.sqrt(1.4) + 2.0) * N * N)
+    return mesh, prm, dt
+
+
 def ellipse_params(omega=0.3, mach=0.2, re=1000.0):
     """Free stream rho = U = T = 1 along +x at Mach M: p_inf = R = 1/(gamma M^2);
     mu from Re on the major axis (length 1); isothermal body at T = 1."""
@@ -150,10 +161,16 @@ def build_workload(name: str) -> Workload:
         mesh, prm, dt = _rotor_large(6)
         return Workload(name, "vortex through rotor: periodic [-20,20]^2, rotating disk r<=4, "
                         "about 247k quads, N=6 (p=5), Euler", mesh, 6, prm, dt, 100)
+    if name == "twin_rotor_n6":
+        mesh, prm, dt = _twin_rotor(6)
+        return Workload(name, "vortex between two counter-rotating rotors (two rotating zones, two "
+                        "sliding interfaces): periodic [-20,20]x[-10,10], disks r<=2 about (-10,0) at "
+                        "omega=0.5 and (10,0) at omega=-0.5, 123,450 quads, N=6 (p=5), Euler", mesh, 6,
+                        prm, dt, 100)
     raise KeyError(name)
 
 
-WORKLOADS = ("couette_n3", "vortex_n4", "vortex_n5", "ellipse_n5", "tank_n4", "rotor_n6")
+WORKLOADS = ("couette_n3", "vortex_n4", "vortex_n5", "ellipse_n5", "tank_n4", "rotor_n6", "twin_rotor_n6")
 
 
 def min_edge(mesh) -> float:

@@ -20,6 +20,20 @@ def small_rotor(scale=1, shift_L=0.0, shift_R=0.0, n_hole=6, n_core=4):
                              n_ring_out=2 * scale, shift_L=shift_L, shift_R=shift_R)
 
 
+def small_twin(omega2=-0.45, n_core2=None, shift_L=0.0, shift_R=0.0):
+    """Two rotating disks in a periodic 12 x 6 box (384 cells)."""
+    return meshes.twin_rotor_mesh(half_width=3.0, n_cart=12, n_hole=8, r_interface=1.5, n_core=4,
+                                  core_half=0.6, n_ring_in=2, n_ring_out=2, omega2=omega2,
+                                  shift_L=shift_L, shift_R=shift_R, n_core2=n_core2)
+
+
+def small_row(n_rotors, omegas, shift_L=0.0, n_cores=None):
+    """A row of n_rotors small disks (zones 1 .. n_rotors)."""
+    return meshes.rotor_row_mesh(n_rotors, half_width=3.0, n_cart=12, n_hole=8, r_interface=1.5, n_core=4,
+                                 core_half=0.6, n_ring_in=2, n_ring_out=2, omegas=omegas, shift_L=shift_L,
+                                 n_cores=n_cores)
+
+
 def face_kinds(mesh):
     """Per element: True if the cell has a curved edge or a non-conforming face."""
     E = len(mesh["elem_nodes"])

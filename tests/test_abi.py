@@ -53,3 +53,30 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(pkg, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError):
         pkg.lib()
+
+
+def test_ctypes_layouts_match_the_header(tmp_path):
+    # sizes and field offsets of the public structs, as gcc lays out include/ssd.h
+    import subprocess
+
+    import paper_1503_02198_gb300 as pkg
+    structs = {"sd_mesh": pkg.sd_mesh, "sd_zone": pkg.sd_zone, "sd_params": pkg.sd_params}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ssd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+    assert pkg.SD_MAX_ZONES == 4

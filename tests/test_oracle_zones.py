@@ -8,21 +8,13 @@ conservation through both interfaces, the half-turn symmetry of a symmetric
 two-disk mesh, and a frozen aligned zone equal to the same cells joined
 conformingly.
 """
-import math
-
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
 
-from helpers import face_kinds, neighbours_of, sp_weights
+from helpers import face_kinds, neighbours_of, small_row, small_twin, sp_weights
 from ssd_inputs import fields, meshes
 from ssd_inputs.workloads import FlowParams
-
-
-def small_twin(omega2=-0.45, n_core2=None, shift_L=0.0, shift_R=0.0):
-    return meshes.twin_rotor_mesh(half_width=3.0, n_cart=12, n_hole=8, r_interface=1.5, n_core=4,
-                                  core_half=0.6, n_ring_in=2, n_ring_out=2, omega2=omega2,
-                                  shift_L=shift_L, shift_R=shift_R, n_core2=n_core2)
 
 
 def test_twin_mesh_tables(oracle_mod):
@@ -189,3 +181,21 @@ def test_frozen_aligned_zone_equals_conforming_cells(oracle_mod):
         Q = oa.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=3, amp=0.2, scale=2.0))
         ra, rb = oa.residual(Q, 0.21), ob.residual(Q, 0.21)
         assert np.abs(ra - rb).max() < 5e-11 * np.abs(rb).max()
+
+
+def test_four_zones_conserve_and_a_fifth_is_rejected(oracle_mod):
+    # the most rotating zones a mesh may have, each at its own rate and with
+    # its own number of interface faces
+    m = small_row(4, (-0.6, 0.3, 1.1), shift_L=0.1, n_cores=(4, 3, 5, 2))
+    o = oracle_mod.Oracle(m, 3, FlowParams(omega=0.9))
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=2, amp=0.2, scale=3.0))
+    R = o.residual(Q, 0.41)
+    J = o.sp_jacobian()
+    w = sp_weights(oracle_mod, 3)
+    total = np.einsum("evji,eji,j,i->v", R, J, w, w)
+    scale = np.einsum("evji,eji,j,i->v", np.abs(R), J, w, w)
+    assert (np.abs(total) < 1e-13 * scale).all(), total / scale
+    for zone in (1, 2, 3, 4):
+        assert len(o.mortars(0.41, zone)["lf"]) > 0
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle(small_row(5, (-0.6, 0.3, 1.1, 0.2)), 3, FlowParams(omega=0.9))
