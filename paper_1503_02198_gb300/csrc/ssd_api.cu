@@ -528,10 +528,10 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   std::vector<int> eflag(Ep, 0), tab_elem;
   const bool otf = h->eng->metrics_on_the_fly();
   for (size_t k = 0; k < E; ++k) {
-    int f = zone[k];  // bits 0-2
+    int f = zone[k];
     if (!otf || curved[k]) {
       tab_elem.push_back((int)k);
-      f |= (int)tab_elem.size() << 3;
+      f |= (int)tab_elem.size() << kZoneBits;
     }
     eflag[k] = f;
   }

@@ -338,11 +338,11 @@ struct ElemGeo {
   }
   // the same with the flag and the bilinear record already at hand (e.g. in shared memory)
   __device__ __forceinline__ void load_rec(const MeshDev &md, int e, int f, const T *r, const T *zt) {
-    const int z = f & 7;
+    const int z = f & kZoneMask;
     c = zt[z];
     s = zt[kZT + z];
     om = zt[2 * kZT + z];
-    const int ti = (f >> 3) - 1;
+    const int ti = (f >> kZoneBits) - 1;
     if (OTF && ti < 0) {
       tab = nullptr;
       const T v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4], v5 = r[5], v6 = r[6], v7 = r[7];
@@ -446,7 +446,7 @@ struct ElemGeo {
   // 1 / |J| at SP (X_i, X_j) straight from the cell flag and the unrotated
   // record or table (|J| does not change under the rotation)
   static __device__ __forceinline__ T inv_jac_t0(const MeshDev &md, int f, const T *r, int i, int j) {
-    const int ti = (f >> 1) - 1;
+    const int ti = (f >> kZoneBits) - 1;
     if (OTF && ti < 0) {
       const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
       const T xx = r[2] + eta * r[6], yx = r[3] + eta * r[7], xe = r[4] + xi * r[6], ye = r[5] + xi * r[7];
@@ -708,7 +708,7 @@ __device__ __forceinline__ void k_face_point(const MeshDev &md, int t) {
   const T *g = (const T *)md.fgeo + (size_t)fi * 5 * N;
   T nx = g[j], ny = g[N + j];
   const T sA = g[2 * N + j], sB = g[3 * N + j], vgn = g[4 * N + j];
-  const int z = md.eflag[efA >> 2] & 7;
+  const int z = md.eflag[efA >> 2] & kZoneMask;
   if (z) {
     const T *zt = zone_tab<T>(md.clk);
     const T c = zt[z], s = zt[kZT + z];
@@ -783,7 +783,7 @@ __device__ __forceinline__ void bface_geom(const MeshDev &md, int b, int j, T &n
   T ax, ay, ag;
   G.face(f, j, ax, ay, ag);
   double uw = 0.0, vw = 0.0;
-  const int z = md.eflag[e] & 7;
+  const int z = md.eflag[e] & kZoneMask;
   if (z) {
     // wall velocity omega_z x (R(theta_z) x0), x0 relative to the zone's centre
     const double c = md.clk->c[z], s = md.clk->s[z], om = md.clk->om[z];

@@ -12,6 +12,9 @@ constexpr int kMaxN = 8;
 // rigidly about its own centre and has its own sliding interface)
 constexpr int kMaxZones = 4;
 constexpr int kZT = kMaxZones + 1;  // per-zone table entries, zone 0 included
+// cell flag: zone in the low kZoneBits bits, (metric table index + 1) above
+constexpr int kZoneBits = 3, kZoneMask = (1 << kZoneBits) - 1;
+static_assert(kMaxZones <= kZoneMask, "zone bits");
 
 // Device-resident clock of the current stage (the rotation angles never
 // leave FP64: theta_z = omega_z * t_stage, Sec. 2.2).  Per zone z: the
@@ -90,8 +93,8 @@ struct MeshDev {
   const int *zone;        // [E]
   const int *frame;       // [E] frame zone
   const double *zpar;     // [kZT][4] per zone: centre x, y, omega, interface radius
-  // eflag[e]: bits 0-2 = zone; (table index + 1) << 3, or 0 for a straight
-  // cell whose bilinear metrics are computed on the fly
+  // eflag[e]: bits 0-2 = zone; (table index + 1) << kZoneBits, or 0 above
+  // them for a straight cell whose bilinear metrics are computed on the fly
   const int *eflag;
   int nTab;               // number of metric tables
   const int *tab_elem;    // [nTab] element of each table

@@ -243,7 +243,7 @@ __device__ __forceinline__ void k_face_visc_point(const MeshDev &md, int t) {
   const T *g = (const T *)md.fgeo + (size_t)fi * 5 * N;
   T nx = g[j], ny = g[N + j];
   const T sA = g[2 * N + j], sB = g[3 * N + j], vgn = g[4 * N + j];
-  const int z = md.eflag[efA >> 2] & 7;
+  const int z = md.eflag[efA >> 2] & kZoneMask;
   if (z) {
     const T *zt = zone_tab<T>(md.clk);
     const T c = zt[z], s = zt[kZT + z];
