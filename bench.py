@@ -100,8 +100,8 @@ class ClockSampler:
 # profiles/k_volume_fp32_rotor_n6.md; valid only for the kernel source it was
 # taken on: SHA-256 of the engine text that k_volume is built from (the
 # ElemGeo metrics and VolCfg through the end of k_volume); otherwise null.
-PROFILED_TRAFFIC = {"bytes": (389.07e6 + 328.85e6 + 673.48e6 + 331.02e6 + 673.47e6 + 329.73e6) / 3,
-                    "kernel_sha256": "ae1f4e35b72381ac79256414963982e9a4c2a4fc8690384eead960d67f90039a"}
+PROFILED_TRAFFIC = {"bytes": (389.03e6 + 328.56e6 + 673.56e6 + 330.71e6 + 673.44e6 + 329.70e6) / 3,
+                    "kernel_sha256": "71e036ac8769dccb98705d7bdc53c1504e3b2a235021e5aa42949adb92c03851"}
 
 
 def volume_kernel_source():
@@ -376,6 +376,14 @@ def run_tank(ssd, stream, steps, warmup):
     return run_config(ssd, stream, "tank_n4", steps, warmup, rest, "uniform fluid at rest (Sec. 4)")
 
 
+def run_twin(ssd, stream, steps, warmup):
+    """Two counter-rotating rotors (123,450 cells, N = 6, Euler; two rotating
+    zones, each with its own sliding interface) with the strength-5 vortex
+    between them."""
+    return run_config(ssd, stream, "twin_rotor_n6", steps, warmup, lambda x, y: fields.isentropic_vortex(x, y),
+                      "strength-5 vortex at the origin, between the two disks")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,6 +401,7 @@ def main():
     ap.add_argument("--ellipse-steps", type=int, default=200)
     ap.add_argument("--tank-steps", type=int, default=200)
     ap.add_argument("--couette-steps", type=int, default=200)
+    ap.add_argument("--twin-steps", type=int, default=200)
     ap.add_argument("--fp32s-steps", type=int, default=-1, help="FP32-state leg steps (-1: same as --steps)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -559,6 +568,7 @@ def main():
     ellipse = run_ellipse(ssd, stream, args.ellipse_steps, 5) if args.ellipse_steps > 0 else None
     tank = run_tank(ssd, stream, args.tank_steps, 5) if args.tank_steps > 0 else None
     couette = run_couette(ssd, stream, args.couette_steps, 5) if args.couette_steps > 0 else None
+    twin = run_twin(ssd, stream, args.twin_steps, 5) if args.twin_steps > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -583,6 +593,7 @@ def main():
             "ellipse": ellipse,
             "tank": tank,
             "couette": couette,
+            "twin_rotor": twin,
             "kernel_ms": prof,
             "interface_fraction": prof["mortar"] * 3 / prof["step"],
             "fp32_fma_peak_tflops": fp32_peak,
