@@ -44,6 +44,34 @@
 
 namespace ssd {
 
+// Programmatic dependent launch: the kernels of a step are launched with
+// programmatic stream serialization (launch_pdl), so a grid may be scheduled
+// while the grid before it drains.  Every such kernel first waits until the
+// grid before it has completed and its writes are visible, then allows the
+// next grid to be scheduled; without the attribute the wait returns at once.
+// Since each grid waits for its predecessor before it can complete, the
+// order of the whole stream is kept.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---------------------------------------------------------------------------
 // constants
 // ---------------------------------------------------------------------------
@@ -648,11 +676,13 @@ static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, dou
 
 // block (0, ii): interface ii of one stage
 static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_i, double *work_d) {
+  pdl_enter();
   clock_merge_body(md, blockIdx.y, c, dt, work_i, work_d, md.clk);
 }
 
 // block (b, ii): the clock and interface ii's mortar table of stage b of a step
 static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt) {
+  pdl_enter();
   const int b = blockIdx.x;
   MeshDev m = md;
   m.clk = sm.clk[b];
@@ -824,6 +854,7 @@ __device__ __forceinline__ void k_bface_point(const MeshDev &md, int t) {
 // conforming and periodic faces, the next nB N threads the boundary faces.
 template <typename T, int N, bool OTF>
 __global__ void k_faces(MeshDev md) {
+  pdl_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < md.nF * N) k_face_point<T, N, OTF>(md, t);
   else if (t < (md.nF + md.nB) * N) k_bface_point<T, N, OTF>(md, t - md.nF * N);
@@ -847,6 +878,7 @@ enum { MORTAR_RUSANOV = 0, MORTAR_AVG_Q = 1, MORTAR_RUSANOV_FV = 2 };
 
 template <typename T, int N, int MMODE>
 __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md) {
+  pdl_enter();
   constexpr int MPB = MortCfg<N>::MPB;
   constexpr int NV = MMODE == MORTAR_RUSANOV_FV ? 8 : 4;  // projected values per point
   // h_i(o + s z_q) and w_q h_i(o + s z_q) [q][i]: formed in FP64, stored in
@@ -1026,6 +1058,7 @@ enum { GATHER_FLUX = 0, GATHER_Q = 1 };
 
 template <typename T, int N, int GMODE>
 __global__ void k_mortar_gather(MeshDev md) {
+  pdl_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int nLR = md.nL + md.nR;
   if (t >= nLR * N) return;
@@ -1087,6 +1120,7 @@ static __global__ void k_join(const float *__restrict__ hi, const float *__restr
 // face traces [E][4][4][N] of a state (compute-precision values)
 template <typename T, int N>
 __global__ void k_trace(MeshDev md, const T *__restrict__ Q) {
+  pdl_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= md.E * 16 * N) return;
   const int e = t / (16 * N);
@@ -1240,6 +1274,7 @@ template <typename T, int N, int MODE, bool OTF, bool AUX, bool LO>
 __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T, N, OTF, AUX, LO>::MINB)
     k_volume(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
              T *w_out, const T *w_in, int ntiles) {
+  pdl_enter();
   using C = VolCfg<T, N, OTF, AUX, LO>;
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
   constexpr bool FF = C::FF, DF = C::DF;
@@ -1587,7 +1622,10 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
 
 namespace ssd {
 
-static __global__ void k_advance(DevClock *clk, double dt) { clk->t_n = clk->t_n + dt; }
+static __global__ void k_advance(DevClock *clk, double dt) {
+  pdl_enter();
+  clk->t_n = clk->t_n + dt;
+}
 
 // ---------------------------------------------------------------------------
 // engine
@@ -1753,42 +1791,43 @@ struct EngineImpl : Engine {
 
   void trace(const MeshDev &md, StatePtr q, cudaStream_t s) override {
     const int n = md.E * 16 * N;
-    k_trace<T, N><<<(n + 255) / 256, 256, 0, s>>>(md, (const T *)q.hi);
+    launch_pdl(k_trace<T, N>, (n + 255) / 256, 256, 0, s, md, (const T *)q.hi);
   }
 
   void clock_merge(const MeshDev &md, double c, double dt, cudaStream_t s) override {
-    k_clock_merge<<<dim3(1, md.nI), 1024, merge_smem, s>>>(md, c, dt, scratch_i, scratch_d);
+    launch_pdl(k_clock_merge, dim3(1, md.nI), 1024, merge_smem, s, md, c, dt, scratch_i, scratch_d);
   }
 
   void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                         cudaStream_t s) override {
-    k_clock_merge<<<dim3(1, md.nI), 1024, merge_smem, s>>>(md, c, dt, work_i, work_d);
+    launch_pdl(k_clock_merge, dim3(1, md.nI), 1024, merge_smem, s, md, c, dt, work_i, work_d);
   }
 
   void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, cudaStream_t s) override {
-    k_clock_merge_stages<<<dim3(sm.n, md.nI), 1024, merge_smem, s>>>(md, sm, dt);
+    launch_pdl(k_clock_merge_stages, dim3(sm.n, md.nI), 1024, merge_smem, s, md, sm, dt);
   }
 
   template <int MMODE, int GMODE>
   void mortar_pass(const MeshDev &md, cudaStream_t s) {
     constexpr int MPB = MortCfg<N>::MPB;
-    k_mortar_flux<T, N, MMODE><<<(md.nM + MPB - 1) / MPB, MortCfg<N>::THREADS, 0, s>>>(md);
+    launch_pdl(k_mortar_flux<T, N, MMODE>, (md.nM + MPB - 1) / MPB, MortCfg<N>::THREADS, 0, s, md);
     const int n = (md.nL + md.nR) * N;
-    k_mortar_gather<T, N, GMODE><<<(n + 127) / 128, 128, 0, s>>>(md);
+    launch_pdl(k_mortar_gather<T, N, GMODE>, (n + 127) / 128, 128, 0, s, md);
   }
 
   void faces(const MeshDev &md, StatePtr q, cudaStream_t s) override {
     const int np = (md.nF + md.nB) * N;
     if (!md.viscous) {
-      if (np > 0) k_faces<T, N, OTF><<<(np + face_block - 1) / face_block, face_block, 0, s>>>(md);
+      if (np > 0) launch_pdl(k_faces<T, N, OTF>, (np + face_block - 1) / face_block, face_block, 0, s, md);
       return;
     }
     // common solution, gradient traces, then common inviscid + viscous fluxes
-    if (np > 0) k_faces_cq<T, N, OTF><<<(np + 255) / 256, 256, 0, s>>>(md);
+    if (np > 0) launch_pdl(k_faces_cq<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
     if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
     constexpr int EPBv = VisCfg<T, N>::EPB;
-    k_grad_trace<T, N, OTF><<<(md.E + EPBv - 1) / EPBv, VisCfg<T, N>::THREADS, 0, s>>>(md, (const T *)q.hi);
-    if (np > 0) k_faces_visc<T, N, OTF><<<(np + 255) / 256, 256, 0, s>>>(md);
+    launch_pdl(k_grad_trace<T, N, OTF>, (md.E + EPBv - 1) / EPBv, VisCfg<T, N>::THREADS, 0, s, md,
+               (const T *)q.hi);
+    if (np > 0) launch_pdl(k_faces_visc<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
   }
 
   void mortars(const MeshDev &md, cudaStream_t s) override {
@@ -1804,8 +1843,8 @@ struct EngineImpl : Engine {
     using C = VolCfg<T, N, OTF, AUX, LO>;
     const int ntiles = (md.E + C::EPB - 1) / C::EPB;
     const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
-    k_volume<T, N, MODE, OTF, AUX, LO><<<std::min(ntiles, grid), C::THREADS, C::SMEM, s>>>(
-        md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
+    launch_pdl(k_volume<T, N, MODE, OTF, AUX, LO>, std::min(ntiles, grid), C::THREADS, C::SMEM, s, md, in, base,
+               out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
   }
 
   void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk, int mode,
@@ -1815,11 +1854,11 @@ struct EngineImpl : Engine {
       const int grid = (md.E + EPBv - 1) / EPBv;
       const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
       if (mode == MODE_RESIDUAL)
-        k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO><<<grid, VisCfg<T, N>::THREADS, 0, s>>>(
-            md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
+        launch_pdl(k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO>, grid, VisCfg<T, N>::THREADS, 0, s, md, in, base,
+                   out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
       else
-        k_volume_visc<T, N, MODE_RK, OTF, LO><<<grid, VisCfg<T, N>::THREADS, 0, s>>>(
-            md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
+        launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO>, grid, VisCfg<T, N>::THREADS, 0, s, md, in, base, out, R,
+                   c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
       return;
     }
     if (mode == MODE_RESIDUAL) launch_volume<MODE_RESIDUAL, false>(md, in, base, out, R, rk, grid_res, s);
@@ -1855,7 +1894,9 @@ struct EngineImpl : Engine {
     }
   }
 
-  void advance(const MeshDev &md, double dt, cudaStream_t s) override { k_advance<<<1, 1, 0, s>>>(md.clk, dt); }
+  void advance(const MeshDev &md, double dt, cudaStream_t s) override {
+    launch_pdl(k_advance, 1, 1, 0, s, md.clk, dt);
+  }
 
   void sp_coords(const MeshDev &md, double t, double *xy, cudaStream_t s) override {
     k_spxy<N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, t, xy);

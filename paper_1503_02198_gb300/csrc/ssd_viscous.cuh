@@ -93,6 +93,7 @@ __device__ __forceinline__ void k_bface_cq_point(const MeshDev &md, int t) {
 // common solution at all face points of a stage (conforming, then boundary)
 template <typename T, int N, bool OTF>
 __global__ void k_faces_cq(MeshDev md) {
+  pdl_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < md.nF * N) k_face_cq_point<T, N>(md, t);
   else if (t < (md.nF + md.nB) * N) k_bface_cq_point<T, N, OTF>(md, t - md.nF * N);
@@ -167,6 +168,7 @@ __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne
 // gradient traces GTR [E][4 faces][8][N]: component v = dQ_v/dx, 4 + v = dQ_v/dy
 template <typename T, int N, bool OTF>
 __global__ void __launch_bounds__(VisCfg<T, N>::THREADS) k_grad_trace(MeshDev md, const T *__restrict__ Q) {
+  pdl_enter();
   constexpr int EPB = VisCfg<T, N>::EPB, NT = VisCfg<T, N>::THREADS, NN = N * N;
   __shared__ T sQ[EPB][4][NN];
   __shared__ T sCQ[EPB][16 * N];
@@ -291,6 +293,7 @@ __device__ __forceinline__ void k_bface_visc_point(const MeshDev &md, int t) {
 // common inviscid + viscous fluxes at all face points of a stage
 template <typename T, int N, bool OTF>
 __global__ void k_faces_visc(MeshDev md) {
+  pdl_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < md.nF * N) k_face_visc_point<T, N>(md, t);
   else if (t < (md.nF + md.nB) * N) k_bface_visc_point<T, N, OTF>(md, t - md.nF * N);
@@ -302,6 +305,7 @@ template <typename T, int N, int MODE, bool OTF, bool LO>
 __global__ void __launch_bounds__(VisCfg<T, N>::THREADS, VisCfg<T, N>::MINB)
     k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
                   T *w_out, const T *w_in) {
+  pdl_enter();
   constexpr int EPB = VisCfg<T, N>::EPB, NT = VisCfg<T, N>::THREADS, NN = N * N;
   constexpr bool FF = std::is_same<T, float>::value;
   __shared__ T sQ[EPB][4][NN];
