@@ -46,15 +46,13 @@ namespace ssd {
 
 // Programmatic dependent launch: the kernels of a step are launched with
 // programmatic stream serialization (launch_pdl), so a grid may be scheduled
-// while the grid before it drains.  Every such kernel first waits until the
-// grid before it has completed and its writes are visible, then allows the
-// next grid to be scheduled; without the attribute the wait returns at once.
-// Since each grid waits for its predecessor before it can complete, the
-// order of the whole stream is kept.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// as the blocks of the grid before it exit (no early trigger: dependent
+// blocks parked beside a running grid slowed it down).  Every such kernel
+// first waits until the grid before it has completed and its writes are
+// visible; without the attribute the wait returns at once.  Since each grid
+// waits for its predecessor before it can complete, the order of the whole
+// stream is kept.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
