@@ -880,6 +880,25 @@ int sd_info(const sd_handle *h, int *n_elems, int *N, long long *n_dofs) {
 
 static size_t state_bytes(const sd_handle *h) { return sizeof(double) * (size_t)h->E * 4 * h->N * h->N; }
 
+}  // extern "C"
+
+namespace {
+// The device address of a host buffer the GPU can read and write directly
+// (pinned by cudaHostAlloc / cudaMallocHost / cudaHostRegister and mapped into
+// the device's address space; over NVLink-C2C on a Grace host), or null for
+// pageable memory, which goes through a staged copy instead.
+void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+}  // namespace
+
+extern "C" {
+
 int sd_set_state(sd_handle *h, const double *Q, int on_device) {
   if (!h || !Q) return fail(h, SD_ERR_ARG, "null argument");
   cudaError_t e = cudaSuccess;
@@ -887,8 +906,10 @@ int sd_set_state(sd_handle *h, const double *Q, int on_device) {
     e = cudaMemcpyAsync(h->eng->A().hi, Q, state_bytes(h),
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
   } else {
-    const double *src = Q;
-    if (!on_device) {
+    // the conversion reads the caller's buffer itself when the device can
+    // address it (pinned host memory), else a staged copy
+    const double *src = on_device ? Q : (const double *)mapped_host(Q);
+    if (!src) {
       e = cudaMemcpyAsync(h->stage, Q, state_bytes(h), cudaMemcpyHostToDevice, h->stream);
       src = h->stage;
     }
@@ -908,10 +929,12 @@ int sd_get_state(sd_handle *h, double *Q, int on_device) {
     e = cudaMemcpyAsync(Q, h->eng->A().hi, state_bytes(h),
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
   } else {
-    double *dst = on_device ? Q : h->stage;
+    // written straight into a pinned host buffer, else staged and copied
+    double *direct = on_device ? Q : (double *)mapped_host(Q);
+    double *dst = direct ? direct : h->stage;
     h->eng->get_state(h->md, dst, h->stream);
     e = cudaGetLastError();
-    if (!e && !on_device) e = cudaMemcpyAsync(Q, dst, state_bytes(h), cudaMemcpyDeviceToHost, h->stream);
+    if (!e && !direct) e = cudaMemcpyAsync(Q, dst, state_bytes(h), cudaMemcpyDeviceToHost, h->stream);
   }
   if (!e) e = cudaStreamSynchronize(h->stream);
   if (e) return cuda_fail(h, e, "sd_get_state");

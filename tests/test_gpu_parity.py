@@ -291,3 +291,28 @@ def test_zero_steps_change_nothing(ssd, oracle_mod):
     s.sd_step(0.01, 0)
     s.sd_sync()
     assert np.array_equal(s.sd_get_state(), Q) and s.sd_get_time() == 1.5
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_pinned_and_pageable_host_buffers_agree(ssd, oracle_mod, precision):
+    # a pinned host buffer is read / written by the conversion kernels directly,
+    # a pageable one goes through a staged copy: both must give the same bits
+    import torch
+    m = small_rotor(shift_R=0.05)
+    prm = FlowParams(omega=0.9)
+    o = oracle_mod.Oracle(m, 4, prm)
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=8, amp=0.2, scale=3.0))
+    a = ssd.Solver(m, 3, prm, precision=precision)
+    b = ssd.Solver(m, 3, prm, precision=precision)
+    a.sd_set_state(Q)                                   # numpy: pageable
+    pin = torch.from_numpy(Q.copy()).pin_memory()
+    b.sd_set_state(pin)                                 # pinned
+    for s in (a, b):
+        s.sd_step(1e-3, 2)
+        s.sd_sync()
+    qa = a.sd_get_state()
+    out = torch.empty(Q.shape, dtype=torch.float64).pin_memory()
+    b.sd_get_state(out)
+    assert np.array_equal(qa, out.numpy())
+    a.close()
+    b.close()
