@@ -553,16 +553,27 @@ def main():
     solver.sd_step(dt, 1)
     solver.sd_get_state(pin_out)
     barrier()
+    t_set = t_rest = 0.0
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        solver.sd_set_state(pin_in)
+        ta = time.perf_counter()
+        solver.sd_set_state(pin_in)  # returns once the state is on the device
+        tb = time.perf_counter()
         solver.sd_step(dt, 1)
-        solver.sd_get_state(pin_out)
+        solver.sd_get_state(pin_out)  # waits for the step, then the state is on the host
+        t_set += tb - ta
+        t_rest += time.perf_counter() - tb
     solver.sd_sync()
     e2e_s, e2e_work = aggregate_ranks(time.perf_counter() - t0, dofs * args.e2e_steps)
     state_bytes = dofs * 8
     e2e = {"value": e2e_work / e2e_s if e2e_s > 0 else 0.0, "unit": "DOF-updates/s",
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes}
+    if args.e2e_steps > 0:
+        # per step: set_state (host -> device, FP64 state), then the step and
+        # get_state (device -> host); the host link, not the step, dominates
+        n_e = args.e2e_steps
+        e2e.update({"set_state_ms": 1e3 * t_set / n_e, "step_and_get_state_ms": 1e3 * t_rest / n_e,
+                    "h2d_gbs": state_bytes / (t_set / n_e) / 1e9 if t_set > 0 else None})
 
     batched = run_batched(ssd, args.batch_cases, args.batch_steps) if args.batch_cases > 0 else None
     ellipse = run_ellipse(ssd, stream, args.ellipse_steps, 5) if args.ellipse_steps > 0 else None
