@@ -1642,6 +1642,7 @@ struct EngineImpl : Engine {
   size_t nval = 0, nalloc_vals = 0;
   int merge_smem = 0;
   int grid_res = 1, grid_rk = 1, grid_aux = 1;  // persistent grid sizes of the volume kernel
+  int grid_visc_res = 1, grid_visc_rk = 1;       // and of the viscous volume kernel
   int sms = 1, occ_rk = 1;         // SM count, resident volume CTAs per SM
   int face_block = 256;            // block size of the conforming-face kernel
   int face_block_max = 256;        // the most threads per block its registers allow
@@ -1773,6 +1774,23 @@ struct EngineImpl : Engine {
       occ_rk = std::max(1, occ1);
       grid_rk = occ_rk * sms;
       grid_aux = std::max(1, occ2) * sms;
+      // the persistent viscous volume kernel likewise
+      using V = VisVolCfg<T, N>;
+      int ov0 = 0, ov1 = 0;
+      if ((err = cudaFuncSetAttribute(k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, V::SMEM)))
+        return err;
+      if ((err = cudaFuncSetAttribute(k_volume_visc<T, N, MODE_RK, OTF, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      V::SMEM)))
+        return err;
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ov0, k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO>,
+                                                               V::THREADS, V::SMEM)))
+        return err;
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ov1, k_volume_visc<T, N, MODE_RK, OTF, LO>, V::THREADS,
+                                                               V::SMEM)))
+        return err;
+      grid_visc_res = std::max(1, ov0) * sms;
+      grid_visc_rk = std::max(1, ov1) * sms;
     }
     {
       cudaFuncAttributes fa;
@@ -1848,15 +1866,15 @@ struct EngineImpl : Engine {
   void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk, int mode,
               cudaStream_t s) override {
     if (md.viscous) {
-      constexpr int EPBv = VisCfg<T, N>::EPB;
-      const int grid = (md.E + EPBv - 1) / EPBv;
+      using V = VisVolCfg<T, N>;
+      const int ntiles = (md.E + V::EPB - 1) / V::EPB;
       const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
       if (mode == MODE_RESIDUAL)
-        launch_pdl(k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO>, grid, VisCfg<T, N>::THREADS, 0, s, md, in, base,
-                   out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
+        launch_pdl(k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO>, std::min(ntiles, grid_visc_res), V::THREADS,
+                   V::SMEM, s, md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
       else
-        launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO>, grid, VisCfg<T, N>::THREADS, 0, s, md, in, base, out, R,
-                   c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in);
+        launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO>, std::min(ntiles, grid_visc_rk), V::THREADS, V::SMEM, s,
+                   md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
       return;
     }
     if (mode == MODE_RESIDUAL) launch_volume<MODE_RESIDUAL, false>(md, in, base, out, R, rk, grid_res, s);

@@ -21,7 +21,8 @@
 //                              projected back as one sum
 //   k_volume_visc              inviscid + viscous fluxes at interior FPs (with
 //                              the stored SP gradients), divergence, Runge-Kutta
-//                              update, traces
+//                              update, traces; persistent, tiles fed by 1-D
+//                              bulk copies one tile ahead
 #pragma once
 
 namespace ssd {
@@ -103,8 +104,7 @@ __global__ void k_faces_cq(MeshDev md) {
 
 // Elements per block of the viscous kernels (two threads per SP line pair:
 // 2 N threads per element): chosen so that a block is whole warps where the
-// 48 KB of static shared memory of k_volume_visc (20 N^2 + 16 N values per
-// element) allows it.
+// 48 KB of static shared memory of k_grad_trace allows it.
 template <typename T, int N>
 struct VisCfg {
   static constexpr bool F = sizeof(T) == 4;
@@ -112,7 +112,7 @@ struct VisCfg {
   static constexpr int THREADS = EPB * 2 * N;
   // resident blocks per SM the register budget is set for: about 16 warps
   static constexpr int MINB = 16 / ((THREADS + 31) / 32) > 0 ? 16 / ((THREADS + 31) / 32) : 1;
-  static_assert(EPB * (20 * N * N + 16 * N) * (int)sizeof(T) <= 48 * 1024, "static shared memory");
+  static_assert(EPB * (12 * N * N + 16 * N) * (int)sizeof(T) <= 48 * 1024, "static shared memory");
 };
 
 // Gradients at the SPs of a tile (thread per SP line, then per SP): on
@@ -301,181 +301,242 @@ __global__ void k_faces_visc(MeshDev md) {
 
 // ---- volume ------------------------------------------------------------------
 
+// Shared-memory layout of the persistent viscous volume kernel: two stages of
+// a tile's state (4 N^2 values per element), SP gradients (8 N^2: x then y)
+// and common fluxes (16 N), each one contiguous run as in global memory, so a
+// tile arrives by three 1-D bulk copies; then the two divergence arrays.
+template <typename T, int N>
+struct VisVolCfg {
+  static constexpr int EPB = VisCfg<T, N>::EPB, THREADS = VisCfg<T, N>::THREADS, NN = N * N;
+  static constexpr int QE = 4 * NN * (int)sizeof(T), GE = 8 * NN * (int)sizeof(T), CE = 16 * N * (int)sizeof(T);
+  static constexpr int O_Q = 0, O_G = O_Q + EPB * QE, O_C = O_G + EPB * GE;
+  static constexpr int STAGE = ((O_C + EPB * CE) + 127) / 128 * 128;
+  static constexpr int O_RF = 2 * STAGE, O_RG = O_RF + EPB * QE;
+  static constexpr int O_BAR = ((O_RG + EPB * QE) + 15) / 16 * 16;
+  static constexpr int SMEM = O_BAR + 2 * 8;
+  static_assert(QE % 16 == 0 && GE % 16 == 0 && CE % 16 == 0, "bulk-copy sizes and alignment");
+  // resident CTAs per SM the register budget is set for: the smaller of the
+  // warp target of VisCfg and what the shared memory admits
+  static constexpr int BY_SMEM = 228 * 1024 / (SMEM + 1024);
+  static constexpr int MINB = VisCfg<T, N>::MINB < BY_SMEM ? VisCfg<T, N>::MINB : (BY_SMEM > 0 ? BY_SMEM : 1);
+};
+
+// Inviscid + viscous fluxes at the interior FPs with the stored SP gradients,
+// common fluxes at the end FPs, divergence, Runge-Kutta stage, traces.
+// Persistent: each CTA walks tiles of EPB elements; thread 0 issues the next
+// tile's three bulk copies into the other stage while the CTA computes the
+// current one.  Every wait is bounded (device flag bit 2 on timeout).
 template <typename T, int N, int MODE, bool OTF, bool LO>
-__global__ void __launch_bounds__(VisCfg<T, N>::THREADS, VisCfg<T, N>::MINB)
+__global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MINB)
     k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
-                  T *w_out, const T *w_in) {
+                  T *w_out, const T *w_in, int ntiles) {
   pdl_enter();
-  constexpr int EPB = VisCfg<T, N>::EPB, NT = VisCfg<T, N>::THREADS, NN = N * N;
+  using C = VisVolCfg<T, N>;
+  constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
   constexpr bool FF = std::is_same<T, float>::value;
-  __shared__ T sQ[EPB][4][NN];
-  __shared__ T sCF[EPB][16 * N];
-  __shared__ T sDx[EPB][4][NN];
-  __shared__ T sDe[EPB][4][NN];
-  __shared__ T sRF[EPB][4][NN];
-  __shared__ T sRG[EPB][4][NN];
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = (uint64_t *)(smem + C::O_BAR);
+  T(*sRF)[4][NN] = (T(*)[4][NN])(smem + C::O_RF);
+  T(*sRG)[4][NN] = (T(*)[4][NN])(smem + C::O_RG);
   const VolBasis<T, N> &B = cVB<T, N>;
-  const int e0 = blockIdx.x * EPB;
-  const int ne = min(EPB, md.E - e0);
-  // the state, the common fluxes and the SP gradients that k_grad_trace
-  // formed from this state in this stage
-  const T *gsp = (const T *)md.GSP + (size_t)e0 * 8 * NN;
-  for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) {
-    (&sQ[0][0][0])[i] = ((const T *)in.hi)[(size_t)e0 * 4 * NN + i];
-    const int l2 = i / (4 * NN), r = i - l2 * 4 * NN;
-    (&sDx[0][0][0])[i] = gsp[(size_t)l2 * 8 * NN + r];
-    (&sDe[0][0][0])[i] = gsp[(size_t)l2 * 8 * NN + 4 * NN + r];
+  // the state, the SP gradients that k_grad_trace formed from it in this
+  // stage, and the common fluxes of tile tl into stage st
+  auto issue = [&](int tl, int st) {
+    unsigned char *sb = smem + st * C::STAGE;
+    const size_t e0 = (size_t)tl * EPB;
+    const uint32_t ne = (uint32_t)min(EPB, md.E - (int)e0);
+    mbar_expect_tx(&bar[st], ne * (C::QE + C::GE + C::CE));
+    bulk_g2s(sb + C::O_Q, (const T *)in.hi + e0 * 4 * NN, ne * C::QE, &bar[st]);
+    bulk_g2s(sb + C::O_G, (const T *)md.GSP + e0 * 8 * NN, ne * C::GE, &bar[st]);
+    bulk_g2s(sb + C::O_C, (const T *)md.CF + e0 * 16 * N, ne * C::CE, &bar[st]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
   }
-  for (int i = threadIdx.x; i < ne * 16 * N; i += NT) (&sCF[0][0])[i] = ((const T *)md.CF)[(size_t)e0 * 16 * N + i];
   __syncthreads();
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
   const T *zt = zone_tab<T>(md.clk);
   const T gm1 = pick<T>(md.gm1, md.gm1_f);
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
   const int d = r / N, m = r - d * N;
-  if (le < ne) {
-    ElemGeo<T, N, OTF> G;
-    G.load(md, e0 + le, zt);
-    T acc[4][N];
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v][k] = 0;
-#pragma unroll
-    for (int i = 0; i <= N; ++i) {
-      T f[4];
-      if (i == 0 || i == N) {
-        const int face = d == 0 ? (i == 0 ? 3 : 1) : (i == 0 ? 0 : 2);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) f[v] = sCF[le][(face * 4 + v) * N + m];
-      } else {
-        T qf[4], g8[8];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          T a = 0, bx = 0, by = 0;
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const int sp = d == 0 ? m * N + k : k * N + m;
-            const T h = B.Hf[i * N + k];
-            a += sQ[le][v][sp] * h;
-            bx += sDx[le][v][sp] * h;
-            by += sDe[le][v][sp] * h;
-          }
-          qf[v] = a;
-          g8[v] = bx;
-          g8[4 + v] = by;
-        }
-        T vx, vy, vg;
-        if (d == 0) G.xi_fp(i, m, vx, vy, vg);
-        else G.eta_fp(m, i, vx, vy, vg);
-        const T p = pressure_of(qf, gm1);
-        normal_flux(qf, p, vx, vy, vg, f);
-        T Fv[4], Gv[4];
-        viscous_flux(qf, g8, g8 + 4, md, Fv, Gv);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) f[v] += vx * Fv[v] + vy * Gv[v];
-      }
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const T w = B.Dm[k * (N + 1) + i];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v][k] += w * f[v];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        if (d == 0) sRF[le][v][m * N + k] = acc[v][k];
-        else sRG[le][v][k * N + m] = acc[v][k];
-      }
-  }
-  __syncthreads();
   bool bad = false;
-  for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
-    const int l2 = idx / NN, sp = idx - l2 * NN;
-    ElemGeo<T, N, OTF> G;
-    G.load(md, e0 + l2, zt);
-    const T iJ = G.inv_jac(sp % N, sp / N);
-    const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
-    if (MODE == MODE_RESIDUAL) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-    } else if (!FF) {
-      double qn[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const size_t ii = gi + v * NN;
-        const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-        const double qk = (double)sQ[l2][v][sp];
-        double inc = (double)rk.bdt * R;
-        if (has_base) inc += (double)rk.a0 * (((const double *)base.hi)[ii] - qk);
-        if (w_in) inc += (double)w_in[ii];
-        qn[v] = qk + inc;
-        if (w_out) w_out[ii] = (T)((double)rk.ddt * R - (double)rk.g * inc);
-      }
-      const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
-      bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        ((double *)out.hi)[gi + v * NN] = qn[v];
-        sQ[l2][v][sp] = (T)qn[v];
-      }
-    } else {
-      float hv[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const size_t ii = gi + v * NN;
-        const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
-        const float h = (float)sQ[l2][v][sp];
-        float inc = (float)rk.bdt * R;
-        if constexpr (LO) {
-          const float l = ((const float *)in.lo)[ii];
-          if (has_base)
-            inc = fmaf((float)rk.a0, (((const float *)base.hi)[ii] - h) + (((const float *)base.lo)[ii] - l), inc);
-          if (w_in) inc += (float)w_in[ii];
-          float sum, err;
-          two_sum(h, inc, sum, err);
-          err += l;
-          const float H = sum + err;
-          ((float *)out.hi)[ii] = H;
-          ((float *)out.lo)[ii] = err - (H - sum);
-          hv[v] = H;
-        } else {
-          // single-float state: the stage result is rounded to float once
-          if (has_base) inc = fmaf((float)rk.a0, ((const float *)base.hi)[ii] - h, inc);
-          if (w_in) inc += (float)w_in[ii];
-          const float H = h + inc;
-          ((float *)out.hi)[ii] = H;
-          hv[v] = H;
-        }
-        if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
-      }
-      const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
-      bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) sQ[l2][v][sp] = (T)hv[v];
+  int it = 0;
+  for (; tile < ntiles; tile += gridDim.x, ++it) {
+    const int st = it & 1;
+    const int next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles) {
+      // the other stage was last read before the previous iteration's closing
+      // barrier; order those generic reads before the async writes
+      fence_proxy_async_smem();
+      issue(next, st ^ 1);
     }
-  }
-  if (MODE == MODE_RK) {
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&md.clk->flags, 1);
+    if (!cta_wait(&bar[st], (uint32_t)((it >> 1) & 1))) {
+      if (threadIdx.x == 0) {
+        atomicOr(&md.clk->flags, 4);
+        // let the copy in flight land before the CTA exits
+        if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+      }
+      return;
+    }
+    unsigned char *sb = smem + st * C::STAGE;
+    T(*sQ)[4][NN] = (T(*)[4][NN])(sb + C::O_Q);
+    const T(*sG)[8][NN] = (const T(*)[8][NN])(sb + C::O_G);
+    const T(*sCF)[16 * N] = (const T(*)[16 * N])(sb + C::O_C);
+    const int e0 = tile * EPB;
+    const int ne = min(EPB, md.E - e0);
+    // ---- phase 1: one thread per SP line ----
     if (le < ne) {
-      T *tr = (T *)md.TR + (size_t)(e0 + le) * 16 * N;
-      const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+      ElemGeo<T, N, OTF> G;
+      G.load(md, e0 + le, zt);
+      T acc[4][N];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        T a0 = 0, a1 = 0;
+      for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v][k] = 0;
+#pragma unroll
+      for (int i = 0; i <= N; ++i) {
+        T f[4];
+        if (i == 0 || i == N) {
+          const int face = d == 0 ? (i == 0 ? 3 : 1) : (i == 0 ? 0 : 2);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) f[v] = sCF[le][(face * 4 + v) * N + m];
+        } else {
+          T qf[4], g8[8];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            T a = 0, bx = 0, by = 0;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+              const int sp = d == 0 ? m * N + k : k * N + m;
+              const T h = B.Hf[i * N + k];
+              a += sQ[le][v][sp] * h;
+              bx += sG[le][v][sp] * h;
+              by += sG[le][4 + v][sp] * h;
+            }
+            qf[v] = a;
+            g8[v] = bx;
+            g8[4 + v] = by;
+          }
+          T vx, vy, vg;
+          if (d == 0) G.xi_fp(i, m, vx, vy, vg);
+          else G.eta_fp(m, i, vx, vy, vg);
+          const T p = pressure_of(qf, gm1);
+          normal_flux(qf, p, vx, vy, vg, f);
+          T Fv[4], Gv[4];
+          viscous_flux(qf, g8, g8 + 4, md, Fv, Gv);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) f[v] += vx * Fv[v] + vy * Gv[v];
+        }
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-          const T qk = d == 0 ? sQ[le][v][m * N + k] : sQ[le][v][k * N + m];
-          a0 += qk * B.H0[k];
-          a1 += qk * B.H1[k];
+          const T w = B.Dm[k * (N + 1) + i];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[v][k] += w * f[v];
         }
-        tr[(fa * 4 + v) * N + m] = a0;
-        tr[(fb * 4 + v) * N + m] = a1;
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          if (d == 0) sRF[le][v][m * N + k] = acc[v][k];
+          else sRG[le][v][k * N + m] = acc[v][k];
+        }
+    }
+    __syncthreads();
+    // ---- phase 2: dQ/dt at the SPs and the Runge-Kutta stage ----
+    for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
+      const int l2 = idx / NN, sp = idx - l2 * NN;
+      ElemGeo<T, N, OTF> G;
+      G.load(md, e0 + l2, zt);
+      const T iJ = G.inv_jac(sp % N, sp / N);
+      const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
+      if (MODE == MODE_RESIDUAL) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+      } else if (!FF) {
+        double qn[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const size_t ii = gi + v * NN;
+          const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+          const double qk = (double)sQ[l2][v][sp];
+          double inc = (double)rk.bdt * R;
+          if (has_base) inc += (double)rk.a0 * (((const double *)base.hi)[ii] - qk);
+          if (w_in) inc += (double)w_in[ii];
+          qn[v] = qk + inc;
+          if (w_out) w_out[ii] = (T)((double)rk.ddt * R - (double)rk.g * inc);
+        }
+        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
+        bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          ((double *)out.hi)[gi + v * NN] = qn[v];
+          sQ[l2][v][sp] = (T)qn[v];
+        }
+      } else {
+        float hv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const size_t ii = gi + v * NN;
+          const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+          const float h = (float)sQ[l2][v][sp];
+          float inc = (float)rk.bdt * R;
+          if constexpr (LO) {
+            const float l = ((const float *)in.lo)[ii];
+            if (has_base)
+              inc = fmaf((float)rk.a0, (((const float *)base.hi)[ii] - h) + (((const float *)base.lo)[ii] - l), inc);
+            if (w_in) inc += (float)w_in[ii];
+            float sum, err;
+            two_sum(h, inc, sum, err);
+            err += l;
+            const float H = sum + err;
+            ((float *)out.hi)[ii] = H;
+            ((float *)out.lo)[ii] = err - (H - sum);
+            hv[v] = H;
+          } else {
+            // single-float state: the stage result is rounded to float once
+            if (has_base) inc = fmaf((float)rk.a0, ((const float *)base.hi)[ii] - h, inc);
+            if (w_in) inc += (float)w_in[ii];
+            const float H = h + inc;
+            ((float *)out.hi)[ii] = H;
+            hv[v] = H;
+          }
+          if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
+        }
+        const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
+        bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sQ[l2][v][sp] = (T)hv[v];
       }
     }
+    if (MODE == MODE_RK) {
+      __syncthreads();
+      // ---- phase 3: face traces of the new state, one thread per SP line ----
+      if (le < ne) {
+        T *tr = (T *)md.TR + (size_t)(e0 + le) * 16 * N;
+        const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          T a0 = 0, a1 = 0;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const T qk = d == 0 ? sQ[le][v][m * N + k] : sQ[le][v][k * N + m];
+            a0 += qk * B.H0[k];
+            a1 += qk * B.H1[k];
+          }
+          tr[(fa * 4 + v) * N + m] = a0;
+          tr[(fb * 4 + v) * N + m] = a1;
+        }
+      }
+    }
+    // every read of this tile's stage is done before it is refilled
+    __syncthreads();
   }
+  if (MODE == MODE_RK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&md.clk->flags, 1);
 }
 
 }  // namespace ssd
