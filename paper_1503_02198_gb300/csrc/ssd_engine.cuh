@@ -1643,6 +1643,7 @@ struct EngineImpl : Engine {
   int merge_smem = 0;
   int grid_res = 1, grid_rk = 1, grid_aux = 1;  // persistent grid sizes of the volume kernel
   int grid_visc_res = 1, grid_visc_rk = 1;       // and of the viscous volume kernel
+  int grid_grad = 1;                              // and of the gradient kernel
   int sms = 1, occ_rk = 1;         // SM count, resident volume CTAs per SM
   int face_block = 256;            // block size of the conforming-face kernel
   int face_block_max = 256;        // the most threads per block its registers allow
@@ -1791,6 +1792,14 @@ struct EngineImpl : Engine {
         return err;
       grid_visc_res = std::max(1, ov0) * sms;
       grid_visc_rk = std::max(1, ov1) * sms;
+      int og = 0;
+      if ((err = cudaFuncSetAttribute(k_grad_trace<T, N, OTF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      GradCfg<T, N>::SMEM)))
+        return err;
+      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&og, k_grad_trace<T, N, OTF>, GradCfg<T, N>::THREADS,
+                                                               GradCfg<T, N>::SMEM)))
+        return err;
+      grid_grad = std::max(1, og) * sms;
     }
     {
       cudaFuncAttributes fa;
@@ -1840,9 +1849,10 @@ struct EngineImpl : Engine {
     // common solution, gradient traces, then common inviscid + viscous fluxes
     if (np > 0) launch_pdl(k_faces_cq<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
     if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
-    constexpr int EPBv = VisCfg<T, N>::EPB;
-    launch_pdl(k_grad_trace<T, N, OTF>, (md.E + EPBv - 1) / EPBv, VisCfg<T, N>::THREADS, 0, s, md,
-               (const T *)q.hi);
+    using Gc = GradCfg<T, N>;
+    const int ntg = (md.E + Gc::EPB - 1) / Gc::EPB;
+    launch_pdl(k_grad_trace<T, N, OTF>, std::min(ntg, grid_grad), Gc::THREADS, Gc::SMEM, s, md, (const T *)q.hi,
+               ntg);
     if (np > 0) launch_pdl(k_faces_visc<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
   }
 

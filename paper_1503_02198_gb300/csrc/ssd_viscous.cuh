@@ -103,8 +103,7 @@ __global__ void k_faces_cq(MeshDev md) {
 // ---- gradients ---------------------------------------------------------------
 
 // Elements per block of the viscous kernels (two threads per SP line pair:
-// 2 N threads per element): chosen so that a block is whole warps where the
-// 48 KB of static shared memory of k_grad_trace allows it.
+// 2 N threads per element): chosen so that a block is whole warps.
 template <typename T, int N>
 struct VisCfg {
   static constexpr bool F = sizeof(T) == 4;
@@ -112,7 +111,6 @@ struct VisCfg {
   static constexpr int THREADS = EPB * 2 * N;
   // resident blocks per SM the register budget is set for: about 16 warps
   static constexpr int MINB = 16 / ((THREADS + 31) / 32) > 0 ? 16 / ((THREADS + 31) / 32) : 1;
-  static_assert(EPB * (12 * N * N + 16 * N) * (int)sizeof(T) <= 48 * 1024, "static shared memory");
 };
 
 // Gradients at the SPs of a tile (thread per SP line, then per SP): on
@@ -165,50 +163,106 @@ __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne
   }
 }
 
-// gradient traces GTR [E][4 faces][8][N]: component v = dQ_v/dx, 4 + v = dQ_v/dy
+// Shared-memory layout of the persistent gradient kernel: two stages of a
+// tile's state (4 N^2 values per element) and common solution (16 N), one
+// contiguous run each as in global memory; then the gradient arrays.
+template <typename T, int N>
+struct GradCfg {
+  static constexpr int EPB = VisCfg<T, N>::EPB, THREADS = VisCfg<T, N>::THREADS, NN = N * N;
+  static constexpr int QE = 4 * NN * (int)sizeof(T), CE = 16 * N * (int)sizeof(T);
+  static constexpr int O_Q = 0, O_C = O_Q + EPB * QE;
+  static constexpr int STAGE = ((O_C + EPB * CE) + 127) / 128 * 128;
+  static constexpr int O_DX = 2 * STAGE, O_DE = O_DX + EPB * QE;
+  static constexpr int O_BAR = ((O_DE + EPB * QE) + 15) / 16 * 16;
+  static constexpr int SMEM = O_BAR + 2 * 8;
+  static_assert(QE % 16 == 0 && CE % 16 == 0, "bulk-copy sizes and alignment");
+};
+
+// SP gradients GSP [E][8][N][N] and gradient traces GTR [E][4 faces][8][N]
+// (component v = dQ_v/dx, 4 + v = dQ_v/dy).  Persistent: each CTA walks
+// tiles; thread 0 issues the next tile's state and common solution (two 1-D
+// bulk copies) into the other stage while the CTA computes the current one.
 template <typename T, int N, bool OTF>
-__global__ void __launch_bounds__(VisCfg<T, N>::THREADS) k_grad_trace(MeshDev md, const T *__restrict__ Q) {
+__global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(MeshDev md, const T *__restrict__ Q,
+                                                                       int ntiles) {
   pdl_enter();
-  constexpr int EPB = VisCfg<T, N>::EPB, NT = VisCfg<T, N>::THREADS, NN = N * N;
-  __shared__ T sQ[EPB][4][NN];
-  __shared__ T sCQ[EPB][16 * N];
-  __shared__ T sDx[EPB][4][NN];
-  __shared__ T sDe[EPB][4][NN];
-  const int e0 = blockIdx.x * EPB;
-  const int ne = min(EPB, md.E - e0);
-  for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) (&sQ[0][0][0])[i] = Q[(size_t)e0 * 4 * NN + i];
-  for (int i = threadIdx.x; i < ne * 16 * N; i += NT) (&sCQ[0][0])[i] = ((const T *)md.CQ)[(size_t)e0 * 16 * N + i];
-  __syncthreads();
-  tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, zone_tab<T>(md.clk));
-  __syncthreads();
-  // the SP gradients for the volume kernel of this stage
-  for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) {
-    const int l2 = i / (4 * NN), r = i - l2 * 4 * NN;
-    T *gs = (T *)md.GSP + (size_t)(e0 + l2) * 8 * NN;
-    gs[r] = (&sDx[0][0][0])[i];
-    gs[4 * NN + r] = (&sDe[0][0][0])[i];
+  using C = GradCfg<T, N>;
+  constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bar = (uint64_t *)(smem + C::O_BAR);
+  T(*sDx)[4][NN] = (T(*)[4][NN])(smem + C::O_DX);
+  T(*sDe)[4][NN] = (T(*)[4][NN])(smem + C::O_DE);
+  auto issue = [&](int tl, int st) {
+    unsigned char *sb = smem + st * C::STAGE;
+    const size_t e0 = (size_t)tl * EPB;
+    const uint32_t ne = (uint32_t)min(EPB, md.E - (int)e0);
+    mbar_expect_tx(&bar[st], ne * (C::QE + C::CE));
+    bulk_g2s(sb + C::O_Q, Q + e0 * 4 * NN, ne * C::QE, &bar[st]);
+    bulk_g2s(sb + C::O_C, (const T *)md.CQ + e0 * 16 * N, ne * C::CE, &bar[st]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
   }
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  const T *zt = zone_tab<T>(md.clk);
   const VolBasis<T, N> &B = cVB<T, N>;
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
   const int d = r / N, m = r - d * N;
-  if (le < ne) {
-    T *g = (T *)md.GTR + (size_t)(e0 + le) * 32 * N;
-    const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int v = c & 3;
-      T a0 = 0, a1 = 0;
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const int sp = d == 0 ? m * N + k : k * N + m;
-        const T val = c < 4 ? sDx[le][v][sp] : sDe[le][v][sp];
-        a0 += val * B.H0[k];
-        a1 += val * B.H1[k];
-      }
-      g[(fa * 8 + c) * N + m] = a0;
-      g[(fb * 8 + c) * N + m] = a1;
+  int it = 0;
+  for (; tile < ntiles; tile += gridDim.x, ++it) {
+    const int st = it & 1;
+    const int next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles) {
+      fence_proxy_async_smem();
+      issue(next, st ^ 1);
     }
+    if (!cta_wait(&bar[st], (uint32_t)((it >> 1) & 1))) {
+      if (threadIdx.x == 0) {
+        atomicOr(&md.clk->flags, 4);
+        if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+      }
+      return;
+    }
+    unsigned char *sb = smem + st * C::STAGE;
+    T(*sQ)[4][NN] = (T(*)[4][NN])(sb + C::O_Q);
+    T(*sCQ)[16 * N] = (T(*)[16 * N])(sb + C::O_C);
+    const int e0 = tile * EPB;
+    const int ne = min(EPB, md.E - e0);
+    tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, zt);
+    __syncthreads();
+    // the SP gradients for the volume kernel of this stage
+    for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) {
+      const int l2 = i / (4 * NN), rr = i - l2 * 4 * NN;
+      T *gs = (T *)md.GSP + (size_t)(e0 + l2) * 8 * NN;
+      gs[rr] = (&sDx[0][0][0])[i];
+      gs[4 * NN + rr] = (&sDe[0][0][0])[i];
+    }
+    if (le < ne) {
+      T *g = (T *)md.GTR + (size_t)(e0 + le) * 32 * N;
+      const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int v = c & 3;
+        T a0 = 0, a1 = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const int sp = d == 0 ? m * N + k : k * N + m;
+          const T val = c < 4 ? sDx[le][v][sp] : sDe[le][v][sp];
+          a0 += val * B.H0[k];
+          a1 += val * B.H1[k];
+        }
+        g[(fa * 8 + c) * N + m] = a0;
+        g[(fb * 8 + c) * N + m] = a1;
+      }
+    }
+    // every read of this tile's stage and of the gradient arrays is done
+    // before they are refilled
+    __syncthreads();
   }
 }
 
