@@ -502,6 +502,70 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     }
     __syncthreads();
     // ---- phase 2: dQ/dt at the SPs and the Runge-Kutta stage ----
+    if constexpr (MODE == MODE_RK && FF) {
+      // FP32: the base state and the lo planes of an SP come from global
+      // memory; the next SP's loads are issued before this SP's stores (later
+      // stages update the state in place, so the compiler keeps loads behind
+      // earlier stores unless the program orders them first)
+      auto fetch = [&](int idx, float *bh, float *kl, float *bl) {
+        const int l2 = idx / NN, sp = idx - l2 * NN;
+        const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          bh[v] = has_base ? ((const float *)base.hi)[gi + v * NN] : 0.0f;
+          kl[v] = LO ? ((const float *)in.lo)[gi + v * NN] : 0.0f;
+          bl[v] = (LO && has_base) ? ((const float *)base.lo)[gi + v * NN] : 0.0f;
+        }
+      };
+      float bh[4], kl[4], bl[4];
+      if ((int)threadIdx.x < ne * NN) fetch(threadIdx.x, bh, kl, bl);
+      for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
+        float nbh[4], nkl[4], nbl[4];
+        if (idx + NT < ne * NN) fetch(idx + NT, nbh, nkl, nbl);
+        const int l2 = idx / NN, sp = idx - l2 * NN;
+        ElemGeo<T, N, OTF> G;
+        G.load(md, e0 + l2, zt);
+        const T iJ = G.inv_jac(sp % N, sp / N);
+        const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
+        float hv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const size_t ii = gi + v * NN;
+          const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+          const float h = (float)sQ[l2][v][sp];
+          float inc = (float)rk.bdt * R;
+          if constexpr (LO) {
+            const float l = kl[v];
+            if (has_base) inc = fmaf((float)rk.a0, (bh[v] - h) + (bl[v] - l), inc);
+            if (w_in) inc += (float)w_in[ii];
+            float sum, err;
+            two_sum(h, inc, sum, err);
+            err += l;
+            const float H = sum + err;
+            ((float *)out.hi)[ii] = H;
+            ((float *)out.lo)[ii] = err - (H - sum);
+            hv[v] = H;
+          } else {
+            // single-float state: the stage result is rounded to float once
+            if (has_base) inc = fmaf((float)rk.a0, bh[v] - h, inc);
+            if (w_in) inc += (float)w_in[ii];
+            const float H = h + inc;
+            ((float *)out.hi)[ii] = H;
+            hv[v] = H;
+          }
+          if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
+        }
+        const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
+        bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          sQ[l2][v][sp] = (T)hv[v];
+          bh[v] = nbh[v];
+          kl[v] = nkl[v];
+          bl[v] = nbl[v];
+        }
+      }
+    } else
     for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
       const int l2 = idx / NN, sp = idx - l2 * NN;
       ElemGeo<T, N, OTF> G;
