@@ -241,8 +241,9 @@ const char *sd_batch_last_error(const sd_batch *b);
  * milliseconds per launch of ms[0] stage clock + mortar merge, ms[1]
  * conforming, periodic and wall faces, ms[2] mortar projection + gather
  * (the paper's "interface" work), ms[3] volume kernel (divergence, RK update,
- * traces); ms[4] = mean milliseconds per whole step.  Advances the solution
- * by reps steps; synchronises. */
+ * traces); ms[4] = mean milliseconds per whole step.  The mortar flux is
+ * timed as its own launch here; sd_step runs it inside the face launch of
+ * the same pass.  Advances the solution by reps steps; synchronises. */
 int sd_profile_step(sd_handle *h, double dt, int reps, double *ms);
 
 /* Measured FMA throughput of the current GPU in TFLOP/s (2 flops per FMA)

@@ -874,10 +874,10 @@ struct MortCfg {
 // back-projection is linear, Eq. prjF2)
 enum { MORTAR_RUSANOV = 0, MORTAR_AVG_Q = 1, MORTAR_RUSANOV_FV = 2 };
 
-template <typename T, int N, int MMODE>
-__global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md) {
-  pdl_enter();
-  constexpr int MPB = MortCfg<N>::MPB;
+// The mortar flux of MPB mortars of block blk: thread (mortar lm < MPB, side,
+// point); threads beyond MPB * 2 N only take part in the barriers.
+template <typename T, int N, int MMODE, int MPB>
+__device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
   constexpr int NV = MMODE == MORTAR_RUSANOV_FV ? 8 : 4;  // projected values per point
   // h_i(o + s z_q) and w_q h_i(o + s z_q) [q][i]: formed in FP64, stored in
   // the compute type once
@@ -891,8 +891,8 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
   const int lm = threadIdx.x / (2 * N);
   const int r = threadIdx.x - lm * 2 * N;
   const int sd = r / N, p = r - sd * N;
-  const int m = blockIdx.x * MPB + lm;
-  const bool act = m < md.nM;
+  const int m = blk * MPB + lm;
+  const bool act = lm < MPB && m < md.nM;
   const MortBasis<N> &B = cMB<N>;
   double o = 0.0, s = 0.0;
   int ef = 0, rev = 0;
@@ -1046,6 +1046,12 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
       out[v * N + p] = (T)s * acc;
     }
   }
+}
+
+template <typename T, int N, int MMODE>
+__global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md) {
+  pdl_enter();
+  mortar_flux_body<T, N, MMODE, MortCfg<N>::MPB>(md, blockIdx.x);
 }
 
 // Sum of the mortar contributions of each interface face (fixed order: the
@@ -1620,6 +1626,38 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
 
 namespace ssd {
 
+// One launch for a face pass and the mortar flux of the same pass, which are
+// independent: blocks [0, nmb) compute the mortar fluxes (MortCfg's MPB
+// mortars each; the latency-bound mortar chain then runs under the face
+// work), the rest one face point per thread.  MMODE selects the pair:
+// RUSANOV with k_faces, AVG_Q with k_faces_cq, RUSANOV_FV with k_faces_visc.
+constexpr int kFusedBlock = 256;
+
+template <typename T, int N, bool OTF, int MMODE>
+__global__ void __launch_bounds__(kFusedBlock) k_faces_mortar(MeshDev md, int nmb) {
+  pdl_enter();
+  static_assert(MortCfg<N>::THREADS <= kFusedBlock, "mortar block");
+  if ((int)blockIdx.x < nmb) {
+    mortar_flux_body<T, N, MMODE, MortCfg<N>::MPB>(md, blockIdx.x);
+    return;
+  }
+  const int t = ((int)blockIdx.x - nmb) * kFusedBlock + threadIdx.x;
+  if (t < md.nF * N) {
+    if (MMODE == MORTAR_RUSANOV) k_face_point<T, N, OTF>(md, t);
+    else if (MMODE == MORTAR_AVG_Q) k_face_cq_point<T, N>(md, t);
+    else k_face_visc_point<T, N>(md, t);
+  } else if (t < (md.nF + md.nB) * N) {
+    const int tb = t - md.nF * N;
+    if (MMODE == MORTAR_RUSANOV) k_bface_point<T, N, OTF>(md, tb);
+    else if (MMODE == MORTAR_AVG_Q) k_bface_cq_point<T, N, OTF>(md, tb);
+    else k_bface_visc_point<T, N, OTF>(md, tb);
+  }
+}
+
+}  // namespace ssd
+
+namespace ssd {
+
 static __global__ void k_advance(DevClock *clk, double dt) {
   pdl_enter();
   clk->t_n = clk->t_n + dt;
@@ -1644,6 +1682,7 @@ struct EngineImpl : Engine {
   int grid_res = 1, grid_rk = 1, grid_aux = 1;  // persistent grid sizes of the volume kernel
   int grid_visc_res = 1, grid_visc_rk = 1;       // and of the viscous volume kernel
   int grid_grad = 1;                              // and of the gradient kernel
+  bool fuse_faces_mortar = true;                  // mortar flux inside the face launch
   int sms = 1, occ_rk = 1;         // SM count, resident volume CTAs per SM
   int face_block = 256;            // block size of the conforming-face kernel
   int face_block_max = 256;        // the most threads per block its registers allow
@@ -1833,35 +1872,56 @@ struct EngineImpl : Engine {
   }
 
   template <int MMODE, int GMODE>
-  void mortar_pass(const MeshDev &md, cudaStream_t s) {
+  void mortar_pass(const MeshDev &md, cudaStream_t s, bool flux = true) {
     constexpr int MPB = MortCfg<N>::MPB;
-    launch_pdl(k_mortar_flux<T, N, MMODE>, (md.nM + MPB - 1) / MPB, MortCfg<N>::THREADS, 0, s, md);
+    if (flux) launch_pdl(k_mortar_flux<T, N, MMODE>, (md.nM + MPB - 1) / MPB, MortCfg<N>::THREADS, 0, s, md);
     const int n = (md.nL + md.nR) * N;
     launch_pdl(k_mortar_gather<T, N, GMODE>, (n + 127) / 128, 128, 0, s, md);
   }
 
+  // a face pass fused with the mortar flux of the same pass (meshes with an
+  // interface); the gather follows as its own launch
+  template <int MMODE>
+  void fused_pass(const MeshDev &md, cudaStream_t s) {
+    constexpr int MPB = MortCfg<N>::MPB;
+    const int nmb = (md.nM + MPB - 1) / MPB;
+    const int np = (md.nF + md.nB) * N;
+    launch_pdl(k_faces_mortar<T, N, OTF, MMODE>, nmb + (np + kFusedBlock - 1) / kFusedBlock, kFusedBlock, 0, s, md,
+               nmb);
+  }
+  bool fused(const MeshDev &md) const { return fuse_faces_mortar && md.nL > 0; }
+
   void faces(const MeshDev &md, StatePtr q, cudaStream_t s) override {
     const int np = (md.nF + md.nB) * N;
     if (!md.viscous) {
-      if (np > 0) launch_pdl(k_faces<T, N, OTF>, (np + face_block - 1) / face_block, face_block, 0, s, md);
+      if (fused(md)) fused_pass<MORTAR_RUSANOV>(md, s);
+      else if (np > 0) launch_pdl(k_faces<T, N, OTF>, (np + face_block - 1) / face_block, face_block, 0, s, md);
       return;
     }
     // common solution, gradient traces, then common inviscid + viscous fluxes
-    if (np > 0) launch_pdl(k_faces_cq<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
-    if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
+    if (fused(md)) {
+      fused_pass<MORTAR_AVG_Q>(md, s);
+      mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s, false);
+    } else {
+      if (np > 0) launch_pdl(k_faces_cq<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
+      if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
+    }
     using Gc = GradCfg<T, N>;
     const int ntg = (md.E + Gc::EPB - 1) / Gc::EPB;
     launch_pdl(k_grad_trace<T, N, OTF>, std::min(ntg, grid_grad), Gc::THREADS, Gc::SMEM, s, md, (const T *)q.hi,
                ntg);
-    if (np > 0) launch_pdl(k_faces_visc<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
+    if (fused(md)) fused_pass<MORTAR_RUSANOV_FV>(md, s);
+    else if (np > 0) launch_pdl(k_faces_visc<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
   }
 
+  // the gather (and, when not fused into the face pass, the mortar flux)
   void mortars(const MeshDev &md, cudaStream_t s) override {
     if (md.nL > 0) {
-      if (md.viscous) mortar_pass<MORTAR_RUSANOV_FV, GATHER_FLUX>(md, s);
-      else mortar_pass<MORTAR_RUSANOV, GATHER_FLUX>(md, s);
+      if (md.viscous) mortar_pass<MORTAR_RUSANOV_FV, GATHER_FLUX>(md, s, !fused(md));
+      else mortar_pass<MORTAR_RUSANOV, GATHER_FLUX>(md, s, !fused(md));
     }
   }
+  void set_fusion(bool on) override { fuse_faces_mortar = on; }
 
   template <int MODE, bool AUX>
   void launch_volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk,

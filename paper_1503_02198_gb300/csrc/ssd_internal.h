@@ -184,6 +184,9 @@ struct Engine {
   // q: the stage's state (the viscous chain needs its gradients)
   virtual void faces(const MeshDev &md, StatePtr q, cudaStream_t s) = 0;
   virtual void mortars(const MeshDev &md, cudaStream_t s) = 0;
+  // true (default): the mortar flux runs inside the face launch of the same
+  // pass; false: as its own launch in mortars() (per-phase timing)
+  virtual void set_fusion(bool on) = 0;
   void couple(const MeshDev &md, StatePtr q, double c, double dt, cudaStream_t s) {
     clock_merge(md, c, dt, s);
     faces(md, q, s);
