@@ -140,14 +140,15 @@ def volume_bytes_per_element(N, w_c, w_s=8):
 def launches_per_step(mesh, viscous=0):
     """Kernels of one captured SSP-RK3 step: one merge launch for the clocks
     and mortar tables of all three stages; per stage the face kernel
-    (conforming and boundary points in one launch), the two mortar kernels
-    (if an interface) and the volume kernel, plus for a viscous stage the
-    common-solution face kernel, its mortar pair and the gradient-trace
-    kernel; then the clock advance."""
-    iface = int(len(mesh["ifaces_L"]) > 0)
-    per_stage = 1 + 2 * iface + 1
+    (conforming and boundary points, and the mortar flux when the mesh has an
+    interface, in one launch), the mortar gather (if an interface) and the
+    volume kernel, plus for a viscous stage the common-solution face kernel
+    (with its mortar flux), its gather and the gradient-trace kernel; then
+    the clock advance."""
+    iface = int(len(mesh["ifaces_L"]) > 0 or any(len(z["ifaces_L"]) > 0 for z in mesh.get("zones", [])))
+    per_stage = 1 + iface + 1
     if viscous:
-        per_stage += 1 + 2 * iface + 1
+        per_stage += 1 + iface + 1
     return 1 + 3 * per_stage + 1
 
 
