@@ -100,8 +100,8 @@ class ClockSampler:
 # profiles/k_volume_fp32_rotor_n6.md; valid only for the kernel source it was
 # taken on: SHA-256 of the engine text that k_volume is built from (the
 # ElemGeo metrics and VolCfg through the end of k_volume); otherwise null.
-PROFILED_TRAFFIC = {"bytes": (389.03e6 + 328.56e6 + 673.56e6 + 330.71e6 + 673.44e6 + 329.70e6) / 3,
-                    "kernel_sha256": "71e036ac8769dccb98705d7bdc53c1504e3b2a235021e5aa42949adb92c03851"}
+PROFILED_TRAFFIC = {"bytes": (389.06e6 + 328.52e6 + 673.47e6 + 331.29e6 + 673.47e6 + 329.67e6) / 3,
+                    "kernel_sha256": "0ca2e437d4cfb2bcce0666b0130d3e18685380c94531e4392a21f1c5248948b6"}
 
 
 def volume_kernel_source():
