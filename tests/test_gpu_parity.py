@@ -316,3 +316,26 @@ def test_pinned_and_pageable_host_buffers_agree(ssd, oracle_mod, precision):
     assert np.array_equal(qa, out.numpy())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision,viscous", [(0, 0), (1, 0), (1, 1)])
+def test_profiled_steps_equal_graph_steps(ssd, oracle_mod, precision, viscous):
+    # sd_profile_step runs the mortar flux as its own launch (to time it);
+    # sd_step runs it inside the face launch of the same pass: the same
+    # arithmetic, so the same bits
+    m = small_rotor(shift_R=0.05)
+    prm = FlowParams(omega=0.9, viscous=viscous, mu=0.02 * viscous)
+    o = oracle_mod.Oracle(m, 4, prm)
+    Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=12, amp=0.2, scale=3.0))
+    a = ssd.Solver(m, 3, prm, precision=precision)
+    b = ssd.Solver(m, 3, prm, precision=precision)
+    for s in (a, b):
+        s.sd_set_state(Q)
+        s.sd_set_time(0.3)
+    a.sd_step(1e-3, 3)
+    a.sd_sync()
+    b.sd_profile_step(1e-3, reps=3)
+    assert a.sd_get_time() == b.sd_get_time()
+    assert np.array_equal(a.sd_get_state(), b.sd_get_state())
+    a.close()
+    b.close()
