@@ -118,7 +118,7 @@ struct VisCfg {
 template <typename T, int N, bool OTF>
 __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne, T (*sQ)[4][N * N],
                                                T (*sCQ)[16 * N], T (*sDx)[4][N * N], T (*sDe)[4][N * N],
-                                               const T *zt) {
+                                               const T *zt, const int *sEF, const T *sEG) {
   constexpr int NN = N * N, NT = VisCfg<T, N>::THREADS;
   const VolBasis<T, N> &B = cVB<T, N>;
   const int le = threadIdx.x / (2 * N);
@@ -151,7 +151,7 @@ __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne
   for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
     const int l2 = idx / NN, sp = idx - l2 * NN;
     ElemGeo<T, N, OTF> G;
-    G.load(md, e0 + l2, zt);
+    G.load_rec(md, e0 + l2, sEF[l2], sEG + l2 * 8, zt);
     T xix, xiy, etx, ety;
     G.sp_grad(sp % N, sp / N, xix, xiy, etx, ety);
 #pragma unroll
@@ -170,8 +170,9 @@ template <typename T, int N>
 struct GradCfg {
   static constexpr int EPB = VisCfg<T, N>::EPB, THREADS = VisCfg<T, N>::THREADS, NN = N * N;
   static constexpr int QE = 4 * NN * (int)sizeof(T), CE = 16 * N * (int)sizeof(T);
-  static constexpr int O_Q = 0, O_C = O_Q + EPB * QE;
-  static constexpr int STAGE = ((O_C + EPB * CE) + 127) / 128 * 128;
+  static constexpr int GEE = 8 * (int)sizeof(T);  // bilinear cell record
+  static constexpr int O_Q = 0, O_C = O_Q + EPB * QE, O_EG = O_C + EPB * CE, O_EF = O_EG + EPB * GEE;
+  static constexpr int STAGE = ((O_EF + EPB * 4) + 127) / 128 * 128;
   static constexpr int O_DX = 2 * STAGE, O_DE = O_DX + EPB * QE;
   static constexpr int O_BAR = ((O_DE + EPB * QE) + 15) / 16 * 16;
   static constexpr int SMEM = O_BAR + 2 * 8;
@@ -192,13 +193,17 @@ __global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(MeshDev m
   uint64_t *bar = (uint64_t *)(smem + C::O_BAR);
   T(*sDx)[4][NN] = (T(*)[4][NN])(smem + C::O_DX);
   T(*sDe)[4][NN] = (T(*)[4][NN])(smem + C::O_DE);
+  // the cell records (on-the-fly path) and flags come along; the flags are
+  // copied in whole groups of 4 (16 bytes), within the tile-padded array
   auto issue = [&](int tl, int st) {
     unsigned char *sb = smem + st * C::STAGE;
     const size_t e0 = (size_t)tl * EPB;
-    const uint32_t ne = (uint32_t)min(EPB, md.E - (int)e0);
-    mbar_expect_tx(&bar[st], ne * (C::QE + C::CE));
+    const uint32_t ne = (uint32_t)min(EPB, md.E - (int)e0), nf = (ne + 3u) & ~3u;
+    mbar_expect_tx(&bar[st], ne * (C::QE + C::CE + (OTF ? C::GEE : 0)) + nf * 4u);
     bulk_g2s(sb + C::O_Q, Q + e0 * 4 * NN, ne * C::QE, &bar[st]);
     bulk_g2s(sb + C::O_C, (const T *)md.CQ + e0 * 16 * N, ne * C::CE, &bar[st]);
+    if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, ne * C::GEE, &bar[st]);
+    bulk_g2s(sb + C::O_EF, md.eflag + e0, nf * 4u, &bar[st]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -231,9 +236,11 @@ __global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(MeshDev m
     unsigned char *sb = smem + st * C::STAGE;
     T(*sQ)[4][NN] = (T(*)[4][NN])(sb + C::O_Q);
     T(*sCQ)[16 * N] = (T(*)[16 * N])(sb + C::O_C);
+    const T *sEG = (const T *)(sb + C::O_EG);
+    const int *sEF = (const int *)(sb + C::O_EF);
     const int e0 = tile * EPB;
     const int ne = min(EPB, md.E - e0);
-    tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, zt);
+    tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, zt, sEF, sEG);
     __syncthreads();
     // the SP gradients for the volume kernel of this stage
     for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) {
@@ -363,8 +370,10 @@ template <typename T, int N>
 struct VisVolCfg {
   static constexpr int EPB = VisCfg<T, N>::EPB, THREADS = VisCfg<T, N>::THREADS, NN = N * N;
   static constexpr int QE = 4 * NN * (int)sizeof(T), GE = 8 * NN * (int)sizeof(T), CE = 16 * N * (int)sizeof(T);
-  static constexpr int O_Q = 0, O_G = O_Q + EPB * QE, O_C = O_G + EPB * GE;
-  static constexpr int STAGE = ((O_C + EPB * CE) + 127) / 128 * 128;
+  static constexpr int GEE = 8 * (int)sizeof(T);  // bilinear cell record
+  static constexpr int O_Q = 0, O_G = O_Q + EPB * QE, O_C = O_G + EPB * GE, O_EG = O_C + EPB * CE;
+  static constexpr int O_EF = O_EG + EPB * GEE;
+  static constexpr int STAGE = ((O_EF + EPB * 4) + 127) / 128 * 128;
   static constexpr int O_RF = 2 * STAGE, O_RG = O_RF + EPB * QE;
   static constexpr int O_BAR = ((O_RG + EPB * QE) + 15) / 16 * 16;
   static constexpr int SMEM = O_BAR + 2 * 8;
@@ -395,14 +404,18 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
   const VolBasis<T, N> &B = cVB<T, N>;
   // the state, the SP gradients that k_grad_trace formed from it in this
   // stage, and the common fluxes of tile tl into stage st
+  // with the cell records (on-the-fly path) and flags, the flags in whole
+  // groups of 4 (16 bytes), within the tile-padded array
   auto issue = [&](int tl, int st) {
     unsigned char *sb = smem + st * C::STAGE;
     const size_t e0 = (size_t)tl * EPB;
-    const uint32_t ne = (uint32_t)min(EPB, md.E - (int)e0);
-    mbar_expect_tx(&bar[st], ne * (C::QE + C::GE + C::CE));
+    const uint32_t ne = (uint32_t)min(EPB, md.E - (int)e0), nf = (ne + 3u) & ~3u;
+    mbar_expect_tx(&bar[st], ne * (C::QE + C::GE + C::CE + (OTF ? C::GEE : 0)) + nf * 4u);
     bulk_g2s(sb + C::O_Q, (const T *)in.hi + e0 * 4 * NN, ne * C::QE, &bar[st]);
     bulk_g2s(sb + C::O_G, (const T *)md.GSP + e0 * 8 * NN, ne * C::GE, &bar[st]);
     bulk_g2s(sb + C::O_C, (const T *)md.CF + e0 * 16 * N, ne * C::CE, &bar[st]);
+    if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, ne * C::GEE, &bar[st]);
+    bulk_g2s(sb + C::O_EF, md.eflag + e0, nf * 4u, &bar[st]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -440,12 +453,14 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     T(*sQ)[4][NN] = (T(*)[4][NN])(sb + C::O_Q);
     const T(*sG)[8][NN] = (const T(*)[8][NN])(sb + C::O_G);
     const T(*sCF)[16 * N] = (const T(*)[16 * N])(sb + C::O_C);
+    const T *sEG = (const T *)(sb + C::O_EG);
+    const int *sEF = (const int *)(sb + C::O_EF);
     const int e0 = tile * EPB;
     const int ne = min(EPB, md.E - e0);
     // ---- phase 1: one thread per SP line ----
     if (le < ne) {
       ElemGeo<T, N, OTF> G;
-      G.load(md, e0 + le, zt);
+      G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, zt);
       T acc[4][N];
 #pragma unroll
       for (int k = 0; k < N; ++k)
@@ -523,9 +538,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
         float nbh[4], nkl[4], nbl[4];
         if (idx + NT < ne * NN) fetch(idx + NT, nbh, nkl, nbl);
         const int l2 = idx / NN, sp = idx - l2 * NN;
-        ElemGeo<T, N, OTF> G;
-        G.load(md, e0 + l2, zt);
-        const T iJ = G.inv_jac(sp % N, sp / N);
+        const T iJ = ElemGeo<T, N, OTF>::inv_jac_t0(md, sEF[l2], sEG + l2 * 8, sp % N, sp / N);
         const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
         float hv[4];
 #pragma unroll
@@ -568,9 +581,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     } else
     for (int idx = threadIdx.x; idx < ne * NN; idx += NT) {
       const int l2 = idx / NN, sp = idx - l2 * NN;
-      ElemGeo<T, N, OTF> G;
-      G.load(md, e0 + l2, zt);
-      const T iJ = G.inv_jac(sp % N, sp / N);
+      const T iJ = ElemGeo<T, N, OTF>::inv_jac_t0(md, sEF[l2], sEG + l2 * 8, sp % N, sp / N);
       const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
       if (MODE == MODE_RESIDUAL) {
 #pragma unroll
