@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import small_rotor
+from helpers import small_rotor, small_twin
 from ssd_inputs import fields, meshes
 from ssd_inputs.workloads import FlowParams
 
@@ -28,6 +28,7 @@ def _cases():
         (meshes.couette_mesh(2, 12, 2, 16), 2, visc),
         (meshes.perturb_nodes(meshes.periodic_box_mesh(5, 2.0), 0.2, seed=1), 4, FlowParams()),
         (small_rotor(2), 5, FlowParams(omega=0.5)),
+        (small_twin(omega2=-0.6, shift_L=0.05), 3, FlowParams(omega=0.7)),  # two rotating zones
     ]
 
 
@@ -42,7 +43,7 @@ def test_batch_equals_individual_runs(ssd, precision):
     cases = _cases()
     batch = ssd.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], precision=precision,
                       tune_dt=1e-4)
-    dts = [1e-3, 7e-4, 2e-4, 1e-3, 5e-4]
+    dts = [1e-3, 7e-4, 2e-4, 1e-3, 5e-4, 8e-4]
     starts = []
     for k, (m, p, prm) in enumerate(cases):
         q = _state(batch.cases[k], k, prm)
