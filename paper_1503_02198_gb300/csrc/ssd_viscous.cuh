@@ -177,6 +177,7 @@ struct GradCfg {
   static constexpr int O_BAR = ((O_DE + EPB * QE) + 15) / 16 * 16;
   static constexpr int SMEM = O_BAR + 2 * 8;
   static_assert(QE % 16 == 0 && CE % 16 == 0, "bulk-copy sizes and alignment");
+  static_assert(SMEM <= 227 * 1024, "dynamic shared memory of one CTA");
 };
 
 // SP gradients GSP [E][8][N][N] and gradient traces GTR [E][4 faces][8][N]
@@ -378,6 +379,7 @@ struct VisVolCfg {
   static constexpr int O_BAR = ((O_RG + EPB * QE) + 15) / 16 * 16;
   static constexpr int SMEM = O_BAR + 2 * 8;
   static_assert(QE % 16 == 0 && GE % 16 == 0 && CE % 16 == 0, "bulk-copy sizes and alignment");
+  static_assert(SMEM <= 227 * 1024, "dynamic shared memory of one CTA");
   // resident CTAs per SM the register budget is set for: the smaller of the
   // warp target of VisCfg and what the shared memory admits
   static constexpr int BY_SMEM = 228 * 1024 / (SMEM + 1024);
