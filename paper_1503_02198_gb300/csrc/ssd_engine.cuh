@@ -1244,7 +1244,6 @@ struct VolCfg {
   static_assert((SE * (int)sizeof(T)) % 16 == 0 && (SC * (int)sizeof(T)) % 16 == 0, "bulk-copy alignment");
   static_assert(QE % 16 == 0 && CE % 16 == 0 && QB % 16 == 0, "bulk-copy sizes");
   static_assert(EPB <= 32, "one warp-0 lane per element");
-  static_assert(SMEM <= 227 * 1024, "dynamic shared memory of one CTA");
   // resident CTAs per SM the register budget is set for (228 KB of shared
   // memory per SM, 1 KB of it reserved per CTA)
   static constexpr int MINB = (228 * 1024 / (SMEM + 1024)) < 8 ? (228 * 1024 / (SMEM + 1024)) : 8;
