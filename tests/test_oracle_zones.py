@@ -199,3 +199,22 @@ def test_four_zones_conserve_and_a_fifth_is_rejected(oracle_mod):
         assert len(o.mortars(0.41, zone)["lf"]) > 0
     with pytest.raises(ValueError):
         oracle_mod.Oracle(small_row(5, (-0.6, 0.3, 1.1, 0.2)), 3, FlowParams(omega=0.9))
+
+
+def test_full_twin_rotor_workload_mesh(oracle_mod):
+    # the two-zone bench workload: valid for the oracle (every face classified,
+    # both interfaces closed), positive Jacobian at every SP, each interface's
+    # mortars tiling its faces
+    from ssd_inputs.workloads import build_workload
+    w = build_workload("twin_rotor_n6")
+    m = w.mesh
+    assert len(m["elem_nodes"]) == 123450 and len(m["zones"]) == 1
+    o = oracle_mod.Oracle(m, 3, w.params)
+    assert (o.sp_jacobian() > 0).all()
+    for zone in (1, 2):
+        mo = o.mortars(0.37, zone)
+        zl = m if zone == 1 else m["zones"][0]
+        nL = len(zl["ifaces_L"])
+        sums = np.zeros(nL)
+        np.add.at(sums, mo["lf"], mo["sL"])
+        np.testing.assert_allclose(sums, 1.0, atol=1e-13)
