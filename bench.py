@@ -275,47 +275,63 @@ def run_reference(args):
 
 def run_batched(ssd, ncases, steps):
     """Batched form: a seeded mix of independent cases (Couette, rotor and
-    rotating-ellipse families, 1k-8k cells, p = 2..5, omega in [0.1, 1], FP32
-    path) advanced by one CUDA-graph launch per step, against the same cases
-    stepped one after another with their own graphs.  Wall-clock time around
+    rotating-ellipse families, 1k-8k cells, p = 2..5, omega in [0.1, 1])
+    advanced by one CUDA-graph launch per step, on the FP32 path and, for the
+    speedup and the accuracy, on the FP64 path; against the same FP32 cases
+    stepped through their own handles (each its own graph and stream, issued
+    one after another, so they run concurrently).  Wall-clock time around
     synchronised calls."""
     from ssd_inputs.workloads import batch_cases
     cases = batch_cases(ncases)
-    b = ssd.Batch([c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases],
-                  precision=ssd.SD_PREC_FP32, tune_dt=1e-5)
-    states = []
-    for k, (name, mesh, p, prm, dt) in enumerate(cases):
-        if name.startswith("ellipse"):
-            q = b.cases[k].state_from(lambda x, y, prm=prm: fields.uniform(x, y, rho=prm.rho_inf, u=prm.u_inf,
-                                                                          v=prm.v_inf, p=prm.p_inf))
-        elif prm.viscous:
-            q = b.cases[k].state_from(lambda x, y, prm=prm: fields.uniform(x, y, rho=1.0, p=prm.Rgas))
-        else:
-            q = b.cases[k].state_from(lambda x, y: fields.isentropic_vortex(x, y))
-        states.append(q)
-        b.cases[k].sd_set_state(q)
     dts = [c[4] for c in cases]
-    dofs = sum(c.n_dofs for c in b.cases)
-    b.sd_batch_step(dts, 5)
-    b.sd_batch_sync()
-    t0 = time.perf_counter()
-    b.sd_batch_step(dts, steps)
-    b.sd_batch_sync()
-    el = time.perf_counter() - t0
-    # the same cases, one after another, each with its own graph
-    for k, c in enumerate(b.cases):
-        c.sd_set_state(states[k])
-    t1 = time.perf_counter()
-    for k, c in enumerate(b.cases):
-        c.sd_step(dts[k], steps)
-    for c in b.cases:
-        c.sd_sync()
-    el_sep = time.perf_counter() - t1
-    b.close()
+
+    def start(b, k, name, prm):
+        if name.startswith("ellipse"):
+            return b.cases[k].state_from(lambda x, y: fields.uniform(x, y, rho=prm.rho_inf, u=prm.u_inf,
+                                                                    v=prm.v_inf, p=prm.p_inf))
+        if prm.viscous:
+            return b.cases[k].state_from(lambda x, y: fields.uniform(x, y, rho=1.0, p=prm.Rgas))
+        return b.cases[k].state_from(lambda x, y: fields.isentropic_vortex(x, y))
+
+    def run(precision, separate=False):
+        b = ssd.Batch([c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases], precision=precision,
+                      tune_dt=1e-5)
+        states = [start(b, k, c[0], c[3]) for k, c in enumerate(cases)]
+        for k, q in enumerate(states):
+            b.cases[k].sd_set_state(q)
+        dofs = sum(c.n_dofs for c in b.cases)
+        b.sd_batch_step(dts, 5)
+        b.sd_batch_sync()
+        for k, q in enumerate(states):
+            b.cases[k].sd_set_state(q)
+            b.cases[k].sd_set_time(0.0)
+        t0 = time.perf_counter()
+        b.sd_batch_step(dts, steps)
+        b.sd_batch_sync()
+        el = time.perf_counter() - t0
+        finals = [c.sd_get_state() for c in b.cases]
+        el_sep = None
+        if separate:
+            for k, c in enumerate(b.cases):
+                c.sd_set_state(states[k])
+            t1 = time.perf_counter()
+            for k, c in enumerate(b.cases):
+                c.sd_step(dts[k], steps)
+            for c in b.cases:
+                c.sd_sync()
+            el_sep = time.perf_counter() - t1
+        b.close()
+        return dofs, el, el_sep, finals
+
+    dofs, el, el_sep, q32 = run(ssd.SD_PREC_FP32, separate=True)
+    _, el64, _, q64 = run(ssd.SD_PREC_FP64)
+    worst = max(float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2))) for a, b in zip(q32, q64))
     return {"value": dofs * steps / el, "unit": "DOF-updates/s", "cases": len(cases), "dofs": dofs,
             "cells": int(sum(len(c[1]["elem_nodes"]) for c in cases)), "steps": steps,
-            "ms_per_step": el / steps * 1e3, "separate_ms_per_step": el_sep / steps * 1e3,
-            "speedup_vs_separate": el_sep / el, "precision": "f32", "autotuned": True,
+            "ms_per_step": el / steps * 1e3, "precision": "f32", "autotuned": True,
+            "fp64_value": dofs * steps / el64, "fp64_ms_per_step": el64 / steps * 1e3,
+            "speedup_vs_fp64": el64 / el, "fp32_rel_l2_vs_fp64_worst_case": worst,
+            "concurrent_handles_ms_per_step": el_sep / steps * 1e3, "speedup_vs_concurrent_handles": el_sep / el,
             "timing": "wall clock around synchronised calls"}
 
 
