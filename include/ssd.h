@@ -177,10 +177,14 @@ const char *sd_last_error(const sd_handle *h);
  * (E * 4 * N * N). Any pointer may be NULL. */
 int sd_info(const sd_handle *h, int *n_elems, int *N, long long *n_dofs);
 
-/* Copy the physical state Q (layout above) into the solver. */
+/* Copy the physical state Q (layout above) into the solver.  on_device: Q is
+ * device memory; else host memory.  A pinned host buffer (cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister) is read by the device directly; pageable
+ * memory goes through a staged copy.  Returns once Q may be reused. */
 int sd_set_state(sd_handle *h, const double *Q, int on_device);
 
-/* Copy the current state out (synchronises). */
+/* Copy the current state out (synchronises); host buffers as for
+ * sd_set_state (a pinned one is written by the device directly). */
 int sd_get_state(sd_handle *h, double *Q, int on_device);
 
 /* Set / read the solution time t (the rotation angle is omega * t). */
