@@ -55,6 +55,8 @@ def lib():
         L.or_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
         L.or_lagrange.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
         L.or_projection.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
+        L.or_rusanov.argtypes = [ctypes.c_double, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 _dp]
         L.or_face_info.restype = ctypes.c_char_p
         L.or_face_info.argtypes = [ctypes.c_void_p, _ip, _ip, _ip]
         L.or_mortar_list.restype = ctypes.c_int
@@ -99,6 +101,16 @@ def projection(N: int, o: float, s: float):
     Pf, Pb = np.zeros((N, N)), np.zeros((N, N))
     lib().or_projection(N, o, s, _d(Pf), _d(Pb))
     return Pf, Pb
+
+
+def rusanov(gamma, qL, qR, n, vgn=0.0):
+    """Rusanov common normal flux of the oracle (Sec. 3.1) for conservative
+    states qL, qR, unit normal n from L to R and normal grid velocity vgn."""
+    qL = np.ascontiguousarray(qL, dtype=np.float64)
+    qR = np.ascontiguousarray(qR, dtype=np.float64)
+    out = np.zeros(4)
+    lib().or_rusanov(float(gamma), _d(qL), _d(qR), float(n[0]), float(n[1]), float(vgn), _d(out))
+    return out
 
 
 def rk54_tableau():

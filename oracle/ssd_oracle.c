@@ -455,6 +455,16 @@ void or_projection(int N, double o, double s, double *Pf, double *Pb) {
     }
 }
 
+/* Rusanov common flux for tests: gamma, the two states (rho, rho u, rho v, E),
+ * the unit normal from L to R and the normal grid velocity -> Fn[4]. */
+void or_rusanov(double gamma, const double *qL, const double *qR, double nx, double ny, double vgn, double *Fn) {
+  or_params p;
+  memset(&p, 0, sizeof p);
+  p.gamma = gamma;
+  p.Rgas = 1.0;
+  rusanov(&p, qL, qR, nx, ny, vgn, Fn);
+}
+
 /* ------------------------------------------------------------------------ */
 /* mesh set-up: face table, interface lists                                   */
 /* ------------------------------------------------------------------------ */

@@ -61,3 +61,18 @@ def rel_err(a, b):
     num = np.abs(a - b).max(axis=(0, 2, 3))
     den = np.abs(b).max(axis=(0, 2, 3))
     return num / den
+
+
+def random_cell_states(E, seed, gamma=1.4):
+    """A seeded random constant state per cell, [E][4] conservative (rho, p
+    in [0.5, 1.5], u, v in [-0.5, 0.5]): O(1) jumps on every face."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rho, u, v, p = (rng.uniform(0.5, 1.5, E), rng.uniform(-0.5, 0.5, E), rng.uniform(-0.5, 0.5, E),
+                    rng.uniform(0.5, 1.5, E))
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)], axis=1)
+
+
+def piecewise_constant(Qc, N):
+    """[E][4][N][N] state holding Qc[e] at every solution point of cell e."""
+    E = len(Qc)
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(Qc)[:, :, None, None], (E, 4, N, N)))
