@@ -55,13 +55,29 @@
  *     stationary zone 0 across its own circular sliding interface; every
  *     interface is coupled by the procedure of Sec. 3.2 on its own.
  */
-#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
-#define OR_MAXN 12
+/* The real type of every value and operation.  The default build is FP64
+ * (real = double), the oracle proper.  With -DOR_REAL_LONG the same source is
+ * compiled with real = long double (64-bit significand on x86-64, IEEE
+ * binary128 on AArch64): an extended-precision reference that shows how much
+ * of the difference between two FP64 evaluations each one carries.  The math
+ * functions are the type-generic ones of <tgmath.h>, so the FP64 build calls
+ * the same double functions as a plain <math.h> build. */
+#ifdef OR_REAL_LONG
+typedef long double real;
+#define OR_PI 3.141592653589793238462643383279502884L
+#else
+typedef double real;
 #define OR_PI 3.14159265358979323846
+#endif
+#include <tgmath.h>
+#undef I /* <complex.h> names the imaginary unit I; the code uses it for an interface */
+#undef complex
+
+#define OR_MAXN 12
 #define OR_MAXZ 4 /* rotating zones */
 
 /* ------------------------------------------------------------------------ */
@@ -69,9 +85,9 @@
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-  double gamma, Rgas, mu, prandtl, omega, T_wall;
+  real gamma, Rgas, mu, prandtl, omega, T_wall;
   int viscous;
-  double rho_inf, u_inf, v_inf, p_inf; /* free stream (inlet state, outlet pressure) */
+  real rho_inf, u_inf, v_inf, p_inf; /* free stream (inlet state, outlet pressure) */
 } or_params;
 
 /* boundary tags */
@@ -85,20 +101,20 @@ enum { FK_NONE = -1, FK_CONF = 0, FK_PERIODIC = 1, FK_BOUNDARY = 2, FK_IFACE_L =
  * (Sec. 2.2), and its circular sliding interface of radius rI with the
  * stationary zone 0 (Sec. 3.2), the rotating cells being the L side. */
 typedef struct {
-  double cx, cy, rI, omega;
+  real cx, cy, rI, omega;
   int nL, nR;                /* interface faces, sorted counter-clockwise */
   int *Lef, *Ref;            /* element-face index */
-  double *La, *Lw, *Ra, *Rw; /* CCW start angle at t = 0 (in [0, 2pi)) and angular width */
+  real *La, *Lw, *Ra, *Rw; /* CCW start angle at t = 0 (in [0, 2pi)) and angular width */
   int *Lrev, *Rrev;          /* 1 if the face parameter runs clockwise */
 } or_iface;
 
 typedef struct {
   int N;
-  double Xs[OR_MAXN];     /* solution points X_s, s = 1..N (stored 0-based) */
-  double Xf[OR_MAXN + 1]; /* flux points X_{s+1/2}, s = 0..N */
+  real Xs[OR_MAXN];     /* solution points X_s, s = 1..N (stored 0-based) */
+  real Xf[OR_MAXN + 1]; /* flux points X_{s+1/2}, s = 0..N */
   /* mesh */
   int nn, ne;
-  double *xy;
+  real *xy;
   int *en, *zone, *arc;
   int *enode; /* [E][4][2]: edge nodes at face parameter 1/3, 2/3 of cubic edges, or NULL */
   int *azone; /* [E]: the zone whose centre the cell's arc edges are drawn about */
@@ -115,11 +131,11 @@ typedef struct {
 /* ------------------------------------------------------------------------ */
 
 /* Legendre polynomial P_n and derivative on [-1, 1] (three-term recurrence) */
-static void legendre(int n, double x, double *P, double *dP) {
-  double p0 = 1.0, p1 = x;
+static void legendre(int n, real x, real *P, real *dP) {
+  real p0 = 1.0, p1 = x;
   if (n == 0) { *P = 1.0; *dP = 0.0; return; }
   for (int k = 2; k <= n; ++k) {
-    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    real p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
     p0 = p1;
     p1 = p2;
   }
@@ -129,26 +145,26 @@ static void legendre(int n, double x, double *P, double *dP) {
 
 /* roots of P_n on [-1,1] in ascending order, by Newton iteration; weights of
  * the Gauss-Legendre rule 2 / ((1 - x^2) P_n'(x)^2) */
-static void gauss_legendre(int n, double *x, double *w) {
+static void gauss_legendre(int n, real *x, real *w) {
   for (int k = 1; k <= n; ++k) {
-    double r = cos(OR_PI * (k - 0.25) / (n + 0.5));
+    real r = cos(OR_PI * (k - 0.25) / (n + 0.5));
     for (int it = 0; it < 200; ++it) {
-      double P, dP;
+      real P, dP;
       legendre(n, r, &P, &dP);
-      double dr = P / dP;
+      real dr = P / dP;
       r -= dr;
       if (fabs(dr) < 1e-17) break;
     }
-    double P, dP;
+    real P, dP;
     legendre(n, r, &P, &dP);
     x[n - k] = r; /* cos(...) decreases with k */
     w[n - k] = 2.0 / ((1.0 - r * r) * dP * dP);
   }
 }
 
-static void make_points(int N, double *Xs, double *Xf) {
+static void make_points(int N, real *Xs, real *Xf) {
   for (int s = 1; s <= N; ++s) Xs[s - 1] = 0.5 * (1.0 - cos((2.0 * s - 1.0) * OR_PI / (2.0 * N)));
-  double z[OR_MAXN], w[OR_MAXN];
+  real z[OR_MAXN], w[OR_MAXN];
   Xf[0] = 0.0;
   Xf[N] = 1.0;
   if (N >= 2) {
@@ -158,18 +174,18 @@ static void make_points(int N, double *Xs, double *Xf) {
 }
 
 /* Lagrange basis on nodes[0..n-1], product formula (Eqs. hbasis / lbasis) */
-static double lag(const double *nodes, int n, int i, double x) {
-  double v = 1.0;
+static real lag(const real *nodes, int n, int i, real x) {
+  real v = 1.0;
   for (int s = 0; s < n; ++s)
     if (s != i) v *= (x - nodes[s]) / (nodes[i] - nodes[s]);
   return v;
 }
 
-static double lag_d(const double *nodes, int n, int i, double x) {
-  double sum = 0.0;
+static real lag_d(const real *nodes, int n, int i, real x) {
+  real sum = 0.0;
   for (int m = 0; m < n; ++m) {
     if (m == i) continue;
-    double v = 1.0 / (nodes[i] - nodes[m]);
+    real v = 1.0 / (nodes[i] - nodes[m]);
     for (int s = 0; s < n; ++s)
       if (s != i && s != m) v *= (x - nodes[s]) / (nodes[i] - nodes[s]);
     sum += v;
@@ -190,17 +206,17 @@ static const int FACE_B[4] = {1, 2, 2, 3}; /* end corner */
  * e(phi0 + d) - e(phi0) = 2 sin(d/2) (-sin(phi0 + d/2), cos(phi0 + d/2)),
  * so the offset keeps full relative precision for short arcs far from the
  * centre. */
-static void edge_curve(const or_mesh *m, double cx, double cy, double px, double py, double qx, double qy, int arc,
-                       const int *mid, double u, double *ox, double *oy, double *dx, double *dy) {
+static void edge_curve(const or_mesh *m, real cx, real cy, real px, real py, real qx, real qy, int arc,
+                       const int *mid, real u, real *ox, real *oy, real *dx, real *dy) {
   if (arc == EDGE_CUBIC) {
     /* cubic Lagrange interpolation through P, M1, M2, Q at u = 0, 1/3, 2/3, 1,
      * written as offsets from P */
-    static const double un[4] = {0.0, 1.0 / 3.0, 2.0 / 3.0, 1.0};
-    double Dx[4] = {0.0, m->xy[2 * mid[0]] - px, m->xy[2 * mid[1]] - px, qx - px};
-    double Dy[4] = {0.0, m->xy[2 * mid[0] + 1] - py, m->xy[2 * mid[1] + 1] - py, qy - py};
+    static const real un[4] = {0.0, 1.0 / 3.0, 2.0 / 3.0, 1.0};
+    real Dx[4] = {0.0, m->xy[2 * mid[0]] - px, m->xy[2 * mid[1]] - px, qx - px};
+    real Dy[4] = {0.0, m->xy[2 * mid[0] + 1] - py, m->xy[2 * mid[1] + 1] - py, qy - py};
     *ox = *oy = *dx = *dy = 0.0;
     for (int k = 1; k < 4; ++k) {
-      double l = lag(un, 4, k, u), ld = lag_d(un, 4, k, u);
+      real l = lag(un, 4, k, u), ld = lag_d(un, 4, k, u);
       *ox += l * Dx[k];
       *oy += l * Dy[k];
       *dx += ld * Dx[k];
@@ -215,14 +231,14 @@ static void edge_curve(const or_mesh *m, double cx, double cy, double px, double
     *dy = qy - py;
     return;
   }
-  double ax = px - cx, ay = py - cy, bx = qx - cx, by = qy - cy;
-  double r = sqrt(ax * ax + ay * ay);
-  double phi0 = atan2(ay, ax);
-  double dphi = atan2(ax * by - ay * bx, ax * bx + ay * by);
-  double half = 0.5 * u * dphi, chord = 2.0 * r * sin(half);
+  real ax = px - cx, ay = py - cy, bx = qx - cx, by = qy - cy;
+  real r = sqrt(ax * ax + ay * ay);
+  real phi0 = atan2(ay, ax);
+  real dphi = atan2(ax * by - ay * bx, ax * bx + ay * by);
+  real half = 0.5 * u * dphi, chord = 2.0 * r * sin(half);
   *ox = -chord * sin(phi0 + half);
   *oy = chord * cos(phi0 + half);
-  double phi = phi0 + u * dphi;
+  real phi = phi0 + u * dphi;
   *dx = -r * dphi * sin(phi);
   *dy = r * dphi * cos(phi);
 }
@@ -232,22 +248,22 @@ static void edge_curve(const or_mesh *m, double cx, double cy, double px, double
  * edge is reproduced exactly.  It is evaluated about the cell's first corner
  * (an exact shift in real arithmetic) so that the round-off of the metrics
  * scales with the cell size rather than with the coordinates. */
-static void map_t0(const or_mesh *m, int e, double xi, double eta, double *g) {
+static void map_t0(const or_mesh *m, int e, real xi, real eta, real *g) {
   const int *n = m->en + 4 * e;
-  double X[4], Y[4];
+  real X[4], Y[4];
   for (int k = 0; k < 4; ++k) {
     X[k] = m->xy[2 * n[k]];
     Y[k] = m->xy[2 * n[k] + 1];
   }
-  double U[4], V[4]; /* corners relative to corner 0 */
+  real U[4], V[4]; /* corners relative to corner 0 */
   for (int k = 0; k < 4; ++k) {
     U[k] = X[k] - X[0];
     V[k] = Y[k] - Y[0];
   }
   const int *a = m->arc + 4 * e;
   const int *md = m->enode ? m->enode + 8 * e : NULL;
-  const double cx = m->zi[m->azone[e] - 1].cx, cy = m->zi[m->azone[e] - 1].cy; /* centre of arc edges */
-  double Bx, By, dBx, dBy, Tx, Ty, dTx, dTy, Lx, Ly, dLx, dLy, Rx, Ry, dRx, dRy;
+  const real cx = m->zi[m->azone[e] - 1].cx, cy = m->zi[m->azone[e] - 1].cy; /* centre of arc edges */
+  real Bx, By, dBx, dBy, Tx, Ty, dTx, dTy, Lx, Ly, dLx, dLy, Rx, Ry, dRx, dRy;
   edge_curve(m, cx, cy, X[0], Y[0], X[1], Y[1], a[0], md ? md + 0 : NULL, xi, &Bx, &By, &dBx, &dBy);  /* f0 */
   edge_curve(m, cx, cy, X[1], Y[1], X[2], Y[2], a[1], md ? md + 2 : NULL, eta, &Rx, &Ry, &dRx, &dRy); /* f1 */
   edge_curve(m, cx, cy, X[3], Y[3], X[2], Y[2], a[2], md ? md + 4 : NULL, xi, &Tx, &Ty, &dTx, &dTy);  /* f2 */
@@ -255,30 +271,30 @@ static void map_t0(const or_mesh *m, int e, double xi, double eta, double *g) {
   /* edge points relative to corner 0 */
   Rx += U[1]; Ry += V[1];
   Tx += U[3]; Ty += V[3];
-  double x = (1 - eta) * Bx + eta * Tx + (1 - xi) * Lx + xi * Rx -
+  real x = (1 - eta) * Bx + eta * Tx + (1 - xi) * Lx + xi * Rx -
              (xi * (1 - eta) * U[1] + xi * eta * U[2] + (1 - xi) * eta * U[3]);
-  double y = (1 - eta) * By + eta * Ty + (1 - xi) * Ly + xi * Ry -
+  real y = (1 - eta) * By + eta * Ty + (1 - xi) * Ly + xi * Ry -
              (xi * (1 - eta) * V[1] + xi * eta * V[2] + (1 - xi) * eta * V[3]);
-  double x_xi = (1 - eta) * dBx + eta * dTx - Lx + Rx - ((1 - eta) * U[1] + eta * U[2] - eta * U[3]);
-  double y_xi = (1 - eta) * dBy + eta * dTy - Ly + Ry - ((1 - eta) * V[1] + eta * V[2] - eta * V[3]);
-  double x_eta = -Bx + Tx + (1 - xi) * dLx + xi * dRx - (-xi * U[1] + xi * U[2] + (1 - xi) * U[3]);
-  double y_eta = -By + Ty + (1 - xi) * dLy + xi * dRy - (-xi * V[1] + xi * V[2] + (1 - xi) * V[3]);
+  real x_xi = (1 - eta) * dBx + eta * dTx - Lx + Rx - ((1 - eta) * U[1] + eta * U[2] - eta * U[3]);
+  real y_xi = (1 - eta) * dBy + eta * dTy - Ly + Ry - ((1 - eta) * V[1] + eta * V[2] - eta * V[3]);
+  real x_eta = -Bx + Tx + (1 - xi) * dLx + xi * dRx - (-xi * U[1] + xi * U[2] + (1 - xi) * U[3]);
+  real y_eta = -By + Ty + (1 - xi) * dLy + xi * dRy - (-xi * V[1] + xi * V[2] + (1 - xi) * V[3]);
   g[0] = X[0] + x; g[1] = Y[0] + y; g[2] = x_xi; g[3] = y_xi; g[4] = x_eta; g[5] = y_eta;
 }
 
 /* Map at time t: cells of rotating zone z are rotated rigidly about the
  * zone's centre by theta = omega_z t (Sec. 2.2: coordinates updated
  * analytically). */
-static void map_at(const or_mesh *m, int e, double xi, double eta, double t, double *g) {
+static void map_at(const or_mesh *m, int e, real xi, real eta, real t, real *g) {
   map_t0(m, e, xi, eta, g);
   if (m->zone[e] >= 1) {
     const or_iface *Z = &m->zi[m->zone[e] - 1];
-    double th = Z->omega * t, c = cos(th), s = sin(th);
-    double dx = g[0] - Z->cx, dy = g[1] - Z->cy;
+    real th = Z->omega * t, c = cos(th), s = sin(th);
+    real dx = g[0] - Z->cx, dy = g[1] - Z->cy;
     g[0] = Z->cx + c * dx - s * dy;
     g[1] = Z->cy + s * dx + c * dy;
     for (int k = 2; k < 6; k += 2) {
-      double vx = g[k], vy = g[k + 1];
+      real vx = g[k], vy = g[k + 1];
       g[k] = c * vx - s * vy;
       g[k + 1] = s * vx + c * vy;
     }
@@ -286,7 +302,7 @@ static void map_at(const or_mesh *m, int e, double xi, double eta, double t, dou
 }
 
 /* grid velocity (u_g, v_g) = omega_z x (r - centre_z) on rotating zone z, 0 elsewhere */
-static void grid_velocity(const or_mesh *m, int e, double x, double y, double *ug, double *vg) {
+static void grid_velocity(const or_mesh *m, int e, real x, real y, real *ug, real *vg) {
   if (m->zone[e] >= 1) {
     const or_iface *Z = &m->zi[m->zone[e] - 1];
     *ug = -Z->omega * (y - Z->cy);
@@ -301,13 +317,13 @@ static void grid_velocity(const or_mesh *m, int e, double x, double y, double *u
 /* Sec. 2: physical fluxes                                                    */
 /* ------------------------------------------------------------------------ */
 
-static double pressure(const or_params *p, const double *q) {
+static real pressure(const or_params *p, const real *q) {
   return (p->gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
 }
 
 /* inviscid fluxes with grid-velocity terms (Sec. 2.2) */
-static void inviscid_flux(const or_params *p, const double *q, double ug, double vg, double *F, double *G) {
-  double u = q[1] / q[0], v = q[2] / q[0], pr = pressure(p, q);
+static void inviscid_flux(const or_params *p, const real *q, real ug, real vg, real *F, real *G) {
+  real u = q[1] / q[0], v = q[2] / q[0], pr = pressure(p, q);
   F[0] = q[1];
   F[1] = q[1] * u + pr;
   F[2] = q[1] * v;
@@ -324,22 +340,22 @@ static void inviscid_flux(const or_params *p, const double *q, double ug, double
 
 /* viscous fluxes (Sec. 2.1) from Q and the physical gradients dQ/dx, dQ/dy of
  * the conservative variables; includes the leading minus sign of the paper */
-static void viscous_flux(const or_params *p, const double *q, const double *qx, const double *qy, double *F,
-                         double *G) {
-  double rho = q[0], u = q[1] / rho, v = q[2] / rho;
-  double ux = (qx[1] - u * qx[0]) / rho, uy = (qy[1] - u * qy[0]) / rho;
-  double vx = (qx[2] - v * qx[0]) / rho, vy = (qy[2] - v * qy[0]) / rho;
-  double pr = pressure(p, q);
-  double T = pr / (rho * p->Rgas);
-  double px = (p->gamma - 1.0) * (qx[3] - (u * qx[1] + v * qx[2] - 0.5 * (u * u + v * v) * qx[0]));
-  double py = (p->gamma - 1.0) * (qy[3] - (u * qy[1] + v * qy[2] - 0.5 * (u * u + v * v) * qy[0]));
-  double Tx = (px - p->Rgas * T * qx[0]) / (rho * p->Rgas);
-  double Ty = (py - p->Rgas * T * qy[0]) / (rho * p->Rgas);
-  double mu = p->mu, lam = -2.0 / 3.0 * mu;
-  double kc = mu * p->gamma * p->Rgas / ((p->gamma - 1.0) * p->prandtl);
-  double txx = 2.0 * mu * ux + lam * (ux + vy);
-  double tyy = 2.0 * mu * vy + lam * (ux + vy);
-  double txy = mu * (uy + vx);
+static void viscous_flux(const or_params *p, const real *q, const real *qx, const real *qy, real *F,
+                         real *G) {
+  real rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  real ux = (qx[1] - u * qx[0]) / rho, uy = (qy[1] - u * qy[0]) / rho;
+  real vx = (qx[2] - v * qx[0]) / rho, vy = (qy[2] - v * qy[0]) / rho;
+  real pr = pressure(p, q);
+  real T = pr / (rho * p->Rgas);
+  real px = (p->gamma - 1.0) * (qx[3] - (u * qx[1] + v * qx[2] - 0.5 * (u * u + v * v) * qx[0]));
+  real py = (p->gamma - 1.0) * (qy[3] - (u * qy[1] + v * qy[2] - 0.5 * (u * u + v * v) * qy[0]));
+  real Tx = (px - p->Rgas * T * qx[0]) / (rho * p->Rgas);
+  real Ty = (py - p->Rgas * T * qy[0]) / (rho * p->Rgas);
+  real mu = p->mu, lam = -2.0 / 3.0 * mu;
+  real kc = mu * p->gamma * p->Rgas / ((p->gamma - 1.0) * p->prandtl);
+  real txx = 2.0 * mu * ux + lam * (ux + vy);
+  real tyy = 2.0 * mu * vy + lam * (ux + vy);
+  real txy = mu * (uy + vx);
   F[0] = 0.0;
   F[1] = -txx;
   F[2] = -txy;
@@ -352,31 +368,31 @@ static void viscous_flux(const or_params *p, const double *q, const double *qx, 
 
 /* conductive heat flux -k grad T from Q and its gradients (the part of the
  * energy viscous flux an adiabatic wall removes): returns k T_x, k T_y */
-static void conduction(const or_params *p, const double *q, const double *qx, const double *qy, double *kTx,
-                       double *kTy) {
-  double rho = q[0], u = q[1] / rho, v = q[2] / rho;
-  double T = pressure(p, q) / (rho * p->Rgas);
-  double px = (p->gamma - 1.0) * (qx[3] - (u * qx[1] + v * qx[2] - 0.5 * (u * u + v * v) * qx[0]));
-  double py = (p->gamma - 1.0) * (qy[3] - (u * qy[1] + v * qy[2] - 0.5 * (u * u + v * v) * qy[0]));
-  double kc = p->mu * p->gamma * p->Rgas / ((p->gamma - 1.0) * p->prandtl);
+static void conduction(const or_params *p, const real *q, const real *qx, const real *qy, real *kTx,
+                       real *kTy) {
+  real rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  real T = pressure(p, q) / (rho * p->Rgas);
+  real px = (p->gamma - 1.0) * (qx[3] - (u * qx[1] + v * qx[2] - 0.5 * (u * u + v * v) * qx[0]));
+  real py = (p->gamma - 1.0) * (qy[3] - (u * qy[1] + v * qy[2] - 0.5 * (u * u + v * v) * qy[0]));
+  real kc = p->mu * p->gamma * p->Rgas / ((p->gamma - 1.0) * p->prandtl);
   *kTx = kc * (px - p->Rgas * T * qx[0]) / (rho * p->Rgas);
   *kTy = kc * (py - p->Rgas * T * qy[0]) / (rho * p->Rgas);
 }
 
 /* Rusanov common normal flux (Sec. 3.1) across a face with unit normal n
  * pointing from L to R; vgn is the grid velocity normal to the face. */
-static void rusanov(const or_params *p, const double *qL, const double *qR, double nx, double ny, double vgn,
-                    double *Fn) {
-  double FL[4], GL[4], FR[4], GR[4];
+static void rusanov(const or_params *p, const real *qL, const real *qR, real nx, real ny, real vgn,
+                    real *Fn) {
+  real FL[4], GL[4], FR[4], GR[4];
   inviscid_flux(p, qL, 0.0, 0.0, FL, GL);
   inviscid_flux(p, qR, 0.0, 0.0, FR, GR);
-  double unL = (qL[1] * nx + qL[2] * ny) / qL[0], unR = (qR[1] * nx + qR[2] * ny) / qR[0];
-  double cL = sqrt(p->gamma * pressure(p, qL) / qL[0]), cR = sqrt(p->gamma * pressure(p, qR) / qR[0]);
-  double lamL = fabs(unL - vgn) + cL, lamR = fabs(unR - vgn) + cR;
-  double lam = lamL > lamR ? lamL : lamR;
+  real unL = (qL[1] * nx + qL[2] * ny) / qL[0], unR = (qR[1] * nx + qR[2] * ny) / qR[0];
+  real cL = sqrt(p->gamma * pressure(p, qL) / qL[0]), cR = sqrt(p->gamma * pressure(p, qR) / qR[0]);
+  real lamL = fabs(unL - vgn) + cL, lamR = fabs(unR - vgn) + cR;
+  real lam = lamL > lamR ? lamL : lamR;
   for (int k = 0; k < 4; ++k) {
-    double fL = FL[k] * nx + GL[k] * ny - vgn * qL[k];
-    double fR = FR[k] * nx + GR[k] * ny - vgn * qR[k];
+    real fL = FL[k] * nx + GL[k] * ny - vgn * qL[k];
+    real fR = FR[k] * nx + GR[k] * ny - vgn * qR[k];
     Fn[k] = 0.5 * (fL + fR) - 0.5 * lam * (qR[k] - qL[k]);
   }
 }
@@ -388,15 +404,15 @@ static void rusanov(const or_params *p, const double *qL, const double *qR, doub
 /* M_ij = int_0^1 h_i h_j dz and S_ij = int_0^1 h_i(o + s z) h_j(z) dz (Eqs.
  * mortarM, mortarS), by (N+2)-point Gauss-Legendre on [0,1] (exact: the
  * integrands have degree 2N-2). */
-static void mortar_MS(int N, const double *Xs, double o, double s, double *M, double *S) {
+static void mortar_MS(int N, const real *Xs, real o, real s, real *M, real *S) {
   int nq = N + 2;
-  double z[OR_MAXN + 2], w[OR_MAXN + 2];
+  real z[OR_MAXN + 2], w[OR_MAXN + 2];
   gauss_legendre(nq, z, w);
   for (int i = 0; i < N; ++i)
     for (int j = 0; j < N; ++j) {
-      double mij = 0.0, sij = 0.0;
+      real mij = 0.0, sij = 0.0;
       for (int q = 0; q < nq; ++q) {
-        double zq = 0.5 * (1.0 + z[q]), wq = 0.5 * w[q];
+        real zq = 0.5 * (1.0 + z[q]), wq = 0.5 * w[q];
         mij += wq * lag(Xs, N, i, zq) * lag(Xs, N, j, zq);
         sij += wq * lag(Xs, N, i, o + s * zq) * lag(Xs, N, j, zq);
       }
@@ -406,8 +422,8 @@ static void mortar_MS(int N, const double *Xs, double o, double s, double *M, do
 }
 
 /* inverse of a small dense matrix by Gauss-Jordan with partial pivoting */
-static int invert(int n, const double *A, double *Ainv) {
-  double W[OR_MAXN * 2 * OR_MAXN];
+static int invert(int n, const real *A, real *Ainv) {
+  real W[OR_MAXN * 2 * OR_MAXN];
   int w2 = 2 * n;
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < w2; ++j) W[i * w2 + j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
@@ -418,15 +434,15 @@ static int invert(int n, const double *A, double *Ainv) {
     if (W[piv * w2 + c] == 0.0) return -1;
     if (piv != c)
       for (int j = 0; j < w2; ++j) {
-        double tmp = W[c * w2 + j];
+        real tmp = W[c * w2 + j];
         W[c * w2 + j] = W[piv * w2 + j];
         W[piv * w2 + j] = tmp;
       }
-    double d = W[c * w2 + c];
+    real d = W[c * w2 + c];
     for (int j = 0; j < w2; ++j) W[c * w2 + j] /= d;
     for (int r = 0; r < n; ++r) {
       if (r == c) continue;
-      double f = W[r * w2 + c];
+      real f = W[r * w2 + c];
       for (int j = 0; j < w2; ++j) W[r * w2 + j] -= f * W[c * w2 + j];
     }
   }
@@ -438,14 +454,14 @@ static int invert(int n, const double *A, double *Ainv) {
 /* Projection matrices for a mortar with offset o and scale s relative to a face:
  *   forward  (Eq. prjQ1):  M Q^Xi = S^T Q^Omega  ->  Pf = M^-1 S^T
  *   backward (Eq. prjF1):  M F^Omega = sum_k s_k S_k F^Xi_k  ->  Pb = s M^-1 S  */
-void or_projection(int N, double o, double s, double *Pf, double *Pb) {
-  double Xs[OR_MAXN], Xf[OR_MAXN + 1], M[OR_MAXN * OR_MAXN], S[OR_MAXN * OR_MAXN], Mi[OR_MAXN * OR_MAXN];
+void or_projection(int N, real o, real s, real *Pf, real *Pb) {
+  real Xs[OR_MAXN], Xf[OR_MAXN + 1], M[OR_MAXN * OR_MAXN], S[OR_MAXN * OR_MAXN], Mi[OR_MAXN * OR_MAXN];
   make_points(N, Xs, Xf);
   mortar_MS(N, Xs, o, s, M, S);
   invert(N, M, Mi);
   for (int i = 0; i < N; ++i)
     for (int j = 0; j < N; ++j) {
-      double f = 0.0, b = 0.0;
+      real f = 0.0, b = 0.0;
       for (int k = 0; k < N; ++k) {
         f += Mi[i * N + k] * S[j * N + k];
         b += Mi[i * N + k] * S[k * N + j];
@@ -457,7 +473,7 @@ void or_projection(int N, double o, double s, double *Pf, double *Pb) {
 
 /* Rusanov common flux for tests: gamma, the two states (rho, rho u, rho v, E),
  * the unit normal from L to R and the normal grid velocity -> Fn[4]. */
-void or_rusanov(double gamma, const double *qL, const double *qR, double nx, double ny, double vgn, double *Fn) {
+void or_rusanov(real gamma, const real *qL, const real *qR, real nx, real ny, real vgn, real *Fn) {
   or_params p;
   memset(&p, 0, sizeof p);
   p.gamma = gamma;
@@ -484,30 +500,30 @@ static void face_nodes(const or_mesh *m, int ef, int *na, int *nb) {
   *nb = m->en[4 * e + FACE_B[f]];
 }
 
-static double wrap2pi(double a) {
-  double r = fmod(a, 2.0 * OR_PI);
+static real wrap2pi(real a) {
+  real r = fmod(a, 2.0 * OR_PI);
   if (r < 0) r += 2.0 * OR_PI;
   return r;
 }
 
 /* signed angle in (-pi, pi] */
-static double wrap_pi(double a) {
-  double r = wrap2pi(a + OR_PI) - OR_PI;
+static real wrap_pi(real a) {
+  real r = wrap2pi(a + OR_PI) - OR_PI;
   return r;
 }
 
 static int setup_interface_side(or_mesh *m, const or_iface *I, int n, const int *faces, int kind, int **ef_out,
-                                double **a_out, double **w_out, int **rev_out) {
+                                real **a_out, real **w_out, int **rev_out) {
   int *ef = malloc(sizeof(int) * (n > 0 ? n : 1));
-  double *a = malloc(sizeof(double) * (n > 0 ? n : 1)), *w = malloc(sizeof(double) * (n > 0 ? n : 1));
+  real *a = malloc(sizeof(real) * (n > 0 ? n : 1)), *w = malloc(sizeof(real) * (n > 0 ? n : 1));
   int *rv = malloc(sizeof(int) * (n > 0 ? n : 1));
   for (int k = 0; k < n; ++k) {
     int e = faces[2 * k], f = faces[2 * k + 1], na, nb;
     ef[k] = 4 * e + f;
     face_nodes(m, ef[k], &na, &nb);
-    double pa = atan2(m->xy[2 * na + 1] - I->cy, m->xy[2 * na] - I->cx);
-    double pb = atan2(m->xy[2 * nb + 1] - I->cy, m->xy[2 * nb] - I->cx);
-    double d = wrap_pi(pb - pa);
+    real pa = atan2(m->xy[2 * na + 1] - I->cy, m->xy[2 * na] - I->cx);
+    real pb = atan2(m->xy[2 * nb + 1] - I->cy, m->xy[2 * nb] - I->cx);
+    real d = wrap_pi(pb - pa);
     if (d > 0) {
       a[k] = wrap2pi(pa);
       w[k] = d;
@@ -527,16 +543,16 @@ static int setup_interface_side(or_mesh *m, const or_iface *I, int n, const int 
   /* sort counter-clockwise by start angle (insertion sort; plain) */
   for (int i = 1; i < n; ++i)
     for (int j = i; j > 0 && a[j] < a[j - 1]; --j) {
-      double ta = a[j]; a[j] = a[j - 1]; a[j - 1] = ta;
-      double tw = w[j]; w[j] = w[j - 1]; w[j - 1] = tw;
+      real ta = a[j]; a[j] = a[j - 1]; a[j - 1] = ta;
+      real tw = w[j]; w[j] = w[j - 1]; w[j - 1] = tw;
       int te = ef[j]; ef[j] = ef[j - 1]; ef[j - 1] = te;
       int tr = rv[j]; rv[j] = rv[j - 1]; rv[j - 1] = tr;
     }
-  double total = 0.0;
+  real total = 0.0;
   for (int k = 0; k < n; ++k) total += w[k];
   *ef_out = ef; *a_out = a; *w_out = w; *rev_out = rv;
   if (n > 0 && fabs(total - 2.0 * OR_PI) > 1e-9) {
-    snprintf(m->err, sizeof m->err, "interface side does not close (%.12f)", total);
+    snprintf(m->err, sizeof m->err, "interface side does not close (%.12f)", (double)total);
     return -1;
   }
   *ef_out = ef; *a_out = a; *w_out = w; *rev_out = rv;
@@ -550,18 +566,18 @@ void or_destroy(or_mesh *m);
  * (nL, nR) and their lists, concatenated in xfaces (L then R, zone by zone).
  * azone (or NULL: the cell's own zone, zone 1 for stationary cells) names the
  * zone whose centre a cell's arc edges are drawn about. */
-or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *zone, const int *arc,
+or_mesh *or_create(int nn, const real *xy, int ne, const int *en, const int *zone, const int *arc,
                    const int *enode, int nb,
                    const int *bfaces, int np, const int *pfaces, int nL, const int *Lf, int nR, const int *Rf,
-                   double cx, double cy, double rI, int N, const double *prm_in, int nxz, const double *xz,
+                   real cx, real cy, real rI, int N, const real *prm_in, int nxz, const real *xz,
                    const int *xcnt, const int *xfaces, const int *azone, char *err, int errlen) {
   or_mesh *m = calloc(1, sizeof(or_mesh));
   m->N = N;
   make_points(N, m->Xs, m->Xf);
   m->nn = nn;
   m->ne = ne;
-  m->xy = malloc(sizeof(double) * 2 * nn);
-  memcpy(m->xy, xy, sizeof(double) * 2 * nn);
+  m->xy = malloc(sizeof(real) * 2 * nn);
+  memcpy(m->xy, xy, sizeof(real) * 2 * nn);
   m->en = malloc(sizeof(int) * 4 * ne);
   memcpy(m->en, en, sizeof(int) * 4 * ne);
   m->zone = malloc(sizeof(int) * ne);
@@ -645,10 +661,10 @@ or_mesh *or_create(int nn, const double *xy, int ne, const int *en, const int *z
     int a0, a1, b0, b1;
     face_nodes(m, efA, &a0, &a1);
     face_nodes(m, efB, &b0, &b1);
-    double dx = 0.5 * (m->xy[2 * b0] + m->xy[2 * b1] - m->xy[2 * a0] - m->xy[2 * a1]);
-    double dy = 0.5 * (m->xy[2 * b0 + 1] + m->xy[2 * b1 + 1] - m->xy[2 * a0 + 1] - m->xy[2 * a1 + 1]);
-    double ds = hypot(m->xy[2 * a0] + dx - m->xy[2 * b0], m->xy[2 * a0 + 1] + dy - m->xy[2 * b0 + 1]);
-    double dr = hypot(m->xy[2 * a0] + dx - m->xy[2 * b1], m->xy[2 * a0 + 1] + dy - m->xy[2 * b1 + 1]);
+    real dx = 0.5 * (m->xy[2 * b0] + m->xy[2 * b1] - m->xy[2 * a0] - m->xy[2 * a1]);
+    real dy = 0.5 * (m->xy[2 * b0 + 1] + m->xy[2 * b1 + 1] - m->xy[2 * a0 + 1] - m->xy[2 * a1 + 1]);
+    real ds = hypot(m->xy[2 * a0] + dx - m->xy[2 * b0], m->xy[2 * a0 + 1] + dy - m->xy[2 * b0 + 1]);
+    real dr = hypot(m->xy[2 * a0] + dx - m->xy[2 * b1], m->xy[2 * a0 + 1] + dy - m->xy[2 * b1 + 1]);
     int rev = dr < ds;
     if (m->fkind[efA] != FK_NONE || m->fkind[efB] != FK_NONE) {
       snprintf(m->err, sizeof m->err, "periodic face repeated");
@@ -769,9 +785,9 @@ void or_destroy(or_mesh *m) {
 }
 
 /* physical coordinates of the SPs at time t, [E][N][N][2] (row j = eta index) */
-void or_sp_coords(const or_mesh *m, double t, double *out) {
+void or_sp_coords(const or_mesh *m, real t, real *out) {
   int N = m->N;
-  double g[6];
+  real g[6];
   for (int e = 0; e < m->ne; ++e)
     for (int j = 0; j < N; ++j)
       for (int i = 0; i < N; ++i) {
@@ -782,9 +798,9 @@ void or_sp_coords(const or_mesh *m, double t, double *out) {
 }
 
 /* |J| at the SPs, [E][N][N] */
-void or_sp_jacobian(const or_mesh *m, double *out) {
+void or_sp_jacobian(const or_mesh *m, real *out) {
   int N = m->N;
-  double g[6];
+  real g[6];
   for (int e = 0; e < m->ne; ++e)
     for (int j = 0; j < N; ++j)
       for (int i = 0; i < N; ++i) {
@@ -793,11 +809,11 @@ void or_sp_jacobian(const or_mesh *m, double *out) {
       }
 }
 
-void or_points(int N, double *Xs, double *Xf) { make_points(N, Xs, Xf); }
+void or_points(int N, real *Xs, real *Xf) { make_points(N, Xs, Xf); }
 
-void or_gauss_legendre(int n, double *x, double *w) { gauss_legendre(n, x, w); }
+void or_gauss_legendre(int n, real *x, real *w) { gauss_legendre(n, x, w); }
 
-void or_lagrange(const double *nodes, int n, const double *x, int nx, double *val, double *der) {
+void or_lagrange(const real *nodes, int n, const real *x, int nx, real *val, real *der) {
   for (int p = 0; p < nx; ++p)
     for (int i = 0; i < n; ++i) {
       val[p * n + i] = lag(nodes, n, i, x[p]);
@@ -835,14 +851,14 @@ static size_t face_index(int N, int e, int f, int v, int j) {
   }
 }
 
-static const double FACE_SIGMA[4] = {-1.0, 1.0, 1.0, -1.0};
+static const real FACE_SIGMA[4] = {-1.0, 1.0, 1.0, -1.0};
 
 /* geometry at face point j of face f of element e, time t: outward unit normal,
  * |S| (length of the contravariant vector), position */
-static void face_geom(const or_mesh *m, int e, int f, int j, double t, double *nx, double *ny, double *S, double *x,
-                      double *y) {
-  double g[6], ax, ay;
-  double xi = 0, eta = 0;
+static void face_geom(const or_mesh *m, int e, int f, int j, real t, real *nx, real *ny, real *S, real *x,
+                      real *y) {
+  real g[6], ax, ay;
+  real xi = 0, eta = 0;
   switch (f) {
     case 0: xi = m->Xs[j]; eta = 0.0; break;
     case 1: xi = 1.0; eta = m->Xs[j]; break;
@@ -852,7 +868,7 @@ static void face_geom(const or_mesh *m, int e, int f, int j, double t, double *n
   map_at(m, e, xi, eta, t, g);
   if (f == 1 || f == 3) { ax = g[5]; ay = -g[4]; }  /* (y_eta, -x_eta) */
   else { ax = -g[3]; ay = g[2]; }                    /* (-y_xi, x_xi) */
-  double len = sqrt(ax * ax + ay * ay);
+  real len = sqrt(ax * ax + ay * ay);
   *S = len;
   *nx = FACE_SIGMA[f] * ax / len;
   *ny = FACE_SIGMA[f] * ay / len;
@@ -863,40 +879,40 @@ static void face_geom(const or_mesh *m, int e, int f, int j, double t, double *n
 typedef struct {
   int nm;            /* number of non-degenerate mortars */
   int *lf, *rf;      /* index into the sorted L / R lists */
-  double *oL, *sL, *oR, *sR, *m0, *dm;
+  real *oL, *sL, *oR, *sR, *m0, *dm;
 } or_mortars;
 
 /* Sec. 3.2: mortars of interface I at stage time t.  Its rotating (L) side
  * is turned by theta = omega t; the mortars are the intervals between
  * consecutive node angles of both sides, in counter-clockwise order. */
-static void build_mortars(const or_iface *I, double t, or_mortars *mo) {
+static void build_mortars(const or_iface *I, real t, or_mortars *mo) {
   int nL = I->nL, nR = I->nR, nb = nL + nR;
-  double th = I->omega * t;
-  double *ang = malloc(sizeof(double) * (nb > 0 ? nb : 1));
+  real th = I->omega * t;
+  real *ang = malloc(sizeof(real) * (nb > 0 ? nb : 1));
   for (int k = 0; k < nL; ++k) ang[k] = wrap2pi(I->La[k] + th);
   for (int k = 0; k < nR; ++k) ang[nL + k] = I->Ra[k];
   for (int i = 1; i < nb; ++i)
-    for (int j = i; j > 0 && ang[j] < ang[j - 1]; --j) { double tt = ang[j]; ang[j] = ang[j - 1]; ang[j - 1] = tt; }
+    for (int j = i; j > 0 && ang[j] < ang[j - 1]; --j) { real tt = ang[j]; ang[j] = ang[j - 1]; ang[j - 1] = tt; }
   mo->nm = 0;
   int na = nb > 0 ? nb : 1;
   mo->lf = malloc(sizeof(int) * na); mo->rf = malloc(sizeof(int) * na);
-  mo->oL = malloc(sizeof(double) * na); mo->sL = malloc(sizeof(double) * na);
-  mo->oR = malloc(sizeof(double) * na); mo->sR = malloc(sizeof(double) * na);
-  mo->m0 = malloc(sizeof(double) * na); mo->dm = malloc(sizeof(double) * na);
+  mo->oL = malloc(sizeof(real) * na); mo->sL = malloc(sizeof(real) * na);
+  mo->oR = malloc(sizeof(real) * na); mo->sR = malloc(sizeof(real) * na);
+  mo->m0 = malloc(sizeof(real) * na); mo->dm = malloc(sizeof(real) * na);
   for (int k = 0; k < nb; ++k) {
-    double a = ang[k], b = (k + 1 < nb) ? ang[k + 1] : ang[0] + 2.0 * OR_PI;
-    double d = b - a;
+    real a = ang[k], b = (k + 1 < nb) ? ang[k + 1] : ang[0] + 2.0 * OR_PI;
+    real d = b - a;
     if (d <= 1e-13) continue;
-    double mid = a + 0.5 * d;
+    real mid = a + 0.5 * d;
     int fl = -1, fr = -1;
-    double oL = 0, oR = 0;
+    real oL = 0, oR = 0;
     for (int q = 0; q < nL; ++q) {
-      double st = wrap2pi(I->La[q] + th);
-      double off = wrap2pi(mid - st);
+      real st = wrap2pi(I->La[q] + th);
+      real off = wrap2pi(mid - st);
       if (off < I->Lw[q]) { fl = q; oL = wrap_pi(a - st); break; }
     }
     for (int q = 0; q < nR; ++q) {
-      double off = wrap2pi(mid - I->Ra[q]);
+      real off = wrap2pi(mid - I->Ra[q]);
       if (off < I->Rw[q]) { fr = q; oR = wrap_pi(a - I->Ra[q]); break; }
     }
     if (fl < 0 || fr < 0) continue;
@@ -919,8 +935,8 @@ static void free_mortars(or_mortars *mo) {
 
 /* Read the N values (per variable) at the face points of element face ef from
  * an FP array in counter-clockwise order (reversed if the face runs clockwise). */
-static void gather_ccw(const or_mesh *m, const double *arr_xi, const double *arr_eta, int ef, int rev, int nv,
-                       double *out) {
+static void gather_ccw(const or_mesh *m, const real *arr_xi, const real *arr_eta, int ef, int rev, int nv,
+                       real *out) {
   int N = m->N, e = ef / 4, f = ef % 4;
   for (int v = 0; v < nv; ++v)
     for (int j = 0; j < N; ++j) {
@@ -939,21 +955,21 @@ static void gather_ccw(const or_mesh *m, const double *arr_xi, const double *arr
  *           face point in Lval / Rval), average both sides, project back.
  * Lin/Rin: per sorted L/R face, nv*N values in CCW order.  Lout/Rout receive the
  * projected-back values in CCW order. */
-static void mortar_couple(const or_mesh *m, const or_iface *I, const or_mortars *mo, int mode, const double *Lin,
-                          const double *Rin, double *Lout, double *Rout) {
+static void mortar_couple(const or_mesh *m, const or_iface *I, const or_mortars *mo, int mode, const real *Lin,
+                          const real *Rin, real *Lout, real *Rout) {
   int N = m->N;
   int nv = 4;
-  memset(Lout, 0, sizeof(double) * I->nL * nv * N);
-  memset(Rout, 0, sizeof(double) * I->nR * nv * N);
-  double PfL[OR_MAXN * OR_MAXN], PbL[OR_MAXN * OR_MAXN], PfR[OR_MAXN * OR_MAXN], PbR[OR_MAXN * OR_MAXN];
+  memset(Lout, 0, sizeof(real) * I->nL * nv * N);
+  memset(Rout, 0, sizeof(real) * I->nR * nv * N);
+  real PfL[OR_MAXN * OR_MAXN], PbL[OR_MAXN * OR_MAXN], PfR[OR_MAXN * OR_MAXN], PbR[OR_MAXN * OR_MAXN];
   for (int k = 0; k < mo->nm; ++k) {
     int fl = mo->lf[k], fr = mo->rf[k];
     or_projection(N, mo->oL[k], mo->sL[k], PfL, PbL);
     or_projection(N, mo->oR[k], mo->sR[k], PfR, PbR);
-    double qL[4 * OR_MAXN], qR[4 * OR_MAXN], fm[4 * OR_MAXN];
+    real qL[4 * OR_MAXN], qR[4 * OR_MAXN], fm[4 * OR_MAXN];
     for (int v = 0; v < nv; ++v)
       for (int i = 0; i < N; ++i) {
-        double sl = 0.0, sr = 0.0;
+        real sl = 0.0, sr = 0.0;
         for (int j = 0; j < N; ++j) {
           sl += PfL[i * N + j] * Lin[(fl * nv + v) * N + j];
           sr += PfR[i * N + j] * Rin[(fr * nv + v) * N + j];
@@ -963,8 +979,8 @@ static void mortar_couple(const or_mesh *m, const or_iface *I, const or_mortars 
       }
     if (mode == 0) {
       for (int i = 0; i < N; ++i) {
-        double phi = mo->m0[k] + m->Xs[i] * mo->dm[k];
-        double a[4], b[4], Fn[4];
+        real phi = mo->m0[k] + m->Xs[i] * mo->dm[k];
+        real a[4], b[4], Fn[4];
         for (int v = 0; v < 4; ++v) { a[v] = qL[v * N + i]; b[v] = qR[v * N + i]; }
         /* on a circle about its zone's centre the grid velocity is tangential */
         rusanov(&m->prm, a, b, cos(phi), sin(phi), 0.0, Fn);
@@ -975,7 +991,7 @@ static void mortar_couple(const or_mesh *m, const or_iface *I, const or_mortars 
     }
     for (int v = 0; v < nv; ++v)
       for (int i = 0; i < N; ++i) {
-        double sl = 0.0, sr = 0.0;
+        real sl = 0.0, sr = 0.0;
         for (int j = 0; j < N; ++j) {
           sl += PbL[i * N + j] * fm[v * N + j];
           sr += PbR[i * N + j] * fm[v * N + j];
@@ -987,7 +1003,7 @@ static void mortar_couple(const or_mesh *m, const or_iface *I, const or_mortars 
 }
 
 /* conservative state from density, velocity and pressure */
-static void from_primitive(const or_params *p, double rho, double u, double v, double pr, double *q) {
+static void from_primitive(const or_params *p, real rho, real u, real v, real pr, real *q) {
   q[0] = rho;
   q[1] = rho * u;
   q[2] = rho * v;
@@ -1010,18 +1026,18 @@ static void from_primitive(const or_params *p, double rho, double u, double v, d
  *   inlet  (Dirichlet): the free stream;
  *   outlet (fixed pressure): interior density and velocity, free-stream
  *          pressure. */
-static void boundary_states(const or_params *p, int tag, const double *qi, double ug, double vg, double nx,
-                            double ny, double *qg, double *qb) {
-  double pr = pressure(p, qi), u = qi[1] / qi[0], v = qi[2] / qi[0];
+static void boundary_states(const or_params *p, int tag, const real *qi, real ug, real vg, real nx,
+                            real ny, real *qg, real *qb) {
+  real pr = pressure(p, qi), u = qi[1] / qi[0], v = qi[2] / qi[0];
   if (tag == BC_WALL) {
-    double rho = pr / (p->Rgas * p->T_wall);
+    real rho = pr / (p->Rgas * p->T_wall);
     from_primitive(p, rho, 2.0 * ug - u, 2.0 * vg - v, pr, qg);
     from_primitive(p, rho, ug, vg, pr, qb);
   } else if (tag == BC_ADIABATIC) {
     from_primitive(p, qi[0], 2.0 * ug - u, 2.0 * vg - v, pr, qg);
     from_primitive(p, qi[0], ug, vg, pr, qb);
   } else if (tag == BC_SLIP) {
-    double wn = (u - ug) * nx + (v - vg) * ny;
+    real wn = (u - ug) * nx + (v - vg) * ny;
     from_primitive(p, qi[0], u - 2.0 * wn * nx, v - 2.0 * wn * ny, pr, qg);
     from_primitive(p, qi[0], u - wn * nx, v - wn * ny, pr, qb);
   } else if (tag == BC_INLET) {
@@ -1034,27 +1050,27 @@ static void boundary_states(const or_params *p, int tag, const double *qi, doubl
 }
 
 typedef struct {
-  double *Qxi, *Qeta;   /* Q at xi / eta FPs */
-  double *Fxi, *Geta;   /* transformed fluxes at xi / eta FPs */
-  double *cQxi, *cQeta; /* common solution at face points (viscous) */
-  double *gxi, *geta;   /* physical gradient at FPs: [E][8][..] as two 4-var blocks */
+  real *Qxi, *Qeta;   /* Q at xi / eta FPs */
+  real *Fxi, *Geta;   /* transformed fluxes at xi / eta FPs */
+  real *cQxi, *cQeta; /* common solution at face points (viscous) */
+  real *gxi, *geta;   /* physical gradient at FPs: [E][8][..] as two 4-var blocks */
 } or_work;
 
 /* Residual; when scale is not NULL it also receives, per SP and variable,
  * (sum_i |l'_i(X_k)| |F~_i| + sum_i |l'_i(X_j)| |G~_i|) / |J|: the magnitude of
  * the terms the divergence adds up, which bounds its round-off. */
-int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *scale);
+int or_residual_ex(or_mesh *m, const real *Q, real t, real *dQdt, real *scale);
 
-int or_residual(or_mesh *m, const double *Q, double t, double *dQdt) { return or_residual_ex(m, Q, t, dQdt, NULL); }
+int or_residual(or_mesh *m, const real *Q, real t, real *dQdt) { return or_residual_ex(m, Q, t, dQdt, NULL); }
 
-int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *scale) {
+int or_residual_ex(or_mesh *m, const real *Q, real t, real *dQdt, real *scale) {
   int N = m->N, ne = m->ne;
   const or_params *P = &m->prm;
   size_t nxf = (size_t)ne * 4 * N * (N + 1);
-  double *Qxi = calloc(nxf, sizeof(double)), *Qeta = calloc(nxf, sizeof(double));
-  double *Fxi = calloc(nxf, sizeof(double)), *Geta = calloc(nxf, sizeof(double));
-  double *cQxi = NULL, *cQeta = NULL, *Gxx = NULL, *Gxy = NULL, *Gex = NULL, *Gey = NULL;
-  double hf[(OR_MAXN + 1) * OR_MAXN], dl[OR_MAXN * (OR_MAXN + 1)];
+  real *Qxi = calloc(nxf, sizeof(real)), *Qeta = calloc(nxf, sizeof(real));
+  real *Fxi = calloc(nxf, sizeof(real)), *Geta = calloc(nxf, sizeof(real));
+  real *cQxi = NULL, *cQeta = NULL, *Gxx = NULL, *Gxy = NULL, *Gex = NULL, *Gey = NULL;
+  real hf[(OR_MAXN + 1) * OR_MAXN], dl[OR_MAXN * (OR_MAXN + 1)];
   /* h_k(X_{i+1/2}) and l'_{i+1/2}(X_k) */
   for (int i = 0; i <= N; ++i)
     for (int k = 0; k < N; ++k) hf[i * N + k] = lag(m->Xs, N, k, m->Xf[i]);
@@ -1066,7 +1082,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
     for (int v = 0; v < 4; ++v)
       for (int j = 0; j < N; ++j)
         for (int i = 0; i <= N; ++i) {
-          double sx = 0.0, se = 0.0;
+          real sx = 0.0, se = 0.0;
           for (int k = 0; k < N; ++k) {
             sx += Q[IQ(e, v, j, k)] * hf[i * N + k];
             se += Q[IQ(e, v, k, j)] * hf[i * N + k];
@@ -1080,7 +1096,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
   for (int e = 0; e < ne; ++e)
     for (int j = 0; j < N; ++j)
       for (int i = 0; i <= N; ++i) {
-        double g[6], q[4], F[4], G[4], ug, vg;
+        real g[6], q[4], F[4], G[4], ug, vg;
         map_at(m, e, m->Xf[i], m->Xs[j], t, g);
         grid_velocity(m, e, g[0], g[1], &ug, &vg);
         for (int v = 0; v < 4; ++v) q[v] = Qxi[IXF(e, v, j, i)];
@@ -1095,32 +1111,32 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
 
   /* mortars of every interface at this stage time */
   or_mortars mos[OR_MAXZ];
-  double *Lins[OR_MAXZ], *Rins[OR_MAXZ], *Louts[OR_MAXZ], *Routs[OR_MAXZ];
+  real *Lins[OR_MAXZ], *Rins[OR_MAXZ], *Louts[OR_MAXZ], *Routs[OR_MAXZ];
   memset(mos, 0, sizeof mos);
   for (int z = 0; z < m->nz; ++z) {
     const or_iface *I = &m->zi[z];
     Lins[z] = Rins[z] = Louts[z] = Routs[z] = NULL;
     if (I->nL == 0) continue;
     build_mortars(I, t, &mos[z]);
-    Lins[z] = malloc(sizeof(double) * I->nL * 4 * N);
-    Rins[z] = malloc(sizeof(double) * I->nR * 4 * N);
-    Louts[z] = malloc(sizeof(double) * I->nL * 4 * N);
-    Routs[z] = malloc(sizeof(double) * I->nR * 4 * N);
+    Lins[z] = malloc(sizeof(real) * I->nL * 4 * N);
+    Rins[z] = malloc(sizeof(real) * I->nR * 4 * N);
+    Louts[z] = malloc(sizeof(real) * I->nL * 4 * N);
+    Routs[z] = malloc(sizeof(real) * I->nR * 4 * N);
   }
 
   /* viscous: common solution, gradients, viscous fluxes at the FPs */
-  double *Fv_face = NULL; /* common viscous normal flux per element face point [E*4][4][N] (outward) */
+  real *Fv_face = NULL; /* common viscous normal flux per element face point [E*4][4][N] (outward) */
   if (P->viscous) {
-    cQxi = calloc(nxf, sizeof(double));
-    cQeta = calloc(nxf, sizeof(double));
-    Gxx = calloc(nxf, sizeof(double)); Gxy = calloc(nxf, sizeof(double));
-    Gex = calloc(nxf, sizeof(double)); Gey = calloc(nxf, sizeof(double));
+    cQxi = calloc(nxf, sizeof(real));
+    cQeta = calloc(nxf, sizeof(real));
+    Gxx = calloc(nxf, sizeof(real)); Gxy = calloc(nxf, sizeof(real));
+    Gex = calloc(nxf, sizeof(real)); Gey = calloc(nxf, sizeof(real));
     /* (a) common solution at every face point */
     for (int e = 0; e < ne; ++e)
       for (int f = 0; f < 4; ++f) {
         int ef = 4 * e + f, kind = m->fkind[ef];
         for (int j = 0; j < N; ++j) {
-          double qi[4], qc[4];
+          real qi[4], qc[4];
           for (int v = 0; v < 4; ++v) {
             size_t id = face_index(N, e, f, v, j);
             qi[v] = (f == 1 || f == 3) ? Qxi[id] : Qeta[id];
@@ -1129,11 +1145,11 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
             int eb = m->fnbr[ef] / 4, fb = m->fnbr[ef] % 4, jb = m->frev[ef] ? N - 1 - j : j;
             for (int v = 0; v < 4; ++v) {
               size_t id = face_index(N, eb, fb, v, jb);
-              double qo = (fb == 1 || fb == 3) ? Qxi[id] : Qeta[id];
+              real qo = (fb == 1 || fb == 3) ? Qxi[id] : Qeta[id];
               qc[v] = 0.5 * (qi[v] + qo);
             }
           } else if (kind == FK_BOUNDARY) {
-            double nx, ny, S, x, y, ug, vg, qg[4];
+            real nx, ny, S, x, y, ug, vg, qg[4];
             face_geom(m, e, f, j, t, &nx, &ny, &S, &x, &y);
             grid_velocity(m, e, x, y, &ug, &vg);
             boundary_states(P, m->ftag[ef], qi, ug, vg, nx, ny, qg, qc);
@@ -1149,7 +1165,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
     for (int z = 0; z < m->nz; ++z) {
       const or_iface *I = &m->zi[z];
       const int nL = I->nL, nR = I->nR;
-      double *Lin = Lins[z], *Rin = Rins[z], *Lout = Louts[z], *Rout = Routs[z];
+      real *Lin = Lins[z], *Rin = Rins[z], *Lout = Louts[z], *Rout = Routs[z];
       const or_mortars *mo = &mos[z];
       if (nL == 0) continue;
       for (int k = 0; k < nL; ++k) gather_ccw(m, Qxi, Qeta, I->Lef[k], I->Lrev[k], 4, Lin + (size_t)k * 4 * N);
@@ -1159,7 +1175,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
         int n = side ? nR : nL;
         for (int k = 0; k < n; ++k) {
           int ef = side ? I->Ref[k] : I->Lef[k], rev = side ? I->Rrev[k] : I->Lrev[k];
-          const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
+          const real *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
           int e = ef / 4, f = ef % 4;
           for (int v = 0; v < 4; ++v)
             for (int j = 0; j < N; ++j) {
@@ -1173,18 +1189,18 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
     /* (b) gradients at the SPs: derivative of the degree-N polynomial through
      * the FP values, with the common solution at the end FPs; mapped to x, y
      * with the metrics at the SP (chain rule). */
-    double *Qx = calloc((size_t)ne * 4 * N * N, sizeof(double)), *Qy = calloc((size_t)ne * 4 * N * N, sizeof(double));
+    real *Qx = calloc((size_t)ne * 4 * N * N, sizeof(real)), *Qy = calloc((size_t)ne * 4 * N * N, sizeof(real));
     for (int e = 0; e < ne; ++e)
       for (int j = 0; j < N; ++j)
         for (int k = 0; k < N; ++k) {
-          double g[6];
+          real g[6];
           map_at(m, e, m->Xs[k], m->Xs[j], t, g);
-          double J = g[2] * g[5] - g[4] * g[3];
+          real J = g[2] * g[5] - g[4] * g[3];
           for (int v = 0; v < 4; ++v) {
-            double dxi = 0.0, deta = 0.0;
+            real dxi = 0.0, deta = 0.0;
             for (int i = 0; i <= N; ++i) {
-              double ax = (i == 0 || i == N) ? cQxi[IXF(e, v, j, i)] : Qxi[IXF(e, v, j, i)];
-              double ae = (i == 0 || i == N) ? cQeta[IEF(e, v, i, k)] : Qeta[IEF(e, v, i, k)];
+              real ax = (i == 0 || i == N) ? cQxi[IXF(e, v, j, i)] : Qxi[IXF(e, v, j, i)];
+              real ae = (i == 0 || i == N) ? cQeta[IEF(e, v, i, k)] : Qeta[IEF(e, v, i, k)];
               dxi += ax * dl[k * (N + 1) + i];
               deta += ae * dl[j * (N + 1) + i];
             }
@@ -1198,7 +1214,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
       for (int v = 0; v < 4; ++v)
         for (int j = 0; j < N; ++j)
           for (int i = 0; i <= N; ++i) {
-            double a = 0, b = 0, c = 0, d = 0;
+            real a = 0, b = 0, c = 0, d = 0;
             for (int k = 0; k < N; ++k) {
               a += Qx[IQ(e, v, j, k)] * hf[i * N + k];
               b += Qy[IQ(e, v, j, k)] * hf[i * N + k];
@@ -1216,7 +1232,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
     for (int e = 0; e < ne; ++e)
       for (int j = 0; j < N; ++j)
         for (int i = 1; i < N; ++i) {
-          double g[6], q[4], qx[4], qy[4], F[4], G[4];
+          real g[6], q[4], qx[4], qy[4], F[4], G[4];
           map_at(m, e, m->Xf[i], m->Xs[j], t, g);
           for (int v = 0; v < 4; ++v) { q[v] = Qxi[IXF(e, v, j, i)]; qx[v] = Gxx[IXF(e, v, j, i)]; qy[v] = Gxy[IXF(e, v, j, i)]; }
           viscous_flux(P, q, qx, qy, F, G);
@@ -1227,12 +1243,12 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
           for (int v = 0; v < 4; ++v) Geta[IEF(e, v, i, j)] += -g[3] * F[v] + g[2] * G[v];
         }
     /* (e) common viscous normal flux at the face points */
-    Fv_face = calloc((size_t)ne * 4 * 4 * N, sizeof(double));
+    Fv_face = calloc((size_t)ne * 4 * 4 * N, sizeof(real));
     for (int e = 0; e < ne; ++e)
       for (int f = 0; f < 4; ++f) {
         int ef = 4 * e + f, kind = m->fkind[ef];
         for (int j = 0; j < N; ++j) {
-          double nx, ny, S, x, y, qc[4], gx[4], gy[4], F[4], G[4], fo[4];
+          real nx, ny, S, x, y, qc[4], gx[4], gy[4], F[4], G[4], fo[4];
           face_geom(m, e, f, j, t, &nx, &ny, &S, &x, &y);
           for (int v = 0; v < 4; ++v) {
             size_t id = face_index(N, e, f, v, j);
@@ -1245,7 +1261,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
           for (int v = 0; v < 4; ++v) fo[v] = F[v] * nx + G[v] * ny; /* own side, outward */
           if (kind == FK_CONF || kind == FK_PERIODIC) {
             int eb = m->fnbr[ef] / 4, fb = m->fnbr[ef] % 4, jb = m->frev[ef] ? N - 1 - j : j;
-            double gbx[4], gby[4], Fb[4], Gb[4];
+            real gbx[4], gby[4], Fb[4], Gb[4];
             for (int v = 0; v < 4; ++v) {
               size_t id = face_index(N, eb, fb, v, jb);
               int isx = (fb == 1 || fb == 3);
@@ -1257,7 +1273,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
           } else if (kind == FK_BOUNDARY) {
             if (m->ftag[ef] == BC_ADIABATIC) {
               /* no heat through the wall: remove the conduction term of the energy flux */
-              double kTx, kTy;
+              real kTx, kTy;
               conduction(P, qc, gx, gy, &kTx, &kTy);
               fo[3] += kTx * nx + kTy * ny;
             }
@@ -1265,7 +1281,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
           } else {
             /* interface: store F_vis . n with n oriented from L to R, in the
              * face's own point order; projected below */
-            double sgn = (kind == FK_IFACE_L) ? 1.0 : -1.0;
+            real sgn = (kind == FK_IFACE_L) ? 1.0 : -1.0;
             for (int v = 0; v < 4; ++v) Fv_face[((size_t)ef * 4 + v) * N + j] = sgn * fo[v];
           }
         }
@@ -1273,15 +1289,15 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
     for (int z = 0; z < m->nz; ++z) {
       const or_iface *I = &m->zi[z];
       const int nL = I->nL, nR = I->nR;
-      double *Lout = Louts[z], *Rout = Routs[z];
+      real *Lout = Louts[z], *Rout = Routs[z];
       const or_mortars *mo = &mos[z];
       if (nL == 0) continue;
-      double *vL = calloc((size_t)nL * 4 * N, sizeof(double)), *vR = calloc((size_t)nR * 4 * N, sizeof(double));
+      real *vL = calloc((size_t)nL * 4 * N, sizeof(real)), *vR = calloc((size_t)nR * 4 * N, sizeof(real));
       for (int side = 0; side < 2; ++side) {
         int n = side ? nR : nL;
         for (int k = 0; k < n; ++k) {
           int ef = side ? I->Ref[k] : I->Lef[k], rev = side ? I->Rrev[k] : I->Lrev[k];
-          double *dst = (side ? vR : vL) + (size_t)k * 4 * N;
+          real *dst = (side ? vR : vL) + (size_t)k * 4 * N;
           for (int v = 0; v < 4; ++v)
             for (int j = 0; j < N; ++j) dst[v * N + j] = Fv_face[((size_t)ef * 4 + v) * N + (rev ? N - 1 - j : j)];
         }
@@ -1291,8 +1307,8 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
         int n = side ? nR : nL;
         for (int k = 0; k < n; ++k) {
           int ef = side ? I->Ref[k] : I->Lef[k], rev = side ? I->Rrev[k] : I->Lrev[k];
-          const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
-          double sgn = side ? -1.0 : 1.0; /* back to outward orientation */
+          const real *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
+          real sgn = side ? -1.0 : 1.0; /* back to outward orientation */
           for (int v = 0; v < 4; ++v)
             for (int j = 0; j < N; ++j) Fv_face[((size_t)ef * 4 + v) * N + (rev ? N - 1 - j : j)] = sgn * src[v * N + j];
         }
@@ -1310,10 +1326,10 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
       int ef = 4 * e + f, kind = m->fkind[ef];
       if (kind == FK_IFACE_L || kind == FK_IFACE_R) continue;
       for (int j = 0; j < N; ++j) {
-        double nx, ny, S, x, y, ug, vg, qi[4], qo[4], Fn[4];
+        real nx, ny, S, x, y, ug, vg, qi[4], qo[4], Fn[4];
         face_geom(m, e, f, j, t, &nx, &ny, &S, &x, &y);
         grid_velocity(m, e, x, y, &ug, &vg);
-        double vgn = ug * nx + vg * ny;
+        real vgn = ug * nx + vg * ny;
         for (int v = 0; v < 4; ++v) {
           size_t id = face_index(N, e, f, v, j);
           qi[v] = (f == 1 || f == 3) ? Qxi[id] : Qeta[id];
@@ -1325,14 +1341,14 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
             qo[v] = (fb == 1 || fb == 3) ? Qxi[id] : Qeta[id];
           }
         } else {
-          double qb[4];
+          real qb[4];
           boundary_states(P, m->ftag[ef], qi, ug, vg, nx, ny, qo, qb);
         }
         rusanov(P, qi, qo, nx, ny, vgn, Fn);
         for (int v = 0; v < 4; ++v) {
-          double fv = Fv_face ? Fv_face[((size_t)ef * 4 + v) * N + j] : 0.0;
+          real fv = Fv_face ? Fv_face[((size_t)ef * 4 + v) * N + j] : 0.0;
           size_t id = face_index(N, e, f, v, j);
-          double val = FACE_SIGMA[f] * S * (Fn[v] + fv);
+          real val = FACE_SIGMA[f] * S * (Fn[v] + fv);
           if (f == 1 || f == 3) Fxi[id] = val; else Geta[id] = val;
         }
       }
@@ -1341,7 +1357,7 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
   for (int z = 0; z < m->nz; ++z) {
     const or_iface *I = &m->zi[z];
     const int nL = I->nL, nR = I->nR;
-    double *Lin = Lins[z], *Rin = Rins[z], *Lout = Louts[z], *Rout = Routs[z];
+    real *Lin = Lins[z], *Rin = Rins[z], *Lout = Louts[z], *Rout = Routs[z];
     const or_mortars *mo = &mos[z];
     if (nL == 0) continue;
     for (int k = 0; k < nL; ++k) gather_ccw(m, Qxi, Qeta, I->Lef[k], I->Lrev[k], 4, Lin + (size_t)k * 4 * N);
@@ -1352,16 +1368,16 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
       for (int k = 0; k < n; ++k) {
         int ef = side ? I->Ref[k] : I->Lef[k], rev = side ? I->Rrev[k] : I->Lrev[k];
         int e = ef / 4, f = ef % 4;
-        const double *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
-        double sgn = side ? -1.0 : 1.0; /* L -> R normal is outward for L, inward for R */
+        const real *src = (side ? Rout : Lout) + (size_t)k * 4 * N;
+        real sgn = side ? -1.0 : 1.0; /* L -> R normal is outward for L, inward for R */
         for (int j = 0; j < N; ++j) {
           int jj = rev ? N - 1 - j : j;
-          double nx, ny, S, x, y;
+          real nx, ny, S, x, y;
           face_geom(m, e, f, jj, t, &nx, &ny, &S, &x, &y);
           for (int v = 0; v < 4; ++v) {
-            double fv = Fv_face ? Fv_face[((size_t)ef * 4 + v) * N + jj] : 0.0;
+            real fv = Fv_face ? Fv_face[((size_t)ef * 4 + v) * N + jj] : 0.0;
             size_t id = face_index(N, e, f, v, jj);
-            double val = FACE_SIGMA[f] * S * (sgn * src[v * N + j] + fv);
+            real val = FACE_SIGMA[f] * S * (sgn * src[v * N + j] + fv);
             if (f == 1 || f == 3) Fxi[id] = val; else Geta[id] = val;
           }
         }
@@ -1374,18 +1390,18 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
   for (int e = 0; e < ne; ++e)
     for (int j = 0; j < N; ++j)
       for (int k = 0; k < N; ++k) {
-        double g[6];
+        real g[6];
         map_t0(m, e, m->Xs[k], m->Xs[j], g);
-        double J = g[2] * g[5] - g[4] * g[3];
+        real J = g[2] * g[5] - g[4] * g[3];
         for (int v = 0; v < 4; ++v) {
-          double dF = 0.0, dG = 0.0;
+          real dF = 0.0, dG = 0.0;
           for (int i = 0; i <= N; ++i) {
             dF += Fxi[IXF(e, v, j, i)] * dl[k * (N + 1) + i];
             dG += Geta[IEF(e, v, i, k)] * dl[j * (N + 1) + i];
           }
           dQdt[IQ(e, v, j, k)] = -(dF + dG) / J;
           if (scale) {
-            double a = 0.0;
+            real a = 0.0;
             for (int i = 0; i <= N; ++i)
               a += fabs(Fxi[IXF(e, v, j, i)] * dl[k * (N + 1) + i]) + fabs(Geta[IEF(e, v, i, k)] * dl[j * (N + 1) + i]);
             scale[IQ(e, v, j, k)] = a / fabs(J);
@@ -1401,11 +1417,11 @@ int or_residual_ex(or_mesh *m, const double *Q, double t, double *dQdt, double *
 }
 
 /* Three-stage SSP Runge-Kutta (Shu-Osher form), stage times t, t+dt, t+dt/2 */
-int or_step(or_mesh *m, double *Q, double *t, double dt, int nsteps) {
+int or_step(or_mesh *m, real *Q, real *t, real dt, int nsteps) {
   size_t n = (size_t)m->ne * 4 * m->N * m->N;
-  double *q1 = malloc(n * sizeof(double)), *q2 = malloc(n * sizeof(double)), *r = malloc(n * sizeof(double));
+  real *q1 = malloc(n * sizeof(real)), *q2 = malloc(n * sizeof(real)), *r = malloc(n * sizeof(real));
   for (int s = 0; s < nsteps; ++s) {
-    double tn = *t;
+    real tn = *t;
     or_residual(m, Q, tn, r);
     for (size_t i = 0; i < n; ++i) q1[i] = Q[i] + dt * r[i];
     or_residual(m, q1, tn + dt, r);
@@ -1427,18 +1443,18 @@ int or_step(or_mesh *m, double *Q, double *t, double dt, int nsteps) {
  *   u4 = a40 u + a43 u3 + c43 dt L(u3)
  *   u+ = a52 u2 + a53 u3 + c53 dt L(u3) + a54 u4 + c54 dt L(u4)
  * Stage times follow from the coefficients (or_rk54_tableau). */
-static const double RK54_C10 = 0.391752226571890;
-static const double RK54_A20 = 0.444370493651235, RK54_A21 = 0.555629506348765, RK54_C21 = 0.368410593050371;
-static const double RK54_A30 = 0.620101851488403, RK54_A32 = 0.379898148511597, RK54_C32 = 0.251891774271694;
-static const double RK54_A40 = 0.178079954393132, RK54_A43 = 0.821920045606868, RK54_C43 = 0.544974750228521;
-static const double RK54_A52 = 0.517231671970585, RK54_A53 = 0.096059710526147, RK54_C53 = 0.063692468666290;
-static const double RK54_A54 = 0.386708617503269, RK54_C54 = 0.226007483236906;
+static const real RK54_C10 = 0.391752226571890;
+static const real RK54_A20 = 0.444370493651235, RK54_A21 = 0.555629506348765, RK54_C21 = 0.368410593050371;
+static const real RK54_A30 = 0.620101851488403, RK54_A32 = 0.379898148511597, RK54_C32 = 0.251891774271694;
+static const real RK54_A40 = 0.178079954393132, RK54_A43 = 0.821920045606868, RK54_C43 = 0.544974750228521;
+static const real RK54_A52 = 0.517231671970585, RK54_A53 = 0.096059710526147, RK54_C53 = 0.063692468666290;
+static const real RK54_A54 = 0.386708617503269, RK54_C54 = 0.226007483236906;
 
 /* Butcher tableau (A 5x5 row-major, b 5, c 5) of the scheme above, for tests:
  * every stage value is expanded as u + dt sum_j A_ij k_j with k_j = L(stage j). */
-void or_rk54_tableau(double *A, double *b, double *c) {
+void or_rk54_tableau(real *A, real *b, real *c) {
   /* coefficient of dt k_j in stage i (stage 1 = u) */
-  double S[6][5];
+  real S[6][5];
   memset(S, 0, sizeof S);
   /* S[1] = u1 */
   S[1][0] = RK54_C10;
@@ -1451,9 +1467,9 @@ void or_rk54_tableau(double *A, double *b, double *c) {
   for (int j = 0; j < 5; ++j) S[5][j] = RK54_A52 * S[2][j] + RK54_A53 * S[3][j] + RK54_A54 * S[4][j];
   S[5][3] += RK54_C53;
   S[5][4] += RK54_C54;
-  memset(A, 0, sizeof(double) * 25);
+  memset(A, 0, sizeof(real) * 25);
   for (int i = 0; i < 5; ++i) {
-    double ci = 0.0;
+    real ci = 0.0;
     for (int j = 0; j < 5; ++j) {
       A[i * 5 + j] = i == 0 ? 0.0 : S[i][j];
       ci += A[i * 5 + j];
@@ -1463,14 +1479,14 @@ void or_rk54_tableau(double *A, double *b, double *c) {
   for (int j = 0; j < 5; ++j) b[j] = S[5][j];
 }
 
-int or_step_rk54(or_mesh *m, double *Q, double *t, double dt, int nsteps) {
+int or_step_rk54(or_mesh *m, real *Q, real *t, real dt, int nsteps) {
   size_t n = (size_t)m->ne * 4 * m->N * m->N;
-  double *u1 = malloc(n * sizeof(double)), *u2 = malloc(n * sizeof(double)), *u3 = malloc(n * sizeof(double));
-  double *u4 = malloc(n * sizeof(double)), *r = malloc(n * sizeof(double)), *r3 = malloc(n * sizeof(double));
-  double A[25], b[5], c[5];
+  real *u1 = malloc(n * sizeof(real)), *u2 = malloc(n * sizeof(real)), *u3 = malloc(n * sizeof(real));
+  real *u4 = malloc(n * sizeof(real)), *r = malloc(n * sizeof(real)), *r3 = malloc(n * sizeof(real));
+  real A[25], b[5], c[5];
   or_rk54_tableau(A, b, c);
   for (int s = 0; s < nsteps; ++s) {
-    double tn = *t;
+    real tn = *t;
     or_residual(m, Q, tn + c[0] * dt, r);
     for (size_t i = 0; i < n; ++i) u1[i] = Q[i] + RK54_C10 * dt * r[i];
     or_residual(m, u1, tn + c[1] * dt, r);
@@ -1490,8 +1506,8 @@ int or_step_rk54(or_mesh *m, double *Q, double *t, double dt, int nsteps) {
 
 /* mortar list of zone z's interface at time t, for tests: returns the number
  * of mortars (-1 for no such zone); arrays must hold nL + nR entries */
-int or_mortar_list_zone(const or_mesh *m, int z, double t, int *lf, int *rf, double *oL, double *sL, double *oR,
-                        double *sR) {
+int or_mortar_list_zone(const or_mesh *m, int z, real t, int *lf, int *rf, real *oL, real *sL, real *oR,
+                        real *sR) {
   if (z < 1 || z > m->nz) return -1;
   or_mortars mo;
   build_mortars(&m->zi[z - 1], t, &mo);
@@ -1504,6 +1520,6 @@ int or_mortar_list_zone(const or_mesh *m, int z, double t, int *lf, int *rf, dou
 }
 
 /* the same for zone 1 */
-int or_mortar_list(const or_mesh *m, double t, int *lf, int *rf, double *oL, double *sL, double *oR, double *sR) {
+int or_mortar_list(const or_mesh *m, real t, int *lf, int *rf, real *oL, real *sL, real *oR, real *sR) {
   return or_mortar_list_zone(m, 1, t, lf, rf, oL, sL, oR, sR);
 }
