@@ -95,11 +95,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) per launch of the FP32 volume kernel (mean of the
-# three stage launches) from the ncu capture summarised in
-# profiles/k_volume_fp32_rotor_n6.md; valid only for the kernel source it was
-# taken on: SHA-256 of the engine text that k_volume is built from (the
-# ElemGeo metrics and VolCfg through the end of k_volume); otherwise null.
+# DRAM bytes (read + write) per launch of the FP32 volume kernel on this
+# workload (mean of the three stage launches of one step), from one ncu
+# capture of dram__bytes_read.sum + dram__bytes_write.sum; valid only for the
+# kernel source it was taken on: SHA-256 of the engine text that k_volume is
+# built from (the ElemGeo metrics and VolCfg through the end of k_volume);
+# otherwise null.
 PROFILED_TRAFFIC = {"bytes": (389.06e6 + 328.52e6 + 673.47e6 + 331.29e6 + 673.47e6 + 329.67e6) / 3,
                     "kernel_sha256": "0ca2e437d4cfb2bcce0666b0130d3e18685380c94531e4392a21f1c5248948b6"}
 
@@ -135,6 +136,14 @@ def volume_bytes_per_element(N, w_c, w_s=8):
     and the zone tag."""
     state = 4 * N * N * w_s
     return state * (2 + 2.0 / 3.0) + 2 * 16 * N * w_c + 4 * 16 + 4
+
+
+def interface_fraction(prof):
+    """Share of a step spent on sliding-interface work, the paper's
+    "interface" time (Tables 3-10): the stage clock and mortar merge, the
+    mortar projections with their common flux, and the gather, each timed
+    as its own launch by sd_profile_step (per stage; three stages a step)."""
+    return (prof["merge"] + prof["mortar"]) * 3 / prof["step"]
 
 
 def launches_per_step(mesh, viscous=0):
@@ -379,7 +388,7 @@ def run_config(ssd, stream, name, steps, warmup, start, start_label, other_start
             if prec == ssd.SD_PREC_FP32:
                 prof = s.sd_profile_step(w.cfl_dt, reps=5)
                 res["kernel_ms"] = prof
-                res["interface_fraction"] = prof["mortar"] * 3 / prof["step"]
+                res["interface_fraction"] = interface_fraction(prof)
         else:
             s.sd_step(w.cfl_dt, steps)
             s.sd_sync()
@@ -593,7 +602,10 @@ def main():
     achieved = vol_bytes / (prof["volume"] * 1e-3) / 1e9
     traffic = profiled_traffic() if (args.workload == "rotor_n6" and prec == ssd.SD_PREC_FP32) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_volume", "peak_source": peak_src + " hbm_gbs (burst)",
+                "traffic": traffic,
+                "traffic_source": ("stored ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this "
+                                   "kernel source, not a measurement of this run") if traffic else None,
+                "kernel": "k_volume", "peak_source": peak_src + " hbm_gbs (burst)",
                 "algorithmic_bytes_per_launch": vol_bytes}
     try:
         fp32_peak = solver.sd_fma_peak(ssd.SD_PREC_FP32)
@@ -664,7 +676,7 @@ def main():
             "couette": couette,
             "twin_rotor": twin,
             "kernel_ms": prof,
-            "interface_fraction": prof["mortar"] * 3 / prof["step"],
+            "interface_fraction": interface_fraction(prof),
             "fp32_fma_peak_tflops": fp32_peak,
             "roofline": roofline,
             "cpu_baseline": cpu,

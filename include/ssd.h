@@ -271,11 +271,12 @@ int sd_fma_peak(sd_handle *h, int precision, double *tflops);
  * library holds until the process exits.  Calls needing more than 16 MiB
  * return SD_ERR_ARG with a message (with R in host memory the state copy,
  * E * 4 * N * N doubles, counts against the limit; with R in device memory
- * only the interface work does).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) for that device; make that
- * first call before any stream capture.  All calls share the array and
+ * only the interface work does).  Every call looks up the current device's
+ * copy of the array (cudaGetSymbolAddress).  All calls share the array and
  * nothing in it is assumed to start at zero; calls that overlap on the GPU
- * (several handles or streams at once) race on it.  Synchronises. */
+ * (several handles or streams at once) race on it.  Synchronises the
+ * handle's stream, then reports device errors as sd_sync does
+ * (SD_ERR_TIMEOUT: a bounded wait gave up and R is incomplete). */
 int sd_residual_noalloc(sd_handle *h, double *R, int on_device);
 
 #ifdef __cplusplus

@@ -149,6 +149,8 @@ class Oracle:
         L = lib(real)
         self.real = real
         self._dt = _DTYPE[real]
+        self.params = params
+        self._ext = None
         self.N = N
         self.mesh = mesh
         self.E = int(len(mesh["elem_nodes"]))
@@ -198,6 +200,15 @@ class Oracle:
     @property
     def shape(self):
         return (self.E, 4, self.N, self.N)
+
+    def extended(self):
+        """The same mesh, order and parameters in the extended-precision build
+        (created once, on first use)."""
+        if self.real == "long":
+            return self
+        if self._ext is None:
+            self._ext = Oracle(self.mesh, self.N, self.params, real="long")
+        return self._ext
 
     def sp_coords(self, t: float = 0.0):
         out = np.zeros((self.E, self.N, self.N, 2), dtype=self._dt)

@@ -113,16 +113,37 @@ def lib():
     return _lib
 
 
-def _ptr(a, dtype):
-    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+def _ptr(a, dtype, count=None, device=None):
+    """(pointer, on_device) for a numpy array or a torch tensor; with ``count``
+    the buffer must hold exactly that many values, and a CUDA tensor must
+    live on ``device`` (the handle's device) when that is given."""
     if isinstance(a, np.ndarray):
         if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
             raise ValueError(f"need a C-contiguous {dtype} array")
+        if count is not None and a.size != count:
+            raise ValueError(f"need {count} values, got {a.size}")
         return ctypes.c_void_p(a.ctypes.data), 0
     # torch tensor
     if not a.is_contiguous() or str(a.dtype) != "torch.float64":
         raise ValueError("need a contiguous float64 tensor")
+    if count is not None and a.numel() != count:
+        raise ValueError(f"need {count} values, got {a.numel()}")
+    if a.is_cuda and device is not None and a.device.index != device:
+        raise ValueError(f"tensor on cuda:{a.device.index}, the solver on cuda:{device}")
     return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+def _current_device():
+    """The CUDA device current at handle creation (the handle's device), or
+    None when torch is not loaded."""
+    import sys
+    torch = sys.modules.get("torch")
+    if torch is None:
+        return None
+    try:
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except Exception:
+        return None
 
 
 def _mesh_struct(mesh: dict, keep: list) -> sd_mesh:
@@ -186,6 +207,10 @@ class Solver:
         self.E, self.N, self.n_dofs = E.value, N.value, n.value
         self.p = self.N - 1
         self.shape = (self.E, 4, self.N, self.N)
+        self.device = _current_device()
+
+    def _state_ptr(self, a):
+        return _ptr(a, np.float64, self.n_dofs, self.device)
 
     def __init__(self, mesh: dict, p: int, params, precision: int = SD_PREC_FP64, stream=None):
         L = lib()
@@ -213,13 +238,13 @@ class Solver:
         self.close()
 
     def sd_set_state(self, Q):
-        p, dev = _ptr(Q, np.float64)
+        p, dev = self._state_ptr(Q)
         self._check(lib().sd_set_state(self._h, p, dev))
 
     def sd_get_state(self, out=None):
         if out is None:
             out = np.empty(self.shape)
-        p, dev = _ptr(out, np.float64)
+        p, dev = self._state_ptr(out)
         self._check(lib().sd_get_state(self._h, p, dev))
         return out
 
@@ -234,7 +259,7 @@ class Solver:
     def sd_residual(self, out=None):
         if out is None:
             out = np.empty(self.shape)
-        p, dev = _ptr(out, np.float64)
+        p, dev = self._state_ptr(out)
         self._check(lib().sd_residual(self._h, p, dev))
         return out
 
@@ -244,7 +269,7 @@ class Solver:
         cannot allocate, or is created here in host memory."""
         if out is None:
             out = np.empty(self.shape)
-        p, dev = _ptr(out, np.float64)
+        p, dev = self._state_ptr(out)
         self._check(lib().sd_residual_noalloc(self._h, p, dev))
         return out
 
@@ -257,7 +282,7 @@ class Solver:
     def sd_sp_coords(self, t=0.0, out=None):
         if out is None:
             out = np.empty((self.E, self.N, self.N, 2))
-        p, dev = _ptr(out, np.float64)
+        p, dev = _ptr(out, np.float64, self.E * self.N * self.N * 2, self.device)
         self._check(lib().sd_sp_coords(self._h, float(t), p, dev))
         return out
 

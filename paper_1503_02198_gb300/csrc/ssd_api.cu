@@ -7,7 +7,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -229,14 +228,18 @@ const int kFaceB[4] = {1, 2, 2, 3};  // end corner
 
 struct IfaceSide {
   std::vector<int4> face;
-  std::vector<double> a, w, S, iw;
+  std::vector<double> a, a_lo, w, S, iw;  // start angle as a double-double a + a_lo
 };
 
 // one side of the interface of circle (cx, cy, r), appended to out sorted
-// counter-clockwise
+// counter-clockwise.  The angles are formed in long double and the start
+// angle is kept as a double-double (hi + lo): the mortar offsets of Eq. xz
+// are differences of such angles (see the merge kernel).
 int build_iface(sd_handle *h, const sd_mesh *m, double cx, double cy, double r_if, int n, const int *lst,
                 std::vector<int> &kind, int tag, IfaceSide &out) {
-  struct Item { int ef, rev; double a, w, S; };
+  typedef long double ld;
+  const ld tp = 6.283185307179586476925286766559005768L;
+  struct Item { int ef, rev; ld a, w; double S; };
   std::vector<Item> items;
   if (n > 0 && !lst) return fail(h, SD_ERR_ARG, "interface face list missing");
   for (int k = 0; k < n; ++k) {
@@ -247,39 +250,41 @@ int build_iface(sd_handle *h, const sd_mesh *m, double cx, double cy, double r_i
     kind[ef] = tag;
     if (!m->edge_arc[ef]) return fail(h, SD_ERR_MESH, "interface face is not flagged as an arc");
     const int na = m->elem_nodes[4 * e + kFaceA[f]], nb = m->elem_nodes[4 * e + kFaceB[f]];
-    const double ax = m->xy[2 * na] - cx, ay = m->xy[2 * na + 1] - cy;
-    const double bx = m->xy[2 * nb] - cx, by = m->xy[2 * nb + 1] - cy;
-    const double ra = std::hypot(ax, ay), rb = std::hypot(bx, by);
+    const ld ax = (ld)m->xy[2 * na] - cx, ay = (ld)m->xy[2 * na + 1] - cy;
+    const ld bx = (ld)m->xy[2 * nb] - cx, by = (ld)m->xy[2 * nb + 1] - cy;
+    const double ra = (double)std::hypot(ax, ay), rb = (double)std::hypot(bx, by);
     if (std::fabs(ra - r_if) > 1e-9 * std::max(1.0, r_if) || std::fabs(rb - r_if) > 1e-9 * std::max(1.0, r_if))
       return fail(h, SD_ERR_MESH, "interface node not on the interface circle");
-    const double d = std::atan2(ax * by - ay * bx, ax * bx + ay * by);  // signed angle a -> b
+    const ld d = std::atan2(ax * by - ay * bx, ax * bx + ay * by);  // signed angle a -> b
     Item it;
     it.ef = ef;
-    double start = d > 0 ? std::atan2(ay, ax) : std::atan2(by, bx);
-    start = std::fmod(start, 2 * kPi);
-    if (start < 0) start += 2 * kPi;
+    ld start = d > 0 ? std::atan2(ay, ax) : std::atan2(by, bx);
+    start = std::fmod(start, tp);
+    if (start < 0) start += tp;
     it.a = start;
     it.w = std::fabs(d);
     it.rev = d > 0 ? 0 : 1;
-    it.S = ra * it.w;
+    it.S = ra * (double)it.w;
     items.push_back(it);
   }
   std::sort(items.begin(), items.end(), [](const Item &p, const Item &q) { return p.a < q.a; });
-  double total = 0.0;
+  ld total = 0.0;
   for (int k = 0; k < n; ++k) {
     total += items[k].w;
     const Item &p = items[k], &q = items[(k + 1) % n];
-    double gap = std::fmod(q.a - (p.a + p.w) + 4 * kPi, 2 * kPi);
-    if (gap > kPi) gap -= 2 * kPi;
-    if (std::fabs(gap) > 1e-9) return fail(h, SD_ERR_MESH, "interface faces do not tile the circle");
+    ld gap = std::fmod(q.a - (p.a + p.w) + 2 * tp, tp);
+    if (gap > tp / 2) gap -= tp;
+    if (std::fabs(gap) > 1e-9L) return fail(h, SD_ERR_MESH, "interface faces do not tile the circle");
   }
-  if (n > 0 && std::fabs(total - 2 * kPi) > 1e-9) return fail(h, SD_ERR_MESH, "interface side does not close");
+  if (n > 0 && std::fabs(total - tp) > 1e-9L) return fail(h, SD_ERR_MESH, "interface side does not close");
   for (auto &it : items) {
     out.face.push_back(make_int4(it.ef, it.rev, 0, 0));
-    out.a.push_back(it.a);
-    out.w.push_back(it.w);
+    const double hi = (double)it.a;
+    out.a.push_back(hi);
+    out.a_lo.push_back((double)(it.a - (ld)hi));
+    out.w.push_back((double)it.w);
     out.S.push_back(it.S);
-    out.iw.push_back(1.0 / it.w);
+    out.iw.push_back((double)(1.0L / it.w));
   }
   return SD_OK;
 }
@@ -473,7 +478,7 @@ int build_mesh(sd_handle *h, const sd_mesh *m, double omega1) {
   }
   cudaError_t ce;
   int4 *dfaces, *dbfaces, *dL, *dR;
-  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS, *dLiW, *dRiW, *dcub = nullptr, *dzpar;
+  double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS, *dLiW, *dRiW, *dcub = nullptr, *dzpar, *dLal, *dRal;
   int *darcs, *dzone, *dframe, *dzoff, *difz;
   if ((ce = upload(h, &dfaces, faces.data(), faces.size())) || (ce = upload(h, &dbfaces, bfaces.data(), bfaces.size())) ||
       (ce = upload(h, &dL, L.face.data(), L.face.size())) || (ce = upload(h, &dR, R.face.data(), R.face.size())) ||
@@ -481,6 +486,7 @@ int build_mesh(sd_handle *h, const sd_mesh *m, double omega1) {
       (ce = upload(h, &dLS, L.S.data(), L.S.size())) || (ce = upload(h, &dRa, R.a.data(), R.a.size())) ||
       (ce = upload(h, &dRw, R.w.data(), R.w.size())) || (ce = upload(h, &dRS, R.S.data(), R.S.size())) ||
       (ce = upload(h, &dLiW, L.iw.data(), L.iw.size())) || (ce = upload(h, &dRiW, R.iw.data(), R.iw.size())) ||
+      (ce = upload(h, &dLal, L.a_lo.data(), L.a_lo.size())) || (ce = upload(h, &dRal, R.a_lo.data(), R.a_lo.size())) ||
       (ce = upload(h, &dcorn, corners.data(), corners.size())) || (ce = upload(h, &darcs, arcs.data(), arcs.size())) ||
       (ce = upload(h, &dzone, m->elem_zone, (size_t)E)) || (ce = upload(h, &dframe, frame.data(), frame.size())) ||
       (ce = upload(h, &dzpar, zpar.data(), zpar.size())) || (ce = upload(h, &dzoff, zoff.data(), zoff.size())) ||
@@ -494,6 +500,8 @@ int build_mesh(sd_handle *h, const sd_mesh *m, double omega1) {
   md.Lface = dL;
   md.Rface = dR;
   md.La = dLa;
+  md.La_lo = dLal;
+  md.Ra_lo = dRal;
   md.Lw = dLw;
   md.LS = dLS;
   md.Ra = dRa;
@@ -558,7 +566,7 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   if ((e = dalloc(h, &md.contrib, w * 2 * nb * 4 * N))) return e;
   if ((e = dalloc(h, &md.mLf, sizeof(int) * nb))) return e;
   if ((e = dalloc(h, &md.mRf, sizeof(int) * nb))) return e;
-  if ((e = dalloc(h, &md.mgeo, sizeof(double) * 2 * nb))) return e;
+  if ((e = dalloc(h, &md.mgeo, sizeof(double) * 4 * nb))) return e;
   if ((e = dalloc(h, &md.fgeo, w * 5 * N * (md.nF ? md.nF : 1)))) return e;
   if ((e = dalloc(h, &md.Lstart, sizeof(int) * md.nL))) return e;
   if ((e = dalloc(h, &md.Lcount, sizeof(int) * md.nL))) return e;
@@ -592,13 +600,13 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
     sm.clk[k] = sclk + k;
     if ((e = dalloc(h, &sm.mLf[k], sizeof(int) * nb))) return e;
     if ((e = dalloc(h, &sm.mRf[k], sizeof(int) * nb))) return e;
-    if ((e = dalloc(h, &sm.mgeo[k], sizeof(double) * 2 * nb))) return e;
+    if ((e = dalloc(h, &sm.mgeo[k], sizeof(double) * 4 * nb))) return e;
     if ((e = dalloc(h, &sm.Lstart[k], sizeof(int) * md.nL))) return e;
     if ((e = dalloc(h, &sm.Lcount[k], sizeof(int) * md.nL))) return e;
     if ((e = dalloc(h, &sm.Rstart[k], sizeof(int) * md.nR))) return e;
     if ((e = dalloc(h, &sm.Rcount[k], sizeof(int) * md.nR))) return e;
     if ((e = dalloc(h, &sm.work_i[k], sizeof(int) * (2 * nb + 1)))) return e;
-    if ((e = dalloc(h, &sm.work_d[k], sizeof(double) * (md.nL + nb + 1)))) return e;
+    if ((e = dalloc(h, &sm.work_d[k], sizeof(double) * (2 * nb + 1)))) return e;
   }
   if ((e = cudaMemsetAsync(md.CF, 0, w * Ep * 16 * N, h->stream))) return e;
   // zero state
@@ -1375,30 +1383,20 @@ int sd_batch_sync(sd_batch *b) {
 //
 // Work memory of sd_residual_noalloc: one file-scope device array that every
 // GPU loading this library holds until the process exits.  Its name is only a
-// host-side stand-in in host code; the device address comes from
-// cudaGetSymbolAddress, taken once per device.
+// host-side stand-in in host code; the device address of the current device's
+// copy comes from cudaGetSymbolAddress, looked up on every call (a cached
+// address would go stale after cudaDeviceReset or a new primary context).
 static constexpr size_t kNoAllocBytes = 16u << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
-std::mutex g_noalloc_mutex;
-void *g_noalloc_ptr[256] = {};
-
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 cudaError_t noalloc_base(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e) return e;
-  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e) return e;
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return cudaSuccess;
 }
 }  // namespace
@@ -1412,14 +1410,14 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   size_t off = 0;
   const size_t o_mLf = off; off += align256(sizeof(int) * nb);
   const size_t o_mRf = off; off += align256(sizeof(int) * nb);
-  const size_t o_mgeo = off; off += align256(sizeof(double) * 2 * nb);
+  const size_t o_mgeo = off; off += align256(sizeof(double) * 4 * nb);
   const size_t o_Ls = off; off += align256(sizeof(int) * md0.nL);
   const size_t o_Lc = off; off += align256(sizeof(int) * md0.nL);
   const size_t o_Rs = off; off += align256(sizeof(int) * md0.nR);
   const size_t o_Rc = off; off += align256(sizeof(int) * md0.nR);
   const size_t o_con = off; off += align256(w * 2 * nb * 4 * N);
   const size_t o_wi = off; off += align256(sizeof(int) * (2 * nb + 1));
-  const size_t o_wd = off; off += align256(sizeof(double) * (md0.nL + nb + 1));
+  const size_t o_wd = off; off += align256(sizeof(double) * (2 * nb + 1));
   const size_t o_R = off;
   if (!on_device) off += align256(state_bytes(h));
   if (off > kNoAllocBytes) {
@@ -1455,6 +1453,13 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   if (!on_device) e = cudaMemcpyAsync(R, dst, state_bytes(h), cudaMemcpyDeviceToHost, h->stream);
   if (!e) e = cudaStreamSynchronize(h->stream);
   if (e) return cuda_fail(h, e, "sd_residual_noalloc");
+  // a bounded device wait that gave up leaves R incomplete: report it here,
+  // as sd_sync would (the flag read uses the handle's pinned buffer)
+  int flags = 0;
+  const int rc = read_flags(h, &flags, true);
+  if (rc) return rc;
+  if (flags & 4) return fail(h, SD_ERR_TIMEOUT, "a bounded device wait gave up (tile copy did not arrive)");
+  if (flags & 1) return fail(h, SD_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite)");
   return SD_OK;
 }
 

@@ -542,47 +542,98 @@ __device__ __forceinline__ void rusanov(const T *qL, const T *qR, T nx, T ny, T 
 // per-stage coupling kernels
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double wrap_2pi(double a) {
-  const double tp = 6.283185307179586476925286766559;
-  double r = fmod(a, tp);
-  return r < 0.0 ? r + tp : r;
+// Double-double angles (an unevaluated sum hi + lo, |lo| <= ulp(hi) / 2) for
+// the sliding interface: a mortar offset o = (phi_m - phi_f) / width is a
+// difference of two angles near pi divided by a small width, so the absolute
+// round-off of FP64 angles (~1e-16) becomes ~1e-14 in o and reaches the
+// residual of the interface cells amplified by the flux-derivative weights.
+// The t = 0 face angles come from the host in long double; the rotation
+// angle omega t is formed exactly and reduced with a double-double 2 pi.
+struct ddang {
+  double hi, lo;
+};
+
+// 2 pi = kTwoPiHi + kTwoPiLo to about 1e-32
+constexpr double kTwoPiHi = 6.283185307179586476925286766559;
+constexpr double kTwoPiLo = 2.4492935982947064e-16;
+
+// s + e = a + b exactly (Knuth's two-sum)
+__device__ __forceinline__ ddang dd_two_sum(double a, double b) {
+  const double s = a + b;
+  const double bb = s - a;
+  return ddang{s, (a - (s - bb)) + (b - bb)};
 }
 
-__device__ __forceinline__ double wrap_pi(double a) {
-  const double pi = 3.14159265358979323846264338328;
-  return wrap_2pi(a + pi) - pi;
+__device__ __forceinline__ ddang dd_add(ddang a, ddang b) {
+  const ddang s = dd_two_sum(a.hi, b.hi);
+  const double lo = s.lo + (a.lo + b.lo);
+  const double hi = s.hi + lo;
+  return ddang{hi, lo - (hi - s.hi)};
+}
+
+__device__ __forceinline__ ddang dd_sub(ddang a, ddang b) { return dd_add(a, ddang{-b.hi, -b.lo}); }
+
+__device__ __forceinline__ bool dd_lt(ddang a, ddang b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool dd_le(ddang a, ddang b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+
+// into [0, 2 pi) for an angle in [-2 pi, 4 pi)
+__device__ __forceinline__ ddang dd_wrap_2pi(ddang a) {
+  const ddang tp{kTwoPiHi, kTwoPiLo};
+  if (dd_lt(a, ddang{0.0, 0.0})) return dd_add(a, tp);
+  if (!dd_lt(a, tp)) return dd_sub(a, tp);
+  return a;
+}
+
+// theta = omega t reduced to [0, 2 pi) as a double-double: the product is
+// exact (p + e, with the FMA), k = floor(p / 2 pi) turns are taken off with
+// the exact product k kTwoPiHi and k kTwoPiLo
+__device__ __forceinline__ ddang dd_rotation_angle(double om, double t) {
+  const double p = om * t;
+  const double e = fma(om, t, -p);
+  const double k = floor(p / kTwoPiHi);
+  const double kh = k * kTwoPiHi;
+  const double kl = fma(k, kTwoPiHi, -kh);
+  const ddang r = dd_two_sum(p, -kh);
+  const double small = (e - kl) - k * kTwoPiLo;
+  const double lo = r.lo + small;
+  const double hi = r.hi + lo;
+  return dd_wrap_2pi(ddang{hi, lo - (hi - r.hi)});
 }
 
 // Stage clock and mortar table of interface ii (Sec. 3.2: connectivity
 // updated at every stage).  Its mortar k is the interval between merged node
 // positions k and k+1 (counter-clockwise, cyclic); nodes of both sides sorted
-// by angle, L before R on ties.  One CTA per interface; the node angles are
-// searched in shared memory (dynamic, (nL + nR) doubles of the interface);
-// work_i / work_d hold the merged positions and angles.  The CTA of interface
-// 0 also writes the stage clock of every zone: theta_z = omega_z t_stage.
-// The offsets and scales of Eq. xz are formed per mortar in k_mortar_flux.
-// The step's start time t_n is read from *tsrc; the stage clock and the table
-// are written through md.
+// by angle, L before R on ties.  One CTA per interface; the node angles
+// (double-double) are searched in shared memory (dynamic, 2 (nL + nR) doubles
+// of the interface: high parts, then low parts); work_i / work_d hold the
+// merged positions and angles.  The CTA of interface 0 also writes the stage
+// clock of every zone: theta_z = omega_z t_stage.  The offsets and scales of
+// Eq. xz are formed per mortar in the mortar flux.  The step's start time t_n
+// is read from *tsrc; the stage clock and the table are written through md.
 static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, double dt, int *work_i,
                                         double *work_d, const DevClock *tsrc) {
-  extern __shared__ double s_ang[];  // [nL] rotated L angles, then [nR] R angles
-  __shared__ double s_th2;
+  extern __shared__ double s_ang[];  // [nb] high parts (rotated L, then R), [nb] low parts
+  __shared__ double s_th2, s_th2lo;
   __shared__ int s_k0;
-  const double tp = 6.283185307179586476925286766559;
   const double ts = tsrc->t_n + c * dt;
   if (ii == 0 && threadIdx.x < kZT) {
     DevClock *k = md.clk;
     const int z = threadIdx.x;
     const double om = z ? md.zpar[4 * z + 2] : 0.0;
-    double sn = 0.0, cs = 1.0, th2 = 0.0;
+    double sn = 0.0, cs = 1.0;
+    ddang th{0.0, 0.0};
     if (z) {
-      const double th = om * ts;
-      th2 = wrap_2pi(th);
-      sincos(th, &sn, &cs);
+      th = dd_rotation_angle(om, ts);
+      double sh, ch;
+      sincos(th.hi, &sh, &ch);
+      // R(theta) of the double-double angle: first order in the low part
+      cs = ch - sh * th.lo;
+      sn = sh + ch * th.lo;
     } else {
       k->t_stage = ts;
     }
-    k->theta2[z] = th2;
+    k->theta2[z] = th.hi;
+    k->theta2_lo[z] = th.lo;
     k->c[z] = cs;
     k->s[z] = sn;
     k->om[z] = om;
@@ -594,56 +645,66 @@ static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, dou
   const int nL = md.zoff[ii + 1] - Lo, nR = md.zoff[kZT + ii + 1] - Ro, nb = nL + nR;
   const int Mo = Lo + Ro;
   if (threadIdx.x == 0) {
-    s_th2 = wrap_2pi(md.zpar[4 * (ii + 1) + 2] * ts);
+    const ddang th = dd_rotation_angle(md.zpar[4 * (ii + 1) + 2], ts);
+    s_th2 = th.hi;
+    s_th2lo = th.lo;
     s_k0 = 0;
   }
   __syncthreads();
   if (nL == 0) return;
-  const double th2 = s_th2;
-  double *sL = s_ang, *sR = s_ang + nL;
+  const ddang th2{s_th2, s_th2lo};
+  double *sLh = s_ang, *sRh = s_ang + nL, *sLl = s_ang + nb, *sRl = s_ang + nb + nL;
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
-    const double a = md.La[Lo + k] + th2;
-    sL[k] = a >= tp ? a - tp : a;
+    const ddang a = dd_wrap_2pi(dd_add(ddang{md.La[Lo + k], md.La_lo[Lo + k]}, th2));
+    sLh[k] = a.hi;
+    sLl[k] = a.lo;
   }
-  for (int k = threadIdx.x; k < nR; k += blockDim.x) sR[k] = md.Ra[Ro + k];
+  for (int k = threadIdx.x; k < nR; k += blockDim.x) {
+    sRh[k] = md.Ra[Ro + k];
+    sRl[k] = md.Ra_lo[Ro + k];
+  }
   __syncthreads();
   // rotated L angles are a cyclic shift of an ascending list; k0 = index of the minimum
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
     const int kp = k == 0 ? nL - 1 : k - 1;
-    if (sL[k] < sL[kp]) s_k0 = k;
+    if (dd_lt(ddang{sLh[k], sLl[k]}, ddang{sLh[kp], sLl[kp]})) s_k0 = k;
   }
   __syncthreads();
   const int k0 = s_k0;
-  double *mAng = work_d + Mo;     // [nb] merged angles
+  const int nMall = md.nM;
+  double *mAh = work_d + Mo;          // [nb] merged angles: high parts
+  double *mAl = work_d + nMall + Mo;  // and low parts
   int *posL = work_i + 2 * Mo;    // [nL] merged position of L node k (t = 0 index)
   int *posR = posL + nL;          // [nR]
   int *otherL = posL + nb;        // [nL] R face containing the mortar that starts at L node k
   int *otherR = otherL + nL;      // [nR] L face containing the mortar that starts at R node k
   for (int k = threadIdx.x; k < nL; k += blockDim.x) {
-    const double a = sL[k];
+    const ddang a{sLh[k], sLl[k]};
     const int rank = (k - k0 + nL) % nL;
     int lo = 0, hi = nR;  // number of R angles strictly below a
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (sR[mid] < a) lo = mid + 1; else hi = mid;
+      if (dd_lt(ddang{sRh[mid], sRl[mid]}, a)) lo = mid + 1; else hi = mid;
     }
     const int p = rank + lo;
     posL[k] = p;
-    mAng[p] = a;
+    mAh[p] = a.hi;
+    mAl[p] = a.lo;
     otherL[k] = lo == 0 ? nR - 1 : lo - 1;
   }
   for (int k = threadIdx.x; k < nR; k += blockDim.x) {
-    const double a = sR[k];
+    const ddang a{sRh[k], sRl[k]};
     int lo = 0, hi = nL;  // number of rotated L angles <= a (L first on ties)
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       int idx = k0 + mid;
       if (idx >= nL) idx -= nL;
-      if (sL[idx] <= a) lo = mid + 1; else hi = mid;
+      if (dd_le(ddang{sLh[idx], sLl[idx]}, a)) lo = mid + 1; else hi = mid;
     }
     const int p = k + lo;
     posR[k] = p;
-    mAng[p] = a;
+    mAh[p] = a.hi;
+    mAl[p] = a.lo;
     otherR[k] = lo == 0 ? (k0 + nL - 1) % nL : (k0 + lo - 1) % nL;
   }
   __syncthreads();
@@ -665,10 +726,14 @@ static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, dou
   }
   __syncthreads();
   for (int p = threadIdx.x; p < nb; p += blockDim.x) {
-    const double a = mAng[p];
-    const double b = p + 1 < nb ? mAng[p + 1] : mAng[0] + tp;
-    md.mgeo[2 * (Mo + p)] = a;
-    md.mgeo[2 * (Mo + p) + 1] = b - a;
+    const ddang a{mAh[p], mAl[p]};
+    const ddang b = p + 1 < nb ? ddang{mAh[p + 1], mAl[p + 1]}
+                               : dd_add(ddang{mAh[0], mAl[0]}, ddang{kTwoPiHi, kTwoPiLo});
+    const ddang d = dd_sub(b, a);
+    md.mgeo[4 * (Mo + p)] = a.hi;
+    md.mgeo[4 * (Mo + p) + 1] = a.lo;
+    md.mgeo[4 * (Mo + p) + 2] = d.hi + d.lo;
+    md.mgeo[4 * (Mo + p) + 3] = 0.0;
   }
 }
 
@@ -898,18 +963,23 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
   int ef = 0, rev = 0;
   double m0 = 0.0, dm = 0.0;
   if (act) {
-    // Eq. xz: offset and scale of this mortar against its face on side sd
-    m0 = md.mgeo[2 * m];
-    dm = md.mgeo[2 * m + 1];
-    const double tp = 6.283185307179586476925286766559, pi = 0.5 * tp;
+    // Eq. xz: offset and scale of this mortar against its face on side sd,
+    // the angle difference in double-double
+    const ddang m0d{md.mgeo[4 * m], md.mgeo[4 * m + 1]};
+    m0 = m0d.hi;
+    dm = md.mgeo[4 * m + 2];
+    const double pi = 0.5 * kTwoPiHi;
     const int fq = sd ? md.mRf[m] : md.mLf[m];
     // the L side turns with its zone (interface ifz[fq] belongs to zone ifz[fq] + 1)
-    const double th2 = sd ? 0.0 : md.clk->theta2[md.ifz[fq] + 1];
-    double fa = sd ? md.Ra[fq] : md.La[fq] + th2;
-    if (fa >= tp) fa -= tp;
-    double off = m0 - fa;
-    if (off > pi) off -= tp;
-    if (off <= -pi) off += tp;
+    ddang fa{md.Ra[fq], md.Ra_lo[fq]};
+    if (!sd) {
+      const int z = md.ifz[fq] + 1;
+      fa = dd_wrap_2pi(dd_add(ddang{md.La[fq], md.La_lo[fq]}, ddang{md.clk->theta2[z], md.clk->theta2_lo[z]}));
+    }
+    ddang offd = dd_sub(m0d, fa);
+    if (offd.hi > pi) offd = dd_sub(offd, ddang{kTwoPiHi, kTwoPiLo});
+    if (offd.hi <= -pi) offd = dd_add(offd, ddang{kTwoPiHi, kTwoPiLo});
+    const double off = offd.hi + offd.lo;
     const double iw = sd ? md.RiW[fq] : md.LiW[fq];
     o = off * iw;
     s = dm * iw;
@@ -926,11 +996,8 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
       for (int v = 0; v < 4; ++v) q[v] = CQ[((size_t)ef * 4 + v) * N + jj];
 #pragma unroll
       for (int c = 0; c < 8; ++c) g8[c] = GT[((size_t)ef * 8 + c) * N + jj];
-      const double tp = 6.283185307179586476925286766559;
-      double fa = sd ? md.Ra[fq] : md.La[fq] + th2;
-      if (fa >= tp) fa -= tp;
       double sn, cs;
-      sincos(fa + B.Xs[p] * (sd ? md.Rw[fq] : md.Lw[fq]), &sn, &cs);
+      sincos(fa.hi + (fa.lo + B.Xs[p] * (sd ? md.Rw[fq] : md.Lw[fq])), &sn, &cs);
       viscous_normal(q, g8, (T)cs, (T)sn, md, fn);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sQf[lm][sd][NV - 4 + v][p] = fn[v];
@@ -994,7 +1061,7 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
   if (act && sd == 0) {
     if (MMODE != MORTAR_AVG_Q) {
       double sn, cs;
-      sincos(fma(B.Xs[p], dm, m0), &sn, &cs);
+      sincos(m0 + fma(B.Xs[p], dm, md.mgeo[4 * m + 1]), &sn, &cs);
       T qL[4], qR[4], Fn[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -1061,11 +1128,7 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
 enum { GATHER_FLUX = 0, GATHER_Q = 1 };
 
 template <typename T, int N, int GMODE>
-__global__ void k_mortar_gather(MeshDev md) {
-  pdl_enter();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nLR = md.nL + md.nR;
-  if (t >= nLR * N) return;
+__device__ __forceinline__ void gather_point(const MeshDev &md, int t) {
   const int fq = t / N, p = t - fq * N;
   const int sd = fq >= md.nL;
   const int k = sd ? fq - md.nL : fq;
@@ -1099,6 +1162,13 @@ __global__ void k_mortar_gather(MeshDev md) {
     const size_t i = ((size_t)ef * 4 + v) * N + j;
     CF[i] = sc * acc[v];
   }
+}
+
+template <typename T, int N, int GMODE>
+__global__ void k_mortar_gather(MeshDev md) {
+  pdl_enter();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (md.nL + md.nR) * N) gather_point<T, N, GMODE>(md, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -1201,12 +1271,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-template <typename T, int N, bool OTF, bool AUX = false, bool LO = true>
+// default elements per volume tile (a multiple of 4)
+template <int N>
+constexpr int vol_epb_default() { return N == 3 ? 16 : (N == 6 ? 8 : 12); }
+
+template <typename T, int N, bool OTF, bool AUX = false, bool LO = true, int EPBX = 0>
 struct VolCfg {
   static constexpr int NN = N * N;
   static constexpr bool FF = std::is_same<T, float>::value;  // FP32 arithmetic (packed pairs)
   static constexpr bool DF = FF && LO;                       // double-float state (hi + lo planes)
-  static constexpr int EPB = N == 3 ? 16 : (N == 6 ? 8 : 12);  // elements per tile (multiple of 4)
+  static constexpr int EPB = EPBX ? EPBX : vol_epb_default<N>();  // elements per tile (multiple of 4)
   static constexpr int THREADS = EPB * 2 * N;                  // one thread per SP line
   // element strides (values) of the tiles in shared memory: padded so that
   // the elements of a tile start in different banks (a stride of 4 N^2 or 16 N
@@ -1236,9 +1310,10 @@ struct VolCfg {
   // work arrays
   static constexpr int O_RF = SINGLE_END, O_RG = O_RF + QHI;
   static constexpr int O_BAR = ((O_RG + QHI) + 15) / 16 * 16;
-  // the stage's zone table [3][kZT] (cos theta_z, sin theta_z, omega_z)
+  // the stage's zone table [3][kZT] (cos theta_z, sin theta_z, omega_z); two
+  // slots, one per pipeline stage, for a batch whose next item is another case
   static constexpr int O_ZT = O_BAR + 32;
-  static constexpr int SMEM = O_ZT + 3 * kZT * (int)sizeof(T);
+  static constexpr int SMEM = O_ZT + 2 * 3 * kZT * (int)sizeof(T);
   // transaction bytes of the two barriers' copies
   static constexpr int TX_QHI = EPB * QE, TX_CF = EPB * CE;
   static_assert((SE * (int)sizeof(T)) % 16 == 0 && (SC * (int)sizeof(T)) % 16 == 0, "bulk-copy alignment");
@@ -1274,12 +1349,68 @@ struct RkCoef {
   T a0, bdt, g, ddt;
 };
 
-template <typename T, int N, int MODE, bool OTF, bool AUX, bool LO>
-__global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T, N, OTF, AUX, LO>::MINB)
-    k_volume(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
-             T *w_out, const T *w_in, int ntiles) {
+// Arguments of one case's volume launch: the states it reads and writes, the
+// residual output (MODE_RESIDUAL), the stage coefficients and the increments
+// carried between stages of the five-stage scheme.
+template <typename T>
+struct VolArgs {
+  StatePtr in, base, out;
+  double *R;
+  RkCoef<T> rk;
+  int has_base;
+  T *w_out;
+  const T *w_in;
+};
+
+// Work sources of the persistent kernels.  A work item is one tile of one
+// case; the source names the case and its tile and gives that case's mesh
+// view and launch arguments A.  OneCase: one handle, whose tiles are the
+// items.  CaseList: the cases of a batch class, items numbered across all of
+// them (off[c] = first item of case c, off[n] = all items), each case's view
+// and arguments in device memory.
+template <typename A>
+struct OneCase {
+  static constexpr bool kMulti = false;
+  MeshDev md;
+  A a;
+  __device__ __forceinline__ void item(int it, int &c, int &tile) const {
+    c = 0;
+    tile = it;
+  }
+  __device__ __forceinline__ const MeshDev &mesh(int) const { return md; }
+  __device__ __forceinline__ const A &args(int) const { return a; }
+};
+
+template <typename A>
+struct CaseList {
+  static constexpr bool kMulti = true;
+  const MeshDev *md;
+  const A *a;
+  const int *off;
+  int n;
+  __device__ __forceinline__ void item(int it, int &c, int &tile) const {
+    int lo = 0, hi = n - 1;  // the last case whose first item is <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(off + mid) <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    c = lo;
+    tile = it - __ldg(off + lo);
+  }
+  __device__ __forceinline__ const MeshDev &mesh(int c) const { return md[c]; }
+  __device__ __forceinline__ const A &args(int c) const { return a[c]; }
+};
+
+// The persistent volume kernel over the work items of src (see OneCase /
+// CaseList): for a batch class the items of all its cases form one list, and
+// the next item's copies are issued while the current one computes even when
+// it belongs to another case.
+template <typename T, int N, int MODE, bool OTF, bool AUX, bool LO, int EPBX, class Src>
+__global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX>::THREADS, VolCfg<T, N, OTF, AUX, LO, EPBX>::MINB)
+    k_volume(Src src, int nitems) {
   pdl_enter();
-  using C = VolCfg<T, N, OTF, AUX, LO>;
+  using C = VolCfg<T, N, OTF, AUX, LO, EPBX>;
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
   constexpr bool FF = C::FF, DF = C::DF;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1287,37 +1418,45 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
   T(*sRF)[C::SE] = (T(*)[C::SE])(smem + C::O_RF);
   T(*sRG)[C::SE] = (T(*)[C::SE])(smem + C::O_RG);
   const VolBasis<T, N> &B = cVB<T, N>;
-  const bool use_base = MODE == MODE_RK && has_base;
-  const uint32_t txA = C::TX_QHI + C::TX_CF + C::EGB + C::EFB;
-  const uint32_t txB = MODE == MODE_RK ? C::QBL + (use_base ? C::QB + C::QBL : 0) + C::AUXB : 0;
-  T *sZT = (T *)(smem + C::O_ZT);
-  const T gm1 = pick<T>(md.gamma, md.gamma_f) - T(1);
+  // the zone table of the item's case: one copy for a single case, a copy per
+  // stage of the pipeline for a batch (the next item may be another case)
+  T *sZT0 = (T *)(smem + C::O_ZT);
 
   // copies are issued by the lanes of warp 0, one element each, into the
   // padded tile; lane 0 first arms the barrier with the whole byte count
-  auto issueA = [&](int tl, int st, int lane) {
+  auto issueA = [&](int item, int st, int lane) {
+    int cn, tl;
+    src.item(item, cn, tl);
+    const MeshDev &mn = src.mesh(cn);
+    const VolArgs<T> &an = src.args(cn);
     unsigned char *sb = smem + st * C::STAGE;
     const size_t e0 = (size_t)tl * EPB;
-    if (lane == 0) mbar_expect_tx(&bar[st], txA);
+    if (lane == 0) mbar_expect_tx(&bar[st], C::TX_QHI + C::TX_CF + C::EGB + C::EFB);
     __syncwarp();
     if (lane < EPB) {
-      bulk_g2s(sb + C::O_QHI + lane * C::SE * sizeof(T), (const T *)in.hi + (e0 + lane) * 4 * NN, C::QE, &bar[st]);
-      bulk_g2s(sb + C::O_CF + lane * C::SC * sizeof(T), (const T *)md.CF + (e0 + lane) * 16 * N, C::CE, &bar[st]);
+      bulk_g2s(sb + C::O_QHI + lane * C::SE * sizeof(T), (const T *)an.in.hi + (e0 + lane) * 4 * NN, C::QE, &bar[st]);
+      bulk_g2s(sb + C::O_CF + lane * C::SC * sizeof(T), (const T *)mn.CF + (e0 + lane) * 16 * N, C::CE, &bar[st]);
     }
     if (lane == 0) {
-      if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, C::EGB, &bar[st]);
-      bulk_g2s(sb + C::O_EF, md.eflag + e0, C::EFB, &bar[st]);
+      if (OTF) bulk_g2s(sb + C::O_EG, (const T *)mn.egeo + e0 * 8, C::EGB, &bar[st]);
+      bulk_g2s(sb + C::O_EF, mn.eflag + e0, C::EFB, &bar[st]);
+    }
+    if constexpr (Src::kMulti) {
+      if (lane < 3 * kZT) sZT0[st * 3 * kZT + lane] = zone_tab<T>(mn.clk)[lane];
     }
   };
-  auto issueB = [&](int tl) {
+  auto txB_of = [&](const VolArgs<T> &a) -> uint32_t {
+    return MODE == MODE_RK ? C::QBL + (a.has_base ? C::QB + C::QBL : 0) + C::AUXB : 0;
+  };
+  auto issueB = [&](const VolArgs<T> &a, int tl) {
     const size_t e0 = (size_t)tl * EPB;
-    mbar_expect_tx(&bar[2], txB);
-    if (DF) bulk_g2s(smem + C::O_QLO, (const float *)in.lo + e0 * 4 * NN, C::QBL, &bar[2]);
-    if (use_base) {
-      bulk_g2s(smem + C::O_NHI, (const T *)base.hi + e0 * 4 * NN, C::QB, &bar[2]);
-      if (DF) bulk_g2s(smem + C::O_NLO, (const float *)base.lo + e0 * 4 * NN, C::QBL, &bar[2]);
+    mbar_expect_tx(&bar[2], txB_of(a));
+    if (DF) bulk_g2s(smem + C::O_QLO, (const float *)a.in.lo + e0 * 4 * NN, C::QBL, &bar[2]);
+    if (a.has_base) {
+      bulk_g2s(smem + C::O_NHI, (const T *)a.base.hi + e0 * 4 * NN, C::QB, &bar[2]);
+      if (DF) bulk_g2s(smem + C::O_NLO, (const float *)a.base.lo + e0 * 4 * NN, C::QBL, &bar[2]);
     }
-    if (AUX) bulk_g2s(smem + C::O_AUX, w_in + e0 * 4 * NN, C::AUXB, &bar[2]);
+    if (AUX) bulk_g2s(smem + C::O_AUX, a.w_in + e0 * 4 * NN, C::AUXB, &bar[2]);
   };
 
   if (threadIdx.x == 0) {
@@ -1326,27 +1465,37 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
     mbar_init(&bar[2], 1);
     fence_mbar_init();
   }
-  if (threadIdx.x < 3 * kZT) sZT[threadIdx.x] = zone_tab<T>(md.clk)[threadIdx.x];
+  if constexpr (!Src::kMulti) {
+    if (threadIdx.x < 3 * kZT) sZT0[threadIdx.x] = zone_tab<T>(src.mesh(0).clk)[threadIdx.x];
+  }
   __syncthreads();
-  int tile = blockIdx.x;
-  if (threadIdx.x < 32 && tile < ntiles) issueA(tile, 0, threadIdx.x);
+  int item = blockIdx.x;
+  if (threadIdx.x < 32 && item < nitems) issueA(item, 0, threadIdx.x);
   bool bad = false;
   int it = 0;
-  for (; tile < ntiles; tile += gridDim.x, ++it) {
+  for (; item < nitems; item += gridDim.x, ++it) {
     const int st = it & 1;
-    const int next = tile + gridDim.x;
+    const int next = item + gridDim.x;
+    int cs, tile;
+    src.item(item, cs, tile);
+    const MeshDev &md = src.mesh(cs);
+    const VolArgs<T> &va = src.args(cs);
+    const uint32_t txB = txB_of(va);
+    const bool use_base = MODE == MODE_RK && va.has_base;
+    const T gm1 = pick<T>(md.gamma, md.gamma_f) - T(1);
+    const T *sZT = Src::kMulti ? sZT0 + st * 3 * kZT : sZT0;
     if (threadIdx.x < 32) {
       // both refilled regions were last read before the previous iteration's
       // closing barrier; order those generic reads before the async writes
       fence_proxy_async_smem();
-      if (next < ntiles) issueA(next, st ^ 1, threadIdx.x);
-      if (txB && threadIdx.x == 0) issueB(tile);
+      if (next < nitems) issueA(next, st ^ 1, threadIdx.x);
+      if (txB && threadIdx.x == 0) issueB(va, tile);
     }
     if (!cta_wait(&bar[st], (uint32_t)((it >> 1) & 1))) {
       if (threadIdx.x == 0) {
         atomicOr(&md.clk->flags, 4);
         // let the copies in flight land before the CTA exits
-        if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        if (next < nitems) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
         if (txB) mbar_wait_bounded(&bar[2], (uint32_t)(it & 1));
       }
       return;
@@ -1494,7 +1643,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
       if (!cta_wait(&bar[2], (uint32_t)(it & 1))) {
         if (threadIdx.x == 0) {
           atomicOr(&md.clk->flags, 4);
-          if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+          if (next < nitems) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
         }
         return;
       }
@@ -1508,22 +1657,22 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
       const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
       if (MODE == MODE_RESIDUAL) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
+        for (int v = 0; v < 4; ++v) va.R[gi + v * NN] = -(double)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
       } else if (!FF) {
         // FP64: inc = a0 (Q_base - Q_k) + w_in + bdt R;  Q_out = Q_k + inc
         const double(*sN)[4 * NN] = (const double(*)[4 * NN])(smem + C::O_NHI);
         const double(*sW)[4 * NN] = (const double(*)[4 * NN])(smem + C::O_AUX);
-        double *qo = (double *)out.hi;
+        double *qo = (double *)va.out.hi;
         double qn[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const double R = -(double)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
           const double qk = (double)sQ[l2][(v) * NN + sp];
-          double inc = (double)rk.bdt * R;
-          if (use_base) inc += (double)rk.a0 * (sN[l2][(v) * NN + sp] - qk);
+          double inc = (double)va.rk.bdt * R;
+          if (use_base) inc += (double)va.rk.a0 * (sN[l2][(v) * NN + sp] - qk);
           if (AUX) inc += sW[l2][(v) * NN + sp];
           qn[v] = qk + inc;
-          if (w_out) w_out[gi + v * NN] = (T)((double)rk.ddt * R - (double)rk.g * inc);
+          if (va.w_out) va.w_out[gi + v * NN] = (T)((double)va.rk.ddt * R - (double)va.rk.g * inc);
         }
         const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
         bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
@@ -1540,16 +1689,16 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
         const float(*sNH)[4 * NN] = (const float(*)[4 * NN])(smem + C::O_NHI);
         const float(*sNL)[4 * NN] = (const float(*)[4 * NN])(smem + C::O_NLO);
         const float(*sW)[4 * NN] = (const float(*)[4 * NN])(smem + C::O_AUX);
-        float *oh = (float *)out.hi, *ol = (float *)out.lo;
+        float *oh = (float *)va.out.hi, *ol = (float *)va.out.lo;
         float hv[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const float R = -(float)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
           const float h = (float)sQ[l2][(v) * NN + sp];
-          float inc = (float)rk.bdt * R;
+          float inc = (float)va.rk.bdt * R;
           if constexpr (DF) {
             const float l = sKL[l2][(v) * NN + sp];
-            if (use_base) inc = fmaf((float)rk.a0, (sNH[l2][(v) * NN + sp] - h) + (sNL[l2][(v) * NN + sp] - l), inc);
+            if (use_base) inc = fmaf((float)va.rk.a0, (sNH[l2][(v) * NN + sp] - h) + (sNL[l2][(v) * NN + sp] - l), inc);
             if (AUX) inc += sW[l2][(v) * NN + sp];
             float sum, err;
             two_sum(h, inc, sum, err);
@@ -1560,13 +1709,13 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
             hv[v] = H;
           } else {
             // single-float state: the stage result is rounded to float once
-            if (use_base) inc = fmaf((float)rk.a0, sNH[l2][(v) * NN + sp] - h, inc);
+            if (use_base) inc = fmaf((float)va.rk.a0, sNH[l2][(v) * NN + sp] - h, inc);
             if (AUX) inc += sW[l2][(v) * NN + sp];
             const float H = h + inc;
             oh[gi + v * NN] = H;
             hv[v] = H;
           }
-          if (w_out) w_out[gi + v * NN] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
+          if (va.w_out) va.w_out[gi + v * NN] = (T)fmaf(-(float)va.rk.g, inc, (float)va.rk.ddt * R);
         }
         const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) * __frcp_rn(hv[0]));
         bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
@@ -1614,10 +1763,18 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO>::THREADS, VolCfg<T,
         }
       }
     }
-    // every read of this tile's buffers is done before they are refilled
-    __syncthreads();
+    // every read of this tile's buffers is done before they are refilled (a
+    // batch raises the non-physical flag on the tile's own case here)
+    if constexpr (Src::kMulti) {
+      if (__syncthreads_or(bad) && threadIdx.x == 0 && MODE == MODE_RK) atomicOr(&md.clk->flags, 1);
+      bad = false;
+    } else {
+      __syncthreads();
+    }
   }
-  if (MODE == MODE_RK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&md.clk->flags, 1);
+  if constexpr (!Src::kMulti) {
+    if (MODE == MODE_RK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&src.mesh(0).clk->flags, 1);
+  }
 }
 
 }  // namespace ssd
@@ -1663,6 +1820,12 @@ static __global__ void k_advance(DevClock *clk, double dt) {
   clk->t_n = clk->t_n + dt;
 }
 
+}  // namespace ssd
+
+#include "ssd_batch.cuh"
+
+namespace ssd {
+
 // ---------------------------------------------------------------------------
 // engine
 // ---------------------------------------------------------------------------
@@ -1672,6 +1835,35 @@ template <typename T, int N, bool LO = true>
 struct EngineImpl : Engine {
   static constexpr bool OTF = std::is_same<T, float>::value;
   static constexpr bool DF = OTF && LO;
+  using One = OneCase<VolArgs<T>>;
+  using List = CaseList<VolArgs<T>>;
+
+  template <int MODE, class Src>
+  static cudaError_t visc_setup(int *occ) {
+    using V = VisVolCfg<T, N>;
+    auto *k = k_volume_visc<T, N, MODE, OTF, LO, Src>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, V::SMEM);
+    if (err) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, V::THREADS, V::SMEM);
+  }
+  template <class Src>
+  static cudaError_t grad_setup(int *occ) {
+    using G = GradCfg<T, N>;
+    auto *k = k_grad_trace<T, N, OTF, Src>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (err) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, G::THREADS, G::SMEM);
+  }
+
+  // shared-memory attribute and resident CTAs per SM of one volume-kernel variant
+  template <int MODE, bool AUX, int EPBX, class Src>
+  static cudaError_t vol_setup(int *occ) {
+    using C = VolCfg<T, N, OTF, AUX, LO, EPBX>;
+    auto *k = k_volume<T, N, MODE, OTF, AUX, LO, EPBX, Src>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (err) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, C::THREADS, C::SMEM);
+  }
   double *dXs = nullptr, *dXf = nullptr;
   int *scratch_i = nullptr;
   double *scratch_d = nullptr;
@@ -1776,8 +1968,8 @@ struct EngineImpl : Engine {
     if ((err = cudaMemcpyAsync(dXf, hb.Xf, sizeof(double) * (N + 1), cudaMemcpyHostToDevice, s))) return err;
     const int nb = md.nL + md.nR;
     if ((err = cudaMalloc(&scratch_i, sizeof(int) * (2 * nb + 1)))) return err;
-    if ((err = cudaMalloc(&scratch_d, sizeof(double) * (md.nL + nb + 1)))) return err;
-    merge_smem = (int)(sizeof(double) * (md.nbmax > 0 ? md.nbmax : 1));  // one interface's angles
+    if ((err = cudaMalloc(&scratch_d, sizeof(double) * (2 * nb + 1)))) return err;
+    merge_smem = (int)(2 * sizeof(double) * (md.nbmax > 0 ? md.nbmax : 1));  // one interface's angles
     if (merge_smem > 48 * 1024) {
       if ((err = cudaFuncSetAttribute(k_clock_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, merge_smem)))
         return err;
@@ -1792,52 +1984,20 @@ struct EngineImpl : Engine {
       if ((err = cudaGetDevice(&dev))) return err;
       if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return err;
       int occ2 = 0;
-      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RESIDUAL, OTF, false, LO>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, VolCfg<T, N, OTF, false, LO>::SMEM)))
-        return err;
-      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF, false, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      VolCfg<T, N, OTF, false, LO>::SMEM)))
-        return err;
-      if ((err = cudaFuncSetAttribute(k_volume<T, N, MODE_RK, OTF, true, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      VolCfg<T, N, OTF, true, LO>::SMEM)))
-        return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_volume<T, N, MODE_RESIDUAL, OTF, false, LO>,
-                                                               C::THREADS, VolCfg<T, N, OTF, false, LO>::SMEM)))
-        return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_volume<T, N, MODE_RK, OTF, false, LO>, C::THREADS,
-                                                               VolCfg<T, N, OTF, false, LO>::SMEM)))
-        return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_volume<T, N, MODE_RK, OTF, true, LO>, C::THREADS,
-                                                               VolCfg<T, N, OTF, true, LO>::SMEM)))
-        return err;
+      if ((err = vol_setup<MODE_RESIDUAL, false, 0, One>(&occ0))) return err;
+      if ((err = vol_setup<MODE_RK, false, 0, One>(&occ1))) return err;
+      if ((err = vol_setup<MODE_RK, true, 0, One>(&occ2))) return err;
       grid_res = std::max(1, occ0) * sms;
       occ_rk = std::max(1, occ1);
       grid_rk = occ_rk * sms;
       grid_aux = std::max(1, occ2) * sms;
       // the persistent viscous volume kernel likewise
-      using V = VisVolCfg<T, N>;
-      int ov0 = 0, ov1 = 0;
-      if ((err = cudaFuncSetAttribute(k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, V::SMEM)))
-        return err;
-      if ((err = cudaFuncSetAttribute(k_volume_visc<T, N, MODE_RK, OTF, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      V::SMEM)))
-        return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ov0, k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO>,
-                                                               V::THREADS, V::SMEM)))
-        return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ov1, k_volume_visc<T, N, MODE_RK, OTF, LO>, V::THREADS,
-                                                               V::SMEM)))
-        return err;
+      int ov0 = 0, ov1 = 0, og = 0;
+      if ((err = visc_setup<MODE_RESIDUAL, One>(&ov0))) return err;
+      if ((err = visc_setup<MODE_RK, One>(&ov1))) return err;
       grid_visc_res = std::max(1, ov0) * sms;
       grid_visc_rk = std::max(1, ov1) * sms;
-      int og = 0;
-      if ((err = cudaFuncSetAttribute(k_grad_trace<T, N, OTF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      GradCfg<T, N>::SMEM)))
-        return err;
-      if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&og, k_grad_trace<T, N, OTF>, GradCfg<T, N>::THREADS,
-                                                               GradCfg<T, N>::SMEM)))
-        return err;
+      if ((err = grad_setup<One>(&og))) return err;
       grid_grad = std::max(1, og) * sms;
     }
     {
@@ -1908,8 +2068,10 @@ struct EngineImpl : Engine {
     }
     using Gc = GradCfg<T, N>;
     const int ntg = (md.E + Gc::EPB - 1) / Gc::EPB;
-    launch_pdl(k_grad_trace<T, N, OTF>, std::min(ntg, grid_grad), Gc::THREADS, Gc::SMEM, s, md, (const T *)q.hi,
-               ntg);
+    One src;
+    src.md = md;
+    src.a = vol_args(q, StatePtr{nullptr, nullptr}, StatePtr{nullptr, nullptr}, nullptr, RkArgs());
+    launch_pdl(k_grad_trace<T, N, OTF, One>, std::min(ntg, grid_grad), Gc::THREADS, Gc::SMEM, s, src, ntg);
     if (fused(md)) fused_pass<MORTAR_RUSANOV_FV>(md, s);
     else if (np > 0) launch_pdl(k_faces_visc<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
   }
@@ -1923,14 +2085,29 @@ struct EngineImpl : Engine {
   }
   void set_fusion(bool on) override { fuse_faces_mortar = on; }
 
+  static VolArgs<T> vol_args(StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk) {
+    VolArgs<T> a;
+    a.in = in;
+    a.base = base;
+    a.out = out;
+    a.R = R;
+    a.rk = RkCoef<T>{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
+    a.has_base = rk.has_base;
+    a.w_out = (T *)rk.w_out;
+    a.w_in = (const T *)rk.w_in;
+    return a;
+  }
+
   template <int MODE, bool AUX>
   void launch_volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk,
                      int grid, cudaStream_t s) {
     using C = VolCfg<T, N, OTF, AUX, LO>;
     const int ntiles = (md.E + C::EPB - 1) / C::EPB;
-    const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
-    launch_pdl(k_volume<T, N, MODE, OTF, AUX, LO>, std::min(ntiles, grid), C::THREADS, C::SMEM, s, md, in, base,
-               out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
+    One src;
+    src.md = md;
+    src.a = vol_args(in, base, out, R, rk);
+    launch_pdl(k_volume<T, N, MODE, OTF, AUX, LO, 0, One>, std::min(ntiles, grid), C::THREADS, C::SMEM, s, src,
+               ntiles);
   }
 
   void volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk, int mode,
@@ -1938,13 +2115,15 @@ struct EngineImpl : Engine {
     if (md.viscous) {
       using V = VisVolCfg<T, N>;
       const int ntiles = (md.E + V::EPB - 1) / V::EPB;
-      const RkCoef<T> c{(T)rk.a0, (T)rk.bdt, (T)rk.g, (T)rk.ddt};
+      One src;
+      src.md = md;
+      src.a = vol_args(in, base, out, R, rk);
       if (mode == MODE_RESIDUAL)
-        launch_pdl(k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO>, std::min(ntiles, grid_visc_res), V::THREADS,
-                   V::SMEM, s, md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
+        launch_pdl(k_volume_visc<T, N, MODE_RESIDUAL, OTF, LO, One>, std::min(ntiles, grid_visc_res), V::THREADS,
+                   V::SMEM, s, src, ntiles);
       else
-        launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO>, std::min(ntiles, grid_visc_rk), V::THREADS, V::SMEM, s,
-                   md, in, base, out, R, c, rk.has_base, (T *)rk.w_out, (const T *)rk.w_in, ntiles);
+        launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO, One>, std::min(ntiles, grid_visc_rk), V::THREADS, V::SMEM,
+                   s, src, ntiles);
       return;
     }
     if (mode == MODE_RESIDUAL) launch_volume<MODE_RESIDUAL, false>(md, in, base, out, R, rk, grid_res, s);
@@ -1986,6 +2165,222 @@ struct EngineImpl : Engine {
 
   void sp_coords(const MeshDev &md, double t, double *xy, cudaStream_t s) override {
     k_spxy<N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, t, xy);
+  }
+
+  // ---- batched form ----
+  // elements per volume tile the batch autotuner chooses from: the default
+  // tile and a smaller one (more, shorter work items)
+  static constexpr int kEpbAlt = vol_epb_default<N>() >= 12 ? 8 : (vol_epb_default<N>() >= 8 ? 4 : 0);
+  static constexpr int kFaceBlocks[3] = {128, 256, 512};
+
+  struct BatchImpl : BatchClass {
+    int n = 0, nstages = 0, viscous = 0;
+    std::vector<int> E, nF, nB, nM, nL, nR;  // per case
+    std::vector<char> aux;                   // per stage: the stage carries an increment in (w_in)
+    MeshDev *md = nullptr;                   // [nstages][n] stage views
+    VolArgs<T> *va = nullptr;                // [nstages][n]
+    int *off_tile = nullptr, *off_gtile = nullptr, *off_fblk = nullptr, *nmb = nullptr, *off_gpt = nullptr;
+    int ntile = 0, ngtile = 0, nfblk = 0, ngpt = 0;
+    int epb_alt = 0;       // 0: default tile, 1: the smaller tile
+    int face_block = 256;  // face-pass block size
+    int vol_ctas = 0;      // volume (or viscous volume) CTAs per SM
+    int occ[2] = {1, 1};   // resident volume CTAs per SM for the default / smaller tile
+    int occ_visc = 1, occ_grad = 1;
+    std::vector<void *> allocs;
+    ~BatchImpl() override {
+      for (void *p : allocs) cudaFree(p);
+    }
+  };
+
+  int batch_tile_choices(int *out) const override {
+    out[0] = vol_epb_default<N>();
+    if (kEpbAlt) out[1] = kEpbAlt;
+    return kEpbAlt ? 2 : 1;
+  }
+
+  cudaError_t batch_offsets(BatchImpl &b, cudaStream_t s) {
+    const int epb = b.epb_alt ? kEpbAlt : vol_epb_default<N>();
+    const int vepb = b.viscous ? VisVolCfg<T, N>::EPB : epb;
+    constexpr int MPB = MortCfg<N>::MPB;
+    std::vector<int> ot(b.n + 1, 0), og(b.n + 1, 0), of(b.n + 1, 0), nm(b.n, 0), op(b.n + 1, 0);
+    for (int c = 0; c < b.n; ++c) {
+      ot[c + 1] = ot[c] + (b.E[c] + vepb - 1) / vepb;
+      og[c + 1] = og[c] + (b.E[c] + GradCfg<T, N>::EPB - 1) / GradCfg<T, N>::EPB;
+      nm[c] = (b.nM[c] + MPB - 1) / MPB;
+      of[c + 1] = of[c] + nm[c] + ((b.nF[c] + b.nB[c]) * N + b.face_block - 1) / b.face_block;
+      op[c + 1] = op[c] + (b.nL[c] + b.nR[c]) * N;
+    }
+    b.ntile = ot[b.n];
+    b.ngtile = og[b.n];
+    b.nfblk = of[b.n];
+    b.ngpt = op[b.n];
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b.off_tile, ot.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(b.off_gtile, og.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(b.off_fblk, of.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(b.nmb, nm.data(), sizeof(int) * b.n, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(b.off_gpt, op.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice, s))) return e;
+    return cudaStreamSynchronize(s);  // the host vectors go out of scope
+  }
+
+  cudaError_t batch_args(BatchImpl &b, const std::vector<std::vector<BatchStageHost>> &stages, cudaStream_t s) {
+    std::vector<MeshDev> mh((size_t)b.nstages * b.n);
+    std::vector<VolArgs<T>> ah((size_t)b.nstages * b.n);
+    for (int k = 0; k < b.nstages; ++k)
+      for (int c = 0; c < b.n; ++c) {
+        const BatchStageHost &h = stages[k][c];
+        mh[(size_t)k * b.n + c] = h.md;
+        ah[(size_t)k * b.n + c] = vol_args(h.in, h.base, h.out, nullptr, h.rk);
+      }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b.md, mh.data(), sizeof(MeshDev) * mh.size(), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(b.va, ah.data(), sizeof(VolArgs<T>) * ah.size(), cudaMemcpyHostToDevice, s))) return e;
+    return cudaStreamSynchronize(s);
+  }
+
+  BatchClass *batch_class(const std::vector<std::vector<BatchStageHost>> &stages, int viscous,
+                          cudaStream_t s) override {
+    BatchImpl *b = new BatchImpl();
+    b->nstages = (int)stages.size();
+    b->n = b->nstages ? (int)stages[0].size() : 0;
+    b->viscous = viscous;
+    for (int c = 0; c < b->n; ++c) {
+      const MeshDev &m = stages[0][c].md;
+      b->E.push_back(m.E);
+      b->nF.push_back(m.nF);
+      b->nB.push_back(m.nB);
+      b->nM.push_back(m.nM);
+      b->nL.push_back(m.nL);
+      b->nR.push_back(m.nR);
+    }
+    for (int k = 0; k < b->nstages; ++k) b->aux.push_back(stages[k][0].rk.w_in != nullptr);
+    auto al = [&](void **p, size_t bytes) {
+      cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+      if (!e) b->allocs.push_back(*p);
+      return e;
+    };
+    const size_t nk = (size_t)b->nstages * b->n;
+    cudaError_t e = cudaSuccess;
+    if (!e) e = al((void **)&b->md, sizeof(MeshDev) * nk);
+    if (!e) e = al((void **)&b->va, sizeof(VolArgs<T>) * nk);
+    if (!e) e = al((void **)&b->off_tile, sizeof(int) * (b->n + 1));
+    if (!e) e = al((void **)&b->off_gtile, sizeof(int) * (b->n + 1));
+    if (!e) e = al((void **)&b->off_fblk, sizeof(int) * (b->n + 1));
+    if (!e) e = al((void **)&b->nmb, sizeof(int) * (b->n + 1));
+    if (!e) e = al((void **)&b->off_gpt, sizeof(int) * (b->n + 1));
+    if (!e) e = batch_args(*b, stages, s);
+    // resident CTAs per SM of the class's persistent kernels
+    if (!e) e = vol_setup<MODE_RK, false, 0, List>(&b->occ[0]);
+    if (!e) e = vol_setup<MODE_RK, true, 0, List>(&b->occ[0]);
+    if (kEpbAlt) {
+      if (!e) e = vol_setup<MODE_RK, false, kEpbAlt, List>(&b->occ[1]);
+      if (!e) e = vol_setup<MODE_RK, true, kEpbAlt, List>(&b->occ[1]);
+    }
+    if (!e) e = visc_setup<MODE_RK, List>(&b->occ_visc);
+    if (!e) e = grad_setup<List>(&b->occ_grad);
+    if (!e) {
+      b->vol_ctas = b->viscous ? b->occ_visc : b->occ[0];
+      e = batch_offsets(*b, s);
+    }
+    if (e) {
+      delete b;
+      return nullptr;
+    }
+    return b;
+  }
+
+  cudaError_t batch_update(BatchClass *bc, const std::vector<std::vector<BatchStageHost>> &stages,
+                           cudaStream_t s) override {
+    return batch_args(*static_cast<BatchImpl *>(bc), stages, s);
+  }
+
+  void batch_tuning(BatchClass *bc, int *vol_ctas_per_sm, int *tile_elems, int *fblock) override {
+    BatchImpl &b = *static_cast<BatchImpl *>(bc);
+    bool re = false;
+    if (tile_elems && *tile_elems > 0 && !b.viscous) {
+      const int alt = (kEpbAlt && *tile_elems == kEpbAlt) ? 1 : 0;
+      re |= alt != b.epb_alt;
+      b.epb_alt = alt;
+    }
+    const int occ = b.viscous ? b.occ_visc : b.occ[b.epb_alt];
+    if (vol_ctas_per_sm && *vol_ctas_per_sm > 0) b.vol_ctas = std::min(*vol_ctas_per_sm, std::max(1, occ));
+    b.vol_ctas = std::min(b.vol_ctas, std::max(1, occ));
+    if (fblock && *fblock > 0) {
+      const int fb = *fblock <= 128 ? 128 : (*fblock <= 256 ? 256 : 512);
+      re |= fb != b.face_block;
+      b.face_block = fb;
+    }
+    if (re) batch_offsets(b, 0);
+    if (vol_ctas_per_sm) *vol_ctas_per_sm = b.vol_ctas;
+    if (tile_elems) *tile_elems = b.viscous ? VisVolCfg<T, N>::EPB : (b.epb_alt ? kEpbAlt : vol_epb_default<N>());
+    if (fblock) *fblock = b.face_block;
+  }
+
+  void batch_free(BatchClass *bc) override { delete static_cast<BatchImpl *>(bc); }
+
+  template <int MMODE>
+  void batch_face_pass(const BatchImpl &b, const BatchWork &w, cudaStream_t s) {
+    if (b.nfblk == 0) return;
+    if (b.face_block == 128) launch_pdl(k_batch_faces<T, N, OTF, MMODE, 128>, b.nfblk, 128, 0, s, w);
+    else if (b.face_block == 256) launch_pdl(k_batch_faces<T, N, OTF, MMODE, 256>, b.nfblk, 256, 0, s, w);
+    else launch_pdl(k_batch_faces<T, N, OTF, MMODE, 512>, b.nfblk, 512, 0, s, w);
+  }
+
+  template <int GMODE>
+  void batch_gather(const BatchImpl &b, const BatchWork &w, cudaStream_t s) {
+    if (b.ngpt > 0) launch_pdl(k_batch_gather<T, N, GMODE>, (b.ngpt + 127) / 128, 128, 0, s, w, b.ngpt);
+  }
+
+  template <bool AUX, int EPBX>
+  void batch_volume(const BatchImpl &b, const List &src, cudaStream_t s) {
+    using C = VolCfg<T, N, OTF, AUX, LO, EPBX>;
+    launch_pdl(k_volume<T, N, MODE_RK, OTF, AUX, LO, EPBX, List>, std::min(b.ntile, b.vol_ctas * sms), C::THREADS,
+               C::SMEM, s, src, b.ntile);
+  }
+
+  void batch_stage(BatchClass *bc, int k, cudaStream_t s) override {
+    const BatchImpl &b = *static_cast<const BatchImpl *>(bc);
+    BatchWork w{b.md + (size_t)k * b.n, b.off_fblk, b.nmb, b.off_gpt, b.n};
+    List src;
+    src.md = b.md + (size_t)k * b.n;
+    src.a = b.va + (size_t)k * b.n;
+    src.n = b.n;
+    if (!b.viscous) {
+      batch_face_pass<MORTAR_RUSANOV>(b, w, s);
+      batch_gather<GATHER_FLUX>(b, w, s);
+      src.off = b.off_tile;
+      const bool aux = b.aux[k];
+      if (!b.epb_alt) {
+        if (aux) batch_volume<true, 0>(b, src, s);
+        else batch_volume<false, 0>(b, src, s);
+      } else if (kEpbAlt) {
+        if (aux) batch_volume<true, kEpbAlt>(b, src, s);
+        else batch_volume<false, kEpbAlt>(b, src, s);
+      }
+      return;
+    }
+    // common solution, gradients and their traces, common fluxes, volume
+    batch_face_pass<MORTAR_AVG_Q>(b, w, s);
+    batch_gather<GATHER_Q>(b, w, s);
+    using G = GradCfg<T, N>;
+    src.off = b.off_gtile;
+    launch_pdl(k_grad_trace<T, N, OTF, List>, std::min(b.ngtile, b.occ_grad * sms), G::THREADS, G::SMEM, s, src,
+               b.ngtile);
+    batch_face_pass<MORTAR_RUSANOV_FV>(b, w, s);
+    batch_gather<GATHER_FLUX>(b, w, s);
+    using V = VisVolCfg<T, N>;
+    src.off = b.off_tile;
+    launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO, List>, std::min(b.ntile, b.vol_ctas * sms), V::THREADS,
+               V::SMEM, s, src, b.ntile);
+  }
+
+  void batch_merge(const BatchMergeDev &bm, cudaStream_t s) override {
+    if (bm.smem > 48 * 1024) cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, bm.smem);
+    launch_pdl(k_batch_merge, dim3(bm.max_iface, bm.nstages, bm.ncase), 1024, bm.smem, s, bm);
+  }
+
+  void batch_advance(const BatchMergeDev &bm, cudaStream_t s) override {
+    launch_pdl(k_batch_advance, (bm.ncase + 127) / 128, 128, 0, s, bm);
   }
 };
 

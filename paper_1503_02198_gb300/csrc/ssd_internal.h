@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 namespace ssd {
 
 constexpr int kMaxN = 8;
@@ -20,11 +22,15 @@ static_assert(kMaxZones <= kZoneMask, "zone bits");
 // leave FP64: theta_z = omega_z * t_stage, Sec. 2.2).  Per zone z: the
 // rotation R(theta_z) as (c, s) and the angular velocity om; zone 0 holds
 // (1, 0, 0).  c, s, om follow each other so that c points at the zone table
-// [3][kZT] a kernel reads (likewise cf, sf, omf on the FP32 path).
+// [3][kZT] a kernel reads (likewise cf, sf, omf on the FP32 path).  The
+// reduced angle is a double-double theta2 + theta2_lo: the exact product
+// omega_z t_stage reduced modulo 2 pi with a double-double 2 pi, so that
+// mortar offsets (differences of angles near pi) keep full relative accuracy.
 struct DevClock {
   double t_n;           // time at the start of the step
   double t_stage;       // time of the stage being evaluated
-  double theta2[kZT];   // theta_z reduced to [0, 2 pi)
+  double theta2[kZT];   // theta_z reduced to [0, 2 pi): high part
+  double theta2_lo[kZT];  // and low part
   double c[kZT], s[kZT], om[kZT];
   float cf[kZT], sf[kZT], omf[kZT];
   int flags;  // bit 0: non-physical state; bit 1: mesh geometry error; bit 2: a bounded device wait gave up
@@ -65,8 +71,9 @@ struct MeshDev {
   const int4 *bfaces;
   const double *bxy;
   // sliding interfaces, both sides of each sorted counter-clockwise at t = 0
-  // about its zone's centre: (ef, reversed, 0, 0), CCW start angle, angular
-  // width, |S| = r * width.  The lists of all interfaces are concatenated:
+  // about its zone's centre: (ef, reversed, 0, 0), CCW start angle (a
+  // double-double La + La_lo, Ra + Ra_lo, formed on the host in long double),
+  // angular width, |S| = r * width.  The lists of all interfaces are concatenated:
   // interface i (of zone i + 1) owns L faces [zoff[i], zoff[i + 1]), R faces
   // [zoff[kZT + i], zoff[kZT + i + 1]) and mortars [zoff[i] + zoff[kZT + i], ...)
   int nL, nR, nM;
@@ -76,10 +83,11 @@ struct MeshDev {
   const int *ifz;           // [nL + nR] interface of each L, then R, face
   const int4 *Lface, *Rface;
   const double *La, *Lw, *LS, *Ra, *Rw, *RS;
+  const double *La_lo, *Ra_lo;
   const double *LiW, *RiW;  // 1 / angular width
   // per-stage mortar table (written by the merge kernel)
   int *mLf, *mRf;       // [nM] containing L / R face (sorted index)
-  double *mgeo;         // [nM][2]: start angle, angular length
+  double *mgeo;         // [nM][4]: start angle (double-double: high, low), angular length, unused
   int *Lstart, *Lcount; // [nL] first mortar (merged position) and count
   int *Rstart, *Rcount; // [nR]
   void *contrib;        // T [2][nM][4][N] back-projected mortar fluxes
@@ -148,6 +156,32 @@ struct RkArgs {
   void *w_out = nullptr;       // compute-precision [E][4][N][N] or null
 };
 
+// One case's part in a stage of the batched form (host side): its stage view
+// of the mesh, the states the stage reads and writes, and the stage's
+// Runge-Kutta arguments.
+struct BatchStageHost {
+  MeshDev md;
+  StatePtr in, base, out;
+  RkArgs rk;
+};
+
+// The merge and advance launches of a batch: for every case its base view,
+// its stage views, stage records and step size (device arrays); the merge has
+// a block per (interface, stage, case).
+struct BatchMergeDev {
+  int ncase, nstages, max_iface;
+  const MeshDev *md;        // [ncase] base view (its clock holds the step's start time)
+  const MeshDev *md_stage;  // [nstages][ncase] stage views (stage clock, mortar table)
+  const StageMerge *sm;     // [ncase]
+  const double *dt;         // [ncase]
+  int smem;                 // dynamic shared memory: the largest interface's angles
+};
+
+// engine-owned device tables and launch shapes of one class
+struct BatchClass {
+  virtual ~BatchClass() {}
+};
+
 // Per-precision engine: T = double (FP64 path) or float (FP32 path).
 struct Engine {
   virtual ~Engine() {}
@@ -175,7 +209,7 @@ struct Engine {
   // periodic and wall faces; mortar fluxes gathered onto the interface faces
   virtual void clock_merge(const MeshDev &md, double c, double dt, cudaStream_t s) = 0;
   // the same merge with caller-provided work arrays (ints: 2 (nL + nR) + 1,
-  // doubles: nL + (nL + nR) + 1)
+  // doubles: 2 (nL + nR) + 1)
   virtual void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                                 cudaStream_t s) = 0;
   // the clocks and mortar tables of all stages of a step in one launch (the
@@ -202,6 +236,34 @@ struct Engine {
   virtual void *W() const = 0;
   virtual void advance(const MeshDev &md, double dt, cudaStream_t s) = 0;
   virtual void sp_coords(const MeshDev &md, double t, double *xy, cudaStream_t s) = 0;
+
+  // ---- batched form: one launch per phase for every case of a class ----
+  // A class is a set of cases that share this engine's compute type and N
+  // and one viscous flag.  Its device tables hold, per stage, each case's
+  // stage view (clock and mortar table of that stage), its volume arguments
+  // and prefix sums of each kind of work item, so that the kernels walk the
+  // items of all cases of the class as one work list.
+  // stages[k][c]: case c's view and Runge-Kutta arguments of stage k
+  virtual BatchClass *batch_class(const std::vector<std::vector<BatchStageHost>> &stages, int viscous,
+                                  cudaStream_t s) = 0;
+  // new Runge-Kutta arguments (a dt changed); the kernels read them at launch
+  virtual cudaError_t batch_update(BatchClass *bc, const std::vector<std::vector<BatchStageHost>> &stages,
+                                   cudaStream_t s) = 0;
+  // the kernels of stage k of every case of the class: face pass with the
+  // mortar flux, gather (and the viscous chain), volume kernel with the
+  // Runge-Kutta combination and traces
+  virtual void batch_stage(BatchClass *bc, int k, cudaStream_t s) = 0;
+  // launch shapes: volume CTAs per SM (0: keep) and elements per volume tile
+  // (0: keep; one of the values batch_tile_choices lists) and face-pass
+  // block size (0: keep); returns the values in force
+  virtual void batch_tuning(BatchClass *bc, int *vol_ctas_per_sm, int *tile_elems, int *face_block) = 0;
+  virtual int batch_tile_choices(int *out) const = 0;
+  virtual void batch_free(BatchClass *bc) = 0;
+  // the clocks and mortar tables of every stage of every case of a batch in
+  // one launch, and the closing t_n += dt of every case (N-independent; any
+  // engine launches them)
+  virtual void batch_merge(const BatchMergeDev &bm, cudaStream_t s) = 0;
+  virtual void batch_advance(const BatchMergeDev &bm, cudaStream_t s) = 0;
 };
 
 Engine *make_engine_f64(int N);

@@ -184,9 +184,8 @@ struct GradCfg {
 // (component v = dQ_v/dx, 4 + v = dQ_v/dy).  Persistent: each CTA walks
 // tiles; thread 0 issues the next tile's state and common solution (two 1-D
 // bulk copies) into the other stage while the CTA computes the current one.
-template <typename T, int N, bool OTF>
-__global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(MeshDev md, const T *__restrict__ Q,
-                                                                       int ntiles) {
+template <typename T, int N, bool OTF, class Src>
+__global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(Src src, int nitems) {
   pdl_enter();
   using C = GradCfg<T, N>;
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
@@ -194,17 +193,22 @@ __global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(MeshDev m
   uint64_t *bar = (uint64_t *)(smem + C::O_BAR);
   T(*sDx)[4][NN] = (T(*)[4][NN])(smem + C::O_DX);
   T(*sDe)[4][NN] = (T(*)[4][NN])(smem + C::O_DE);
-  // the cell records (on-the-fly path) and flags come along; the flags are
+  // the state of the stage (the item's case's input state), the common
+  // solution, the cell records (on-the-fly path) and flags; the flags are
   // copied in whole groups of 4 (16 bytes), within the tile-padded array
-  auto issue = [&](int tl, int st) {
+  auto issue = [&](int item, int st) {
+    int cn, tl;
+    src.item(item, cn, tl);
+    const MeshDev &mn = src.mesh(cn);
+    const T *Q = (const T *)src.args(cn).in.hi;
     unsigned char *sb = smem + st * C::STAGE;
     const size_t e0 = (size_t)tl * EPB;
-    const uint32_t ne = (uint32_t)min(EPB, md.E - (int)e0), nf = (ne + 3u) & ~3u;
+    const uint32_t ne = (uint32_t)min(EPB, mn.E - (int)e0), nf = (ne + 3u) & ~3u;
     mbar_expect_tx(&bar[st], ne * (C::QE + C::CE + (OTF ? C::GEE : 0)) + nf * 4u);
     bulk_g2s(sb + C::O_Q, Q + e0 * 4 * NN, ne * C::QE, &bar[st]);
-    bulk_g2s(sb + C::O_C, (const T *)md.CQ + e0 * 16 * N, ne * C::CE, &bar[st]);
-    if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, ne * C::GEE, &bar[st]);
-    bulk_g2s(sb + C::O_EF, md.eflag + e0, nf * 4u, &bar[st]);
+    bulk_g2s(sb + C::O_C, (const T *)mn.CQ + e0 * 16 * N, ne * C::CE, &bar[st]);
+    if (OTF) bulk_g2s(sb + C::O_EG, (const T *)mn.egeo + e0 * 8, ne * C::GEE, &bar[st]);
+    bulk_g2s(sb + C::O_EF, mn.eflag + e0, nf * 4u, &bar[st]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -212,25 +216,28 @@ __global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(MeshDev m
     fence_mbar_init();
   }
   __syncthreads();
-  int tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
-  const T *zt = zone_tab<T>(md.clk);
+  int item = blockIdx.x;
+  if (threadIdx.x == 0 && item < nitems) issue(item, 0);
   const VolBasis<T, N> &B = cVB<T, N>;
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
   const int d = r / N, m = r - d * N;
   int it = 0;
-  for (; tile < ntiles; tile += gridDim.x, ++it) {
+  for (; item < nitems; item += gridDim.x, ++it) {
     const int st = it & 1;
-    const int next = tile + gridDim.x;
-    if (threadIdx.x == 0 && next < ntiles) {
+    const int next = item + gridDim.x;
+    int cs, tile;
+    src.item(item, cs, tile);
+    const MeshDev &md = src.mesh(cs);
+    const T *zt = zone_tab<T>(md.clk);
+    if (threadIdx.x == 0 && next < nitems) {
       fence_proxy_async_smem();
       issue(next, st ^ 1);
     }
     if (!cta_wait(&bar[st], (uint32_t)((it >> 1) & 1))) {
       if (threadIdx.x == 0) {
         atomicOr(&md.clk->flags, 4);
-        if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        if (next < nitems) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
       }
       return;
     }
@@ -391,10 +398,9 @@ struct VisVolCfg {
 // Persistent: each CTA walks tiles of EPB elements; thread 0 issues the next
 // tile's three bulk copies into the other stage while the CTA computes the
 // current one.  Every wait is bounded (device flag bit 2 on timeout).
-template <typename T, int N, int MODE, bool OTF, bool LO>
+template <typename T, int N, int MODE, bool OTF, bool LO, class Src>
 __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MINB)
-    k_volume_visc(MeshDev md, StatePtr in, StatePtr base, StatePtr out, double *Rout, RkCoef<T> rk, int has_base,
-                  T *w_out, const T *w_in, int ntiles) {
+    k_volume_visc(Src src, int nitems) {
   pdl_enter();
   using C = VisVolCfg<T, N>;
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
@@ -408,16 +414,19 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
   // stage, and the common fluxes of tile tl into stage st
   // with the cell records (on-the-fly path) and flags, the flags in whole
   // groups of 4 (16 bytes), within the tile-padded array
-  auto issue = [&](int tl, int st) {
+  auto issue = [&](int item, int st) {
+    int cn, tl;
+    src.item(item, cn, tl);
+    const MeshDev &mn = src.mesh(cn);
     unsigned char *sb = smem + st * C::STAGE;
     const size_t e0 = (size_t)tl * EPB;
-    const uint32_t ne = (uint32_t)min(EPB, md.E - (int)e0), nf = (ne + 3u) & ~3u;
+    const uint32_t ne = (uint32_t)min(EPB, mn.E - (int)e0), nf = (ne + 3u) & ~3u;
     mbar_expect_tx(&bar[st], ne * (C::QE + C::GE + C::CE + (OTF ? C::GEE : 0)) + nf * 4u);
-    bulk_g2s(sb + C::O_Q, (const T *)in.hi + e0 * 4 * NN, ne * C::QE, &bar[st]);
-    bulk_g2s(sb + C::O_G, (const T *)md.GSP + e0 * 8 * NN, ne * C::GE, &bar[st]);
-    bulk_g2s(sb + C::O_C, (const T *)md.CF + e0 * 16 * N, ne * C::CE, &bar[st]);
-    if (OTF) bulk_g2s(sb + C::O_EG, (const T *)md.egeo + e0 * 8, ne * C::GEE, &bar[st]);
-    bulk_g2s(sb + C::O_EF, md.eflag + e0, nf * 4u, &bar[st]);
+    bulk_g2s(sb + C::O_Q, (const T *)src.args(cn).in.hi + e0 * 4 * NN, ne * C::QE, &bar[st]);
+    bulk_g2s(sb + C::O_G, (const T *)mn.GSP + e0 * 8 * NN, ne * C::GE, &bar[st]);
+    bulk_g2s(sb + C::O_C, (const T *)mn.CF + e0 * 16 * N, ne * C::CE, &bar[st]);
+    if (OTF) bulk_g2s(sb + C::O_EG, (const T *)mn.egeo + e0 * 8, ne * C::GEE, &bar[st]);
+    bulk_g2s(sb + C::O_EF, mn.eflag + e0, nf * 4u, &bar[st]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -425,19 +434,29 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     fence_mbar_init();
   }
   __syncthreads();
-  int tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
-  const T *zt = zone_tab<T>(md.clk);
-  const T gm1 = pick<T>(md.gm1, md.gm1_f);
+  int item = blockIdx.x;
+  if (threadIdx.x == 0 && item < nitems) issue(item, 0);
   const int le = threadIdx.x / (2 * N);
   const int r = threadIdx.x - le * 2 * N;
   const int d = r / N, m = r - d * N;
   bool bad = false;
   int it = 0;
-  for (; tile < ntiles; tile += gridDim.x, ++it) {
+  for (; item < nitems; item += gridDim.x, ++it) {
     const int st = it & 1;
-    const int next = tile + gridDim.x;
-    if (threadIdx.x == 0 && next < ntiles) {
+    const int next = item + gridDim.x;
+    int cs, tile;
+    src.item(item, cs, tile);
+    const MeshDev &md = src.mesh(cs);
+    const VolArgs<T> &va = src.args(cs);
+    const StatePtr in = va.in, base = va.base, out = va.out;
+    const RkCoef<T> rk = va.rk;
+    const int has_base = va.has_base;
+    T *const w_out = va.w_out;
+    const T *const w_in = va.w_in;
+    double *const Rout = va.R;
+    const T *zt = zone_tab<T>(md.clk);
+    const T gm1 = pick<T>(md.gm1, md.gm1_f);
+    if (threadIdx.x == 0 && next < nitems) {
       // the other stage was last read before the previous iteration's closing
       // barrier; order those generic reads before the async writes
       fence_proxy_async_smem();
@@ -447,7 +466,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
       if (threadIdx.x == 0) {
         atomicOr(&md.clk->flags, 4);
         // let the copy in flight land before the CTA exits
-        if (next < ntiles) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        if (next < nitems) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
       }
       return;
     }
@@ -664,10 +683,18 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
         }
       }
     }
-    // every read of this tile's stage is done before it is refilled
-    __syncthreads();
+    // every read of this tile's stage is done before it is refilled (a batch
+    // raises the non-physical flag on the tile's own case here)
+    if constexpr (Src::kMulti) {
+      if (__syncthreads_or(bad) && threadIdx.x == 0 && MODE == MODE_RK) atomicOr(&md.clk->flags, 1);
+      bad = false;
+    } else {
+      __syncthreads();
+    }
   }
-  if (MODE == MODE_RK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&md.clk->flags, 1);
+  if constexpr (!Src::kMulti) {
+    if (MODE == MODE_RK && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&src.mesh(0).clk->flags, 1);
+  }
 }
 
 }  // namespace ssd

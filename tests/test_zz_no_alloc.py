@@ -8,7 +8,7 @@ import pytest
 
 from helpers import small_rotor
 from ssd_inputs import fields, meshes
-from ssd_inputs.workloads import FlowParams
+from ssd_inputs.workloads import FlowParams, build_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ def ssd():
     return pkg
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_noalloc_matches_residual_on_consecutive_calls(ssd, precision):
     import torch
     m = small_rotor(shift_R=0.05)
@@ -64,3 +64,24 @@ def test_noalloc_rejects_work_beyond_its_fixed_size(ssd):
     s.sd_residual_noalloc(dev)
     ref = s.sd_residual()
     _close(dev.cpu().numpy(), ref, TOL64)
+
+
+def test_noalloc_viscous_matches_oracle(ssd, oracle_mod):
+    # the viscous chain (common solution, gradient traces, viscous mortar
+    # procedure) runs through the same fixed work memory: the Taylor-Couette
+    # annulus, two consecutive calls, against the oracle
+    w = build_workload("couette_n3")
+    o = oracle_mod.Oracle(w.mesh, w.N, w.params)
+    s = ssd.Solver(w.mesh, w.N - 1, w.params, precision=0)
+    for seed, t in ((3, 0.2), (4, 1.7)):
+        Q = o.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=seed, amp=0.05, u0=0.1, v0=0.05))
+        s.sd_set_state(Q)
+        s.sd_set_time(t)
+        _close(s.sd_residual_noalloc(), o.residual(Q, t), TOL64)
+
+
+def test_noalloc_checks_the_output_buffer(ssd):
+    import torch
+    s = ssd.Solver(small_rotor(), 2, FlowParams(omega=0.5), precision=0)
+    with pytest.raises(ValueError):
+        s.sd_residual_noalloc(torch.empty(s.n_dofs - 1, dtype=torch.float64, device="cuda"))
