@@ -39,7 +39,7 @@ enum {
   SD_ERR_UNSUPPORTED = -6  /* valid request this build does not support (e.g. p) */
 };
 
-enum { SD_PREC_FP64 = 0, SD_PREC_FP32 = 1, SD_PREC_FP32S = 2 };
+enum { SD_PREC_FP64 = 0, SD_PREC_FP32 = 1, SD_PREC_FP32S = 2, SD_PREC_FP32_TF32 = 3 };
 
 /* Boundary tags of sd_mesh.bfaces.  Each acts through a ghost state in the
  * Rusanov flux; the state on the boundary is the common solution of the
@@ -146,7 +146,13 @@ typedef struct {
                        (a double-float pair per value); or SD_PREC_FP32S: as SD_PREC_FP32
                        with the state stored as one float per value, each Runge-Kutta
                        stage result rounded to float (half the state bytes; the state
-                       carries float round-off, about 6e-8 relative per stage) */
+                       carries float round-off, about 6e-8 relative per stage); or
+                       SD_PREC_FP32_TF32: as SD_PREC_FP32 with the inviscid volume
+                       kernel's interpolation (Eq. Qt) and divergence (Eqs. Ft, Gt)
+                       contractions on the tensor cores, each product as three TF32
+                       matrix multiplies of a big/small split of both operands
+                       (3xTF32, near-FP32 accuracy); Navier-Stokes meshes keep the
+                       FMA-pipe kernels; not available in the batched form */
   void *stream;     /* cudaStream_t to queue work on; NULL = a non-blocking stream the handle creates */
   int rk_stages;    /* time integrator: 0 or 3 = three-stage SSP-RK3 (Shu-Osher); 5 = the
                        five-stage fourth-order SSP-RK of Sec. 4 (Spiteri-Ruuth coefficients) */
@@ -207,19 +213,36 @@ int sd_step(sd_handle *h, double dt, int nsteps);
  * rho <= 0, p <= 0 or a non-finite value since the last sd_sync. */
 int sd_sync(sd_handle *h);
 
+/* Test aid for the bounded device waits, off by default (on = 0).  With
+ * on = 1 the volume kernel of later residuals and steps arms the copy
+ * barrier of its first work item with 16 bytes more than that item's copies
+ * deliver and gives that one wait a short poll limit: the wait gives up, the
+ * kernel raises its timeout flag, lets the copies it has issued land and
+ * returns, and sd_sync (or sd_residual_noalloc) reports SD_ERR_TIMEOUT; the
+ * result of that call is incomplete.  Every issued copy still lands; nothing
+ * faults or hangs.  on = 0 restores normal operation.  Synchronises. */
+int sd_test_wait_timeout(sd_handle *h, int on);
+
 /* Physical coordinates of the solution points at time t, [E][N][N][2]. */
 int sd_sp_coords(sd_handle *h, double t, double *xy, int on_device);
 
 /* ---- batched form: many independent cases, one CUDA-graph launch per step ----
  * Each case has its own mesh, polynomial degree and parameters (its own
- * rotation rate).  sd_batch_step advances every case by nsteps steps with one
- * graph launch per step; the graph holds one branch per case, so the small
- * kernels of different cases run concurrently.  With tune_dt > 0 the batch
- * autotunes each case's launch shapes (persistent volume CTAs per SM, face
- * kernel block size) at creation by timing a few steps of size tune_dt from
- * a uniform state; the state and time are reset to zero afterwards. */
+ * rotation rate and step size); all cases share the precision and the
+ * Runge-Kutta scheme.  The cases are grouped into classes of equal N and
+ * viscous flag; every phase of a stage (face pass with the mortar flux,
+ * gather, gradients, volume kernel) is one launch per class whose work list
+ * spans all cases of the class (per-case prefix sums of faces, mortars and
+ * element tiles; the persistent volume kernels walk (case, tile) items), and
+ * the stage clocks and mortar tables of every case come from one merge
+ * launch per step.  sd_batch_step runs one CUDA-graph launch per step.  With
+ * tune_dt > 0 an autotuner chooses, per class, the elements per volume tile,
+ * the face-pass block size and the volume CTAs per SM by timing a few batch
+ * steps of size tune_dt from a uniform state; states and times are reset to
+ * zero afterwards. */
 typedef struct sd_batch sd_batch;
 
+/* SD_ERR_ARG if the cases differ in precision or Runge-Kutta scheme. */
 int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_params *prm, double tune_dt,
                     sd_batch **out);
 int sd_batch_destroy(sd_batch *b);
@@ -238,6 +261,12 @@ int sd_batch_step(sd_batch *b, const double *dt, int nsteps);
 /* Wait for the batch; returns the first case error (SD_ERR_NONPHYSICAL ...). */
 int sd_batch_sync(sd_batch *b);
 const char *sd_batch_last_error(const sd_batch *b);
+
+/* Classes of the batch and, for class i, info[0..5] = N, viscous flag,
+ * number of cases, elements per volume tile, volume CTAs per SM and face-pass
+ * block size in force (the autotuner's choice). */
+int sd_batch_classes(const sd_batch *b);
+int sd_batch_class_info(sd_batch *b, int i, int *info);
 
 /* Measurement aid (the paper reports wall time split into interface and
  * total time, Tables 3-10): runs reps steps outside the CUDA graph with CUDA

@@ -16,7 +16,9 @@ import numpy as np
 from . import build as _build_mod
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libssd.so")
+# SSD_LIBRARY=debug selects the debug build (index checks in the kernels)
+_DEBUG = os.environ.get("SSD_LIBRARY", "") == "debug"
+LIB_PATH = os.path.join(_HERE, "_build", "libssd_debug.so" if _DEBUG else "libssd.so")
 
 SD_OK = 0
 SD_ERR_ARG = -1
@@ -28,6 +30,7 @@ SD_ERR_UNSUPPORTED = -6
 SD_PREC_FP64 = 0
 SD_PREC_FP32 = 1
 SD_PREC_FP32S = 2
+SD_PREC_FP32_TF32 = 3
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -70,7 +73,7 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    return _build_mod.build(force=force)
+    return _build_mod.build(force=force, debug=_DEBUG)
 
 
 def lib():
@@ -99,6 +102,7 @@ def lib():
         L.sd_profile_step.argtypes = [vp, ctypes.c_double, ctypes.c_int, _c_dbl_p]
         L.sd_fma_peak.argtypes = [vp, ctypes.c_int, _c_dbl_p]
         L.sd_residual_noalloc.argtypes = [vp, vp, ctypes.c_int]
+        L.sd_test_wait_timeout.argtypes = [vp, ctypes.c_int]
         L.sd_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.POINTER(sd_mesh)), _c_int_p,
                                       ctypes.POINTER(sd_params), ctypes.c_double, ctypes.POINTER(vp)]
         L.sd_batch_destroy.argtypes = [vp]
@@ -109,6 +113,8 @@ def lib():
         L.sd_batch_sync.argtypes = [vp]
         L.sd_batch_last_error.argtypes = [vp]
         L.sd_batch_last_error.restype = ctypes.c_char_p
+        L.sd_batch_classes.argtypes = [vp]
+        L.sd_batch_class_info.argtypes = [vp, ctypes.c_int, _c_int_p]
         _lib = L
     return _lib
 
@@ -279,6 +285,9 @@ class Solver:
     def sd_sync(self):
         self._check(lib().sd_sync(self._h))
 
+    def sd_test_wait_timeout(self, on):
+        self._check(lib().sd_test_wait_timeout(self._h, int(on)))
+
     def sd_sp_coords(self, t=0.0, out=None):
         if out is None:
             out = np.empty((self.E, self.N, self.N, 2))
@@ -341,3 +350,14 @@ class Batch:
 
     def sd_batch_sync(self):
         self._check(lib().sd_batch_sync(self._b))
+
+    def class_info(self):
+        """Per class of cases (equal N and viscous flag): its size and the
+        launch shapes in force (the autotuner's choice)."""
+        out = []
+        for i in range(lib().sd_batch_classes(self._b)):
+            info = (ctypes.c_int * 6)()
+            self._check(lib().sd_batch_class_info(self._b, i, info))
+            out.append({"N": info[0], "viscous": info[1], "cases": info[2], "tile_elems": info[3],
+                        "vol_ctas_per_sm": info[4], "face_block": info[5]})
+        return out

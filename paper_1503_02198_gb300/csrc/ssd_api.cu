@@ -529,9 +529,8 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   cudaError_t e;
   double *bxy;
   DevClock *clk;
-  // every per-element array holds a whole number of volume-kernel tiles
-  const int tile = h->eng->tile_elems();
-  const size_t Ep = (E + tile - 1) / tile * tile;
+  // every per-element array holds a whole number of tiles of every size
+  const size_t Ep = (E + kElemPad - 1) / kElemPad * kElemPad;
   // metric tables: every cell on the FP64 path, arc cells only on the on-the-fly path
   std::vector<int> eflag(Ep, 0), tab_elem;
   const bool otf = h->eng->metrics_on_the_fly();
@@ -713,11 +712,22 @@ void queue_stage(sd_handle *h, int k, StatePtr q, StatePtr base, StatePtr out, c
   h->eng->volume(m, q, base, out, nullptr, rk, MODE_RK, h->stream);
 }
 
-void queue_step(sd_handle *h, double dt) {
-  MeshDev &md = h->md;
+// The stages of one time step of size dt: per stage the state it reads, the
+// base state, the state it writes, its Runge-Kutta arguments and its view of
+// the mesh (its own clock and mortar table); c[k] = stage time fraction.
+// Returns the number of stages.  Every stage is  out = in + a0 (base - in) +
+// w_in + bdt L(in)  (RkArgs), the Shu-Osher form rewritten around the stage
+// input (the weights of a Shu-Osher stage sum to one).
+int step_plan(sd_handle *h, double dt, BatchStageHost *plan, double *c) {
   Engine *g = h->eng;
-  cudaStream_t s = h->stream;
   const StatePtr A = g->A(), B = g->B(), none{nullptr, nullptr};
+  auto set = [&](int k, StatePtr in, StatePtr base, StatePtr out, const RkArgs &rk) {
+    plan[k].md = stage_view(h, k);
+    plan[k].in = in;
+    plan[k].base = base;
+    plan[k].out = out;
+    plan[k].rk = rk;
+  };
   if (h->prm.rk_stages != 5) {
     // SSP-RK3: Q1 = Qn + dt L(Qn); Q2 = 3/4 Qn + 1/4 (Q1 + dt L(Q1));
     // Qn+1 = 1/3 Qn + 2/3 (Q2 + dt L(Q2)); stage times 0, 1, 1/2
@@ -725,38 +735,42 @@ void queue_step(sd_handle *h, double dt) {
     r1.bdt = dt;
     r2.has_base = 1, r2.a0 = 0.75, r2.bdt = 0.25 * dt;
     r3.has_base = 1, r3.a0 = 1.0 / 3.0, r3.bdt = 2.0 / 3.0 * dt;
-    StageMerge &sm = h->sm;
-    sm.n = 3;
-    sm.c[0] = 0.0, sm.c[1] = 1.0, sm.c[2] = 0.5;
-    g->merge_stages(md, sm, dt, s);
-    queue_stage(h, 0, A, none, B, r1);
-    queue_stage(h, 1, B, A, B, r2);
-    queue_stage(h, 2, B, A, A, r3);
-  } else {
-    // u -> A, u1 -> B, u2 -> C, u3 -> B, u4 -> A (u is not needed after the
-    // fourth stage), u+ -> A; W carries a53 (u3 - u4) + c53 dt L(u3)
-    const StatePtr Cs = g->C();
-    void *W = g->W();
-    double c[5];
-    rk54_times(c);
-    RkArgs r1, r2, r3, r4, r5;
-    r1.bdt = Rk54::c10 * dt;
-    r2.has_base = 1, r2.a0 = Rk54::a20, r2.bdt = Rk54::c21 * dt;
-    r3.has_base = 1, r3.a0 = Rk54::a30, r3.bdt = Rk54::c32 * dt;
-    r4.has_base = 1, r4.a0 = Rk54::a40, r4.bdt = Rk54::c43 * dt, r4.g = Rk54::a53, r4.ddt = Rk54::c53 * dt;
-    r4.w_out = W;
-    r5.has_base = 1, r5.a0 = Rk54::a52, r5.bdt = Rk54::c54 * dt, r5.w_in = W;
-    StageMerge &sm = h->sm;
-    sm.n = 5;
-    for (int k = 0; k < 5; ++k) sm.c[k] = c[k];
-    g->merge_stages(md, sm, dt, s);
-    queue_stage(h, 0, A, none, B, r1);
-    queue_stage(h, 1, B, A, Cs, r2);
-    queue_stage(h, 2, Cs, A, B, r3);
-    queue_stage(h, 3, B, A, A, r4);
-    queue_stage(h, 4, A, Cs, A, r5);
+    c[0] = 0.0, c[1] = 1.0, c[2] = 0.5;
+    set(0, A, none, B, r1);
+    set(1, B, A, B, r2);
+    set(2, B, A, A, r3);
+    return 3;
   }
-  g->advance(md, dt, s);
+  // u -> A, u1 -> B, u2 -> C, u3 -> B, u4 -> A (u is not needed after the
+  // fourth stage), u+ -> A; W carries a53 (u3 - u4) + c53 dt L(u3)
+  const StatePtr Cs = g->C();
+  void *W = g->W();
+  rk54_times(c);
+  RkArgs r1, r2, r3, r4, r5;
+  r1.bdt = Rk54::c10 * dt;
+  r2.has_base = 1, r2.a0 = Rk54::a20, r2.bdt = Rk54::c21 * dt;
+  r3.has_base = 1, r3.a0 = Rk54::a30, r3.bdt = Rk54::c32 * dt;
+  r4.has_base = 1, r4.a0 = Rk54::a40, r4.bdt = Rk54::c43 * dt, r4.g = Rk54::a53, r4.ddt = Rk54::c53 * dt;
+  r4.w_out = W;
+  r5.has_base = 1, r5.a0 = Rk54::a52, r5.bdt = Rk54::c54 * dt, r5.w_in = W;
+  set(0, A, none, B, r1);
+  set(1, B, A, Cs, r2);
+  set(2, Cs, A, B, r3);
+  set(3, B, A, A, r4);
+  set(4, A, Cs, A, r5);
+  return 5;
+}
+
+void queue_step(sd_handle *h, double dt) {
+  BatchStageHost plan[kMaxStages];
+  double c[kMaxStages];
+  const int n = step_plan(h, dt, plan, c);
+  StageMerge &sm = h->sm;
+  sm.n = n;
+  for (int k = 0; k < n; ++k) sm.c[k] = c[k];
+  h->eng->merge_stages(h->md, sm, dt, h->stream);
+  for (int k = 0; k < n; ++k) queue_stage(h, k, plan[k].in, plan[k].base, plan[k].out, plan[k].rk);
+  h->eng->advance(h->md, dt, h->stream);
 }
 
 }  // namespace
@@ -791,7 +805,8 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
     g_create_error = "rk_stages must be 0 or 3 (SSP-RK3) or 5 (SSP-RK(5,4))";
     return SD_ERR_ARG;
   }
-  if (prm->precision != SD_PREC_FP64 && prm->precision != SD_PREC_FP32 && prm->precision != SD_PREC_FP32S) {
+  if (prm->precision != SD_PREC_FP64 && prm->precision != SD_PREC_FP32 && prm->precision != SD_PREC_FP32S &&
+      prm->precision != SD_PREC_FP32_TF32) {
     g_create_error = "unknown precision";
     return SD_ERR_ARG;
   }
@@ -817,9 +832,11 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
   if (!rc) rc = build_mesh(h, m, prm->omega);
   if (!rc) {
     h->eng = prm->precision == SD_PREC_FP64   ? make_engine_f64(N)
-             : prm->precision == SD_PREC_FP32 ? make_engine_f32(N)
+             : prm->precision == SD_PREC_FP32 || prm->precision == SD_PREC_FP32_TF32 ? make_engine_f32(N)
                                               : make_engine_f32s(N);
     if (!h->eng) rc = fail(h, SD_ERR_UNSUPPORTED, "no engine for this N");
+    else if (prm->precision == SD_PREC_FP32_TF32 && !h->eng->set_tensor_cores(true))
+      rc = fail(h, SD_ERR_UNSUPPORTED, "no tensor-core contractions in this engine");
   }
   if (!rc && (ce = cudaMallocHost(&h->h_pinned, 64))) rc = cuda_fail(h, ce, "pinned buffer");
   if (!rc) {
@@ -1033,7 +1050,21 @@ int sd_sync(sd_handle *h) {
   int rc = read_flags(h, &flags, true);
   if (rc) return rc;
   if (flags & 4) return fail(h, SD_ERR_TIMEOUT, "a bounded device wait gave up (tile copy did not arrive)");
+  if (flags & 8) return fail(h, SD_ERR_MESH, "a mesh, mortar or batch work-list index was out of range");
   if (flags & 1) return fail(h, SD_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite)");
+  return SD_OK;
+}
+
+int sd_test_wait_timeout(sd_handle *h, int on) {
+  if (!h) return SD_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e) return cuda_fail(h, e, "sd_test_wait_timeout");
+  h->md.test_tx_extra = on ? 16 : 0;
+  h->md.test_poll = on ? 4096 : 0;
+  if (h->step_exec) {  // the captured step holds the mesh view by value
+    cudaGraphExecDestroy(h->step_exec);
+    h->step_exec = nullptr;
+  }
   return SD_OK;
 }
 
@@ -1149,15 +1180,29 @@ int sd_fma_peak(sd_handle *h, int precision, double *tflops) {
 }
 
 // ---------------------------------------------------------------------------
-// batched form: independent cases advanced by one graph launch per step
+// batched form: independent cases, one launch per phase for all cases of a
+// class, the whole step one CUDA graph
 // ---------------------------------------------------------------------------
 
 struct sd_batch {
-  std::vector<sd_handle *> cases;
-  std::vector<double> dt;      // dt of the captured graph, per case
+  std::vector<sd_handle *> cases;  // the caller's order
+  // classes: cases sharing N and the viscous flag, each with the engine that
+  // launches its kernels and that engine's tables of the class
+  struct Cls {
+    Engine *eng = nullptr;
+    BatchClass *bc = nullptr;
+    std::vector<int> members;  // case indices, in class order
+    int N = 0, viscous = 0;
+  };
+  std::vector<Cls> classes;
+  std::vector<int> order;      // internal (class-major) position -> case index
+  int nstages = 0;
+  std::vector<double> dt;      // step of each case the device tables hold (caller's order)
+  BatchMergeDev bm{};
+  std::vector<void *> allocs;  // merge tables
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<cudaEvent_t> ev; // fork / join events (one per case + origin)
+  std::vector<cudaEvent_t> ev;  // case -> batch ordering events (one per case + origin)
   std::string err;
 };
 
@@ -1167,65 +1212,136 @@ void free_batch(sd_batch *b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto &c : b->classes)
+    if (c.bc) c.eng->batch_free(c.bc);
+  for (void *p : b->allocs) cudaFree(p);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   for (sd_handle *h : b->cases) free_handle(h);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
 
-// Autotuner: for one case, time a few SSP-RK3 steps of each candidate launch
-// shape (volume CTAs per SM x face block size) from a uniform state and keep
-// the fastest.  The case's state and time are reset afterwards.
-int tune_case(sd_handle *h, double dt) {
-  int maxc = 1, cur = 0, fb = 0;
-  h->eng->tuning(&cur, &maxc, &fb);
-  const int fblocks[3] = {128, 256, 512};
-  cudaEvent_t a, z;
-  cudaEventCreate(&a);
-  cudaEventCreate(&z);
-  float best = 1e30f;
-  int best_c = cur, best_f = fb;
-  // uniform state: rho = 1, p = 1, at rest
-  const size_t n = (size_t)h->E * 4 * h->N * h->N, nn = (size_t)h->N * h->N;
-  std::vector<double> q(n, 0.0);
-  const double e0 = 1.0 / (h->prm.gamma - 1.0);
-  for (int e = 0; e < h->E; ++e)
-    for (size_t k = 0; k < nn; ++k) {
-      q[((size_t)e * 4 + 0) * nn + k] = 1.0;
-      q[((size_t)e * 4 + 3) * nn + k] = e0;
-    }
-  int rc = SD_OK;
-  for (int c = 1; c <= maxc && !rc; ++c)
-    for (int f = 0; f < 3 && !rc; ++f) {
-      int cc = c, ff = fblocks[f];
-      h->eng->tuning(&cc, nullptr, &ff);
-      if ((rc = sd_set_state(h, q.data(), 0))) break;
-      const StatePtr A = h->eng->A();
-      h->eng->trace(h->md, A, h->stream);
-      queue_step(h, dt);  // warm-up
-      cudaEventRecord(a, h->stream);
-      for (int k = 0; k < 3; ++k) queue_step(h, dt);
-      cudaEventRecord(z, h->stream);
-      cudaError_t e = cudaEventSynchronize(z);
-      if (e) rc = cuda_fail(h, e, "autotuner");
-      float ms = 0;
-      cudaEventElapsedTime(&ms, a, z);
-      if (!rc && ms < best) {
-        best = ms;
-        best_c = cc;
-        best_f = ff;
-      }
-    }
-  cudaEventDestroy(a);
-  cudaEventDestroy(z);
-  h->eng->tuning(&best_c, nullptr, &best_f);
-  if (!rc) {
-    std::fill(q.begin(), q.end(), 0.0);
-    rc = sd_set_state(h, q.data(), 0);
+// each class's per-stage view and Runge-Kutta arguments of its cases for the
+// steps dts (caller's order)
+std::vector<std::vector<BatchStageHost>> class_stages(sd_batch *b, const sd_batch::Cls &cl, const double *dts) {
+  std::vector<std::vector<BatchStageHost>> st(b->nstages, std::vector<BatchStageHost>(cl.members.size()));
+  for (size_t c = 0; c < cl.members.size(); ++c) {
+    sd_handle *h = b->cases[cl.members[c]];
+    BatchStageHost plan[kMaxStages];
+    double cc[kMaxStages];
+    step_plan(h, dts[cl.members[c]], plan, cc);
+    for (int k = 0; k < b->nstages; ++k) st[k][c] = plan[k];
   }
-  if (!rc) rc = sd_set_time(h, 0.0);
-  int flags = 0;
-  if (!rc) rc = read_flags(h, &flags, true);
+  return st;
+}
+
+// new steps: the classes' Runge-Kutta arguments and the merge's dt array
+cudaError_t batch_set_dt(sd_batch *b, const double *dts) {
+  cudaError_t e = cudaSuccess;
+  for (auto &cl : b->classes)
+    if (!e) e = cl.eng->batch_update(cl.bc, class_stages(b, cl, dts), b->stream);
+  std::vector<double> d(b->order.size());
+  for (size_t i = 0; i < b->order.size(); ++i) d[i] = dts[b->order[i]];
+  if (!e) e = cudaMemcpyAsync((void *)b->bm.dt, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice, b->stream);
+  if (!e) e = cudaStreamSynchronize(b->stream);
+  if (!e) b->dt.assign(dts, dts + b->cases.size());
+  return e;
+}
+
+// one step of every case: the merge of all stages of all cases, then per
+// stage each class's face pass, gather(s) and volume kernel, then t_n += dt
+void queue_batch_step(sd_batch *b) {
+  Engine *e0 = b->classes[0].eng;
+  e0->batch_merge(b->bm, b->stream);
+  for (int k = 0; k < b->nstages; ++k)
+    for (auto &cl : b->classes) cl.eng->batch_stage(cl.bc, k, b->stream);
+  e0->batch_advance(b->bm, b->stream);
+}
+
+// uniform state (rho = 1, p = 1, at rest) in every case, time 0
+int batch_reset(sd_batch *b, double fill) {
+  for (sd_handle *h : b->cases) {
+    const size_t n = (size_t)h->E * 4 * h->N * h->N, nn = (size_t)h->N * h->N;
+    std::vector<double> q(n, 0.0);
+    if (fill > 0.0) {
+      const double e0 = fill / (h->prm.gamma - 1.0);
+      for (int e = 0; e < h->E; ++e)
+        for (size_t k = 0; k < nn; ++k) {
+          q[((size_t)e * 4 + 0) * nn + k] = fill;
+          q[((size_t)e * 4 + 3) * nn + k] = e0;
+        }
+    }
+    int rc = sd_set_state(h, q.data(), 0);
+    if (!rc) rc = sd_set_time(h, 0.0);
+    if (rc) return rc;
+    h->eng->trace(h->md, h->eng->A(), h->stream);
+    h->traces_valid = true;
+    if (cudaStreamSynchronize(h->stream)) return SD_ERR_CUDA;
+  }
+  return SD_OK;
+}
+
+// Autotuner: for each class in turn, time a few batch steps (the other
+// classes at their current shapes) for every candidate launch shape -- the
+// elements per volume tile, the face-pass block size and the volume CTAs per
+// SM -- and keep the fastest; then reset every case to zero state and time.
+int batch_autotune(sd_batch *b) {
+  cudaEvent_t ta, tz;
+  cudaEventCreate(&ta);
+  cudaEventCreate(&tz);
+  int rc = batch_reset(b, 1.0);
+  for (auto &cl : b->classes) {
+    if (rc) break;
+    int tiles[2], ntl = cl.eng->batch_tile_choices(tiles);
+    if (cl.viscous) ntl = 1;
+    int occ = 1000, cur_t = 0, cur_f = 0;
+    cl.eng->batch_tuning(cl.bc, &occ, &cur_t, &cur_f, b->stream);  // occ: the most CTAs per SM of the current tile
+    float best = 1e30f;
+    int bt = cur_t, bf = cur_f, bc = occ;
+    const int fbs[3] = {128, 256, 512};
+    for (int ti = 0; ti < ntl && !rc; ++ti)
+      for (int fi = 0; fi < 3 && !rc; ++fi) {
+        int t = cl.viscous ? 0 : tiles[ti], f = fbs[fi], cmax = 1000;
+        cl.eng->batch_tuning(cl.bc, &cmax, &t, &f, b->stream);  // the largest CTA count this tile admits
+        const int cands[2] = {cmax, (cmax + 1) / 2};
+        for (int ci = 0; ci < (cmax > 1 ? 2 : 1) && !rc; ++ci) {
+          int cc = cands[ci];
+          cl.eng->batch_tuning(cl.bc, &cc, nullptr, nullptr, b->stream);
+          queue_batch_step(b);  // warm-up
+          cudaEventRecord(ta, b->stream);
+          for (int r = 0; r < 3; ++r) queue_batch_step(b);
+          cudaEventRecord(tz, b->stream);
+          cudaError_t ce = cudaGetLastError();
+          if (!ce) ce = cudaEventSynchronize(tz);
+          if (ce) {
+            b->err = std::string("batch autotuner (class N = ") + std::to_string(cl.N) + (cl.viscous ? ", NS" : ", Euler") +
+                     ", tile " + std::to_string(t) + ", face block " + std::to_string(f) + ", CTAs/SM " +
+                     std::to_string(cc) + "): " + cudaGetErrorString(ce);
+            rc = SD_ERR_CUDA;
+            break;
+          }
+          float ms = 0;
+          cudaEventElapsedTime(&ms, ta, tz);
+          if (ms < best) best = ms, bt = t, bf = f, bc = cc;
+        }
+      }
+    cl.eng->batch_tuning(cl.bc, &bc, &bt, &bf, b->stream);
+  }
+  cudaEventDestroy(ta);
+  cudaEventDestroy(tz);
+  if (!rc) rc = batch_reset(b, 0.0);
+  // a non-physical state while timing from the uniform start is possible and
+  // harmless (the flag is cleared); a wait that gave up or (debug build) an
+  // index out of range is an error
+  for (size_t i = 0; i < b->cases.size() && !rc; ++i) {
+    int flags = 0;
+    rc = read_flags(b->cases[i], &flags, true);
+    if (!rc && (flags & (4 | 8))) {
+      b->err = "batch autotuner, case " + std::to_string(i) +
+               ((flags & 8) ? ": a mesh or mortar table index was out of range" : ": a bounded device wait gave up");
+      rc = (flags & 8) ? SD_ERR_MESH : SD_ERR_TIMEOUT;
+    }
+  }
   return rc;
 }
 
@@ -1240,37 +1356,101 @@ int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_
     g_create_error = "bad batch arguments";
     return SD_ERR_ARG;
   }
-  sd_batch *b = new sd_batch();
-  cudaError_t ce = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-  if (ce) {
-    g_create_error = std::string("batch stream: ") + cudaGetErrorString(ce);
-    free_batch(b);
-    return SD_ERR_CUDA;
+  for (int i = 1; i < n; ++i)
+    if (prm[i].precision != prm[0].precision || (prm[i].rk_stages == 5) != (prm[0].rk_stages == 5)) {
+      g_create_error = "all cases of a batch need the same precision and Runge-Kutta scheme";
+      return SD_ERR_ARG;
+    }
+  if (prm[0].precision == SD_PREC_FP32_TF32) {
+    g_create_error = "the batched form runs the FP32 contractions on the FMA pipe (SD_PREC_FP32)";
+    return SD_ERR_UNSUPPORTED;
   }
+  sd_batch *b = new sd_batch();
+  auto fail_b = [&](int code, const std::string &msg) {
+    g_create_error = msg;
+    free_batch(b);
+    return code;
+  };
+  cudaError_t ce = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (ce) return fail_b(SD_ERR_CUDA, std::string("batch stream: ") + cudaGetErrorString(ce));
   for (int i = 0; i < n; ++i) {
     sd_params pi = prm[i];
-    pi.stream = nullptr;  // every case gets its own stream (a branch of the step graph)
+    pi.stream = nullptr;  // every case keeps its own stream for its own calls
     sd_handle *h = nullptr;
     int rc = sd_create(meshes[i], p[i], &pi, &h);
-    if (rc) {
-      g_create_error = "case " + std::to_string(i) + ": " + g_create_error;
-      free_batch(b);
-      return rc;
-    }
+    if (rc) return fail_b(rc, "case " + std::to_string(i) + ": " + g_create_error);
     b->cases.push_back(h);
-    if (tune_dt > 0.0 && (rc = tune_case(h, tune_dt))) {
-      g_create_error = "case " + std::to_string(i) + " autotuner: " + h->err;
-      free_batch(b);
-      return rc;
+  }
+  // classes: by N, then Euler before Navier-Stokes
+  for (int N = 3; N <= 6; ++N)
+    for (int visc = 0; visc <= 1; ++visc) {
+      sd_batch::Cls cl;
+      cl.N = N;
+      cl.viscous = visc;
+      for (int i = 0; i < n; ++i)
+        if (b->cases[i]->N == N && (b->cases[i]->prm.viscous != 0) == (visc != 0)) cl.members.push_back(i);
+      if (cl.members.empty()) continue;
+      cl.eng = b->cases[cl.members[0]]->eng;
+      for (int i : cl.members) b->order.push_back(i);
+      b->classes.push_back(cl);
     }
+  // the merge and advance tables of every case (class-major order)
+  {
+    BatchStageHost plan[kMaxStages];
+    double c[kMaxStages];
+    b->nstages = step_plan(b->cases[0], 1.0, plan, c);
+    std::vector<MeshDev> base(n), stage((size_t)b->nstages * n);
+    std::vector<StageMerge> sms(n);
+    int max_iface = 1, smem = 8;
+    for (int i = 0; i < n; ++i) {
+      sd_handle *h = b->cases[b->order[i]];
+      step_plan(h, 1.0, plan, c);
+      h->sm.n = b->nstages;
+      for (int k = 0; k < b->nstages; ++k) {
+        h->sm.c[k] = c[k];
+        stage[(size_t)k * n + i] = plan[k].md;
+      }
+      base[i] = h->md;
+      sms[i] = h->sm;
+      max_iface = std::max(max_iface, h->md.nI);
+      smem = std::max(smem, (int)(2 * sizeof(double) * std::max(1, h->md.nbmax)));
+    }
+    auto dup = [&](const void *src, size_t bytes, void **dst) {
+      cudaError_t e = cudaMalloc(dst, bytes);
+      if (e) return e;
+      b->allocs.push_back(*dst);
+      return src ? cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, b->stream) : cudaSuccess;
+    };
+    void *dmd = nullptr, *dst = nullptr, *dsm = nullptr, *ddt = nullptr;
+    if ((ce = dup(base.data(), sizeof(MeshDev) * n, &dmd)) ||
+        (ce = dup(stage.data(), sizeof(MeshDev) * stage.size(), &dst)) ||
+        (ce = dup(sms.data(), sizeof(StageMerge) * n, &dsm)) || (ce = dup(nullptr, sizeof(double) * n, &ddt)) ||
+        (ce = cudaStreamSynchronize(b->stream)))
+      return fail_b(SD_ERR_CUDA, std::string("batch tables: ") + cudaGetErrorString(ce));
+    b->bm.ncase = n;
+    b->bm.nstages = b->nstages;
+    b->bm.max_iface = max_iface;
+    b->bm.md = (const MeshDev *)dmd;
+    b->bm.md_stage = (const MeshDev *)dst;
+    b->bm.sm = (const StageMerge *)dsm;
+    b->bm.dt = (const double *)ddt;
+    b->bm.smem = smem;
+  }
+  const double dt0 = tune_dt > 0.0 ? tune_dt : 1.0;
+  std::vector<double> dts(n, dt0);
+  for (auto &cl : b->classes) {
+    cl.bc = cl.eng->batch_class(class_stages(b, cl, dts.data()), cl.viscous, b->stream);
+    if (!cl.bc) return fail_b(SD_ERR_CUDA, "batch class tables: " + std::string(cudaGetErrorString(cudaGetLastError())));
+  }
+  if ((ce = batch_set_dt(b, dts.data()))) return fail_b(SD_ERR_CUDA, std::string("batch dt: ") + cudaGetErrorString(ce));
+  if (tune_dt > 0.0) {
+    const int rc = batch_autotune(b);
+    if (rc) return fail_b(rc, b->err.empty() ? std::string("batch autotuner failed") : b->err);
   }
   b->ev.resize(n + 1);
   for (auto &e : b->ev)
-    if ((ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) {
-      g_create_error = std::string("batch events: ") + cudaGetErrorString(ce);
-      free_batch(b);
-      return SD_ERR_CUDA;
-    }
+    if ((ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming)))
+      return fail_b(SD_ERR_CUDA, std::string("batch events: ") + cudaGetErrorString(ce));
   *out = b;
   return SD_OK;
 }
@@ -1289,6 +1469,22 @@ sd_handle *sd_batch_case(sd_batch *b, int i) {
 
 const char *sd_batch_last_error(const sd_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
+int sd_batch_classes(const sd_batch *b) { return b ? (int)b->classes.size() : 0; }
+
+int sd_batch_class_info(sd_batch *b, int i, int *info) {
+  if (!b || !info || i < 0 || i >= (int)b->classes.size()) return SD_ERR_ARG;
+  sd_batch::Cls &cl = b->classes[i];
+  int ctas = 0, tile = 0, fb = 0;
+  cl.eng->batch_tuning(cl.bc, &ctas, &tile, &fb, b->stream);
+  info[0] = cl.N;
+  info[1] = cl.viscous;
+  info[2] = (int)cl.members.size();
+  info[3] = tile;
+  info[4] = ctas;
+  info[5] = fb;
+  return SD_OK;
+}
+
 int sd_batch_step(sd_batch *b, const double *dt, int nsteps) {
   if (!b || !dt || nsteps < 0) return SD_ERR_ARG;
   const int n = (int)b->cases.size();
@@ -1299,39 +1495,35 @@ int sd_batch_step(sd_batch *b, const double *dt, int nsteps) {
     }
   if (nsteps == 0) return SD_OK;
   cudaError_t e;
-  // every case's earlier work (state copies, traces) is ordered before the graph
+  // every case's earlier work (state copies) is ordered before the steps;
+  // the traces of a new state are formed on the batch stream
   for (int i = 0; i < n; ++i) {
     sd_handle *h = b->cases[i];
-    if (!h->traces_valid) {
-      h->eng->trace(h->md, h->eng->A(), h->stream);
-      h->traces_valid = true;
-    }
     if ((e = cudaEventRecord(b->ev[i], h->stream)) || (e = cudaStreamWaitEvent(b->stream, b->ev[i], 0))) {
       b->err = std::string("batch ordering: ") + cudaGetErrorString(e);
       return SD_ERR_CUDA;
     }
   }
-  bool same = b->exec && (int)b->dt.size() == n;
-  for (int i = 0; same && i < n; ++i) same = b->dt[i] == dt[i];
-  if (!same) {
-    if (b->exec) {
-      cudaGraphExecDestroy(b->exec);
-      b->exec = nullptr;
+  for (int i = 0; i < n; ++i) {
+    sd_handle *h = b->cases[i];
+    if (!h->traces_valid) {
+      h->eng->trace(h->md, h->eng->A(), b->stream);
+      h->traces_valid = true;
     }
-    // one graph per step: a branch per case, forked from and joined to the batch stream
+  }
+  bool same = (int)b->dt.size() == n;
+  for (int i = 0; same && i < n; ++i) same = b->dt[i] == dt[i];
+  if (!same && (e = batch_set_dt(b, dt))) {
+    b->err = std::string("batch dt: ") + cudaGetErrorString(e);
+    return SD_ERR_CUDA;
+  }
+  if (!b->exec) {
     cudaGraph_t g;
     if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal))) {
       b->err = std::string("batch capture: ") + cudaGetErrorString(e);
       return SD_ERR_CUDA;
     }
-    cudaEventRecord(b->ev[n], b->stream);
-    for (int i = 0; i < n; ++i) {
-      sd_handle *h = b->cases[i];
-      cudaStreamWaitEvent(h->stream, b->ev[n], 0);
-      queue_step(h, dt[i]);
-      cudaEventRecord(b->ev[i], h->stream);
-      cudaStreamWaitEvent(b->stream, b->ev[i], 0);
-    }
+    queue_batch_step(b);
     cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(b->stream, &g);
     if (le || e) {
@@ -1345,7 +1537,6 @@ int sd_batch_step(sd_batch *b, const double *dt, int nsteps) {
       b->err = std::string("batch instantiate: ") + cudaGetErrorString(e);
       return SD_ERR_CUDA;
     }
-    b->dt.assign(dt, dt + n);
   }
   for (int k = 0; k < nsteps; ++k)
     if ((e = cudaGraphLaunch(b->exec, b->stream))) {
@@ -1459,6 +1650,7 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   const int rc = read_flags(h, &flags, true);
   if (rc) return rc;
   if (flags & 4) return fail(h, SD_ERR_TIMEOUT, "a bounded device wait gave up (tile copy did not arrive)");
+  if (flags & 8) return fail(h, SD_ERR_MESH, "a mesh, mortar or batch work-list index was out of range");
   if (flags & 1) return fail(h, SD_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite)");
   return SD_OK;
 }

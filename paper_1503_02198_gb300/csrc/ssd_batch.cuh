@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(FB) k_batch_faces(BatchWork w) {
   const int lb = (int)blockIdx.x - __ldg(w.off_fblk + c);
   const MeshDev &md = w.md[c];
   const int nmb = __ldg(w.nmb + c);
+  if (!batch_check(md, lb >= 0 && nmb >= 0 && (lb < nmb || (lb - nmb) * FB < (md.nF + md.nB) * N))) return;
   if (lb < nmb) {
     mortar_flux_body<T, N, MMODE, MortCfg<N>::MPB>(md, lb);
     return;
@@ -69,7 +70,10 @@ __global__ void k_batch_gather(BatchWork w, int total) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   const int c = case_of(w.off_gpt, w.n, t);
-  gather_point<T, N, GMODE>(w.md[c], t - __ldg(w.off_gpt + c));
+  const MeshDev &md = w.md[c];
+  const int lt = t - __ldg(w.off_gpt + c);
+  if (!batch_check(md, lt >= 0 && lt < (md.nL + md.nR) * N)) return;
+  gather_point<T, N, GMODE>(md, lt);
 }
 
 // Stage clocks and mortar tables of every stage of every case of a batch:

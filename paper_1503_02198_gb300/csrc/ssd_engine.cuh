@@ -37,6 +37,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <type_traits>
 
 #include "ssd_internal.h"
@@ -68,6 +69,26 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Debug build (-DSSD_DEBUG): indices read from the mesh and mortar tables are
+// checked before use; a bad one raises device flag bit 3 (reported by sd_sync
+// as SD_ERR_MESH) and the access is skipped.  Kernels never trap.  In the
+// normal build the check is the constant true.
+#ifdef SSD_DEBUG
+__device__ __forceinline__ bool ssd_check(const MeshDev &md, bool ok) {
+  if (!ok) atomicOr(&md.clk->flags, 8);
+  return ok;
+}
+#else
+__device__ __forceinline__ bool ssd_check(const MeshDev &, bool) { return true; }
+#endif
+// The same check in every build, for the work lists of the batched form (a
+// work item, face block or gather point outside its case is reported and its
+// memory accesses skipped).
+__device__ __forceinline__ bool batch_check(const MeshDev &md, bool ok) {
+  if (!ok) atomicOr(&md.clk->flags, 8);
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -111,6 +132,23 @@ struct GeoLayout {
   static constexpr int grad = 6 * NF + N * N;                  // xi_x, xi_y, eta_x, eta_y at SPs [4][N*N]
   static constexpr int G = 6 * NF + 5 * N * N;
 };
+
+// a b + c d and a b - c d with one fixed rounding: the first product is fused
+// into an FMA, the second rounded first.  Left to the compiler, either product
+// of such a sum may be fused, and two kernels that inline the same expression
+// (a single case's kernel and a batch class's) may choose differently and
+// differ in the last bit; written out, every kernel computes the same bits.
+template <typename T>
+__device__ __forceinline__ T mul_add(T a, T b, T c, T d) {
+  return fma(a, b, c * d);
+}
+template <typename T>
+__device__ __forceinline__ T mul_sub(T a, T b, T c, T d) {
+  return fma(a, b, -(c * d));
+}
+// a product that is never fused into a later addition
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // a parameter in the compute type, taken from its float copy on the FP32
 // path so that no FP64 instruction runs there
@@ -368,18 +406,19 @@ struct ElemGeo {
     c = zt[z];
     s = zt[kZT + z];
     om = zt[2 * kZT + z];
-    const int ti = (f >> kZoneBits) - 1;
+    int ti = (f >> kZoneBits) - 1;
+    if (!ssd_check(md, ti < md.nTab && (OTF || ti >= 0))) ti = 0;
     if (OTF && ti < 0) {
       tab = nullptr;
       const T v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4], v5 = r[5], v6 = r[6], v7 = r[7];
-      x0 = c * v0 - s * v1;
-      y0 = s * v0 + c * v1;
-      e1x = c * v2 - s * v3;
-      e1y = s * v2 + c * v3;
-      e3x = c * v4 - s * v5;
-      e3y = s * v4 + c * v5;
-      dx = c * v6 - s * v7;
-      dy = s * v6 + c * v7;
+      x0 = mul_sub(c, v0, s, v1);
+      y0 = mul_add(s, v0, c, v1);
+      e1x = mul_sub(c, v2, s, v3);
+      e1y = mul_add(s, v2, c, v3);
+      e3x = mul_sub(c, v4, s, v5);
+      e3y = mul_add(s, v4, c, v5);
+      dx = mul_sub(c, v6, s, v7);
+      dy = mul_add(s, v6, c, v7);
     } else {
       tab = (const T *)md.geo + (size_t)ti * L::G;
     }
@@ -394,13 +433,13 @@ struct ElemGeo {
       g = T(0);
       if (om != T(0)) {
         const T px = x0 + xi * e1x + eta * xe, py = y0 + xi * e1y + eta * ye;
-        g = om * (px * vy - py * vx);
+        g = om * mul_sub(px, vy, py, vx);
       }
     } else {
       const int k = j * (N + 1) + i;
       const T ax = tab[L::ax + k], ay = tab[L::ay + k];
-      vx = c * ax - s * ay;
-      vy = s * ax + c * ay;
+      vx = mul_sub(c, ax, s, ay);
+      vy = mul_add(s, ax, c, ay);
       g = tab[L::gx + k];
     }
   }
@@ -414,13 +453,13 @@ struct ElemGeo {
       g = T(0);
       if (om != T(0)) {
         const T px = x0 + eta * e3x + xi * xx, py = y0 + eta * e3y + xi * yx;
-        g = om * (px * vy - py * vx);
+        g = om * mul_sub(px, vy, py, vx);
       }
     } else {
       const int k = l * N + i;
       const T bx = tab[L::bx + k], by = tab[L::by + k];
-      vx = c * bx - s * by;
-      vy = s * bx + c * by;
+      vx = mul_sub(c, bx, s, by);
+      vy = mul_add(s, bx, c, by);
       g = tab[L::gy + k];
     }
   }
@@ -443,7 +482,7 @@ struct ElemGeo {
         vx[i] = sg * ty;
         vy[i] = -sg * tx;
         const T px = x0 + u * Bx + w * tx, py = y0 + u * By + w * ty;
-        vg[i] = om * (px * vy[i] - py * vx[i]);
+        vg[i] = om * mul_sub(px, vy[i], py, vx[i]);
       }
     } else {
 #pragma unroll
@@ -465,7 +504,7 @@ struct ElemGeo {
     if (OTF && tab == nullptr) {
       const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
       const T xx = e1x + eta * dx, yx = e1y + eta * dy, xe = e3x + xi * dx, ye = e3y + xi * dy;
-      return recip(xx * ye - xe * yx);
+      return recip(mul_sub(xx, ye, xe, yx));
     }
     return tab[L::iJ + j * N + i];
   }
@@ -476,7 +515,7 @@ struct ElemGeo {
     if (OTF && ti < 0) {
       const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
       const T xx = r[2] + eta * r[6], yx = r[3] + eta * r[7], xe = r[4] + xi * r[6], ye = r[5] + xi * r[7];
-      return recip(xx * ye - xe * yx);
+      return recip(mul_sub(xx, ye, xe, yx));
     }
     return ((const T *)md.geo + (size_t)ti * L::G)[L::iJ + j * N + i];
   }
@@ -485,7 +524,7 @@ struct ElemGeo {
     if (OTF && tab == nullptr) {
       const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
       const T xx = e1x + eta * dx, yx = e1y + eta * dy, xe = e3x + xi * dx, ye = e3y + xi * dy;
-      const T iJ = T(1) / (xx * ye - xe * yx);
+      const T iJ = T(1) / mul_sub(xx, ye, xe, yx);
       xix = ye * iJ;
       xiy = -xe * iJ;
       etx = -yx * iJ;
@@ -494,10 +533,10 @@ struct ElemGeo {
       const int k = j * N + i;
       const T a = tab[L::grad + k], b = tab[L::grad + N * N + k];
       const T c2 = tab[L::grad + 2 * N * N + k], d2 = tab[L::grad + 3 * N * N + k];
-      xix = c * a - s * b;
-      xiy = s * a + c * b;
-      etx = c * c2 - s * d2;
-      ety = s * c2 + c * d2;
+      xix = mul_sub(c, a, s, b);
+      xiy = mul_add(s, a, c, b);
+      etx = mul_sub(c, c2, s, d2);
+      ety = mul_add(s, c2, c, d2);
     }
   }
 };
@@ -508,18 +547,18 @@ struct ElemGeo {
 
 template <typename T>
 __device__ __forceinline__ T pressure_of(const T *q, T gm1) {
-  return gm1 * (q[3] - T(0.5) * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+  return gm1 * (q[3] - T(0.5) * mul_add(q[1], q[1], q[2], q[2]) / q[0]);
 }
 
 // normal ALE inviscid flux through a (not necessarily unit) vector (nx, ny):
 // (F - u_g Q, G - v_g Q) . n  with vgn = V_g . n
 template <typename T>
 __device__ __forceinline__ void normal_flux(const T *q, T p, T nx, T ny, T vgn, T *f) {
-  const T un = (q[1] * nx + q[2] * ny) / q[0];
-  f[0] = q[0] * un - vgn * q[0];
-  f[1] = q[1] * un + p * nx - vgn * q[1];
-  f[2] = q[2] * un + p * ny - vgn * q[2];
-  f[3] = (q[3] + p) * un - vgn * q[3];
+  const T un = mul_add(q[1], nx, q[2], ny) / q[0];
+  f[0] = mul_sub(q[0], un, vgn, q[0]);
+  f[1] = fma(q[1], un, mul_sub(p, nx, vgn, q[1]));
+  f[2] = fma(q[2], un, mul_sub(p, ny, vgn, q[2]));
+  f[3] = mul_sub(q[3] + p, un, vgn, q[3]);
 }
 
 // Rusanov common flux (Sec. 3.1) for unit normal n from L to R
@@ -530,12 +569,12 @@ __device__ __forceinline__ void rusanov(const T *qL, const T *qR, T nx, T ny, T 
   T fL[4], fR[4];
   normal_flux(qL, pL, nx, ny, vgn, fL);
   normal_flux(qR, pR, nx, ny, vgn, fR);
-  const T unL = (qL[1] * nx + qL[2] * ny) / qL[0], unR = (qR[1] * nx + qR[2] * ny) / qR[0];
+  const T unL = mul_add(qL[1], nx, qL[2], ny) / qL[0], unR = mul_add(qR[1], nx, qR[2], ny) / qR[0];
   const T lL = fabs(unL - vgn) + sqrt(gamma * pL / qL[0]);
   const T lR = fabs(unR - vgn) + sqrt(gamma * pR / qR[0]);
   const T lam = lL > lR ? lL : lR;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) Fn[v] = T(0.5) * (fL[v] + fR[v]) - T(0.5) * lam * (qR[v] - qL[v]);
+  for (int v = 0; v < 4; ++v) Fn[v] = mul_sub(T(0.5), fL[v] + fR[v], T(0.5) * lam, qR[v] - qL[v]);
 }
 
 // ---------------------------------------------------------------------------
@@ -791,6 +830,7 @@ __device__ __forceinline__ void k_face_point(const MeshDev &md, int t) {
   const int fi = t / N, j = t - fi * N;
   const int4 fc = md.faces[fi];
   const int efA = fc.x, efB = fc.y, jB = fc.z ? N - 1 - j : j;
+  if (!ssd_check(md, efA >= 0 && efA < 4 * md.E && efB >= 0 && efB < 4 * md.E)) return;
   const T *TR = (const T *)md.TR;
   T qA[4], qB[4];
 #pragma unroll
@@ -805,7 +845,7 @@ __device__ __forceinline__ void k_face_point(const MeshDev &md, int t) {
   if (z) {
     const T *zt = zone_tab<T>(md.clk);
     const T c = zt[z], s = zt[kZT + z];
-    const T rx = c * nx - s * ny, ry = s * nx + c * ny;
+    const T rx = mul_sub(c, nx, s, ny), ry = mul_add(s, nx, c, ny);
     nx = rx;
     ny = ry;
   }
@@ -825,7 +865,7 @@ __device__ __forceinline__ void from_primitive(T rho, T u, T v, T p, T gm1, T *q
   q[0] = rho;
   q[1] = rho * u;
   q[2] = rho * v;
-  q[3] = p / gm1 + T(0.5) * rho * (u * u + v * v);
+  q[3] = p / gm1 + T(0.5) * rho * mul_add(u, u, v, v);
 }
 
 // Boundary conditions (Secs. 4.2-4.3 name them; these are the readings): the
@@ -850,7 +890,7 @@ __device__ __forceinline__ void boundary_states(const MeshDev &md, int tag, cons
     from_primitive(rho, T(2) * ug - u, T(2) * vg - v, p, gm1, qg);
     from_primitive(rho, ug, vg, p, gm1, qb);
   } else if (tag == SD_BC_SLIP) {
-    const T wn = (u - ug) * nx + (v - vg) * ny;
+    const T wn = mul_add(u - ug, nx, v - vg, ny);
     from_primitive(q[0], u - T(2) * wn * nx, v - T(2) * wn * ny, p, gm1, qg);
     from_primitive(q[0], u - wn * nx, v - wn * ny, p, gm1, qb);
   } else if (tag == SD_BC_INLET) {
@@ -881,10 +921,10 @@ __device__ __forceinline__ void bface_geom(const MeshDev &md, int b, int j, T &n
     // wall velocity omega_z x (R(theta_z) x0), x0 relative to the zone's centre
     const double c = md.clk->c[z], s = md.clk->s[z], om = md.clk->om[z];
     const double x0 = md.bxy[((size_t)b * N + j) * 2], y0 = md.bxy[((size_t)b * N + j) * 2 + 1];
-    uw = -om * (s * x0 + c * y0);
-    vw = om * (c * x0 - s * y0);
+    uw = -om * mul_add(s, x0, c, y0);
+    vw = om * mul_sub(c, x0, s, y0);
   }
-  const T S = sqrt(ax * ax + ay * ay), sg = (T)face_sigma(f);
+  const T S = sqrt(mul_add(ax, ax, ay, ay)), sg = (T)face_sigma(f);
   nx = sg * ax / S;
   ny = sg * ay / S;
   vgn = sg * ag / S;
@@ -899,6 +939,7 @@ __device__ __forceinline__ void k_bface_point(const MeshDev &md, int t) {
   const int b = t / N, j = t - b * N;
   const int4 bf = md.bfaces[b];
   const int ef = bf.x;
+  if (!ssd_check(md, ef >= 0 && ef < 4 * md.E)) return;
   const T *TR = (const T *)md.TR;
   T q[4], qg[4], qb[4];
 #pragma unroll
@@ -969,7 +1010,8 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
     m0 = m0d.hi;
     dm = md.mgeo[4 * m + 2];
     const double pi = 0.5 * kTwoPiHi;
-    const int fq = sd ? md.mRf[m] : md.mLf[m];
+    int fq = sd ? md.mRf[m] : md.mLf[m];
+    if (!ssd_check(md, fq >= 0 && fq < (sd ? md.nR : md.nL))) fq = 0;
     // the L side turns with its zone (interface ifz[fq] belongs to zone ifz[fq] + 1)
     ddang fa{md.Ra[fq], md.Ra_lo[fq]};
     if (!sd) {
@@ -1139,6 +1181,8 @@ __device__ __forceinline__ void gather_point(const MeshDev &md, int t) {
   // the face's mortars run cyclically through its interface's mortar range [m0, m1)
   const int ii = md.ifz[fq];
   const int m0 = md.zoff[ii] + md.zoff[kZT + ii], m1 = md.zoff[ii + 1] + md.zoff[kZT + ii + 1];
+  if (!ssd_check(md, start >= m0 && start < m1 && cnt >= 1 && cnt <= m1 - m0 && fc.x >= 0 && fc.x < 4 * md.E))
+    return;
   T acc[4] = {0, 0, 0, 0};
   int mi = start;
   for (int c = 0; c < cnt; ++c) {
@@ -1243,8 +1287,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 // bounded wait: gives up after a fixed number of polls (each poll may suspend
 // the thread for a hardware-defined time), so a lost copy cannot hang the GPU
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 22); ++i)
+constexpr int kWaitPolls = 1 << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int polls = kWaitPolls) {
+  for (int i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -1275,7 +1320,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 template <int N>
 constexpr int vol_epb_default() { return N == 3 ? 16 : (N == 6 ? 8 : 12); }
 
-template <typename T, int N, bool OTF, bool AUX = false, bool LO = true, int EPBX = 0>
+template <typename T, int N, bool OTF, bool AUX = false, bool LO = true, int EPBX = 0, bool TC = false>
 struct VolCfg {
   static constexpr int NN = N * N;
   static constexpr bool FF = std::is_same<T, float>::value;  // FP32 arithmetic (packed pairs)
@@ -1313,7 +1358,12 @@ struct VolCfg {
   // the stage's zone table [3][kZT] (cos theta_z, sin theta_z, omega_z); two
   // slots, one per pipeline stage, for a batch whose next item is another case
   static constexpr int O_ZT = O_BAR + 32;
-  static constexpr int SMEM = O_ZT + 2 * 3 * kZT * (int)sizeof(T);
+  // tensor-core variant: the tile's rows (direction, element, SP line,
+  // variable) with 8 flux-point columns, for the interpolated values and then
+  // the fluxes (the operands of the two contractions)
+  static constexpr int TC_ROWS = 8 * EPB * N;
+  static constexpr int O_TC = ((O_ZT + 2 * 3 * kZT * (int)sizeof(T)) + 127) / 128 * 128;
+  static constexpr int SMEM = TC ? O_TC + TC_ROWS * 8 * 4 : O_ZT + 2 * 3 * kZT * (int)sizeof(T);
   // transaction bytes of the two barriers' copies
   static constexpr int TX_QHI = EPB * QE, TX_CF = EPB * CE;
   static_assert((SE * (int)sizeof(T)) % 16 == 0 && (SC * (int)sizeof(T)) % 16 == 0, "bulk-copy alignment");
@@ -1328,18 +1378,18 @@ struct VolCfg {
 template <typename T>
 __device__ __forceinline__ void point_flux(const T *q, T vx, T vy, T vg, T gm1, T *f) {
   const T ir = recip(q[0]);
-  const T p = gm1 * (q[3] - T(0.5) * (q[1] * q[1] + q[2] * q[2]) * ir);
-  const T un = (q[1] * vx + q[2] * vy) * ir;
-  f[0] = q[0] * un - vg * q[0];
-  f[1] = q[1] * un + p * vx - vg * q[1];
-  f[2] = q[2] * un + p * vy - vg * q[2];
-  f[3] = (q[3] + p) * un - vg * q[3];
+  const T p = gm1 * (q[3] - T(0.5) * mul_add(q[1], q[1], q[2], q[2]) * ir);
+  const T un = mul_add(q[1], vx, q[2], vy) * ir;
+  f[0] = mul_sub(q[0], un, vg, q[0]);
+  f[1] = fma(q[1], un, mul_sub(p, vx, vg, q[1]));
+  f[2] = fma(q[2], un, mul_sub(p, vy, vg, q[2]));
+  f[3] = mul_sub(q[3] + p, un, vg, q[3]);
 }
 
 // bounded wait by warp 0 only; the other warps wait at the barrier without issuing
-__device__ __forceinline__ bool cta_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool cta_wait(uint64_t *bar, uint32_t parity, int polls = kWaitPolls) {
   bool ok = true;
-  if (threadIdx.x < 32) ok = mbar_wait_bounded(bar, parity);
+  if (threadIdx.x < 32) ok = mbar_wait_bounded(bar, parity, polls);
   return __syncthreads_and(ok) != 0;
 }
 
@@ -1402,15 +1452,151 @@ struct CaseList {
   __device__ __forceinline__ const A &args(int c) const { return a[c]; }
 };
 
+// ---- 3xTF32 tensor-core contractions (the optional path of the FP32 form) ----
+// A float x is split into two TF32 values, x = big + small (+ the remainder
+// below TF32 resolution); a product is taken as big_a big_b + big_a small_b +
+// small_a big_b, three m16n8k8 TF32 MMAs accumulating in FP32, which keeps
+// close to FP32 accuracy.
+
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void tf32_split(float x, uint32_t &big, uint32_t &small) {
+  big = tf32_of(x);
+  small = tf32_of(x - __uint_as_float(big));
+}
+
+// D += A B for one m16n8k8 tile (A row-major 16 x 8, B column-major 8 x 8,
+// TF32 inputs, FP32 accumulators; fragments as the PTX ISA lays them out)
+__device__ __forceinline__ void mma_tf32(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// 3xTF32 product of one A fragment (four floats) with a split B fragment
+__device__ __forceinline__ void mma_3xtf32(float *d, const float *af, const uint32_t *bb, const uint32_t *bs) {
+  uint32_t ab[4], as[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) tf32_split(af[q], ab[q], as[q]);
+  mma_tf32(d, as, bb[0], bb[1]);
+  mma_tf32(d, ab, bs[0], bs[1]);
+  mma_tf32(d, ab, bb[0], bb[1]);
+}
+
+// Phase 1 of the FP32 volume kernel on the tensor cores.  Rows of the tile:
+// r = ((d EPB + e) N + line) 4 + v (direction d, element e, SP line, variable
+// v), 16 per MMA tile.  (1) interpolation: X[r][i] = sum_k Q[r][k] Hf[i][k]
+// (Eq. Qt at the flux points i = 0..N, K = the N SPs of the line, padded to 8);
+// (2) each line's thread forms the transformed fluxes at its interior flux
+// points from X, the common fluxes at its end points, into the same rows;
+// (3) divergence: R[r][k] = sum_i F[r][i] Dm[k][i] (Eqs. Ft, Gt), into the
+// tile's divergence arrays.  Full warps take the MMA tiles; barriers between.
+template <typename T, int N, bool OTF, class C>
+__device__ __forceinline__ void volume_phase1_tc(const MeshDev &md, int e0, int ne, const T (*sQ)[C::SE],
+                                                 const T (*sCF)[C::SC], const int *sEF, const T *sEG,
+                                                 const T *sZT, T gm1, T (*sRF)[C::SE], T (*sRG)[C::SE],
+                                                 float (*sX)[8]) {
+  constexpr int EPB = C::EPB, NN = N * N, NT = C::THREADS, MT = C::TC_ROWS / 16, NW = NT / 32;
+  const VolBasis<T, N> &B = cVB<T, N>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  // value of row r at K index k (the SP of the line), 0 beyond the N SPs
+  auto qval = [&](int r, int k) -> float {
+    const int v = r & 3, line = (r >> 2) % N, de = (r >> 2) / N, e = de % EPB, d = de / EPB;
+    if (k >= N) return 0.0f;
+    return (float)(d == 0 ? sQ[e][v * NN + line * N + k] : sQ[e][v * NN + k * N + line]);
+  };
+  // (1) interpolation, B[k][n] = Hf[n][k] (n = flux point)
+  if (warp < NW) {
+    uint32_t bb[2], bs[2];
+    {
+      const float h0 = (g <= N && t < N) ? (float)B.Hf[g * N + t] : 0.0f;
+      const float h1 = (g <= N && t + 4 < N) ? (float)B.Hf[g * N + t + 4] : 0.0f;
+      tf32_split(h0, bb[0], bs[0]);
+      tf32_split(h1, bb[1], bs[1]);
+    }
+    for (int mt = warp; mt < MT; mt += NW) {
+      const int r0 = mt * 16;
+      float af[4] = {qval(r0 + g, t), qval(r0 + g + 8, t), qval(r0 + g, t + 4), qval(r0 + g + 8, t + 4)};
+      float dd[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_3xtf32(dd, af, bb, bs);
+      sX[r0 + g][2 * t] = dd[0];
+      sX[r0 + g][2 * t + 1] = dd[1];
+      sX[r0 + g + 8][2 * t] = dd[2];
+      sX[r0 + g + 8][2 * t + 1] = dd[3];
+    }
+  }
+  __syncthreads();
+  // (2) fluxes, one thread per SP line (as the FFMA path)
+  {
+    const int d = threadIdx.x >= EPB * N ? 1 : 0;
+    const int tl = threadIdx.x - d * EPB * N;
+    const int le = tl / N, mline = tl - le * N;
+    if (le < ne && threadIdx.x < 2 * EPB * N) {
+      ElemGeo<T, N, OTF> G;
+      G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, sZT);
+      T mvx[N + 1], mvy[N + 1], mvg[N + 1];
+      G.line_metrics(d, mline, mvx, mvy, mvg);
+      const int rb = ((d * EPB + le) * N + mline) * 4;
+      const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
+#pragma unroll
+      for (int i = 1; i < N; ++i) {
+        const float qf[4] = {sX[rb][i], sX[rb + 1][i], sX[rb + 2][i], sX[rb + 3][i]};
+        float f[4];
+        point_flux(qf, (float)mvx[i], (float)mvy[i], (float)mvg[i], (float)gm1, f);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sX[rb + v][i] = f[v];
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        sX[rb + v][0] = (float)sCF[le][(fa * 4 + v) * N + mline];
+        sX[rb + v][N] = (float)sCF[le][(fb * 4 + v) * N + mline];
+      }
+    }
+  }
+  __syncthreads();
+  // (3) divergence, B[i][n] = Dm[n][i] (n = SP of the line)
+  if (warp < NW) {
+    uint32_t bb[2], bs[2];
+    {
+      const float w0 = (g < N && t <= N) ? (float)B.Dm[g * (N + 1) + t] : 0.0f;
+      const float w1 = (g < N && t + 4 <= N) ? (float)B.Dm[g * (N + 1) + t + 4] : 0.0f;
+      tf32_split(w0, bb[0], bs[0]);
+      tf32_split(w1, bb[1], bs[1]);
+    }
+    for (int mt = warp; mt < MT; mt += NW) {
+      const int r0 = mt * 16;
+      float af[4] = {sX[r0 + g][t], sX[r0 + g + 8][t], sX[r0 + g][t + 4], sX[r0 + g + 8][t + 4]};
+      float dd[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_3xtf32(dd, af, bb, bs);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + g + (q >> 1) * 8, k = 2 * t + (q & 1);
+        if (k >= N) continue;
+        const int v = r & 3, line = (r >> 2) % N, de = (r >> 2) / N, e = de % EPB, d = de / EPB;
+        if (d == 0) sRF[e][v * NN + line * N + k] = (T)dd[q];
+        else sRG[e][v * NN + k * N + line] = (T)dd[q];
+      }
+    }
+  }
+}
+
 // The persistent volume kernel over the work items of src (see OneCase /
 // CaseList): for a batch class the items of all its cases form one list, and
 // the next item's copies are issued while the current one computes even when
 // it belongs to another case.
-template <typename T, int N, int MODE, bool OTF, bool AUX, bool LO, int EPBX, class Src>
-__global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX>::THREADS, VolCfg<T, N, OTF, AUX, LO, EPBX>::MINB)
+template <typename T, int N, int MODE, bool OTF, bool AUX, bool LO, int EPBX, class Src, bool TC = false>
+__global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX, TC>::THREADS,
+                                  VolCfg<T, N, OTF, AUX, LO, EPBX, TC>::MINB)
     k_volume(Src src, int nitems) {
   pdl_enter();
-  using C = VolCfg<T, N, OTF, AUX, LO, EPBX>;
+  using C = VolCfg<T, N, OTF, AUX, LO, EPBX, TC>;
+  static_assert(!TC || (C::FF && LO), "the tensor-core contractions are a variant of the FP32 form");
   constexpr int EPB = C::EPB, NT = C::THREADS, NN = N * N;
   constexpr bool FF = C::FF, DF = C::DF;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1430,8 +1616,16 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX>::THREADS, Vol
     const MeshDev &mn = src.mesh(cn);
     const VolArgs<T> &an = src.args(cn);
     unsigned char *sb = smem + st * C::STAGE;
+    if (!batch_check(mn, tl >= 0 && tl * EPB < mn.E)) {
+      // a work item outside its case: the barrier is armed with nothing to
+      // wait for and the tile computes on stale data, writing nothing
+      if (lane == 0) mbar_expect_tx(&bar[st], 0);
+      return;
+    }
     const size_t e0 = (size_t)tl * EPB;
-    if (lane == 0) mbar_expect_tx(&bar[st], C::TX_QHI + C::TX_CF + C::EGB + C::EFB);
+    // (the test switch of sd_test_wait_timeout arms work item 0 with more
+    // bytes than its copies deliver; it is 0 otherwise)
+    if (lane == 0) mbar_expect_tx(&bar[st], C::TX_QHI + C::TX_CF + C::EGB + C::EFB + (item == 0 ? mn.test_tx_extra : 0));
     __syncwarp();
     if (lane < EPB) {
       bulk_g2s(sb + C::O_QHI + lane * C::SE * sizeof(T), (const T *)an.in.hi + (e0 + lane) * 4 * NN, C::QE, &bar[st]);
@@ -1491,10 +1685,10 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX>::THREADS, Vol
       if (next < nitems) issueA(next, st ^ 1, threadIdx.x);
       if (txB && threadIdx.x == 0) issueB(va, tile);
     }
-    if (!cta_wait(&bar[st], (uint32_t)((it >> 1) & 1))) {
+    if (!cta_wait(&bar[st], (uint32_t)((it >> 1) & 1), (item == 0 && md.test_poll) ? md.test_poll : kWaitPolls)) {
       if (threadIdx.x == 0) {
         atomicOr(&md.clk->flags, 4);
-        // let the copies in flight land before the CTA exits
+        // let the copies in flight land before the CTA exits (full limits)
         if (next < nitems) mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
         if (txB) mbar_wait_bounded(&bar[2], (uint32_t)(it & 1));
       }
@@ -1512,7 +1706,10 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX>::THREADS, Vol
     const int d = threadIdx.x >= EPB * N ? 1 : 0;
     const int tl = threadIdx.x - d * EPB * N;
     const int le = tl / N, mline = tl - le * N;
-    if (le < ne) {
+    if constexpr (TC) {
+      volume_phase1_tc<T, N, OTF, C>(md, e0, ne, sQ, sCF, sEF, sEG, sZT, gm1, sRF, sRG,
+                                     (float(*)[8])(smem + C::O_TC));
+    } else if (le < ne) {
       ElemGeo<T, N, OTF> G;
       G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, sZT);
       T mvx[N + 1], mvy[N + 1], mvg[N + 1];
@@ -1668,13 +1865,13 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX>::THREADS, Vol
         for (int v = 0; v < 4; ++v) {
           const double R = -(double)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
           const double qk = (double)sQ[l2][(v) * NN + sp];
-          double inc = (double)va.rk.bdt * R;
-          if (use_base) inc += (double)va.rk.a0 * (sN[l2][(v) * NN + sp] - qk);
+          double inc = __dmul_rn((double)va.rk.bdt, R);
+          if (use_base) inc = fma((double)va.rk.a0, sN[l2][(v) * NN + sp] - qk, inc);
           if (AUX) inc += sW[l2][(v) * NN + sp];
           qn[v] = qk + inc;
-          if (va.w_out) va.w_out[gi + v * NN] = (T)((double)va.rk.ddt * R - (double)va.rk.g * inc);
+          if (va.w_out) va.w_out[gi + v * NN] = (T)mul_sub((double)va.rk.ddt, R, (double)va.rk.g, inc);
         }
-        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
+        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * mul_add(qn[1], qn[1], qn[2], qn[2]) / qn[0]);
         bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -1695,7 +1892,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX>::THREADS, Vol
         for (int v = 0; v < 4; ++v) {
           const float R = -(float)((sRF[l2][(v) * NN + sp] + sRG[l2][(v) * NN + sp]) * iJ);
           const float h = (float)sQ[l2][(v) * NN + sp];
-          float inc = (float)va.rk.bdt * R;
+          float inc = __fmul_rn((float)va.rk.bdt, R);
           if constexpr (DF) {
             const float l = sKL[l2][(v) * NN + sp];
             if (use_base) inc = fmaf((float)va.rk.a0, (sNH[l2][(v) * NN + sp] - h) + (sNL[l2][(v) * NN + sp] - l), inc);
@@ -1717,7 +1914,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX>::THREADS, Vol
           }
           if (va.w_out) va.w_out[gi + v * NN] = (T)fmaf(-(float)va.rk.g, inc, (float)va.rk.ddt * R);
         }
-        const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) * __frcp_rn(hv[0]));
+        const float pr = (float)gm1 * (hv[3] - 0.5f * mul_add(hv[1], hv[1], hv[2], hv[2]) * __frcp_rn(hv[0]));
         bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) sQ[l2][(v) * NN + sp] = (T)hv[v];
@@ -1856,10 +2053,10 @@ struct EngineImpl : Engine {
   }
 
   // shared-memory attribute and resident CTAs per SM of one volume-kernel variant
-  template <int MODE, bool AUX, int EPBX, class Src>
+  template <int MODE, bool AUX, int EPBX, class Src, bool TC = false>
   static cudaError_t vol_setup(int *occ) {
-    using C = VolCfg<T, N, OTF, AUX, LO, EPBX>;
-    auto *k = k_volume<T, N, MODE, OTF, AUX, LO, EPBX, Src>;
+    using C = VolCfg<T, N, OTF, AUX, LO, EPBX, TC>;
+    auto *k = k_volume<T, N, MODE, OTF, AUX, LO, EPBX, Src, TC>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (err) return err;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, C::THREADS, C::SMEM);
@@ -1877,6 +2074,9 @@ struct EngineImpl : Engine {
   bool fuse_faces_mortar = true;                  // mortar flux inside the face launch
   int sms = 1, occ_rk = 1;         // SM count, resident volume CTAs per SM
   int face_block = 256;            // block size of the conforming-face kernel
+  bool tc = false;                 // volume contractions on the tensor cores (3xTF32, FP32 form)
+  static constexpr bool kTC = OTF && LO;  // the engines that have the tensor-core variant
+  int grid_tc_res = 1, grid_tc_rk = 1, grid_tc_aux = 1;
   int face_block_max = 256;        // the most threads per block its registers allow
 
   ~EngineImpl() override {
@@ -1987,6 +2187,15 @@ struct EngineImpl : Engine {
       if ((err = vol_setup<MODE_RESIDUAL, false, 0, One>(&occ0))) return err;
       if ((err = vol_setup<MODE_RK, false, 0, One>(&occ1))) return err;
       if ((err = vol_setup<MODE_RK, true, 0, One>(&occ2))) return err;
+      if constexpr (kTC) {
+        int t0 = 0, t1 = 0, t2 = 0;
+        if ((err = vol_setup<MODE_RESIDUAL, false, 0, One, true>(&t0))) return err;
+        if ((err = vol_setup<MODE_RK, false, 0, One, true>(&t1))) return err;
+        if ((err = vol_setup<MODE_RK, true, 0, One, true>(&t2))) return err;
+        grid_tc_res = std::max(1, t0) * sms;
+        grid_tc_rk = std::max(1, t1) * sms;
+        grid_tc_aux = std::max(1, t2) * sms;
+      }
       grid_res = std::max(1, occ0) * sms;
       occ_rk = std::max(1, occ1);
       grid_rk = occ_rk * sms;
@@ -2098,15 +2307,15 @@ struct EngineImpl : Engine {
     return a;
   }
 
-  template <int MODE, bool AUX>
+  template <int MODE, bool AUX, bool TC = false>
   void launch_volume(const MeshDev &md, StatePtr in, StatePtr base, StatePtr out, double *R, const RkArgs &rk,
                      int grid, cudaStream_t s) {
-    using C = VolCfg<T, N, OTF, AUX, LO>;
+    using C = VolCfg<T, N, OTF, AUX, LO, 0, TC>;
     const int ntiles = (md.E + C::EPB - 1) / C::EPB;
     One src;
     src.md = md;
     src.a = vol_args(in, base, out, R, rk);
-    launch_pdl(k_volume<T, N, MODE, OTF, AUX, LO, 0, One>, std::min(ntiles, grid), C::THREADS, C::SMEM, s, src,
+    launch_pdl(k_volume<T, N, MODE, OTF, AUX, LO, 0, One, TC>, std::min(ntiles, grid), C::THREADS, C::SMEM, s, src,
                ntiles);
   }
 
@@ -2126,9 +2335,21 @@ struct EngineImpl : Engine {
                    s, src, ntiles);
       return;
     }
+    if constexpr (kTC) {
+      if (tc) {
+        if (mode == MODE_RESIDUAL) launch_volume<MODE_RESIDUAL, false, true>(md, in, base, out, R, rk, grid_tc_res, s);
+        else if (rk.w_in) launch_volume<MODE_RK, true, true>(md, in, base, out, R, rk, grid_tc_aux, s);
+        else launch_volume<MODE_RK, false, true>(md, in, base, out, R, rk, grid_tc_rk, s);
+        return;
+      }
+    }
     if (mode == MODE_RESIDUAL) launch_volume<MODE_RESIDUAL, false>(md, in, base, out, R, rk, grid_res, s);
     else if (rk.w_in) launch_volume<MODE_RK, true>(md, in, base, out, R, rk, grid_aux, s);
     else launch_volume<MODE_RK, false>(md, in, base, out, R, rk, grid_rk, s);
+  }
+  bool set_tensor_cores(bool on) override {
+    tc = kTC && on;
+    return tc == on;
   }
 
   cudaError_t alloc_rk54() override {
@@ -2142,8 +2363,6 @@ struct EngineImpl : Engine {
   }
   StatePtr C() const override { return StatePtr{sC[0], sC[1]}; }
   void *W() const override { return sW; }
-
-  int tile_elems() const override { return VolCfg<T, N, OTF, false, LO>::EPB; }
 
   // launch shapes chosen by the batch autotuner: volume CTAs per SM (capped
   // by occupancy; 0 keeps the current value) and the face-kernel block size
@@ -2172,6 +2391,9 @@ struct EngineImpl : Engine {
   // tile and a smaller one (more, shorter work items)
   static constexpr int kEpbAlt = vol_epb_default<N>() >= 12 ? 8 : (vol_epb_default<N>() >= 8 ? 4 : 0);
   static constexpr int kFaceBlocks[3] = {128, 256, 512};
+  static_assert(kElemPad % vol_epb_default<N>() == 0 && (kEpbAlt == 0 || kElemPad % kEpbAlt == 0) &&
+                    kElemPad % VisCfg<T, N>::EPB == 0,
+                "every tile size divides the element padding");
 
   struct BatchImpl : BatchClass {
     int n = 0, nstages = 0, viscous = 0;
@@ -2191,6 +2413,21 @@ struct EngineImpl : Engine {
       for (void *p : allocs) cudaFree(p);
     }
   };
+
+  // debug build: after each batch launch outside a graph capture, wait and
+  // name the launch if it failed
+  static void dbg_sync(cudaStream_t s, const char *what) {
+#ifdef SSD_DEBUG
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e) fprintf(stderr, "ssd debug: N=%d %s: %s\n", N, what, cudaGetErrorString(e));
+    }
+#else
+    (void)s;
+    (void)what;
+#endif
+  }
 
   int batch_tile_choices(int *out) const override {
     out[0] = vol_epb_default<N>();
@@ -2294,7 +2531,7 @@ struct EngineImpl : Engine {
     return batch_args(*static_cast<BatchImpl *>(bc), stages, s);
   }
 
-  void batch_tuning(BatchClass *bc, int *vol_ctas_per_sm, int *tile_elems, int *fblock) override {
+  void batch_tuning(BatchClass *bc, int *vol_ctas_per_sm, int *tile_elems, int *fblock, cudaStream_t s) override {
     BatchImpl &b = *static_cast<BatchImpl *>(bc);
     bool re = false;
     if (tile_elems && *tile_elems > 0 && !b.viscous) {
@@ -2302,15 +2539,15 @@ struct EngineImpl : Engine {
       re |= alt != b.epb_alt;
       b.epb_alt = alt;
     }
-    const int occ = b.viscous ? b.occ_visc : b.occ[b.epb_alt];
-    if (vol_ctas_per_sm && *vol_ctas_per_sm > 0) b.vol_ctas = std::min(*vol_ctas_per_sm, std::max(1, occ));
-    b.vol_ctas = std::min(b.vol_ctas, std::max(1, occ));
+    const int occ = std::max(1, b.viscous ? b.occ_visc : b.occ[b.epb_alt]);
+    if (vol_ctas_per_sm && *vol_ctas_per_sm > 0) b.vol_ctas = std::min(*vol_ctas_per_sm, occ);
+    b.vol_ctas = std::max(1, std::min(b.vol_ctas, occ));
     if (fblock && *fblock > 0) {
       const int fb = *fblock <= 128 ? 128 : (*fblock <= 256 ? 256 : 512);
       re |= fb != b.face_block;
       b.face_block = fb;
     }
-    if (re) batch_offsets(b, 0);
+    if (re) batch_offsets(b, s);
     if (vol_ctas_per_sm) *vol_ctas_per_sm = b.vol_ctas;
     if (tile_elems) *tile_elems = b.viscous ? VisVolCfg<T, N>::EPB : (b.epb_alt ? kEpbAlt : vol_epb_default<N>());
     if (fblock) *fblock = b.face_block;
@@ -2324,18 +2561,21 @@ struct EngineImpl : Engine {
     if (b.face_block == 128) launch_pdl(k_batch_faces<T, N, OTF, MMODE, 128>, b.nfblk, 128, 0, s, w);
     else if (b.face_block == 256) launch_pdl(k_batch_faces<T, N, OTF, MMODE, 256>, b.nfblk, 256, 0, s, w);
     else launch_pdl(k_batch_faces<T, N, OTF, MMODE, 512>, b.nfblk, 512, 0, s, w);
+    dbg_sync(s, "batch face pass");
   }
 
   template <int GMODE>
   void batch_gather(const BatchImpl &b, const BatchWork &w, cudaStream_t s) {
     if (b.ngpt > 0) launch_pdl(k_batch_gather<T, N, GMODE>, (b.ngpt + 127) / 128, 128, 0, s, w, b.ngpt);
+    dbg_sync(s, "batch gather");
   }
 
   template <bool AUX, int EPBX>
   void batch_volume(const BatchImpl &b, const List &src, cudaStream_t s) {
     using C = VolCfg<T, N, OTF, AUX, LO, EPBX>;
-    launch_pdl(k_volume<T, N, MODE_RK, OTF, AUX, LO, EPBX, List>, std::min(b.ntile, b.vol_ctas * sms), C::THREADS,
-               C::SMEM, s, src, b.ntile);
+    launch_pdl(k_volume<T, N, MODE_RK, OTF, AUX, LO, EPBX, List>, std::max(1, std::min(b.ntile, b.vol_ctas * sms)),
+               C::THREADS, C::SMEM, s, src, b.ntile);
+    dbg_sync(s, "batch volume");
   }
 
   void batch_stage(BatchClass *bc, int k, cudaStream_t s) override {
@@ -2364,19 +2604,22 @@ struct EngineImpl : Engine {
     batch_gather<GATHER_Q>(b, w, s);
     using G = GradCfg<T, N>;
     src.off = b.off_gtile;
-    launch_pdl(k_grad_trace<T, N, OTF, List>, std::min(b.ngtile, b.occ_grad * sms), G::THREADS, G::SMEM, s, src,
-               b.ngtile);
+    launch_pdl(k_grad_trace<T, N, OTF, List>, std::max(1, std::min(b.ngtile, std::max(1, b.occ_grad) * sms)),
+               G::THREADS, G::SMEM, s, src, b.ngtile);
+    dbg_sync(s, "batch gradients");
     batch_face_pass<MORTAR_RUSANOV_FV>(b, w, s);
     batch_gather<GATHER_FLUX>(b, w, s);
     using V = VisVolCfg<T, N>;
     src.off = b.off_tile;
-    launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO, List>, std::min(b.ntile, b.vol_ctas * sms), V::THREADS,
-               V::SMEM, s, src, b.ntile);
+    launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO, List>, std::max(1, std::min(b.ntile, b.vol_ctas * sms)),
+               V::THREADS, V::SMEM, s, src, b.ntile);
+    dbg_sync(s, "batch viscous volume");
   }
 
   void batch_merge(const BatchMergeDev &bm, cudaStream_t s) override {
     if (bm.smem > 48 * 1024) cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, bm.smem);
     launch_pdl(k_batch_merge, dim3(bm.max_iface, bm.nstages, bm.ncase), 1024, bm.smem, s, bm);
+    dbg_sync(s, "batch merge");
   }
 
   void batch_advance(const BatchMergeDev &bm, cudaStream_t s) override {

@@ -14,6 +14,10 @@ constexpr int kMaxN = 8;
 // rigidly about its own centre and has its own sliding interface)
 constexpr int kMaxZones = 4;
 constexpr int kZT = kMaxZones + 1;  // per-zone table entries, zone 0 included
+// Per-element arrays are padded to a multiple of kElemPad elements: every tile
+// size the persistent kernels use (4, 8, 12, 16 elements) divides it, so a
+// tile that copies whole tiles stays inside the arrays whichever size runs.
+constexpr int kElemPad = 48;
 // cell flag: zone in the low kZoneBits bits, (metric table index + 1) above
 constexpr int kZoneBits = 3, kZoneMask = (1 << kZoneBits) - 1;
 static_assert(kMaxZones <= kZoneMask, "zone bits");
@@ -33,7 +37,8 @@ struct DevClock {
   double theta2_lo[kZT];  // and low part
   double c[kZT], s[kZT], om[kZT];
   float cf[kZT], sf[kZT], omf[kZT];
-  int flags;  // bit 0: non-physical state; bit 1: mesh geometry error; bit 2: a bounded device wait gave up
+  int flags;  // bit 0: non-physical state; bit 1: mesh geometry error; bit 2: a bounded device wait gave up;
+              // bit 3: (debug build) a table index out of range
   int pad;
 };
 
@@ -125,6 +130,9 @@ struct MeshDev {
   int any_farfield;                     // the mesh has inlet or outlet faces
   float gamma_f;  // the same rounded to float (FP32 path)
   int viscous;
+  // test switch of the bounded waits (sd_test_wait_timeout), 0 otherwise: extra
+  // transaction bytes armed on volume work item 0 and its wait's poll limit
+  int test_tx_extra, test_poll;
 };
 
 enum { MODE_RESIDUAL = 0, MODE_RK = 1 };
@@ -189,9 +197,6 @@ struct Engine {
   virtual size_t compute_word() const = 0;
   // true: straight cells get their metrics on the fly (tables only for arc cells)
   virtual bool metrics_on_the_fly() const = 0;
-  // elements per volume-kernel tile; every per-element device array holds a
-  // whole number of tiles (padding elements are never computed on)
-  virtual int tile_elems() const = 0;
   // get / set the tunable launch shapes (see EngineImpl::tuning)
   virtual void tuning(int *vol_ctas_per_sm, int *max_ctas_per_sm, int *face_block) = 0;
   // the two state buffers A and B: E elements, storage for Epad >= E
@@ -221,6 +226,9 @@ struct Engine {
   // true (default): the mortar flux runs inside the face launch of the same
   // pass; false: as its own launch in mortars() (per-phase timing)
   virtual void set_fusion(bool on) = 0;
+  // the inviscid volume kernel's interpolation and divergence contractions on
+  // the tensor cores (3xTF32; FP32 form only); returns false if unavailable
+  virtual bool set_tensor_cores(bool on) = 0;
   void couple(const MeshDev &md, StatePtr q, double c, double dt, cudaStream_t s) {
     clock_merge(md, c, dt, s);
     faces(md, q, s);
@@ -256,7 +264,8 @@ struct Engine {
   // launch shapes: volume CTAs per SM (0: keep) and elements per volume tile
   // (0: keep; one of the values batch_tile_choices lists) and face-pass
   // block size (0: keep); returns the values in force
-  virtual void batch_tuning(BatchClass *bc, int *vol_ctas_per_sm, int *tile_elems, int *face_block) = 0;
+  virtual void batch_tuning(BatchClass *bc, int *vol_ctas_per_sm, int *tile_elems, int *face_block,
+                            cudaStream_t s) = 0;
   virtual int batch_tile_choices(int *out) const = 0;
   virtual void batch_free(BatchClass *bc) = 0;
   // the clocks and mortar tables of every stage of every case of a batch in

@@ -37,24 +37,26 @@ __device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *q
   const T kc = conduct ? pick<T>(md.kc, md.kc_f) : T(0);
   const T ir = T(1) / q[0];
   const T u = q[1] * ir, v = q[2] * ir;
-  const T ux = (qx[1] - u * qx[0]) * ir, uy = (qy[1] - u * qy[0]) * ir;
-  const T vx = (qx[2] - v * qx[0]) * ir, vy = (qy[2] - v * qy[0]) * ir;
-  const T ke = T(0.5) * (u * u + v * v);
+  // velocity gradients rounded as products (mul_rn): they are summed with each
+  // other below, where an FMA could otherwise take either one
+  const T ux = mul_rn(qx[1] - u * qx[0], ir), uy = mul_rn(qy[1] - u * qy[0], ir);
+  const T vx = mul_rn(qx[2] - v * qx[0], ir), vy = mul_rn(qy[2] - v * qy[0], ir);
+  const T ke = T(0.5) * mul_add(u, u, v, v);
   const T p = gm1 * (q[3] - ke * q[0]);
   const T Tt = p * ir / Rg;
-  const T px = gm1 * (qx[3] - (u * qx[1] + v * qx[2] - ke * qx[0]));
-  const T py = gm1 * (qy[3] - (u * qy[1] + v * qy[2] - ke * qy[0]));
+  const T px = mul_rn(gm1, qx[3] - fma(u, qx[1], mul_sub(v, qx[2], ke, qx[0])));
+  const T py = mul_rn(gm1, qy[3] - fma(u, qy[1], mul_sub(v, qy[2], ke, qy[0])));
   const T Tx = (px - Rg * Tt * qx[0]) * ir / Rg, Ty = (py - Rg * Tt * qy[0]) * ir / Rg;
   const T lam = T(-2) / T(3) * mu, dv = ux + vy;
-  const T txx = T(2) * mu * ux + lam * dv, tyy = T(2) * mu * vy + lam * dv, txy = mu * (uy + vx);
+  const T txx = mul_add(T(2) * mu, ux, lam, dv), tyy = mul_add(T(2) * mu, vy, lam, dv), txy = mu * (uy + vx);
   F[0] = 0;
   F[1] = -txx;
   F[2] = -txy;
-  F[3] = -(u * txx + v * txy + kc * Tx);
+  F[3] = -fma(u, txx, mul_add(v, txy, kc, Tx));
   G[0] = 0;
   G[1] = -txy;
   G[2] = -tyy;
-  G[3] = -(u * txy + v * tyy + kc * Ty);
+  G[3] = -fma(u, txy, mul_add(v, tyy, kc, Ty));
 }
 
 // ---- common solution -------------------------------------------------------
@@ -157,8 +159,8 @@ __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const T a = sDx[l2][v][sp], b = sDe[l2][v][sp];
-      sDx[l2][v][sp] = xix * a + etx * b;
-      sDe[l2][v][sp] = xiy * a + ety * b;
+      sDx[l2][v][sp] = mul_add(xix, a, etx, b);
+      sDe[l2][v][sp] = mul_add(xiy, a, ety, b);
     }
   }
 }
@@ -202,6 +204,10 @@ __global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(Src src, 
     const MeshDev &mn = src.mesh(cn);
     const T *Q = (const T *)src.args(cn).in.hi;
     unsigned char *sb = smem + st * C::STAGE;
+    if (!batch_check(mn, tl >= 0 && tl * EPB < mn.E)) {
+      mbar_expect_tx(&bar[st], 0);  // a work item outside its case: nothing copied
+      return;
+    }
     const size_t e0 = (size_t)tl * EPB;
     const uint32_t ne = (uint32_t)min(EPB, mn.E - (int)e0), nf = (ne + 3u) & ~3u;
     mbar_expect_tx(&bar[st], ne * (C::QE + C::CE + (OTF ? C::GEE : 0)) + nf * 4u);
@@ -290,7 +296,7 @@ __device__ __forceinline__ void viscous_normal(const T *q, const T *g8, T nx, T 
   T F[4], G[4];
   viscous_flux(q, g8, g8 + 4, md, F, G, conduct);
 #pragma unroll
-  for (int v = 0; v < 4; ++v) fn[v] = F[v] * nx + G[v] * ny;
+  for (int v = 0; v < 4; ++v) fn[v] = mul_add(F[v], nx, G[v], ny);
 }
 
 template <typename T, int N>
@@ -318,7 +324,7 @@ __device__ __forceinline__ void k_face_visc_point(const MeshDev &md, int t) {
   if (z) {
     const T *zt = zone_tab<T>(md.clk);
     const T c = zt[z], s = zt[kZT + z];
-    const T rx = c * nx - s * ny, ry = s * nx + c * ny;
+    const T rx = mul_sub(c, nx, s, ny), ry = mul_add(s, nx, c, ny);
     nx = rx;
     ny = ry;
   }
@@ -419,6 +425,10 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     src.item(item, cn, tl);
     const MeshDev &mn = src.mesh(cn);
     unsigned char *sb = smem + st * C::STAGE;
+    if (!batch_check(mn, tl >= 0 && tl * EPB < mn.E)) {
+      mbar_expect_tx(&bar[st], 0);  // a work item outside its case: nothing copied
+      return;
+    }
     const size_t e0 = (size_t)tl * EPB;
     const uint32_t ne = (uint32_t)min(EPB, mn.E - (int)e0), nf = (ne + 3u) & ~3u;
     mbar_expect_tx(&bar[st], ne * (C::QE + C::GE + C::CE + (OTF ? C::GEE : 0)) + nf * 4u);
@@ -519,7 +529,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           T Fv[4], Gv[4];
           viscous_flux(qf, g8, g8 + 4, md, Fv, Gv);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) f[v] += vx * Fv[v] + vy * Gv[v];
+          for (int v = 0; v < 4; ++v) f[v] = fma(vx, Fv[v], fma(vy, Gv[v], f[v]));
         }
 #pragma unroll
         for (int k = 0; k < N; ++k) {
@@ -567,7 +577,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           const size_t ii = gi + v * NN;
           const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
           const float h = (float)sQ[l2][v][sp];
-          float inc = (float)rk.bdt * R;
+          float inc = __fmul_rn((float)rk.bdt, R);
           if constexpr (LO) {
             const float l = kl[v];
             if (has_base) inc = fmaf((float)rk.a0, (bh[v] - h) + (bl[v] - l), inc);
@@ -589,7 +599,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           }
           if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
         }
-        const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
+        const float pr = (float)gm1 * (hv[3] - 0.5f * mul_add(hv[1], hv[1], hv[2], hv[2]) / hv[0]);
         bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -614,13 +624,13 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           const size_t ii = gi + v * NN;
           const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
           const double qk = (double)sQ[l2][v][sp];
-          double inc = (double)rk.bdt * R;
-          if (has_base) inc += (double)rk.a0 * (((const double *)base.hi)[ii] - qk);
+          double inc = __dmul_rn((double)rk.bdt, R);
+          if (has_base) inc = fma((double)rk.a0, ((const double *)base.hi)[ii] - qk, inc);
           if (w_in) inc += (double)w_in[ii];
           qn[v] = qk + inc;
-          if (w_out) w_out[ii] = (T)((double)rk.ddt * R - (double)rk.g * inc);
+          if (w_out) w_out[ii] = (T)mul_sub((double)rk.ddt, R, (double)rk.g, inc);
         }
-        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * (qn[1] * qn[1] + qn[2] * qn[2]) / qn[0]);
+        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * mul_add(qn[1], qn[1], qn[2], qn[2]) / qn[0]);
         bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -634,7 +644,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           const size_t ii = gi + v * NN;
           const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
           const float h = (float)sQ[l2][v][sp];
-          float inc = (float)rk.bdt * R;
+          float inc = __fmul_rn((float)rk.bdt, R);
           if constexpr (LO) {
             const float l = ((const float *)in.lo)[ii];
             if (has_base)
@@ -657,7 +667,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           }
           if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
         }
-        const float pr = (float)gm1 * (hv[3] - 0.5f * (hv[1] * hv[1] + hv[2] * hv[2]) / hv[0]);
+        const float pr = (float)gm1 * (hv[3] - 0.5f * mul_add(hv[1], hv[1], hv[2], hv[2]) / hv[0]);
         bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) sQ[l2][v][sp] = (T)hv[v];
