@@ -138,6 +138,22 @@ def volume_bytes_per_element(N, w_c, w_s=8):
     return state * (2 + 2.0 / 3.0) + 2 * 16 * N * w_c + 4 * 16 + 4
 
 
+def volume_flops_per_element(N):
+    """FP64 floating-point operations one element takes in the volume kernel
+    in a Runge-Kutta stage with a base state, counted from the kernel (an FMA
+    counts 2).  Per SP line (2 N of them): at each of the N - 1 interior flux
+    points the rotated metric vector (6), the interpolation of 4 variables
+    (8 N) and the transformed ALE flux (28: pressure 7, normal velocity 4,
+    the four flux components 3 + 5 + 5 + 4, besides one reciprocal); at all
+    N + 1 flux points the divergence into N SPs (8 N); the face traces of the
+    new state (16 N).  Per SP: the residual and the Runge-Kutta combination
+    of 4 variables (7 each) and the positivity check (6, besides one
+    division).  Divisions / reciprocals, (N - 1) per line and one per SP, are
+    not counted."""
+    per_line = (N - 1) * (6 + 8 * N + 28) + (N + 1) * 8 * N + 16 * N
+    return 2 * N * per_line + N * N * 34
+
+
 def interface_fraction(prof):
     """Share of a step spent on sliding-interface work, the paper's
     "interface" time (Tables 3-10): the stage clock and mortar merge, the
@@ -282,16 +298,20 @@ def run_reference(args):
     return 0
 
 
-def run_batched(ssd, ncases, steps):
-    """Batched form: a seeded mix of independent cases (Couette, rotor and
-    rotating-ellipse families, 1k-8k cells, p = 2..5, omega in [0.1, 1])
-    advanced by one CUDA-graph launch per step, on the FP32 path and, for the
-    speedup and the accuracy, on the FP64 path; against the same FP32 cases
-    stepped through their own handles (each its own graph and stream, issued
-    one after another, so they run concurrently).  Wall-clock time around
+def run_batched(ssd, ncases, steps, max_cells=50000):
+    """Batched form (config 3): a seeded mix of independent cases (Couette,
+    rotor and rotating-ellipse families, 1k-50k cells, p = 2..5, omega in
+    [0.1, 1]) advanced together -- one launch per phase for all cases of a
+    class (equal N and viscous flag), one CUDA graph per step -- on the FP32
+    path with autotuned launch shapes and, for the speedup and the accuracy,
+    on the FP64 path (default shapes); against the same FP32 cases stepped
+    through their own handles (each its own graph and stream, issued one
+    after another, so they run concurrently).  Wall-clock time around
     synchronised calls."""
     from ssd_inputs.workloads import batch_cases
-    cases = batch_cases(ncases)
+    t_gen = time.perf_counter()
+    cases = batch_cases(ncases, max_cells=max_cells)
+    t_gen = time.perf_counter() - t_gen
     dts = [c[4] for c in cases]
 
     def start(b, k, name, prm):
@@ -302,9 +322,11 @@ def run_batched(ssd, ncases, steps):
             return b.cases[k].state_from(lambda x, y: fields.uniform(x, y, rho=1.0, p=prm.Rgas))
         return b.cases[k].state_from(lambda x, y: fields.isentropic_vortex(x, y))
 
-    def run(precision, separate=False):
+    def run(precision, tune_dt, separate=False):
+        t0 = time.perf_counter()
         b = ssd.Batch([c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases], precision=precision,
-                      tune_dt=1e-5)
+                      tune_dt=tune_dt)
+        t_create = time.perf_counter() - t0
         states = [start(b, k, c[0], c[3]) for k, c in enumerate(cases)]
         for k, q in enumerate(states):
             b.cases[k].sd_set_state(q)
@@ -319,8 +341,14 @@ def run_batched(ssd, ncases, steps):
         b.sd_batch_sync()
         el = time.perf_counter() - t0
         finals = [c.sd_get_state() for c in b.cases]
+        info = b.class_info()
         el_sep = None
         if separate:
+            for k, c in enumerate(b.cases):
+                c.sd_set_state(states[k])
+                c.sd_step(dts[k], 5)
+            for c in b.cases:
+                c.sd_sync()
             for k, c in enumerate(b.cases):
                 c.sd_set_state(states[k])
             t1 = time.perf_counter()
@@ -330,18 +358,20 @@ def run_batched(ssd, ncases, steps):
                 c.sd_sync()
             el_sep = time.perf_counter() - t1
         b.close()
-        return dofs, el, el_sep, finals
+        return dofs, el, el_sep, finals, info, t_create
 
-    dofs, el, el_sep, q32 = run(ssd.SD_PREC_FP32, separate=True)
-    _, el64, _, q64 = run(ssd.SD_PREC_FP64)
+    dofs, el, el_sep, q32, info, t_create = run(ssd.SD_PREC_FP32, 1e-5, separate=True)
+    _, el64, _, q64, _, _ = run(ssd.SD_PREC_FP64, 0.0)
     worst = max(float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2))) for a, b in zip(q32, q64))
+    cells = [int(len(c[1]["elem_nodes"])) for c in cases]
     return {"value": dofs * steps / el, "unit": "DOF-updates/s", "cases": len(cases), "dofs": dofs,
-            "cells": int(sum(len(c[1]["elem_nodes"]) for c in cases)), "steps": steps,
-            "ms_per_step": el / steps * 1e3, "precision": "f32", "autotuned": True,
-            "fp64_value": dofs * steps / el64, "fp64_ms_per_step": el64 / steps * 1e3,
+            "cells": int(sum(cells)), "cells_min": min(cells), "cells_max": max(cells), "steps": steps,
+            "ms_per_step": el / steps * 1e3, "precision": "f32", "autotuned": True, "classes": info,
+            "fp64_value": dofs * steps / el64, "fp64_ms_per_step": el64 / steps * 1e3, "fp64_autotuned": False,
             "speedup_vs_fp64": el64 / el, "fp32_rel_l2_vs_fp64_worst_case": worst,
             "concurrent_handles_ms_per_step": el_sep / steps * 1e3, "speedup_vs_concurrent_handles": el_sep / el,
-            "timing": "wall clock around synchronised calls"}
+            "timing": "wall clock around synchronised calls", "mesh_generation_s": t_gen,
+            "create_and_tune_s": t_create}
 
 
 def start_field(w):
@@ -440,6 +470,60 @@ def run_tank(ssd, stream, steps, warmup):
     return run_config(ssd, stream, "tank_n4", steps, warmup, rest, "uniform fluid at rest (Sec. 4)")
 
 
+def run_vortex(ssd, stream, t_end=0.25):
+    """The vortex configuration (Sec. 4.1): the strength-5 isentropic vortex
+    convected through the rotating disk of the 6,016-cell mesh, N = 4 and 5,
+    to t_end.  Per N: FP32 and FP64 throughput (CUDA events on the solver's
+    stream), the density L2 error against the exact translated vortex at
+    t_end, the FP32-vs-FP64 state difference, and the FP64 error and order
+    from the same run on the h/2 mesh (24,064 cells)."""
+    import torch
+    from ssd_inputs.workloads import vortex_family
+    vortex = lambda x, y: fields.isentropic_vortex(x, y)
+
+    def run(N, scale, prec):
+        mesh, prm, dt = vortex_family(N, scale)
+        n = int(math.ceil(t_end / dt))
+        dt = t_end / n
+        s = ssd.Solver(mesh, N - 1, prm, precision=prec, stream=stream.cuda_stream)
+        q0 = s.state_from(vortex)
+        s.sd_set_state(q0)
+        s.sd_step(dt, 5)
+        s.sd_sync()
+        s.sd_set_state(q0)
+        s.sd_set_time(0.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.sd_step(dt, n)
+        b.record(stream)
+        b.synchronize()
+        s.sd_sync()
+        ms = a.elapsed_time(b)
+        t = s.sd_get_time()
+        Q = s.sd_get_state()
+        xy = s.sd_sp_coords(t)
+        ex = fields.isentropic_vortex(xy[..., 0], xy[..., 1], t=t, period=(-10.0, 20.0))
+        err = float(np.sqrt(np.mean((Q[:, 0] - ex[..., 0]) ** 2)))
+        res = {"value": s.n_dofs * n / (ms * 1e-3), "unit": "DOF-updates/s", "ms_per_step": ms / n, "steps": n,
+               "elements": s.E, "l2_error_rho": err}
+        s.close()
+        return res, Q
+
+    out = {"workload": "vortex_n4 / vortex_n5", "t_end": t_end,
+           "description": "isentropic vortex (strength 5) on periodic [-10,10]^2, rotating disk r<=3 at "
+                          "omega=pi/4, 6,016 quads"}
+    for N in (4, 5):
+        r32, q32 = run(N, 1, ssd.SD_PREC_FP32)
+        r64, q64 = run(N, 1, ssd.SD_PREC_FP64)
+        fine, _ = run(N, 2, ssd.SD_PREC_FP64)
+        out[f"N{N}"] = {"fp32": r32, "fp64": r64,
+                        "fp32_rel_l2_vs_fp64": float(np.sqrt(np.sum((q32 - q64) ** 2) / np.sum(q64 ** 2))),
+                        "fp32_speedup": r32["value"] / r64["value"],
+                        "fp64_h2": {"elements": fine["elements"], "l2_error_rho": fine["l2_error_rho"],
+                                    "order": math.log2(r64["l2_error_rho"] / fine["l2_error_rho"])}}
+    return out
+
+
 def run_twin(ssd, stream, steps, warmup):
     """Two counter-rotating rotors (123,450 cells, N = 6, Euler; two rotating
     zones, each with its own sliding interface) with the strength-5 vortex
@@ -455,18 +539,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rotor_n6")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32s"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32s", "tf32"])
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--batch-cases", type=int, default=64)
+    # the batched form is held off the GPU by default (0 cases): a 64-case run
+    # of it stopped on a device error whose cause is not yet found
+    ap.add_argument("--batch-cases", type=int, default=0)
     ap.add_argument("--batch-steps", type=int, default=50)
+    ap.add_argument("--batch-max-cells", type=int, default=50000)
     ap.add_argument("--ellipse-steps", type=int, default=200)
     ap.add_argument("--tank-steps", type=int, default=200)
     ap.add_argument("--couette-steps", type=int, default=200)
     ap.add_argument("--twin-steps", type=int, default=200)
+    ap.add_argument("--vortex-t", type=float, default=0.25, help="vortex-configuration leg end time (0: skip)")
     ap.add_argument("--fp32s-steps", type=int, default=-1, help="FP32-state leg steps (-1: same as --steps)")
+    ap.add_argument("--tf32-steps", type=int, default=-1, help="3xTF32 tensor-core leg steps (-1: same as --steps)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -486,7 +575,8 @@ def main():
 
     w = build_workload(args.workload)
     N, dt = w.N, w.cfl_dt
-    prec = {"fp32": ssd.SD_PREC_FP32, "fp64": ssd.SD_PREC_FP64, "fp32s": ssd.SD_PREC_FP32S}[args.precision]
+    prec = {"fp32": ssd.SD_PREC_FP32, "fp64": ssd.SD_PREC_FP64, "fp32s": ssd.SD_PREC_FP32S,
+            "tf32": ssd.SD_PREC_FP32_TF32}[args.precision]
     stream = torch.cuda.Stream()
     solver = ssd.Solver(w.mesh, N - 1, w.params, precision=prec, stream=stream.cuda_stream)
     Q0 = solver.state_from(start_field(w))
@@ -546,20 +636,34 @@ def main():
         b.synchronize()
         s64.sd_sync()
         ms64 = a.elapsed_time(b)
-        # bring FP64 to the same step count as the FP32 run, compare states
-        rest = args.steps - args.fp64_steps
-        if rest > 0:
-            s64.sd_step(dt, rest)
-            s64.sd_sync()
+        # the FP64 state after the FP32 run's steps (warm-up + timed), from the same start
+        s64.sd_set_state(Q0)
+        s64.sd_set_time(0.0)
+        s64.sd_step(dt, args.warmup + args.steps)
+        s64.sd_sync()
         Q64 = s64.sd_get_state()
         rel = float(np.sqrt(np.sum((Q - Q64) ** 2) / np.sum(Q64 ** 2)))
         fp64 = {"value": dofs * args.fp64_steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.fp64_steps,
                 "fp32_rel_l2_vs_fp64": rel, "fp32_speedup": (dofs * args.steps / (ms * 1e-3)) /
                 (dofs * args.fp64_steps / (ms64 * 1e-3))}
-        try:
-            fp64["fma_peak_tflops"] = s64.sd_fma_peak(ssd.SD_PREC_FP64)
-        except Exception:
-            pass
+        peak64 = s64.sd_fma_peak(ssd.SD_PREC_FP64)
+        fp64["fma_peak_tflops"] = peak64
+        # the FP64 volume kernel against the FP64 pipe (its bound: GB300's FP64
+        # rate is 1/64 of FP32) and against HBM
+        prof64 = s64.sd_profile_step(dt, reps=3)
+        fl64 = volume_flops_per_element(N) * s64.E
+        ach64 = fl64 / (prof64["volume"] * 1e-3) / 1e12
+        vb64 = volume_bytes_per_element(N, 8, 8) * s64.E
+        pk_hbm, _ = _peaks()
+        fp64["kernel_ms"] = prof64
+        fp64["interface_fraction"] = interface_fraction(prof64)
+        fp64["roofline"] = {"bound": "alu", "pipe": "fp64", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                            "frac": ach64 / peak64, "kernel": "k_volume",
+                            "peak_source": "measured FP64 FMA throughput of this GPU (sd_fma_peak)",
+                            "algorithmic_flops_per_launch": fl64,
+                            "flops_per_element": volume_flops_per_element(N),
+                            "hbm_achieved_gbs": vb64 / (prof64["volume"] * 1e-3) / 1e9,
+                            "hbm_frac": vb64 / (prof64["volume"] * 1e-3) / 1e9 / pk_hbm}
         s64.close()
 
     # FP32 state storage on the same workload: throughput, volume-kernel
@@ -592,6 +696,33 @@ def main():
         fp32s["roofline"] = {"bound": "hbm", "achieved": ach3, "peak": pk, "unit": "GB/s", "frac": ach3 / pk,
                              "kernel": "k_volume", "algorithmic_bytes_per_launch": vb3}
         s3.close()
+
+    # the FP32 form with the volume contractions on the tensor cores (3xTF32):
+    # throughput, volume-kernel time, difference from the FP64 path
+    tf32 = None
+    if args.tf32_steps < 0:
+        args.tf32_steps = args.steps
+    if prec == ssd.SD_PREC_FP32 and args.tf32_steps > 0:
+        st = ssd.Solver(w.mesh, N - 1, w.params, precision=ssd.SD_PREC_FP32_TF32, stream=stream.cuda_stream)
+        st.sd_set_state(Q0)
+        st.sd_step(dt, args.warmup)
+        st.sd_sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st.sd_step(dt, args.tf32_steps)
+        b.record(stream)
+        b.synchronize()
+        st.sd_sync()
+        mst = a.elapsed_time(b)
+        tf32 = {"value": dofs * args.tf32_steps / (mst * 1e-3), "unit": "DOF-updates/s",
+                "ms_per_step": mst / args.tf32_steps, "steps": args.tf32_steps,
+                "contractions": "interpolation and divergence as 3xTF32 mma.sync m16n8k8 (tensor pipe)"}
+        if fp64 is not None and args.tf32_steps == args.steps:
+            Qt = st.sd_get_state()
+            tf32["rel_l2_vs_fp64"] = float(np.sqrt(np.sum((Qt - Q64) ** 2) / np.sum(Q64 ** 2)))
+            tf32["rel_l2_vs_fp32_ffma"] = float(np.sqrt(np.sum((Qt - Q) ** 2) / np.sum(Q ** 2)))
+        tf32["kernel_ms"] = st.sd_profile_step(dt, reps=5)
+        st.close()
 
     # per-kernel timing (CUDA events on the handle's stream) -> roofline of the volume kernel
     prof = solver.sd_profile_step(dt, reps=5)
@@ -642,11 +773,15 @@ def main():
         e2e.update({"set_state_ms": 1e3 * t_set / n_e, "step_and_get_state_ms": 1e3 * t_rest / n_e,
                     "h2d_gbs": state_bytes / (t_set / n_e) / 1e9 if t_set > 0 else None})
 
-    batched = run_batched(ssd, args.batch_cases, args.batch_steps) if args.batch_cases > 0 else None
+    batched = (run_batched(ssd, args.batch_cases, args.batch_steps, args.batch_max_cells)
+               if args.batch_cases > 0 else
+               {"held": "not run: the batched kernels are held off the GPU until an error seen in a 64-case "
+                        "run is explained"})
     ellipse = run_ellipse(ssd, stream, args.ellipse_steps, 5) if args.ellipse_steps > 0 else None
     tank = run_tank(ssd, stream, args.tank_steps, 5) if args.tank_steps > 0 else None
     couette = run_couette(ssd, stream, args.couette_steps, 5) if args.couette_steps > 0 else None
     twin = run_twin(ssd, stream, args.twin_steps, 5) if args.twin_steps > 0 else None
+    vortex = run_vortex(ssd, stream, args.vortex_t) if args.vortex_t > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -670,11 +805,13 @@ def main():
             "l2_error_rho_vs_exact": l2_rho, "t_final": t_end,
             "fp64": fp64,
             "fp32_state": fp32s,
+            "tf32x3": tf32,
             "batched": batched,
             "ellipse": ellipse,
             "tank": tank,
             "couette": couette,
             "twin_rotor": twin,
+            "vortex": vortex,
             "kernel_ms": prof,
             "interface_fraction": interface_fraction(prof),
             "fp32_fma_peak_tflops": fp32_peak,
