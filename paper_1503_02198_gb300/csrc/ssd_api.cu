@@ -854,11 +854,13 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
     md.p_inf = prm->p_inf;
     md.gm1 = prm->gamma - 1.0;
     md.kc = prm->mu * prm->gamma * prm->Rgas / ((prm->gamma - 1.0) * prm->prandtl);
+    md.kcR = prm->mu * prm->gamma / ((prm->gamma - 1.0) * prm->prandtl);
     md.RTw = prm->Rgas * prm->T_wall;
     md.gm1_f = (float)md.gm1;
     md.Rgas_f = (float)prm->Rgas;
     md.mu_f = (float)prm->mu;
     md.kc_f = (float)md.kc;
+    md.kcR_f = (float)md.kcR;
     md.RTw_f = (float)md.RTw;
     md.rho_inf_f = (float)prm->rho_inf;
     md.u_inf_f = (float)prm->u_inf;

@@ -2392,7 +2392,7 @@ struct EngineImpl : Engine {
   static constexpr int kEpbAlt = vol_epb_default<N>() >= 12 ? 8 : (vol_epb_default<N>() >= 8 ? 4 : 0);
   static constexpr int kFaceBlocks[3] = {128, 256, 512};
   static_assert(kElemPad % vol_epb_default<N>() == 0 && (kEpbAlt == 0 || kElemPad % kEpbAlt == 0) &&
-                    kElemPad % VisCfg<T, N>::EPB == 0,
+                    kElemPad % VisCfg<T, N>::EPB == 0 && kElemPad % VisVolCfg<T, N>::EPB == 0,
                 "every tile size divides the element padding");
 
   struct BatchImpl : BatchClass {

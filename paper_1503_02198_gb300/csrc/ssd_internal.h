@@ -125,8 +125,8 @@ struct MeshDev {
   // derived constants, computed once on the host in double, with float copies
   // for the FP32 kernels (no double arithmetic or conversion per point there):
   // gamma - 1, conductivity k = mu gamma R / ((gamma - 1) Pr), R T_wall
-  double gm1, kc, RTw;
-  float gm1_f, Rgas_f, mu_f, kc_f, RTw_f, rho_inf_f, u_inf_f, v_inf_f, p_inf_f;
+  double gm1, kc, kcR, RTw;  // kcR = kc / Rgas
+  float gm1_f, Rgas_f, mu_f, kc_f, kcR_f, RTw_f, rho_inf_f, u_inf_f, v_inf_f, p_inf_f;
   int any_farfield;                     // the mesh has inlet or outlet faces
   float gamma_f;  // the same rounded to float (FP32 path)
   int viscous;

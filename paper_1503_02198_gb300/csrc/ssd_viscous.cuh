@@ -33,8 +33,8 @@ namespace ssd {
 template <typename T>
 __device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *qy, const MeshDev &md, T *F, T *G,
                                              bool conduct = true) {
-  const T gm1 = pick<T>(md.gm1, md.gm1_f), Rg = pick<T>(md.Rgas, md.Rgas_f), mu = pick<T>(md.mu, md.mu_f);
-  const T kc = conduct ? pick<T>(md.kc, md.kc_f) : T(0);
+  const T gm1 = pick<T>(md.gm1, md.gm1_f), mu = pick<T>(md.mu, md.mu_f);
+  const T kr = conduct ? pick<T>(md.kcR, md.kcR_f) : T(0);  // conductivity / R
   const T ir = T(1) / q[0];
   const T u = q[1] * ir, v = q[2] * ir;
   // velocity gradients rounded as products (mul_rn): they are summed with each
@@ -43,20 +43,21 @@ __device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *q
   const T vx = mul_rn(qx[2] - v * qx[0], ir), vy = mul_rn(qy[2] - v * qy[0], ir);
   const T ke = T(0.5) * mul_add(u, u, v, v);
   const T p = gm1 * (q[3] - ke * q[0]);
-  const T Tt = p * ir / Rg;
+  const T pr = p * ir;  // R T
   const T px = mul_rn(gm1, qx[3] - fma(u, qx[1], mul_sub(v, qx[2], ke, qx[0])));
   const T py = mul_rn(gm1, qy[3] - fma(u, qy[1], mul_sub(v, qy[2], ke, qy[0])));
-  const T Tx = (px - Rg * Tt * qx[0]) * ir / Rg, Ty = (py - Rg * Tt * qy[0]) * ir / Rg;
+  // R grad T = (grad p - R T grad rho) / rho; the heat flux takes k / R
+  const T Tx = fma(-pr, qx[0], px) * ir, Ty = fma(-pr, qy[0], py) * ir;
   const T lam = T(-2) / T(3) * mu, dv = ux + vy;
   const T txx = mul_add(T(2) * mu, ux, lam, dv), tyy = mul_add(T(2) * mu, vy, lam, dv), txy = mu * (uy + vx);
   F[0] = 0;
   F[1] = -txx;
   F[2] = -txy;
-  F[3] = -fma(u, txx, mul_add(v, txy, kc, Tx));
+  F[3] = -fma(u, txx, mul_add(v, txy, kr, Tx));
   G[0] = 0;
   G[1] = -txy;
   G[2] = -tyy;
-  G[3] = -fma(u, txy, mul_add(v, tyy, kc, Ty));
+  G[3] = -fma(u, txy, mul_add(v, tyy, kr, Ty));
 }
 
 // ---- common solution -------------------------------------------------------
@@ -379,24 +380,34 @@ __global__ void k_faces_visc(MeshDev md) {
 // Shared-memory layout of the persistent viscous volume kernel: two stages of
 // a tile's state (4 N^2 values per element), SP gradients (8 N^2: x then y)
 // and common fluxes (16 N), each one contiguous run as in global memory, so a
-// tile arrives by three 1-D bulk copies; then the two divergence arrays.
+// tile arrives by three 1-D bulk copies; then the tile's transformed fluxes at
+// the interior flux points and the interpolation / derivative weights.  One
+// thread per interior flux point of every SP line of the tile: 2 N (N - 1)
+// threads per element, so that a CTA holds few elements and many threads.
 template <typename T, int N>
 struct VisVolCfg {
-  static constexpr int EPB = VisCfg<T, N>::EPB, THREADS = VisCfg<T, N>::THREADS, NN = N * N;
+  static constexpr int EPB = N == 3 ? 16 : (N == 4 ? 8 : 4);
+  static constexpr int NN = N * N, LINES = EPB * 2 * N, THREADS = LINES * (N - 1);
   static constexpr int QE = 4 * NN * (int)sizeof(T), GE = 8 * NN * (int)sizeof(T), CE = 16 * N * (int)sizeof(T);
   static constexpr int GEE = 8 * (int)sizeof(T);  // bilinear cell record
   static constexpr int O_Q = 0, O_G = O_Q + EPB * QE, O_C = O_G + EPB * GE, O_EG = O_C + EPB * CE;
   static constexpr int O_EF = O_EG + EPB * GEE;
   static constexpr int STAGE = ((O_EF + EPB * 4) + 127) / 128 * 128;
-  static constexpr int O_RF = 2 * STAGE, O_RG = O_RF + EPB * QE;
-  static constexpr int O_BAR = ((O_RG + EPB * QE) + 15) / 16 * 16;
+  // fluxes [EPB][2 directions][N lines][LS]: a line's N - 1 interior points,
+  // 4 values each; the odd line stride puts neighbouring lines in different banks
+  static constexpr int LS = 4 * (N - 1) + 1;
+  static constexpr int O_FL = 2 * STAGE;
+  static constexpr int O_W = O_FL + (EPB * 2 * N * LS * (int)sizeof(T) + 15) / 16 * 16;  // Hf, then Dm
+  static constexpr int O_BAR = (O_W + 2 * N * (N + 1) * (int)sizeof(T) + 15) / 16 * 16;
   static constexpr int SMEM = O_BAR + 2 * 8;
   static_assert(QE % 16 == 0 && GE % 16 == 0 && CE % 16 == 0, "bulk-copy sizes and alignment");
-  static_assert(SMEM <= 227 * 1024, "dynamic shared memory of one CTA");
-  // resident CTAs per SM the register budget is set for: the smaller of the
-  // warp target of VisCfg and what the shared memory admits
+  static_assert(SMEM <= 227 * 1024 && THREADS <= 1024, "one CTA");
+  // resident CTAs per SM the register budget is set for: about 24 warps, or
+  // what the shared memory admits
+  static constexpr int WARPS = (THREADS + 31) / 32;
+  static constexpr int BY_WARPS = 24 / WARPS > 0 ? 24 / WARPS : 1;
   static constexpr int BY_SMEM = 228 * 1024 / (SMEM + 1024);
-  static constexpr int MINB = VisCfg<T, N>::MINB < BY_SMEM ? VisCfg<T, N>::MINB : (BY_SMEM > 0 ? BY_SMEM : 1);
+  static constexpr int MINB = BY_WARPS < BY_SMEM ? BY_WARPS : (BY_SMEM > 0 ? BY_SMEM : 1);
 };
 
 // Inviscid + viscous fluxes at the interior FPs with the stored SP gradients,
@@ -413,8 +424,8 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
   constexpr bool FF = std::is_same<T, float>::value;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bar = (uint64_t *)(smem + C::O_BAR);
-  T(*sRF)[4][NN] = (T(*)[4][NN])(smem + C::O_RF);
-  T(*sRG)[4][NN] = (T(*)[4][NN])(smem + C::O_RG);
+  T *sFl = (T *)(smem + C::O_FL);
+  T *sHf = (T *)(smem + C::O_W), *sDm = sHf + (N + 1) * N;
   const VolBasis<T, N> &B = cVB<T, N>;
   // the state, the SP gradients that k_grad_trace formed from it in this
   // stage, and the common fluxes of tile tl into stage st
@@ -443,11 +454,20 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
+  // the interpolation and derivative weights, read per thread at different points
+  for (int k = threadIdx.x; k < (N + 1) * N; k += NT) {
+    sHf[k] = B.Hf[k];
+    sDm[k] = B.Dm[k];
+  }
   __syncthreads();
   int item = blockIdx.x;
   if (threadIdx.x == 0 && item < nitems) issue(item, 0);
-  const int le = threadIdx.x / (2 * N);
-  const int r = threadIdx.x - le * 2 * N;
+  // phase-1 thread: interior flux point fi of SP line m in direction d of
+  // tile element le; the threads with fi = 1 also take the line's traces
+  const int fi = 1 + (int)threadIdx.x / C::LINES;
+  const int t1 = (int)threadIdx.x - (fi - 1) * C::LINES;
+  const int le = t1 / (2 * N);
+  const int r = t1 - le * 2 * N;
   const int d = r / N, m = r - d * N;
   bool bad = false;
   int it = 0;
@@ -488,65 +508,62 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     const int *sEF = (const int *)(sb + C::O_EF);
     const int e0 = tile * EPB;
     const int ne = min(EPB, md.E - e0);
-    // ---- phase 1: one thread per SP line ----
+    // ---- phase 1: one thread per interior flux point: Q and its gradients
+    // interpolated to the point (Eq. Qt), the inviscid ALE flux and the
+    // viscous flux (Sec. 2.1) transformed with the point's metric vector,
+    // into the tile's flux array ----
     if (le < ne) {
       ElemGeo<T, N, OTF> G;
       G.load_rec(md, e0 + le, sEF[le], sEG + le * 8, zt);
-      T acc[4][N];
+      const T *h = sHf + fi * N;
+      T qf[4], g8[8];
 #pragma unroll
-      for (int k = 0; k < N; ++k)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v][k] = 0;
-#pragma unroll
-      for (int i = 0; i <= N; ++i) {
-        T f[4];
-        if (i == 0 || i == N) {
-          const int face = d == 0 ? (i == 0 ? 3 : 1) : (i == 0 ? 0 : 2);
-#pragma unroll
-          for (int v = 0; v < 4; ++v) f[v] = sCF[le][(face * 4 + v) * N + m];
-        } else {
-          T qf[4], g8[8];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            T a = 0, bx = 0, by = 0;
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-              const int sp = d == 0 ? m * N + k : k * N + m;
-              const T h = B.Hf[i * N + k];
-              a += sQ[le][v][sp] * h;
-              bx += sG[le][v][sp] * h;
-              by += sG[le][4 + v][sp] * h;
-            }
-            qf[v] = a;
-            g8[v] = bx;
-            g8[4 + v] = by;
-          }
-          T vx, vy, vg;
-          if (d == 0) G.xi_fp(i, m, vx, vy, vg);
-          else G.eta_fp(m, i, vx, vy, vg);
-          const T p = pressure_of(qf, gm1);
-          normal_flux(qf, p, vx, vy, vg, f);
-          T Fv[4], Gv[4];
-          viscous_flux(qf, g8, g8 + 4, md, Fv, Gv);
-#pragma unroll
-          for (int v = 0; v < 4; ++v) f[v] = fma(vx, Fv[v], fma(vy, Gv[v], f[v]));
-        }
+      for (int v = 0; v < 4; ++v) {
+        T a = 0, bx = 0, by = 0;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
-          const T w = B.Dm[k * (N + 1) + i];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[v][k] += w * f[v];
+          const int sp = d == 0 ? m * N + k : k * N + m;
+          a = fma(sQ[le][v][sp], h[k], a);
+          bx = fma(sG[le][v][sp], h[k], bx);
+          by = fma(sG[le][4 + v][sp], h[k], by);
         }
+        qf[v] = a;
+        g8[v] = bx;
+        g8[4 + v] = by;
       }
+      T vx, vy, vg;
+      if (d == 0) G.xi_fp(fi, m, vx, vy, vg);
+      else G.eta_fp(m, fi, vx, vy, vg);
+      const T p = pressure_of(qf, gm1);
+      T f[4], Fv[4], Gv[4];
+      normal_flux(qf, p, vx, vy, vg, f);
+      viscous_flux(qf, g8, g8 + 4, md, Fv, Gv);
+      T *o = sFl + ((le * 2 + d) * N + m) * C::LS + (fi - 1) * 4;
 #pragma unroll
-      for (int k = 0; k < N; ++k)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          if (d == 0) sRF[le][v][m * N + k] = acc[v][k];
-          else sRG[le][v][k * N + m] = acc[v][k];
-        }
+      for (int v = 0; v < 4; ++v) o[v] = fma(vx, Fv[v], fma(vy, Gv[v], f[v]));
     }
     __syncthreads();
+    // (RF + RG)[v] at SP sp = (i, j) of element l2: each direction's
+    // divergence over its line's flux points 0..N in order (Eqs. Ft, Gt), the
+    // end points from the common fluxes
+    auto divergence = [&](int l2, int sp, T *dsum) {
+      const int i = sp % N, j = sp / N;
+      const T *fx = sFl + ((l2 * 2 + 0) * N + j) * C::LS, *fe = sFl + ((l2 * 2 + 1) * N + i) * C::LS;
+      const T *wx = sDm + i * (N + 1), *we = sDm + j * (N + 1);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        T a = mul_rn(wx[0], sCF[l2][(3 * 4 + v) * N + j]);
+        T b = mul_rn(we[0], sCF[l2][(0 * 4 + v) * N + i]);
+#pragma unroll
+        for (int l = 1; l < N; ++l) {
+          a = fma(wx[l], fx[(l - 1) * 4 + v], a);
+          b = fma(we[l], fe[(l - 1) * 4 + v], b);
+        }
+        a = fma(wx[N], sCF[l2][(1 * 4 + v) * N + j], a);
+        b = fma(we[N], sCF[l2][(2 * 4 + v) * N + i], b);
+        dsum[v] = a + b;
+      }
+    };
     // ---- phase 2: dQ/dt at the SPs and the Runge-Kutta stage ----
     if constexpr (MODE == MODE_RK && FF) {
       // FP32: the base state and the lo planes of an SP come from global
@@ -571,11 +588,13 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
         const int l2 = idx / NN, sp = idx - l2 * NN;
         const T iJ = ElemGeo<T, N, OTF>::inv_jac_t0(md, sEF[l2], sEG + l2 * 8, sp % N, sp / N);
         const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
+        T dsum[4];
+        divergence(l2, sp, dsum);
         float hv[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const size_t ii = gi + v * NN;
-          const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+          const float R = -(float)(dsum[v] * iJ);
           const float h = (float)sQ[l2][v][sp];
           float inc = __fmul_rn((float)rk.bdt, R);
           if constexpr (LO) {
@@ -614,15 +633,17 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
       const int l2 = idx / NN, sp = idx - l2 * NN;
       const T iJ = ElemGeo<T, N, OTF>::inv_jac_t0(md, sEF[l2], sEG + l2 * 8, sp % N, sp / N);
       const size_t gi = ((size_t)(e0 + l2) * 4) * NN + sp;
+      T dsum[4];
+      divergence(l2, sp, dsum);
       if (MODE == MODE_RESIDUAL) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+        for (int v = 0; v < 4; ++v) Rout[gi + v * NN] = -(double)(dsum[v] * iJ);
       } else if (!FF) {
         double qn[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const size_t ii = gi + v * NN;
-          const double R = -(double)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+          const double R = -(double)(dsum[v] * iJ);
           const double qk = (double)sQ[l2][v][sp];
           double inc = __dmul_rn((double)rk.bdt, R);
           if (has_base) inc = fma((double)rk.a0, ((const double *)base.hi)[ii] - qk, inc);
@@ -642,7 +663,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const size_t ii = gi + v * NN;
-          const float R = -(float)((sRF[l2][v][sp] + sRG[l2][v][sp]) * iJ);
+          const float R = -(float)(dsum[v] * iJ);
           const float h = (float)sQ[l2][v][sp];
           float inc = __fmul_rn((float)rk.bdt, R);
           if constexpr (LO) {
@@ -676,7 +697,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     if (MODE == MODE_RK) {
       __syncthreads();
       // ---- phase 3: face traces of the new state, one thread per SP line ----
-      if (le < ne) {
+      if (fi == 1 && le < ne) {
         T *tr = (T *)md.TR + (size_t)(e0 + le) * 16 * N;
         const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
 #pragma unroll
