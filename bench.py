@@ -97,12 +97,13 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch of the FP32 volume kernel on this
 # workload (mean of the three stage launches of one step), from one ncu
-# capture of dram__bytes_read.sum + dram__bytes_write.sum; valid only for the
+# capture of dram__bytes_read.sum + dram__bytes_write.sum (the capture and its
+# command: profiles/k_volume_fp32_rotor_n6.md); valid only for the
 # kernel source it was taken on: SHA-256 of the engine text that k_volume is
 # built from (the ElemGeo metrics and VolCfg through the end of k_volume);
 # otherwise null.
-PROFILED_TRAFFIC = {"bytes": (389.06e6 + 328.52e6 + 673.47e6 + 331.29e6 + 673.47e6 + 329.67e6) / 3,
-                    "kernel_sha256": "0ca2e437d4cfb2bcce0666b0130d3e18685380c94531e4392a21f1c5248948b6"}
+PROFILED_TRAFFIC = {"bytes": (389.10e6 + 328.65e6 + 673.43e6 + 330.93e6 + 673.55e6 + 329.78e6) / 3,
+                    "kernel_sha256": "849cf856f5f1d69f8f0edbee3b565f59ac0fa61648e5507922ea3b9cbaf0e4d7"}
 
 
 def volume_kernel_source():
