@@ -158,11 +158,26 @@ __device__ __forceinline__ T pick(double d, float f) {
   else return (T)d;
 }
 
-// 1 / x: one correctly rounded reciprocal on the FP32 path, a division in FP64
+// 1 / x in FP64 by Newton's iteration for the reciprocal, r <- r + r (1 - x r)
+// (each step squares the relative error), started from the hardware's
+// approximate reciprocal (rcp.approx.ftz.f64); two steps bring the seed's
+// error below double round-off, leaving at most an ulp or so against the
+// correctly rounded 1 / x.  For normal, finite, non-zero x (densities and
+// Jacobians here); the FP64 pipe then spends four FMAs instead of a division.
+__device__ __forceinline__ double recip_newton(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
+// 1 / x: one correctly rounded reciprocal on the FP32 path, Newton's
+// iteration in FP64
 template <typename T>
 __device__ __forceinline__ T recip(T x) {
   if constexpr (std::is_same<T, float>::value) return __frcp_rn(x);
-  else return T(1) / x;
+  else return recip_newton(x);
 }
 
 // face f of an element: sign sigma_f with F~_end = sigma_f |S| F.n_out
@@ -545,33 +560,46 @@ struct ElemGeo {
 // physics (Sec. 2)
 // ---------------------------------------------------------------------------
 
+// pressure from the conservative state with ir = 1 / rho at hand
+template <typename T>
+__device__ __forceinline__ T pressure_ir(const T *q, T ir, T gm1) {
+  return gm1 * fma(-(T(0.5) * mul_add(q[1], q[1], q[2], q[2])), ir, q[3]);
+}
+
 template <typename T>
 __device__ __forceinline__ T pressure_of(const T *q, T gm1) {
-  return gm1 * (q[3] - T(0.5) * mul_add(q[1], q[1], q[2], q[2]) / q[0]);
+  return pressure_ir(q, recip(q[0]), gm1);
 }
 
 // normal ALE inviscid flux through a (not necessarily unit) vector (nx, ny):
-// (F - u_g Q, G - v_g Q) . n  with vgn = V_g . n
+// (F - u_g Q, G - v_g Q) . n  with vgn = V_g . n, ir = 1 / rho
 template <typename T>
-__device__ __forceinline__ void normal_flux(const T *q, T p, T nx, T ny, T vgn, T *f) {
-  const T un = mul_add(q[1], nx, q[2], ny) / q[0];
+__device__ __forceinline__ void normal_flux_ir(const T *q, T ir, T p, T nx, T ny, T vgn, T *f) {
+  const T un = mul_add(q[1], nx, q[2], ny) * ir;
   f[0] = mul_sub(q[0], un, vgn, q[0]);
   f[1] = fma(q[1], un, mul_sub(p, nx, vgn, q[1]));
   f[2] = fma(q[2], un, mul_sub(p, ny, vgn, q[2]));
   f[3] = mul_sub(q[3] + p, un, vgn, q[3]);
 }
 
-// Rusanov common flux (Sec. 3.1) for unit normal n from L to R
+template <typename T>
+__device__ __forceinline__ void normal_flux(const T *q, T p, T nx, T ny, T vgn, T *f) {
+  normal_flux_ir(q, recip(q[0]), p, nx, ny, vgn, f);
+}
+
+// Rusanov common flux (Sec. 3.1) for unit normal n from L to R; one
+// reciprocal density per side
 template <typename T>
 __device__ __forceinline__ void rusanov(const T *qL, const T *qR, T nx, T ny, T vgn, T gamma, T *Fn) {
   const T gm1 = gamma - T(1);
-  const T pL = pressure_of(qL, gm1), pR = pressure_of(qR, gm1);
+  const T irL = recip(qL[0]), irR = recip(qR[0]);
+  const T pL = pressure_ir(qL, irL, gm1), pR = pressure_ir(qR, irR, gm1);
   T fL[4], fR[4];
-  normal_flux(qL, pL, nx, ny, vgn, fL);
-  normal_flux(qR, pR, nx, ny, vgn, fR);
-  const T unL = mul_add(qL[1], nx, qL[2], ny) / qL[0], unR = mul_add(qR[1], nx, qR[2], ny) / qR[0];
-  const T lL = fabs(unL - vgn) + sqrt(gamma * pL / qL[0]);
-  const T lR = fabs(unR - vgn) + sqrt(gamma * pR / qR[0]);
+  normal_flux_ir(qL, irL, pL, nx, ny, vgn, fL);
+  normal_flux_ir(qR, irR, pR, nx, ny, vgn, fR);
+  const T unL = mul_add(qL[1], nx, qL[2], ny) * irL, unR = mul_add(qR[1], nx, qR[2], ny) * irR;
+  const T lL = fabs(unL - vgn) + sqrt(gamma * pL * irL);
+  const T lR = fabs(unR - vgn) + sqrt(gamma * pR * irR);
   const T lam = lL > lR ? lL : lR;
 #pragma unroll
   for (int v = 0; v < 4; ++v) Fn[v] = mul_sub(T(0.5), fL[v] + fR[v], T(0.5) * lam, qR[v] - qL[v]);
@@ -1871,7 +1899,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX, TC>::THREADS,
           qn[v] = qk + inc;
           if (va.w_out) va.w_out[gi + v * NN] = (T)mul_sub((double)va.rk.ddt, R, (double)va.rk.g, inc);
         }
-        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * mul_add(qn[1], qn[1], qn[2], qn[2]) / qn[0]);
+        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * mul_add(qn[1], qn[1], qn[2], qn[2]) * recip(qn[0]));
         bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {

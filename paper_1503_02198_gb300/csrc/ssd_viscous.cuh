@@ -35,7 +35,7 @@ __device__ __forceinline__ void viscous_flux(const T *q, const T *qx, const T *q
                                              bool conduct = true) {
   const T gm1 = pick<T>(md.gm1, md.gm1_f), mu = pick<T>(md.mu, md.mu_f);
   const T kr = conduct ? pick<T>(md.kcR, md.kcR_f) : T(0);  // conductivity / R
-  const T ir = T(1) / q[0];
+  const T ir = recip(q[0]);
   const T u = q[1] * ir, v = q[2] * ir;
   // velocity gradients rounded as products (mul_rn): they are summed with each
   // other below, where an FMA could otherwise take either one
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           qn[v] = qk + inc;
           if (w_out) w_out[ii] = (T)mul_sub((double)rk.ddt, R, (double)rk.g, inc);
         }
-        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * mul_add(qn[1], qn[1], qn[2], qn[2]) / qn[0]);
+        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * mul_add(qn[1], qn[1], qn[2], qn[2]) * recip(qn[0]));
         bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
