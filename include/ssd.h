@@ -223,6 +223,15 @@ int sd_sync(sd_handle *h);
  * faults or hangs.  on = 0 restores normal operation.  Synchronises. */
 int sd_test_wait_timeout(sd_handle *h, int on);
 
+/* Test aid for the handle's reciprocal 1/x (the density and Jacobian
+ * reciprocals of its kernels): y[i] = 1 / x[i] computed on the GPU in the
+ * handle's compute type (FP64: Newton's iteration from the hardware's
+ * approximate reciprocal; FP32: the correctly rounded reciprocal), for n host
+ * values x (normal, finite, non-zero) into host y.  Allocates and frees a
+ * device buffer of 16 n bytes; synchronises.  SD_ERR_ARG for n < 0 or null
+ * arrays with n > 0. */
+int sd_test_reciprocal(sd_handle *h, const double *x, double *y, int n);
+
 /* Physical coordinates of the solution points at time t, [E][N][N][2]. */
 int sd_sp_coords(sd_handle *h, double t, double *xy, int on_device);
 

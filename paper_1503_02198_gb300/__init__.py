@@ -103,6 +103,7 @@ def lib():
         L.sd_fma_peak.argtypes = [vp, ctypes.c_int, _c_dbl_p]
         L.sd_residual_noalloc.argtypes = [vp, vp, ctypes.c_int]
         L.sd_test_wait_timeout.argtypes = [vp, ctypes.c_int]
+        L.sd_test_reciprocal.argtypes = [vp, _c_dbl_p, _c_dbl_p, ctypes.c_int]
         L.sd_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.POINTER(sd_mesh)), _c_int_p,
                                       ctypes.POINTER(sd_params), ctypes.c_double, ctypes.POINTER(vp)]
         L.sd_batch_destroy.argtypes = [vp]
@@ -287,6 +288,14 @@ class Solver:
 
     def sd_test_wait_timeout(self, on):
         self._check(lib().sd_test_wait_timeout(self._h, int(on)))
+
+    def sd_test_reciprocal(self, x):
+        """1 / x in the handle's compute type, on the GPU (test aid)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty_like(x)
+        self._check(lib().sd_test_reciprocal(self._h, x.ctypes.data_as(_c_dbl_p), y.ctypes.data_as(_c_dbl_p),
+                                              int(x.size)))
+        return y
 
     def sd_sp_coords(self, t=0.0, out=None):
         if out is None:

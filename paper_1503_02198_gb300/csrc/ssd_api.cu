@@ -1057,6 +1057,21 @@ int sd_sync(sd_handle *h) {
   return SD_OK;
 }
 
+int sd_test_reciprocal(sd_handle *h, const double *x, double *y, int n) {
+  if (!h || n < 0 || (n > 0 && (!x || !y))) return fail(h, SD_ERR_ARG, "sd_test_reciprocal: bad arguments");
+  if (n == 0) return SD_OK;
+  double *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(double) * 2 * (size_t)n);
+  if (!e) e = cudaMemcpyAsync(d, x, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream);
+  if (!e) h->eng->reciprocal(d, d + n, n, h->stream);
+  if (!e) e = cudaGetLastError();
+  if (!e) e = cudaMemcpyAsync(y, d + n, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  if (d) cudaFree(d);
+  if (e) return cuda_fail(h, e, "sd_test_reciprocal");
+  return SD_OK;
+}
+
 int sd_test_wait_timeout(sd_handle *h, int on) {
   if (!h) return SD_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(h->stream);

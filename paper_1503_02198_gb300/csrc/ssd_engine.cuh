@@ -373,6 +373,13 @@ __global__ void k_bgeo(MeshDev md, const double *__restrict__ Xs, double *bxy) {
 }
 
 // physical SP coordinates at time t, [E][N][N][2]
+// y = recip(x) in the compute type, one thread per value (test of recip)
+template <typename T>
+__global__ void k_reciprocal(const double *x, double *y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (double)recip<T>((T)x[i]);
+}
+
 template <int N>
 __global__ void k_spxy(MeshDev md, const double *__restrict__ Xs, double t, double *out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2412,6 +2419,10 @@ struct EngineImpl : Engine {
 
   void sp_coords(const MeshDev &md, double t, double *xy, cudaStream_t s) override {
     k_spxy<N><<<(md.E + 127) / 128, 128, 0, s>>>(md, dXs, t, xy);
+  }
+
+  void reciprocal(const double *x, double *y, int n, cudaStream_t s) override {
+    if (n > 0) k_reciprocal<T><<<(n + 255) / 256, 256, 0, s>>>(x, y, n);
   }
 
   // ---- batched form ----

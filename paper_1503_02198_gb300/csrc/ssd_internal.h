@@ -244,6 +244,8 @@ struct Engine {
   virtual void *W() const = 0;
   virtual void advance(const MeshDev &md, double dt, cudaStream_t s) = 0;
   virtual void sp_coords(const MeshDev &md, double t, double *xy, cudaStream_t s) = 0;
+  // the compute type's reciprocal (recip) of n device values, for its test
+  virtual void reciprocal(const double *x, double *y, int n, cudaStream_t s) = 0;
 
   // ---- batched form: one launch per phase for every case of a class ----
   // A class is a set of cases that share this engine's compute type and N
