@@ -102,8 +102,8 @@ class ClockSampler:
 # kernel source it was taken on: SHA-256 of the engine text that k_volume is
 # built from (the ElemGeo metrics and VolCfg through the end of k_volume);
 # otherwise null.
-PROFILED_TRAFFIC = {"bytes": (389.10e6 + 328.65e6 + 673.43e6 + 330.93e6 + 673.55e6 + 329.78e6) / 3,
-                    "kernel_sha256": "849cf856f5f1d69f8f0edbee3b565f59ac0fa61648e5507922ea3b9cbaf0e4d7"}
+PROFILED_TRAFFIC = {"bytes": (389.28e6 + 329.15e6 + 673.67e6 + 330.94e6 + 673.72e6 + 329.72e6) / 3,
+                    "kernel_sha256": "27835dd39041711c5e2caa4956736e6f276d045df4dbcf46a3aede673d6a4b0c"}
 
 
 def volume_kernel_source():

@@ -182,7 +182,7 @@ struct sd_handle {
   Engine *eng = nullptr;
   MeshDev md{};
   std::vector<void *> allocs;
-  std::vector<int> zone_v, curved_v;  // per element: zone, has an arc edge
+  std::vector<int> zone_v, curved_v, iface_v;  // per element: zone, has an arc edge, has an interface face
   double *stage = nullptr;    // FP64 staging of host states (FP32 path)
   double *scratch = nullptr;  // device copy of a host residual
   bool traces_valid = false;
@@ -476,10 +476,17 @@ int build_mesh(sd_handle *h, const sd_mesh *m, double omega1) {
     h->zone_v.push_back(m->elem_zone[e]);
     h->curved_v.push_back(bits != 0);
   }
+  // each element face's interface face (k of the L list, nL + k of the R list)
+  std::vector<int> efi(4 * (size_t)E, -1);
+  for (size_t k = 0; k < L.face.size(); ++k) efi[L.face[k].x] = (int)k;
+  for (size_t k = 0; k < R.face.size(); ++k) efi[R.face[k].x] = (int)(L.face.size() + k);
+  h->iface_v.assign(E, 0);
+  for (int ef = 0; ef < 4 * E; ++ef)
+    if (efi[ef] >= 0) h->iface_v[ef / 4] = 1;
   cudaError_t ce;
   int4 *dfaces, *dbfaces, *dL, *dR;
   double *dcorn, *dLa, *dLw, *dLS, *dRa, *dRw, *dRS, *dLiW, *dRiW, *dcub = nullptr, *dzpar, *dLal, *dRal;
-  int *darcs, *dzone, *dframe, *dzoff, *difz;
+  int *darcs, *dzone, *dframe, *dzoff, *difz, *defi;
   if ((ce = upload(h, &dfaces, faces.data(), faces.size())) || (ce = upload(h, &dbfaces, bfaces.data(), bfaces.size())) ||
       (ce = upload(h, &dL, L.face.data(), L.face.size())) || (ce = upload(h, &dR, R.face.data(), R.face.size())) ||
       (ce = upload(h, &dLa, L.a.data(), L.a.size())) || (ce = upload(h, &dLw, L.w.data(), L.w.size())) ||
@@ -490,7 +497,7 @@ int build_mesh(sd_handle *h, const sd_mesh *m, double omega1) {
       (ce = upload(h, &dcorn, corners.data(), corners.size())) || (ce = upload(h, &darcs, arcs.data(), arcs.size())) ||
       (ce = upload(h, &dzone, m->elem_zone, (size_t)E)) || (ce = upload(h, &dframe, frame.data(), frame.size())) ||
       (ce = upload(h, &dzpar, zpar.data(), zpar.size())) || (ce = upload(h, &dzoff, zoff.data(), zoff.size())) ||
-      (ce = upload(h, &difz, ifz.data(), ifz.size())) ||
+      (ce = upload(h, &difz, ifz.data(), ifz.size())) || (ce = upload(h, &defi, efi.data(), efi.size())) ||
       (any_cubic && (ce = upload(h, &dcub, cubic.data(), cubic.size()))))
     return cuda_fail(h, ce, "mesh upload");
   md.cubic = dcub;
@@ -516,6 +523,7 @@ int build_mesh(sd_handle *h, const sd_mesh *m, double omega1) {
   md.zpar = dzpar;
   md.zoff = dzoff;
   md.ifz = difz;
+  md.efi = defi;
   h->zpar = zpar;
   // (host vectors are released when this function returns: wait for the copies)
   if ((ce = cudaStreamSynchronize(h->stream))) return cuda_fail(h, ce, "mesh upload");
@@ -540,6 +548,7 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
       tab_elem.push_back((int)k);
       f |= (int)tab_elem.size() << kZoneBits;
     }
+    if (h->iface_v[k]) f |= kIfaceBit;
     eflag[k] = f;
   }
   int *deflag, *dtab;

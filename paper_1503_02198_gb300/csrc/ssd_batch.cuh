@@ -5,8 +5,9 @@
 //
 // A class's work for one stage is a list of items numbered across its cases,
 // with per-case prefix sums: face-pass blocks (the mortar-flux blocks of a
-// case first, then its face-point blocks), gather points, and volume /
-// gradient tiles (the persistent kernels walk them through CaseList).  Each
+// case first, then its face-point blocks) and volume / gradient tiles (the
+// persistent kernels walk them through CaseList and gather the mortar
+// contributions of their interface faces themselves).  Each
 // case's stage view of the mesh (its stage clock and mortar table) and its
 // volume arguments sit in device arrays, so a changed step size is a copy
 // into those arrays, not a new graph.
@@ -19,7 +20,6 @@ struct BatchWork {
   const MeshDev *md;    // [n] each case's view of the stage
   const int *off_fblk;  // [n + 1] first block of each case in the fused face pass
   const int *nmb;       // [n] mortar-flux blocks of each case (its first blocks)
-  const int *off_gpt;   // [n + 1] first gather point of each case
   int n;
 };
 
@@ -61,19 +61,6 @@ __global__ void __launch_bounds__(FB) k_batch_faces(BatchWork w) {
     else if (MMODE == MORTAR_AVG_Q) k_bface_cq_point<T, N, OTF>(md, tb);
     else k_bface_visc_point<T, N, OTF>(md, tb);
   }
-}
-
-// the mortar gather of every case of a class: one thread per interface point
-template <typename T, int N, int GMODE>
-__global__ void k_batch_gather(BatchWork w, int total) {
-  pdl_enter();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const int c = case_of(w.off_gpt, w.n, t);
-  const MeshDev &md = w.md[c];
-  const int lt = t - __ldg(w.off_gpt + c);
-  if (!batch_check(md, lt >= 0 && lt < (md.nL + md.nR) * N)) return;
-  gather_point<T, N, GMODE>(md, lt);
 }
 
 // Stage clocks and mortar tables of every stage of every case of a batch:

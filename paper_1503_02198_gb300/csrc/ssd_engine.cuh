@@ -24,9 +24,9 @@
 //   k_mortar_flux   per mortar: L2 projection of both sides' face traces
 //                   (Eq. prjQ2), Rusanov at the mortar SPs, back-projection
 //                   weights of the common flux (Eq. prjF2)
-//   k_mortar_gather per interface face point: deterministic sum over the
-//                   face's mortars -> common flux of the face
-//   k_volume        per element: SP -> FP interpolation (Eq. Qt), transformed
+//   k_volume        per element: the common fluxes of its interface faces as
+//                   the deterministic sum over each face's mortars (the
+//                   gather), SP -> FP interpolation (Eq. Qt), transformed
 //                   ALE fluxes (Eq. transform_relation), common fluxes at the
 //                   end FPs, divergence (Eqs. Ft, Gt), RK update and the face
 //                   traces of the new state
@@ -84,7 +84,7 @@ __device__ __forceinline__ bool ssd_check(const MeshDev &md, bool ok) {
 __device__ __forceinline__ bool ssd_check(const MeshDev &, bool) { return true; }
 #endif
 // The same check in every build, for the work lists of the batched form (a
-// work item, face block or gather point outside its case is reported and its
+// work item or face block outside its case is reported and its
 // memory accesses skipped).
 __device__ __forceinline__ bool batch_check(const MeshDev &md, bool ok) {
   if (!ok) atomicOr(&md.clk->flags, 8);
@@ -428,7 +428,7 @@ struct ElemGeo {
     c = zt[z];
     s = zt[kZT + z];
     om = zt[2 * kZT + z];
-    int ti = (f >> kZoneBits) - 1;
+    int ti = ((f & ~kIfaceBit) >> kZoneBits) - 1;
     if (!ssd_check(md, ti < md.nTab && (OTF || ti >= 0))) ti = 0;
     if (OTF && ti < 0) {
       tab = nullptr;
@@ -533,7 +533,7 @@ struct ElemGeo {
   // 1 / |J| at SP (X_i, X_j) straight from the cell flag and the unrotated
   // record or table (|J| does not change under the rotation)
   static __device__ __forceinline__ T inv_jac_t0(const MeshDev &md, int f, const T *r, int i, int j) {
-    const int ti = (f >> kZoneBits) - 1;
+    const int ti = ((f & ~kIfaceBit) >> kZoneBits) - 1;
     if (OTF && ti < 0) {
       const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
       const T xx = r[2] + eta * r[6], yx = r[3] + eta * r[7], xe = r[4] + xi * r[6], ye = r[5] + xi * r[7];
@@ -1204,9 +1204,14 @@ __global__ void __launch_bounds__(MortCfg<N>::THREADS) k_mortar_flux(MeshDev md)
 // for R).  One thread per (side, face, point).
 enum { GATHER_FLUX = 0, GATHER_Q = 1 };
 
+// The common value at point p of interface face fq (L faces first, then R):
+// the sum of the contributions of the face's mortars, in their
+// counter-clockwise order -- the common solution (GATHER_Q) or, scaled by
+// sigma_f |S| and the side's sign, the common flux (GATHER_FLUX).  Also gives
+// the element face ef and its point j.  False for a bad table entry (debug
+// build).
 template <typename T, int N, int GMODE>
-__device__ __forceinline__ void gather_point(const MeshDev &md, int t) {
-  const int fq = t / N, p = t - fq * N;
+__device__ __forceinline__ bool gather_sum(const MeshDev &md, int fq, int p, T *out, int &ef, int &j) {
   const int sd = fq >= md.nL;
   const int k = sd ? fq - md.nL : fq;
   const int start = sd ? md.Rstart[k] : md.Lstart[k];
@@ -1217,7 +1222,7 @@ __device__ __forceinline__ void gather_point(const MeshDev &md, int t) {
   const int ii = md.ifz[fq];
   const int m0 = md.zoff[ii] + md.zoff[kZT + ii], m1 = md.zoff[ii + 1] + md.zoff[kZT + ii + 1];
   if (!ssd_check(md, start >= m0 && start < m1 && cnt >= 1 && cnt <= m1 - m0 && fc.x >= 0 && fc.x < 4 * md.E))
-    return;
+    return false;
   T acc[4] = {0, 0, 0, 0};
   int mi = start;
   for (int c = 0; c < cnt; ++c) {
@@ -1225,30 +1230,57 @@ __device__ __forceinline__ void gather_point(const MeshDev &md, int t) {
     for (int v = 0; v < 4; ++v) acc[v] += cb[((size_t)mi * 4 + v) * N + p];
     mi = mi + 1 == m1 ? m0 : mi + 1;
   }
-  const int ef = fc.x, f = ef & 3;
-  const int j = fc.y ? N - 1 - p : p;
+  ef = fc.x;
+  j = fc.y ? N - 1 - p : p;
   if (GMODE == GATHER_Q) {
-    T *CQ = (T *)md.CQ;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) CQ[((size_t)ef * 4 + v) * N + j] = acc[v];
-    return;
+    for (int v = 0; v < 4; ++v) out[v] = acc[v];
+    return true;
   }
   const T S = (T)(sd ? md.RS[k] : md.LS[k]);
-  const T sc = (T)face_sigma(f) * S * (sd ? T(-1) : T(1));
-  T *CF = (T *)md.CF;
+  const T sc = (T)face_sigma(ef & 3) * S * (sd ? T(-1) : T(1));
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const size_t i = ((size_t)ef * 4 + v) * N + j;
-    CF[i] = sc * acc[v];
-  }
+  for (int v = 0; v < 4; ++v) out[v] = sc * acc[v];
+  return true;
 }
 
+// The gather inside the kernel that reads its result: the interface faces of
+// the tile elements e0 + [0, ne) get their common values (per element 16 N
+// values [face][variable][point], element stride `stride`) in the tile's
+// shared copy; with `global` also in CQ / CF.  Returns whether the tile had
+// an interface cell (then the caller synchronises before reading the tile).
 template <typename T, int N, int GMODE>
-__global__ void k_mortar_gather(MeshDev md) {
-  pdl_enter();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (md.nL + md.nR) * N) gather_point<T, N, GMODE>(md, t);
+__device__ __forceinline__ bool gather_tile(const MeshDev &md, int e0, int ne, const int *sEF, T *tile, int stride,
+                                            bool global, int nthreads) {
+  // the tile's flags in 16-byte groups (a tile's flags are copied in whole
+  // groups of 4, the cells past the mesh's last carrying 0)
+  int any = 0;
+  for (int q = 0; q < (ne + 3) / 4; ++q) {
+    const int4 f4 = reinterpret_cast<const int4 *>(sEF)[q];
+    any |= f4.x | f4.y | f4.z | f4.w;
+  }
+  if (!(any & kIfaceBit)) return false;
+  for (int u = threadIdx.x; u < ne * 4 * N; u += nthreads) {
+    const int le = u / (4 * N), r = u - le * 4 * N, f = r / N, jj = r - f * N;
+    if (!(sEF[le] & kIfaceBit)) continue;
+    const int fq = md.efi[4 * (e0 + le) + f];
+    if (fq < 0) continue;
+    const int k = fq >= md.nL ? fq - md.nL : fq;
+    const int rev = (fq >= md.nL ? md.Rface[k] : md.Lface[k]).y;
+    T val[4];
+    int ef, j;
+    if (!gather_sum<T, N, GMODE>(md, fq, rev ? N - 1 - jj : jj, val, ef, j)) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) tile[le * stride + (f * 4 + v) * N + jj] = val[v];
+    if (global) {
+      T *dst = (T *)(GMODE == GATHER_Q ? md.CQ : md.CF);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dst[((size_t)ef * 4 + v) * N + j] = val[v];
+    }
+  }
+  return true;
 }
+
 
 // ---------------------------------------------------------------------------
 // state conversion and traces
@@ -1736,6 +1768,9 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX, TC>::THREADS,
     const T *sEG = (const T *)(sb + C::O_EG);
     const int e0 = tile * EPB;
     const int ne = min(EPB, md.E - e0);
+    // the tile's interface faces: their common fluxes from the mortar
+    // contributions (the gather of Eq. prjF2 over each face's mortars)
+    if (gather_tile<T, N, GATHER_FLUX>(md, e0, ne, sEF, (T *)(sb + C::O_CF), C::SC, false, NT)) __syncthreads();
     // ---- phase 1: one thread per SP line: threads [0, EPB N) take the xi
     // lines, the rest the eta lines, so that most warps run one direction ----
     const int d = threadIdx.x >= EPB * N ? 1 : 0;
@@ -2275,16 +2310,17 @@ struct EngineImpl : Engine {
     launch_pdl(k_clock_merge_stages, dim3(sm.n, md.nI), 1024, merge_smem, s, md, sm, dt);
   }
 
-  template <int MMODE, int GMODE>
-  void mortar_pass(const MeshDev &md, cudaStream_t s, bool flux = true) {
+  // the mortar flux as its own launch; the gather of its contributions into
+  // each interface face is done by the kernel that reads the result
+  // (gather_tile in k_volume, k_volume_visc, k_grad_trace)
+  template <int MMODE>
+  void mortar_flux(const MeshDev &md, cudaStream_t s) {
     constexpr int MPB = MortCfg<N>::MPB;
-    if (flux) launch_pdl(k_mortar_flux<T, N, MMODE>, (md.nM + MPB - 1) / MPB, MortCfg<N>::THREADS, 0, s, md);
-    const int n = (md.nL + md.nR) * N;
-    launch_pdl(k_mortar_gather<T, N, GMODE>, (n + 127) / 128, 128, 0, s, md);
+    launch_pdl(k_mortar_flux<T, N, MMODE>, (md.nM + MPB - 1) / MPB, MortCfg<N>::THREADS, 0, s, md);
   }
 
   // a face pass fused with the mortar flux of the same pass (meshes with an
-  // interface); the gather follows as its own launch
+  // interface)
   template <int MMODE>
   void fused_pass(const MeshDev &md, cudaStream_t s) {
     constexpr int MPB = MortCfg<N>::MPB;
@@ -2305,10 +2341,9 @@ struct EngineImpl : Engine {
     // common solution, gradient traces, then common inviscid + viscous fluxes
     if (fused(md)) {
       fused_pass<MORTAR_AVG_Q>(md, s);
-      mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s, false);
     } else {
       if (np > 0) launch_pdl(k_faces_cq<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
-      if (md.nL > 0) mortar_pass<MORTAR_AVG_Q, GATHER_Q>(md, s);
+      if (md.nL > 0) mortar_flux<MORTAR_AVG_Q>(md, s);
     }
     using Gc = GradCfg<T, N>;
     const int ntg = (md.E + Gc::EPB - 1) / Gc::EPB;
@@ -2320,11 +2355,12 @@ struct EngineImpl : Engine {
     else if (np > 0) launch_pdl(k_faces_visc<T, N, OTF>, (np + 255) / 256, 256, 0, s, md);
   }
 
-  // the gather (and, when not fused into the face pass, the mortar flux)
+  // the mortar flux when it is not fused into the face pass (the gather is
+  // done by the volume kernel)
   void mortars(const MeshDev &md, cudaStream_t s) override {
-    if (md.nL > 0) {
-      if (md.viscous) mortar_pass<MORTAR_RUSANOV_FV, GATHER_FLUX>(md, s, !fused(md));
-      else mortar_pass<MORTAR_RUSANOV, GATHER_FLUX>(md, s, !fused(md));
+    if (md.nL > 0 && !fused(md)) {
+      if (md.viscous) mortar_flux<MORTAR_RUSANOV_FV>(md, s);
+      else mortar_flux<MORTAR_RUSANOV>(md, s);
     }
   }
   void set_fusion(bool on) override { fuse_faces_mortar = on; }
@@ -2440,8 +2476,8 @@ struct EngineImpl : Engine {
     std::vector<char> aux;                   // per stage: the stage carries an increment in (w_in)
     MeshDev *md = nullptr;                   // [nstages][n] stage views
     VolArgs<T> *va = nullptr;                // [nstages][n]
-    int *off_tile = nullptr, *off_gtile = nullptr, *off_fblk = nullptr, *nmb = nullptr, *off_gpt = nullptr;
-    int ntile = 0, ngtile = 0, nfblk = 0, ngpt = 0;
+    int *off_tile = nullptr, *off_gtile = nullptr, *off_fblk = nullptr, *nmb = nullptr;
+    int ntile = 0, ngtile = 0, nfblk = 0;
     int epb_alt = 0;       // 0: default tile, 1: the smaller tile
     int face_block = 256;  // face-pass block size
     int vol_ctas = 0;      // volume (or viscous volume) CTAs per SM
@@ -2478,24 +2514,21 @@ struct EngineImpl : Engine {
     const int epb = b.epb_alt ? kEpbAlt : vol_epb_default<N>();
     const int vepb = b.viscous ? VisVolCfg<T, N>::EPB : epb;
     constexpr int MPB = MortCfg<N>::MPB;
-    std::vector<int> ot(b.n + 1, 0), og(b.n + 1, 0), of(b.n + 1, 0), nm(b.n, 0), op(b.n + 1, 0);
+    std::vector<int> ot(b.n + 1, 0), og(b.n + 1, 0), of(b.n + 1, 0), nm(b.n, 0);
     for (int c = 0; c < b.n; ++c) {
       ot[c + 1] = ot[c] + (b.E[c] + vepb - 1) / vepb;
       og[c + 1] = og[c] + (b.E[c] + GradCfg<T, N>::EPB - 1) / GradCfg<T, N>::EPB;
       nm[c] = (b.nM[c] + MPB - 1) / MPB;
       of[c + 1] = of[c] + nm[c] + ((b.nF[c] + b.nB[c]) * N + b.face_block - 1) / b.face_block;
-      op[c + 1] = op[c] + (b.nL[c] + b.nR[c]) * N;
     }
     b.ntile = ot[b.n];
     b.ngtile = og[b.n];
     b.nfblk = of[b.n];
-    b.ngpt = op[b.n];
     cudaError_t e;
     if ((e = cudaMemcpyAsync(b.off_tile, ot.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaMemcpyAsync(b.off_gtile, og.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaMemcpyAsync(b.off_fblk, of.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaMemcpyAsync(b.nmb, nm.data(), sizeof(int) * b.n, cudaMemcpyHostToDevice, s))) return e;
-    if ((e = cudaMemcpyAsync(b.off_gpt, op.data(), sizeof(int) * (b.n + 1), cudaMemcpyHostToDevice, s))) return e;
     return cudaStreamSynchronize(s);  // the host vectors go out of scope
   }
 
@@ -2543,7 +2576,6 @@ struct EngineImpl : Engine {
     if (!e) e = al((void **)&b->off_gtile, sizeof(int) * (b->n + 1));
     if (!e) e = al((void **)&b->off_fblk, sizeof(int) * (b->n + 1));
     if (!e) e = al((void **)&b->nmb, sizeof(int) * (b->n + 1));
-    if (!e) e = al((void **)&b->off_gpt, sizeof(int) * (b->n + 1));
     if (!e) e = batch_args(*b, stages, s);
     // resident CTAs per SM of the class's persistent kernels
     if (!e) e = vol_setup<MODE_RK, false, 0, List>(&b->occ[0]);
@@ -2603,11 +2635,6 @@ struct EngineImpl : Engine {
     dbg_sync(s, "batch face pass");
   }
 
-  template <int GMODE>
-  void batch_gather(const BatchImpl &b, const BatchWork &w, cudaStream_t s) {
-    if (b.ngpt > 0) launch_pdl(k_batch_gather<T, N, GMODE>, (b.ngpt + 127) / 128, 128, 0, s, w, b.ngpt);
-    dbg_sync(s, "batch gather");
-  }
 
   template <bool AUX, int EPBX>
   void batch_volume(const BatchImpl &b, const List &src, cudaStream_t s) {
@@ -2619,14 +2646,13 @@ struct EngineImpl : Engine {
 
   void batch_stage(BatchClass *bc, int k, cudaStream_t s) override {
     const BatchImpl &b = *static_cast<const BatchImpl *>(bc);
-    BatchWork w{b.md + (size_t)k * b.n, b.off_fblk, b.nmb, b.off_gpt, b.n};
+    BatchWork w{b.md + (size_t)k * b.n, b.off_fblk, b.nmb, b.n};
     List src;
     src.md = b.md + (size_t)k * b.n;
     src.a = b.va + (size_t)k * b.n;
     src.n = b.n;
     if (!b.viscous) {
       batch_face_pass<MORTAR_RUSANOV>(b, w, s);
-      batch_gather<GATHER_FLUX>(b, w, s);
       src.off = b.off_tile;
       const bool aux = b.aux[k];
       if (!b.epb_alt) {
@@ -2640,14 +2666,12 @@ struct EngineImpl : Engine {
     }
     // common solution, gradients and their traces, common fluxes, volume
     batch_face_pass<MORTAR_AVG_Q>(b, w, s);
-    batch_gather<GATHER_Q>(b, w, s);
     using G = GradCfg<T, N>;
     src.off = b.off_gtile;
     launch_pdl(k_grad_trace<T, N, OTF, List>, std::max(1, std::min(b.ngtile, std::max(1, b.occ_grad) * sms)),
                G::THREADS, G::SMEM, s, src, b.ngtile);
     dbg_sync(s, "batch gradients");
     batch_face_pass<MORTAR_RUSANOV_FV>(b, w, s);
-    batch_gather<GATHER_FLUX>(b, w, s);
     using V = VisVolCfg<T, N>;
     src.off = b.off_tile;
     launch_pdl(k_volume_visc<T, N, MODE_RK, OTF, LO, List>, std::max(1, std::min(b.ntile, b.vol_ctas * sms)),

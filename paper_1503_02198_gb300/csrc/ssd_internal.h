@@ -20,6 +20,8 @@ constexpr int kZT = kMaxZones + 1;  // per-zone table entries, zone 0 included
 constexpr int kElemPad = 48;
 // cell flag: zone in the low kZoneBits bits, (metric table index + 1) above
 constexpr int kZoneBits = 3, kZoneMask = (1 << kZoneBits) - 1;
+// and bit 30: the cell has a face on a sliding interface
+constexpr int kIfaceBit = 1 << 30;
 static_assert(kMaxZones <= kZoneMask, "zone bits");
 
 // Device-resident clock of the current stage (the rotation angles never
@@ -107,8 +109,12 @@ struct MeshDev {
   const int *frame;       // [E] frame zone
   const double *zpar;     // [kZT][4] per zone: centre x, y, omega, interface radius
   // eflag[e]: bits 0-2 = zone; (table index + 1) << kZoneBits, or 0 above
-  // them for a straight cell whose bilinear metrics are computed on the fly
+  // them for a straight cell whose bilinear metrics are computed on the fly;
+  // kIfaceBit if the cell has an interface face
   const int *eflag;
+  // [4 E] per element face ef = 4 e + f: its interface face (L faces first,
+  // then R: k or nL + k), or -1
+  const int *efi;
   int nTab;               // number of metric tables
   const int *tab_elem;    // [nTab] element of each table
   void *geo;              // T [nTab][G] metric tables (see ssd_engine.cuh)

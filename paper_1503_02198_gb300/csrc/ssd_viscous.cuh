@@ -5,8 +5,9 @@
 // Per stage, after the stage clock and mortar merge:
 //   k_faces_cq                 common solution Q_c on conforming faces (average)
 //                              and boundaries (the state on the boundary)
-//   k_mortar_flux<MORTAR_AVG_Q> + gather   Q_c on the interface: both sides
-//                              projected to the mortars, averaged, projected back
+//   k_mortar_flux<MORTAR_AVG_Q>  Q_c on the interface: both sides projected
+//                              to the mortars, averaged, projected back (summed
+//                              into each face by the gradient kernel)
 //   k_grad_trace               gradients of the conservative variables at the
 //                              SPs (derivative of the degree-N polynomial through
 //                              the FP values with Q_c at the end FPs, chain rule
@@ -15,10 +16,11 @@
 //   k_faces_visc               Rusanov + average of both sides' viscous normal
 //                              flux evaluated with Q_c (boundaries: boundary state,
 //                              interior gradient)
-//   k_mortar_flux<MORTAR_RUSANOV_FV> + gather: traces and the viscous normal
-//                              flux of both sides projected to the mortars in one
-//                              pass, Rusanov + average of the viscous fluxes,
-//                              projected back as one sum
+//   k_mortar_flux<MORTAR_RUSANOV_FV>: traces and the viscous normal flux of
+//                              both sides projected to the mortars in one pass,
+//                              Rusanov + average of the viscous fluxes, projected
+//                              back as one sum (summed into each face by the
+//                              viscous volume kernel)
 //   k_volume_visc              inviscid + viscous fluxes at interior FPs (with
 //                              the stored SP gradients), divergence, Runge-Kutta
 //                              update, traces; persistent, tiles fed by 1-D
@@ -117,11 +119,12 @@ struct VisCfg {
 };
 
 // Gradients at the SPs of a tile (thread per SP line, then per SP): on
-// return sDx / sDe hold Q_x / Q_y.  The caller synchronises before and after.
+// return sDx / sDe hold Q_x / Q_y, and gsp (the tile's rows of GSP,
+// [element][8][N^2]) the same.  The caller synchronises before and after.
 template <typename T, int N, bool OTF>
 __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne, T (*sQ)[4][N * N],
                                                T (*sCQ)[16 * N], T (*sDx)[4][N * N], T (*sDe)[4][N * N],
-                                               const T *zt, const int *sEF, const T *sEG) {
+                                               const T *zt, const int *sEF, const T *sEG, T *gsp) {
   constexpr int NN = N * N, NT = VisCfg<T, N>::THREADS;
   const VolBasis<T, N> &B = cVB<T, N>;
   const int le = threadIdx.x / (2 * N);
@@ -157,11 +160,15 @@ __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne
     G.load_rec(md, e0 + l2, sEF[l2], sEG + l2 * 8, zt);
     T xix, xiy, etx, ety;
     G.sp_grad(sp % N, sp / N, xix, xiy, etx, ety);
+    T *g = gsp + (size_t)l2 * 8 * NN + sp;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const T a = sDx[l2][v][sp], b = sDe[l2][v][sp];
-      sDx[l2][v][sp] = mul_add(xix, a, etx, b);
-      sDe[l2][v][sp] = mul_add(xiy, a, ety, b);
+      const T gx = mul_add(xix, a, etx, b), gy = mul_add(xiy, a, ety, b);
+      sDx[l2][v][sp] = gx;
+      sDe[l2][v][sp] = gy;
+      g[v * NN] = gx;
+      g[(4 + v) * NN] = gy;
     }
   }
 }
@@ -255,15 +262,12 @@ __global__ void __launch_bounds__(GradCfg<T, N>::THREADS) k_grad_trace(Src src, 
     const int *sEF = (const int *)(sb + C::O_EF);
     const int e0 = tile * EPB;
     const int ne = min(EPB, md.E - e0);
-    tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, zt, sEF, sEG);
+    // the tile's interface faces: their common solution from the mortar
+    // contributions, also into CQ for the viscous mortar pass that follows
+    if (gather_tile<T, N, GATHER_Q>(md, e0, ne, sEF, (T *)(sb + C::O_C), 16 * N, true, NT)) __syncthreads();
+    // the SP gradients, also stored for the volume kernel of this stage
+    tile_gradients<T, N, OTF>(md, e0, ne, sQ, sCQ, sDx, sDe, zt, sEF, sEG, (T *)md.GSP + (size_t)e0 * 8 * NN);
     __syncthreads();
-    // the SP gradients for the volume kernel of this stage
-    for (int i = threadIdx.x; i < ne * 4 * NN; i += NT) {
-      const int l2 = i / (4 * NN), rr = i - l2 * 4 * NN;
-      T *gs = (T *)md.GSP + (size_t)(e0 + l2) * 8 * NN;
-      gs[rr] = (&sDx[0][0][0])[i];
-      gs[4 * NN + rr] = (&sDe[0][0][0])[i];
-    }
     if (le < ne) {
       T *g = (T *)md.GTR + (size_t)(e0 + le) * 32 * N;
       const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
@@ -508,6 +512,8 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     const int *sEF = (const int *)(sb + C::O_EF);
     const int e0 = tile * EPB;
     const int ne = min(EPB, md.E - e0);
+    // the tile's interface faces: their common fluxes from the mortar contributions
+    if (gather_tile<T, N, GATHER_FLUX>(md, e0, ne, sEF, (T *)(sb + C::O_C), 16 * N, false, NT)) __syncthreads();
     // ---- phase 1: one thread per interior flux point: Q and its gradients
     // interpolated to the point (Eq. Qt), the inviscid ALE flux and the
     // viscous flux (Sec. 2.1) transformed with the point's metric vector,
