@@ -1015,6 +1015,19 @@ struct MortCfg {
 // back-projection is linear, Eq. prjF2)
 enum { MORTAR_RUSANOV = 0, MORTAR_AVG_Q = 1, MORTAR_RUSANOV_FV = 2 };
 
+// cos and sin of an angle formed in FP64 (an interface normal), evaluated in
+// the compute type: in double on the FP64 path; on the FP32 path in float from
+// the angle rounded to float (its absolute error, ~2.4e-7 over [0, 2 pi), is
+// below the FP32 form's own round-off of the fluxes the normal multiplies)
+template <typename T>
+__device__ __forceinline__ void normal_of(double ang, T &cs, T &sn) {
+  if constexpr (std::is_same<T, float>::value) {
+    sincosf((float)ang, &sn, &cs);
+  } else {
+    sincos(ang, &sn, &cs);
+  }
+}
+
 // The mortar flux of MPB mortars of block blk: thread (mortar lm < MPB, side,
 // point); threads beyond MPB * 2 N only take part in the barriers.
 template <typename T, int N, int MMODE, int MPB>
@@ -1073,9 +1086,9 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
       for (int v = 0; v < 4; ++v) q[v] = CQ[((size_t)ef * 4 + v) * N + jj];
 #pragma unroll
       for (int c = 0; c < 8; ++c) g8[c] = GT[((size_t)ef * 8 + c) * N + jj];
-      double sn, cs;
-      sincos(fa.hi + (fa.lo + B.Xs[p] * (sd ? md.Rw[fq] : md.Lw[fq])), &sn, &cs);
-      viscous_normal(q, g8, (T)cs, (T)sn, md, fn);
+      T sn, cs;
+      normal_of<T>(fa.hi + (fa.lo + B.Xs[p] * (sd ? md.Rw[fq] : md.Lw[fq])), cs, sn);
+      viscous_normal(q, g8, cs, sn, md, fn);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sQf[lm][sd][NV - 4 + v][p] = fn[v];
     }
@@ -1084,19 +1097,21 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) sQf[lm][sd][v][p] = TR[((size_t)ef * 4 + v) * N + jj];
     }
-    // Lagrange values at the mapped quadrature point x = o + s z_p
+    // Lagrange values at the mapped quadrature point x = o + s z_p: x and its
+    // distances to the SPs in FP64 (they cancel), the products in the compute
+    // type (on the FP32 path each weight is then good to a few float ulps)
     const double x = fma(s, B.zq[p], o);
-    double dif[N];
+    T dif[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) dif[k] = x - B.Xs[k];
+    for (int k = 0; k < N; ++k) dif[k] = (T)(x - B.Xs[k]);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      double h = B.cden[i];
+      T h = (T)B.cden[i];
 #pragma unroll
       for (int k = 0; k < N; ++k)
         if (k != i) h *= dif[k];
-      sH[lm][sd][p][i] = (T)h;
-      sWH[lm][sd][p][i] = (T)(B.wq[p] * h);
+      sH[lm][sd][p][i] = h;
+      sWH[lm][sd][p][i] = (T)B.wq[p] * h;
     }
   }
   __syncthreads();
@@ -1137,8 +1152,8 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
   // a rotation about the circle's centre is tangential: v_g . n = 0)
   if (act && sd == 0) {
     if (MMODE != MORTAR_AVG_Q) {
-      double sn, cs;
-      sincos(m0 + fma(B.Xs[p], dm, md.mgeo[4 * m + 1]), &sn, &cs);
+      T sn, cs;
+      normal_of<T>(m0 + fma(B.Xs[p], dm, md.mgeo[4 * m + 1]), cs, sn);
       T qL[4], qR[4], Fn[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
