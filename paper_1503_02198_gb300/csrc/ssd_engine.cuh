@@ -7,8 +7,10 @@
 // interpolation, flux and divergence arithmetic in float; the state is kept
 // as a double-float pair (hi + lo) and the Runge-Kutta accumulation uses exact
 // two-sum arithmetic on the FP32 pipe (GB300's FP64 pipe runs at 1/64 of the
-// FP32 rate); the rotation angle, the mortar geometry and the mortar
-// projection weights stay FP64 in both paths (Sec. 3.2).
+// FP32 rate); the rotation angles (double-double), the mortar node order and
+// the mortar offsets and scales (Eq. xz) are extended FP64 in both paths; the
+// FP32 path evaluates the interface normals and the Lagrange products of the
+// projection weights in float (Sec. 3.2).
 //
 // Per step, once: k_clock_merge_stages, one CTA per stage (stage time t_k)
 //                   and interface: theta_z = omega_z t_k of every rotating

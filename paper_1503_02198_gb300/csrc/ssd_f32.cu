@@ -1,5 +1,6 @@
-// FP32 path: interpolation, flux and divergence arithmetic in float; state,
-// Runge-Kutta accumulation, rotation angle and mortar geometry stay FP64.
+// FP32 path: interpolation, flux and divergence arithmetic in float; the
+// state and its Runge-Kutta accumulation in double-float; rotation angles and
+// mortar offsets in extended FP64.
 #include "ssd_engine.cuh"
 
 namespace ssd {
