@@ -409,7 +409,7 @@ struct VisVolCfg {
   // resident CTAs per SM the register budget is set for: about 24 warps, or
   // what the shared memory admits
   static constexpr int WARPS = (THREADS + 31) / 32;
-  static constexpr int BY_WARPS = 24 / WARPS > 0 ? 24 / WARPS : 1;
+  static constexpr int BY_WARPS = 32 / WARPS > 0 ? 32 / WARPS : 1;
   static constexpr int BY_SMEM = 228 * 1024 / (SMEM + 1024);
   static constexpr int MINB = BY_WARPS < BY_SMEM ? BY_WARPS : (BY_SMEM > 0 ? BY_SMEM : 1);
 };
