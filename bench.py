@@ -97,8 +97,7 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch of the FP32 volume kernel on this
 # workload (mean of the three stage launches of one step), from one ncu
-# capture of dram__bytes_read.sum + dram__bytes_write.sum (the capture and its
-# command: profiles/k_volume_fp32_rotor_n6.md); valid only for the
+# capture of dram__bytes_read.sum + dram__bytes_write.sum; valid only for the
 # kernel source it was taken on: SHA-256 of the engine text that k_volume is
 # built from (the ElemGeo metrics and VolCfg through the end of k_volume);
 # otherwise null.
