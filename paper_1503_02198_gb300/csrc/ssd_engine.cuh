@@ -663,10 +663,13 @@ __device__ __forceinline__ ddang dd_wrap_2pi(ddang a) {
 // theta = omega t reduced to [0, 2 pi) as a double-double: the product is
 // exact (p + e, with the FMA), k = floor(p / 2 pi) turns are taken off with
 // the exact product k kTwoPiHi and k kTwoPiLo
+constexpr double kInvTwoPi = 0.15915494309189535;  // 1 / (2 pi), rounded
 __device__ __forceinline__ ddang dd_rotation_angle(double om, double t) {
   const double p = om * t;
   const double e = fma(om, t, -p);
-  const double k = floor(p / kTwoPiHi);
+  // any integer k near p / 2 pi will do: the reduction below is exact for it
+  // and the final wrap brings the angle into [0, 2 pi)
+  const double k = floor(p * kInvTwoPi);
   const double kh = k * kTwoPiHi;
   const double kl = fma(k, kTwoPiHi, -kh);
   const ddang r = dd_two_sum(p, -kh);
@@ -692,9 +695,10 @@ static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, dou
   __shared__ double s_th2, s_th2lo;
   __shared__ int s_k0;
   const double ts = tsrc->t_n + c * dt;
-  if (ii == 0 && threadIdx.x < kZT) {
+  // the zone clocks on warp 1, beside warp 0's angle of this interface
+  if (ii == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + kZT) {
     DevClock *k = md.clk;
-    const int z = threadIdx.x;
+    const int z = threadIdx.x - 32;
     const double om = z ? md.zpar[4 * z + 2] : 0.0;
     double sn = 0.0, cs = 1.0;
     ddang th{0.0, 0.0};
