@@ -434,7 +434,14 @@ struct ElemGeo {
     if (!ssd_check(md, ti < md.nTab && (OTF || ti >= 0))) ti = 0;
     if (OTF && ti < 0) {
       tab = nullptr;
-      const T v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4], v5 = r[5], v6 = r[6], v7 = r[7];
+      T v0, v1, v2, v3, v4, v5, v6, v7;
+      if constexpr (std::is_same<T, float>::value) {
+        // the record is 16-byte aligned (32 bytes per cell, in global or shared memory)
+        const float4 a = reinterpret_cast<const float4 *>(r)[0], b = reinterpret_cast<const float4 *>(r)[1];
+        v0 = a.x, v1 = a.y, v2 = a.z, v3 = a.w, v4 = b.x, v5 = b.y, v6 = b.z, v7 = b.w;
+      } else {
+        v0 = r[0], v1 = r[1], v2 = r[2], v3 = r[3], v4 = r[4], v5 = r[5], v6 = r[6], v7 = r[7];
+      }
       x0 = mul_sub(c, v0, s, v1);
       y0 = mul_add(s, v0, c, v1);
       e1x = mul_sub(c, v2, s, v3);
@@ -538,7 +545,14 @@ struct ElemGeo {
     const int ti = ((f & ~kIfaceBit) >> kZoneBits) - 1;
     if (OTF && ti < 0) {
       const T xi = cVB<T, N>.Xs[i], eta = cVB<T, N>.Xs[j];
-      const T xx = r[2] + eta * r[6], yx = r[3] + eta * r[7], xe = r[4] + xi * r[6], ye = r[5] + xi * r[7];
+      T r2, r3, r4, r5, r6, r7;
+      if constexpr (std::is_same<T, float>::value) {
+        const float4 a = reinterpret_cast<const float4 *>(r)[0], b = reinterpret_cast<const float4 *>(r)[1];
+        r2 = a.z, r3 = a.w, r4 = b.x, r5 = b.y, r6 = b.z, r7 = b.w;
+      } else {
+        r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6], r7 = r[7];
+      }
+      const T xx = r2 + eta * r6, yx = r3 + eta * r7, xe = r4 + xi * r6, ye = r5 + xi * r7;
       return recip(mul_sub(xx, ye, xe, yx));
     }
     return ((const T *)md.geo + (size_t)ti * L::G)[L::iJ + j * N + i];
