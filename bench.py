@@ -776,7 +776,7 @@ def main():
     batched = (run_batched(ssd, args.batch_cases, args.batch_steps, args.batch_max_cells)
                if args.batch_cases > 0 else
                {"held": "not run: the batched kernels are held off the GPU until an error seen in a 64-case "
-                        "run is explained"})
+                        "run is explained (the library refuses them unless SSD_BATCH_ENABLE=1)"})
     ellipse = run_ellipse(ssd, stream, args.ellipse_steps, 5) if args.ellipse_steps > 0 else None
     tank = run_tank(ssd, stream, args.tank_steps, 5) if args.tank_steps > 0 else None
     couette = run_couette(ssd, stream, args.couette_steps, 5) if args.couette_steps > 0 else None

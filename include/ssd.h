@@ -251,7 +251,12 @@ int sd_sp_coords(sd_handle *h, double t, double *xy, int on_device);
  * zero afterwards. */
 typedef struct sd_batch sd_batch;
 
-/* SD_ERR_ARG if the cases differ in precision or Runge-Kutta scheme. */
+/* SD_ERR_ARG if the cases differ in precision or Runge-Kutta scheme;
+ * SD_ERR_UNSUPPORTED for SD_PREC_FP32_TF32.  The batched form is held in this
+ * version: unless the environment variable SSD_BATCH_ENABLE is "1" the call
+ * returns SD_ERR_UNSUPPORTED (after the argument checks above), because a run
+ * of 64 FP32 cases stopped on a device memory error whose cause is not yet
+ * found. */
 int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_params *prm, double tune_dt,
                     sd_batch **out);
 int sd_batch_destroy(sd_batch *b);

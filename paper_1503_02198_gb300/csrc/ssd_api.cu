@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1390,6 +1391,18 @@ int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_
   if (prm[0].precision == SD_PREC_FP32_TF32) {
     g_create_error = "the batched form runs the FP32 contractions on the FMA pipe (SD_PREC_FP32)";
     return SD_ERR_UNSUPPORTED;
+  }
+  // Held: a 64-case batch (1k-8k cells, p = 2..5, FP32) stopped on a device
+  // memory error in its first steps and the cause is not yet found, so the
+  // batched kernels run only on request (environment SSD_BATCH_ENABLE=1).
+  {
+    const char *on = std::getenv("SSD_BATCH_ENABLE");
+    if (!on || std::string(on) != "1") {
+      g_create_error =
+          "the batched form is held (a 64-case run stopped on a device memory error whose cause is not yet "
+          "found); set SSD_BATCH_ENABLE=1 to run it";
+      return SD_ERR_UNSUPPORTED;
+    }
   }
   sd_batch *b = new sd_batch();
   auto fail_b = [&](int code, const std::string &msg) {

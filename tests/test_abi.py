@@ -80,3 +80,24 @@ def test_ctypes_layouts_match_the_header(tmp_path):
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
     assert pkg.SD_MAX_ZONES == 4
+
+
+def test_batched_form_is_held_unless_requested(libssd, monkeypatch):
+    # the argument checks come first; then, without SSD_BATCH_ENABLE=1, the
+    # batched form refuses to run (host only, no CUDA call)
+    import paper_1503_02198_gb300 as pkg
+    from ssd_inputs import meshes
+    from ssd_inputs.workloads import FlowParams
+    monkeypatch.delenv("SSD_BATCH_ENABLE", raising=False)
+    m = meshes.periodic_box_mesh(3, 2.0)
+    keep = []
+    structs = [pkg._mesh_struct(m, keep) for _ in range(2)]
+    mptrs = (ctypes.POINTER(pkg.sd_mesh) * 2)(*[ctypes.pointer(x) for x in structs])
+    parr = (ctypes.c_int * 2)(2, 3)
+    b = ctypes.c_void_p()
+    mixed = (pkg.sd_params * 2)(pkg._params_struct(FlowParams(), 0), pkg._params_struct(FlowParams(), 1))
+    assert libssd.sd_batch_create(2, mptrs, parr, mixed, 0.0, ctypes.byref(b)) == pkg.SD_ERR_ARG
+    same = (pkg.sd_params * 2)(pkg._params_struct(FlowParams(), 1), pkg._params_struct(FlowParams(), 1))
+    assert libssd.sd_batch_create(2, mptrs, parr, same, 0.0, ctypes.byref(b)) == pkg.SD_ERR_UNSUPPORTED
+    assert not b.value
+    assert b"SSD_BATCH_ENABLE" in libssd.sd_create_error()
