@@ -101,8 +101,8 @@ class ClockSampler:
 # kernel source it was taken on: SHA-256 of the engine text that k_volume is
 # built from (the ElemGeo metrics and VolCfg through the end of k_volume);
 # otherwise null.
-PROFILED_TRAFFIC = {"bytes": (389.28e6 + 329.15e6 + 673.67e6 + 330.94e6 + 673.72e6 + 329.72e6) / 3,
-                    "kernel_sha256": "27835dd39041711c5e2caa4956736e6f276d045df4dbcf46a3aede673d6a4b0c"}
+PROFILED_TRAFFIC = {"bytes": (389.22e6 + 329.38e6 + 673.64e6 + 331.13e6 + 673.64e6 + 329.97e6) / 3,
+                    "kernel_sha256": "de5b15ca7413870bdc0b262478b67ca117fbab9a5afb50eef15abb2879f1b625"}
 
 
 def volume_kernel_source():
