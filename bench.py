@@ -156,9 +156,10 @@ def volume_flops_per_element(N):
 
 def interface_fraction(prof):
     """Share of a step spent on sliding-interface work, the paper's
-    "interface" time (Tables 3-10): the stage clock and mortar merge, the
-    mortar projections with their common flux, and the gather, each timed
-    as its own launch by sd_profile_step (per stage; three stages a step)."""
+    "interface" time (Tables 3-10): the stage clock and mortar merge and the
+    mortar projections with their common flux, each timed as its own launch
+    by sd_profile_step (per stage; three stages a step; the sum over each
+    face's mortars runs inside the volume kernel and is not counted)."""
     return (prof["merge"] + prof["mortar"]) * 3 / prof["step"]
 
 
@@ -166,14 +167,11 @@ def launches_per_step(mesh, viscous=0):
     """Kernels of one captured SSP-RK3 step: one merge launch for the clocks
     and mortar tables of all three stages; per stage the face kernel
     (conforming and boundary points, and the mortar flux when the mesh has an
-    interface, in one launch), the mortar gather (if an interface) and the
-    volume kernel, plus for a viscous stage the common-solution face kernel
-    (with its mortar flux), its gather and the gradient-trace kernel; then
-    the clock advance."""
-    iface = int(len(mesh["ifaces_L"]) > 0 or any(len(z["ifaces_L"]) > 0 for z in mesh.get("zones", [])))
-    per_stage = 1 + iface + 1
-    if viscous:
-        per_stage += 1 + iface + 1
+    interface, in one launch) and the volume kernel (which sums the mortar
+    contributions of its interface faces itself), plus for a viscous stage the
+    common-solution face kernel (with its mortar flux) and the gradient-trace
+    kernel; then the clock advance."""
+    per_stage = 2 + (2 if viscous else 0)
     return 1 + 3 * per_stage + 1
 
 
