@@ -133,14 +133,17 @@ __device__ __forceinline__ void tile_gradients(const MeshDev &md, int e0, int ne
   if (le < ne) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      T val[N + 1];
+      T val[N + 1], qv[N];
       val[0] = sCQ[le][((d == 0 ? 3 : 0) * 4 + v) * N + m];
       val[N] = sCQ[le][((d == 0 ? 1 : 2) * 4 + v) * N + m];
+      // the line's N values, read once for all its flux points
+#pragma unroll
+      for (int k = 0; k < N; ++k) qv[k] = sQ[le][v][d == 0 ? m * N + k : k * N + m];
 #pragma unroll
       for (int i = 1; i < N; ++i) {
         T acc = 0;
 #pragma unroll
-        for (int k = 0; k < N; ++k) acc += (d == 0 ? sQ[le][v][m * N + k] : sQ[le][v][k * N + m]) * B.Hf[i * N + k];
+        for (int k = 0; k < N; ++k) acc += qv[k] * B.Hf[i * N + k];
         val[i] = acc;
       }
 #pragma unroll
