@@ -189,6 +189,10 @@ struct sd_handle {
   bool traces_valid = false;
   cudaGraphExec_t step_exec = nullptr;
   double graph_dt = 0.0;
+  // the captured step's side branch: the stage merges that run beside the
+  // stages (see queue_step)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_rest = nullptr, ev_stage0 = nullptr, ev_next = nullptr;
   double *h_pinned = nullptr;  // small pinned buffer for clock reads / writes
   StageMerge sm{};             // per-stage clocks, mortar tables and merge work arrays
   std::string err;
@@ -658,6 +662,9 @@ void free_handle(sd_handle *h) {
   delete h->eng;
   for (void *p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  for (cudaEvent_t e : {h->ev_start, h->ev_rest, h->ev_stage0, h->ev_next})
+    if (e) cudaEventDestroy(e);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -771,15 +778,50 @@ int step_plan(sd_handle *h, double dt, BatchStageHost *plan, double *c) {
   return 5;
 }
 
-void queue_step(sd_handle *h, double dt) {
-  BatchStageHost plan[kMaxStages];
+// CTAs of the merges beside the stages: small, so that the persistent
+// kernels running at the same time keep their places on those SMs
+constexpr int kSideMergeThreads = 256;
+
+// the step's stage time fractions into h->sm; returns the plan of its stages
+int plan_step(sd_handle *h, double dt, BatchStageHost *plan) {
   double c[kMaxStages];
   const int n = step_plan(h, dt, plan, c);
-  StageMerge &sm = h->sm;
-  sm.n = n;
-  for (int k = 0; k < n; ++k) sm.c[k] = c[k];
-  h->eng->merge_stages(h->md, sm, dt, h->stream);
-  for (int k = 0; k < n; ++k) queue_stage(h, k, plan[k].in, plan[k].base, plan[k].out, plan[k].rk);
+  h->sm.n = n;
+  for (int k = 0; k < n; ++k) h->sm.c[k] = c[k];
+  return n;
+}
+
+// Stage 0's clock and mortar table at the step's start time t_n (before the
+// first captured step of a call; each captured step then merges the next
+// step's stage 0 itself).
+void queue_merge_stage0(sd_handle *h, double dt) {
+  BatchStageHost plan[kMaxStages];
+  plan_step(h, dt, plan);
+  h->eng->merge_stages(h->md, h->sm, dt, 0, 1, 0.0, 1024, h->stream);
+}
+
+// One time step for capture.  The merges depend on time only, so they leave
+// the critical path: stages 1..n-1 are merged on the side stream beside stage
+// 0's kernels, and stage 0 of the next step (at t_n + dt, the value k_advance
+// forms) beside stages 1..n-1, after stage 0's kernels have read its table.
+// Stage 0 of this step was merged by the previous step or by the prologue.
+void queue_step(sd_handle *h, double dt) {
+  BatchStageHost plan[kMaxStages];
+  const int n = plan_step(h, dt, plan);
+  const StageMerge &sm = h->sm;
+  cudaEventRecord(h->ev_start, h->stream);
+  cudaStreamWaitEvent(h->side, h->ev_start, 0);
+  h->eng->merge_stages(h->md, sm, dt, 1, n - 1, 0.0, kSideMergeThreads, h->side);
+  cudaEventRecord(h->ev_rest, h->side);
+  queue_stage(h, 0, plan[0].in, plan[0].base, plan[0].out, plan[0].rk);
+  cudaEventRecord(h->ev_stage0, h->stream);
+  cudaStreamWaitEvent(h->side, h->ev_stage0, 0);
+  h->eng->merge_stages(h->md, sm, dt, 0, 1, 1.0, kSideMergeThreads, h->side);
+  cudaEventRecord(h->ev_next, h->side);
+  cudaStreamWaitEvent(h->stream, h->ev_rest, 0);
+  for (int k = 1; k < n; ++k) queue_stage(h, k, plan[k].in, plan[k].base, plan[k].out, plan[k].rk);
+  // the next step's merge read t_n: it ends before t_n += dt
+  cudaStreamWaitEvent(h->stream, h->ev_next, 0);
   h->eng->advance(h->md, dt, h->stream);
 }
 
@@ -849,6 +891,9 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
       rc = fail(h, SD_ERR_UNSUPPORTED, "no tensor-core contractions in this engine");
   }
   if (!rc && (ce = cudaMallocHost(&h->h_pinned, 64))) rc = cuda_fail(h, ce, "pinned buffer");
+  if (!rc && (ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking))) rc = cuda_fail(h, ce, "side stream");
+  for (cudaEvent_t *e : {&h->ev_start, &h->ev_rest, &h->ev_stage0, &h->ev_next})
+    if (!rc && (ce = cudaEventCreateWithFlags(e, cudaEventDisableTiming))) rc = cuda_fail(h, ce, "events");
   if (!rc) {
     MeshDev &md = h->md;
     md.gamma_f = (float)prm->gamma;
@@ -1049,6 +1094,8 @@ int sd_step(sd_handle *h, double dt, int nsteps) {
     if (e) return cuda_fail(h, e, "graph instantiate");
     h->graph_dt = dt;
   }
+  queue_merge_stage0(h, dt);
+  if ((e = cudaGetLastError())) return cuda_fail(h, e, "merge kernel");
   for (int k = 0; k < nsteps; ++k)
     if ((e = cudaGraphLaunch(h->step_exec, h->stream))) return cuda_fail(h, e, "graph launch");
   return SD_OK;

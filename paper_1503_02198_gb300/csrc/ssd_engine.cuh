@@ -12,12 +12,14 @@
 // FP32 path evaluates the interface normals and the Lagrange products of the
 // projection weights in float (Sec. 3.2).
 //
-// Per step, once: k_clock_merge_stages, one CTA per stage (stage time t_k)
+// Per step:      k_clock_merge_stages, one CTA per stage (stage time t_k)
 //                   and interface: theta_z = omega_z t_k of every rotating
 //                   zone; merge of the interface's rotated L node angles
 //                   with its R node angles -> mortars, (o, s) of each mortar
 //                   against its L and R face (Eq. xz), face ranges, into the
-//                   stage's own clock record and mortar table
+//                   stage's own clock record and mortar table.  Off the
+//                   critical path: stages 1.. are merged beside stage 0's
+//                   kernels, and stage 0 of the next step beside stage 1's
 //                   (k_clock_merge: the same for one stage, e.g. a residual)
 // Per stage:
 //   k_faces         one launch for every face point: conforming and periodic
@@ -837,10 +839,12 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_
   clock_merge_body(md, blockIdx.y, c, dt, work_i, work_d, md.clk);
 }
 
-// block (b, ii): the clock and interface ii's mortar table of stage b of a step
-static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt) {
+// block (x, ii): the clock and interface ii's mortar table of stage b = b0 + x
+// of a step, at t_n + (c_b + cadd) dt (cadd = 1: stage b of the next step,
+// whose start time t_n + dt is formed as k_advance forms it)
+static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt, int b0, double cadd) {
   pdl_enter();
-  const int b = blockIdx.x;
+  const int b = b0 + (int)blockIdx.x;
   MeshDev m = md;
   m.clk = sm.clk[b];
   m.mLf = sm.mLf[b];
@@ -850,7 +854,7 @@ static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt
   m.Rstart = sm.Rstart[b];
   m.Rcount = sm.Rcount[b];
   m.mgeo = sm.mgeo[b];
-  clock_merge_body(m, blockIdx.y, sm.c[b], dt, sm.work_i[b], sm.work_d[b], md.clk);
+  clock_merge_body(m, blockIdx.y, sm.c[b] + cadd, dt, sm.work_i[b], sm.work_d[b], md.clk);
 }
 
 // t = 0 geometry of every conforming / periodic face point (one thread per point)
@@ -2341,8 +2345,10 @@ struct EngineImpl : Engine {
     launch_pdl(k_clock_merge, dim3(1, md.nI), 1024, merge_smem, s, md, c, dt, work_i, work_d);
   }
 
-  void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, cudaStream_t s) override {
-    launch_pdl(k_clock_merge_stages, dim3(sm.n, md.nI), 1024, merge_smem, s, md, sm, dt);
+  void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, int first, int count, double cadd,
+                    int threads, cudaStream_t s) override {
+    if (count > 0)
+      launch_pdl(k_clock_merge_stages, dim3(count, md.nI), threads, merge_smem, s, md, sm, dt, first, cadd);
   }
 
   // the mortar flux as its own launch; the gather of its contributions into
