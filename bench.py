@@ -164,17 +164,18 @@ def interface_fraction(prof):
 
 
 def launches_per_step(mesh, viscous=0):
-    """Kernels of one captured SSP-RK3 step: two merge launches on the side
-    branch (the clocks and mortar tables of stages 1 and 2 beside stage 0, and
-    stage 0 of the next step beside stages 1 and 2); per stage the face kernel
-    (conforming and boundary points, and the mortar flux when the mesh has an
-    interface, in one launch) and the volume kernel (which sums the mortar
-    contributions of its interface faces itself), plus for a viscous stage the
-    common-solution face kernel (with its mortar flux) and the gradient-trace
-    kernel; then the clock advance.  (Each sd_step call adds one merge of its
-    first step's stage 0.)"""
+    """Kernels of one captured SSP-RK3 step: on the side branch two merges,
+    each a merge launch and a launch forming the mortar offsets of Eq. xz (the
+    clocks and mortar tables of stages 1 and 2 beside stage 0, and stage 0 of
+    the next step beside stages 1 and 2), then the clock advance; per stage
+    the face kernel (conforming and boundary points, and the mortar flux when
+    the mesh has an interface, in one launch) and the volume kernel (which
+    sums the mortar contributions of its interface faces itself), plus for a
+    viscous stage the common-solution face kernel (with its mortar flux) and
+    the gradient-trace kernel.  (Each sd_step call adds the two launches of
+    its first step's stage-0 merge.)"""
     per_stage = 2 + (2 if viscous else 0)
-    return 2 + 3 * per_stage + 1
+    return 2 * 2 + 3 * per_stage + 1
 
 
 SAMPLE_LADDER = (  # (n_cart, n_hole, n_core, n_ring_in, n_ring_out) of the rotor family
@@ -819,7 +820,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
-            "gpu_launches": launches_per_step(w.mesh, w.params.viscous) * args.steps + 1,
+            "gpu_launches": launches_per_step(w.mesh, w.params.viscous) * args.steps + 2,
         }
         print(json.dumps(line))
     if world > 1:

@@ -580,6 +580,7 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   if ((e = dalloc(h, &md.mLf, sizeof(int) * nb))) return e;
   if ((e = dalloc(h, &md.mRf, sizeof(int) * nb))) return e;
   if ((e = dalloc(h, &md.mgeo, sizeof(double) * 4 * nb))) return e;
+  if ((e = dalloc(h, &md.msd, sizeof(MortSide) * 2 * nb))) return e;
   if ((e = dalloc(h, &md.fgeo, w * 5 * N * (md.nF ? md.nF : 1)))) return e;
   if ((e = dalloc(h, &md.Lstart, sizeof(int) * md.nL))) return e;
   if ((e = dalloc(h, &md.Lcount, sizeof(int) * md.nL))) return e;
@@ -614,6 +615,7 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
     if ((e = dalloc(h, &sm.mLf[k], sizeof(int) * nb))) return e;
     if ((e = dalloc(h, &sm.mRf[k], sizeof(int) * nb))) return e;
     if ((e = dalloc(h, &sm.mgeo[k], sizeof(double) * 4 * nb))) return e;
+    if ((e = dalloc(h, &sm.msd[k], sizeof(MortSide) * 2 * nb))) return e;
     if ((e = dalloc(h, &sm.Lstart[k], sizeof(int) * md.nL))) return e;
     if ((e = dalloc(h, &sm.Lcount[k], sizeof(int) * md.nL))) return e;
     if ((e = dalloc(h, &sm.Rstart[k], sizeof(int) * md.nR))) return e;
@@ -713,6 +715,7 @@ MeshDev stage_view(const sd_handle *h, int k) {
   m.mLf = sm.mLf[k];
   m.mRf = sm.mRf[k];
   m.mgeo = sm.mgeo[k];
+  m.msd = sm.msd[k];
   m.Lstart = sm.Lstart[k];
   m.Lcount = sm.Lcount[k];
   m.Rstart = sm.Rstart[k];
@@ -803,8 +806,9 @@ void queue_merge_stage0(sd_handle *h, double dt) {
 // One time step for capture.  The merges depend on time only, so they leave
 // the critical path: stages 1..n-1 are merged on the side stream beside stage
 // 0's kernels, and stage 0 of the next step (at t_n + dt, the value k_advance
-// forms) beside stages 1..n-1, after stage 0's kernels have read its table.
-// Stage 0 of this step was merged by the previous step or by the prologue.
+// forms) beside stages 1..n-1, after stage 0's kernels have read its table;
+// then the same side stream advances t_n (only the merges read it).  Stage 0
+// of this step was merged by the previous step or by the prologue.
 void queue_step(sd_handle *h, double dt) {
   BatchStageHost plan[kMaxStages];
   const int n = plan_step(h, dt, plan);
@@ -817,12 +821,12 @@ void queue_step(sd_handle *h, double dt) {
   cudaEventRecord(h->ev_stage0, h->stream);
   cudaStreamWaitEvent(h->side, h->ev_stage0, 0);
   h->eng->merge_stages(h->md, sm, dt, 0, 1, 1.0, kSideMergeThreads, h->side);
+  h->eng->advance(h->md, dt, h->side);
   cudaEventRecord(h->ev_next, h->side);
   cudaStreamWaitEvent(h->stream, h->ev_rest, 0);
   for (int k = 1; k < n; ++k) queue_stage(h, k, plan[k].in, plan[k].base, plan[k].out, plan[k].rk);
-  // the next step's merge read t_n: it ends before t_n += dt
+  // the side branch rejoins: the step ends when both have
   cudaStreamWaitEvent(h->stream, h->ev_next, 0);
-  h->eng->advance(h->md, dt, h->stream);
 }
 
 }  // namespace
@@ -1487,7 +1491,7 @@ int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_
     b->nstages = step_plan(b->cases[0], 1.0, plan, c);
     std::vector<MeshDev> base(n), stage((size_t)b->nstages * n);
     std::vector<StageMerge> sms(n);
-    int max_iface = 1, smem = 8;
+    int max_iface = 1, smem = 8, max_nm = 0;
     for (int i = 0; i < n; ++i) {
       sd_handle *h = b->cases[b->order[i]];
       step_plan(h, 1.0, plan, c);
@@ -1499,6 +1503,7 @@ int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_
       base[i] = h->md;
       sms[i] = h->sm;
       max_iface = std::max(max_iface, h->md.nI);
+      max_nm = std::max(max_nm, h->md.nM);
       smem = std::max(smem, (int)(2 * sizeof(double) * std::max(1, h->md.nbmax)));
     }
     auto dup = [&](const void *src, size_t bytes, void **dst) {
@@ -1516,6 +1521,7 @@ int sd_batch_create(int n, const sd_mesh *const *meshes, const int *p, const sd_
     b->bm.ncase = n;
     b->bm.nstages = b->nstages;
     b->bm.max_iface = max_iface;
+    b->bm.max_nm = max_nm;
     b->bm.md = (const MeshDev *)dmd;
     b->bm.md_stage = (const MeshDev *)dst;
     b->bm.sm = (const StageMerge *)dsm;
@@ -1688,6 +1694,7 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   const size_t o_mLf = off; off += align256(sizeof(int) * nb);
   const size_t o_mRf = off; off += align256(sizeof(int) * nb);
   const size_t o_mgeo = off; off += align256(sizeof(double) * 4 * nb);
+  const size_t o_msd = off; off += align256(sizeof(MortSide) * 2 * nb);
   const size_t o_Ls = off; off += align256(sizeof(int) * md0.nL);
   const size_t o_Lc = off; off += align256(sizeof(int) * md0.nL);
   const size_t o_Rs = off; off += align256(sizeof(int) * md0.nR);
@@ -1713,6 +1720,7 @@ int sd_residual_noalloc(sd_handle *h, double *R, int on_device) {
   md.mLf = (int *)(b + o_mLf);
   md.mRf = (int *)(b + o_mRf);
   md.mgeo = (double *)(b + o_mgeo);
+  md.msd = (MortSide *)(b + o_msd);
   md.Lstart = (int *)(b + o_Ls);
   md.Lcount = (int *)(b + o_Lc);
   md.Rstart = (int *)(b + o_Rs);

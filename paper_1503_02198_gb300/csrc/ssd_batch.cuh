@@ -76,6 +76,13 @@ static __global__ void k_batch_merge(BatchMergeDev bm) {
                    base.clk);
 }
 
+// Eq. xz of every mortar of every stage of every case (after k_batch_merge):
+// block (x, stage k, case c)
+static __global__ void __launch_bounds__(kXzBlock) k_batch_xz(BatchMergeDev bm) {
+  pdl_enter();
+  mortar_xz_body(bm.md_stage[(size_t)blockIdx.y * bm.ncase + blockIdx.z], blockIdx.x * kXzBlock + threadIdx.x);
+}
+
 // the end of a step of every case: t_n += dt
 static __global__ void k_batch_advance(BatchMergeDev bm) {
   pdl_enter();

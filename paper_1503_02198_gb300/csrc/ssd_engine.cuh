@@ -703,8 +703,9 @@ __device__ __forceinline__ ddang dd_rotation_angle(double om, double t) {
 // of the interface: high parts, then low parts); work_i / work_d hold the
 // merged positions and angles.  The CTA of interface 0 also writes the stage
 // clock of every zone: theta_z = omega_z t_stage.  The offsets and scales of
-// Eq. xz are formed per mortar in the mortar flux.  The step's start time t_n
-// is read from *tsrc; the stage clock and the table are written through md.
+// Eq. xz of each mortar against its faces are formed here too, for the mortar
+// flux kernels of the stage.  The step's start time t_n is read from *tsrc;
+// the stage clock and the tables are written through md.
 static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, double dt, int *work_i,
                                         double *work_d, const DevClock *tsrc) {
   extern __shared__ double s_ang[];  // [nb] high parts (rotated L, then R), [nb] low parts
@@ -833,6 +834,51 @@ static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, dou
   }
 }
 
+// Eq. xz of mortar m against its face on side sd (0: L, 1: R) of a stage
+// whose merge has run: the offset of the mortar's start from the face's
+// start angle (the L face's turned by its zone's stage angle), a
+// double-double difference taken into (-pi, pi], and the mortar's length,
+// both over the face's angular width.  One thread per (mortar, side), so the
+// FP64 work spreads over many SMs.
+static __device__ __forceinline__ void mortar_xz_body(const MeshDev &md, int t) {
+  if (t >= 2 * md.nM) return;
+  const int sd = t >= md.nM, m = t - sd * md.nM;
+  const double pi = 0.5 * kTwoPiHi;
+  const ddang m0d{md.mgeo[4 * m], md.mgeo[4 * m + 1]};
+  const double dm = md.mgeo[4 * m + 2];
+  const int fq = sd ? md.mRf[m] : md.mLf[m];
+  MortSide ms{};
+  if (ssd_check(md, fq >= 0 && fq < (sd ? md.nR : md.nL))) {
+    ddang fa{md.Ra[fq], md.Ra_lo[fq]};
+    if (!sd) {
+      // interface ifz[fq] belongs to zone ifz[fq] + 1
+      const int z = md.ifz[fq] + 1;
+      fa = dd_wrap_2pi(dd_add(ddang{md.La[fq], md.La_lo[fq]}, ddang{md.clk->theta2[z], md.clk->theta2_lo[z]}));
+    }
+    ddang offd = dd_sub(m0d, fa);
+    if (offd.hi > pi) offd = dd_sub(offd, ddang{kTwoPiHi, kTwoPiLo});
+    if (offd.hi <= -pi) offd = dd_add(offd, ddang{kTwoPiHi, kTwoPiLo});
+    const double off = offd.hi + offd.lo;
+    const double iw = sd ? md.RiW[fq] : md.LiW[fq];
+    const int4 fc = sd ? md.Rface[fq] : md.Lface[fq];
+    ms.o = off * iw;
+    ms.s = dm * iw;
+    ms.fa_hi = fa.hi;
+    ms.fa_lo = fa.lo;
+    ms.w = sd ? md.Rw[fq] : md.Lw[fq];
+    ms.ef = fc.x;
+    ms.rev = fc.y;
+  }
+  md.msd[t] = ms;
+}
+
+constexpr int kXzBlock = 128;
+
+static __global__ void __launch_bounds__(kXzBlock) k_mortar_xz(MeshDev md) {
+  pdl_enter();
+  mortar_xz_body(md, blockIdx.x * kXzBlock + threadIdx.x);
+}
+
 // block (0, ii): interface ii of one stage
 static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_i, double *work_d) {
   pdl_enter();
@@ -855,6 +901,19 @@ static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt
   m.Rcount = sm.Rcount[b];
   m.mgeo = sm.mgeo[b];
   clock_merge_body(m, blockIdx.y, sm.c[b] + cadd, dt, sm.work_i[b], sm.work_d[b], md.clk);
+}
+
+// block (x, y): Eq. xz of mortars [x kXzBlock / 2 ...) of stage b0 + y
+static __global__ void __launch_bounds__(kXzBlock) k_mortar_xz_stages(MeshDev md, StageMerge sm, int b0) {
+  pdl_enter();
+  const int b = b0 + (int)blockIdx.y;
+  MeshDev m = md;
+  m.clk = sm.clk[b];
+  m.mLf = sm.mLf[b];
+  m.mRf = sm.mRf[b];
+  m.mgeo = sm.mgeo[b];
+  m.msd = sm.msd[b];
+  mortar_xz_body(m, blockIdx.x * kXzBlock + threadIdx.x);
 }
 
 // t = 0 geometry of every conforming / periodic face point (one thread per point)
@@ -1077,29 +1136,15 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
   double m0 = 0.0, dm = 0.0;
   if (act) {
     // Eq. xz: offset and scale of this mortar against its face on side sd,
-    // the angle difference in double-double
-    const ddang m0d{md.mgeo[4 * m], md.mgeo[4 * m + 1]};
-    m0 = m0d.hi;
+    // formed by the stage's merge
+    const MortSide ms = md.msd[(size_t)sd * md.nM + m];
+    m0 = md.mgeo[4 * m];
     dm = md.mgeo[4 * m + 2];
-    const double pi = 0.5 * kTwoPiHi;
-    int fq = sd ? md.mRf[m] : md.mLf[m];
-    if (!ssd_check(md, fq >= 0 && fq < (sd ? md.nR : md.nL))) fq = 0;
-    // the L side turns with its zone (interface ifz[fq] belongs to zone ifz[fq] + 1)
-    ddang fa{md.Ra[fq], md.Ra_lo[fq]};
-    if (!sd) {
-      const int z = md.ifz[fq] + 1;
-      fa = dd_wrap_2pi(dd_add(ddang{md.La[fq], md.La_lo[fq]}, ddang{md.clk->theta2[z], md.clk->theta2_lo[z]}));
-    }
-    ddang offd = dd_sub(m0d, fa);
-    if (offd.hi > pi) offd = dd_sub(offd, ddang{kTwoPiHi, kTwoPiLo});
-    if (offd.hi <= -pi) offd = dd_add(offd, ddang{kTwoPiHi, kTwoPiLo});
-    const double off = offd.hi + offd.lo;
-    const double iw = sd ? md.RiW[fq] : md.LiW[fq];
-    o = off * iw;
-    s = dm * iw;
-    const int4 fc = sd ? md.Rface[fq] : md.Lface[fq];
-    ef = fc.x;
-    rev = fc.y;
+    o = ms.o;
+    s = ms.s;
+    ef = ms.ef;
+    rev = ms.rev;
+    if (!ssd_check(md, ef >= 0 && ef < 4 * md.E)) ef = 0;
     const int jj = rev ? N - 1 - p : p;
     if (MMODE == MORTAR_RUSANOV_FV) {
       // viscous normal flux of this face point with the common solution and
@@ -1111,7 +1156,7 @@ __device__ __forceinline__ void mortar_flux_body(const MeshDev &md, int blk) {
 #pragma unroll
       for (int c = 0; c < 8; ++c) g8[c] = GT[((size_t)ef * 8 + c) * N + jj];
       T sn, cs;
-      normal_of<T>(fa.hi + (fa.lo + B.Xs[p] * (sd ? md.Rw[fq] : md.Lw[fq])), cs, sn);
+      normal_of<T>(ms.fa_hi + (ms.fa_lo + B.Xs[p] * ms.w), cs, sn);
       viscous_normal(q, g8, cs, sn, md, fn);
 #pragma unroll
       for (int v = 0; v < 4; ++v) sQf[lm][sd][NV - 4 + v][p] = fn[v];
@@ -2338,18 +2383,22 @@ struct EngineImpl : Engine {
 
   void clock_merge(const MeshDev &md, double c, double dt, cudaStream_t s) override {
     launch_pdl(k_clock_merge, dim3(1, md.nI), 1024, merge_smem, s, md, c, dt, scratch_i, scratch_d);
+    if (md.nM > 0) launch_pdl(k_mortar_xz, xz_blocks(md), kXzBlock, 0, s, md);
   }
 
   void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                         cudaStream_t s) override {
     launch_pdl(k_clock_merge, dim3(1, md.nI), 1024, merge_smem, s, md, c, dt, work_i, work_d);
+    if (md.nM > 0) launch_pdl(k_mortar_xz, xz_blocks(md), kXzBlock, 0, s, md);
   }
 
   void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, int first, int count, double cadd,
                     int threads, cudaStream_t s) override {
-    if (count > 0)
-      launch_pdl(k_clock_merge_stages, dim3(count, md.nI), threads, merge_smem, s, md, sm, dt, first, cadd);
+    if (count <= 0) return;
+    launch_pdl(k_clock_merge_stages, dim3(count, md.nI), threads, merge_smem, s, md, sm, dt, first, cadd);
+    if (md.nM > 0) launch_pdl(k_mortar_xz_stages, dim3(xz_blocks(md), count), kXzBlock, 0, s, md, sm, first);
   }
+  static unsigned xz_blocks(const MeshDev &md) { return (unsigned)((2 * md.nM + kXzBlock - 1) / kXzBlock); }
 
   // the mortar flux as its own launch; the gather of its contributions into
   // each interface face is done by the kernel that reads the result
@@ -2724,6 +2773,11 @@ struct EngineImpl : Engine {
     if (bm.smem > 48 * 1024) cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, bm.smem);
     launch_pdl(k_batch_merge, dim3(bm.max_iface, bm.nstages, bm.ncase), 1024, bm.smem, s, bm);
     dbg_sync(s, "batch merge");
+    if (bm.max_nm > 0) {
+      launch_pdl(k_batch_xz, dim3((2 * bm.max_nm + kXzBlock - 1) / kXzBlock, bm.nstages, bm.ncase), kXzBlock, 0, s,
+                 bm);
+      dbg_sync(s, "batch mortar offsets");
+    }
   }
 
   void batch_advance(const BatchMergeDev &bm, cudaStream_t s) override {

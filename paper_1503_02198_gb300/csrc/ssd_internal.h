@@ -67,6 +67,15 @@ struct StatePtr {
   void *lo;
 };
 
+// Eq. xz for one mortar against its face on one side, formed by the merge of
+// the stage: offset o and scale s of the mortar in the face's reference
+// coordinate, the face's rotated start angle (double-double) and angular
+// width, its element-face index and orientation
+struct __align__(16) MortSide {
+  double o, s, fa_hi, fa_lo, w;
+  int ef, rev;
+};
+
 // Everything a kernel needs, by value (device pointers + sizes + parameters).
 struct MeshDev {
   int E, N;
@@ -95,6 +104,7 @@ struct MeshDev {
   // per-stage mortar table (written by the merge kernel)
   int *mLf, *mRf;       // [nM] containing L / R face (sorted index)
   double *mgeo;         // [nM][4]: start angle (double-double: high, low), angular length, unused
+  MortSide *msd;        // [2][nM]: Eq. xz of each mortar against its L, then its R face
   int *Lstart, *Lcount; // [nL] first mortar (merged position) and count
   int *Rstart, *Rcount; // [nR]
   void *contrib;        // T [2][nM][4][N] back-projected mortar fluxes
@@ -155,6 +165,7 @@ struct StageMerge {
   int *mLf[kMaxStages], *mRf[kMaxStages];
   int *Lstart[kMaxStages], *Lcount[kMaxStages], *Rstart[kMaxStages], *Rcount[kMaxStages];
   double *mgeo[kMaxStages];
+  MortSide *msd[kMaxStages];
   int *work_i[kMaxStages];
   double *work_d[kMaxStages];
 };
@@ -184,6 +195,7 @@ struct BatchStageHost {
 // a block per (interface, stage, case).
 struct BatchMergeDev {
   int ncase, nstages, max_iface;
+  int max_nm;               // the most mortars of one case
   const MeshDev *md;        // [ncase] base view (its clock holds the step's start time)
   const MeshDev *md_stage;  // [nstages][ncase] stage views (stage clock, mortar table)
   const StageMerge *sm;     // [ncase]
