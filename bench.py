@@ -164,18 +164,17 @@ def interface_fraction(prof):
 
 
 def launches_per_step(mesh, viscous=0):
-    """Kernels of one captured SSP-RK3 step: on the side branch two merges,
-    each a merge launch and a launch forming the mortar offsets of Eq. xz (the
-    clocks and mortar tables of stages 1 and 2 beside stage 0, and stage 0 of
-    the next step beside stages 1 and 2), then the clock advance; per stage
-    the face kernel (conforming and boundary points, and the mortar flux when
-    the mesh has an interface, in one launch) and the volume kernel (which
-    sums the mortar contributions of its interface faces itself), plus for a
-    viscous stage the common-solution face kernel (with its mortar flux) and
-    the gradient-trace kernel.  (Each sd_step call adds the two launches of
-    its first step's stage-0 merge.)"""
+    """Kernels of one captured SSP-RK3 step: on the side branch, beside the
+    whole step, the merge of the next step's three stages (clocks and mortar
+    tables), the launch forming their mortar offsets (Eq. xz) and the clock
+    advance; per stage the face kernel (conforming and boundary points, and
+    the mortar flux when the mesh has an interface, in one launch) and the
+    volume kernel (which sums the mortar contributions of its interface faces
+    itself), plus for a viscous stage the common-solution face kernel (with
+    its mortar flux) and the gradient-trace kernel.  (Each sd_step call adds
+    the two launches merging its first step.)"""
     per_stage = 2 + (2 if viscous else 0)
-    return 2 * 2 + 3 * per_stage + 1
+    return 3 + 3 * per_stage
 
 
 SAMPLE_LADDER = (  # (n_cart, n_hole, n_core, n_ring_in, n_ring_out) of the rotor family

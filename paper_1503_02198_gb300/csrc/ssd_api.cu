@@ -187,14 +187,15 @@ struct sd_handle {
   double *stage = nullptr;    // FP64 staging of host states (FP32 path)
   double *scratch = nullptr;  // device copy of a host residual
   bool traces_valid = false;
-  cudaGraphExec_t step_exec = nullptr;
+  // the captured step, one per set of stage tables it reads (see queue_step)
+  cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
   double graph_dt = 0.0;
-  // the captured step's side branch: the stage merges that run beside the
-  // stages (see queue_step)
+  // the captured step's side branch: the merges of the next step's stages
   cudaStream_t side = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_rest = nullptr, ev_stage0 = nullptr, ev_next = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_next = nullptr;
   double *h_pinned = nullptr;  // small pinned buffer for clock reads / writes
   StageMerge sm{};             // per-stage clocks, mortar tables and merge work arrays
+  StageMerge sm_b{};           // a second set: a captured step reads one and merges the next step into the other
   std::string err;
 };
 
@@ -605,23 +606,24 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
     if ((e = cudaStreamSynchronize(h->stream))) return e;  // c0 leaves scope
     md.clk0 = dc0;
   }
-  // the stage records of a time step (see StageMerge)
+  // the stage records of a time step (see StageMerge), two sets
   DevClock *sclk;
-  if ((e = dalloc(h, &sclk, sizeof(DevClock) * kMaxStages))) return e;
-  if ((e = cudaMemsetAsync(sclk, 0, sizeof(DevClock) * kMaxStages, h->stream))) return e;
-  for (int k = 0; k < kMaxStages; ++k) {
-    StageMerge &sm = h->sm;
-    sm.clk[k] = sclk + k;
-    if ((e = dalloc(h, &sm.mLf[k], sizeof(int) * nb))) return e;
-    if ((e = dalloc(h, &sm.mRf[k], sizeof(int) * nb))) return e;
-    if ((e = dalloc(h, &sm.mgeo[k], sizeof(double) * 4 * nb))) return e;
-    if ((e = dalloc(h, &sm.msd[k], sizeof(MortSide) * 2 * nb))) return e;
-    if ((e = dalloc(h, &sm.Lstart[k], sizeof(int) * md.nL))) return e;
-    if ((e = dalloc(h, &sm.Lcount[k], sizeof(int) * md.nL))) return e;
-    if ((e = dalloc(h, &sm.Rstart[k], sizeof(int) * md.nR))) return e;
-    if ((e = dalloc(h, &sm.Rcount[k], sizeof(int) * md.nR))) return e;
-    if ((e = dalloc(h, &sm.work_i[k], sizeof(int) * (2 * nb + 1)))) return e;
-    if ((e = dalloc(h, &sm.work_d[k], sizeof(double) * (2 * nb + 1)))) return e;
+  if ((e = dalloc(h, &sclk, sizeof(DevClock) * 2 * kMaxStages))) return e;
+  if ((e = cudaMemsetAsync(sclk, 0, sizeof(DevClock) * 2 * kMaxStages, h->stream))) return e;
+  for (int k = 0; k < 2 * kMaxStages; ++k) {
+    StageMerge &sm = k < kMaxStages ? h->sm : h->sm_b;
+    const int kk = k % kMaxStages;
+    sm.clk[kk] = sclk + k;
+    if ((e = dalloc(h, &sm.mLf[kk], sizeof(int) * nb))) return e;
+    if ((e = dalloc(h, &sm.mRf[kk], sizeof(int) * nb))) return e;
+    if ((e = dalloc(h, &sm.mgeo[kk], sizeof(double) * 4 * nb))) return e;
+    if ((e = dalloc(h, &sm.msd[kk], sizeof(MortSide) * 2 * nb))) return e;
+    if ((e = dalloc(h, &sm.Lstart[kk], sizeof(int) * md.nL))) return e;
+    if ((e = dalloc(h, &sm.Lcount[kk], sizeof(int) * md.nL))) return e;
+    if ((e = dalloc(h, &sm.Rstart[kk], sizeof(int) * md.nR))) return e;
+    if ((e = dalloc(h, &sm.Rcount[kk], sizeof(int) * md.nR))) return e;
+    if ((e = dalloc(h, &sm.work_i[kk], sizeof(int) * (2 * nb + 1)))) return e;
+    if ((e = dalloc(h, &sm.work_d[kk], sizeof(double) * (2 * nb + 1)))) return e;
   }
   if ((e = cudaMemsetAsync(md.CF, 0, w * Ep * 16 * N, h->stream))) return e;
   // zero state
@@ -634,22 +636,28 @@ cudaError_t alloc_buffers(sd_handle *h, const std::vector<int> &zone, const std:
   return cudaStreamSynchronize(h->stream);
 }
 
-// device flags: the OR of the primary clock's and the stage records' (the
-// kernels of a step raise them on their stage's record)
+// device flags: the OR of the primary clock's and the stage records' of both
+// sets (the kernels of a step raise them on their stage's record)
+constexpr int kFlagRecs = 1 + 2 * kMaxStages;
+constexpr size_t kPinnedBytes = 64;  // h_pinned: the flag words, or one double
+static_assert(sizeof(int) * kFlagRecs <= kPinnedBytes, "flag words fit the pinned buffer");
 int read_flags(sd_handle *h, int *flags, bool clear) {
   int *hp = (int *)h->h_pinned;
-  DevClock *rec[1 + kMaxStages] = {h->md.clk};
-  for (int k = 0; k < kMaxStages; ++k) rec[1 + k] = h->sm.clk[k];
+  DevClock *rec[kFlagRecs] = {h->md.clk};
+  for (int k = 0; k < kMaxStages; ++k) {
+    rec[1 + k] = h->sm.clk[k];
+    rec[1 + kMaxStages + k] = h->sm_b.clk[k];
+  }
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 1 + kMaxStages && !e; ++k)
+  for (int k = 0; k < kFlagRecs && !e; ++k)
     if (rec[k]) e = cudaMemcpyAsync(hp + k, &rec[k]->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (!e) e = cudaStreamSynchronize(h->stream);
   if (e) return cuda_fail(h, e, "reading device flags");
   *flags = 0;
-  for (int k = 0; k < 1 + kMaxStages; ++k)
+  for (int k = 0; k < kFlagRecs; ++k)
     if (rec[k]) *flags |= hp[k];
   if (clear && *flags) {
-    for (int k = 0; k < 1 + kMaxStages && !e; ++k)
+    for (int k = 0; k < kFlagRecs && !e; ++k)
       if (rec[k]) e = cudaMemsetAsync(&rec[k]->flags, 0, sizeof(int), h->stream);
     if (!e) e = cudaStreamSynchronize(h->stream);
     if (e) return cuda_fail(h, e, "clearing device flags");
@@ -657,14 +665,22 @@ int read_flags(sd_handle *h, int *flags, bool clear) {
   return SD_OK;
 }
 
+void drop_step_graphs(sd_handle *h) {
+  for (cudaGraphExec_t &g : h->step_exec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
 void free_handle(sd_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
+  drop_step_graphs(h);
   delete h->eng;
   for (void *p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
-  for (cudaEvent_t e : {h->ev_start, h->ev_rest, h->ev_stage0, h->ev_next})
+  for (cudaEvent_t e : {h->ev_start, h->ev_next})
     if (e) cudaEventDestroy(e);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -707,10 +723,11 @@ void rk54_times(double *c) {
 // queue the stages of one step; every stage is  out = in + a0 (base - in) +
 // w_in + bdt L(in)  (RkArgs), which is the Shu-Osher form rewritten around
 // the stage input (the weights of a Shu-Osher stage sum to one)
-// the MeshDev a stage's kernels see: its own clock and mortar table
-MeshDev stage_view(const sd_handle *h, int k) {
+// the MeshDev a stage's kernels see: its own clock and mortar table (of set
+// 0, or of the second set)
+MeshDev stage_view(const sd_handle *h, int k, int set = 0) {
   MeshDev m = h->md;
-  const StageMerge &sm = h->sm;
+  const StageMerge &sm = set ? h->sm_b : h->sm;
   m.clk = sm.clk[k];
   m.mLf = sm.mLf[k];
   m.mRf = sm.mRf[k];
@@ -723,10 +740,10 @@ MeshDev stage_view(const sd_handle *h, int k) {
   return m;
 }
 
-// one stage after the step's merge: common fluxes of the stage's state q,
-// then the volume kernel (divergence, Runge-Kutta combination, traces)
-void queue_stage(sd_handle *h, int k, StatePtr q, StatePtr base, StatePtr out, const RkArgs &rk) {
-  const MeshDev m = stage_view(h, k);
+// one stage after the step's merge (m: the stage's view): common fluxes of
+// the stage's state q, then the volume kernel (divergence, Runge-Kutta
+// combination, traces)
+void queue_stage(sd_handle *h, const MeshDev &m, StatePtr q, StatePtr base, StatePtr out, const RkArgs &rk) {
   h->eng->faces(m, q, h->stream);
   h->eng->mortars(m, h->stream);
   h->eng->volume(m, q, base, out, nullptr, rk, MODE_RK, h->stream);
@@ -734,15 +751,16 @@ void queue_stage(sd_handle *h, int k, StatePtr q, StatePtr base, StatePtr out, c
 
 // The stages of one time step of size dt: per stage the state it reads, the
 // base state, the state it writes, its Runge-Kutta arguments and its view of
-// the mesh (its own clock and mortar table); c[k] = stage time fraction.
-// Returns the number of stages.  Every stage is  out = in + a0 (base - in) +
-// w_in + bdt L(in)  (RkArgs), the Shu-Osher form rewritten around the stage
-// input (the weights of a Shu-Osher stage sum to one).
-int step_plan(sd_handle *h, double dt, BatchStageHost *plan, double *c) {
+// the mesh (its own clock and mortar table, of stage-table set ts); c[k] =
+// stage time fraction.  Returns the number of stages.  Every stage is  out =
+// in + a0 (base - in) + w_in + bdt L(in)  (RkArgs), the Shu-Osher form
+// rewritten around the stage input (the weights of a Shu-Osher stage sum to
+// one).
+int step_plan(sd_handle *h, double dt, BatchStageHost *plan, double *c, int ts = 0) {
   Engine *g = h->eng;
   const StatePtr A = g->A(), B = g->B(), none{nullptr, nullptr};
   auto set = [&](int k, StatePtr in, StatePtr base, StatePtr out, const RkArgs &rk) {
-    plan[k].md = stage_view(h, k);
+    plan[k].md = stage_view(h, k, ts);
     plan[k].in = in;
     plan[k].base = base;
     plan[k].out = out;
@@ -785,47 +803,42 @@ int step_plan(sd_handle *h, double dt, BatchStageHost *plan, double *c) {
 // kernels running at the same time keep their places on those SMs
 constexpr int kSideMergeThreads = 256;
 
-// the step's stage time fractions into h->sm; returns the plan of its stages
-int plan_step(sd_handle *h, double dt, BatchStageHost *plan) {
+// the step's stage time fractions into both stage-table sets; returns the
+// plan of its stages reading set ts
+int plan_step(sd_handle *h, double dt, BatchStageHost *plan, int ts) {
   double c[kMaxStages];
-  const int n = step_plan(h, dt, plan, c);
-  h->sm.n = n;
-  for (int k = 0; k < n; ++k) h->sm.c[k] = c[k];
+  const int n = step_plan(h, dt, plan, c, ts);
+  for (StageMerge *sm : {&h->sm, &h->sm_b}) {
+    sm->n = n;
+    for (int k = 0; k < n; ++k) sm->c[k] = c[k];
+  }
   return n;
 }
 
-// Stage 0's clock and mortar table at the step's start time t_n (before the
-// first captured step of a call; each captured step then merges the next
-// step's stage 0 itself).
-void queue_merge_stage0(sd_handle *h, double dt) {
+// The clocks and tables of every stage of the step starting at t_n, into
+// set 0 (before the first captured step of a call; each captured step then
+// merges the next step into the other set).
+void queue_merge_first(sd_handle *h, double dt) {
   BatchStageHost plan[kMaxStages];
-  plan_step(h, dt, plan);
-  h->eng->merge_stages(h->md, h->sm, dt, 0, 1, 0.0, 1024, h->stream);
+  const int n = plan_step(h, dt, plan, 0);
+  h->eng->merge_stages(h->md, h->sm, dt, 0, n, 0, 1024, h->stream);
 }
 
-// One time step for capture.  The merges depend on time only, so they leave
-// the critical path: stages 1..n-1 are merged on the side stream beside stage
-// 0's kernels, and stage 0 of the next step (at t_n + dt, the value k_advance
-// forms) beside stages 1..n-1, after stage 0's kernels have read its table;
-// then the same side stream advances t_n (only the merges read it).  Stage 0
-// of this step was merged by the previous step or by the prologue.
-void queue_step(sd_handle *h, double dt) {
+// One time step for capture, reading stage-table set ts.  The merges depend
+// on time only, so they leave the critical path: on the side stream, beside
+// the whole step, every stage of the next step (start time t_n + dt, formed
+// as k_advance forms it) is merged into the other set, which no kernel of
+// this step reads; then the side stream advances t_n (only the merges read
+// it) and rejoins at the end of the step.
+void queue_step(sd_handle *h, double dt, int ts) {
   BatchStageHost plan[kMaxStages];
-  const int n = plan_step(h, dt, plan);
-  const StageMerge &sm = h->sm;
+  const int n = plan_step(h, dt, plan, ts);
   cudaEventRecord(h->ev_start, h->stream);
   cudaStreamWaitEvent(h->side, h->ev_start, 0);
-  h->eng->merge_stages(h->md, sm, dt, 1, n - 1, 0.0, kSideMergeThreads, h->side);
-  cudaEventRecord(h->ev_rest, h->side);
-  queue_stage(h, 0, plan[0].in, plan[0].base, plan[0].out, plan[0].rk);
-  cudaEventRecord(h->ev_stage0, h->stream);
-  cudaStreamWaitEvent(h->side, h->ev_stage0, 0);
-  h->eng->merge_stages(h->md, sm, dt, 0, 1, 1.0, kSideMergeThreads, h->side);
+  h->eng->merge_stages(h->md, ts ? h->sm : h->sm_b, dt, 0, n, 1, kSideMergeThreads, h->side);
   h->eng->advance(h->md, dt, h->side);
   cudaEventRecord(h->ev_next, h->side);
-  cudaStreamWaitEvent(h->stream, h->ev_rest, 0);
-  for (int k = 1; k < n; ++k) queue_stage(h, k, plan[k].in, plan[k].base, plan[k].out, plan[k].rk);
-  // the side branch rejoins: the step ends when both have
+  for (int k = 0; k < n; ++k) queue_stage(h, plan[k].md, plan[k].in, plan[k].base, plan[k].out, plan[k].rk);
   cudaStreamWaitEvent(h->stream, h->ev_next, 0);
 }
 
@@ -894,9 +907,9 @@ int sd_create(const sd_mesh *m, int p, const sd_params *prm, sd_handle **out) {
     else if (prm->precision == SD_PREC_FP32_TF32 && !h->eng->set_tensor_cores(true))
       rc = fail(h, SD_ERR_UNSUPPORTED, "no tensor-core contractions in this engine");
   }
-  if (!rc && (ce = cudaMallocHost(&h->h_pinned, 64))) rc = cuda_fail(h, ce, "pinned buffer");
+  if (!rc && (ce = cudaMallocHost(&h->h_pinned, kPinnedBytes))) rc = cuda_fail(h, ce, "pinned buffer");
   if (!rc && (ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking))) rc = cuda_fail(h, ce, "side stream");
-  for (cudaEvent_t *e : {&h->ev_start, &h->ev_rest, &h->ev_stage0, &h->ev_next})
+  for (cudaEvent_t *e : {&h->ev_start, &h->ev_next})
     if (!rc && (ce = cudaEventCreateWithFlags(e, cudaEventDisableTiming))) rc = cuda_fail(h, ce, "events");
   if (!rc) {
     MeshDev &md = h->md;
@@ -1081,27 +1094,32 @@ int sd_step(sd_handle *h, double dt, int nsteps) {
     if ((e = cudaGetLastError())) return cuda_fail(h, e, "trace kernel");
     h->traces_valid = true;
   }
-  if (!h->step_exec || h->graph_dt != dt) {
-    if (h->step_exec) {
-      cudaGraphExecDestroy(h->step_exec);
-      h->step_exec = nullptr;
+  if (!h->step_exec[0] || h->graph_dt != dt) {
+    drop_step_graphs(h);
+    // one captured step per stage-table set it reads; each merges the next
+    // step into the other set
+    for (int ts = 0; ts < 2; ++ts) {
+      cudaGraph_t graph;
+      if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)))
+        return cuda_fail(h, e, "graph capture");
+      queue_step(h, dt, ts);
+      cudaError_t le = cudaGetLastError();
+      e = cudaStreamEndCapture(h->stream, &graph);
+      if (le) return cuda_fail(h, le, "graph capture (launch)");
+      if (e) return cuda_fail(h, e, "graph capture (end)");
+      e = cudaGraphInstantiate(&h->step_exec[ts], graph, 0);
+      cudaGraphDestroy(graph);
+      if (e) {
+        drop_step_graphs(h);
+        return cuda_fail(h, e, "graph instantiate");
+      }
     }
-    cudaGraph_t graph;
-    if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal))) return cuda_fail(h, e, "graph capture");
-    queue_step(h, dt);
-    cudaError_t le = cudaGetLastError();
-    e = cudaStreamEndCapture(h->stream, &graph);
-    if (le) return cuda_fail(h, le, "graph capture (launch)");
-    if (e) return cuda_fail(h, e, "graph capture (end)");
-    e = cudaGraphInstantiate(&h->step_exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e) return cuda_fail(h, e, "graph instantiate");
     h->graph_dt = dt;
   }
-  queue_merge_stage0(h, dt);
-  if ((e = cudaGetLastError())) return cuda_fail(h, e, "merge kernel");
+  queue_merge_first(h, dt);
+  if ((e = cudaGetLastError())) return cuda_fail(h, e, "merge kernels");
   for (int k = 0; k < nsteps; ++k)
-    if ((e = cudaGraphLaunch(h->step_exec, h->stream))) return cuda_fail(h, e, "graph launch");
+    if ((e = cudaGraphLaunch(h->step_exec[k & 1], h->stream))) return cuda_fail(h, e, "graph launch");
   return SD_OK;
 }
 
@@ -1139,10 +1157,7 @@ int sd_test_wait_timeout(sd_handle *h, int on) {
   if (e) return cuda_fail(h, e, "sd_test_wait_timeout");
   h->md.test_tx_extra = on ? 16 : 0;
   h->md.test_poll = on ? 4096 : 0;
-  if (h->step_exec) {  // the captured step holds the mesh view by value
-    cudaGraphExecDestroy(h->step_exec);
-    h->step_exec = nullptr;
-  }
+  drop_step_graphs(h);  // the captured steps hold the mesh view by value
   return SD_OK;
 }
 

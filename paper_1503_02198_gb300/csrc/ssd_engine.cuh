@@ -704,14 +704,16 @@ __device__ __forceinline__ ddang dd_rotation_angle(double om, double t) {
 // merged positions and angles.  The CTA of interface 0 also writes the stage
 // clock of every zone: theta_z = omega_z t_stage.  The offsets and scales of
 // Eq. xz of each mortar against its faces are formed here too, for the mortar
-// flux kernels of the stage.  The step's start time t_n is read from *tsrc;
-// the stage clock and the tables are written through md.
+// flux kernels of the stage.  The step's start time t_n is read from *tsrc
+// (ahead: the next step's, t_n + dt, formed as k_advance forms it); the stage
+// clock and the tables are written through md.
 static __device__ void clock_merge_body(const MeshDev &md, int ii, double c, double dt, int *work_i,
-                                        double *work_d, const DevClock *tsrc) {
+                                        double *work_d, const DevClock *tsrc, bool ahead = false) {
   extern __shared__ double s_ang[];  // [nb] high parts (rotated L, then R), [nb] low parts
   __shared__ double s_th2, s_th2lo;
   __shared__ int s_k0;
-  const double ts = tsrc->t_n + c * dt;
+  const double t0 = ahead ? tsrc->t_n + dt : tsrc->t_n;
+  const double ts = t0 + c * dt;
   // the zone clocks on warp 1, beside warp 0's angle of this interface
   if (ii == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + kZT) {
     DevClock *k = md.clk;
@@ -886,9 +888,8 @@ static __global__ void k_clock_merge(MeshDev md, double c, double dt, int *work_
 }
 
 // block (x, ii): the clock and interface ii's mortar table of stage b = b0 + x
-// of a step, at t_n + (c_b + cadd) dt (cadd = 1: stage b of the next step,
-// whose start time t_n + dt is formed as k_advance forms it)
-static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt, int b0, double cadd) {
+// of a step (ahead: of the next step)
+static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt, int b0, int ahead) {
   pdl_enter();
   const int b = b0 + (int)blockIdx.x;
   MeshDev m = md;
@@ -900,7 +901,7 @@ static __global__ void k_clock_merge_stages(MeshDev md, StageMerge sm, double dt
   m.Rstart = sm.Rstart[b];
   m.Rcount = sm.Rcount[b];
   m.mgeo = sm.mgeo[b];
-  clock_merge_body(m, blockIdx.y, sm.c[b] + cadd, dt, sm.work_i[b], sm.work_d[b], md.clk);
+  clock_merge_body(m, blockIdx.y, sm.c[b], dt, sm.work_i[b], sm.work_d[b], md.clk, ahead != 0);
 }
 
 // block (x, y): Eq. xz of mortars [x kXzBlock / 2 ...) of stage b0 + y
@@ -2392,10 +2393,10 @@ struct EngineImpl : Engine {
     if (md.nM > 0) launch_pdl(k_mortar_xz, xz_blocks(md), kXzBlock, 0, s, md);
   }
 
-  void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, int first, int count, double cadd,
+  void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, int first, int count, int ahead,
                     int threads, cudaStream_t s) override {
     if (count <= 0) return;
-    launch_pdl(k_clock_merge_stages, dim3(count, md.nI), threads, merge_smem, s, md, sm, dt, first, cadd);
+    launch_pdl(k_clock_merge_stages, dim3(count, md.nI), threads, merge_smem, s, md, sm, dt, first, ahead);
     if (md.nM > 0) launch_pdl(k_mortar_xz_stages, dim3(xz_blocks(md), count), kXzBlock, 0, s, md, sm, first);
   }
   static unsigned xz_blocks(const MeshDev &md) { return (unsigned)((2 * md.nM + kXzBlock - 1) / kXzBlock); }

@@ -235,10 +235,11 @@ struct Engine {
   // doubles: 2 (nL + nR) + 1)
   virtual void clock_merge_into(const MeshDev &md, double c, double dt, int *work_i, double *work_d,
                                 cudaStream_t s) = 0;
-  // the clocks and mortar tables of stages first .. first + count - 1 of a
-  // step in one launch, at t_n + (c_k + cadd) dt (t_n read from md.clk), CTAs
-  // of the given size
-  virtual void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, int first, int count, double cadd,
+  // the clocks, mortar tables and mortar offsets (Eq. xz) of stages first ..
+  // first + count - 1 of a step, at t_n + c_k dt (t_n read from md.clk; with
+  // ahead, of the next step: t_n + dt in place of t_n), merge CTAs of the
+  // given size
+  virtual void merge_stages(const MeshDev &md, const StageMerge &sm, double dt, int first, int count, int ahead,
                             int threads, cudaStream_t s) = 0;
   // q: the stage's state (the viscous chain needs its gradients)
   virtual void faces(const MeshDev &md, StatePtr q, cudaStream_t s) = 0;
