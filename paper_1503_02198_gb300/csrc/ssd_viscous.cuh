@@ -705,21 +705,24 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
     }
     if (MODE == MODE_RK) {
       __syncthreads();
-      // ---- phase 3: face traces of the new state, one thread per SP line ----
-      if (fi == 1 && le < ne) {
-        T *tr = (T *)md.TR + (size_t)(e0 + le) * 16 * N;
-        const int fa = d == 0 ? 3 : 0, fb = d == 0 ? 1 : 2;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
+      // ---- phase 3: face traces of the new state, one thread per SP line
+      // and variable (all the CTA's threads take part) ----
+      for (int q = threadIdx.x; q < 4 * C::LINES; q += NT) {
+        const int v = q / C::LINES, ln = q - v * C::LINES;
+        const int l3 = ln / (2 * N), r3 = ln - l3 * 2 * N;
+        const int d3 = r3 / N, m3 = r3 - d3 * N;
+        if (l3 < ne) {
+          T *tr = (T *)md.TR + (size_t)(e0 + l3) * 16 * N;
+          const int fa = d3 == 0 ? 3 : 0, fb = d3 == 0 ? 1 : 2;
           T a0 = 0, a1 = 0;
 #pragma unroll
           for (int k = 0; k < N; ++k) {
-            const T qk = d == 0 ? sQ[le][v][m * N + k] : sQ[le][v][k * N + m];
+            const T qk = d3 == 0 ? sQ[l3][v][m3 * N + k] : sQ[l3][v][k * N + m3];
             a0 += qk * B.H0[k];
             a1 += qk * B.H1[k];
           }
-          tr[(fa * 4 + v) * N + m] = a0;
-          tr[(fb * 4 + v) * N + m] = a1;
+          tr[(fa * 4 + v) * N + m3] = a0;
+          tr[(fb * 4 + v) * N + m3] = a1;
         }
       }
     }
