@@ -150,6 +150,14 @@ template <typename T>
 __device__ __forceinline__ T mul_sub(T a, T b, T c, T d) {
   return fma(a, b, -(c * d));
 }
+// a state value set that is physical: rho > 0, p > 0 and E finite.  With
+// rho > 0, p = (gamma - 1) (E - |m|^2 / (2 rho)) > 0 is 2 E rho > |m|^2,
+// which needs no division.
+template <typename T>
+__device__ __forceinline__ bool physical(const T *q) {
+  return q[0] > T(0) && T(2) * q[3] * q[0] - mul_add(q[1], q[1], q[2], q[2]) > T(0) && isfinite(q[3]);
+}
+
 // a product that is never fused into a later addition
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
@@ -2026,8 +2034,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX, TC>::THREADS,
           qn[v] = qk + inc;
           if (va.w_out) va.w_out[gi + v * NN] = (T)mul_sub((double)va.rk.ddt, R, (double)va.rk.g, inc);
         }
-        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * mul_add(qn[1], qn[1], qn[2], qn[2]) * recip(qn[0]));
-        bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
+        bad |= !physical(qn);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           qo[gi + v * NN] = qn[v];
@@ -2069,8 +2076,7 @@ __global__ void __launch_bounds__(VolCfg<T, N, OTF, AUX, LO, EPBX, TC>::THREADS,
           }
           if (va.w_out) va.w_out[gi + v * NN] = (T)fmaf(-(float)va.rk.g, inc, (float)va.rk.ddt * R);
         }
-        const float pr = (float)gm1 * (hv[3] - 0.5f * mul_add(hv[1], hv[1], hv[2], hv[2]) * __frcp_rn(hv[0]));
-        bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
+        bad |= !physical(hv);
 #pragma unroll
         for (int v = 0; v < 4; ++v) sQ[l2][(v) * NN + sp] = (T)hv[v];
       }

@@ -627,8 +627,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           }
           if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
         }
-        const float pr = (float)gm1 * (hv[3] - 0.5f * mul_add(hv[1], hv[1], hv[2], hv[2]) / hv[0]);
-        bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
+        bad |= !physical(hv);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           sQ[l2][v][sp] = (T)hv[v];
@@ -660,8 +659,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           qn[v] = qk + inc;
           if (w_out) w_out[ii] = (T)mul_sub((double)rk.ddt, R, (double)rk.g, inc);
         }
-        const double pr = (md.gamma - 1.0) * (qn[3] - 0.5 * mul_add(qn[1], qn[1], qn[2], qn[2]) * recip(qn[0]));
-        bad |= !(qn[0] > 0.0) || !(pr > 0.0) || !isfinite(qn[3]);
+        bad |= !physical(qn);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           ((double *)out.hi)[gi + v * NN] = qn[v];
@@ -697,8 +695,7 @@ __global__ void __launch_bounds__(VisVolCfg<T, N>::THREADS, VisVolCfg<T, N>::MIN
           }
           if (w_out) w_out[ii] = (T)fmaf(-(float)rk.g, inc, (float)rk.ddt * R);
         }
-        const float pr = (float)gm1 * (hv[3] - 0.5f * mul_add(hv[1], hv[1], hv[2], hv[2]) / hv[0]);
-        bad |= !(hv[0] > 0.0f) || !(pr > 0.0f) || !isfinite(hv[3]);
+        bad |= !physical(hv);
 #pragma unroll
         for (int v = 0; v < 4; ++v) sQ[l2][v][sp] = (T)hv[v];
       }

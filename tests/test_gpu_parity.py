@@ -158,6 +158,25 @@ def test_full_size_vortex_residual_fp64(ssd, oracle_mod):
     _check(s.sd_residual(), o.extended().residual(Q, 1.1), TOL64)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_negative_pressure_is_reported(ssd, precision):
+    # positive density, kinetic energy above the total energy in one element:
+    # p = (gamma - 1) (E - |m|^2 / (2 rho)) < 0
+    m = small_rotor()
+    s = ssd.Solver(m, 2, FlowParams(omega=0.5), precision=precision)
+    Q = s.state_from(lambda x, y: fields.uniform(x, y))
+    Q[5, 1] = 3.0 * Q[5, 0]  # momentum 3 rho per unit density
+    Q[5, 3] = 0.5 * Q[5, 0]  # E = rho / 2 < |m|^2 / (2 rho) = 4.5 rho
+    s.sd_set_state(Q)
+    s.sd_step(1e-4, 1)
+    with pytest.raises(ssd.SSDError) as ei:
+        s.sd_sync()
+    assert ei.value.code == ssd.SD_ERR_NONPHYSICAL
+    s.sd_set_state(s.state_from(lambda x, y: fields.uniform(x, y)))
+    s.sd_step(1e-4, 1)
+    s.sd_sync()
+
+
 def test_non_physical_state_is_reported(ssd, oracle_mod):
     m = small_rotor()
     s = ssd.Solver(m, 2, FlowParams(omega=0.5))
