@@ -101,8 +101,8 @@ class ClockSampler:
 # kernel source it was taken on: SHA-256 of the engine text that k_volume is
 # built from (the ElemGeo metrics and VolCfg through the end of k_volume);
 # otherwise null.
-PROFILED_TRAFFIC = {"bytes": (389.22e6 + 329.38e6 + 673.64e6 + 331.13e6 + 673.64e6 + 329.97e6) / 3,
-                    "kernel_sha256": "de5b15ca7413870bdc0b262478b67ca117fbab9a5afb50eef15abb2879f1b625"}
+PROFILED_TRAFFIC = {"bytes": (389.24e6 + 329.19e6 + 673.61e6 + 330.98e6 + 673.61e6 + 329.99e6) / 3,
+                    "kernel_sha256": "a0b69d8a258bb927263a36452dae5090358f52f539841020eb6f8259deb59657"}
 
 
 def volume_kernel_source():
