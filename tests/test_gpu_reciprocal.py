@@ -1,8 +1,8 @@
-"""The kernels' reciprocal 1/x (density and Jacobian reciprocals): in FP64
-Newton's iteration from the hardware's approximate reciprocal, in FP32 the
-correctly rounded reciprocal.  Checked against the exact reciprocal of the
-FP64 input (numpy's IEEE division) over magnitudes from 1e-8 to 1e8: within
-one ulp in FP64, exact after rounding to float in FP32."""
+"""The kernels' reciprocal 1/x (density and Jacobian reciprocals): Newton's
+iteration from the hardware's approximate reciprocal, two steps in FP64, one
+in FP32.  Checked against the exact reciprocal (numpy's IEEE division of the
+input in the same precision) over magnitudes from 1e-8 to 1e8: within one ulp
+in both, and correctly rounded for most inputs."""
 import numpy as np
 import pytest
 
@@ -40,11 +40,14 @@ def test_fp64_reciprocal_within_one_ulp(ssd):
     s.close()
 
 
-def test_fp32_reciprocal_correctly_rounded(ssd):
+def test_fp32_reciprocal_within_one_ulp(ssd):
     s = ssd.Solver(small_rotor(), 2, FlowParams(omega=0.5), precision=ssd.SD_PREC_FP32)
     xf = _inputs().astype(np.float32)
-    y = s.sd_test_reciprocal(xf.astype(np.float64))
-    assert np.array_equal(y.astype(np.float32), (np.float32(1.0) / xf))
+    y = s.sd_test_reciprocal(xf.astype(np.float64)).astype(np.float32)
+    exact = np.float32(1.0) / xf
+    ulps = np.abs(y.astype(np.float64) - exact) / np.spacing(np.abs(exact)).astype(np.float64)
+    assert ulps.max() <= 1.0, (ulps.max(), xf[np.argmax(ulps)])
+    assert np.mean(ulps == 0) > 0.9
     s.close()
 
 
