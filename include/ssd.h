@@ -205,8 +205,13 @@ int sd_residual(sd_handle *h, double *R, int on_device);
 
 /* Advance nsteps steps of size dt with the SSP Runge-Kutta scheme chosen by
  * sd_params.rk_stages (Sec. 3: three stages at t, t + dt, t + dt/2; Sec. 4:
- * five stages); the mortar connectivity is rebuilt at every stage (Sec. 3.2).  Asynchronous: queued on the stream as CUDA-graph
- * launches; errors detected on the device are reported by sd_sync. */
+ * five stages); the mortar connectivity is rebuilt at every stage (Sec. 3.2).
+ * Asynchronous: queued on the handle's stream as two kernel launches (the
+ * stage clocks and mortar tables of the first step) and nsteps CUDA-graph
+ * launches; each captured step also merges the next step's stages on a
+ * second stream of the handle, beside its own kernels, and rejoins before it
+ * ends, so the result is the same as merging each step after the last.
+ * Errors detected on the device are reported by sd_sync. */
 int sd_step(sd_handle *h, double dt, int nsteps);
 
 /* Wait for queued work; returns SD_ERR_NONPHYSICAL if a stage produced
@@ -225,8 +230,8 @@ int sd_test_wait_timeout(sd_handle *h, int on);
 
 /* Test aid for the handle's reciprocal 1/x (the density and Jacobian
  * reciprocals of its kernels): y[i] = 1 / x[i] computed on the GPU in the
- * handle's compute type (FP64: Newton's iteration from the hardware's
- * approximate reciprocal; FP32: the correctly rounded reciprocal), for n host
+ * handle's compute type (Newton's iteration from the hardware's approximate
+ * reciprocal: two steps in FP64, one in FP32; within one ulp), for n host
  * values x (normal, finite, non-zero) into host y.  Allocates and frees a
  * device buffer of 16 n bytes; synchronises.  SD_ERR_ARG for n < 0 or null
  * arrays with n > 0. */
@@ -308,8 +313,8 @@ int sd_fma_peak(sd_handle *h, int precision, double *tflops);
  * call with a host R; this variant allocates nothing.  (The paper has no
  * counterpart: this is a deployment aid, not part of the method.)
  *
- * Work memory: the mortar table, the mortar flux contributions, the merge
- * work arrays and, when R is host memory, the device copy of R all live in one
+ * Work memory: the mortar table and mortar offsets (Eq. xz), the mortar flux
+ * contributions, the merge work arrays and, when R is host memory, the device copy of R all live in one
  * fixed 16 MiB device array inside the library, which every GPU that loads the
  * library holds until the process exits.  Calls needing more than 16 MiB
  * return SD_ERR_ARG with a message (with R in host memory the state copy,
